@@ -1,0 +1,444 @@
+#!/usr/bin/env python
+"""DARE benchmark: resliced Mpix/s and slice latency, 512^2 planes from a 256^3
+directional volume, against the plain FP32 path.
+
+One step = one pass of the whole hot path over one batch of synthetic input:
+empty the volume, rebuild it from the 1600 tracked sweep frames (scatter +
+finalize, Fig. 1), then reslice the 1000-pose trajectory (Eq. 1 / Eq. 2
+weight tables + the tiled reslice, Fig. 2) into 512 x 512 FP32 images and
+coverage masks.  Inputs are resident on the device when the timed region
+starts; the volume (1.3 GB), frames (210 MB) and outputs (1 GB) are all
+larger than L2, so no extra flush is needed.
+
+    python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Prints one JSON line (rank 0).  Under torchrun each rank runs its own
+independent workload (weak scaling: sessions do not exchange data).
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "resliced Mpix/s and p50/p99 slice latency (512² from 256³) vs plain FP32 path"
+WORKLOAD = "dare_256cube_1600f_512px"
+DTYPE_NAMES = {"u8": 0, "f16": 1, "bf16": 2, "f32": 3}
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["dare", "reference"], default="dare")
+    ap.add_argument("--poses", type=int, default=1000)
+    ap.add_argument("--dtype", choices=list(DTYPE_NAMES), default="f32")
+    ap.add_argument("--slots", type=int, default=12)
+    ap.add_argument("--path", choices=["tiled", "plain"], default="tiled")
+    ap.add_argument("--quick", action="store_true", help="main timed loop only (for profiler runs)")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- distributed plumbing
+
+class Dist:
+    def __init__(self):
+        self.world = int(os.environ.get("WORLD_SIZE", "1"))
+        self.rank = int(os.environ.get("RANK", "0"))
+        self.local = int(os.environ.get("LOCAL_RANK", "0"))
+        self.pg = None
+        if self.world > 1:
+            import torch.distributed as dist
+            backend = "nccl" if self._cuda() else "gloo"
+            dist.init_process_group(backend)
+            self.pg = dist
+
+    @staticmethod
+    def _cuda():
+        import torch
+        return torch.cuda.is_available()
+
+    def barrier(self):
+        if self.pg:
+            self.pg.barrier()
+
+    def max(self, x):
+        if not self.pg:
+            return x
+        import torch
+        t = torch.tensor([float(x)], device=f"cuda:{self.local}" if self._cuda() else "cpu")
+        self.pg.all_reduce(t, op=self.pg.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.pg:
+            self.pg.destroy_process_group()
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "50", "-i", str(self.device)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.t.join(timeout=5)
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+                power.append(float(parts[3]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm),
+                "power_w_max": max(power) if power else None}
+
+
+# ---------------------------------------------------------------- helpers
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6400.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("kernels_tiled.cu", "device_common.cuh", "dare_internal.h"):
+        with open(os.path.join(ROOT, "paper_2605_26325_b300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(kernel, n_slices):
+    """DRAM bytes per launch from the committed ncu summary, scaled per slice;
+    None when the kernel source changed since the counters were taken."""
+    path = os.path.join(ROOT, "profiles", "reslice_tiled_dram_traffic.txt")
+    try:
+        kv = dict(line.split("=", 1) for line in open(path).read().split("\n") if "=" in line and not line.startswith("#"))
+    except OSError:
+        return None
+    if kv.get("kernel", "").strip() != kernel or kv.get("src_sha256_16", "").strip() != kernel_source_hash():
+        return None
+    try:
+        return float(kv["dram_bytes_per_slice"]) * n_slices
+    except (KeyError, ValueError):
+        return None
+
+
+def percentile(xs, q):
+    return float(np.percentile(np.asarray(xs), q))
+
+
+# ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
+
+def cpu_baseline(w, n_poses, slots, n_res=8):
+    import oracle
+    t = time.perf_counter()
+    vol = oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames, w.frame_poses, w.frame_px,
+                       oracle.F32, slots)
+    t_build = time.perf_counter() - t
+    t = time.perf_counter()
+    for T in w.reslice_poses[:n_res]:
+        oracle.reslice(vol, T, w.out_w, w.out_h, w.out_px)
+    t_res = (time.perf_counter() - t) / n_res
+    full = t_build + n_poses * t_res
+    px = n_poses * w.out_w * w.out_h
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": px / full / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 oracle on the host: full reconstruction of the {len(w.frames)} frames "
+                       f"(single-threaded, {t_build:.1f} s) + {n_res} of the {n_poses} 512x512 reslices "
+                       f"({t_res * 1e3:.0f} ms each, OpenMP over {cores} threads), extrapolated to one step"),
+            "ms_per_step": full * 1e3}, vol
+
+
+def run_reference(args, dist):
+    if dist.rank != 0:
+        return
+    import oracle
+    import synth
+    w = synth.working_workload(1, n_poses=args.poses)
+    log("reference: building the full oracle volume (untimed)")
+    vol = oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames, w.frame_poses, w.frame_px,
+                       oracle.F32, args.slots)
+    n_res, sub = 4, 400
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+    def step(k):
+        t = time.perf_counter()
+        a = (k * sub) % len(w.frames)
+        oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames[a:a + sub], w.frame_poses[a:a + sub],
+                     w.frame_px, oracle.F32, args.slots)
+        t_b = (time.perf_counter() - t) * len(w.frames) / sub
+        t = time.perf_counter()
+        for j in range(n_res):
+            oracle.reslice(vol, w.reslice_poses[(k * n_res + j) % args.poses], w.out_w, w.out_h, w.out_px)
+        t_r = (time.perf_counter() - t) / n_res
+        return t_b + args.poses * t_r
+
+    for k in range(args.warmup):
+        step(k)
+    times = [step(args.warmup + k) for k in range(args.steps)]
+    full = sum(times) / len(times)
+    px = args.poses * w.out_w * w.out_h
+    value = px / full / 1e6
+    sample = (f"each step: FP64 oracle reconstruction of {sub} of the {len(w.frames)} frames (x{len(w.frames)//sub}) "
+              f"+ {n_res} of the {args.poses} 512x512 reslices (x{args.poses // n_res}) on the full oracle volume, "
+              f"on {cores} host threads")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "poses": args.poses, "storage": "f64 (oracle)"},
+            "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def run_dare(args, dist):
+    import torch
+
+    import paper_2605_26325_b300 as dare
+    import synth
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    device = f"cuda:{dev}"
+    seed = 1 + dist.rank
+    t0 = time.perf_counter()
+    w = synth.working_workload(seed, n_poses=args.poses)
+    log(f"rank {dist.rank}: workload ready in {time.perf_counter() - t0:.1f} s")
+    P, W, H = args.poses, w.out_w, w.out_h
+    dtype = DTYPE_NAMES[args.dtype]
+    s = dare.Session(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, dtype=dtype, max_slots=args.slots,
+                     device=dev, flags=0 if args.quick else dare.DARE_SESSION_SCALAR)
+    stream = torch.cuda.current_stream()
+    frames_d = torch.from_numpy(w.frames).to(device)
+    outs = torch.empty((P, H, W), dtype=torch.float32, device=device)
+    masks = torch.empty((P, H, dare.mask_words(W)), dtype=torch.int32, device=device)
+    reqs = dare.make_requests([(s, w.reslice_poses[i], outs[i], masks[i], w.out_px) for i in range(P)])
+    path = dare.DARE_PATH_TILED if args.path == "tiled" else dare.DARE_PATH_PLAIN
+    params = dare.params_default(path=path)
+
+    def step():
+        s.reset(stream)
+        s.build(frames_d, w.frame_poses, w.frame_px, stream)
+        dare.reslice_batch(reqs, params, stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize()
+    info = s.info()
+    if info.overflow_voxels:
+        log(f"warning: {info.overflow_voxels} voxels hit the {args.slots}-slot capacity")
+    dist.barrier()
+    torch.cuda.synchronize()
+    dare.trace_read()
+    dare.trace_enable(True)
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.1)
+    n0 = dare.launch_count()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    launches = dare.launch_count() - n0
+    clk = clocks.stop()
+    dare.trace_enable(False)
+    trace = dare.trace_read()
+    dist.barrier()
+    ms_total = dist.max(e0.elapsed_time(e1))
+    ms_step = ms_total / args.steps
+    px_step = P * W * H * dist.world
+    value = px_step / (ms_step * 1e-3) / 1e6
+
+    # roofline of the dominant kernel
+    top = max(trace.items(), key=lambda kv: kv[1][1])
+    per_launch_ms = {k: v[1] / max(v[0], 1) for k, v in trace.items()}
+    fp = s.footprint(w.reslice_poses, W, H, w.out_px)
+    rec_bytes = info.record_bytes
+    reslice_alg = float(fp.sum() * rec_bytes + P * (W * H * 4 + H * dare.mask_words(W) * 4) + P * info.n_frames * 4)
+    alg = {"reslice_tiled": reslice_alg, "reslice_plain": reslice_alg}
+    peak, peak_kind = peaks()
+    roof = None
+    if top[0] in alg:
+        achieved = alg[top[0]] / (per_launch_ms[top[0]] * 1e-3) / 1e9
+        roof = {"kernel": top[0], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": profiled_traffic(top[0], P),
+                "algorithmic_bytes_per_launch": alg[top[0]], "launch_ms": per_launch_ms[top[0]],
+                "footprint_voxels_per_slice": float(fp.mean()), "record_bytes": rec_bytes}
+    line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": dist.world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "grid": "256^3 @ 0.4 mm", "frames": int(len(w.frames)),
+                       "frame_px": "256x512 @ 0.2 mm", "poses": P, "out_px": f"{W}x{H} @ 0.2 mm",
+                       "storage": args.dtype, "slots": args.slots, "path": args.path, "weights": "f32",
+                       "step": "reset + rebuild volume from all frames + reslice every pose",
+                       "l2": "inputs larger than L2 (volume, frames and outputs each > 126 MB); no flush",
+                       "parallelism": f"replicas x{dist.world}"},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"], "power_w_max": clk.get("power_w_max")},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(trace.items())}}
+
+    if not args.quick:
+        extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, params, line, step, P, W, H)
+        if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
+            del s
+            torch.cuda.synchronize()
+            cb, _ = cpu_baseline(w, P, args.slots)
+            line["cpu_baseline"] = cb
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, params, line, step, P, W, H):
+    """End-to-end arm, per-slice latency, and the comparators (plain FP32 and scalar trilinear)."""
+    # --- end to end through the public API with host buffers
+    frames_h = torch.from_numpy(w.frames).pin_memory()
+    outs_h = torch.empty(outs.shape, dtype=outs.dtype).pin_memory()
+    masks_h = torch.empty(masks.shape, dtype=masks.dtype).pin_memory()
+
+    def e2e_step():
+        frames_d.copy_(frames_h, non_blocking=True)
+        step()
+        outs_h.copy_(outs, non_blocking=True)
+        masks_h.copy_(masks, non_blocking=True)
+
+    n_e2e = max(2, min(args.steps, 10))
+    e2e_step()
+    torch.cuda.synchronize()
+    dist.barrier()
+    t = time.perf_counter()
+    for _ in range(n_e2e):
+        e2e_step()
+    torch.cuda.synchronize()
+    dt = dist.max((time.perf_counter() - t) / n_e2e)
+    h2d = frames_h.numel() + w.frame_poses.nbytes + P * 16 * 8
+    d2h = outs_h.numel() * 4 + masks_h.numel() * 4
+    line["e2e"] = {"value": P * W * H * dist.world / dt / 1e6, "unit": "Mpix/s", "h2d_bytes_per_step": int(h2d),
+                   "d2h_bytes_per_step": int(d2h), "ms_per_step": dt * 1e3,
+                   "note": "H2D of the frames from pinned host memory, poses from host arrays, D2H of every image "
+                           "and mask, all inside the timed region"}
+
+    # --- reslice-only throughput of each path (volume resident) and build-only time
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    plain = dare.params_default(path=dare.DARE_PATH_PLAIN)
+    tiled = dare.params_default(path=dare.DARE_PATH_TILED)
+    ms_tiled = timed(lambda: dare.reslice_batch(reqs, tiled, stream), 5)
+    ms_plain = timed(lambda: dare.reslice_batch(reqs, plain, stream), 3)
+
+    def build_only():
+        s.reset(stream)
+        s.build(frames_d, w.frame_poses, w.frame_px, stream)
+
+    ms_build = timed(build_only, 5)
+    ms_scalar = timed(lambda: [s.reslice_scalar(w.reslice_poses[i], outs[i], masks[i], w.out_px, stream=stream)
+                               for i in range(P)], 2)
+    px = P * W * H
+    line["paths_mpix_s"] = {"tiled_batched": px / ms_tiled / 1e3, "plain_fp32_batched": px / ms_plain / 1e3,
+                            "scalar_trilinear": px / ms_scalar / 1e3}
+    line["build_ms"] = ms_build
+
+    # --- per-slice latency: query (host call) to image ready on the device
+    def lat(p, n=200):
+        out1 = outs[0]
+        m1 = masks[0]
+        xs = []
+        for i in range(n):
+            T = w.reslice_poses[i % P]
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            s.reslice(T, out1, m1, w.out_px, p, stream=stream)
+            torch.cuda.synchronize()
+            xs.append((time.perf_counter() - t) * 1e3)
+        return {"p50_ms": percentile(xs, 50), "p99_ms": percentile(xs, 99), "samples": n}
+
+    line["latency"] = {"tiled": lat(tiled), "plain_fp32": lat(plain),
+                       "note": "wall time from the host call to the 512x512 image and mask on the device, "
+                               "one plane per call"}
+
+
+def main():
+    args = parse()
+    dist = Dist()
+    try:
+        if args.impl == "reference":
+            run_reference(args, dist)
+        else:
+            run_dare(args, dist)
+    finally:
+        dist.close()
+
+
+if __name__ == "__main__":
+    main()

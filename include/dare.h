@@ -1,0 +1,349 @@
+/*
+ * dare.h -- C ABI of libdare, a CUDA (sm_103a) implementation of DARE,
+ * Directionality-Aware Reslicing of tracked freehand ultrasound
+ * (Jaeggi, Black, Salcudean).
+ *
+ * DARE has two operations:
+ *   - reconstruction (Sec. 2.1 "Volume reconstruction", Fig. 1): tracked 2D
+ *     frames are placed at their poses and voxelised; every voxel keeps a
+ *     list of samples, each an intensity with the orientation of the frame it
+ *     came from;
+ *   - reslicing (Sec. 2.1 "Reslicing", Eq. 1, Eq. 2, Fig. 2): every pixel of a
+ *     virtual plane gathers the samples of its voxel neighbourhood, drops
+ *     samples whose orientation disagrees with the plane's beyond angular
+ *     thresholds, and averages the rest with exponential orientation weights
+ *     (times a distance weight); a pixel with no valid sample is unassigned.
+ *
+ * ---------------------------------------------------------------- conventions
+ * Units are mm.  Poses are row-major 4x4 FP64 rigid transforms.
+ *
+ * Image frame: pixel (u, v) of a W x H image with spacing (sx, sy) sits at
+ * image point q = ((u - (W-1)/2) sx, v sy, 0).  Image x is the lateral
+ * (in-plane) direction of Eq. 1, image y the beam (depth) direction, image z
+ * = x cross y the elevation.
+ *
+ * Grid: dims (nx, ny, nz), spacing h, vol_to_world V.  Voxel (i, j, k) has
+ * its centre at V * (i h, j h, k h); its linear index is i + nx (j + ny k).
+ *
+ * Fixed-point geometry.  For a plane with pose T, the pixel -> voxel map is
+ * g(u, v) = G0 + u A + v B, all in units of 2^-20 voxel (int64), where
+ * G0, A, B are the FP64 values below multiplied by 2^20 and rounded to the
+ * nearest integer, ties to even.  Canonical FP64 evaluation order (no fused
+ * multiply-add; sums left to right), with R_v, t_v and R_t, t_t the rotation
+ * and translation of V and T:
+ *     d    = t_t - t_v
+ *     c0_r = R_v[0][r] R_t[0][0] + R_v[1][r] R_t[1][0] + R_v[2][r] R_t[2][0]
+ *     c1_r = (same with column 1 of R_t)
+ *     tm_r = R_v[0][r] d[0] + R_v[1][r] d[1] + R_v[2][r] d[2]
+ *     G0_r = (tm_r - (0.5 (W-1) sx) c0_r) / h,  A_r = (c0_r sx) / h,
+ *     B_r  = (c1_r sy) / h
+ * Every later index, weight and coverage decision uses these integers, so
+ * any two correct implementations agree on them bit for bit.
+ *
+ * Reconstruction (Fig. 1): a frame pixel lands in the voxel
+ * floor(g / 2^20 + 1/2) per axis (nearest voxel, ties up); pixels outside the
+ * grid are dropped.  One sample is kept per (voxel, frame): the frame id and
+ * the mean of that frame's pixels in the voxel, stored as
+ * round_dtype(RN_fp32(sum / npix)) (u8: round-half-even, clamped to
+ * [0, 255]; f16, bf16: round-to-nearest-even).  The frame's orientation
+ * (the paper stores it as a quaternion per sample) lives once per frame in
+ * the session's frame table; a sample refers to it by frame id.  A voxel
+ * holds at most max_slots samples: beyond that it keeps the samples of
+ * largest npix (ties: lower frame id).
+ *
+ * Reslicing (Eq. 1, Eq. 2): for a sample of frame f and a plane r, with n =
+ * the "acquisition normal" (beam direction R y by default; the image-plane
+ * normal R z on request) and x = the lateral direction R x, both expressed
+ * in the volume frame:
+ *     d_normal = n_f . n_r            (signed)
+ *     d_inplane = |x_f . x_r|
+ *     valid iff d_normal >= cos(thr_normal) and d_inplane >= cos(thr_inplane)
+ *       (a threshold of 180 degrees or more is off)
+ *     w_f = exp(k_normal (d_normal - 1) + k_inplane (d_inplane - 1))
+ * The decisions are taken in FP64 once per (plane, frame).  With the TENT
+ * distance kernel of radius R = 1 (the default; R is the interpolation
+ * distance in voxels) a pixel at g reads the 8 voxels floor(g) + {0,1}^3
+ * with trilinear weights t_c, and
+ *     out = sum t_c w_f I / sum t_c w_f   over the valid samples of those
+ *           voxels, accumulated in FP32;
+ *     a pixel whose denominator is 0 is unassigned: its mask bit is 0 and it
+ *     receives params.unassigned.
+ *
+ * Layouts.
+ *   frames_dev: n x H x W uint8, row-major, frame-major (device memory).
+ *   out_dev:    H x W float32, row-major (device memory).
+ *   mask_dev:   H rows of ceil(W/32) uint32 words; bit (u mod 32) of word
+ *               (v ceil(W/32) + u/32) is pixel (u, v)'s coverage bit; padding
+ *               bits are 0 (device memory).
+ *   records (dare_session_read_records): per voxel, K frame ids (uint16,
+ *               ascending, 0xFFFF = empty, empties last), K values (storage
+ *               type, 0 where empty) and K npix (uint16, saturating).
+ *
+ * Ownership.  The caller owns every *_dev buffer and every host array; host
+ * arrays are read (or written) before the call returns.  A session owns its
+ * volume, frame table and workspace, allocated through its allocator.
+ *
+ * Streams and errors.  Calls that take a stream are asynchronous on it (a
+ * NULL stream is the legacy default stream) unless stated otherwise.
+ * Arguments are checked on the host before anything is queued: a bad
+ * argument returns DARE_E_INVALID (or the status named) and queues nothing.
+ * A CUDA error seen while queueing returns DARE_E_CUDA.  Nothing aborts or
+ * traps.  The message of the last failure on the calling thread is returned
+ * by dare_last_error().  A session is externally synchronised: do not call
+ * into the same session from two threads at once.  Successive calls on one
+ * session may use different streams; the library orders them.
+ */
+#ifndef DARE_H
+#define DARE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DARE_ABI_VERSION 1
+#define DARE_FIX_BITS 20
+#define DARE_EMPTY_FRAME 0xFFFFu
+#define DARE_MAX_FRAMES 65535
+#define DARE_MAX_SLOTS 16
+
+typedef enum {
+    DARE_OK = 0,
+    DARE_E_INVALID = 1,     /* bad argument, nothing queued */
+    DARE_E_OOM = 2,         /* the allocator returned NULL */
+    DARE_E_CUDA = 3,        /* a CUDA call failed */
+    DARE_E_ADMISSION = 4,   /* the device-memory budget would be exceeded */
+    DARE_E_CAPACITY = 5,    /* frame ids would pass the session's max_frames */
+    DARE_E_TIMEOUT = 6,     /* a bounded device wait gave up */
+    DARE_E_STATE = 7,       /* the object is in the wrong state for the call */
+    DARE_E_UNSUPPORTED = 8  /* valid but not implemented on this path */
+} dare_status;
+
+typedef enum { DARE_U8 = 0, DARE_F16 = 1, DARE_BF16 = 2, DARE_F32 = 3 } dare_dtype;
+typedef enum { DARE_TENT = 0, DARE_BOX = 1, DARE_EXP = 2 } dare_dist_kernel;
+typedef enum { DARE_NORMAL_BEAM = 0, DARE_NORMAL_ELEVATION = 1 } dare_normal_axis;
+typedef enum { DARE_WEIGHTS_F32 = 0, DARE_WEIGHTS_F16 = 1 } dare_weight_dtype;
+typedef enum { DARE_PATH_AUTO = 0, DARE_PATH_PLAIN = 1, DARE_PATH_TILED = 2 } dare_path;
+
+typedef struct dare_session_s* dare_session;
+
+/* Voxel grid: dims, spacing (mm) and the rigid volume pose. */
+typedef struct {
+    int32_t dims[3];
+    int32_t reserved;
+    double spacing_mm;
+    double vol_to_world[16];
+} dare_grid;
+
+/*
+ * Device-memory allocator used by a session for its volume and workspace.
+ * alloc returns device memory of at least `bytes` (256-byte aligned) or NULL;
+ * free releases it.  `stream` is the stream of the call that allocates (may
+ * be NULL).  Both NULL: the library uses cudaMalloc / cudaFree.
+ */
+typedef struct {
+    void* (*alloc)(size_t bytes, void* stream, void* ctx);
+    void (*free)(void* ptr, size_t bytes, void* stream, void* ctx);
+    void* ctx;
+} dare_allocator;
+
+#define DARE_SESSION_SCALAR 1 /* also keep the mean-compounding totals (dare_reslice_scalar) */
+
+typedef struct {
+    dare_grid grid;
+    int32_t dtype;       /* dare_dtype of the stored intensities */
+    int32_t max_slots;   /* K, samples per voxel: 4, 8, 12 or 16 */
+    int32_t max_frames;  /* frame ids available to this session, <= 65535 */
+    int32_t device;      /* CUDA device ordinal */
+    int32_t flags;       /* DARE_SESSION_* */
+    int32_t reserved;
+    dare_allocator alloc;
+} dare_session_config;
+
+/* Reslicing parameters (Sec. 2.1; defaults from dare_params_default). */
+typedef struct {
+    double k_normal;        /* Eq. 2, paper: 10 */
+    double k_inplane;       /* Eq. 2, paper: 5 */
+    double thr_normal_deg;  /* paper: 25 */
+    double thr_inplane_deg; /* paper: 15 */
+    double k_dist;          /* rate of the EXP distance kernel */
+    float unassigned;       /* value of an unassigned pixel (default 0) */
+    int32_t radius_vox;     /* R, interpolation distance in voxels (default 1) */
+    int32_t dist_kernel;    /* dare_dist_kernel (default TENT) */
+    int32_t normal_axis;    /* dare_normal_axis (default BEAM) */
+    int32_t weight_dtype;   /* dare_weight_dtype of the per-frame weight table */
+    int32_t path;           /* dare_path: kernel choice */
+} dare_params;
+
+/* A virtual image plane: output size, pixel spacing and pose. */
+typedef struct {
+    int32_t width, height;
+    double px_mm[2];
+    double image_to_world[16];
+} dare_plane;
+
+typedef struct {
+    dare_session session;
+    dare_plane plane;
+    float* out;       /* device, height x width */
+    uint32_t* mask;   /* device, height x ceil(width/32) words */
+} dare_reslice_req;
+
+typedef struct {
+    int64_t volume_bytes;     /* device bytes held for the volume and tables */
+    int64_t workspace_bytes;  /* device bytes held as reusable workspace */
+    int64_t overflow_voxels;  /* voxels that hit max_slots (capacity rule applied) */
+    int64_t version;          /* number of completed dare_build_volume calls */
+    int32_t n_frames;         /* frame ids used so far */
+    int32_t slots;            /* K */
+    int32_t dtype;
+    int32_t record_bytes;     /* device bytes per voxel record */
+    int32_t dims[3];
+    int32_t flags;
+    double spacing_mm;
+    double vol_to_world[16];
+} dare_session_info;
+
+/* Message of the last failure on this thread ("" if none). */
+const char* dare_last_error(void);
+
+int32_t dare_abi_version(void);
+
+/* The paper's parameters (Sec. 2.1): k 10 / 5, thresholds 25 / 15 degrees,
+ * R = 1, TENT, beam normal, FP32 weights, unassigned 0, automatic path. */
+dare_status dare_params_default(dare_params* p);
+
+/*
+ * Bounding box "from the collected transducer positions" (Sec. 2.1): an
+ * axis-aligned grid (identity rotation) of spacing spacing_mm covering every
+ * corner of the n frames (image_to_world: n x 16 host FP64), grown by
+ * margin_vox voxels on each side.  Host only, synchronous.
+ */
+dare_status dare_grid_from_frames(int32_t n, int32_t width, int32_t height, const double px_mm[2],
+                                  const double* image_to_world, double spacing_mm, int32_t margin_vox,
+                                  dare_grid* out);
+
+/* The fixed-point pixel -> voxel affine [G0, A, B] of a plane in a grid
+ * (see "Fixed-point geometry").  Host only. */
+dare_status dare_pixel_affine(const dare_grid* grid, const dare_plane* plane, int64_t out[9]);
+
+/*
+ * Create a session holding an empty directional volume (Fig. 1's grid and
+ * flat sample storage) on cfg->device.  Allocates the volume through
+ * cfg->alloc and clears it (synchronously).  DARE_E_OOM if an allocation
+ * fails, DARE_E_ADMISSION if the device-memory budget set by
+ * dare_set_memory_budget would be exceeded.
+ */
+dare_status dare_session_create(const dare_session_config* cfg, dare_session* out);
+
+/* Wait for the session's queued work, then free everything it holds. */
+dare_status dare_session_destroy(dare_session s);
+
+/* Wait for the session's queued work; report a device-side failure. */
+dare_status dare_session_sync(dare_session s);
+
+dare_status dare_session_query(dare_session s, dare_session_info* out);
+
+/*
+ * Copy the volume to host arrays (synchronous): frame_ids n_vox x K uint16,
+ * values n_vox x K of the storage type, npix n_vox x K uint16; scalar_sum and
+ * scalar_count n_vox uint32 each (only with DARE_SESSION_SCALAR).  Any
+ * pointer may be NULL to skip that array.
+ */
+dare_status dare_session_read_records(dare_session s, uint16_t* frame_ids, void* values, uint16_t* npix,
+                                      uint32_t* scalar_sum, uint32_t* scalar_count);
+
+/* Frame table: n_frames x 9 FP64, row-major rotation of each frame in the
+ * volume frame (columns: lateral, beam, elevation). */
+dare_status dare_session_read_frames(dare_session s, double* rotations);
+
+/*
+ * Save / load a session (checkpoint, resume): a versioned header (grid,
+ * dtype, K, frames), the frame table and the records, with a CRC-32.  A
+ * loaded session reslices bit-identically to the saved one.  load takes the
+ * device, allocator and flags from cfg and everything else from the file;
+ * DARE_E_INVALID on a malformed or corrupted file.
+ */
+dare_status dare_session_save(dare_session s, const char* path);
+dare_status dare_session_load(const dare_session_config* cfg, const char* path, dare_session* out);
+
+/*
+ * Reconstruction (Sec. 2.1, Fig. 1): append n tracked frames to the volume.
+ * frames_dev: n x height x width uint8 on the session's device;
+ * image_to_world: n x 16 host FP64 poses (copied before return).  The frames
+ * get the next n frame ids.  The result is independent of thread scheduling
+ * and equals one call over all frames ever appended.  DARE_E_CAPACITY if the
+ * ids would pass max_frames (nothing queued).  The caller keeps frames_dev
+ * valid until the stream reaches the end of the call.
+ */
+dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t n, int32_t width,
+                              int32_t height, const double px_mm[2], const double* image_to_world,
+                              void* stream);
+
+/*
+ * Reslicing (Sec. 2.1, Eq. 1, Eq. 2, Fig. 2) of one plane into out_dev /
+ * mask_dev (see Layouts).  DARE_E_UNSUPPORTED for a radius or distance
+ * kernel the chosen path does not implement.
+ */
+dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
+                         uint32_t* mask_dev, void* stream);
+
+/*
+ * Reslice n planes, possibly of different sessions and sizes, with one set of
+ * parameters in as few launches as the sessions' storage types allow.  Each
+ * result equals what dare_reslice gives for that request alone.
+ */
+dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream);
+
+/*
+ * Mean-compounding comparator (the scalar reading of the PLUS baseline,
+ * Sec. 2.2): each voxel holds RN_fp32(total / count) of every pixel that
+ * landed in it; a pixel is the trilinear blend of its occupied corners,
+ * renormalised by their weights, or unassigned.  Needs DARE_SESSION_SCALAR.
+ */
+dare_status dare_reslice_scalar(dare_session s, const dare_plane* plane, float unassigned, float* out_dev,
+                                uint32_t* mask_dev, void* stream);
+
+/*
+ * Footprint: for each of n planes, the number of distinct in-grid voxels in
+ * the TENT support of radius 1 of any pixel -- the voxel records a reslice
+ * must read at least once.  counts: n int64 on the host.  Synchronous.
+ */
+dare_status dare_footprint(dare_session s, const dare_plane* planes, int32_t n, int64_t* counts, void* stream);
+
+/*
+ * Empty the volume (all samples, frame ids and scalar totals) on `stream`,
+ * keeping its allocation, grid and configuration; the next build starts at
+ * frame id 0.  Asynchronous.
+ */
+dare_status dare_session_reset(dare_session s, void* stream);
+
+/*
+ * Kernel tracing.  While enabled, every kernel the library launches is
+ * bracketed by two CUDA events recorded on the stream it is launched on;
+ * dare_trace_read waits for them and returns, per kernel name, the number of
+ * launches and their summed device time.  dare_launch_count counts every
+ * kernel launched since the process started, traced or not.
+ */
+typedef struct {
+    char name[48];
+    int64_t launches;
+    double total_ms;
+} dare_kernel_time;
+
+dare_status dare_trace_enable(int32_t on);
+dare_status dare_trace_read(dare_kernel_time* out, int32_t capacity, int32_t* n_out);
+int64_t dare_launch_count(void);
+
+/* Device-memory budget (bytes) shared by all sessions of this process;
+ * 0 = unlimited.  Sessions that would exceed it fail with DARE_E_ADMISSION. */
+dare_status dare_set_memory_budget(int64_t bytes);
+int64_t dare_memory_in_use(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DARE_H */

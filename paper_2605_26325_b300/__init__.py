@@ -1,0 +1,474 @@
+"""Python binding of libdare (DARE: Directionality-Aware Reslicing, CUDA sm_103a).
+
+Argument marshalling only.  Every step of reconstruction and reslicing runs
+in libdare.so's CUDA kernels; there is no CPU fallback: if the library is
+missing or cannot be built, importing the binding's functions raises.
+PyTorch supplies device memory (tensors) and streams.
+
+The raw entry points keep the C names (``dare_reslice``, ...); ``Session``
+wraps a session handle for convenience.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+
+# ---------------------------------------------------------------- constants (dare.h)
+DARE_OK, DARE_E_INVALID, DARE_E_OOM, DARE_E_CUDA = 0, 1, 2, 3
+DARE_E_ADMISSION, DARE_E_CAPACITY, DARE_E_TIMEOUT, DARE_E_STATE, DARE_E_UNSUPPORTED = 4, 5, 6, 7, 8
+DARE_U8, DARE_F16, DARE_BF16, DARE_F32 = 0, 1, 2, 3
+DARE_TENT, DARE_BOX, DARE_EXP = 0, 1, 2
+DARE_NORMAL_BEAM, DARE_NORMAL_ELEVATION = 0, 1
+DARE_WEIGHTS_F32, DARE_WEIGHTS_F16 = 0, 1
+DARE_PATH_AUTO, DARE_PATH_PLAIN, DARE_PATH_TILED = 0, 1, 2
+DARE_SESSION_SCALAR = 1
+DARE_EMPTY_FRAME = 0xFFFF
+DARE_FIX_BITS = 20
+
+STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_ADMISSION", 5: "E_CAPACITY",
+                6: "E_TIMEOUT", 7: "E_STATE", 8: "E_UNSUPPORTED"}
+VALUE_DTYPES = {DARE_U8: np.uint8, DARE_F16: np.float16, DARE_BF16: np.uint16, DARE_F32: np.float32}
+
+
+class DareError(RuntimeError):
+    def __init__(self, status, where, message):
+        self.status = status
+        super().__init__(f"{where}: DARE_{STATUS_NAMES.get(status, status)}: {message}")
+
+
+# ---------------------------------------------------------------- structures (dare.h)
+_d16 = ctypes.c_double * 16
+
+
+class dare_grid(ctypes.Structure):
+    _fields_ = [("dims", ctypes.c_int32 * 3), ("reserved", ctypes.c_int32),
+                ("spacing_mm", ctypes.c_double), ("vol_to_world", _d16)]
+
+
+_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class dare_allocator(ctypes.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class dare_session_config(ctypes.Structure):
+    _fields_ = [("grid", dare_grid), ("dtype", ctypes.c_int32), ("max_slots", ctypes.c_int32),
+                ("max_frames", ctypes.c_int32), ("device", ctypes.c_int32), ("flags", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("alloc", dare_allocator)]
+
+
+class dare_params(ctypes.Structure):
+    _fields_ = [("k_normal", ctypes.c_double), ("k_inplane", ctypes.c_double),
+                ("thr_normal_deg", ctypes.c_double), ("thr_inplane_deg", ctypes.c_double),
+                ("k_dist", ctypes.c_double), ("unassigned", ctypes.c_float), ("radius_vox", ctypes.c_int32),
+                ("dist_kernel", ctypes.c_int32), ("normal_axis", ctypes.c_int32),
+                ("weight_dtype", ctypes.c_int32), ("path", ctypes.c_int32)]
+
+
+class dare_plane(ctypes.Structure):
+    _fields_ = [("width", ctypes.c_int32), ("height", ctypes.c_int32), ("px_mm", ctypes.c_double * 2),
+                ("image_to_world", _d16)]
+
+
+class dare_reslice_req(ctypes.Structure):
+    _fields_ = [("session", ctypes.c_void_p), ("plane", dare_plane), ("out", ctypes.c_void_p),
+                ("mask", ctypes.c_void_p)]
+
+
+class dare_session_info(ctypes.Structure):
+    _fields_ = [("volume_bytes", ctypes.c_int64), ("workspace_bytes", ctypes.c_int64),
+                ("overflow_voxels", ctypes.c_int64), ("version", ctypes.c_int64), ("n_frames", ctypes.c_int32),
+                ("slots", ctypes.c_int32), ("dtype", ctypes.c_int32), ("record_bytes", ctypes.c_int32),
+                ("dims", ctypes.c_int32 * 3), ("flags", ctypes.c_int32), ("spacing_mm", ctypes.c_double),
+                ("vol_to_world", _d16)]
+
+
+class dare_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
+
+
+# ---------------------------------------------------------------- library
+_LIB = None
+_P = ctypes.POINTER
+_vp = ctypes.c_void_p
+
+_SIGNATURES = {
+    "dare_last_error": ([], ctypes.c_char_p),
+    "dare_abi_version": ([], ctypes.c_int32),
+    "dare_params_default": ([_P(dare_params)], ctypes.c_int),
+    "dare_grid_from_frames": ([ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_double),
+                               _P(ctypes.c_double), ctypes.c_double, ctypes.c_int32, _P(dare_grid)], ctypes.c_int),
+    "dare_pixel_affine": ([_P(dare_grid), _P(dare_plane), _P(ctypes.c_int64)], ctypes.c_int),
+    "dare_session_create": ([_P(dare_session_config), _P(_vp)], ctypes.c_int),
+    "dare_session_destroy": ([_vp], ctypes.c_int),
+    "dare_session_sync": ([_vp], ctypes.c_int),
+    "dare_session_query": ([_vp, _P(dare_session_info)], ctypes.c_int),
+    "dare_session_read_records": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
+    "dare_session_read_frames": ([_vp, _P(ctypes.c_double)], ctypes.c_int),
+    "dare_session_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
+    "dare_session_load": ([_P(dare_session_config), ctypes.c_char_p, _P(_vp)], ctypes.c_int),
+    "dare_build_volume": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_double),
+                           _P(ctypes.c_double), _vp], ctypes.c_int),
+    "dare_reslice": ([_vp, _P(dare_plane), _P(dare_params), _vp, _vp, _vp], ctypes.c_int),
+    "dare_reslice_batch": ([_P(dare_reslice_req), ctypes.c_int32, _P(dare_params), _vp], ctypes.c_int),
+    "dare_reslice_scalar": ([_vp, _P(dare_plane), ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
+    "dare_footprint": ([_vp, _P(dare_plane), ctypes.c_int32, _P(ctypes.c_int64), _vp], ctypes.c_int),
+    "dare_session_reset": ([_vp, _vp], ctypes.c_int),
+    "dare_trace_enable": ([ctypes.c_int32], ctypes.c_int),
+    "dare_trace_read": ([_P(dare_kernel_time), ctypes.c_int32, _P(ctypes.c_int32)], ctypes.c_int),
+    "dare_launch_count": ([], ctypes.c_int64),
+    "dare_set_memory_budget": ([ctypes.c_int64], ctypes.c_int),
+    "dare_memory_in_use": ([], ctypes.c_int64),
+}
+
+
+def library_path():
+    return os.path.join(_PKG, "libdare.so")
+
+
+def lib():
+    """Load libdare.so (building it first if the sources are newer).  Raises if
+    the library cannot be built or loaded: there is no fallback path."""
+    global _LIB
+    if _LIB is None:
+        from . import _build
+        path = _build.build()
+        handle = ctypes.CDLL(path)
+        for name, (args, res) in _SIGNATURES.items():
+            fn = getattr(handle, name)
+            fn.argtypes = args
+            fn.restype = res
+        _LIB = handle
+    return _LIB
+
+
+def last_error():
+    return lib().dare_last_error().decode(errors="replace")
+
+
+def check(status, where):
+    if status != DARE_OK:
+        raise DareError(status, where, last_error())
+
+
+def __getattr__(name):
+    # raw C entry points under their own names: paper_2605_26325_b300.dare_reslice(...)
+    if name in _SIGNATURES:
+        return getattr(lib(), name)
+    raise AttributeError(name)
+
+
+# ---------------------------------------------------------------- marshalling helpers
+
+def _mat16(T):
+    a = np.ascontiguousarray(np.asarray(T, dtype=np.float64).reshape(16))
+    return _d16(*a)
+
+
+def make_grid(dims, spacing_mm, vol_to_world) -> dare_grid:
+    g = dare_grid()
+    g.dims[:] = [int(x) for x in dims]
+    g.spacing_mm = float(spacing_mm)
+    g.vol_to_world = _mat16(vol_to_world)
+    return g
+
+
+def make_plane(width, height, px_mm, image_to_world) -> dare_plane:
+    p = dare_plane()
+    p.width, p.height = int(width), int(height)
+    p.px_mm[0], p.px_mm[1] = float(px_mm[0]), float(px_mm[1])
+    p.image_to_world = _mat16(image_to_world)
+    return p
+
+
+def params_default(**overrides) -> dare_params:
+    p = dare_params()
+    check(lib().dare_params_default(ctypes.byref(p)), "dare_params_default")
+    for k, v in overrides.items():
+        if not hasattr(p, k):
+            raise AttributeError(k)
+        setattr(p, k, v)
+    return p
+
+
+def pixel_affine(dims, spacing_mm, vol_to_world, width, height, px_mm, image_to_world):
+    g = make_grid(dims, spacing_mm, vol_to_world)
+    pl = make_plane(width, height, px_mm, image_to_world)
+    out = (ctypes.c_int64 * 9)()
+    check(lib().dare_pixel_affine(ctypes.byref(g), ctypes.byref(pl), out), "dare_pixel_affine")
+    return np.array(out[:], dtype=np.int64)
+
+
+def grid_from_frames(poses, width, height, px_mm, spacing_mm, margin_vox=1):
+    poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(-1, 16))
+    px = (ctypes.c_double * 2)(float(px_mm[0]), float(px_mm[1]))
+    g = dare_grid()
+    check(lib().dare_grid_from_frames(poses.shape[0], int(width), int(height), px,
+                                      poses.ctypes.data_as(_P(ctypes.c_double)), float(spacing_mm),
+                                      int(margin_vox), ctypes.byref(g)), "dare_grid_from_frames")
+    T = np.array(g.vol_to_world[:]).reshape(4, 4)
+    return tuple(g.dims[:]), g.spacing_mm, T
+
+
+def mask_words(width):
+    return (int(width) + 31) // 32
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, dtype_name, shape=None):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"expected a CUDA tensor for {dtype_name}")
+    if not t.is_contiguous():
+        raise ValueError(f"{dtype_name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{dtype_name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def trace_enable(on=True):
+    check(lib().dare_trace_enable(1 if on else 0), "dare_trace_enable")
+
+
+def trace_read():
+    """{kernel name: (launches, total device ms)} since the last read; waits for the events."""
+    cap = 64
+    arr = (dare_kernel_time * cap)()
+    n = ctypes.c_int32()
+    check(lib().dare_trace_read(arr, cap, ctypes.byref(n)), "dare_trace_read")
+    return {arr[i].name.decode(): (int(arr[i].launches), float(arr[i].total_ms)) for i in range(min(n.value, cap))}
+
+
+def launch_count():
+    return int(lib().dare_launch_count())
+
+
+def set_memory_budget(nbytes):
+    check(lib().dare_set_memory_budget(int(nbytes)), "dare_set_memory_budget")
+
+
+def memory_in_use():
+    return int(lib().dare_memory_in_use())
+
+
+class Session:
+    """A directional volume on one device (Sec. 2.1, Fig. 1) and its reslicing."""
+
+    def __init__(self, dims, spacing_mm, vol_to_world, dtype=DARE_F32, max_slots=8, max_frames=65535,
+                 device=0, flags=0, allocator=None, _handle=None):
+        self._cfg = dare_session_config()
+        self._cfg.grid = make_grid(dims, spacing_mm, vol_to_world)
+        self._cfg.dtype = int(dtype)
+        self._cfg.max_slots = int(max_slots)
+        self._cfg.max_frames = int(max_frames)
+        self._cfg.device = int(device)
+        self._cfg.flags = int(flags)
+        self._alloc_keep = None
+        if allocator is not None:
+            self._alloc_keep = allocator
+            self._cfg.alloc = allocator.as_struct()
+        self._h = ctypes.c_void_p()
+        if _handle is not None:
+            self._h = _handle
+        else:
+            check(lib().dare_session_create(ctypes.byref(self._cfg), ctypes.byref(self._h)), "dare_session_create")
+        self.dims = tuple(int(x) for x in dims)
+        self.spacing_mm = float(spacing_mm)
+        self.vol_to_world = np.array(vol_to_world, dtype=np.float64).reshape(4, 4)
+        self.device = int(device)
+
+    @classmethod
+    def load(cls, path, device=0, flags=0, allocator=None):
+        cfg = dare_session_config()
+        cfg.device = int(device)
+        cfg.flags = int(flags)
+        if allocator is not None:
+            cfg.alloc = allocator.as_struct()
+        h = ctypes.c_void_p()
+        check(lib().dare_session_load(ctypes.byref(cfg), str(path).encode(), ctypes.byref(h)), "dare_session_load")
+        info = dare_session_info()
+        check(lib().dare_session_query(h, ctypes.byref(info)), "dare_session_query")
+        obj = cls.__new__(cls)
+        obj._cfg = cfg
+        obj._alloc_keep = allocator
+        obj._h = h
+        obj.dims = tuple(info.dims[:])
+        obj.spacing_mm = float(info.spacing_mm)
+        obj.vol_to_world = np.array(info.vol_to_world[:], dtype=np.float64).reshape(4, 4)
+        obj.device = int(device)
+        return obj
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            check(lib().dare_session_destroy(self._h), "dare_session_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if getattr(self, "_h", None) and self._h.value and _LIB is not None:
+                _LIB.dare_session_destroy(self._h)
+                self._h = ctypes.c_void_p()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    # ---- state
+    def info(self) -> dare_session_info:
+        info = dare_session_info()
+        check(lib().dare_session_query(self._h, ctypes.byref(info)), "dare_session_query")
+        return info
+
+    def sync(self):
+        check(lib().dare_session_sync(self._h), "dare_session_sync")
+
+    def reset(self, stream=None):
+        check(lib().dare_session_reset(self._h, _stream_ptr(stream)), "dare_session_reset")
+
+    def read_records(self, npix=False, scalar=False):
+        """Host copies of the volume: dict(frame_ids (n_vox, K) uint16, values (n_vox, K),
+        npix (n_vox, K) uint16, scalar_sum, scalar_count)."""
+        info = self.info()
+        nv = int(np.prod(info.dims[:]))
+        K = info.slots
+        ids = np.empty((nv, K), np.uint16)
+        vals = np.empty((nv, K), VALUE_DTYPES[info.dtype])
+        np_ = np.empty((nv, K), np.uint16) if npix else None
+        ss = np.empty(nv, np.uint32) if scalar else None
+        sc = np.empty(nv, np.uint32) if scalar else None
+        c = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None
+        check(lib().dare_session_read_records(self._h, c(ids), c(vals), c(np_), c(ss), c(sc)),
+              "dare_session_read_records")
+        return dict(frame_ids=ids, values=vals, npix=np_, scalar_sum=ss, scalar_count=sc)
+
+    def read_frames(self):
+        n = self.info().n_frames
+        out = np.zeros((n, 9), np.float64)
+        check(lib().dare_session_read_frames(self._h, out.ctypes.data_as(_P(ctypes.c_double))),
+              "dare_session_read_frames")
+        return out.reshape(n, 3, 3)
+
+    def save(self, path):
+        check(lib().dare_session_save(self._h, str(path).encode()), "dare_session_save")
+
+    # ---- reconstruction
+    def build(self, frames_dev, poses, px_mm, stream=None):
+        """Append frames (device uint8 tensor (n, H, W)) with host poses (n, 4, 4)."""
+        n, H, W = (int(x) for x in frames_dev.shape)
+        poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(n, 16))
+        px = (ctypes.c_double * 2)(float(px_mm[0]), float(px_mm[1]))
+        import torch
+        if frames_dev.dtype != torch.uint8:
+            raise TypeError("frames must be uint8")
+        check(lib().dare_build_volume(self._h, _dev_ptr(frames_dev, "frames"), n, W, H, px,
+                                      poses.ctypes.data_as(_P(ctypes.c_double)), _stream_ptr(stream)),
+              "dare_build_volume")
+
+    # ---- reslicing
+    def reslice(self, image_to_world, out, mask, px_mm, params=None, stream=None):
+        """Reslice one plane into out (H, W) float32 and mask (H, ceil(W/32)) int32 device tensors."""
+        H, W = (int(x) for x in out.shape)
+        pl = make_plane(W, H, px_mm, image_to_world)
+        p = params if params is not None else params_default()
+        check(lib().dare_reslice(self._h, ctypes.byref(pl), ctypes.byref(p), _dev_ptr(out, "out"),
+                                 _dev_ptr(mask, "mask", (H, mask_words(W))), _stream_ptr(stream)), "dare_reslice")
+
+    def reslice_scalar(self, image_to_world, out, mask, px_mm, unassigned=0.0, stream=None):
+        H, W = (int(x) for x in out.shape)
+        pl = make_plane(W, H, px_mm, image_to_world)
+        check(lib().dare_reslice_scalar(self._h, ctypes.byref(pl), float(unassigned), _dev_ptr(out, "out"),
+                                        _dev_ptr(mask, "mask", (H, mask_words(W))), _stream_ptr(stream)),
+              "dare_reslice_scalar")
+
+    def footprint(self, poses, width, height, px_mm, stream=None):
+        poses = np.asarray(poses, dtype=np.float64).reshape(-1, 4, 4)
+        n = poses.shape[0]
+        planes = (dare_plane * n)(*[make_plane(width, height, px_mm, T) for T in poses])
+        counts = (ctypes.c_int64 * n)()
+        check(lib().dare_footprint(self._h, planes, n, counts, _stream_ptr(stream)), "dare_footprint")
+        return np.array(counts[:], dtype=np.int64)
+
+
+def make_requests(items):
+    """items: iterable of (session, image_to_world, out, mask, px_mm) -> ctypes array of dare_reslice_req."""
+    items = list(items)
+    arr = (dare_reslice_req * len(items))()
+    for i, (s, T, out, mask, px) in enumerate(items):
+        H, W = (int(x) for x in out.shape)
+        arr[i].session = s.handle.value
+        arr[i].plane = make_plane(W, H, px, T)
+        arr[i].out = _dev_ptr(out, "out").value
+        arr[i].mask = _dev_ptr(mask, "mask", (H, mask_words(W))).value
+    return arr
+
+
+def reslice_batch(requests, params=None, stream=None):
+    """requests: ctypes array from make_requests (or the items list)."""
+    if not isinstance(requests, ctypes.Array):
+        requests = make_requests(requests)
+    p = params if params is not None else params_default()
+    check(lib().dare_reslice_batch(requests, len(requests), ctypes.byref(p), _stream_ptr(stream)),
+          "dare_reslice_batch")
+
+
+def unpack_mask(mask_words_np, width):
+    """(H, ceil(W/32)) int32/uint32 words -> (H, W) uint8 coverage bits."""
+    m = np.ascontiguousarray(mask_words_np).view(np.uint32)
+    bits = ((m[:, :, None] >> np.arange(32, dtype=np.uint32)[None, None, :]) & 1).astype(np.uint8)
+    return bits.reshape(m.shape[0], -1)[:, :width]
+
+
+class TorchAllocator:
+    """Routes a session's device allocations through PyTorch's caching allocator."""
+
+    def __init__(self, device=0):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.live = {}
+        self.fail_next = 0  # test hook: make the next N allocations fail
+
+        def _alloc(nbytes, stream, ctx):
+            if self.fail_next > 0:
+                self.fail_next -= 1
+                return None
+            t = self._torch.empty(int(nbytes) + 256, dtype=self._torch.uint8, device=f"cuda:{self.device}")
+            p = (t.data_ptr() + 255) // 256 * 256
+            self.live[p] = t
+            return p
+
+        def _free(ptr, nbytes, stream, ctx):
+            self.live.pop(ptr, None)
+
+        self._alloc_fn = _ALLOC_FN(_alloc)
+        self._free_fn = _FREE_FN(_free)
+
+    def as_struct(self):
+        a = dare_allocator()
+        a.alloc = self._alloc_fn
+        a.free = self._free_fn
+        a.ctx = None
+        return a

@@ -1,0 +1,1131 @@
+// Host side of libdare's C ABI: argument checks, FP64 pose composition, the
+// fixed-point affine, sessions (volume, frame table, workspace), ordering of
+// a session's work across streams, device-memory admission, checkpoints.
+//
+// Compile with -ffp-contract=off: the fixed-point affine follows the
+// canonical FP64 evaluation order documented in dare.h.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "dare_internal.h"
+
+using namespace dare;
+
+namespace {
+
+thread_local std::string g_err;
+std::atomic<int64_t> g_budget{0};
+std::atomic<int64_t> g_in_use{0};
+
+dare_status fail(dare_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return st;
+}
+
+#define CUDA_TRY(expr)                                                                          \
+    do {                                                                                        \
+        cudaError_t e_ = (expr);                                                                \
+        if (e_ != cudaSuccess) return fail(DARE_E_CUDA, "%s: %s", #expr, cudaGetErrorString(e_)); \
+    } while (0)
+
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = true;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+bool finite_all(const double* x, int n) {
+    for (int i = 0; i < n; ++i)
+        if (!std::isfinite(x[i])) return false;
+    return true;
+}
+
+// Rigid: finite, last row (0 0 0 1), orthonormal rotation with det +1.
+bool rigid_ok(const double* T) {
+    if (!finite_all(T, 16)) return false;
+    if (std::fabs(T[12]) > 1e-9 || std::fabs(T[13]) > 1e-9 || std::fabs(T[14]) > 1e-9 || std::fabs(T[15] - 1.0) > 1e-9)
+        return false;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) {
+            double d = T[0 * 4 + i] * T[0 * 4 + j] + T[1 * 4 + i] * T[1 * 4 + j] + T[2 * 4 + i] * T[2 * 4 + j];
+            if (std::fabs(d - (i == j ? 1.0 : 0.0)) > 1e-6) return false;
+        }
+    const double det = T[0] * (T[5] * T[10] - T[6] * T[9]) - T[1] * (T[4] * T[10] - T[6] * T[8]) +
+                       T[2] * (T[4] * T[9] - T[5] * T[8]);
+    return det > 0;
+}
+
+int64_t fix_round(double x) { return static_cast<int64_t>(std::nearbyint(x * static_cast<double>(kFixOne))); }
+
+// Fixed-point pixel -> voxel affine in the canonical order of dare.h.
+void compose_affine(const double* V, double h, const double* T, int32_t W, double sx, double sy, int64_t out[9]) {
+    double d[3], c0[3], c1[3], tm[3];
+    for (int k = 0; k < 3; ++k) d[k] = T[4 * k + 3] - V[4 * k + 3];
+    for (int r = 0; r < 3; ++r) {
+        c0[r] = V[0 * 4 + r] * T[0 * 4 + 0] + V[1 * 4 + r] * T[1 * 4 + 0] + V[2 * 4 + r] * T[2 * 4 + 0];
+        c1[r] = V[0 * 4 + r] * T[0 * 4 + 1] + V[1 * 4 + r] * T[1 * 4 + 1] + V[2 * 4 + r] * T[2 * 4 + 1];
+        tm[r] = V[0 * 4 + r] * d[0] + V[1 * 4 + r] * d[1] + V[2 * 4 + r] * d[2];
+    }
+    const double half_w = 0.5 * static_cast<double>(W - 1) * sx;
+    for (int r = 0; r < 3; ++r) {
+        out[r] = fix_round((tm[r] - half_w * c0[r]) / h);
+        out[3 + r] = fix_round((c0[r] * sx) / h);
+        out[6 + r] = fix_round((c1[r] * sy) / h);
+    }
+}
+
+// Rotation of pose T in the volume frame, R_v^T R_t (row-major 3x3).
+void relative_rotation(const double* V, const double* T, double R[9]) {
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+            R[3 * r + c] = V[0 * 4 + r] * T[0 * 4 + c] + V[1 * 4 + r] * T[1 * 4 + c] + V[2 * 4 + r] * T[2 * 4 + c];
+}
+
+// Largest coefficient magnitude that keeps g = G0 + u A + v B inside int64
+// for any u, v < 2^16 (and keeps voxel coordinates far from overflow).
+constexpr double kMaxFix = 9.0e15;
+
+bool affine_ok(const double* V, double h, const double* T, int32_t W, double sx, double sy) {
+    // evaluate the unrounded magnitudes before quantising
+    double Rrel[9];
+    relative_rotation(V, T, Rrel);
+    double d[3];
+    for (int k = 0; k < 3; ++k) d[k] = T[4 * k + 3] - V[4 * k + 3];
+    for (int r = 0; r < 3; ++r) {
+        double tm = V[0 * 4 + r] * d[0] + V[1 * 4 + r] * d[1] + V[2 * 4 + r] * d[2];
+        double g0 = (tm - 0.5 * (W - 1) * sx * Rrel[3 * r]) / h * static_cast<double>(kFixOne);
+        double a = Rrel[3 * r] * sx / h * static_cast<double>(kFixOne);
+        double b = Rrel[3 * r + 1] * sy / h * static_cast<double>(kFixOne);
+        if (!(std::fabs(g0) < kMaxFix && std::fabs(a) * 65536.0 < kMaxFix && std::fabs(b) * 65536.0 < kMaxFix))
+            return false;
+    }
+    return true;
+}
+
+uint32_t crc32_update(uint32_t crc, const void* data, size_t n) {
+    static uint32_t table[256];
+    static std::once_flag once;
+    std::call_once(once, [] {
+        for (uint32_t i = 0; i < 256; ++i) {
+            uint32_t c = i;
+            for (int k = 0; k < 8; ++k) c = (c & 1) ? 0xEDB88320u ^ (c >> 1) : c >> 1;
+            table[i] = c;
+        }
+    });
+    const uint8_t* p = static_cast<const uint8_t*>(data);
+    crc = ~crc;
+    for (size_t i = 0; i < n; ++i) crc = table[(crc ^ p[i]) & 0xFFu] ^ (crc >> 8);
+    return ~crc;
+}
+
+size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+// ---------------------------------------------------------------- tracing
+
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_trace_on{false};
+std::mutex g_trace_mu;
+struct TraceRec {
+    const char* name;
+    int device;
+    cudaEvent_t a, b;
+};
+std::vector<TraceRec> g_trace_pending;
+std::map<int, std::vector<cudaEvent_t>> g_event_pool;
+std::map<std::string, std::pair<int64_t, double>> g_trace_acc;
+
+cudaEvent_t pooled_event(int dev) {
+    auto& pool = g_event_pool[dev];
+    if (!pool.empty()) {
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return e;
+}
+
+// Brackets the kernel launches of one launcher call (n_kernels of them).
+struct KernelScope {
+    const char* name;
+    cudaStream_t st;
+    int dev = 0;
+    cudaEvent_t a = nullptr, b = nullptr;
+    KernelScope(const char* n, cudaStream_t s, int n_kernels) : name(n), st(s) {
+        g_launches += n_kernels;
+        if (!g_trace_on.load()) return;
+        std::lock_guard<std::mutex> lk(g_trace_mu);
+        cudaGetDevice(&dev);
+        a = pooled_event(dev);
+        b = pooled_event(dev);
+        if (a && b) cudaEventRecord(a, st);
+    }
+    ~KernelScope() {
+        if (!a || !b) return;
+        std::lock_guard<std::mutex> lk(g_trace_mu);
+        cudaEventRecord(b, st);
+        g_trace_pending.push_back({name, dev, a, b});
+    }
+};
+
+}  // namespace
+
+// ---------------------------------------------------------------- session
+
+struct dare_session_s {
+    dare_session_config cfg{};
+    int64_t n_vox = 0;
+    int32_t K = 0, dtype = 0, rec_bytes = 0;
+    uint8_t* rec = nullptr;
+    uint16_t* npix = nullptr;
+    uint32_t* ssum = nullptr;
+    uint32_t* scnt = nullptr;
+    int32_t* count = nullptr;              // scatter counters, all zero between calls
+    double* frames_dev = nullptr;          // max_frames x 9
+    unsigned long long* overflow_dev = nullptr;
+    std::vector<double> frames_host;       // n_frames x 9
+    int32_t n_frames = 0;
+    int64_t version = 0;
+    int64_t volume_bytes = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    // pinned host staging: [0] frame affines / rotations of a build, [1] batch descriptors
+    void* pinned[2] = {nullptr, nullptr};
+    size_t pinned_bytes[2] = {0, 0};
+    cudaEvent_t pinned_ev[2] = {nullptr, nullptr};  // last copy out of each staging buffer
+    cudaEvent_t order_ev = nullptr;        // end of the session's last queued call
+    cudaStream_t last_stream = nullptr;
+    std::vector<std::pair<void*, size_t>> allocs;
+
+    void* dev_alloc(size_t bytes, cudaStream_t st) {
+        void* p = nullptr;
+        if (cfg.alloc.alloc) {
+            p = cfg.alloc.alloc(bytes, st, cfg.alloc.ctx);
+        } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+        }
+        return p;
+    }
+    void dev_free(void* p, size_t bytes, cudaStream_t st) {
+        if (!p) return;
+        if (cfg.alloc.free)
+            cfg.alloc.free(p, bytes, st, cfg.alloc.ctx);
+        else if (!cfg.alloc.alloc)
+            cudaFree(p);
+    }
+};
+
+namespace {
+
+dare_status admit(int64_t bytes) {
+    const int64_t budget = g_budget.load();
+    int64_t cur = g_in_use.load();
+    for (;;) {
+        if (budget > 0 && cur + bytes > budget)
+            return fail(DARE_E_ADMISSION, "device-memory budget exceeded: %lld in use + %lld requested > %lld",
+                        (long long)cur, (long long)bytes, (long long)budget);
+        if (g_in_use.compare_exchange_weak(cur, cur + bytes)) return DARE_OK;
+    }
+}
+
+// Order a call after the session's previous one, whatever stream that used.
+dare_status session_begin(dare_session s, cudaStream_t st) {
+    CUDA_TRY(cudaStreamWaitEvent(st, s->order_ev, 0));
+    return DARE_OK;
+}
+
+dare_status session_end(dare_session s, cudaStream_t st) {
+    CUDA_TRY(cudaEventRecord(s->order_ev, st));
+    s->last_stream = st;
+    return DARE_OK;
+}
+
+dare_status ensure_workspace(dare_session s, size_t bytes, cudaStream_t st) {
+    if (s->ws_bytes >= bytes) return DARE_OK;
+    size_t want = std::max(bytes, s->ws_bytes + s->ws_bytes / 2);
+    want = align_up(want, size_t(1) << 20);
+    if (s->ws) {
+        s->dev_free(s->ws, s->ws_bytes, st);
+        g_in_use -= static_cast<int64_t>(s->ws_bytes);
+        s->ws = nullptr;
+        s->ws_bytes = 0;
+    }
+    dare_status a = admit(static_cast<int64_t>(want));
+    if (a != DARE_OK) {
+        a = admit(static_cast<int64_t>(bytes));
+        if (a != DARE_OK) return a;
+        want = bytes;
+    }
+    s->ws = s->dev_alloc(want, st);
+    if (!s->ws) {
+        g_in_use -= static_cast<int64_t>(want);
+        return fail(DARE_E_OOM, "workspace allocation of %zu bytes failed", want);
+    }
+    s->ws_bytes = want;
+    return DARE_OK;
+}
+
+// Host staging in pinned memory; waits until the previous copy out of it is done.
+dare_status ensure_pinned(dare_session s, int slot, size_t bytes) {
+    CUDA_TRY(cudaEventSynchronize(s->pinned_ev[slot]));
+    if (s->pinned_bytes[slot] >= bytes) return DARE_OK;
+    if (s->pinned[slot]) cudaFreeHost(s->pinned[slot]);
+    s->pinned[slot] = nullptr;
+    s->pinned_bytes[slot] = 0;
+    const size_t want = align_up(std::max(bytes, size_t(1) << 16), 4096);
+    CUDA_TRY(cudaHostAlloc(&s->pinned[slot], want, cudaHostAllocDefault));
+    s->pinned_bytes[slot] = want;
+    return DARE_OK;
+}
+
+dare_status check_plane(const dare_plane* p) {
+    if (!p) return fail(DARE_E_INVALID, "plane is NULL");
+    if (p->width < 1 || p->height < 1 || p->width > 65535 || p->height > 65535)
+        return fail(DARE_E_INVALID, "plane size %dx%d outside [1, 65535]", p->width, p->height);
+    if (!(p->px_mm[0] > 0 && p->px_mm[1] > 0) || !std::isfinite(p->px_mm[0]) || !std::isfinite(p->px_mm[1]))
+        return fail(DARE_E_INVALID, "pixel spacing must be positive and finite");
+    if (!rigid_ok(p->image_to_world)) return fail(DARE_E_INVALID, "image_to_world is not a rigid transform");
+    return DARE_OK;
+}
+
+dare_status check_params(const dare_params* p) {
+    if (!p) return fail(DARE_E_INVALID, "params is NULL");
+    const double xs[5] = {p->k_normal, p->k_inplane, p->thr_normal_deg, p->thr_inplane_deg, p->k_dist};
+    if (!finite_all(xs, 5)) return fail(DARE_E_INVALID, "non-finite parameter");
+    if (p->k_normal < 0 || p->k_inplane < 0) return fail(DARE_E_INVALID, "k_normal and k_inplane must be >= 0");
+    if (p->thr_normal_deg < 0 || p->thr_inplane_deg < 0) return fail(DARE_E_INVALID, "thresholds must be >= 0");
+    if (p->radius_vox < 1) return fail(DARE_E_INVALID, "radius_vox must be >= 1");
+    if (p->dist_kernel < 0 || p->dist_kernel > 2) return fail(DARE_E_INVALID, "unknown distance kernel");
+    if (p->normal_axis < 0 || p->normal_axis > 1) return fail(DARE_E_INVALID, "unknown normal axis");
+    if (p->weight_dtype < 0 || p->weight_dtype > 1) return fail(DARE_E_INVALID, "unknown weight dtype");
+    if (p->path < 0 || p->path > 2) return fail(DARE_E_INVALID, "unknown path");
+    if (p->radius_vox != 1 || p->dist_kernel != DARE_TENT)
+        return fail(DARE_E_UNSUPPORTED, "the CUDA path implements the TENT kernel at radius 1");
+    return DARE_OK;
+}
+
+TableParams table_params(const dare_params* p) {
+    TableParams t{};
+    t.k_normal = p->k_normal;
+    t.k_inplane = p->k_inplane;
+    t.use_normal = p->thr_normal_deg < 180.0;
+    t.use_inplane = p->thr_inplane_deg < 180.0;
+    t.cos_normal = std::cos(p->thr_normal_deg * (M_PI / 180.0));
+    t.cos_inplane = std::cos(p->thr_inplane_deg * (M_PI / 180.0));
+    t.normal_axis = p->normal_axis == DARE_NORMAL_ELEVATION ? 2 : 1;
+    t.half = p->weight_dtype == DARE_WEIGHTS_F16;
+    return t;
+}
+
+void plane_vectors(const dare_session s, const dare_plane* pl, int normal_axis, TableJob* tj) {
+    double R[9];
+    relative_rotation(s->cfg.grid.vol_to_world, pl->image_to_world, R);
+    const int col = normal_axis == DARE_NORMAL_ELEVATION ? 2 : 1;
+    for (int r = 0; r < 3; ++r) {
+        tj->n_r[r] = R[3 * r + col];
+        tj->x_r[r] = R[3 * r + 0];
+    }
+}
+
+ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab, float* out, uint32_t* mask,
+                    float unassigned) {
+    ResliceJob j{};
+    int64_t aff[9];
+    compose_affine(s->cfg.grid.vol_to_world, s->cfg.grid.spacing_mm, pl->image_to_world, pl->width, pl->px_mm[0],
+                   pl->px_mm[1], aff);
+    for (int a = 0; a < 3; ++a) {
+        j.g0[a] = aff[a];
+        j.a[a] = aff[3 + a];
+        j.b[a] = aff[6 + a];
+    }
+    j.rec = s->rec;
+    j.wtab = wtab;
+    j.out = out;
+    j.mask = mask;
+    for (int a = 0; a < 3; ++a) j.dims[a] = s->cfg.grid.dims[a];
+    j.width = pl->width;
+    j.height = pl->height;
+    j.mask_stride = (pl->width + 31) / 32;
+    j.tiles_x = (pl->width + kTileW - 1) / kTileW;
+    j.unassigned = unassigned;
+    return j;
+}
+
+int tiles_of(const dare_plane* pl) {
+    return ((pl->width + kTileW - 1) / kTileW) * ((pl->height + kTileH - 1) / kTileH);
+}
+
+bool use_tiled(const dare_params* p) { return p->path != DARE_PATH_PLAIN; }
+
+}  // namespace
+
+// ---------------------------------------------------------------- ABI
+
+extern "C" {
+
+const char* dare_last_error(void) { return g_err.c_str(); }
+
+int32_t dare_abi_version(void) { return DARE_ABI_VERSION; }
+
+dare_status dare_params_default(dare_params* p) {
+    if (!p) return fail(DARE_E_INVALID, "params is NULL");
+    std::memset(p, 0, sizeof(*p));
+    p->k_normal = 10.0;
+    p->k_inplane = 5.0;
+    p->thr_normal_deg = 25.0;
+    p->thr_inplane_deg = 15.0;
+    p->k_dist = 1.0;
+    p->unassigned = 0.0f;
+    p->radius_vox = 1;
+    p->dist_kernel = DARE_TENT;
+    p->normal_axis = DARE_NORMAL_BEAM;
+    p->weight_dtype = DARE_WEIGHTS_F32;
+    p->path = DARE_PATH_AUTO;
+    return DARE_OK;
+}
+
+dare_status dare_set_memory_budget(int64_t bytes) {
+    if (bytes < 0) return fail(DARE_E_INVALID, "budget must be >= 0");
+    g_budget = bytes;
+    return DARE_OK;
+}
+
+int64_t dare_memory_in_use(void) { return g_in_use.load(); }
+
+dare_status dare_grid_from_frames(int32_t n, int32_t width, int32_t height, const double px_mm[2],
+                                  const double* image_to_world, double spacing_mm, int32_t margin_vox,
+                                  dare_grid* out) {
+    if (n < 1 || width < 1 || height < 1 || !px_mm || !image_to_world || !out || !(spacing_mm > 0) || margin_vox < 0)
+        return fail(DARE_E_INVALID, "bad arguments to dare_grid_from_frames");
+    double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    for (int32_t f = 0; f < n; ++f) {
+        const double* T = image_to_world + 16 * static_cast<size_t>(f);
+        if (!rigid_ok(T)) return fail(DARE_E_INVALID, "pose %d is not rigid", f);
+        for (int cu = 0; cu < 2; ++cu)
+            for (int cv = 0; cv < 2; ++cv) {
+                const double x = ((cu ? width - 1 : 0) - 0.5 * (width - 1)) * px_mm[0];
+                const double y = (cv ? height - 1 : 0) * px_mm[1];
+                for (int a = 0; a < 3; ++a) {
+                    const double w = T[4 * a] * x + T[4 * a + 1] * y + T[4 * a + 3];
+                    lo[a] = std::min(lo[a], w);
+                    hi[a] = std::max(hi[a], w);
+                }
+            }
+    }
+    std::memset(out, 0, sizeof(*out));
+    out->spacing_mm = spacing_mm;
+    for (int a = 0; a < 3; ++a) {
+        const double ext = std::ceil((hi[a] - lo[a]) / spacing_mm);
+        if (!(ext < 1e6)) return fail(DARE_E_INVALID, "bounding box too large");
+        out->dims[a] = static_cast<int32_t>(ext) + 1 + 2 * margin_vox;
+        out->vol_to_world[4 * a + a] = 1.0;
+        out->vol_to_world[4 * a + 3] = lo[a] - margin_vox * spacing_mm;
+    }
+    out->vol_to_world[15] = 1.0;
+    return DARE_OK;
+}
+
+dare_status dare_pixel_affine(const dare_grid* grid, const dare_plane* plane, int64_t out[9]) {
+    if (!grid || !out) return fail(DARE_E_INVALID, "NULL argument");
+    dare_status st = check_plane(plane);
+    if (st != DARE_OK) return st;
+    if (!(grid->spacing_mm > 0) || !rigid_ok(grid->vol_to_world)) return fail(DARE_E_INVALID, "bad grid");
+    if (!affine_ok(grid->vol_to_world, grid->spacing_mm, plane->image_to_world, plane->width, plane->px_mm[0],
+                   plane->px_mm[1]))
+        return fail(DARE_E_INVALID, "plane too far from the grid for fixed-point coordinates");
+    compose_affine(grid->vol_to_world, grid->spacing_mm, plane->image_to_world, plane->width, plane->px_mm[0],
+                   plane->px_mm[1], out);
+    return DARE_OK;
+}
+
+dare_status dare_session_create(const dare_session_config* cfg, dare_session* out) {
+    if (!cfg || !out) return fail(DARE_E_INVALID, "NULL argument");
+    *out = nullptr;
+    const dare_grid& g = cfg->grid;
+    if (g.dims[0] < 1 || g.dims[1] < 1 || g.dims[2] < 1 || g.dims[0] > 4096 || g.dims[1] > 4096 || g.dims[2] > 4096)
+        return fail(DARE_E_INVALID, "grid dims must be in [1, 4096]");
+    if (!(g.spacing_mm > 0) || !std::isfinite(g.spacing_mm)) return fail(DARE_E_INVALID, "spacing must be > 0");
+    if (!rigid_ok(g.vol_to_world)) return fail(DARE_E_INVALID, "vol_to_world is not a rigid transform");
+    if (cfg->dtype < DARE_U8 || cfg->dtype > DARE_F32) return fail(DARE_E_INVALID, "unknown dtype");
+    if (cfg->max_slots != 4 && cfg->max_slots != 8 && cfg->max_slots != 12 && cfg->max_slots != 16)
+        return fail(DARE_E_INVALID, "max_slots must be 4, 8, 12 or 16");
+    if (cfg->max_frames < 1 || cfg->max_frames > DARE_MAX_FRAMES)
+        return fail(DARE_E_INVALID, "max_frames must be in [1, 65535]");
+    if ((cfg->alloc.alloc == nullptr) != (cfg->alloc.free == nullptr))
+        return fail(DARE_E_INVALID, "allocator needs both alloc and free");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || cfg->device < 0 || cfg->device >= ndev) {
+        cudaGetLastError();
+        return fail(DARE_E_INVALID, "device %d not available (%d devices)", cfg->device, ndev);
+    }
+    const int64_t n_vox = int64_t(g.dims[0]) * g.dims[1] * g.dims[2];
+    if (n_vox >= (int64_t(1) << 31)) return fail(DARE_E_INVALID, "grid has 2^31 voxels or more");
+    DeviceGuard dg(cfg->device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device %d", cfg->device);
+
+    auto* s = new dare_session_s();
+    s->cfg = *cfg;
+    s->n_vox = n_vox;
+    s->K = cfg->max_slots;
+    s->dtype = cfg->dtype;
+    s->rec_bytes = record_bytes(s->K, s->dtype);
+    const bool scalar = (cfg->flags & DARE_SESSION_SCALAR) != 0;
+    const size_t b_rec = align_up(size_t(n_vox) * s->rec_bytes, 256);
+    const size_t b_np = align_up(size_t(n_vox) * s->K * 2, 256);
+    const size_t b_sc = scalar ? align_up(size_t(n_vox) * 4, 256) : 0;
+    const size_t b_cnt = align_up(size_t(n_vox) * 4, 256);
+    const size_t b_fr = align_up(size_t(cfg->max_frames) * 9 * 8, 256);
+    const size_t b_ovf = 256;
+    const size_t total = b_rec + b_np + 2 * b_sc + b_cnt + b_fr + b_ovf;
+    dare_status st = admit(static_cast<int64_t>(total));
+    if (st != DARE_OK) {
+        delete s;
+        return st;
+    }
+    uint8_t* base = static_cast<uint8_t*>(s->dev_alloc(total, nullptr));
+    if (!base) {
+        g_in_use -= static_cast<int64_t>(total);
+        delete s;
+        return fail(DARE_E_OOM, "volume allocation of %zu bytes failed", total);
+    }
+    s->allocs.push_back({base, total});
+    s->volume_bytes = static_cast<int64_t>(total);
+    size_t off = 0;
+    s->rec = base + off;
+    off += b_rec;
+    s->npix = reinterpret_cast<uint16_t*>(base + off);
+    off += b_np;
+    if (scalar) {
+        s->ssum = reinterpret_cast<uint32_t*>(base + off);
+        off += b_sc;
+        s->scnt = reinterpret_cast<uint32_t*>(base + off);
+        off += b_sc;
+    }
+    s->count = reinterpret_cast<int32_t*>(base + off);
+    off += b_cnt;
+    s->frames_dev = reinterpret_cast<double*>(base + off);
+    off += b_fr;
+    s->overflow_dev = reinterpret_cast<unsigned long long*>(base + off);
+    auto bail = [&](dare_status code) {
+        dare_session_destroy(s);
+        return code;
+    };
+    if (cudaEventCreateWithFlags(&s->order_ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->pinned_ev[0], cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->pinned_ev[1], cudaEventDisableTiming) != cudaSuccess)
+        return bail(fail(DARE_E_CUDA, "event creation failed"));
+    // clear: empty records, zero counters (synchronous)
+    g_launches += 1;
+    if (launch_fill_records(s->rec, n_vox, s->rec_bytes, s->K, nullptr) != cudaSuccess ||
+        cudaMemset(s->npix, 0, b_np) != cudaSuccess || cudaMemset(s->count, 0, b_cnt) != cudaSuccess ||
+        cudaMemset(s->overflow_dev, 0, b_ovf) != cudaSuccess ||
+        (scalar && cudaMemset(s->ssum, 0, 2 * b_sc) != cudaSuccess) || cudaDeviceSynchronize() != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        return bail(fail(DARE_E_CUDA, "clearing the volume failed: %s", cudaGetErrorString(e)));
+    }
+    if (cudaEventRecord(s->order_ev, nullptr) != cudaSuccess || cudaEventRecord(s->pinned_ev[0], nullptr) != cudaSuccess ||
+        cudaEventRecord(s->pinned_ev[1], nullptr) != cudaSuccess)
+        return bail(fail(DARE_E_CUDA, "event record failed"));
+    *out = s;
+    return DARE_OK;
+}
+
+dare_status dare_session_destroy(dare_session s) {
+    if (!s) return DARE_OK;
+    DeviceGuard dg(s->cfg.device);
+    if (s->order_ev) cudaEventSynchronize(s->order_ev);
+    for (int k = 0; k < 2; ++k)
+        if (s->pinned_ev[k]) cudaEventSynchronize(s->pinned_ev[k]);
+    if (s->ws) {
+        s->dev_free(s->ws, s->ws_bytes, s->last_stream);
+        g_in_use -= static_cast<int64_t>(s->ws_bytes);
+    }
+    for (auto& a : s->allocs) {
+        s->dev_free(a.first, a.second, s->last_stream);
+        g_in_use -= static_cast<int64_t>(a.second);
+    }
+    for (int k = 0; k < 2; ++k) {
+        if (s->pinned[k]) cudaFreeHost(s->pinned[k]);
+        if (s->pinned_ev[k]) cudaEventDestroy(s->pinned_ev[k]);
+    }
+    if (s->order_ev) cudaEventDestroy(s->order_ev);
+    delete s;
+    return DARE_OK;
+}
+
+dare_status dare_session_sync(dare_session s) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    DeviceGuard dg(s->cfg.device);
+    CUDA_TRY(cudaEventSynchronize(s->order_ev));
+    return DARE_OK;
+}
+
+dare_status dare_session_query(dare_session s, dare_session_info* out) {
+    if (!s || !out) return fail(DARE_E_INVALID, "NULL argument");
+    DeviceGuard dg(s->cfg.device);
+    CUDA_TRY(cudaEventSynchronize(s->order_ev));
+    unsigned long long ovf = 0;
+    CUDA_TRY(cudaMemcpy(&ovf, s->overflow_dev, sizeof(ovf), cudaMemcpyDeviceToHost));
+    std::memset(out, 0, sizeof(*out));
+    out->volume_bytes = s->volume_bytes;
+    out->workspace_bytes = static_cast<int64_t>(s->ws_bytes);
+    out->overflow_voxels = static_cast<int64_t>(ovf);
+    out->version = s->version;
+    out->n_frames = s->n_frames;
+    out->slots = s->K;
+    out->dtype = s->dtype;
+    out->record_bytes = s->rec_bytes;
+    for (int a = 0; a < 3; ++a) out->dims[a] = s->cfg.grid.dims[a];
+    out->flags = s->cfg.flags;
+    out->spacing_mm = s->cfg.grid.spacing_mm;
+    std::memcpy(out->vol_to_world, s->cfg.grid.vol_to_world, sizeof(out->vol_to_world));
+    return DARE_OK;
+}
+
+dare_status dare_session_read_records(dare_session s, uint16_t* frame_ids, void* values, uint16_t* npix,
+                                      uint32_t* scalar_sum, uint32_t* scalar_count) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    if ((scalar_sum || scalar_count) && !s->ssum) return fail(DARE_E_STATE, "session keeps no scalar totals");
+    DeviceGuard dg(s->cfg.device);
+    CUDA_TRY(cudaEventSynchronize(s->order_ev));
+    const int vb = value_bytes(s->dtype);
+    if (frame_ids || values) {
+        std::vector<uint8_t> host(size_t(s->n_vox) * s->rec_bytes);
+        CUDA_TRY(cudaMemcpy(host.data(), s->rec, host.size(), cudaMemcpyDeviceToHost));
+        for (int64_t v = 0; v < s->n_vox; ++v) {
+            const uint8_t* r = host.data() + size_t(v) * s->rec_bytes;
+            if (frame_ids) std::memcpy(frame_ids + size_t(v) * s->K, r, size_t(2) * s->K);
+            if (values)
+                std::memcpy(static_cast<uint8_t*>(values) + size_t(v) * s->K * vb, r + 2 * s->K, size_t(s->K) * vb);
+        }
+    }
+    if (npix) CUDA_TRY(cudaMemcpy(npix, s->npix, size_t(s->n_vox) * s->K * 2, cudaMemcpyDeviceToHost));
+    if (scalar_sum) CUDA_TRY(cudaMemcpy(scalar_sum, s->ssum, size_t(s->n_vox) * 4, cudaMemcpyDeviceToHost));
+    if (scalar_count) CUDA_TRY(cudaMemcpy(scalar_count, s->scnt, size_t(s->n_vox) * 4, cudaMemcpyDeviceToHost));
+    return DARE_OK;
+}
+
+dare_status dare_session_read_frames(dare_session s, double* rotations) {
+    if (!s || (!rotations && s->n_frames > 0)) return fail(DARE_E_INVALID, "NULL argument");
+    if (s->n_frames > 0) std::memcpy(rotations, s->frames_host.data(), s->frames_host.size() * sizeof(double));
+    return DARE_OK;
+}
+
+dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t n, int32_t width, int32_t height,
+                              const double px_mm[2], const double* image_to_world, void* stream) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    if (n < 0 || width < 1 || height < 1 || width > 65535 || height > 65535)
+        return fail(DARE_E_INVALID, "bad frame count or size");
+    if (n == 0) return DARE_OK;
+    if (!frames_dev || !image_to_world || !px_mm) return fail(DARE_E_INVALID, "NULL argument");
+    if (!(px_mm[0] > 0 && px_mm[1] > 0) || !std::isfinite(px_mm[0]) || !std::isfinite(px_mm[1]))
+        return fail(DARE_E_INVALID, "pixel spacing must be positive and finite");
+    if (int64_t(s->n_frames) + n > s->cfg.max_frames)
+        return fail(DARE_E_CAPACITY, "%d frames + %d new exceed max_frames %d", s->n_frames, n, s->cfg.max_frames);
+    const int64_t npx = int64_t(width) * height;
+    if (npx > kMaxPixelsPerChunk) return fail(DARE_E_INVALID, "frame too large");
+    const double* V = s->cfg.grid.vol_to_world;
+    const double h = s->cfg.grid.spacing_mm;
+    std::vector<int64_t> aff(size_t(n) * 9);
+    std::vector<double> rot(size_t(n) * 9);
+    for (int32_t f = 0; f < n; ++f) {
+        const double* T = image_to_world + 16 * size_t(f);
+        if (!rigid_ok(T)) return fail(DARE_E_INVALID, "frame pose %d is not a rigid transform", f);
+        if (!affine_ok(V, h, T, width, px_mm[0], px_mm[1]))
+            return fail(DARE_E_INVALID, "frame %d too far from the grid for fixed-point coordinates", f);
+        compose_affine(V, h, T, width, px_mm[0], px_mm[1], &aff[9 * size_t(f)]);
+        relative_rotation(V, T, &rot[9 * size_t(f)]);
+    }
+    DeviceGuard dg(s->cfg.device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int32_t chunk = static_cast<int32_t>(std::max<int64_t>(1, kMaxPixelsPerChunk / npx));
+    const int32_t n_chunk = std::min(n, chunk);
+    // workspace: offsets (n_vox + 1), scan block sums, entries, affines
+    const int64_t nbs = scan_block_sums_needed(s->n_vox);
+    const size_t o_off = 0;
+    const size_t o_bs = align_up(o_off + size_t(s->n_vox + 1) * 4, 256);
+    const size_t o_ent = align_up(o_bs + size_t(nbs) * 4, 256);
+    const size_t o_aff = align_up(o_ent + size_t(n_chunk) * npx * 4, 256);
+    const size_t ws_need = align_up(o_aff + size_t(n) * 9 * 8, 256);
+    dare_status rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    rc = ensure_workspace(s, ws_need, st);
+    if (rc != DARE_OK) return rc;
+    rc = ensure_pinned(s, 0, size_t(n) * 9 * 8 * 2);
+    if (rc != DARE_OK) return rc;
+    uint8_t* ws = static_cast<uint8_t*>(s->ws);
+    int32_t* offsets = reinterpret_cast<int32_t*>(ws + o_off);
+    int32_t* bsums = reinterpret_cast<int32_t*>(ws + o_bs);
+    uint32_t* entries = reinterpret_cast<uint32_t*>(ws + o_ent);
+    int64_t* aff_dev = reinterpret_cast<int64_t*>(ws + o_aff);
+    uint8_t* pin = static_cast<uint8_t*>(s->pinned[0]);
+    std::memcpy(pin, aff.data(), aff.size() * 8);
+    std::memcpy(pin + aff.size() * 8, rot.data(), rot.size() * 8);
+    CUDA_TRY(cudaMemcpyAsync(aff_dev, pin, aff.size() * 8, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(s->frames_dev + size_t(s->n_frames) * 9, pin + aff.size() * 8, rot.size() * 8,
+                             cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaEventRecord(s->pinned_ev[0], st));
+    for (int32_t c0 = 0; c0 < n; c0 += n_chunk) {
+        const int32_t nc = std::min(n_chunk, n - c0);
+        ScatterArgs a{};
+        a.frames = frames_dev + size_t(c0) * npx;
+        a.affines = aff_dev + size_t(c0) * 9;
+        a.n = nc;
+        a.width = width;
+        a.height = height;
+        for (int k = 0; k < 3; ++k) a.dims[k] = s->cfg.grid.dims[k];
+        a.frame_base = s->n_frames + c0;
+        {
+            KernelScope ks("scatter_count", st, 1);
+            CUDA_TRY(launch_scatter_count(a, s->count, st));
+        }
+        {
+            KernelScope ks("exclusive_scan", st, 3);
+            CUDA_TRY(launch_exclusive_scan(s->count, offsets, s->n_vox, bsums, nbs, st));
+        }
+        {
+            KernelScope ks("scatter_place", st, 1);
+            CUDA_TRY(launch_scatter_place(a, s->count, offsets, entries, st));
+        }
+        {
+            KernelScope ks("finalize", st, 1);
+            CUDA_TRY(launch_finalize(offsets, entries, s->n_vox, s->rec, s->npix, s->ssum, s->scnt, s->K, s->dtype,
+                                     s->overflow_dev, st));
+        }
+    }
+    rc = session_end(s, st);
+    if (rc != DARE_OK) return rc;
+    s->frames_host.insert(s->frames_host.end(), rot.begin(), rot.end());
+    s->n_frames += n;
+    s->version += 1;
+    return DARE_OK;
+}
+
+dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
+                         uint32_t* mask_dev, void* stream) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    dare_status rc = check_plane(plane);
+    if (rc != DARE_OK) return rc;
+    rc = check_params(params);
+    if (rc != DARE_OK) return rc;
+    if (!out_dev || !mask_dev) return fail(DARE_E_INVALID, "output pointers are NULL");
+    if (!affine_ok(s->cfg.grid.vol_to_world, s->cfg.grid.spacing_mm, plane->image_to_world, plane->width,
+                   plane->px_mm[0], plane->px_mm[1]))
+        return fail(DARE_E_INVALID, "plane too far from the grid for fixed-point coordinates");
+    DeviceGuard dg(s->cfg.device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    const int wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
+    rc = ensure_workspace(s, align_up(size_t(std::max(s->n_frames, 1)) * wb, 256), st);
+    if (rc != DARE_OK) return rc;
+    TableJob tj{};
+    plane_vectors(s, plane, params->normal_axis, &tj);
+    tj.frames = s->frames_dev;
+    tj.wtab = s->ws;
+    tj.n_frames = s->n_frames;
+    if (s->n_frames > 0) {
+        KernelScope ks("weight_table", st, 1);
+        CUDA_TRY(launch_weight_tables(nullptr, &tj, 1, s->n_frames, table_params(params), st));
+    }
+    ResliceJob job = make_job(s, plane, s->ws, out_dev, mask_dev, params->unassigned);
+    const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
+    if (use_tiled(params)) {
+        job.tile_base = 0;
+        KernelScope ks("reslice_tiled", st, 1);
+        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), s->K, s->dtype, half_w, st));
+    } else {
+        KernelScope ks("reslice_plain", st, 1);
+        CUDA_TRY(launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, s->K, s->dtype, half_w, st));
+    }
+    return session_end(s, st);
+}
+
+dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream) {
+    if (n < 0 || (n > 0 && !reqs)) return fail(DARE_E_INVALID, "bad request list");
+    if (n == 0) return DARE_OK;
+    dare_status rc = check_params(params);
+    if (rc != DARE_OK) return rc;
+    dare_session s0 = reqs[0].session;
+    for (int32_t i = 0; i < n; ++i) {
+        const dare_reslice_req& r = reqs[i];
+        if (!r.session) return fail(DARE_E_INVALID, "request %d has no session", i);
+        if (r.session->cfg.device != s0->cfg.device) return fail(DARE_E_INVALID, "requests span devices");
+        rc = check_plane(&r.plane);
+        if (rc != DARE_OK) return fail(rc, "request %d: %s", i, g_err.c_str());
+        if (!r.out || !r.mask) return fail(DARE_E_INVALID, "request %d: output pointers are NULL", i);
+        if (!affine_ok(r.session->cfg.grid.vol_to_world, r.session->cfg.grid.spacing_mm, r.plane.image_to_world,
+                       r.plane.width, r.plane.px_mm[0], r.plane.px_mm[1]))
+            return fail(DARE_E_INVALID, "request %d: plane too far from the grid", i);
+    }
+    DeviceGuard dg(s0->cfg.device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    // distinct sessions, in first-seen order
+    std::vector<dare_session> sess;
+    for (int32_t i = 0; i < n; ++i)
+        if (std::find(sess.begin(), sess.end(), reqs[i].session) == sess.end()) sess.push_back(reqs[i].session);
+    for (auto* s : sess) {
+        rc = session_begin(s, st);
+        if (rc != DARE_OK) return rc;
+    }
+    const int wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
+    // workspace: tables, then table jobs, then reslice jobs
+    std::vector<size_t> t_off(n);
+    size_t o = 0;
+    int max_frames = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        t_off[i] = o;
+        o = align_up(o + size_t(std::max(reqs[i].session->n_frames, 1)) * wb, 256);
+        max_frames = std::max(max_frames, reqs[i].session->n_frames);
+    }
+    const size_t o_tj = o;
+    const size_t o_rj = align_up(o_tj + size_t(n) * sizeof(TableJob), 256);
+    const size_t need = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    rc = ensure_workspace(s0, need, st);
+    if (rc != DARE_OK) return rc;
+    const size_t desc_bytes = need - o_tj;
+    rc = ensure_pinned(s0, 1, desc_bytes);
+    if (rc != DARE_OK) return rc;
+    uint8_t* ws = static_cast<uint8_t*>(s0->ws);
+    uint8_t* pin = static_cast<uint8_t*>(s0->pinned[1]);
+    auto* tjs = reinterpret_cast<TableJob*>(pin);
+    auto* rjs = reinterpret_cast<ResliceJob*>(pin + (o_rj - o_tj));
+    // order jobs by (K, dtype) so each launch covers one group
+    std::vector<int32_t> order(n);
+    for (int32_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        const auto* sa = reqs[a].session;
+        const auto* sb = reqs[b].session;
+        return sa->K != sb->K ? sa->K < sb->K : sa->dtype < sb->dtype;
+    });
+    int total_tiles = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        const dare_reslice_req& r = reqs[order[k]];
+        void* wtab = ws + t_off[order[k]];
+        TableJob tj{};
+        plane_vectors(r.session, &r.plane, params->normal_axis, &tj);
+        tj.frames = r.session->frames_dev;
+        tj.wtab = wtab;
+        tj.n_frames = r.session->n_frames;
+        tjs[k] = tj;
+        rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, params->unassigned);
+        rjs[k].tile_base = total_tiles;
+        total_tiles += tiles_of(&r.plane);
+    }
+    CUDA_TRY(cudaMemcpyAsync(ws + o_tj, pin, desc_bytes, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaEventRecord(s0->pinned_ev[1], st));
+    const auto* tj_dev = reinterpret_cast<const TableJob*>(ws + o_tj);
+    const auto* rj_dev = reinterpret_cast<const ResliceJob*>(ws + o_rj);
+    if (max_frames > 0) {
+        KernelScope ks("weight_table", st, 1);
+        CUDA_TRY(launch_weight_tables(tj_dev, nullptr, n, max_frames, table_params(params), st));
+    }
+    const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
+    for (int32_t k0 = 0; k0 < n;) {
+        const auto* sg = reqs[order[k0]].session;
+        int32_t k1 = k0;
+        int max_w = 0, max_h = 0;
+        while (k1 < n && reqs[order[k1]].session->K == sg->K && reqs[order[k1]].session->dtype == sg->dtype) {
+            max_w = std::max(max_w, reqs[order[k1]].plane.width);
+            max_h = std::max(max_h, reqs[order[k1]].plane.height);
+            ++k1;
+        }
+        if (use_tiled(params)) {
+            // tile bases restart per group
+            const int base = rjs[k0].tile_base;
+            const int end = (k1 < n) ? rjs[k1].tile_base : total_tiles;
+            KernelScope ks("reslice_tiled", st, 1);
+            CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, end - base, sg->K, sg->dtype, half_w, st));
+        } else {
+            KernelScope ks("reslice_plain", st, 1);
+            CUDA_TRY(launch_reslice_plain(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
+        }
+        k0 = k1;
+    }
+    for (auto* s : sess) {
+        rc = session_end(s, st);
+        if (rc != DARE_OK) return rc;
+    }
+    return DARE_OK;
+}
+
+dare_status dare_reslice_scalar(dare_session s, const dare_plane* plane, float unassigned, float* out_dev,
+                                uint32_t* mask_dev, void* stream) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    dare_status rc = check_plane(plane);
+    if (rc != DARE_OK) return rc;
+    if (!s->ssum) return fail(DARE_E_STATE, "session was created without DARE_SESSION_SCALAR");
+    if (!out_dev || !mask_dev) return fail(DARE_E_INVALID, "output pointers are NULL");
+    if (!affine_ok(s->cfg.grid.vol_to_world, s->cfg.grid.spacing_mm, plane->image_to_world, plane->width,
+                   plane->px_mm[0], plane->px_mm[1]))
+        return fail(DARE_E_INVALID, "plane too far from the grid for fixed-point coordinates");
+    DeviceGuard dg(s->cfg.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    ResliceJob job = make_job(s, plane, nullptr, out_dev, mask_dev, unassigned);
+    {
+        KernelScope ks("reslice_scalar", st, 1);
+        CUDA_TRY(launch_reslice_scalar(job, s->ssum, s->scnt, st));
+    }
+    return session_end(s, st);
+}
+
+dare_status dare_footprint(dare_session s, const dare_plane* planes, int32_t n, int64_t* counts, void* stream) {
+    if (!s || (n > 0 && (!planes || !counts)) || n < 0) return fail(DARE_E_INVALID, "bad arguments");
+    for (int32_t i = 0; i < n; ++i) {
+        dare_status rc = check_plane(planes + i);
+        if (rc != DARE_OK) return rc;
+        if (!affine_ok(s->cfg.grid.vol_to_world, s->cfg.grid.spacing_mm, planes[i].image_to_world, planes[i].width,
+                       planes[i].px_mm[0], planes[i].px_mm[1]))
+            return fail(DARE_E_INVALID, "plane %d too far from the grid", i);
+    }
+    if (n == 0) return DARE_OK;
+    DeviceGuard dg(s->cfg.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    dare_status rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    const size_t words = size_t((s->n_vox + 31) / 32);
+    const size_t need = align_up(words * 4, 256) + 256 * size_t(n);
+    rc = ensure_workspace(s, need, st);
+    if (rc != DARE_OK) return rc;
+    uint32_t* bitmap = static_cast<uint32_t*>(s->ws);
+    auto* cnt = reinterpret_cast<unsigned long long*>(static_cast<uint8_t*>(s->ws) + align_up(words * 4, 256));
+    CUDA_TRY(cudaMemsetAsync(cnt, 0, 256 * size_t(n), st));
+    for (int32_t i = 0; i < n; ++i) {
+        CUDA_TRY(cudaMemsetAsync(bitmap, 0, words * 4, st));
+        ResliceJob job = make_job(s, planes + i, nullptr, nullptr, nullptr, 0.0f);
+        KernelScope ks("footprint", st, 1);
+        CUDA_TRY(launch_footprint(job, bitmap, cnt + 32 * size_t(i), st));
+    }
+    std::vector<unsigned long long> host(32 * size_t(n));
+    CUDA_TRY(cudaMemcpyAsync(host.data(), cnt, host.size() * 8, cudaMemcpyDeviceToHost, st));
+    rc = session_end(s, st);
+    if (rc != DARE_OK) return rc;
+    CUDA_TRY(cudaStreamSynchronize(st));
+    for (int32_t i = 0; i < n; ++i) counts[i] = static_cast<int64_t>(host[32 * size_t(i)]);
+    return DARE_OK;
+}
+
+dare_status dare_session_reset(dare_session s, void* stream) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    DeviceGuard dg(s->cfg.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    dare_status rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    {
+        KernelScope ks("fill_records", st, 1);
+        CUDA_TRY(launch_fill_records(s->rec, s->n_vox, s->rec_bytes, s->K, st));
+    }
+    CUDA_TRY(cudaMemsetAsync(s->npix, 0, size_t(s->n_vox) * s->K * 2, st));
+    if (s->ssum) {
+        CUDA_TRY(cudaMemsetAsync(s->ssum, 0, size_t(s->n_vox) * 4, st));
+        CUDA_TRY(cudaMemsetAsync(s->scnt, 0, size_t(s->n_vox) * 4, st));
+    }
+    CUDA_TRY(cudaMemsetAsync(s->overflow_dev, 0, sizeof(unsigned long long), st));
+    rc = session_end(s, st);
+    if (rc != DARE_OK) return rc;
+    s->frames_host.clear();
+    s->n_frames = 0;
+    s->version = 0;
+    return DARE_OK;
+}
+
+dare_status dare_trace_enable(int32_t on) {
+    g_trace_on = on != 0;
+    return DARE_OK;
+}
+
+dare_status dare_trace_read(dare_kernel_time* out, int32_t capacity, int32_t* n_out) {
+    if (capacity < 0 || (capacity > 0 && !out) || !n_out) return fail(DARE_E_INVALID, "bad arguments");
+    std::lock_guard<std::mutex> lk(g_trace_mu);
+    dare_status rc = DARE_OK;
+    for (auto& r : g_trace_pending) {
+        float ms = 0.0f;
+        if (cudaEventSynchronize(r.b) != cudaSuccess || cudaEventElapsedTime(&ms, r.a, r.b) != cudaSuccess) {
+            cudaError_t e = cudaGetLastError();
+            rc = fail(DARE_E_CUDA, "trace event: %s", cudaGetErrorString(e));
+        }
+        auto& acc = g_trace_acc[r.name];
+        acc.first += 1;
+        acc.second += ms;
+        g_event_pool[r.device].push_back(r.a);
+        g_event_pool[r.device].push_back(r.b);
+    }
+    g_trace_pending.clear();
+    int32_t n = 0;
+    for (auto& kv : g_trace_acc) {
+        if (n < capacity) {
+            std::memset(&out[n], 0, sizeof(out[n]));
+            std::snprintf(out[n].name, sizeof(out[n].name), "%s", kv.first.c_str());
+            out[n].launches = kv.second.first;
+            out[n].total_ms = kv.second.second;
+        }
+        ++n;
+    }
+    *n_out = n;
+    g_trace_acc.clear();
+    return rc;
+}
+
+int64_t dare_launch_count(void) { return g_launches.load(); }
+
+// ---------------------------------------------------------------- checkpoint
+
+namespace {
+struct FileHeader {
+    char magic[8];          // "DAREVOL1"
+    int32_t abi;
+    int32_t dims[3];
+    double spacing_mm;
+    double vol_to_world[16];
+    int32_t dtype, slots, max_frames, n_frames, flags, rec_bytes;
+    int64_t n_vox;
+    int64_t version;
+    uint32_t crc;           // CRC-32 of everything after the header
+    uint32_t reserved;
+};
+}  // namespace
+
+dare_status dare_session_save(dare_session s, const char* path) {
+    if (!s || !path) return fail(DARE_E_INVALID, "NULL argument");
+    DeviceGuard dg(s->cfg.device);
+    CUDA_TRY(cudaEventSynchronize(s->order_ev));
+    std::vector<uint8_t> rec(size_t(s->n_vox) * s->rec_bytes);
+    std::vector<uint8_t> np(size_t(s->n_vox) * s->K * 2);
+    std::vector<uint8_t> sc(s->ssum ? size_t(s->n_vox) * 8 : 0);
+    CUDA_TRY(cudaMemcpy(rec.data(), s->rec, rec.size(), cudaMemcpyDeviceToHost));
+    CUDA_TRY(cudaMemcpy(np.data(), s->npix, np.size(), cudaMemcpyDeviceToHost));
+    if (s->ssum) {
+        CUDA_TRY(cudaMemcpy(sc.data(), s->ssum, size_t(s->n_vox) * 4, cudaMemcpyDeviceToHost));
+        CUDA_TRY(cudaMemcpy(sc.data() + size_t(s->n_vox) * 4, s->scnt, size_t(s->n_vox) * 4, cudaMemcpyDeviceToHost));
+    }
+    FileHeader hd{};
+    std::memcpy(hd.magic, "DAREVOL1", 8);
+    hd.abi = DARE_ABI_VERSION;
+    for (int a = 0; a < 3; ++a) hd.dims[a] = s->cfg.grid.dims[a];
+    hd.spacing_mm = s->cfg.grid.spacing_mm;
+    std::memcpy(hd.vol_to_world, s->cfg.grid.vol_to_world, sizeof(hd.vol_to_world));
+    hd.dtype = s->dtype;
+    hd.slots = s->K;
+    hd.max_frames = s->cfg.max_frames;
+    hd.n_frames = s->n_frames;
+    hd.flags = s->cfg.flags & DARE_SESSION_SCALAR;
+    hd.rec_bytes = s->rec_bytes;
+    hd.n_vox = s->n_vox;
+    hd.version = s->version;
+    uint32_t crc = 0;
+    crc = crc32_update(crc, s->frames_host.data(), s->frames_host.size() * 8);
+    crc = crc32_update(crc, rec.data(), rec.size());
+    crc = crc32_update(crc, np.data(), np.size());
+    crc = crc32_update(crc, sc.data(), sc.size());
+    hd.crc = crc;
+    FILE* fp = std::fopen(path, "wb");
+    if (!fp) return fail(DARE_E_INVALID, "cannot open %s for writing", path);
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1;
+    ok = ok && (s->frames_host.empty() || std::fwrite(s->frames_host.data(), 8, s->frames_host.size(), fp) == s->frames_host.size());
+    ok = ok && std::fwrite(rec.data(), 1, rec.size(), fp) == rec.size();
+    ok = ok && std::fwrite(np.data(), 1, np.size(), fp) == np.size();
+    ok = ok && (sc.empty() || std::fwrite(sc.data(), 1, sc.size(), fp) == sc.size());
+    ok = (std::fclose(fp) == 0) && ok;
+    if (!ok) return fail(DARE_E_INVALID, "writing %s failed", path);
+    return DARE_OK;
+}
+
+dare_status dare_session_load(const dare_session_config* cfg, const char* path, dare_session* out) {
+    if (!cfg || !path || !out) return fail(DARE_E_INVALID, "NULL argument");
+    *out = nullptr;
+    FILE* fp = std::fopen(path, "rb");
+    if (!fp) return fail(DARE_E_INVALID, "cannot open %s", path);
+    FileHeader hd{};
+    auto close_fail = [&](const char* why) {
+        std::fclose(fp);
+        return fail(DARE_E_INVALID, "%s: %s", path, why);
+    };
+    if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "DAREVOL1", 8) != 0)
+        return close_fail("not a DARE volume file");
+    if (hd.abi != DARE_ABI_VERSION) return close_fail("ABI version mismatch");
+    if (hd.n_frames < 0 || hd.n_frames > hd.max_frames || hd.max_frames > DARE_MAX_FRAMES ||
+        hd.n_vox != int64_t(hd.dims[0]) * hd.dims[1] * hd.dims[2] || hd.n_vox <= 0 ||
+        hd.rec_bytes != record_bytes(hd.slots, hd.dtype))
+        return close_fail("inconsistent header");
+    std::vector<double> frames(size_t(hd.n_frames) * 9);
+    std::vector<uint8_t> rec(size_t(hd.n_vox) * hd.rec_bytes);
+    std::vector<uint8_t> np(size_t(hd.n_vox) * hd.slots * 2);
+    std::vector<uint8_t> sc((hd.flags & DARE_SESSION_SCALAR) ? size_t(hd.n_vox) * 8 : 0);
+    bool ok = frames.empty() || std::fread(frames.data(), 8, frames.size(), fp) == frames.size();
+    ok = ok && std::fread(rec.data(), 1, rec.size(), fp) == rec.size();
+    ok = ok && std::fread(np.data(), 1, np.size(), fp) == np.size();
+    ok = ok && (sc.empty() || std::fread(sc.data(), 1, sc.size(), fp) == sc.size());
+    if (!ok) return close_fail("truncated file");
+    std::fclose(fp);
+    uint32_t crc = 0;
+    crc = crc32_update(crc, frames.data(), frames.size() * 8);
+    crc = crc32_update(crc, rec.data(), rec.size());
+    crc = crc32_update(crc, np.data(), np.size());
+    crc = crc32_update(crc, sc.data(), sc.size());
+    if (crc != hd.crc) return fail(DARE_E_INVALID, "%s: CRC mismatch (corrupted file)", path);
+    dare_session_config c = *cfg;
+    for (int a = 0; a < 3; ++a) c.grid.dims[a] = hd.dims[a];
+    c.grid.spacing_mm = hd.spacing_mm;
+    std::memcpy(c.grid.vol_to_world, hd.vol_to_world, sizeof(hd.vol_to_world));
+    c.dtype = hd.dtype;
+    c.max_slots = hd.slots;
+    c.max_frames = hd.max_frames;
+    c.flags = (cfg->flags & ~DARE_SESSION_SCALAR) | (hd.flags & DARE_SESSION_SCALAR);
+    dare_session s = nullptr;
+    dare_status rc = dare_session_create(&c, &s);
+    if (rc != DARE_OK) return rc;
+    DeviceGuard dg(s->cfg.device);
+    auto bail = [&](cudaError_t e) {
+        dare_session_destroy(s);
+        return fail(DARE_E_CUDA, "upload failed: %s", cudaGetErrorString(e));
+    };
+    cudaError_t e;
+    if ((e = cudaMemcpy(s->rec, rec.data(), rec.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
+    if ((e = cudaMemcpy(s->npix, np.data(), np.size(), cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
+    if (!frames.empty() &&
+        (e = cudaMemcpy(s->frames_dev, frames.data(), frames.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+        return bail(e);
+    if (!sc.empty()) {
+        if ((e = cudaMemcpy(s->ssum, sc.data(), size_t(hd.n_vox) * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
+        if ((e = cudaMemcpy(s->scnt, sc.data() + size_t(hd.n_vox) * 4, size_t(hd.n_vox) * 4, cudaMemcpyHostToDevice)) !=
+            cudaSuccess)
+            return bail(e);
+    }
+    s->frames_host = std::move(frames);
+    s->n_frames = hd.n_frames;
+    s->version = hd.version;
+    *out = s;
+    return DARE_OK;
+}
+
+}  // extern "C"

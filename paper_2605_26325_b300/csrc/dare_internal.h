@@ -1,0 +1,93 @@
+// Internal types shared by the host side (api.cpp) and the kernels (*.cu).
+//
+// Device record layout (one per voxel, 16-byte aligned, stride rec_bytes =
+// round_up(2 K + K sizeof(value), 16)):
+//   bytes [0, 2K)          K frame ids, uint16, ascending, 0xFFFF = empty (last)
+//   bytes [2K, 2K + K vb)  K stored intensities of the storage type
+// The build-only npix plane holds K uint16 per voxel in a separate array.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#include "../../include/dare.h"
+
+namespace dare {
+
+constexpr int kFixBits = DARE_FIX_BITS;
+constexpr int64_t kFixOne = int64_t(1) << kFixBits;
+constexpr int kMaxPixelsPerChunk = 1 << 30;  // entries of one scatter pass
+
+inline int value_bytes(int dtype) { return dtype == DARE_U8 ? 1 : (dtype == DARE_F32 ? 4 : 2); }
+inline int record_bytes(int K, int dtype) { return (2 * K + K * value_bytes(dtype) + 15) / 16 * 16; }
+
+// One plane to reslice, as the kernels see it.
+struct ResliceJob {
+    int64_t g0[3], a[3], b[3];  // fixed-point pixel -> voxel affine (2^-20 voxel)
+    const uint8_t* rec;         // records of the plane's volume
+    const void* wtab;           // per-frame weight table (float or __half)
+    float* out;                 // height x width
+    uint32_t* mask;             // height x mask_stride
+    int32_t dims[3];
+    int32_t width, height;
+    int32_t mask_stride;        // ceil(width / 32)
+    int32_t tile_base;          // first tile of this job in a batched launch
+    int32_t tiles_x;            // tiles per tile row
+    float unassigned;
+    int32_t pad;
+};
+
+// Inputs of the per-(plane, frame) weight table of Eq. 1 / Eq. 2.
+struct TableJob {
+    double n_r[3];          // plane normal (beam or elevation) in the volume frame
+    double x_r[3];          // plane lateral direction in the volume frame
+    const double* frames;   // n_frames x 9 row-major rotations (volume frame)
+    void* wtab;             // output, n_frames entries
+    int32_t n_frames;
+    int32_t pad;
+};
+
+struct TableParams {
+    double k_normal, k_inplane;
+    double cos_normal, cos_inplane;
+    int32_t use_normal, use_inplane;  // thresholds active
+    int32_t normal_axis;              // 1: beam column, 2: elevation column
+    int32_t half;                     // table in FP16
+};
+
+struct ScatterArgs {
+    const uint8_t* frames;    // n x H x W
+    const int64_t* affines;   // n x 9 (G0, A, B)
+    int32_t n, width, height;
+    int32_t dims[3];
+    int32_t frame_base;       // global id of frame 0 of this chunk
+};
+
+// ------------------------------------------------------------ launchers (kernels.cu)
+cudaError_t launch_weight_tables(const TableJob* jobs_dev, const TableJob* one_job, int n_jobs, int max_frames,
+                                 const TableParams& p, cudaStream_t st);
+cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int max_w,
+                                 int max_h, int K, int dtype, int half_weights, cudaStream_t st);
+cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, cudaStream_t st);
+cudaError_t launch_scatter_place(const ScatterArgs& a, int32_t* count, const int32_t* offsets, uint32_t* entries,
+                                 cudaStream_t st);
+cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
+                                  int64_t block_sums_len, cudaStream_t st);
+int64_t scan_block_sums_needed(int64_t n);
+cudaError_t launch_finalize(const int32_t* offsets, const uint32_t* entries, int64_t n_vox, uint8_t* rec,
+                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
+                            unsigned long long* overflow, cudaStream_t st);
+cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
+                                  cudaStream_t st);
+cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned long long* count, cudaStream_t st);
+cudaError_t launch_fill_records(uint8_t* rec, int64_t n_vox, int rec_bytes, int K, cudaStream_t st);
+
+// tiled kernel (kernels_tiled.cu)
+cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
+                                 int tile_offset, int n_tiles, int K, int dtype, int half_weights, cudaStream_t st);
+constexpr int kTileW = 32;
+constexpr int kTileH = 16;
+
+}  // namespace dare

@@ -1,0 +1,89 @@
+// Device helpers shared by the reslice kernels: record decoding and the
+// fixed-point pixel coordinate.
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "dare_internal.h"
+
+namespace dare {
+namespace dev {
+
+__device__ __forceinline__ float to_f(uint8_t v) { return static_cast<float>(v); }
+__device__ __forceinline__ float to_f(__half v) { return __half2float(v); }
+__device__ __forceinline__ float to_f(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float to_f(float v) { return v; }
+
+__device__ __forceinline__ float weight_of(const float* w, int id) { return __ldg(w + id); }
+__device__ __forceinline__ float weight_of(const __half* w, int id) { return __half2float(__ldg(w + id)); }
+
+template <int K, typename VT>
+struct RecShape {
+    static constexpr int kBytes = (2 * K + K * int(sizeof(VT)) + 15) / 16 * 16;
+    static constexpr int kVec = kBytes / 16;
+    static constexpr int kWords = kBytes / 4;
+};
+
+__device__ __forceinline__ uint32_t word_of(const uint4* r, int w) {
+    const uint4 q = r[w >> 2];
+    const int k = w & 3;
+    return k == 0 ? q.x : (k == 1 ? q.y : (k == 2 ? q.z : q.w));
+}
+
+// frame id of slot s (s is a compile-time constant after unrolling)
+template <int K, typename VT>
+__device__ __forceinline__ uint32_t slot_id(const uint4* r, int s) {
+    return (word_of(r, s >> 1) >> (16 * (s & 1))) & 0xFFFFu;
+}
+
+template <int K, typename VT>
+__device__ __forceinline__ float slot_value(const uint4* r, int s) {
+    if constexpr (sizeof(VT) == 1) {
+        const int b = 2 * K + s;
+        return static_cast<float>((word_of(r, b >> 2) >> (8 * (b & 3))) & 0xFFu);
+    } else if constexpr (sizeof(VT) == 2) {
+        const uint32_t w = word_of(r, K / 2 + (s >> 1));
+        const unsigned short bits = static_cast<unsigned short>((w >> (16 * (s & 1))) & 0xFFFFu);
+        VT v;
+        memcpy(&v, &bits, 2);
+        return to_f(v);
+    } else {
+        return __uint_as_float(word_of(r, K / 2 + s));
+    }
+}
+
+template <int K, typename VT>
+__device__ __forceinline__ void load_record(const uint8_t* p, uint4 (&r)[RecShape<K, VT>::kVec]) {
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int i = 0; i < RecShape<K, VT>::kVec; ++i) r[i] = __ldg(q + i);
+}
+
+// Fixed-point pixel coordinate: integer voxel part and 20-bit fraction.
+struct PixelCoord {
+    int c0[3];
+    float fr[3];
+    bool any;  // false when no corner of the TENT(R=1) support can be in the grid
+};
+
+__device__ __forceinline__ PixelCoord pixel_coord(const ResliceJob& J, int u, int v) {
+    PixelCoord pc;
+    pc.any = true;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t G = J.g0[a] + static_cast<int64_t>(u) * J.a[a] + static_cast<int64_t>(v) * J.b[a];
+        const int64_t c = G >> kFixBits;  // arithmetic shift: floor
+        pc.fr[a] = static_cast<float>(static_cast<int32_t>(G & (kFixOne - 1))) * (1.0f / static_cast<float>(kFixOne));
+        if (c < -1 || c > J.dims[a] - 1) {
+            pc.any = false;
+            pc.c0[a] = 0;
+        } else {
+            pc.c0[a] = static_cast<int>(c);
+        }
+    }
+    return pc;
+}
+
+}  // namespace dev
+}  // namespace dare

@@ -1,0 +1,600 @@
+// DARE device kernels for sm_103a: per-frame weight tables (Eq. 1, Eq. 2),
+// the plain one-thread-per-pixel reslice, the reconstruction scatter
+// (count / scan / place / finalize), the mean-compounding comparator and the
+// footprint counter.
+//
+// The path is a gather, not a contraction: no tensor cores.  Every kernel is
+// bounded by memory or by issue rate, so the work is laid out for coalescing
+// (warps walk image rows, records are 16-byte aligned and loaded as uint4).
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <cfloat>
+#include <climits>
+
+#include "dare_internal.h"
+#include "device_common.cuh"
+
+namespace dare {
+namespace {
+
+using namespace dev;
+
+
+// ------------------------------------------------------------------ S2: weight table
+
+__global__ void __launch_bounds__(256) k_weight_table(const TableJob* __restrict__ jobs,
+                                                      const __grid_constant__ TableJob one, TableParams p) {
+    const TableJob& J = jobs ? jobs[blockIdx.y] : one;
+    const int n = J.n_frames;
+    const double n0 = J.n_r[0], n1 = J.n_r[1], n2 = J.n_r[2];
+    const double x0 = J.x_r[0], x1 = J.x_r[1], x2 = J.x_r[2];
+    const int col = p.normal_axis;  // 1 = beam, 2 = elevation
+    for (int f = blockIdx.x * blockDim.x + threadIdx.x; f < n; f += gridDim.x * blockDim.x) {
+        const double* R = J.frames + 9 * static_cast<size_t>(f);
+        // Eq. 1: signed normal agreement, absolute in-plane agreement
+        const double dn = R[col] * n0 + R[3 + col] * n1 + R[6 + col] * n2;
+        const double di = fabs(R[0] * x0 + R[3] * x1 + R[6] * x2);
+        const bool pass = (!p.use_normal || dn >= p.cos_normal) && (!p.use_inplane || di >= p.cos_inplane);
+        float w = 0.0f;
+        if (pass) {
+            // Eq. 2; a valid sample never gets weight 0 (coverage stays exact)
+            w = fmaxf(expf(static_cast<float>(p.k_normal * (dn - 1.0) + p.k_inplane * (di - 1.0))), FLT_MIN);
+        }
+        if (p.half) {
+            __half h = __float2half_rn(w);
+            if (pass && __half2float(h) == 0.0f) h = __ushort_as_half(1);  // smallest subnormal
+            static_cast<__half*>(J.wtab)[f] = h;
+        } else {
+            static_cast<float*>(J.wtab)[f] = w;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ K1: plain reslice
+
+// One thread per pixel, 32 x 8 threads per block; a warp walks 32 pixels of a
+// row, so its ballot is the row's mask word.  Every pixel reads the full
+// records of its 8 TENT corners straight from global memory.
+template <int K, typename VT, typename WT>
+__device__ __forceinline__ void plain_body(const ResliceJob& J) {
+    const int lane = threadIdx.x;
+    const int u = blockIdx.x * 32 + lane;
+    const int v = blockIdx.y * 8 + threadIdx.y;
+    if (v >= J.height || static_cast<int>(blockIdx.x) * 32 >= J.width) return;  // warp-uniform
+    const bool active = u < J.width;
+    const WT* wt = static_cast<const WT*>(J.wtab);
+    float num = 0.0f, den = 0.0f;
+    if (active) {
+        const PixelCoord pc = pixel_coord(J, u, v);
+        if (pc.any) {
+#pragma unroll 1
+            for (int corner = 0; corner < 8; ++corner) {
+                const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+                const int cx = pc.c0[0] + dx, cy = pc.c0[1] + dy, cz = pc.c0[2] + dz;
+                if (cx < 0 || cy < 0 || cz < 0 || cx >= J.dims[0] || cy >= J.dims[1] || cz >= J.dims[2]) continue;
+                const float t = (dx ? pc.fr[0] : 1.0f - pc.fr[0]) * (dy ? pc.fr[1] : 1.0f - pc.fr[1]) *
+                                (dz ? pc.fr[2] : 1.0f - pc.fr[2]);
+                const int64_t vi = cx + static_cast<int64_t>(J.dims[0]) * (cy + static_cast<int64_t>(J.dims[1]) * cz);
+                uint4 r[RecShape<K, VT>::kVec];
+                load_record<K, VT>(J.rec + vi * RecShape<K, VT>::kBytes, r);
+#pragma unroll
+                for (int s = 0; s < K; ++s) {
+                    const uint32_t id = slot_id<K, VT>(r, s);
+                    if (id == DARE_EMPTY_FRAME) break;
+                    const float w = t * weight_of(wt, static_cast<int>(id));
+                    num = fmaf(w, slot_value<K, VT>(r, s), num);
+                    den += w;
+                }
+            }
+        }
+        J.out[static_cast<int64_t>(v) * J.width + u] = den > 0.0f ? num / den : J.unassigned;
+    }
+    const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);
+    if (lane == 0) J.mask[static_cast<int64_t>(v) * J.mask_stride + blockIdx.x] = bits;
+}
+
+template <int K, typename VT, typename WT>
+__global__ void __launch_bounds__(256) k_reslice_plain_one(const __grid_constant__ ResliceJob J) {
+    plain_body<K, VT, WT>(J);
+}
+
+template <int K, typename VT, typename WT>
+__global__ void __launch_bounds__(256) k_reslice_plain_batch(const ResliceJob* __restrict__ jobs) {
+    plain_body<K, VT, WT>(jobs[blockIdx.z]);
+}
+
+template <int K, typename VT, typename WT>
+cudaError_t plain_launch(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int max_w, int max_h,
+                         cudaStream_t st) {
+    dim3 block(32, 8);
+    dim3 grid((max_w + 31) / 32, (max_h + 7) / 8, one ? 1 : n_jobs);
+    if (one)
+        k_reslice_plain_one<K, VT, WT><<<grid, block, 0, st>>>(*one);
+    else
+        k_reslice_plain_batch<K, VT, WT><<<grid, block, 0, st>>>(jobs_dev);
+    return cudaPeekAtLastError();
+}
+
+template <int K, typename VT>
+cudaError_t plain_launch_w(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int max_w, int max_h,
+                           int half_w, cudaStream_t st) {
+    return half_w ? plain_launch<K, VT, __half>(jobs_dev, one, n_jobs, max_w, max_h, st)
+                  : plain_launch<K, VT, float>(jobs_dev, one, n_jobs, max_w, max_h, st);
+}
+
+template <int K>
+cudaError_t plain_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int max_w, int max_h,
+                           int dtype, int half_w, cudaStream_t st) {
+    switch (dtype) {
+    case DARE_U8: return plain_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, max_w, max_h, half_w, st);
+    case DARE_F16: return plain_launch_w<K, __half>(jobs_dev, one, n_jobs, max_w, max_h, half_w, st);
+    case DARE_BF16: return plain_launch_w<K, __nv_bfloat16>(jobs_dev, one, n_jobs, max_w, max_h, half_w, st);
+    case DARE_F32: return plain_launch_w<K, float>(jobs_dev, one, n_jobs, max_w, max_h, half_w, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ reconstruction scatter
+
+// Nearest voxel of pixel (u, v) of frame f, or -1 outside the grid.
+__device__ __forceinline__ int64_t scatter_voxel(const ScatterArgs& A, int f, int u, int v) {
+    const int64_t* aff = A.affines + 9 * static_cast<int64_t>(f);
+    int64_t c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t G = __ldg(aff + a) + static_cast<int64_t>(u) * __ldg(aff + 3 + a) +
+                          static_cast<int64_t>(v) * __ldg(aff + 6 + a);
+        c[a] = (G + kFixOne / 2) >> kFixBits;  // floor(g + 1/2)
+        if (c[a] < 0 || c[a] >= A.dims[a]) return -1;
+    }
+    return c[0] + static_cast<int64_t>(A.dims[0]) * (c[1] + static_cast<int64_t>(A.dims[1]) * c[2]);
+}
+
+// blockIdx.y = frame; threads walk the frame's pixels in row-major order so
+// neighbouring lanes tend to share a voxel and one atomic serves the group.
+__global__ void __launch_bounds__(256) k_scatter_count(const __grid_constant__ ScatterArgs A, int32_t* count) {
+    const int f = blockIdx.y;
+    const int npx = A.width * A.height;
+    const int lane = threadIdx.x & 31;
+    for (int base = blockIdx.x * blockDim.x; base < npx; base += gridDim.x * blockDim.x) {
+        const int p = base + threadIdx.x;
+        int64_t vi = -1;
+        if (p < npx) vi = scatter_voxel(A, f, p % A.width, p / A.width);
+        const unsigned grp = __match_any_sync(0xFFFFFFFFu, vi);
+        const int leader = __ffs(grp) - 1;
+        if (vi >= 0 && lane == leader) atomicAdd(count + vi, __popc(grp));
+    }
+}
+
+__global__ void __launch_bounds__(256) k_scatter_place(const __grid_constant__ ScatterArgs A, int32_t* count,
+                                                       const int32_t* __restrict__ offsets,
+                                                       uint32_t* __restrict__ entries) {
+    const int f = blockIdx.y;
+    const int npx = A.width * A.height;
+    const int lane = threadIdx.x & 31;
+    const uint8_t* img = A.frames + static_cast<int64_t>(f) * npx;
+    const uint32_t fid = static_cast<uint32_t>(A.frame_base + f);
+    for (int base = blockIdx.x * blockDim.x; base < npx; base += gridDim.x * blockDim.x) {
+        const int p = base + threadIdx.x;
+        int64_t vi = -1;
+        uint32_t val = 0;
+        if (p < npx) {
+            vi = scatter_voxel(A, f, p % A.width, p / A.width);
+            if (vi >= 0) val = __ldg(img + p);
+        }
+        const unsigned grp = __match_any_sync(0xFFFFFFFFu, vi);
+        const int leader = __ffs(grp) - 1;
+        int old = 0;
+        if (vi >= 0 && lane == leader) old = atomicSub(count + vi, __popc(grp));
+        old = __shfl_sync(0xFFFFFFFFu, old, leader);
+        if (vi >= 0) {
+            const int rank = __popc(grp & ((1u << lane) - 1u));
+            // the group fills positions [old - size, old) of the voxel's range
+            const int pos = offsets[vi] + old - __popc(grp) + rank;
+            entries[pos] = (fid << 8) | val;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ exclusive scan (3 passes)
+
+constexpr int kScanThreads = 1024;
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ int block_exclusive_scan(int x, int* smem, int* total) {
+    // warp scan
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int incl = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+        if (lane >= o) incl += y;
+    }
+    if (lane == 31) smem[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        int s = lane < (blockDim.x >> 5) ? smem[lane] : 0;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, s, o);
+            if (lane >= o) s += y;
+        }
+        smem[lane] = s;  // inclusive warp totals
+    }
+    __syncthreads();
+    const int warp_off = warp > 0 ? smem[warp - 1] : 0;
+    *total = smem[(blockDim.x >> 5) - 1];
+    __syncthreads();
+    return warp_off + incl - x;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __restrict__ in, int64_t n,
+                                                              int32_t* __restrict__ block_sums) {
+    __shared__ int smem[32];
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < n) s += in[base + i];
+    int total;
+    block_exclusive_scan(s, smem, &total);
+    if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(int32_t* block_sums, int64_t nb) {
+    __shared__ int smem[32];
+    __shared__ int carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < nb; base += kScanThreads) {
+        const int64_t i = base + threadIdx.x;
+        const int x = i < nb ? block_sums[i] : 0;
+        int total;
+        const int ex = block_exclusive_scan(x, smem, &total);
+        if (i < nb) block_sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t* __restrict__ in, int64_t n,
+                                                            const int32_t* __restrict__ block_sums,
+                                                            int32_t* __restrict__ out) {
+    __shared__ int smem[32];
+    const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
+    int vals[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        vals[i] = base + i < n ? in[base + i] : 0;
+        s += vals[i];
+    }
+    int total;
+    int run = block_sums[blockIdx.x] + block_exclusive_scan(s, smem, &total);
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        if (base + i < n) out[base + i] = run;
+        run += vals[i];
+    }
+    if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
+}
+
+// ------------------------------------------------------------------ finalize
+
+template <typename VT>
+__device__ __forceinline__ VT round_store(int sum, int cnt);
+template <>
+__device__ __forceinline__ float round_store<float>(int sum, int cnt) {
+    return __fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt));
+}
+template <>
+__device__ __forceinline__ __half round_store<__half>(int sum, int cnt) {
+    return __float2half_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 round_store<__nv_bfloat16>(int sum, int cnt) {
+    return __float2bfloat16_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
+}
+template <>
+__device__ __forceinline__ uint8_t round_store<uint8_t>(int sum, int cnt) {
+    const unsigned r = __float2uint_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
+    return static_cast<uint8_t>(r > 255u ? 255u : r);
+}
+
+// One thread per voxel.  The voxel's new entries (frame id << 8 | pixel) are
+// grouped by frame id in ascending order with a selection loop; the result
+// is merged with the samples already stored (whose ids are all lower) and,
+// when more than K samples exist, the K of largest npix are kept (ties:
+// lower frame id).  Integer sums make the outcome independent of the order
+// in which the scatter wrote the entries.
+template <int K, typename VT>
+__global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ offsets,
+                                                  const uint32_t* __restrict__ entries, int64_t n_vox,
+                                                  uint8_t* __restrict__ rec, uint16_t* __restrict__ npix,
+                                                  uint32_t* __restrict__ scal_sum, uint32_t* __restrict__ scal_cnt,
+                                                  unsigned long long* overflow) {
+    constexpr int RB = RecShape<K, VT>::kBytes;
+    for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n_vox;
+         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int s = offsets[v], e = offsets[v + 1];
+        if (s == e) continue;
+        uint16_t* ids = reinterpret_cast<uint16_t*>(rec + v * RB);
+        VT* vals = reinterpret_cast<VT*>(rec + v * RB + 2 * K);
+        uint16_t* np = npix + v * K;
+        int Lid[K], Lnp[K], Lcnt[K], Lsum[K];
+        VT Lraw[K];
+        bool Lnew[K];
+        int m = 0;
+#pragma unroll
+        for (int k = 0; k < K; ++k) {
+            const int id = ids[k];
+            if (id != DARE_EMPTY_FRAME && m == k) {
+                Lid[m] = id;
+                Lnp[m] = np[k];
+                Lcnt[m] = 0;
+                Lsum[m] = 0;
+                Lraw[m] = vals[k];
+                Lnew[m] = false;
+                ++m;
+            }
+        }
+        bool over = false;
+        uint32_t total = 0;
+        int last = -1;
+        for (;;) {
+            int next = INT_MAX, cnt = 0, sum = 0;
+            for (int i = s; i < e; ++i) {
+                const uint32_t x = __ldg(entries + i);
+                const int f = static_cast<int>(x >> 8);
+                if (f > last) {
+                    if (f < next) {
+                        next = f;
+                        cnt = 1;
+                        sum = static_cast<int>(x & 0xFFu);
+                    } else if (f == next) {
+                        ++cnt;
+                        sum += static_cast<int>(x & 0xFFu);
+                    }
+                }
+            }
+            if (next == INT_MAX) break;
+            total += static_cast<uint32_t>(sum);
+            last = next;
+            const int cs = cnt < 65535 ? cnt : 65535;
+            int slot = -1;
+            if (m < K) {
+                slot = m++;
+            } else {
+                over = true;
+                int wi = 0;
+                for (int k = 1; k < K; ++k)
+                    if (Lnp[k] < Lnp[wi] || (Lnp[k] == Lnp[wi] && Lid[k] > Lid[wi])) wi = k;
+                if (cs > Lnp[wi] || (cs == Lnp[wi] && next < Lid[wi])) slot = wi;
+            }
+            if (slot >= 0) {
+                Lid[slot] = next;
+                Lnp[slot] = cs;
+                Lcnt[slot] = cnt;
+                Lsum[slot] = sum;
+                Lnew[slot] = true;
+            }
+        }
+        // order by frame id (insertion sort over at most K entries)
+        for (int i = 1; i < m; ++i) {
+            const int id = Lid[i], pn = Lnp[i], c = Lcnt[i], sm = Lsum[i];
+            const VT raw = Lraw[i];
+            const bool nw = Lnew[i];
+            int j = i - 1;
+            while (j >= 0 && Lid[j] > id) {
+                Lid[j + 1] = Lid[j]; Lnp[j + 1] = Lnp[j]; Lcnt[j + 1] = Lcnt[j];
+                Lsum[j + 1] = Lsum[j]; Lraw[j + 1] = Lraw[j]; Lnew[j + 1] = Lnew[j];
+                --j;
+            }
+            Lid[j + 1] = id; Lnp[j + 1] = pn; Lcnt[j + 1] = c; Lsum[j + 1] = sm; Lraw[j + 1] = raw; Lnew[j + 1] = nw;
+        }
+        for (int k = 0; k < K; ++k) {
+            if (k < m) {
+                ids[k] = static_cast<uint16_t>(Lid[k]);
+                vals[k] = Lnew[k] ? round_store<VT>(Lsum[k], Lcnt[k]) : Lraw[k];
+                np[k] = static_cast<uint16_t>(Lnp[k]);
+            } else {
+                ids[k] = static_cast<uint16_t>(DARE_EMPTY_FRAME);
+                vals[k] = VT(0);
+                np[k] = 0;
+            }
+        }
+        if (scal_sum) {
+            scal_sum[v] += total;
+            scal_cnt[v] += static_cast<uint32_t>(e - s);
+        }
+        if (over) atomicAdd(overflow, 1ull);
+    }
+}
+
+template <int K>
+cudaError_t finalize_k(const int32_t* off, const uint32_t* ent, int64_t n_vox, uint8_t* rec, uint16_t* npix,
+                       uint32_t* ss, uint32_t* sc, int dtype, unsigned long long* ovf, cudaStream_t st) {
+    const int threads = 256;
+    const int64_t want = (n_vox + threads - 1) / threads;
+    const int blocks = static_cast<int>(want < 148 * 64 ? want : 148 * 64);
+    switch (dtype) {
+    case DARE_U8: k_finalize<K, uint8_t><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
+    case DARE_F16: k_finalize<K, __half><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
+    case DARE_BF16:
+        k_finalize<K, __nv_bfloat16><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        break;
+    case DARE_F32: k_finalize<K, float><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaPeekAtLastError();
+}
+
+// ------------------------------------------------------------------ comparator, footprint, fill
+
+__global__ void __launch_bounds__(256) k_reslice_scalar(const __grid_constant__ ResliceJob J,
+                                                        const uint32_t* __restrict__ ssum,
+                                                        const uint32_t* __restrict__ scnt) {
+    const int lane = threadIdx.x;
+    const int u = blockIdx.x * 32 + lane;
+    const int v = blockIdx.y * 8 + threadIdx.y;
+    if (v >= J.height) return;
+    const bool active = u < J.width;
+    float num = 0.0f, den = 0.0f;
+    if (active) {
+        const PixelCoord pc = pixel_coord(J, u, v);
+        if (pc.any) {
+            for (int corner = 0; corner < 8; ++corner) {
+                const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+                const int cx = pc.c0[0] + dx, cy = pc.c0[1] + dy, cz = pc.c0[2] + dz;
+                if (cx < 0 || cy < 0 || cz < 0 || cx >= J.dims[0] || cy >= J.dims[1] || cz >= J.dims[2]) continue;
+                const int64_t vi = cx + static_cast<int64_t>(J.dims[0]) * (cy + static_cast<int64_t>(J.dims[1]) * cz);
+                const uint32_t c = __ldg(scnt + vi);
+                if (c == 0) continue;
+                const float t = (dx ? pc.fr[0] : 1.0f - pc.fr[0]) * (dy ? pc.fr[1] : 1.0f - pc.fr[1]) *
+                                (dz ? pc.fr[2] : 1.0f - pc.fr[2]);
+                const float S = __fdiv_rn(static_cast<float>(__ldg(ssum + vi)), static_cast<float>(c));
+                num = fmaf(t, S, num);
+                den += t;
+            }
+        }
+        J.out[static_cast<int64_t>(v) * J.width + u] = den > 0.0f ? num / den : J.unassigned;
+    }
+    const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);
+    if (lane == 0) J.mask[static_cast<int64_t>(v) * J.mask_stride + blockIdx.x] = bits;
+}
+
+__global__ void __launch_bounds__(256) k_footprint(const __grid_constant__ ResliceJob J, uint32_t* bitmap,
+                                                   unsigned long long* count) {
+    const int u = blockIdx.x * 32 + threadIdx.x;
+    const int v = blockIdx.y * 8 + threadIdx.y;
+    unsigned fresh = 0;
+    if (u < J.width && v < J.height) {
+        const PixelCoord pc = pixel_coord(J, u, v);
+        if (pc.any) {
+            for (int corner = 0; corner < 8; ++corner) {
+                const int cx = pc.c0[0] + (corner & 1), cy = pc.c0[1] + ((corner >> 1) & 1), cz = pc.c0[2] + (corner >> 2);
+                if (cx < 0 || cy < 0 || cz < 0 || cx >= J.dims[0] || cy >= J.dims[1] || cz >= J.dims[2]) continue;
+                const int64_t vi = cx + static_cast<int64_t>(J.dims[0]) * (cy + static_cast<int64_t>(J.dims[1]) * cz);
+                const uint32_t bit = 1u << (vi & 31);
+                const uint32_t old = atomicOr(bitmap + (vi >> 5), bit);
+                if (!(old & bit)) ++fresh;
+            }
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fresh += __shfl_down_sync(0xFFFFFFFFu, fresh, o);
+    if ((threadIdx.x & 31) == 0 && fresh) atomicAdd(count, static_cast<unsigned long long>(fresh));
+}
+
+// Empty records: frame ids 0xFFFF, values 0.
+__global__ void k_fill_records(uint4* rec, int64_t n_vec, int vec_per_rec, int id_bytes) {
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < n_vec;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int within = static_cast<int>(i % vec_per_rec) * 16;
+        uint32_t w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            uint32_t x = 0;
+            for (int b = 0; b < 4; ++b)
+                if (within + 4 * k + b < id_bytes) x |= 0xFFu << (8 * b);
+            w[k] = x;
+        }
+        rec[i] = make_uint4(w[0], w[1], w[2], w[3]);
+    }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ launchers
+
+cudaError_t launch_weight_tables(const TableJob* jobs_dev, const TableJob* one_job, int n_jobs, int max_frames,
+                                 const TableParams& p, cudaStream_t st) {
+    if (n_jobs <= 0 || max_frames <= 0) return cudaSuccess;
+    const int threads = 256;
+    dim3 grid((max_frames + threads - 1) / threads, one_job ? 1 : n_jobs);
+    TableJob dummy{};
+    k_weight_table<<<grid, threads, 0, st>>>(one_job ? nullptr : jobs_dev, one_job ? *one_job : dummy, p);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int max_w,
+                                 int max_h, int K, int dtype, int half_weights, cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    switch (K) {
+    case 4: return plain_launch_k<4>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, half_weights, st);
+    case 8: return plain_launch_k<8>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, half_weights, st);
+    case 12: return plain_launch_k<12>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, half_weights, st);
+    case 16: return plain_launch_k<16>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, half_weights, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    const int npx = a.width * a.height;
+    const int bx = (npx + 255) / 256;
+    dim3 grid(bx < 64 ? bx : 64, a.n);
+    k_scatter_count<<<grid, 256, 0, st>>>(a, count);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_scatter_place(const ScatterArgs& a, int32_t* count, const int32_t* offsets, uint32_t* entries,
+                                 cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    const int npx = a.width * a.height;
+    const int bx = (npx + 255) / 256;
+    dim3 grid(bx < 64 ? bx : 64, a.n);
+    k_scatter_place<<<grid, 256, 0, st>>>(a, count, offsets, entries);
+    return cudaPeekAtLastError();
+}
+
+int64_t scan_block_sums_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
+
+cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
+                                  int64_t block_sums_len, cudaStream_t st) {
+    const int64_t nb = (n + kScanTile - 1) / kScanTile;
+    if (nb + 1 > block_sums_len || nb > INT_MAX) return cudaErrorInvalidValue;
+    k_scan_reduce<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums);
+    k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb);
+    k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums, out);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_finalize(const int32_t* offsets, const uint32_t* entries, int64_t n_vox, uint8_t* rec,
+                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
+                            unsigned long long* overflow, cudaStream_t st) {
+    switch (K) {
+    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
+                                  cudaStream_t st) {
+    dim3 grid((job.width + 31) / 32, (job.height + 7) / 8);
+    k_reslice_scalar<<<grid, dim3(32, 8), 0, st>>>(job, scal_sum, scal_cnt);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned long long* count, cudaStream_t st) {
+    dim3 grid((job.width + 31) / 32, (job.height + 7) / 8);
+    k_footprint<<<grid, dim3(32, 8), 0, st>>>(job, bitmap, count);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_fill_records(uint8_t* rec, int64_t n_vox, int rec_bytes, int K, cudaStream_t st) {
+    const int64_t n_vec = n_vox * (rec_bytes / 16);
+    const int64_t want = (n_vec + 255) / 256;
+    const int blocks = static_cast<int>(want < 148 * 32 ? want : 148 * 32);
+    if (blocks <= 0) return cudaSuccess;
+    k_fill_records<<<blocks, 256, 0, st>>>(reinterpret_cast<uint4*>(rec), n_vec, rec_bytes / 16, 2 * K);
+    return cudaPeekAtLastError();
+}
+
+}  // namespace dare

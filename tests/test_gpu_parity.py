@@ -1,0 +1,334 @@
+"""GPU parity: the CUDA path, called through the C ABI, against the FP64 oracle.
+
+Bit-exact: voxel assignment, frame ids, stored values, npix, coverage masks.
+Floating point: |gpu - oracle| <= 1e-5 max(|oracle|, 1) for FP32 weight tables
+(FP32 accumulation vs the oracle's FP64 on the same stored values).
+"""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import paper_2605_26325_b300 as dare
+import synth
+from gpu_helpers import (DEV, assert_parity, gpu_reslice, gpu_session, new_outputs, ora_params, oracle_dense,
+                         oracle_volume)
+
+pytestmark = pytest.mark.gpu
+
+DTYPES = [dare.DARE_U8, dare.DARE_F16, dare.DARE_BF16, dare.DARE_F32]
+PATHS = [dare.DARE_PATH_PLAIN, dare.DARE_PATH_TILED]
+
+
+@pytest.fixture(scope="module")
+def tiny_f32(tiny):
+    s = gpu_session(tiny, dare.DARE_F32, 8)
+    v = oracle_volume(tiny, dare.DARE_F32, 8)
+    yield s, v
+    s.close()
+
+
+# ------------------------------------------------------------------ reconstruction
+
+@pytest.mark.parametrize("dtype", DTYPES)
+@pytest.mark.parametrize("K", [4, 8])
+def test_build_records_bit_exact(tiny, dtype, K):
+    """Fig. 1 voxelisation: every voxel's (frame id, stored value, npix) list equals
+    the oracle's, including the capacity rule (tiny has up to 5 samples/voxel)."""
+    s = gpu_session(tiny, dtype, K)
+    vol = oracle_volume(tiny, dtype, K)
+    ids, vals, npix, _ = oracle_dense(vol, K, dtype)
+    g = s.read_records(npix=True)
+    assert np.array_equal(g["frame_ids"], ids)
+    assert np.array_equal(g["values"].view(np.uint8), vals.view(np.uint8))
+    assert np.array_equal(g["npix"], npix)
+    assert s.info().overflow_voxels == vol.n_overflow
+    assert s.info().n_frames == len(tiny.frames)
+    s.close()
+
+
+def test_build_append_equals_one_call(tiny):
+    """Appending in chunks (incremental integration, Sec. 4) gives the volume a
+    single call gives; scalar totals too."""
+    a = gpu_session(tiny, dare.DARE_F16, 4, flags=dare.DARE_SESSION_SCALAR, chunks=[0, 37, 120, 121, 200])
+    b = gpu_session(tiny, dare.DARE_F16, 4, flags=dare.DARE_SESSION_SCALAR)
+    ra, rb = a.read_records(npix=True, scalar=True), b.read_records(npix=True, scalar=True)
+    for k in ("frame_ids", "npix", "scalar_sum", "scalar_count"):
+        assert np.array_equal(ra[k], rb[k]), k
+    assert np.array_equal(ra["values"].view(np.uint16), rb["values"].view(np.uint16))
+    e = oracle_volume(tiny, dare.DARE_F16, 4).export()
+    assert np.array_equal(ra["scalar_sum"].astype(np.int64), e["tot_sum"])
+    assert np.array_equal(ra["scalar_count"].astype(np.int64), e["tot_npix"])
+    assert a.info().version == 4 and b.info().version == 1
+    a.close()
+    b.close()
+
+
+def test_build_frame_table(tiny, tiny_f32):
+    s, _ = tiny_f32
+    R = s.read_frames()
+    V = tiny.grid.vol_to_world
+    ref = np.einsum("ji,njk->nik", V[:3, :3], tiny.frame_poses[:, :3, :3])
+    assert np.allclose(R, ref, atol=1e-15)
+
+
+# ------------------------------------------------------------------ reslicing
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("dtype", DTYPES)
+def test_reslice_parity_tiny(tiny, path, dtype):
+    """Eq. 1 / Eq. 2 reslicing of the 16 tiny poses (near-frame, moderately
+    rotated, uniformly random -- the last fully unassigned)."""
+    s = gpu_session(tiny, dtype, 8)
+    vol = oracle_volume(tiny, dtype, 8)
+    p = dare.params_default(path=path)
+    covered = 0
+    for T in tiny.reslice_poses:
+        out, mw = gpu_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, p)
+        ref, rm = oracle.reslice(vol, T, tiny.out_w, tiny.out_h, tiny.out_px, ora_params(p))
+        assert_parity(out, mw, ref, rm, tiny.out_w)
+        covered += rm.sum()
+    assert covered > 0.4 * 16 * tiny.out_w * tiny.out_h
+    s.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_reslice_variants(tiny, tiny_f32, path):
+    """Elevation reading of Eq. 1's normal, thresholds off with k = 0
+    (orientation-blind), custom constants, NaN for unassigned pixels."""
+    s, vol = tiny_f32
+    variants = [
+        dare.params_default(path=path, normal_axis=dare.DARE_NORMAL_ELEVATION),
+        dare.params_default(path=path, k_normal=0.0, k_inplane=0.0, thr_normal_deg=180.0, thr_inplane_deg=180.0),
+        dare.params_default(path=path, k_normal=3.0, k_inplane=20.0, thr_normal_deg=40.0, thr_inplane_deg=5.0),
+        dare.params_default(path=path, unassigned=float("nan")),
+    ]
+    for p in variants:
+        for T in tiny.reslice_poses[[0, 5, 9, 13]]:
+            out, mw = gpu_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, p)
+            ref, rm = oracle.reslice(vol, T, tiny.out_w, tiny.out_h, tiny.out_px, ora_params(p))
+            assert_parity(out, mw, ref, rm, tiny.out_w, unassigned=float(p.unassigned))
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_reslice_fp16_weights(tiny, path):
+    """FP16 weight table: masks stay bit-exact; values within the bound of a
+    relative weight error eps = 2^-11: |d out| <= 2 eps / (1 - eps) (max I - min I)."""
+    s = gpu_session(tiny, dare.DARE_F16, 8)
+    vol = oracle_volume(tiny, dare.DARE_F16, 8)
+    p = dare.params_default(path=path, weight_dtype=dare.DARE_WEIGHTS_F16)
+    eps = 2.0 ** -11
+    bound = 2 * eps / (1 - eps) * 255.0 + 1e-3
+    for T in tiny.reslice_poses[:12]:
+        out, mw = gpu_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, p)
+        ref, rm = oracle.reslice(vol, T, tiny.out_w, tiny.out_h, tiny.out_px, ora_params(p))
+        assert np.array_equal(dare.unpack_mask(mw, tiny.out_w), rm)
+        cov = rm.astype(bool)
+        assert np.max(np.abs(out[cov] - ref[cov]), initial=0) <= bound
+    s.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("W,H", [(1, 1), (37, 23), (33, 17), (200, 5), (5, 200), (64, 48)])
+def test_reslice_ragged_sizes(tiny, tiny_f32, path, W, H):
+    """Output sizes that are not multiples of the 32 x 16 tile or of 32-bit mask words."""
+    s, vol = tiny_f32
+    p = dare.params_default(path=path)
+    px = (0.31, 0.27)
+    for T in tiny.reslice_poses[[1, 8]]:
+        T = synth.plane_pose_centred(T[:3, :3], np.zeros(3), W, H, *px)
+        out, mw = gpu_reslice(s, T, W, H, px, p)
+        ref, rm = oracle.reslice(vol, T, W, H, px, ora_params(p))
+        assert_parity(out, mw, ref, rm, W)
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_reslice_edge_cases(tiny, path):
+    """A session with no frames, and a plane entirely outside the grid: every
+    pixel unassigned, every mask bit 0."""
+    p = dare.params_default(path=path, unassigned=-1.0)
+    empty = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world)
+    out, mw = gpu_reslice(empty, tiny.reslice_poses[0], 40, 30, tiny.out_px, p)
+    assert np.all(out == -1.0) and not mw.any()
+    empty.close()
+    s = gpu_session(tiny, dare.DARE_F32, 8)
+    far = tiny.reslice_poses[0].copy()
+    far[:3, 3] += 500.0
+    out, mw = gpu_reslice(s, far, 64, 64, tiny.out_px, p)
+    assert np.all(out == -1.0) and not mw.any()
+    s.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_batch_equals_single(tiny, path):
+    """dare_reslice_batch over two sessions of different storage types and
+    uneven output sizes: each result equals the request resliced alone, and the
+    oracle."""
+    s1 = gpu_session(tiny, dare.DARE_F32, 8)
+    s2 = gpu_session(tiny, dare.DARE_U8, 4)
+    v1 = oracle_volume(tiny, dare.DARE_F32, 8)
+    v2 = oracle_volume(tiny, dare.DARE_U8, 4)
+    p = dare.params_default(path=path)
+    sizes = [(128, 128), (37, 23), (256, 64), (64, 200), (1, 1), (96, 96)]
+    items, singles, refs = [], [], []
+    for i, (W, H) in enumerate(sizes * 2):
+        s, v = (s1, v1) if i % 2 == 0 else (s2, v2)
+        T = synth.plane_pose_centred(tiny.reslice_poses[i % 16][:3, :3], np.zeros(3), W, H, *tiny.out_px)
+        out, mask = new_outputs(W, H)
+        items.append((s, T, out, mask, tiny.out_px))
+        singles.append(gpu_reslice(s, T, W, H, tiny.out_px, p))
+        refs.append(oracle.reslice(v, T, W, H, tiny.out_px, ora_params(p)) + (W,))
+    dare.reslice_batch(items, p)
+    torch.cuda.synchronize()
+    for (s, T, out, mask, _), (o1, m1), (ref, rm, W) in zip(items, singles, refs):
+        assert np.array_equal(out.cpu().numpy(), o1) or np.allclose(out.cpu().numpy(), o1, rtol=1e-6, atol=1e-6)
+        assert np.array_equal(mask.cpu().numpy(), m1)
+        assert_parity(out.cpu().numpy(), mask.cpu().numpy(), ref, rm, W)
+    s1.close()
+    s2.close()
+
+
+# ------------------------------------------------------------------ comparator, footprint
+
+def test_scalar_comparator(tiny):
+    s = gpu_session(tiny, dare.DARE_F32, 8, flags=dare.DARE_SESSION_SCALAR)
+    vol = oracle_volume(tiny, dare.DARE_F32, 8)
+    for T in tiny.reslice_poses[[0, 3, 12]]:
+        out, mask = new_outputs(tiny.out_w, tiny.out_h)
+        s.reslice_scalar(T, out, mask, tiny.out_px)
+        torch.cuda.synchronize()
+        ref, rm = oracle.reslice_scalar(vol, T, tiny.out_w, tiny.out_h, tiny.out_px)
+        assert_parity(out.cpu().numpy(), mask.cpu().numpy(), ref, rm, tiny.out_w)
+    s.close()
+
+
+def test_footprint_counts(tiny, tiny_f32):
+    s, _ = tiny_f32
+    got = s.footprint(tiny.reslice_poses, tiny.out_w, tiny.out_h, tiny.out_px)
+    ref = [oracle.footprint(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, T, tiny.out_w, tiny.out_h,
+                            tiny.out_px) for T in tiny.reslice_poses]
+    assert list(got) == ref
+
+
+# ------------------------------------------------------------------ checkpoint, memory, capacity
+
+def test_save_load_roundtrip(tiny, tmp_path):
+    s = gpu_session(tiny, dare.DARE_BF16, 8, flags=dare.DARE_SESSION_SCALAR)
+    path = tmp_path / "vol.dare"
+    s.save(path)
+    t = dare.Session.load(path)
+    assert t.dims == s.dims and t.info().n_frames == s.info().n_frames
+    p = dare.params_default()
+    for T in tiny.reslice_poses[[0, 9]]:
+        a = gpu_reslice(s, T, 96, 80, tiny.out_px, p)
+        b = gpu_reslice(t, T, 96, 80, tiny.out_px, p)
+        assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    raw = bytearray(path.read_bytes())
+    raw[len(raw) // 2] ^= 0x40
+    bad = tmp_path / "bad.dare"
+    bad.write_bytes(bytes(raw))
+    with pytest.raises(dare.DareError) as ei:
+        dare.Session.load(bad)
+    assert ei.value.status == dare.DARE_E_INVALID and "CRC" in str(ei.value)
+    s.close()
+    t.close()
+
+
+def test_allocator_hook_and_oom(tiny):
+    """Volumes and workspace come from PyTorch's caching allocator through the
+    callback; a failing allocation returns DARE_E_OOM and leaves the session usable."""
+    alloc = dare.TorchAllocator(0)
+    alloc.fail_next = 1
+    with pytest.raises(dare.DareError) as ei:
+        dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, allocator=alloc)
+    assert ei.value.status == dare.DARE_E_OOM
+    s = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, allocator=alloc)
+    assert len(alloc.live) == 1
+    ft = torch.from_numpy(tiny.frames).to(DEV)
+    alloc.fail_next = 1  # the build's workspace
+    with pytest.raises(dare.DareError) as ei:
+        s.build(ft, tiny.frame_poses, tiny.frame_px)
+    assert ei.value.status == dare.DARE_E_OOM
+    s.build(ft, tiny.frame_poses, tiny.frame_px)
+    ref = gpu_session(tiny, dare.DARE_F32, 8)
+    p = dare.params_default()
+    a = gpu_reslice(s, tiny.reslice_poses[2], 64, 64, tiny.out_px, p)
+    b = gpu_reslice(ref, tiny.reslice_poses[2], 64, 64, tiny.out_px, p)
+    assert np.array_equal(a[0], b[0])
+    s.close()
+    ref.close()
+    assert len(alloc.live) == 0
+
+
+def test_memory_budget_admission(tiny):
+    base = dare.memory_in_use()
+    dare.set_memory_budget(base + 1024)
+    try:
+        with pytest.raises(dare.DareError) as ei:
+            dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world)
+        assert ei.value.status == dare.DARE_E_ADMISSION
+    finally:
+        dare.set_memory_budget(0)
+    s = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world)
+    assert dare.memory_in_use() > base
+    s.close()
+    assert dare.memory_in_use() == base
+
+
+def test_frame_capacity(tiny):
+    s = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, max_frames=150)
+    ft = torch.from_numpy(tiny.frames).to(DEV)
+    with pytest.raises(dare.DareError) as ei:
+        s.build(ft, tiny.frame_poses, tiny.frame_px)
+    assert ei.value.status == dare.DARE_E_CAPACITY
+    assert s.info().n_frames == 0
+    s.build(ft[:150], tiny.frame_poses[:150], tiny.frame_px)
+    assert s.info().n_frames == 150
+    s.close()
+
+
+def test_unsupported_kernel_is_reported(tiny, tiny_f32):
+    s, _ = tiny_f32
+    out, mask = new_outputs(8, 8)
+    for p in (dare.params_default(radius_vox=2), dare.params_default(dist_kernel=dare.DARE_BOX)):
+        with pytest.raises(dare.DareError) as ei:
+            s.reslice(tiny.reslice_poses[0], out, mask, tiny.out_px, p)
+        assert ei.value.status == dare.DARE_E_UNSUPPORTED
+
+
+def test_reset_then_rebuild_equals_fresh(tiny):
+    s = gpu_session(tiny, dare.DARE_F16, 8, flags=dare.DARE_SESSION_SCALAR)
+    ft = torch.from_numpy(tiny.frames).to(DEV)
+    s.reset()
+    info = s.info()
+    assert info.n_frames == 0 and info.version == 0
+    g = s.read_records(npix=True, scalar=True)
+    assert np.all(g["frame_ids"] == 0xFFFF) and not g["npix"].any() and not g["scalar_count"].any()
+    s.build(ft, tiny.frame_poses, tiny.frame_px)
+    fresh = gpu_session(tiny, dare.DARE_F16, 8, flags=dare.DARE_SESSION_SCALAR)
+    a, b = s.read_records(npix=True, scalar=True), fresh.read_records(npix=True, scalar=True)
+    for k in ("frame_ids", "npix", "scalar_sum", "scalar_count"):
+        assert np.array_equal(a[k], b[k])
+    assert np.array_equal(a["values"].view(np.uint16), b["values"].view(np.uint16))
+    s.close()
+    fresh.close()
+
+
+def test_trace_and_launch_count(tiny, tiny_f32):
+    s, _ = tiny_f32
+    dare.trace_read()
+    n0 = dare.launch_count()
+    dare.trace_enable(True)
+    try:
+        p = dare.params_default()
+        gpu_reslice(s, tiny.reslice_poses[0], 64, 64, tiny.out_px, p)
+        gpu_reslice(s, tiny.reslice_poses[1], 64, 64, tiny.out_px, dare.params_default(path=dare.DARE_PATH_PLAIN))
+        t = dare.trace_read()
+    finally:
+        dare.trace_enable(False)
+    assert dare.launch_count() - n0 == 4
+    assert t["reslice_tiled"][0] == 1 and t["reslice_plain"][0] == 1 and t["weight_table"][0] == 2
+    assert all(ms > 0 for _, ms in t.values())
