@@ -105,7 +105,8 @@ __device__ void tile_geometry(const ResliceJob& J, int u0, int v0, int u1, int v
     T.b2 = b2;
     T.n1 = max(0, t1 - b1 + 1);
     T.n2 = max(0, t2 - b2 + 1);
-    T.levels = static_cast<int>(floor(2.0 * T.spread + 2e-6)) + 2;
+    // levels floor(gd - spread) .. floor(gd + spread) + 1: at most floor(2 spread) + 3
+    T.levels = static_cast<int>(floor(2.0 * T.spread + 2e-6)) + 3;
     const long long ncol = static_cast<long long>(T.n1) * T.n2;
     if (ncol > kColMax || ncol * T.levels > kSlotMax) T.direct = 1;
     // inverse of the 2x2 map (u, v) -> (g_e1, g_e2)
