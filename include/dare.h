@@ -298,6 +298,30 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
 dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream);
 
 /*
+ * Allocation-free variant of dare_reslice.  The paper has no counterpart:
+ * this entry point exists for callers that must not ask for device memory
+ * while they run, e.g. a preview loop on the expert's console thread with a
+ * fixed latency budget (cudaMalloc / cudaFree can block and synchronise the
+ * device), or an application whose device memory is entirely owned by
+ * another component once it has started.
+ *
+ * Same arguments, checks and result as dare_reslice (same kernels), except
+ * that the plane's per-frame weight table goes to a fixed array in device
+ * memory inside the library instead of the session's workspace.  That array
+ * holds DARE_NOALLOC_MAX_FRAMES weights (64 KB): a session with more frames
+ * is rejected with DARE_E_INVALID and nothing is queued.  Every GPU that
+ * loads the library keeps the array until the process exits.  All calls
+ * share it: calls that overlap on the GPU (unordered streams) race and give
+ * wrong images; order them or use dare_reslice.  The first call on a device
+ * looks up the array's device address on that device (no allocation); make
+ * that first call before any stream capture.  The session, its volume and
+ * the outputs must already exist; this call allocates nothing itself.
+ */
+#define DARE_NOALLOC_MAX_FRAMES 16384
+dare_status dare_reslice_noalloc(dare_session s, const dare_plane* plane, const dare_params* params,
+                                 float* out_dev, uint32_t* mask_dev, void* stream);
+
+/*
  * Mean-compounding comparator (the scalar reading of the PLUS baseline,
  * Sec. 2.2): each voxel holds RN_fp32(total / count) of every pixel that
  * landed in it; a pixel is the trilinear blend of its occupied corners,

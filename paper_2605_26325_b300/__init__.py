@@ -29,6 +29,7 @@ DARE_PATH_AUTO, DARE_PATH_PLAIN, DARE_PATH_TILED = 0, 1, 2
 DARE_SESSION_SCALAR = 1
 DARE_EMPTY_FRAME = 0xFFFF
 DARE_FIX_BITS = 20
+DARE_NOALLOC_MAX_FRAMES = 16384
 
 STATUS_NAMES = {0: "OK", 1: "E_INVALID", 2: "E_OOM", 3: "E_CUDA", 4: "E_ADMISSION", 5: "E_CAPACITY",
                 6: "E_TIMEOUT", 7: "E_STATE", 8: "E_UNSUPPORTED"}
@@ -118,6 +119,7 @@ _SIGNATURES = {
                            _P(ctypes.c_double), _vp], ctypes.c_int),
     "dare_reslice": ([_vp, _P(dare_plane), _P(dare_params), _vp, _vp, _vp], ctypes.c_int),
     "dare_reslice_batch": ([_P(dare_reslice_req), ctypes.c_int32, _P(dare_params), _vp], ctypes.c_int),
+    "dare_reslice_noalloc": ([_vp, _P(dare_plane), _P(dare_params), _vp, _vp, _vp], ctypes.c_int),
     "dare_reslice_scalar": ([_vp, _P(dare_plane), ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
     "dare_footprint": ([_vp, _P(dare_plane), ctypes.c_int32, _P(ctypes.c_int64), _vp], ctypes.c_int),
     "dare_session_reset": ([_vp, _vp], ctypes.c_int),

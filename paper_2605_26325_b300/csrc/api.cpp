@@ -1129,3 +1129,55 @@ dare_status dare_session_load(const dare_session_config* cfg, const char* path, 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free reslice support
+
+namespace dare {
+
+dare_status set_error(dare_status st, const char* msg) { return fail(st, "%s", msg); }
+
+int session_device(dare_session s) { return s ? s->cfg.device : -1; }
+
+// dare_reslice with a caller-provided weight table of wtab_bytes bytes on the
+// session's device; queues the same kernels and allocates nothing.
+dare_status reslice_with_table(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
+                               uint32_t* mask_dev, void* stream, void* wtab, size_t wtab_bytes, int max_frames) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    dare_status rc = check_plane(plane);
+    if (rc != DARE_OK) return rc;
+    rc = check_params(params);
+    if (rc != DARE_OK) return rc;
+    if (!out_dev || !mask_dev) return fail(DARE_E_INVALID, "output pointers are NULL");
+    if (!affine_ok(s->cfg.grid.vol_to_world, s->cfg.grid.spacing_mm, plane->image_to_world, plane->width,
+                   plane->px_mm[0], plane->px_mm[1]))
+        return fail(DARE_E_INVALID, "plane too far from the grid for fixed-point coordinates");
+    const size_t wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
+    if (s->n_frames > max_frames || size_t(s->n_frames) * wb > wtab_bytes)
+        return fail(DARE_E_INVALID, "the allocation-free reslice holds weights for at most %d frames; "
+                    "this session has %d (use dare_reslice)", max_frames, s->n_frames);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    TableJob tj{};
+    plane_vectors(s, plane, params->normal_axis, &tj);
+    tj.frames = s->frames_dev;
+    tj.wtab = wtab;
+    tj.n_frames = s->n_frames;
+    if (s->n_frames > 0) {
+        KernelScope ks("weight_table", st, 1);
+        CUDA_TRY(launch_weight_tables(nullptr, &tj, 1, s->n_frames, table_params(params), st));
+    }
+    ResliceJob job = make_job(s, plane, wtab, out_dev, mask_dev, params->unassigned);
+    const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
+    if (use_tiled(params)) {
+        job.tile_base = 0;
+        KernelScope ks("reslice_tiled", st, 1);
+        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), s->K, s->dtype, half_w, st));
+    } else {
+        KernelScope ks("reslice_plain", st, 1);
+        CUDA_TRY(launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, s->K, s->dtype, half_w, st));
+    }
+    return session_end(s, st);
+}
+
+}  // namespace dare

@@ -88,6 +88,12 @@ cudaError_t launch_fill_records(uint8_t* rec, int64_t n_vox, int rec_bytes, int 
 cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
                                  int tile_offset, int n_tiles, int K, int dtype, int half_weights, cudaStream_t st);
 constexpr int kTileW = 32;
+
+// allocation-free reslice support (api.cpp)
+dare_status set_error(dare_status st, const char* msg);
+int session_device(dare_session s);
+dare_status reslice_with_table(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
+                               uint32_t* mask_dev, void* stream, void* wtab, size_t wtab_bytes, int max_frames);
 constexpr int kTileH = 16;
 
 }  // namespace dare
