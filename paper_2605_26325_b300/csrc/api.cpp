@@ -373,6 +373,41 @@ ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab
     j.mask_stride = (pl->width + 31) / 32;
     j.tiles_x = (pl->width + kTileW - 1) / kTileW;
     j.unassigned = unassigned;
+    // plane geometry for the tiled kernel, from the quantised affine
+    const double sc = 1.0 / static_cast<double>(kFixOne);
+    double A[3], B[3], G0[3];
+    for (int a = 0; a < 3; ++a) {
+        A[a] = static_cast<double>(aff[3 + a]) * sc;
+        B[a] = static_cast<double>(aff[6 + a]) * sc;
+        G0[a] = static_cast<double>(aff[a]) * sc;
+    }
+    const double n[3] = {A[1] * B[2] - A[2] * B[1], A[2] * B[0] - A[0] * B[2], A[0] * B[1] - A[1] * B[0]};
+    int d = 0;
+    if (std::fabs(n[1]) > std::fabs(n[d])) d = 1;
+    if (std::fabs(n[2]) > std::fabs(n[d])) d = 2;
+    const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
+    j.d = d;
+    const double det = A[e1] * B[e2] - A[e2] * B[e1];
+    if (n[d] == 0.0 || det == 0.0) {
+        j.direct = 1;
+        return j;
+    }
+    const double b1 = -n[e1] / n[d], b2 = -n[e2] / n[d];
+    const double spread = std::fabs(b1) + std::fabs(b2);
+    j.beta1 = static_cast<float>(b1);
+    j.beta2 = static_cast<float>(b2);
+    j.alpha = static_cast<float>(G0[d] - b1 * G0[e1] - b2 * G0[e2]);
+    j.spread = static_cast<float>(spread);
+    j.levels = static_cast<int32_t>(std::floor(2.0 * spread + 0.05)) + 3;
+    const double m00 = B[e2] / det, m01 = -B[e1] / det, m10 = -A[e2] / det, m11 = A[e1] / det;
+    j.m00 = static_cast<float>(m00);
+    j.m01 = static_cast<float>(m01);
+    j.m10 = static_cast<float>(m10);
+    j.m11 = static_cast<float>(m11);
+    j.ou = static_cast<float>(-(m00 * G0[e1] + m01 * G0[e2]));
+    j.ov = static_cast<float>(-(m10 * G0[e1] + m11 * G0[e2]));
+    j.hu = static_cast<float>(std::fabs(m00) + std::fabs(m01) + 0.25);
+    j.hv = static_cast<float>(std::fabs(m10) + std::fabs(m11) + 0.25);
     return j;
 }
 

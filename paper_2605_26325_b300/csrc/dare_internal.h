@@ -36,7 +36,14 @@ struct ResliceJob {
     int32_t tile_base;          // first tile of this job in a batched launch
     int32_t tiles_x;            // tiles per tile row
     float unassigned;
-    int32_t pad;
+    // plane geometry for the tiled kernel (host FP64, stored as FP32 with margins):
+    // d = axis of the largest normal component in voxel space; on the plane
+    // g_d = alpha + beta1 g_e1 + beta2 g_e2; (u, v) = (ou, ov) + M (g_e1, g_e2).
+    int32_t d;                  // 0, 1, 2
+    int32_t levels;             // level slots per column, floor(2 spread + 0.05) + 3
+    int32_t direct;             // 1: degenerate plane, every pixel gathers directly
+    float alpha, beta1, beta2, spread;
+    float m00, m01, m10, m11, ou, ov, hu, hv;
 };
 
 // Inputs of the per-(plane, frame) weight table of Eq. 1 / Eq. 2.
