@@ -373,6 +373,7 @@ ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab
     j.mask_stride = (pl->width + 31) / 32;
     j.tiles_x = (pl->width + kTileW - 1) / kTileW;
     j.unassigned = unassigned;
+    j.n_frames = s->n_frames;
     // plane geometry for the tiled kernel, from the quantised affine
     const double sc = 1.0 / static_cast<double>(kFixOne);
     double A[3], B[3], G0[3];
@@ -388,7 +389,10 @@ ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab
     const int e1 = d == 0 ? 1 : 0, e2 = d == 2 ? 1 : 2;
     j.d = d;
     const double det = A[e1] * B[e2] - A[e2] * B[e1];
-    if (n[d] == 0.0 || det == 0.0) {
+    bool small_steps = true;  // the tiled kernel steps pixels in int32: |A|, |B| < 2^25 (2^-20 voxel units)
+    for (int a = 0; a < 3; ++a)
+        small_steps = small_steps && std::llabs(aff[3 + a]) < (int64_t(1) << 25) && std::llabs(aff[6 + a]) < (int64_t(1) << 25);
+    if (n[d] == 0.0 || det == 0.0 || !small_steps) {
         j.direct = 1;
         return j;
     }
@@ -795,7 +799,7 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
     if (use_tiled(params)) {
         job.tile_base = 0;
         KernelScope ks("reslice_tiled", st, 1);
-        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), s->K, s->dtype, half_w, st));
+        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, s->K, s->dtype, half_w, st));
     } else {
         KernelScope ks("reslice_plain", st, 1);
         CUDA_TRY(launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, s->K, s->dtype, half_w, st));
@@ -897,8 +901,13 @@ dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const da
             // tile bases restart per group
             const int base = rjs[k0].tile_base;
             const int end = (k1 < n) ? rjs[k1].tile_base : total_tiles;
+            // same tile count for every job of the group: 2-D grid without a job search
+            const int per = tiles_of(&reqs[order[k0]].plane);
+            bool uniform = k1 - k0 <= 65535;
+            for (int32_t k = k0; uniform && k < k1; ++k) uniform = tiles_of(&reqs[order[k]].plane) == per;
             KernelScope ks("reslice_tiled", st, 1);
-            CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, end - base, sg->K, sg->dtype, half_w, st));
+            CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base, uniform ? 1 : 0,
+                                          sg->K, sg->dtype, half_w, st));
         } else {
             KernelScope ks("reslice_plain", st, 1);
             CUDA_TRY(launch_reslice_plain(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
@@ -1207,7 +1216,7 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
     if (use_tiled(params)) {
         job.tile_base = 0;
         KernelScope ks("reslice_tiled", st, 1);
-        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), s->K, s->dtype, half_w, st));
+        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, s->K, s->dtype, half_w, st));
     } else {
         KernelScope ks("reslice_plain", st, 1);
         CUDA_TRY(launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, s->K, s->dtype, half_w, st));

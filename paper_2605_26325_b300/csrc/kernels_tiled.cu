@@ -1,4 +1,4 @@
-// Tiled DARE reslice (sm_103a): one CTA per 32 x 16 pixel tile.
+// Tiled DARE reslice (sm_103a): one CTA per 32 x 64 pixel tile.
 //
 // For a plane r the orientation weight w_f of Eq. 2 depends only on the
 // sample's frame f, so the weighted average of Sec. 2.1 with TENT weights t_c
@@ -33,6 +33,9 @@ using namespace dev;
 constexpr int kThreads = 256;
 constexpr int kColMax = 1024;
 constexpr int kSlotMax = 4096;   // (A, B) float2 slots: 32 KB
+#ifndef DARE_TILED_MIN_BLOCKS
+#define DARE_TILED_MIN_BLOCKS 4
+#endif
 constexpr float kMargin = 0.02f; // voxel; > FP32 error of the plane height for |g| < 2^14
 
 template <int D>
@@ -75,11 +78,10 @@ __device__ __forceinline__ float2 collapse_voxel(const uint8_t* rec, int64_t vi,
     float A = 0.0f, B = 0.0f;
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-        if (s < count) {
-            const float w = weight_of(wt, static_cast<int>(slot_id<K, VT>(r, s)));
-            A = fmaf(w, slot_value<K, VT>(r, s), A);
-            B += w;
-        }
+        if (s >= count) break;
+        const float w = weight_of(wt, static_cast<int>(slot_id<K, VT>(r, s)));
+        A = fmaf(w, slot_value<K, VT>(r, s), A);
+        B += w;
     }
     return make_float2(A, B);
 }
@@ -109,33 +111,49 @@ __device__ __forceinline__ int64_t axis_fix(const ResliceJob& J, int a, int u, i
     return J.g0[a] + static_cast<int64_t>(u) * J.a[a] + static_cast<int64_t>(v) * J.b[a];
 }
 
-__device__ __forceinline__ float fix_frac(int64_t G) {
-    return static_cast<float>(static_cast<int32_t>(G & (kFixOne - 1))) * (1.0f / static_cast<float>(kFixOne));
-}
+// Per-tile set-up, computed by one thread and shared through shared memory.
+struct TileSetup {
+    int job;
+    int u0, v0, u1, v1;      // pixel range of the tile
+    int b1, b2, n1, n2;      // column box
+    int direct;
+    int R1, R2, Rd;          // 20-bit remainders of the tile origin's coordinates
+    int O1, O2, Od;          // integer parts, relative to the box (clamped far outside when irrelevant)
+};
 
-template <int K, typename VT, typename WT, int D>
-__device__ __forceinline__ void tile_body(const ResliceJob& J, int u0, int v0, int u1, int v1, float2* sAB,
-                                          int* sCol) {
+template <int D>
+__device__ void tile_setup(const ResliceJob& J, int u0, int v0, int u1, int v1, TileSetup& T) {
     constexpr int E1 = Axes<D>::E1, E2 = Axes<D>::E2;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const WT* wt = static_cast<const WT*>(J.wtab);
-
-    // exact bounding box of the tile's corner pixels in (e1, e2), grown by the TENT support
     int64_t lo1 = INT64_MAX, hi1 = INT64_MIN, lo2 = INT64_MAX, hi2 = INT64_MIN;
-#pragma unroll
     for (int k = 0; k < 4; ++k) {
         const int u = (k & 1) ? u1 : u0, v = (k & 2) ? v1 : v0;
         const int64_t f1 = axis_fix(J, E1, u, v) >> kFixBits, f2 = axis_fix(J, E2, u, v) >> kFixBits;
         lo1 = lmin(lo1, f1); hi1 = lmax(hi1, f1);
         lo2 = lmin(lo2, f2); hi2 = lmax(hi2, f2);
     }
-    const int b1 = static_cast<int>(lmax(lmin(lo1, J.dims[E1]), 0));
-    const int b2 = static_cast<int>(lmax(lmin(lo2, J.dims[E2]), 0));
-    const int n1 = static_cast<int>(lmax(0, lmin(hi1 + 1, J.dims[E1] - 1) - b1 + 1));
-    const int n2 = static_cast<int>(lmax(0, lmin(hi2 + 1, J.dims[E2] - 1) - b2 + 1));
-    const int ncol = n1 * n2;
-    const int L = J.levels;
-    const bool direct = J.direct || ncol > kColMax || ncol * L > kSlotMax;
+    T.b1 = static_cast<int>(lmax(lmin(lo1, J.dims[E1]), 0));
+    T.b2 = static_cast<int>(lmax(lmin(lo2, J.dims[E2]), 0));
+    T.n1 = static_cast<int>(lmax(0, lmin(hi1 + 1, J.dims[E1] - 1) - T.b1 + 1));
+    T.n2 = static_cast<int>(lmax(0, lmin(hi2 + 1, J.dims[E2] - 1) - T.b2 + 1));
+    const int ncol = T.n1 * T.n2;
+    T.direct = J.direct || ncol > kColMax || ncol * J.levels > kSlotMax;
+    const int64_t G1 = axis_fix(J, E1, u0, v0), G2 = axis_fix(J, E2, u0, v0), Gd = axis_fix(J, D, u0, v0);
+    T.R1 = static_cast<int>(G1 & (kFixOne - 1));
+    T.R2 = static_cast<int>(G2 & (kFixOne - 1));
+    T.Rd = static_cast<int>(Gd & (kFixOne - 1));
+    T.O1 = static_cast<int>(lmax(lmin((G1 >> kFixBits) - T.b1, 1 << 24), -(1 << 24)));
+    T.O2 = static_cast<int>(lmax(lmin((G2 >> kFixBits) - T.b2, 1 << 24), -(1 << 24)));
+    T.Od = static_cast<int>(lmax(lmin(Gd >> kFixBits, 1 << 24), -(1 << 24)));
+}
+
+template <int K, typename VT, typename WT, int D>
+__device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& T, int u0, int v0, int u1, int v1,
+                                          float2* sAB, int* sCol) {
+    constexpr int E1 = Axes<D>::E1, E2 = Axes<D>::E2;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const WT* wt = static_cast<const WT*>(J.wtab);
+    const int b1 = T.b1, b2 = T.b2, n1 = T.n1, n2 = T.n2, ncol = n1 * n2, L = J.levels;
+    const bool direct = T.direct != 0;
 
     if (!direct) {
         // (A) per column: level range, then one collapse per candidate voxel
@@ -158,18 +176,19 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, int u0, int v0, i
                 cnt = max(0, min(hi - lo + 1, L));
             }
             sCol[c] = (lo & 0xFFFF) | (cnt << 16);
-            for (int lev = 0; lev < cnt; ++lev) {
-                const int cd = lo + lev;
-                const int x = D == 0 ? cd : c1;
-                const int y = D == 1 ? cd : (E1 == 1 ? c1 : c2);
-                const int z = D == 2 ? cd : c2;
-                const int64_t vi = x + static_cast<int64_t>(J.dims[0]) * (y + static_cast<int64_t>(J.dims[1]) * z);
-                sAB[c * L + lev] = collapse_voxel<K, VT, WT>(J.rec, vi, wt);
-            }
+            const int64_t base = (D == 0 ? 0 : c1) + static_cast<int64_t>(J.dims[0]) *
+                                 ((D == 1 ? 0 : (E1 == 1 ? c1 : c2)) + static_cast<int64_t>(J.dims[1]) * (D == 2 ? 0 : c2));
+            const int64_t step = D == 0 ? 1 : (D == 1 ? static_cast<int64_t>(J.dims[0])
+                                                      : static_cast<int64_t>(J.dims[0]) * J.dims[1]);
+            for (int lev = 0; lev < cnt; ++lev)
+                sAB[c * L + lev] = collapse_voxel<K, VT, WT>(J.rec, base + (lo + lev) * step, wt);
         }
         __syncthreads();
     }
-    // (B) pixels: a warp walks the 32 pixels of a tile row
+    // (B) pixels: a warp walks the 32 pixels of a tile row; int32 steps from the tile origin
+    const int A1 = static_cast<int>(J.a[E1]), B1 = static_cast<int>(J.b[E1]);
+    const int A2 = static_cast<int>(J.a[E2]), B2 = static_cast<int>(J.b[E2]);
+    const int Ad = static_cast<int>(J.a[D]), Bd = static_cast<int>(J.b[D]);
     for (int r = warp; r < kTileH; r += kThreads / 32) {
         const int v = v0 + r;
         if (v > v1) break;  // warp-uniform
@@ -180,23 +199,30 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, int u0, int v0, i
             if (direct) {
                 direct_pixel<K, VT, WT>(J, u, v, num, den);
             } else {
-                const int64_t G1 = axis_fix(J, E1, u, v), G2 = axis_fix(J, E2, u, v), Gd = axis_fix(J, D, u, v);
-                const int64_t k1 = (G1 >> kFixBits) - b1, k2 = (G2 >> kFixBits) - b2, fd = Gd >> kFixBits;
-                const float p1 = fix_frac(G1), p2 = fix_frac(G2), pd = fix_frac(Gd);
+                const int du = u - u0, dv = v - v0;
+                const int r1 = T.R1 + du * A1 + dv * B1;
+                const int r2 = T.R2 + du * A2 + dv * B2;
+                const int rd = T.Rd + du * Ad + dv * Bd;
+                const int k1 = (r1 >> kFixBits) + T.O1, k2 = (r2 >> kFixBits) + T.O2, fd = (rd >> kFixBits) + T.Od;
+                const float p1 = static_cast<float>(r1 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
+                const float p2 = static_cast<float>(r2 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
+                const float pd = static_cast<float>(rd & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
-                        if (k1 + i < 0 || k1 + i >= n1 || k2 + j < 0 || k2 + j >= n2) continue;
-                        const int c = static_cast<int>(k1 + i) + n1 * static_cast<int>(k2 + j);
+                        if (static_cast<unsigned>(k1 + i) >= static_cast<unsigned>(n1) ||
+                            static_cast<unsigned>(k2 + j) >= static_cast<unsigned>(n2))
+                            continue;
+                        const int c = k1 + i + n1 * (k2 + j);
                         const int info = sCol[c];
-                        const int64_t lev = fd - (info & 0xFFFF);
+                        const int lev = fd - (info & 0xFFFF);
                         const int cnt = info >> 16;
                         const float wc = (i ? p1 : 1.0f - p1) * (j ? p2 : 1.0f - p2);
 #pragma unroll
                         for (int k = 0; k < 2; ++k) {
-                            if (lev + k < 0 || lev + k >= cnt) continue;
-                            const float2 ab = sAB[c * L + static_cast<int>(lev) + k];
+                            if (static_cast<unsigned>(lev + k) >= static_cast<unsigned>(cnt)) continue;
+                            const float2 ab = sAB[c * L + lev + k];
                             const float t = wc * (k ? pd : 1.0f - pd);
                             num = fmaf(t, ab.x, num);
                             den = fmaf(t, ab.y, den);
@@ -211,49 +237,76 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, int u0, int v0, i
     }
 }
 
+// One CTA per tile.  With `uniform` every job has `n_tiles` tiles and the job
+// is blockIdx.y; otherwise blockIdx.x runs over all tiles of the launch and
+// thread 0 finds the job by binary search over tile_base.
 template <int K, typename VT, typename WT>
-__global__ void __launch_bounds__(kThreads, 4) k_reslice_tiled(const ResliceJob* __restrict__ jobs, int n_jobs,
-                                                               int tile_offset,
-                                                               const __grid_constant__ ResliceJob one) {
+__global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_tiled(const ResliceJob* __restrict__ jobs,
+                                                                                   int n_jobs, int tile_offset,
+                                                                                   int uniform,
+                                                                                   const __grid_constant__ ResliceJob one) {
     __shared__ float2 sAB[kSlotMax];
     __shared__ int sCol[kColMax];  // per column: lowest level | (level count << 16)
-    const int tile = tile_offset + static_cast<int>(blockIdx.x);
-    const ResliceJob& J = jobs ? jobs[find_job(jobs, n_jobs, tile)] : one;
-    const int lt = tile - J.tile_base;
-    const int ty = lt / J.tiles_x, tx = lt - ty * J.tiles_x;
-    const int u0 = tx * kTileW, v0 = ty * kTileH;
-    const int u1 = min(u0 + kTileW, J.width) - 1, v1 = min(v0 + kTileH, J.height) - 1;
+    __shared__ TileSetup T;
+    if (threadIdx.x == 0) {
+        int lt;
+        if (!jobs) {
+            T.job = 0;
+            lt = static_cast<int>(blockIdx.x);
+        } else if (uniform) {
+            T.job = static_cast<int>(blockIdx.y);
+            lt = static_cast<int>(blockIdx.x);
+        } else {
+            const int tile = tile_offset + static_cast<int>(blockIdx.x);
+            T.job = find_job(jobs, n_jobs, tile);
+            lt = tile - __ldg(&jobs[T.job].tile_base);
+        }
+        const ResliceJob& J0 = jobs ? jobs[T.job] : one;
+        const int ty = lt / J0.tiles_x, tx = lt - ty * J0.tiles_x;
+        T.u0 = tx * kTileW;
+        T.v0 = ty * kTileH;
+        T.u1 = min(T.u0 + kTileW, J0.width) - 1;
+        T.v1 = min(T.v0 + kTileH, J0.height) - 1;
+        if (J0.d == 0) tile_setup<0>(J0, T.u0, T.v0, T.u1, T.v1, T);
+        else if (J0.d == 1) tile_setup<1>(J0, T.u0, T.v0, T.u1, T.v1, T);
+        else tile_setup<2>(J0, T.u0, T.v0, T.u1, T.v1, T);
+    }
+    __syncthreads();
+    const ResliceJob& J = jobs ? jobs[T.job] : one;
     switch (J.d) {
-    case 0: tile_body<K, VT, WT, 0>(J, u0, v0, u1, v1, sAB, sCol); break;
-    case 1: tile_body<K, VT, WT, 1>(J, u0, v0, u1, v1, sAB, sCol); break;
-    default: tile_body<K, VT, WT, 2>(J, u0, v0, u1, v1, sAB, sCol); break;
+    case 0: tile_body<K, VT, WT, 0>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    case 1: tile_body<K, VT, WT, 1>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    default: tile_body<K, VT, WT, 2>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
     }
 }
 
+// n_tiles: tiles of the whole launch, or per job when `uniform`.
 template <int K, typename VT, typename WT>
 cudaError_t tiled_launch(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                         int n_tiles, cudaStream_t st) {
+                         int n_tiles, int uniform, cudaStream_t st) {
     ResliceJob dummy{};
-    k_reslice_tiled<K, VT, WT><<<n_tiles, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset,
-                                                            one ? *one : dummy);
+    const dim3 grid(n_tiles, (one || !uniform) ? 1 : n_jobs);
+    k_reslice_tiled<K, VT, WT><<<grid, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset,
+                                                         uniform, one ? *one : dummy);
     return cudaPeekAtLastError();
 }
 
 template <int K, typename VT>
 cudaError_t tiled_launch_w(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                           int n_tiles, int half_w, cudaStream_t st) {
-    return half_w ? tiled_launch<K, VT, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, st)
-                  : tiled_launch<K, VT, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, st);
+                           int n_tiles, int uniform, int half_w, cudaStream_t st) {
+    return half_w ? tiled_launch<K, VT, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, st)
+                  : tiled_launch<K, VT, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, st);
 }
 
 template <int K>
 cudaError_t tiled_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                           int n_tiles, int dtype, int half_w, cudaStream_t st) {
+                           int n_tiles, int uniform, int dtype, int half_w, cudaStream_t st) {
     switch (dtype) {
-    case DARE_U8: return tiled_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, tile_offset, n_tiles, half_w, st);
-    case DARE_F16: return tiled_launch_w<K, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, half_w, st);
-    case DARE_BF16: return tiled_launch_w<K, __nv_bfloat16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, half_w, st);
-    case DARE_F32: return tiled_launch_w<K, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, half_w, st);
+    case DARE_U8: return tiled_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, half_w, st);
+    case DARE_F16: return tiled_launch_w<K, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, half_w, st);
+    case DARE_BF16:
+        return tiled_launch_w<K, __nv_bfloat16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, half_w, st);
+    case DARE_F32: return tiled_launch_w<K, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, half_w, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -261,13 +314,15 @@ cudaError_t tiled_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, in
 }  // namespace
 
 cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int tile_offset,
-                                 int n_tiles, int K, int dtype, int half_weights, cudaStream_t st) {
+                                 int n_tiles, int uniform, int K, int dtype, int half_weights, cudaStream_t st) {
     if (n_jobs <= 0 || n_tiles <= 0) return cudaSuccess;
     switch (K) {
-    case 4: return tiled_launch_k<4>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, dtype, half_weights, st);
-    case 8: return tiled_launch_k<8>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, dtype, half_weights, st);
-    case 12: return tiled_launch_k<12>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, dtype, half_weights, st);
-    case 16: return tiled_launch_k<16>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, dtype, half_weights, st);
+    case 4: return tiled_launch_k<4>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, dtype, half_weights, st);
+    case 8: return tiled_launch_k<8>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, dtype, half_weights, st);
+    case 12:
+        return tiled_launch_k<12>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, dtype, half_weights, st);
+    case 16:
+        return tiled_launch_k<16>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, dtype, half_weights, st);
     }
     return cudaErrorInvalidValue;
 }
