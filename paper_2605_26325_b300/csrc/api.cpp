@@ -703,14 +703,14 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
     DeviceGuard dg(s->cfg.device);
     if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int32_t chunk = static_cast<int32_t>(std::max<int64_t>(1, kMaxPixelsPerChunk / npx));
+    const int32_t chunk = static_cast<int32_t>(std::min<int64_t>(65535, std::max<int64_t>(1, kMaxPixelsPerChunk / npx)));
     const int32_t n_chunk = std::min(n, chunk);
     // workspace: offsets (n_vox + 1), scan block sums, entries, affines
     const int64_t nbs = scan_block_sums_needed(s->n_vox);
     const size_t o_off = 0;
     const size_t o_bs = align_up(o_off + size_t(s->n_vox + 1) * 4, 256);
     const size_t o_ent = align_up(o_bs + size_t(nbs) * 4, 256);
-    const size_t o_aff = align_up(o_ent + size_t(n_chunk) * npx * 4, 256);
+    const size_t o_aff = align_up(o_ent + size_t(n_chunk) * npx * 8, 256);
     const size_t ws_need = align_up(o_aff + size_t(n) * 9 * 8, 256);
     dare_status rc = session_begin(s, st);
     if (rc != DARE_OK) return rc;
@@ -721,7 +721,7 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
     uint8_t* ws = static_cast<uint8_t*>(s->ws);
     int32_t* offsets = reinterpret_cast<int32_t*>(ws + o_off);
     int32_t* bsums = reinterpret_cast<int32_t*>(ws + o_bs);
-    uint32_t* entries = reinterpret_cast<uint32_t*>(ws + o_ent);
+    auto* entries = reinterpret_cast<unsigned long long*>(ws + o_ent);
     int64_t* aff_dev = reinterpret_cast<int64_t*>(ws + o_aff);
     uint8_t* pin = static_cast<uint8_t*>(s->pinned[0]);
     std::memcpy(pin, aff.data(), aff.size() * 8);
@@ -740,6 +740,10 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
         a.height = height;
         for (int k = 0; k < 3; ++k) a.dims[k] = s->cfg.grid.dims[k];
         a.frame_base = s->n_frames + c0;
+        a.small_steps = 1;
+        for (int32_t f = c0; f < c0 + nc; ++f)
+            for (int k = 3; k < 9; ++k)
+                if (std::llabs(aff[9 * size_t(f) + k]) >= (int64_t(1) << 25)) a.small_steps = 0;
         {
             KernelScope ks("scatter_count", st, 1);
             CUDA_TRY(launch_scatter_count(a, s->count, st));

@@ -18,7 +18,7 @@ namespace dare {
 
 constexpr int kFixBits = DARE_FIX_BITS;
 constexpr int64_t kFixOne = int64_t(1) << kFixBits;
-constexpr int kMaxPixelsPerChunk = 1 << 30;  // entries of one scatter pass
+constexpr int kMaxPixelsPerChunk = 1 << 28;  // pixels of one scatter pass (8-byte entries at most one per pixel)
 
 inline int value_bytes(int dtype) { return dtype == DARE_U8 ? 1 : (dtype == DARE_F32 ? 4 : 2); }
 inline int record_bytes(int K, int dtype) { return (2 * K + K * value_bytes(dtype) + 15) / 16 * 16; }
@@ -71,20 +71,21 @@ struct ScatterArgs {
     int32_t n, width, height;
     int32_t dims[3];
     int32_t frame_base;       // global id of frame 0 of this chunk
+    int32_t small_steps;      // every |A|, |B| < 2^25: tiles step pixels in int32
 };
 
-// ------------------------------------------------------------ launchers (kernels.cu)
+// ------------------------------------------------------------ launchers (kernels.cu, kernels_build.cu)
 cudaError_t launch_weight_tables(const TableJob* jobs_dev, const TableJob* one_job, int n_jobs, int max_frames,
                                  const TableParams& p, cudaStream_t st);
 cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int max_w,
                                  int max_h, int K, int dtype, int half_weights, cudaStream_t st);
 cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, cudaStream_t st);
-cudaError_t launch_scatter_place(const ScatterArgs& a, int32_t* count, const int32_t* offsets, uint32_t* entries,
-                                 cudaStream_t st);
+cudaError_t launch_scatter_place(const ScatterArgs& a, int32_t* count, const int32_t* offsets,
+                                 unsigned long long* entries, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
                                   int64_t block_sums_len, cudaStream_t st);
 int64_t scan_block_sums_needed(int64_t n);
-cudaError_t launch_finalize(const int32_t* offsets, const uint32_t* entries, int64_t n_vox, uint8_t* rec,
+cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
                             uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
                             unsigned long long* overflow, cudaStream_t st);
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,

@@ -1,7 +1,6 @@
 // DARE device kernels for sm_103a: per-frame weight tables (Eq. 1, Eq. 2),
-// the plain one-thread-per-pixel reslice, the reconstruction scatter
-// (count / scan / place / finalize), the mean-compounding comparator and the
-// footprint counter.
+// the plain one-thread-per-pixel reslice, the exclusive scan used by the
+// reconstruction, the mean-compounding comparator and the footprint counter.
 //
 // The path is a gather, not a contraction: no tensor cores.  Every kernel is
 // bounded by memory or by issue rate, so the work is laid out for coalescing
@@ -135,68 +134,6 @@ cudaError_t plain_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, in
     return cudaErrorInvalidValue;
 }
 
-// ------------------------------------------------------------------ reconstruction scatter
-
-// Nearest voxel of pixel (u, v) of frame f, or -1 outside the grid.
-__device__ __forceinline__ int64_t scatter_voxel(const ScatterArgs& A, int f, int u, int v) {
-    const int64_t* aff = A.affines + 9 * static_cast<int64_t>(f);
-    int64_t c[3];
-#pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int64_t G = __ldg(aff + a) + static_cast<int64_t>(u) * __ldg(aff + 3 + a) +
-                          static_cast<int64_t>(v) * __ldg(aff + 6 + a);
-        c[a] = (G + kFixOne / 2) >> kFixBits;  // floor(g + 1/2)
-        if (c[a] < 0 || c[a] >= A.dims[a]) return -1;
-    }
-    return c[0] + static_cast<int64_t>(A.dims[0]) * (c[1] + static_cast<int64_t>(A.dims[1]) * c[2]);
-}
-
-// blockIdx.y = frame; threads walk the frame's pixels in row-major order so
-// neighbouring lanes tend to share a voxel and one atomic serves the group.
-__global__ void __launch_bounds__(256) k_scatter_count(const __grid_constant__ ScatterArgs A, int32_t* count) {
-    const int f = blockIdx.y;
-    const int npx = A.width * A.height;
-    const int lane = threadIdx.x & 31;
-    for (int base = blockIdx.x * blockDim.x; base < npx; base += gridDim.x * blockDim.x) {
-        const int p = base + threadIdx.x;
-        int64_t vi = -1;
-        if (p < npx) vi = scatter_voxel(A, f, p % A.width, p / A.width);
-        const unsigned grp = __match_any_sync(0xFFFFFFFFu, vi);
-        const int leader = __ffs(grp) - 1;
-        if (vi >= 0 && lane == leader) atomicAdd(count + vi, __popc(grp));
-    }
-}
-
-__global__ void __launch_bounds__(256) k_scatter_place(const __grid_constant__ ScatterArgs A, int32_t* count,
-                                                       const int32_t* __restrict__ offsets,
-                                                       uint32_t* __restrict__ entries) {
-    const int f = blockIdx.y;
-    const int npx = A.width * A.height;
-    const int lane = threadIdx.x & 31;
-    const uint8_t* img = A.frames + static_cast<int64_t>(f) * npx;
-    const uint32_t fid = static_cast<uint32_t>(A.frame_base + f);
-    for (int base = blockIdx.x * blockDim.x; base < npx; base += gridDim.x * blockDim.x) {
-        const int p = base + threadIdx.x;
-        int64_t vi = -1;
-        uint32_t val = 0;
-        if (p < npx) {
-            vi = scatter_voxel(A, f, p % A.width, p / A.width);
-            if (vi >= 0) val = __ldg(img + p);
-        }
-        const unsigned grp = __match_any_sync(0xFFFFFFFFu, vi);
-        const int leader = __ffs(grp) - 1;
-        int old = 0;
-        if (vi >= 0 && lane == leader) old = atomicSub(count + vi, __popc(grp));
-        old = __shfl_sync(0xFFFFFFFFu, old, leader);
-        if (vi >= 0) {
-            const int rank = __popc(grp & ((1u << lane) - 1u));
-            // the group fills positions [old - size, old) of the voxel's range
-            const int pos = offsets[vi] + old - __popc(grp) + rank;
-            entries[pos] = (fid << 8) | val;
-        }
-    }
-}
-
 // ------------------------------------------------------------------ exclusive scan (3 passes)
 
 constexpr int kScanThreads = 1024;
@@ -280,156 +217,6 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t* __res
         run += vals[i];
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
-}
-
-// ------------------------------------------------------------------ finalize
-
-template <typename VT>
-__device__ __forceinline__ VT round_store(int sum, int cnt);
-template <>
-__device__ __forceinline__ float round_store<float>(int sum, int cnt) {
-    return __fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt));
-}
-template <>
-__device__ __forceinline__ __half round_store<__half>(int sum, int cnt) {
-    return __float2half_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
-}
-template <>
-__device__ __forceinline__ __nv_bfloat16 round_store<__nv_bfloat16>(int sum, int cnt) {
-    return __float2bfloat16_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
-}
-template <>
-__device__ __forceinline__ uint8_t round_store<uint8_t>(int sum, int cnt) {
-    const unsigned r = __float2uint_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
-    return static_cast<uint8_t>(r > 255u ? 255u : r);
-}
-
-// One thread per voxel.  The voxel's new entries (frame id << 8 | pixel) are
-// grouped by frame id in ascending order with a selection loop; the result
-// is merged with the samples already stored (whose ids are all lower) and,
-// when more than K samples exist, the K of largest npix are kept (ties:
-// lower frame id).  Integer sums make the outcome independent of the order
-// in which the scatter wrote the entries.
-template <int K, typename VT>
-__global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ offsets,
-                                                  const uint32_t* __restrict__ entries, int64_t n_vox,
-                                                  uint8_t* __restrict__ rec, uint16_t* __restrict__ npix,
-                                                  uint32_t* __restrict__ scal_sum, uint32_t* __restrict__ scal_cnt,
-                                                  unsigned long long* overflow) {
-    constexpr int RB = RecShape<K, VT>::kBytes;
-    for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n_vox;
-         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int s = offsets[v], e = offsets[v + 1];
-        if (s == e) continue;
-        uint16_t* ids = reinterpret_cast<uint16_t*>(rec + v * RB);
-        VT* vals = reinterpret_cast<VT*>(rec + v * RB + 2 * K);
-        uint16_t* np = npix + v * K;
-        int Lid[K], Lnp[K], Lcnt[K], Lsum[K];
-        VT Lraw[K];
-        bool Lnew[K];
-        int m = 0;
-#pragma unroll
-        for (int k = 0; k < K; ++k) {
-            const int id = ids[k];
-            if (id != DARE_EMPTY_FRAME && m == k) {
-                Lid[m] = id;
-                Lnp[m] = np[k];
-                Lcnt[m] = 0;
-                Lsum[m] = 0;
-                Lraw[m] = vals[k];
-                Lnew[m] = false;
-                ++m;
-            }
-        }
-        bool over = false;
-        uint32_t total = 0;
-        int last = -1;
-        for (;;) {
-            int next = INT_MAX, cnt = 0, sum = 0;
-            for (int i = s; i < e; ++i) {
-                const uint32_t x = __ldg(entries + i);
-                const int f = static_cast<int>(x >> 8);
-                if (f > last) {
-                    if (f < next) {
-                        next = f;
-                        cnt = 1;
-                        sum = static_cast<int>(x & 0xFFu);
-                    } else if (f == next) {
-                        ++cnt;
-                        sum += static_cast<int>(x & 0xFFu);
-                    }
-                }
-            }
-            if (next == INT_MAX) break;
-            total += static_cast<uint32_t>(sum);
-            last = next;
-            const int cs = cnt < 65535 ? cnt : 65535;
-            int slot = -1;
-            if (m < K) {
-                slot = m++;
-            } else {
-                over = true;
-                int wi = 0;
-                for (int k = 1; k < K; ++k)
-                    if (Lnp[k] < Lnp[wi] || (Lnp[k] == Lnp[wi] && Lid[k] > Lid[wi])) wi = k;
-                if (cs > Lnp[wi] || (cs == Lnp[wi] && next < Lid[wi])) slot = wi;
-            }
-            if (slot >= 0) {
-                Lid[slot] = next;
-                Lnp[slot] = cs;
-                Lcnt[slot] = cnt;
-                Lsum[slot] = sum;
-                Lnew[slot] = true;
-            }
-        }
-        // order by frame id (insertion sort over at most K entries)
-        for (int i = 1; i < m; ++i) {
-            const int id = Lid[i], pn = Lnp[i], c = Lcnt[i], sm = Lsum[i];
-            const VT raw = Lraw[i];
-            const bool nw = Lnew[i];
-            int j = i - 1;
-            while (j >= 0 && Lid[j] > id) {
-                Lid[j + 1] = Lid[j]; Lnp[j + 1] = Lnp[j]; Lcnt[j + 1] = Lcnt[j];
-                Lsum[j + 1] = Lsum[j]; Lraw[j + 1] = Lraw[j]; Lnew[j + 1] = Lnew[j];
-                --j;
-            }
-            Lid[j + 1] = id; Lnp[j + 1] = pn; Lcnt[j + 1] = c; Lsum[j + 1] = sm; Lraw[j + 1] = raw; Lnew[j + 1] = nw;
-        }
-        for (int k = 0; k < K; ++k) {
-            if (k < m) {
-                ids[k] = static_cast<uint16_t>(Lid[k]);
-                vals[k] = Lnew[k] ? round_store<VT>(Lsum[k], Lcnt[k]) : Lraw[k];
-                np[k] = static_cast<uint16_t>(Lnp[k]);
-            } else {
-                ids[k] = static_cast<uint16_t>(DARE_EMPTY_FRAME);
-                vals[k] = VT(0);
-                np[k] = 0;
-            }
-        }
-        if (scal_sum) {
-            scal_sum[v] += total;
-            scal_cnt[v] += static_cast<uint32_t>(e - s);
-        }
-        if (over) atomicAdd(overflow, 1ull);
-    }
-}
-
-template <int K>
-cudaError_t finalize_k(const int32_t* off, const uint32_t* ent, int64_t n_vox, uint8_t* rec, uint16_t* npix,
-                       uint32_t* ss, uint32_t* sc, int dtype, unsigned long long* ovf, cudaStream_t st) {
-    const int threads = 256;
-    const int64_t want = (n_vox + threads - 1) / threads;
-    const int blocks = static_cast<int>(want < 148 * 64 ? want : 148 * 64);
-    switch (dtype) {
-    case DARE_U8: k_finalize<K, uint8_t><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
-    case DARE_F16: k_finalize<K, __half><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
-    case DARE_BF16:
-        k_finalize<K, __nv_bfloat16><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
-        break;
-    case DARE_F32: k_finalize<K, float><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
-    default: return cudaErrorInvalidValue;
-    }
-    return cudaPeekAtLastError();
 }
 
 // ------------------------------------------------------------------ comparator, footprint, fill
@@ -532,25 +319,6 @@ cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* o
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, cudaStream_t st) {
-    if (a.n <= 0) return cudaSuccess;
-    const int npx = a.width * a.height;
-    const int bx = (npx + 255) / 256;
-    dim3 grid(bx < 64 ? bx : 64, a.n);
-    k_scatter_count<<<grid, 256, 0, st>>>(a, count);
-    return cudaPeekAtLastError();
-}
-
-cudaError_t launch_scatter_place(const ScatterArgs& a, int32_t* count, const int32_t* offsets, uint32_t* entries,
-                                 cudaStream_t st) {
-    if (a.n <= 0) return cudaSuccess;
-    const int npx = a.width * a.height;
-    const int bx = (npx + 255) / 256;
-    dim3 grid(bx < 64 ? bx : 64, a.n);
-    k_scatter_place<<<grid, 256, 0, st>>>(a, count, offsets, entries);
-    return cudaPeekAtLastError();
-}
-
 int64_t scan_block_sums_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
@@ -561,18 +329,6 @@ cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, in
     k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb);
     k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums, out);
     return cudaPeekAtLastError();
-}
-
-cudaError_t launch_finalize(const int32_t* offsets, const uint32_t* entries, int64_t n_vox, uint8_t* rec,
-                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
-                            unsigned long long* overflow, cudaStream_t st) {
-    switch (K) {
-    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
-    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
-    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
-    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
-    }
-    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,

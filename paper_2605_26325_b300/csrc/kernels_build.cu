@@ -1,0 +1,378 @@
+// Reconstruction kernels (Sec. 2.1 "Volume reconstruction", Fig. 1) for
+// sm_103a: pixel -> nearest voxel, one sample per (voxel, frame) holding the
+// mean of that frame's pixels in the voxel, samples kept per voxel in frame
+// order.
+//
+// Pipeline per chunk of frames:
+//   count  -- each CTA takes a 32 x 32 pixel tile of one frame and sums its
+//             pixels per voxel in a shared-memory hash table; every (voxel,
+//             tile) pair then bumps that voxel's counter once;
+//   scan   -- exclusive prefix sum of the counters (kernels.cu);
+//   place  -- the same tiles again; every (voxel, tile) pair writes one entry
+//             (frame id, npix, sum) into the voxel's range and returns the
+//             counter to zero;
+//   finalize -- one thread per voxel groups its entries by frame id (a frame
+//             split across tiles has several), appends the new samples after
+//             the stored ones (their ids are all lower) and applies the
+//             capacity rule when more than K samples exist.
+// Integer sums make the result independent of scheduling order.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include <climits>
+
+#include "dare_internal.h"
+
+namespace dare {
+namespace {
+
+constexpr int kTile = 32;             // frame tile: 32 x 32 pixels
+constexpr int kThreads = 256;         // 4 pixels per thread
+constexpr int kHash = 2048;           // >= 2 x pixels per tile: never full
+constexpr int kEmptyKey = -1;
+
+// Nearest voxel of pixel (u, v) (floor(g + 1/2) per axis), or -1 outside the grid.
+__device__ __forceinline__ int scatter_voxel(const int64_t* aff, const int* dims, int u, int v) {
+    int c[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t G = aff[a] + static_cast<int64_t>(u) * aff[3 + a] + static_cast<int64_t>(v) * aff[6 + a];
+        const int64_t q = (G + kFixOne / 2) >> kFixBits;
+        if (q < 0 || q >= dims[a]) return -1;
+        c[a] = static_cast<int>(q);
+    }
+    return c[0] + dims[0] * (c[1] + dims[1] * c[2]);
+}
+
+__device__ __forceinline__ void hash_add(int* keys, unsigned* npx, unsigned* sums, int vi, unsigned n, unsigned s) {
+    unsigned h = (static_cast<unsigned>(vi) * 2654435761u) >> 21;  // 11-bit Fibonacci hash
+    for (;;) {  // at most kTile^2 distinct keys in kHash slots: terminates
+        const int k0 = atomicCAS(keys + h, kEmptyKey, vi);
+        if (k0 == kEmptyKey || k0 == vi) {
+            atomicAdd(npx + h, n);
+            atomicAdd(sums + h, s);
+            return;
+        }
+        h = (h + 1) & (kHash - 1);
+    }
+}
+
+// Shared-memory aggregation of one frame tile: keys[h] = voxel, npx/sums[h] = its pixel count and sum.
+// Each thread owns the horizontal pixel pair (2 tx, 2 tx + 1) of rows ty, ty + 16; a pair that lands
+// in one voxel is combined before touching shared memory.
+__device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int u0, int v0, int* keys,
+                                               unsigned* npx, unsigned* sums) {
+    for (int i = threadIdx.x; i < kHash; i += kThreads) {
+        keys[i] = kEmptyKey;
+        npx[i] = 0u;
+        sums[i] = 0u;
+    }
+    __shared__ int64_t aff[9];
+    if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
+    __syncthreads();
+    const uint8_t* img = A.frames + static_cast<int64_t>(f) * A.width * A.height;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int u = u0 + 2 * tx;
+    // int32 steps from the tile origin when |A|, |B| < 2^25 (host flag), else int64 per pixel
+    int base[3] = {0, 0, 0}, ra[3] = {0, 0, 0}, rb[3] = {0, 0, 0}, r0[3] = {0, 0, 0};
+    if (A.small_steps) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int64_t G = aff[a] + static_cast<int64_t>(u0) * aff[3 + a] + static_cast<int64_t>(v0) * aff[6 + a] +
+                              kFixOne / 2;
+            const int64_t F = G >> kFixBits;
+            base[a] = static_cast<int>(F < -(1 << 24) ? -(1 << 24) : (F > (1 << 24) ? (1 << 24) : F));
+            r0[a] = static_cast<int>(G & (kFixOne - 1));
+            ra[a] = static_cast<int>(aff[3 + a]);
+            rb[a] = static_cast<int>(aff[6 + a]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+        const int v = v0 + ty + 16 * k;
+        if (v >= A.height) continue;
+        int vi[2];
+        unsigned val[2];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            vi[e] = -1;
+            val[e] = 0;
+            const int uu = u + e;
+            if (uu >= A.width) continue;
+            if (A.small_steps) {
+                const int du = uu - u0, dv = v - v0;
+                int c[3];
+                bool in = true;
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    c[a] = base[a] + ((r0[a] + du * ra[a] + dv * rb[a]) >> kFixBits);
+                    in = in && c[a] >= 0 && c[a] < A.dims[a];
+                }
+                if (in) vi[e] = c[0] + A.dims[0] * (c[1] + A.dims[1] * c[2]);
+            } else {
+                vi[e] = scatter_voxel(aff, A.dims, uu, v);
+            }
+            if (vi[e] >= 0) val[e] = __ldg(img + static_cast<int64_t>(v) * A.width + uu);
+        }
+        if (vi[0] >= 0 && vi[0] == vi[1]) {
+            hash_add(keys, npx, sums, vi[0], 2u, val[0] + val[1]);
+        } else {
+            if (vi[0] >= 0) hash_add(keys, npx, sums, vi[0], 1u, val[0]);
+            if (vi[1] >= 0) hash_add(keys, npx, sums, vi[1], 1u, val[1]);
+        }
+    }
+    __syncthreads();
+}
+
+template <bool kPlace>
+__global__ void __launch_bounds__(kThreads) k_scatter_tiles(const __grid_constant__ ScatterArgs A, int32_t* count,
+                                                            const int32_t* __restrict__ offsets,
+                                                            unsigned long long* __restrict__ entries) {
+    __shared__ int keys[kHash];
+    __shared__ unsigned npx[kHash];
+    __shared__ unsigned sums[kHash];
+    const int tiles_x = (A.width + kTile - 1) / kTile;
+    const int f = blockIdx.y;
+    const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
+    aggregate_tile(A, f, u0, v0, keys, npx, sums);
+    const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
+    for (int i = threadIdx.x; i < kHash; i += kThreads) {
+        const int vi = keys[i];
+        if (vi == kEmptyKey) continue;
+        if (kPlace) {
+            const int pos = offsets[vi] + atomicSub(count + vi, 1) - 1;
+            entries[pos] = fid | (static_cast<unsigned long long>(npx[i]) << 32) | sums[i];
+        } else {
+            atomicAdd(count + vi, 1);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ finalize
+
+template <typename VT>
+__device__ __forceinline__ VT round_store(int sum, int cnt);
+template <>
+__device__ __forceinline__ float round_store<float>(int sum, int cnt) {
+    return __fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt));
+}
+template <>
+__device__ __forceinline__ __half round_store<__half>(int sum, int cnt) {
+    return __float2half_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 round_store<__nv_bfloat16>(int sum, int cnt) {
+    return __float2bfloat16_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
+}
+template <>
+__device__ __forceinline__ uint8_t round_store<uint8_t>(int sum, int cnt) {
+    const unsigned r = __float2uint_rn(__fdiv_rn(static_cast<float>(sum), static_cast<float>(cnt)));
+    return static_cast<uint8_t>(r > 255u ? 255u : r);
+}
+
+__device__ __forceinline__ int ent_frame(unsigned long long e) { return static_cast<int>(e >> 48); }
+__device__ __forceinline__ int ent_npix(unsigned long long e) { return static_cast<int>((e >> 32) & 0xFFFFu); }
+__device__ __forceinline__ int ent_sum(unsigned long long e) { return static_cast<int>(e & 0xFFFFFFFFu); }
+
+// General merge: the m_old stored samples plus the new entries grouped by
+// frame; more than K samples keep the K of largest npix (ties: lower id).
+template <int K, typename VT>
+__device__ __noinline__ bool merge_general(const unsigned long long* entries, int s, int e, int m_old, uint16_t* ids,
+                                           VT* vals, uint16_t* np) {
+    int Lid[K], Lnp[K], Lcnt[K], Lsum[K];
+    VT Lraw[K];
+    bool Lnew[K];
+    for (int k = 0; k < m_old; ++k) {
+        Lid[k] = ids[k];
+        Lnp[k] = np[k];
+        Lcnt[k] = 0;
+        Lsum[k] = 0;
+        Lraw[k] = vals[k];
+        Lnew[k] = false;
+    }
+    int m = m_old;
+    bool over = false;
+    int last = -1;
+    for (;;) {
+        int next = 0xFFFF, cnt = 0, sum = 0;
+        for (int i = s; i < e; ++i) {
+            const unsigned long long x = entries[i];
+            const int f = ent_frame(x);
+            if (f > last && f < next) {
+                next = f;
+                cnt = ent_npix(x);
+                sum = ent_sum(x);
+            } else if (f == next) {
+                cnt += ent_npix(x);
+                sum += ent_sum(x);
+            }
+        }
+        if (next == 0xFFFF) break;
+        last = next;
+        const int cs = cnt < 65535 ? cnt : 65535;
+        int slot = -1;
+        if (m < K) {
+            slot = m++;
+        } else {
+            over = true;
+            int wi = 0;
+            for (int k = 1; k < K; ++k)
+                if (Lnp[k] < Lnp[wi] || (Lnp[k] == Lnp[wi] && Lid[k] > Lid[wi])) wi = k;
+            if (cs > Lnp[wi] || (cs == Lnp[wi] && next < Lid[wi])) slot = wi;
+        }
+        if (slot >= 0) {
+            Lid[slot] = next;
+            Lnp[slot] = cs;
+            Lcnt[slot] = cnt;
+            Lsum[slot] = sum;
+            Lnew[slot] = true;
+        }
+    }
+    for (int i = 1; i < m; ++i) {  // order by frame id
+        const int id = Lid[i], pn = Lnp[i], c = Lcnt[i], sm = Lsum[i];
+        const VT raw = Lraw[i];
+        const bool nw = Lnew[i];
+        int j = i - 1;
+        while (j >= 0 && Lid[j] > id) {
+            Lid[j + 1] = Lid[j]; Lnp[j + 1] = Lnp[j]; Lcnt[j + 1] = Lcnt[j];
+            Lsum[j + 1] = Lsum[j]; Lraw[j + 1] = Lraw[j]; Lnew[j + 1] = Lnew[j];
+            --j;
+        }
+        Lid[j + 1] = id; Lnp[j + 1] = pn; Lcnt[j + 1] = c; Lsum[j + 1] = sm; Lraw[j + 1] = raw; Lnew[j + 1] = nw;
+    }
+    for (int k = 0; k < K; ++k) {
+        if (k < m) {
+            ids[k] = static_cast<uint16_t>(Lid[k]);
+            vals[k] = Lnew[k] ? round_store<VT>(Lsum[k], Lcnt[k]) : Lraw[k];
+            np[k] = static_cast<uint16_t>(Lnp[k]);
+        } else {
+            ids[k] = static_cast<uint16_t>(DARE_EMPTY_FRAME);
+            vals[k] = VT(0);
+            np[k] = 0;
+        }
+    }
+    return over;
+}
+
+constexpr int kRegEntries = 16;  // entries a voxel keeps in registers on the fast path
+
+template <int K, typename VT>
+__global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ offsets,
+                                                  const unsigned long long* __restrict__ entries, int64_t n_vox,
+                                                  uint8_t* __restrict__ rec, uint16_t* __restrict__ npix,
+                                                  uint32_t* __restrict__ scal_sum, uint32_t* __restrict__ scal_cnt,
+                                                  unsigned long long* overflow) {
+    constexpr int RB = (2 * K + K * static_cast<int>(sizeof(VT)) + 15) / 16 * 16;
+    for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n_vox;
+         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int s = offsets[v], e = offsets[v + 1];
+        if (s == e) continue;
+        uint16_t* ids = reinterpret_cast<uint16_t*>(rec + v * RB);
+        VT* vals = reinterpret_cast<VT*>(rec + v * RB + 2 * K);
+        uint16_t* np = npix + v * K;
+        int m_old = 0;
+        while (m_old < K && ids[m_old] != DARE_EMPTY_FRAME) ++m_old;
+        const int n = e - s;
+        uint32_t tot_sum = 0, tot_cnt = 0;
+        bool over = false;
+        bool done = false;
+        if (n <= kRegEntries) {
+            unsigned long long ent[kRegEntries];
+#pragma unroll
+            for (int i = 0; i < kRegEntries; ++i) {
+                ent[i] = i < n ? __ldg(entries + s + i) : (0xFFFFull << 48);
+                tot_sum += static_cast<uint32_t>(ent_sum(ent[i]));
+                tot_cnt += static_cast<uint32_t>(ent_npix(ent[i]));
+            }
+            // fast path: new samples (ascending frame id) go after the stored ones
+            int m = m_old, last = -1;
+            done = true;
+            for (;;) {
+                int next = 0xFFFF, cnt = 0, sum = 0;
+#pragma unroll
+                for (int i = 0; i < kRegEntries; ++i) {
+                    const int f = ent_frame(ent[i]);
+                    const bool lower = f > last && f < next;
+                    const bool same = f == next;
+                    cnt = lower ? ent_npix(ent[i]) : (same ? cnt + ent_npix(ent[i]) : cnt);
+                    sum = lower ? ent_sum(ent[i]) : (same ? sum + ent_sum(ent[i]) : sum);
+                    next = lower ? f : next;
+                }
+                if (next == 0xFFFF) break;
+                if (m == K) {  // more than K samples: capacity rule
+                    done = false;
+                    break;
+                }
+                ids[m] = static_cast<uint16_t>(next);
+                vals[m] = round_store<VT>(sum, cnt);
+                np[m] = static_cast<uint16_t>(cnt < 65535 ? cnt : 65535);
+                ++m;
+                last = next;
+            }
+        } else {
+            for (int i = s; i < e; ++i) {
+                tot_sum += static_cast<uint32_t>(ent_sum(entries[i]));
+                tot_cnt += static_cast<uint32_t>(ent_npix(entries[i]));
+            }
+        }
+        if (!done) over = merge_general<K, VT>(entries, s, e, m_old, ids, vals, np);
+        if (scal_sum) {
+            scal_sum[v] += tot_sum;
+            scal_cnt[v] += tot_cnt;
+        }
+        if (over) atomicAdd(overflow, 1ull);
+    }
+}
+
+template <int K>
+cudaError_t finalize_k(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
+                       uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, unsigned long long* ovf,
+                       cudaStream_t st) {
+    const int threads = 256;
+    const int64_t want = (n_vox + threads - 1) / threads;
+    const int blocks = static_cast<int>(want < 148 * 64 ? want : 148 * 64);
+    switch (dtype) {
+    case DARE_U8: k_finalize<K, uint8_t><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
+    case DARE_F16: k_finalize<K, __half><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
+    case DARE_BF16:
+        k_finalize<K, __nv_bfloat16><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        break;
+    case DARE_F32: k_finalize<K, float><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaPeekAtLastError();
+}
+
+dim3 scatter_grid(const ScatterArgs& a) {
+    const int tiles = ((a.width + kTile - 1) / kTile) * ((a.height + kTile - 1) / kTile);
+    return dim3(tiles, a.n);
+}
+
+}  // namespace
+
+cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    k_scatter_tiles<false><<<scatter_grid(a), kThreads, 0, st>>>(a, count, nullptr, nullptr);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_scatter_place(const ScatterArgs& a, int32_t* count, const int32_t* offsets,
+                                 unsigned long long* entries, cudaStream_t st) {
+    if (a.n <= 0) return cudaSuccess;
+    k_scatter_tiles<true><<<scatter_grid(a), kThreads, 0, st>>>(a, count, offsets, entries);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
+                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
+                            unsigned long long* overflow, cudaStream_t st) {
+    switch (K) {
+    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dare
