@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--dtype", choices=list(DTYPE_NAMES), default="f32")
     ap.add_argument("--slots", type=int, default=12)
     ap.add_argument("--path", choices=["tiled", "plain"], default="tiled")
+    ap.add_argument("--workload", choices=["working", "batched"], default="working",
+                    help="working: the 256^3 step (default); batched: 64 uneven volumes through a graph-replayed plan")
+    ap.add_argument("--volumes", type=int, default=64, help="volumes of the batched workload")
     ap.add_argument("--quick", action="store_true", help="main timed loop only (for profiler runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
@@ -428,12 +431,94 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
                                "one plane per call"}
 
 
+def run_batched(args, dist):
+    """Uneven batch: every plane of 64 volumes of different sizes resliced by one
+    autotuned plan replayed through a CUDA graph (volumes built untimed)."""
+    import torch
+
+    import paper_2605_26325_b300 as dare
+    import synth
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    device = f"cuda:{dev}"
+    t0 = time.perf_counter()
+    vols = synth.batched_workload(3 + dist.rank, n_volumes=args.volumes)
+    log(f"rank {dist.rank}: batched workload ready in {time.perf_counter() - t0:.1f} s")
+    stream = torch.cuda.current_stream()
+    sessions, items = [], []
+    overflow = 0
+    for v in vols:
+        s = dare.Session(v.grid.dims, v.grid.spacing, v.grid.vol_to_world, dtype=dare.DARE_F16, max_slots=8,
+                         device=dev)
+        fr = torch.from_numpy(v.frames).to(device)
+        s.build(fr, v.frame_poses, v.frame_px, stream)
+        torch.cuda.synchronize()
+        del fr
+        overflow += s.info().overflow_voxels
+        sessions.append(s)
+        for T, (W, H) in zip(v.plane_poses, v.plane_sizes):
+            out = torch.empty((H, W), dtype=torch.float32, device=device)
+            mask = torch.empty((H, dare.mask_words(W)), dtype=torch.int32, device=device)
+            items.append((s, T, out, mask, v.plane_px))
+    px = sum(o.numel() for _, _, o, _, _ in items)
+    reqs = dare.make_requests(items)
+    t = time.perf_counter()
+    plan = dare.Plan(reqs, dare.params_default(path=dare.DARE_PATH_AUTO), stream)
+    tune_s = time.perf_counter() - t
+
+    def timed(fn, reps):
+        for _ in range(max(args.warmup, 3)):
+            fn()
+        torch.cuda.synchronize()
+        dist.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(reps):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return dist.max(a.elapsed_time(b) / reps)
+
+    clocks = ClockSampler(dev)
+    clocks.start()
+    n0 = dare.launch_count()
+    reps = max(args.steps, 300)  # about a second of replays, long enough for the clock sampler
+    ms_plan = timed(lambda: plan.launch(stream), reps)
+    launches = (dare.launch_count() - n0) // (reps + max(args.warmup, 3))
+    clk = clocks.stop()
+    ms_batch = timed(lambda: dare.reslice_batch(reqs, dare.params_default(), stream), args.steps)
+    ms_plain = timed(lambda: dare.reslice_batch(reqs, dare.params_default(path=dare.DARE_PATH_PLAIN), stream), 3)
+    info = plan.info()
+    line = {"metric": "resliced Mpix/s, uneven batch of 64 volumes through one graph-replayed plan",
+            "value": px * dist.world / ms_plan / 1e3, "unit": "Mpix/s", "n_gpus": dist.world, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": ms_plan, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"dare_batch_{len(vols)}vol_uneven", "volumes": len(vols), "planes": len(items),
+                       "out_mpix": px / 1e6, "storage": "f16", "slots": 8,
+                       "dims": "U(96..384, 96..384, 96..256) @ 0.4 mm", "sizes": "{128,256,512,640}^2",
+                       "overflow_voxels": int(overflow)},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "gpu_launches": int(launches),
+            "plan": {"groups": info["n_groups"], "choice": info["choice"], "tune_ms": info["tune_ms"],
+                     "tune_s": tune_s},
+            "paths_mpix_s": {"plan_graph": px / ms_plan / 1e3, "batch_call_tiled": px / ms_batch / 1e3,
+                             "batch_call_plain": px / ms_plain / 1e3}}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    plan.close()
+    for s in sessions:
+        s.close()
+
+
 def main():
     args = parse()
     dist = Dist()
     try:
         if args.impl == "reference":
             run_reference(args, dist)
+        elif args.workload == "batched":
+            run_batched(args, dist)
         else:
             run_dare(args, dist)
     finally:

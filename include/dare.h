@@ -298,6 +298,41 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
 dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream);
 
 /*
+ * Reslice plans: a fixed set of requests (sessions, output sizes and buffers)
+ * prepared once and replayed many times, for a stream of batches whose poses
+ * change (the batched workloads behind Sec. 3's timing and a serving loop).
+ * dare_plan_create groups the requests by storage type and slot count,
+ * chooses each group's kernel (with params->path == DARE_PATH_AUTO by timing
+ * the plain kernel and the tiled kernel with 32- and 64-row tiles on these
+ * very requests; results are cached per shape for the process), allocates
+ * the plan's device workspace and pinned staging, and captures the
+ * descriptor upload, the weight tables and the reslice launches into one CUDA
+ * graph (synchronous; writes the outputs while tuning).
+ * dare_plan_set_poses replaces every request's image_to_world (n x 16 host
+ * FP64, copied; waits for the previous launch's upload to finish).
+ * dare_plan_launch replays the graph on `stream`; each result equals
+ * dare_reslice of that request.  A session whose frame count changed since
+ * the plan was created makes launch fail with DARE_E_STATE (re-create the
+ * plan); rebuilding it to the same frame count is fine.
+ */
+typedef struct dare_plan_s* dare_plan;
+
+typedef struct {
+    int32_t n_requests;
+    int32_t n_groups;        /* launches per replay (one per storage type / K) */
+    int32_t choice[8];       /* per group: 0 = plain kernel, 32 or 64 = tiled, tile rows */
+    float tune_ms[8][3];     /* per group: measured plain, tiled-32, tiled-64 (0 if not timed) */
+    int64_t workspace_bytes;
+} dare_plan_info;
+
+dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream,
+                             dare_plan* out);
+dare_status dare_plan_set_poses(dare_plan p, const double* image_to_world);
+dare_status dare_plan_launch(dare_plan p, void* stream);
+dare_status dare_plan_query(dare_plan p, dare_plan_info* out);
+dare_status dare_plan_destroy(dare_plan p);
+
+/*
  * Allocation-free variant of dare_reslice.  The paper has no counterpart:
  * this entry point exists for callers that must not ask for device memory
  * while they run, e.g. a preview loop on the expert's console thread with a

@@ -91,6 +91,11 @@ class dare_session_info(ctypes.Structure):
                 ("vol_to_world", _d16)]
 
 
+class dare_plan_info(ctypes.Structure):
+    _fields_ = [("n_requests", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("choice", ctypes.c_int32 * 8),
+                ("tune_ms", (ctypes.c_float * 3) * 8), ("workspace_bytes", ctypes.c_int64)]
+
+
 class dare_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -120,6 +125,11 @@ _SIGNATURES = {
     "dare_reslice": ([_vp, _P(dare_plane), _P(dare_params), _vp, _vp, _vp], ctypes.c_int),
     "dare_reslice_batch": ([_P(dare_reslice_req), ctypes.c_int32, _P(dare_params), _vp], ctypes.c_int),
     "dare_reslice_noalloc": ([_vp, _P(dare_plane), _P(dare_params), _vp, _vp, _vp], ctypes.c_int),
+    "dare_plan_create": ([_P(dare_reslice_req), ctypes.c_int32, _P(dare_params), _vp, _P(_vp)], ctypes.c_int),
+    "dare_plan_set_poses": ([_vp, _P(ctypes.c_double)], ctypes.c_int),
+    "dare_plan_launch": ([_vp, _vp], ctypes.c_int),
+    "dare_plan_query": ([_vp, _P(dare_plan_info)], ctypes.c_int),
+    "dare_plan_destroy": ([_vp], ctypes.c_int),
     "dare_reslice_scalar": ([_vp, _P(dare_plane), ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
     "dare_footprint": ([_vp, _P(dare_plane), ctypes.c_int32, _P(ctypes.c_int64), _vp], ctypes.c_int),
     "dare_session_reset": ([_vp, _vp], ctypes.c_int),
@@ -434,6 +444,45 @@ def reslice_batch(requests, params=None, stream=None):
     p = params if params is not None else params_default()
     check(lib().dare_reslice_batch(requests, len(requests), ctypes.byref(p), _stream_ptr(stream)),
           "dare_reslice_batch")
+
+
+class Plan:
+    """A fixed request set replayed through a CUDA graph (dare_plan_*)."""
+
+    def __init__(self, requests, params=None, stream=None):
+        if not isinstance(requests, ctypes.Array):
+            requests = make_requests(requests)
+        self._reqs = requests  # keeps the descriptors alive
+        self.n = len(requests)
+        p = params if params is not None else params_default()
+        self._h = ctypes.c_void_p()
+        check(lib().dare_plan_create(requests, self.n, ctypes.byref(p), _stream_ptr(stream), ctypes.byref(self._h)),
+              "dare_plan_create")
+
+    def set_poses(self, poses):
+        poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(self.n, 16))
+        check(lib().dare_plan_set_poses(self._h, poses.ctypes.data_as(_P(ctypes.c_double))), "dare_plan_set_poses")
+
+    def launch(self, stream=None):
+        check(lib().dare_plan_launch(self._h, _stream_ptr(stream)), "dare_plan_launch")
+
+    def info(self):
+        i = dare_plan_info()
+        check(lib().dare_plan_query(self._h, ctypes.byref(i)), "dare_plan_query")
+        return {"n_requests": i.n_requests, "n_groups": i.n_groups, "choice": list(i.choice[:i.n_groups]),
+                "tune_ms": [list(i.tune_ms[g]) for g in range(i.n_groups)], "workspace_bytes": i.workspace_bytes}
+
+    def close(self):
+        if self._h and self._h.value:
+            check(lib().dare_plan_destroy(self._h), "dare_plan_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value and _LIB is not None:
+                _LIB.dare_plan_destroy(self._h)
+        except Exception:
+            pass
 
 
 def unpack_mask(mask_words_np, width):

@@ -415,8 +415,8 @@ ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab
     return j;
 }
 
-int tiles_of(const dare_plane* pl) {
-    return ((pl->width + kTileW - 1) / kTileW) * ((pl->height + kTileH - 1) / kTileH);
+int tiles_of(const dare_plane* pl, int tile_h = kTileH) {
+    return ((pl->width + kTileW - 1) / kTileW) * ((pl->height + tile_h - 1) / tile_h);
 }
 
 bool use_tiled(const dare_params* p) { return p->path != DARE_PATH_PLAIN; }
@@ -803,7 +803,7 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
     if (use_tiled(params)) {
         job.tile_base = 0;
         KernelScope ks("reslice_tiled", st, 1);
-        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, s->K, s->dtype, half_w, st));
+        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, kTileH, s->K, s->dtype, half_w, st));
     } else {
         KernelScope ks("reslice_plain", st, 1);
         CUDA_TRY(launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, s->K, s->dtype, half_w, st));
@@ -911,7 +911,7 @@ dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const da
             for (int32_t k = k0; uniform && k < k1; ++k) uniform = tiles_of(&reqs[order[k]].plane) == per;
             KernelScope ks("reslice_tiled", st, 1);
             CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base, uniform ? 1 : 0,
-                                          sg->K, sg->dtype, half_w, st));
+                                          kTileH, sg->K, sg->dtype, half_w, st));
         } else {
             KernelScope ks("reslice_plain", st, 1);
             CUDA_TRY(launch_reslice_plain(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
@@ -1220,7 +1220,7 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
     if (use_tiled(params)) {
         job.tile_base = 0;
         KernelScope ks("reslice_tiled", st, 1);
-        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, s->K, s->dtype, half_w, st));
+        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, kTileH, s->K, s->dtype, half_w, st));
     } else {
         KernelScope ks("reslice_plain", st, 1);
         CUDA_TRY(launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, s->K, s->dtype, half_w, st));
@@ -1229,3 +1229,335 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
 }
 
 }  // namespace dare
+
+// ---------------------------------------------------------------- plans (graph-replayed batches, autotuned)
+
+struct dare_plan_s {
+    struct Group {
+        int32_t k0 = 0, k1 = 0;   // range in `order`
+        int K = 0, dtype = 0;
+        int choice = kTileH;      // 0 = plain, else tiled tile rows
+        int max_w = 0, max_h = 0;
+        float tune_ms[3] = {0, 0, 0};
+    };
+    std::vector<dare_reslice_req> reqs;
+    dare_params params{};
+    std::vector<dare_session> sessions;
+    std::vector<int32_t> frames_at_create;
+    std::vector<int32_t> order;
+    std::vector<size_t> t_off;
+    std::vector<Group> groups;
+    int device = 0;
+    int max_frames = 0;
+    size_t o_tj = 0, o_rj = 0, desc_bytes = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    void* pinned = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaEvent_t done_ev = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+};
+
+namespace {
+
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_cache;
+
+int plan_tiles(const dare_plane* pl, int choice) { return choice == 0 ? 0 : tiles_of(pl, choice); }
+
+// Descriptors of every request for the plan's current poses and kernel choices,
+// written to its pinned staging buffer.
+void plan_fill(dare_plan p) {
+    uint8_t* pin = static_cast<uint8_t*>(p->pinned);
+    auto* tjs = reinterpret_cast<TableJob*>(pin);
+    auto* rjs = reinterpret_cast<ResliceJob*>(pin + (p->o_rj - p->o_tj));
+    uint8_t* ws = static_cast<uint8_t*>(p->ws);
+    for (const auto& g : p->groups) {
+        int tile_base = 0;
+        for (int32_t k = g.k0; k < g.k1; ++k) {
+            const dare_reslice_req& r = p->reqs[p->order[k]];
+            void* wtab = ws + p->t_off[p->order[k]];
+            TableJob tj{};
+            plane_vectors(r.session, &r.plane, p->params.normal_axis, &tj);
+            tj.frames = r.session->frames_dev;
+            tj.wtab = wtab;
+            tj.n_frames = r.session->n_frames;
+            tjs[k] = tj;
+            rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, p->params.unassigned);
+            rjs[k].tile_base = tile_base;
+            tile_base += plan_tiles(&r.plane, g.choice);
+        }
+    }
+}
+
+cudaError_t plan_group_launch(dare_plan p, const dare_plan_s::Group& g, cudaStream_t st) {
+    const auto* rj_dev = reinterpret_cast<const ResliceJob*>(static_cast<uint8_t*>(p->ws) + p->o_rj);
+    const int half_w = p->params.weight_dtype == DARE_WEIGHTS_F16;
+    if (g.choice == 0)
+        return launch_reslice_plain(rj_dev + g.k0, nullptr, g.k1 - g.k0, g.max_w, g.max_h, g.K, g.dtype, half_w, st);
+    const int per = tiles_of(&p->reqs[p->order[g.k0]].plane, g.choice);
+    bool uniform = g.k1 - g.k0 <= 65535;
+    int total = 0;
+    for (int32_t k = g.k0; k < g.k1; ++k) {
+        const int t = tiles_of(&p->reqs[p->order[k]].plane, g.choice);
+        uniform = uniform && t == per;
+        total += t;
+    }
+    return launch_reslice_tiled(rj_dev + g.k0, nullptr, g.k1 - g.k0, 0, uniform ? per : total, uniform ? 1 : 0,
+                                g.choice, g.K, g.dtype, half_w, st);
+}
+
+cudaError_t plan_tables_launch(dare_plan p, cudaStream_t st) {
+    const auto* tj_dev = reinterpret_cast<const TableJob*>(static_cast<uint8_t*>(p->ws) + p->o_tj);
+    return launch_weight_tables(tj_dev, nullptr, static_cast<int>(p->reqs.size()), p->max_frames,
+                                table_params(&p->params), st);
+}
+
+std::string tune_key(dare_plan p, const dare_plan_s::Group& g) {
+    long long px = 0;
+    for (int32_t k = g.k0; k < g.k1; ++k) px += int64_t(p->reqs[p->order[k]].plane.width) * p->reqs[p->order[k]].plane.height;
+    char buf[160];
+    std::snprintf(buf, sizeof(buf), "d%d K%d t%d n%d w%d h%d px%lld f%d hw%d", p->device, g.K, g.dtype, g.k1 - g.k0,
+                  g.max_w, g.max_h, px, p->max_frames, p->params.weight_dtype);
+    return buf;
+}
+
+// Time one group's candidate kernels on the plan's own requests; keep the fastest.
+dare_status plan_tune(dare_plan p, dare_plan_s::Group& g, cudaStream_t st) {
+    const std::string key = tune_key(p, g);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tune_cache.find(key);
+        if (it != g_tune_cache.end()) {
+            g.choice = it->second;
+            return DARE_OK;
+        }
+    }
+    const int cands[3] = {0, 32, 64};
+    cudaEvent_t a = nullptr, b = nullptr;
+    CUDA_TRY(cudaEventCreate(&a));
+    CUDA_TRY(cudaEventCreate(&b));
+    float best = 1e30f;
+    int best_c = kTileH;
+    for (int ci = 0; ci < 3; ++ci) {
+        g.choice = cands[ci];
+        plan_fill(p);
+        CUDA_TRY(cudaMemcpyAsync(static_cast<uint8_t*>(p->ws) + p->o_tj, p->pinned, p->desc_bytes,
+                                 cudaMemcpyHostToDevice, st));
+        CUDA_TRY(plan_tables_launch(p, st));
+        CUDA_TRY(plan_group_launch(p, g, st));  // warm-up
+        float ms = 1e30f;
+        for (int rep = 0; rep < 3; ++rep) {
+            CUDA_TRY(cudaEventRecord(a, st));
+            CUDA_TRY(plan_group_launch(p, g, st));
+            CUDA_TRY(cudaEventRecord(b, st));
+            CUDA_TRY(cudaEventSynchronize(b));
+            float t = 0;
+            CUDA_TRY(cudaEventElapsedTime(&t, a, b));
+            ms = std::min(ms, t);
+        }
+        g.tune_ms[ci] = ms;
+        if (ms < best) {
+            best = ms;
+            best_c = cands[ci];
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    g.choice = best_c;
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_cache[key] = best_c;
+    return DARE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+dare_status dare_plan_destroy(dare_plan p) {
+    if (!p) return DARE_OK;
+    DeviceGuard dg(p->device);
+    if (p->done_ev) cudaEventSynchronize(p->done_ev);
+    if (p->exec) cudaGraphExecDestroy(p->exec);
+    if (p->graph) cudaGraphDestroy(p->graph);
+    if (p->cap) cudaStreamDestroy(p->cap);
+    if (p->done_ev) cudaEventDestroy(p->done_ev);
+    if (p->pinned) cudaFreeHost(p->pinned);
+    if (p->ws && !p->sessions.empty()) {
+        p->sessions[0]->dev_free(p->ws, p->ws_bytes, nullptr);
+        g_in_use -= static_cast<int64_t>(p->ws_bytes);
+    }
+    delete p;
+    return DARE_OK;
+}
+
+dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream,
+                             dare_plan* out) {
+    if (!out) return fail(DARE_E_INVALID, "out is NULL");
+    *out = nullptr;
+    if (n <= 0 || !reqs) return fail(DARE_E_INVALID, "a plan needs at least one request");
+    dare_status rc = check_params(params);
+    if (rc != DARE_OK) return rc;
+    for (int32_t i = 0; i < n; ++i) {
+        const dare_reslice_req& r = reqs[i];
+        if (!r.session) return fail(DARE_E_INVALID, "request %d has no session", i);
+        if (r.session->cfg.device != reqs[0].session->cfg.device) return fail(DARE_E_INVALID, "requests span devices");
+        rc = check_plane(&r.plane);
+        if (rc != DARE_OK) return fail(rc, "request %d: %s", i, g_err.c_str());
+        if (!r.out || !r.mask) return fail(DARE_E_INVALID, "request %d: output pointers are NULL", i);
+        if (!affine_ok(r.session->cfg.grid.vol_to_world, r.session->cfg.grid.spacing_mm, r.plane.image_to_world,
+                       r.plane.width, r.plane.px_mm[0], r.plane.px_mm[1]))
+            return fail(DARE_E_INVALID, "request %d: plane too far from the grid", i);
+    }
+    auto* p = new dare_plan_s();
+    p->reqs.assign(reqs, reqs + n);
+    p->params = *params;
+    p->device = reqs[0].session->cfg.device;
+    DeviceGuard dg(p->device);
+    auto bail = [&](dare_status code) {
+        dare_plan_destroy(p);
+        return code;
+    };
+    for (int32_t i = 0; i < n; ++i)
+        if (std::find(p->sessions.begin(), p->sessions.end(), reqs[i].session) == p->sessions.end()) {
+            p->sessions.push_back(reqs[i].session);
+            p->frames_at_create.push_back(reqs[i].session->n_frames);
+        }
+    p->order.resize(n);
+    for (int32_t i = 0; i < n; ++i) p->order[i] = i;
+    std::stable_sort(p->order.begin(), p->order.end(), [&](int32_t a, int32_t b) {
+        const auto* sa = reqs[a].session;
+        const auto* sb = reqs[b].session;
+        return sa->K != sb->K ? sa->K < sb->K : sa->dtype < sb->dtype;
+    });
+    for (int32_t k0 = 0; k0 < n;) {
+        dare_plan_s::Group g;
+        const auto* sg = reqs[p->order[k0]].session;
+        g.k0 = k0;
+        g.K = sg->K;
+        g.dtype = sg->dtype;
+        int32_t k1 = k0;
+        while (k1 < n && reqs[p->order[k1]].session->K == g.K && reqs[p->order[k1]].session->dtype == g.dtype) {
+            g.max_w = std::max(g.max_w, reqs[p->order[k1]].plane.width);
+            g.max_h = std::max(g.max_h, reqs[p->order[k1]].plane.height);
+            ++k1;
+        }
+        g.k1 = k1;
+        g.choice = params->path == DARE_PATH_PLAIN ? 0 : kTileH;
+        p->groups.push_back(g);
+        k0 = k1;
+    }
+    if (p->groups.size() > 8) return bail(fail(DARE_E_INVALID, "a plan holds at most 8 storage-type/slot groups"));
+    const int wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
+    p->t_off.resize(n);
+    size_t o = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        p->t_off[i] = o;
+        o = align_up(o + size_t(std::max(reqs[i].session->n_frames, 1)) * wb, 256);
+        p->max_frames = std::max(p->max_frames, reqs[i].session->n_frames);
+    }
+    p->o_tj = o;
+    p->o_rj = align_up(p->o_tj + size_t(n) * sizeof(TableJob), 256);
+    const size_t need = align_up(p->o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    p->desc_bytes = need - p->o_tj;
+    rc = admit(static_cast<int64_t>(need));
+    if (rc != DARE_OK) return bail(rc);
+    p->ws = p->sessions[0]->dev_alloc(need, static_cast<cudaStream_t>(stream));
+    if (!p->ws) {
+        g_in_use -= static_cast<int64_t>(need);
+        return bail(fail(DARE_E_OOM, "plan workspace allocation of %zu bytes failed", need));
+    }
+    p->ws_bytes = need;
+    if (cudaHostAlloc(&p->pinned, p->desc_bytes, cudaHostAllocDefault) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&p->cap, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&p->done_ev, cudaEventDisableTiming) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(DARE_E_CUDA, "plan set-up failed"));
+    }
+    // tuning and capture run on the plan's own stream, after the sessions' queued work
+    for (auto* s : p->sessions) {
+        if (cudaStreamWaitEvent(p->cap, s->order_ev, 0) != cudaSuccess) return bail(fail(DARE_E_CUDA, "wait failed"));
+    }
+    if (params->path == DARE_PATH_AUTO)
+        for (auto& g : p->groups) {
+            rc = plan_tune(p, g, p->cap);
+            if (rc != DARE_OK) return bail(rc);
+        }
+    plan_fill(p);
+    if (cudaStreamSynchronize(p->cap) != cudaSuccess) return bail(fail(DARE_E_CUDA, "plan tuning failed"));
+    cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+        cudaError_t e1 = cudaMemcpyAsync(static_cast<uint8_t*>(p->ws) + p->o_tj, p->pinned, p->desc_bytes,
+                                         cudaMemcpyHostToDevice, p->cap);
+        if (e1 == cudaSuccess && p->max_frames > 0) e1 = plan_tables_launch(p, p->cap);
+        for (auto& g : p->groups)
+            if (e1 == cudaSuccess) e1 = plan_group_launch(p, g, p->cap);
+        e = cudaStreamEndCapture(p->cap, &p->graph);
+        if (e == cudaSuccess) e = e1;
+    }
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&p->exec, p->graph, 0);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return bail(fail(DARE_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e)));
+    }
+    if (cudaEventRecord(p->done_ev, p->cap) != cudaSuccess) return bail(fail(DARE_E_CUDA, "event record failed"));
+    *out = p;
+    return DARE_OK;
+}
+
+dare_status dare_plan_set_poses(dare_plan p, const double* image_to_world) {
+    if (!p || !image_to_world) return fail(DARE_E_INVALID, "NULL argument");
+    const int32_t n = static_cast<int32_t>(p->reqs.size());
+    for (int32_t i = 0; i < n; ++i) {
+        const double* T = image_to_world + 16 * size_t(i);
+        const dare_reslice_req& r = p->reqs[i];
+        if (!rigid_ok(T)) return fail(DARE_E_INVALID, "pose %d is not a rigid transform", i);
+        if (!affine_ok(r.session->cfg.grid.vol_to_world, r.session->cfg.grid.spacing_mm, T, r.plane.width,
+                       r.plane.px_mm[0], r.plane.px_mm[1]))
+            return fail(DARE_E_INVALID, "pose %d too far from the grid", i);
+    }
+    DeviceGuard dg(p->device);
+    CUDA_TRY(cudaEventSynchronize(p->done_ev));
+    for (int32_t i = 0; i < n; ++i) std::memcpy(p->reqs[i].plane.image_to_world, image_to_world + 16 * size_t(i), 128);
+    plan_fill(p);
+    return DARE_OK;
+}
+
+dare_status dare_plan_launch(dare_plan p, void* stream) {
+    if (!p) return fail(DARE_E_INVALID, "plan is NULL");
+    for (size_t i = 0; i < p->sessions.size(); ++i)
+        if (p->sessions[i]->n_frames != p->frames_at_create[i])
+            return fail(DARE_E_STATE, "a session's frame count changed since the plan was made; re-create the plan");
+    DeviceGuard dg(p->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (auto* s : p->sessions) {
+        dare_status rc = session_begin(s, st);
+        if (rc != DARE_OK) return rc;
+    }
+    {
+        KernelScope ks("plan_graph", st, (p->max_frames > 0 ? 1 : 0) + static_cast<int>(p->groups.size()));
+        CUDA_TRY(cudaGraphLaunch(p->exec, st));
+    }
+    CUDA_TRY(cudaEventRecord(p->done_ev, st));
+    for (auto* s : p->sessions) {
+        dare_status rc = session_end(s, st);
+        if (rc != DARE_OK) return rc;
+    }
+    return DARE_OK;
+}
+
+dare_status dare_plan_query(dare_plan p, dare_plan_info* out) {
+    if (!p || !out) return fail(DARE_E_INVALID, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n_requests = static_cast<int32_t>(p->reqs.size());
+    out->n_groups = static_cast<int32_t>(p->groups.size());
+    for (size_t g = 0; g < p->groups.size() && g < 8; ++g) {
+        out->choice[g] = p->groups[g].choice;
+        for (int c = 0; c < 3; ++c) out->tune_ms[g][c] = p->groups[g].tune_ms[c];
+    }
+    out->workspace_bytes = static_cast<int64_t>(p->ws_bytes);
+    return DARE_OK;
+}
+
+}  // extern "C"

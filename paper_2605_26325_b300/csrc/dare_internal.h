@@ -94,10 +94,10 @@ cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned l
 cudaError_t launch_fill_records(uint8_t* rec, int64_t n_vox, int rec_bytes, int K, cudaStream_t st);
 
 // tiled kernel (kernels_tiled.cu)
-// uniform != 0: every job has n_tiles tiles (2-D grid, no job search)
+// uniform != 0: every job has n_tiles tiles (2-D grid, no job search); tile_h: 32 or 64
 cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
-                                 int tile_offset, int n_tiles, int uniform, int K, int dtype, int half_weights,
-                                 cudaStream_t st);
+                                 int tile_offset, int n_tiles, int uniform, int tile_h, int K, int dtype,
+                                 int half_weights, cudaStream_t st);
 constexpr int kTileW = 32;
 
 // allocation-free reslice support (api.cpp)
@@ -105,9 +105,6 @@ dare_status set_error(dare_status st, const char* msg);
 int session_device(dare_session s);
 dare_status reslice_with_table(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
                                uint32_t* mask_dev, void* stream, void* wtab, size_t wtab_bytes, int max_frames);
-#ifndef DARE_TILE_H
-#define DARE_TILE_H 64
-#endif
-constexpr int kTileH = DARE_TILE_H;
+constexpr int kTileH = 64;  // default tile height; plans may autotune 32 or 64
 
 }  // namespace dare

@@ -1,4 +1,4 @@
-// Tiled DARE reslice (sm_103a): one CTA per 32 x 64 pixel tile.
+// Tiled DARE reslice (sm_103a): one CTA per 32 x TH pixel tile (TH = 32 or 64).
 //
 // For a plane r the orientation weight w_f of Eq. 2 depends only on the
 // sample's frame f, so the weighted average of Sec. 2.1 with TENT weights t_c
@@ -146,7 +146,7 @@ __device__ void tile_setup(const ResliceJob& J, int u0, int v0, int u1, int v1, 
     T.Od = static_cast<int>(lmax(lmin(Gd >> kFixBits, 1 << 24), -(1 << 24)));
 }
 
-template <int K, typename VT, typename WT, int D>
+template <int K, typename VT, typename WT, int D, int TH>
 __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& T, int u0, int v0, int u1, int v1,
                                           float2* sAB, int* sCol) {
     constexpr int E1 = Axes<D>::E1, E2 = Axes<D>::E2;
@@ -189,7 +189,7 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
     const int A1 = static_cast<int>(J.a[E1]), B1 = static_cast<int>(J.b[E1]);
     const int A2 = static_cast<int>(J.a[E2]), B2 = static_cast<int>(J.b[E2]);
     const int Ad = static_cast<int>(J.a[D]), Bd = static_cast<int>(J.b[D]);
-    for (int r = warp; r < kTileH; r += kThreads / 32) {
+    for (int r = warp; r < TH; r += kThreads / 32) {
         const int v = v0 + r;
         if (v > v1) break;  // warp-uniform
         const int u = u0 + lane;
@@ -240,7 +240,7 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
 // One CTA per tile.  With `uniform` every job has `n_tiles` tiles and the job
 // is blockIdx.y; otherwise blockIdx.x runs over all tiles of the launch and
 // thread 0 finds the job by binary search over tile_base.
-template <int K, typename VT, typename WT>
+template <int K, typename VT, typename WT, int TH>
 __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_tiled(const ResliceJob* __restrict__ jobs,
                                                                                    int n_jobs, int tile_offset,
                                                                                    int uniform,
@@ -264,9 +264,9 @@ __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_til
         const ResliceJob& J0 = jobs ? jobs[T.job] : one;
         const int ty = lt / J0.tiles_x, tx = lt - ty * J0.tiles_x;
         T.u0 = tx * kTileW;
-        T.v0 = ty * kTileH;
+        T.v0 = ty * TH;
         T.u1 = min(T.u0 + kTileW, J0.width) - 1;
-        T.v1 = min(T.v0 + kTileH, J0.height) - 1;
+        T.v1 = min(T.v0 + TH, J0.height) - 1;
         if (J0.d == 0) tile_setup<0>(J0, T.u0, T.v0, T.u1, T.v1, T);
         else if (J0.d == 1) tile_setup<1>(J0, T.u0, T.v0, T.u1, T.v1, T);
         else tile_setup<2>(J0, T.u0, T.v0, T.u1, T.v1, T);
@@ -274,39 +274,49 @@ __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_til
     __syncthreads();
     const ResliceJob& J = jobs ? jobs[T.job] : one;
     switch (J.d) {
-    case 0: tile_body<K, VT, WT, 0>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
-    case 1: tile_body<K, VT, WT, 1>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
-    default: tile_body<K, VT, WT, 2>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    case 0: tile_body<K, VT, WT, 0, TH>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    case 1: tile_body<K, VT, WT, 1, TH>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    default: tile_body<K, VT, WT, 2, TH>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
     }
 }
 
 // n_tiles: tiles of the whole launch, or per job when `uniform`.
 template <int K, typename VT, typename WT>
 cudaError_t tiled_launch(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                         int n_tiles, int uniform, cudaStream_t st) {
+                         int n_tiles, int uniform, int tile_h, cudaStream_t st) {
     ResliceJob dummy{};
     const dim3 grid(n_tiles, (one || !uniform) ? 1 : n_jobs);
-    k_reslice_tiled<K, VT, WT><<<grid, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset,
-                                                         uniform, one ? *one : dummy);
+    if (tile_h == 32)
+        k_reslice_tiled<K, VT, WT, 32><<<grid, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset,
+                                                                 uniform, one ? *one : dummy);
+    else if (tile_h == 64)
+        k_reslice_tiled<K, VT, WT, 64><<<grid, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset,
+                                                                 uniform, one ? *one : dummy);
+    else
+        return cudaErrorInvalidValue;
     return cudaPeekAtLastError();
 }
 
 template <int K, typename VT>
 cudaError_t tiled_launch_w(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                           int n_tiles, int uniform, int half_w, cudaStream_t st) {
-    return half_w ? tiled_launch<K, VT, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, st)
-                  : tiled_launch<K, VT, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, st);
+                           int n_tiles, int uniform, int tile_h, int half_w, cudaStream_t st) {
+    return half_w ? tiled_launch<K, VT, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, st)
+                  : tiled_launch<K, VT, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, st);
 }
 
 template <int K>
 cudaError_t tiled_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                           int n_tiles, int uniform, int dtype, int half_w, cudaStream_t st) {
+                           int n_tiles, int uniform, int tile_h, int dtype, int half_w, cudaStream_t st) {
     switch (dtype) {
-    case DARE_U8: return tiled_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, half_w, st);
-    case DARE_F16: return tiled_launch_w<K, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, half_w, st);
+    case DARE_U8:
+        return tiled_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, half_w, st);
+    case DARE_F16:
+        return tiled_launch_w<K, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, half_w, st);
     case DARE_BF16:
-        return tiled_launch_w<K, __nv_bfloat16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, half_w, st);
-    case DARE_F32: return tiled_launch_w<K, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, half_w, st);
+        return tiled_launch_w<K, __nv_bfloat16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, half_w,
+                                                st);
+    case DARE_F32:
+        return tiled_launch_w<K, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, half_w, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -314,15 +324,15 @@ cudaError_t tiled_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, in
 }  // namespace
 
 cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int tile_offset,
-                                 int n_tiles, int uniform, int K, int dtype, int half_weights, cudaStream_t st) {
+                                 int n_tiles, int uniform, int tile_h, int K, int dtype, int half_weights,
+                                 cudaStream_t st) {
     if (n_jobs <= 0 || n_tiles <= 0) return cudaSuccess;
+    const int u = uniform, th = tile_h, hw = half_weights;
     switch (K) {
-    case 4: return tiled_launch_k<4>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, dtype, half_weights, st);
-    case 8: return tiled_launch_k<8>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, dtype, half_weights, st);
-    case 12:
-        return tiled_launch_k<12>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, dtype, half_weights, st);
-    case 16:
-        return tiled_launch_k<16>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, dtype, half_weights, st);
+    case 4: return tiled_launch_k<4>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, u, th, dtype, hw, st);
+    case 8: return tiled_launch_k<8>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, u, th, dtype, hw, st);
+    case 12: return tiled_launch_k<12>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, u, th, dtype, hw, st);
+    case 16: return tiled_launch_k<16>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, u, th, dtype, hw, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -302,3 +302,49 @@ def working_workload(seed=1, n_poses=1000, render=True):
     frames = render_frames(ph, poses, W, H, sx, sy) if render else None
     rp = smooth_trajectory(seed, n_poses, 1000.0, 512, 512, 0.2, 0.2, tilts)
     return Workload("dare_256cube_1600f_512px", grid, W, H, (sx, sy), poses, frames, 512, 512, (0.2, 0.2), rp, tilts)
+
+
+@dataclass
+class BatchVolume:
+    grid: Grid
+    frame_w: int
+    frame_h: int
+    frame_px: tuple
+    frame_poses: np.ndarray
+    frames: np.ndarray
+    plane_poses: np.ndarray      # (m, 4, 4)
+    plane_sizes: list            # m x (W, H)
+    plane_px: tuple
+
+
+def batched_workload(seed=3, n_volumes=64, frame_step_mm=0.8, px_mm=0.4, plane_px_mm=0.3, render=True):
+    """Uneven batch: n_volumes grids with dims drawn uniformly from 96^3 to
+    384 x 384 x 256 at 0.4 mm, each scanned by 2-6 linear sweeps (per-volume
+    phantom seed, beam tilts in [-40, 40] deg, sometimes 90), each with 8-32
+    reslice planes whose sizes are drawn from {128, 256, 512, 640}^2 (square)."""
+    rng = np.random.default_rng(np.random.SeedSequence([int(seed), 0xBA7C]))
+    vols = []
+    for k in range(n_volumes):
+        dims = (int(rng.integers(96, 385)), int(rng.integers(96, 385)), int(rng.integers(96, 257)))
+        grid = centred_grid(dims, 0.4)
+        ext = grid.extent
+        W = int(math.ceil(ext[0] / px_mm))
+        H = int(math.ceil(ext[2] * 1.1 / px_mm))
+        n_sweeps = int(rng.integers(2, 7))
+        tilts = [float(rng.uniform(-40, 40)) for _ in range(n_sweeps)]
+        if rng.random() < 0.3:
+            tilts[-1] = 90.0
+        n_frames = max(2, int(ext[1] / frame_step_mm))
+        vseed = int(rng.integers(0, 2**31 - 1))
+        poses = np.concatenate([sweep_poses(vseed, s, n_frames, H, px_mm, t, float(ext[1]), centre=(0.0, 0.0, 0.0))
+                                for s, t in enumerate(tilts)])
+        ph = make_phantom(vseed, float(min(ext)), 4 + int(rng.integers(0, 5)), 1)
+        frames = render_frames(ph, poses, W, H, px_mm, px_mm) if render else None
+        m = int(rng.integers(8, 33))
+        sizes = [int(rng.choice([128, 256, 512, 640])) for _ in range(m)]
+        base = perturbed_poses(vseed, poses, m, 10.0, 3.0)
+        planes = np.stack([plane_pose_centred(base[i][:3, :3], base[i][:3, 3] + base[i][:3, :3] @ np.array(
+            [0.0, 0.5 * (H - 1) * px_mm, 0.0]), sizes[i], sizes[i], plane_px_mm, plane_px_mm) for i in range(m)])
+        vols.append(BatchVolume(grid, W, H, (px_mm, px_mm), poses, frames, planes, [(z, z) for z in sizes],
+                                (plane_px_mm, plane_px_mm)))
+    return vols

@@ -332,3 +332,49 @@ def test_trace_and_launch_count(tiny, tiny_f32):
     assert dare.launch_count() - n0 == 4
     assert t["reslice_tiled"][0] == 1 and t["reslice_plain"][0] == 1 and t["weight_table"][0] == 2
     assert all(ms > 0 for _, ms in t.values())
+
+
+@pytest.mark.parametrize("path", [dare.DARE_PATH_AUTO, dare.DARE_PATH_PLAIN, dare.DARE_PATH_TILED])
+def test_plan_graph_replay(tiny, path):
+    """A plan (graph capture, autotuned kernels) over two sessions of different
+    storage types and uneven sizes equals dare_reslice per request, and a replay
+    after set_poses equals the new poses resliced alone."""
+    s1 = gpu_session(tiny, dare.DARE_F32, 8)
+    s2 = gpu_session(tiny, dare.DARE_F16, 4)
+    p = dare.params_default(path=path)
+    sizes = [(128, 128), (37, 23), (256, 64), (64, 200), (96, 96), (128, 128), (128, 128)]
+    items, poses_a, poses_b = [], [], []
+    for i, (W, H) in enumerate(sizes):
+        s = s1 if i % 2 == 0 else s2
+        Ta = synth.plane_pose_centred(tiny.reslice_poses[i][:3, :3], np.zeros(3), W, H, *tiny.out_px)
+        Tb = synth.plane_pose_centred(tiny.reslice_poses[i + 7][:3, :3], np.zeros(3), W, H, *tiny.out_px)
+        out, mask = new_outputs(W, H)
+        items.append((s, Ta, out, mask, tiny.out_px))
+        poses_a.append(Ta)
+        poses_b.append(Tb)
+    plan = dare.Plan(items, p)
+    info = plan.info()
+    assert info["n_groups"] == 2 and info["n_requests"] == len(sizes)
+    if path == dare.DARE_PATH_AUTO:
+        assert all(c in (0, 32, 64) for c in info["choice"])
+    for poses in (poses_a, poses_b):
+        plan.set_poses(np.stack(poses))
+        for _, _, out, mask, _ in items:
+            out.fill_(-7.0)
+        plan.launch()
+        torch.cuda.synchronize()
+        for (s, _, out, mask, px), T in zip(items, poses):
+            H, W = out.shape
+            o1, m1 = gpu_reslice(s, T, W, H, px, dare.params_default())
+            assert np.array_equal(mask.cpu().numpy(), m1)
+            cov = dare.unpack_mask(m1, W).astype(bool)
+            got = out.cpu().numpy()
+            assert np.all(np.abs(got[cov] - o1[cov]) <= 1e-5 * np.maximum(np.abs(o1[cov]), 1))
+            assert np.all(got[~cov] == 0.0)
+    s1.reset()
+    with pytest.raises(dare.DareError) as ei:
+        plan.launch()
+    assert ei.value.status == dare.DARE_E_STATE
+    plan.close()
+    s1.close()
+    s2.close()
