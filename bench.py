@@ -49,8 +49,10 @@ def parse():
     ap.add_argument("--dtype", choices=list(DTYPE_NAMES), default="f32")
     ap.add_argument("--slots", type=int, default=12)
     ap.add_argument("--path", choices=["tiled", "plain"], default="tiled")
-    ap.add_argument("--workload", choices=["working", "batched"], default="working",
-                    help="working: the 256^3 step (default); batched: 64 uneven volumes through a graph-replayed plan")
+    ap.add_argument("--workload", choices=["working", "batched", "serving"], default="working",
+                    help="working: the 256^3 step (default); batched: 64 uneven volumes through a graph-replayed "
+                         "plan; serving: 16 sessions under Poisson pose streams with live ingestion")
+    ap.add_argument("--duration", type=float, default=10.0, help="seconds of the serving run")
     ap.add_argument("--volumes", type=int, default=64, help="volumes of the batched workload")
     ap.add_argument("--quick", action="store_true", help="main timed loop only (for profiler runs)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
@@ -511,6 +513,175 @@ def run_batched(args, dist):
         s.close()
 
 
+def run_serving(args, dist):
+    """16 sessions (dims 128^3 .. 512x512x384, u8/f16) admitted under a 120 GB
+    device-memory budget; each session's poses arrive as a Poisson stream at
+    60-1000 Hz with a fixed output size in 256^2 .. 640^2; two sessions ingest
+    new sweep frames live (30 frames/s in batches of 3).  Reports throughput
+    and submit-to-done latency percentiles."""
+    import torch
+
+    import paper_2605_26325_b300 as dare
+    import synth
+
+    dev = dist.local
+    torch.cuda.set_device(dev)
+    device = f"cuda:{dev}"
+    rng = np.random.default_rng(np.random.SeedSequence([11, dist.rank]))
+    dare.set_memory_budget(120 * 10**9)
+    t0 = time.perf_counter()
+    sessions, meta, rejected = [], [], 0
+    for k in range(16):
+        dims = (int(rng.integers(128, 513)), int(rng.integers(128, 513)), int(rng.integers(128, 385)))
+        grid = synth.centred_grid(dims, 0.4)
+        ext = grid.extent
+        W, H = int(np.ceil(ext[0] / 0.4)), int(np.ceil(ext[2] * 1.1 / 0.4))
+        tilts = [float(rng.uniform(-40, 40)) for _ in range(int(rng.integers(2, 5)))]
+        nf = int(ext[1] / 0.8)
+        vseed = int(rng.integers(0, 2**31 - 1))
+        ph = synth.make_phantom(vseed, float(min(ext)), 6, 1)
+        poses = np.concatenate([synth.sweep_poses(vseed, i, nf, H, 0.4, t, float(ext[1])) for i, t in enumerate(tilts)])
+        dtype = dare.DARE_U8 if k % 2 == 0 else dare.DARE_F16
+        try:
+            s = dare.Session(dims, 0.4, grid.vol_to_world, dtype=dtype, max_slots=8, device=dev)
+        except dare.DareError as e:
+            if e.status != dare.DARE_E_ADMISSION:
+                raise
+            rejected += 1
+            continue
+        frames = torch.from_numpy(synth.render_frames(ph, poses, W, H, 0.4, 0.4)).to(device)
+        s.build(frames, poses, (0.4, 0.4))
+        torch.cuda.synchronize()
+        del frames
+        live = None
+        if len(meta) < 2:  # the first two admitted sessions get a live sweep
+            lp = synth.sweep_poses(vseed, 99, int(30 * args.duration) + 6, H, 0.4, float(rng.uniform(-40, 40)),
+                                   float(ext[1]))
+            live = (torch.from_numpy(synth.render_frames(ph, lp, W, H, 0.4, 0.4)).to(device), lp)
+        size = int(rng.choice([256, 320, 384, 448, 512, 576, 640]))
+        rate = float(rng.uniform(60, 1000))
+        traj = synth.smooth_trajectory(vseed, int(args.duration * 1000) + 10, 1000.0, size, size, 0.3, 0.3, tilts,
+                                       pos_sigma_mm=0.15 * float(min(ext)))
+        sessions.append(s)
+        meta.append({"dims": dims, "dtype": "u8" if dtype == dare.DARE_U8 else "f16", "size": size, "rate": rate,
+                     "traj": traj, "live": live, "W": W, "H": H})
+    log(f"rank {dist.rank}: {len(sessions)} sessions admitted ({rejected} rejected), in use "
+        f"{dare.memory_in_use() / 1e9:.1f} GB, set-up {time.perf_counter() - t0:.1f} s")
+    # arrivals: merged Poisson streams
+    arrivals = []
+    for i, m in enumerate(meta):
+        t = 0.0
+        while True:
+            t += float(rng.exponential(1.0 / m["rate"]))
+            if t >= args.duration:
+                break
+            arrivals.append((t, i))
+    arrivals.sort()
+    ring = 64
+    bufs = [[(torch.empty((m["size"], m["size"]), dtype=torch.float32, device=device),
+              torch.empty((m["size"], dare.mask_words(m["size"])), dtype=torch.int32, device=device))
+             for _ in range(ring)] for m in meta]
+    free = [list(range(ring)) for _ in meta]
+    server = dare.Server(device=dev, lanes=3, max_batch=64)
+    tag_of = {}
+    lat, ingest_lat, px_done, dropped = [], [], 0, 0
+
+    def collect():
+        nonlocal px_done
+        for tag, status, kind, t_sub, t_done in server.poll():
+            if status != dare.DARE_OK:
+                raise RuntimeError(f"request {tag} failed with status {status}")
+            if kind == 1:
+                ingest_lat.append((t_done - t_sub) * 1e3)
+                continue
+            i, b = tag_of.pop(tag)
+            free[i].append(b)
+            lat.append((t_done - t_sub) * 1e3)
+            px_done += meta[i]["size"] ** 2
+
+    # untimed warm-up: every session's kernels once (CUDA loads kernels lazily on first launch) and one
+    # ingest per live session
+    tag = 1 << 50
+    for i, m in enumerate(meta):
+        out, mask = bufs[i][0]
+        server.submit(sessions[i], m["traj"][0], out, mask, (0.3, 0.3), tag)
+        tag += 1
+    ingest_idx = [0, 0]
+    for j in range(min(2, len(meta))):
+        fr, lp = meta[j]["live"]
+        server.ingest(sessions[j], fr[0:3], lp[0:3], (0.4, 0.4), tag=tag)
+        ingest_idx[j] = 3
+        tag += 1
+    server.drain(60.0)
+    server.poll()
+    tag = 0
+    dist.barrier()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    start = dare.clock_seconds()
+    next_ingest = 0.0
+    k = 0
+    while k < len(arrivals):
+        now = dare.clock_seconds() - start
+        while k < len(arrivals) and arrivals[k][0] <= now:
+            t_arr, i = arrivals[k]
+            k += 1
+            if not free[i]:
+                collect()
+            if not free[i]:
+                dropped += 1
+                continue
+            b = free[i].pop()
+            out, mask = bufs[i][b]
+            traj = meta[i]["traj"]
+            server.submit(sessions[i], traj[min(int(t_arr * 1000), len(traj) - 1)], out, mask, (0.3, 0.3), tag)
+            tag_of[tag] = (i, b)
+            tag += 1
+        while now >= next_ingest and next_ingest < args.duration:
+            for j in range(min(2, len(meta))):
+                fr, lp = meta[j]["live"]
+                a = ingest_idx[j]
+                if a + 3 <= fr.shape[0]:
+                    server.ingest(sessions[j], fr[a:a + 3], lp[a:a + 3], (0.4, 0.4), tag=(1 << 40) + tag)
+                    ingest_idx[j] = a + 3
+                    tag += 1
+            next_ingest += 0.1
+        collect()
+        if k < len(arrivals):
+            wait = arrivals[k][0] - (dare.clock_seconds() - start)
+            if wait > 2e-4:
+                time.sleep(min(wait, 1e-3))
+    server.drain(60.0)
+    collect()
+    wall = dare.clock_seconds() - start
+    clk = clocks.stop()
+    st = server.stats()
+    server.close()
+    lat = np.asarray(lat)
+    line = {"metric": "serving: resliced Mpix/s and submit-to-done latency over 16 sessions",
+            "value": px_done / wall / 1e6 * dist.world, "unit": "Mpix/s", "n_gpus": dist.world,
+            "steps": len(lat), "warmup": 0, "ms_per_step": float(np.mean(lat)) if lat.size else None,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "dare_serving_16sessions", "duration_s": args.duration,
+                       "sessions": len(sessions), "rejected_by_budget": rejected, "budget_gb": 120,
+                       "device_gb_in_use": dare.memory_in_use() / 1e9,
+                       "rates_hz": [round(m["rate"]) for m in meta], "sizes": [m["size"] for m in meta],
+                       "dims": [m["dims"] for m in meta], "storage": [m["dtype"] for m in meta],
+                       "live_ingest_sessions": min(2, len(meta)), "lanes": 3, "max_batch": 64},
+            "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "p99.9": percentile(lat, 99.9),
+                           "max": float(lat.max())},
+            "ingest_latency_ms": {"p50": percentile(ingest_lat, 50), "max": float(max(ingest_lat))}
+            if ingest_lat else None,
+            "requests": int(lat.size), "dropped_no_buffer": int(dropped),
+            "server": {k2: int(v) for k2, v in st.items()},
+            "mean_batch": st["completed"] / max(st["batches"], 1),
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+    for s in sessions:
+        s.close()
+
+
 def main():
     args = parse()
     dist = Dist()
@@ -519,6 +690,8 @@ def main():
             run_reference(args, dist)
         elif args.workload == "batched":
             run_batched(args, dist)
+        elif args.workload == "serving":
+            run_serving(args, dist)
         else:
             run_dare(args, dist)
     finally:

@@ -333,6 +333,58 @@ dare_status dare_plan_query(dare_plan p, dare_plan_info* out);
 dare_status dare_plan_destroy(dare_plan p);
 
 /*
+ * Serving loop: many sessions' reslice requests arriving over time (the
+ * expert console's haptic pose stream, Sec. 1) plus live frame ingestion
+ * (incremental integration, Sec. 4).  A dispatcher thread batches every
+ * pending request whenever one of `lanes` streams is free (continuous
+ * batching: requests arriving while others run join the next batch), so the
+ * batches of different lanes overlap on the device.  A batch waits only for
+ * the ingests of the sessions it reads; an ingest waits for the reslices in
+ * flight, then runs dare_build_volume on the server's ingest stream.  Every
+ * result equals dare_reslice of that request against the volume as of its
+ * submission.  Completions are stamped by a host callback on the stream that
+ * finishes them, on the clock of dare_clock_seconds.
+ *
+ * Sessions given to a server must be idle (dare_session_sync) and must not be
+ * used outside the server until dare_server_drain returns.  frames_dev of an
+ * ingest must stay valid until its completion is polled.  Submission is
+ * thread-safe; the server allocates its per-lane workspace itself.
+ */
+typedef struct dare_server_s* dare_server;
+
+typedef struct {
+    int32_t device;
+    int32_t lanes;      /* batches in flight at once, 1..8 (default 2 when 0) */
+    int32_t max_batch;  /* requests per batch (default 64 when 0) */
+    int32_t reserved;
+    dare_params params;
+} dare_server_config;
+
+typedef struct {
+    uint64_t tag;
+    int32_t status;     /* dare_status of the request */
+    int32_t kind;       /* 0 reslice, 1 ingest */
+    double submit_s;    /* dare_clock_seconds at submission */
+    double done_s;      /* dare_clock_seconds when its stream finished it */
+} dare_completion;
+
+typedef struct {
+    int64_t submitted, completed, batches, ingests;
+    int64_t max_batch_seen;
+    int32_t lanes, reserved;
+} dare_server_stats;
+
+double dare_clock_seconds(void);
+dare_status dare_server_create(const dare_server_config* cfg, dare_server* out);
+dare_status dare_server_submit(dare_server sv, const dare_reslice_req* req, uint64_t tag);
+dare_status dare_server_ingest(dare_server sv, dare_session s, const uint8_t* frames_dev, int32_t n, int32_t width,
+                               int32_t height, const double px_mm[2], const double* image_to_world, uint64_t tag);
+dare_status dare_server_poll(dare_server sv, dare_completion* out, int32_t capacity, int32_t* n_out);
+dare_status dare_server_drain(dare_server sv, double timeout_s);
+dare_status dare_server_stats_get(dare_server sv, dare_server_stats* out);
+dare_status dare_server_destroy(dare_server sv);
+
+/*
  * Allocation-free variant of dare_reslice.  The paper has no counterpart:
  * this entry point exists for callers that must not ask for device memory
  * while they run, e.g. a preview loop on the expert's console thread with a

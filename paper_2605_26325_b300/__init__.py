@@ -96,6 +96,22 @@ class dare_plan_info(ctypes.Structure):
                 ("tune_ms", (ctypes.c_float * 3) * 8), ("workspace_bytes", ctypes.c_int64)]
 
 
+class dare_server_config(ctypes.Structure):
+    _fields_ = [("device", ctypes.c_int32), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32), ("params", dare_params)]
+
+
+class dare_completion(ctypes.Structure):
+    _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("kind", ctypes.c_int32),
+                ("submit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+
+
+class dare_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
+                ("ingests", ctypes.c_int64), ("max_batch_seen", ctypes.c_int64), ("lanes", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class dare_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int64), ("total_ms", ctypes.c_double)]
 
@@ -136,6 +152,15 @@ _SIGNATURES = {
     "dare_trace_enable": ([ctypes.c_int32], ctypes.c_int),
     "dare_trace_read": ([_P(dare_kernel_time), ctypes.c_int32, _P(ctypes.c_int32)], ctypes.c_int),
     "dare_launch_count": ([], ctypes.c_int64),
+    "dare_clock_seconds": ([], ctypes.c_double),
+    "dare_server_create": ([_P(dare_server_config), _P(_vp)], ctypes.c_int),
+    "dare_server_submit": ([_vp, _P(dare_reslice_req), ctypes.c_uint64], ctypes.c_int),
+    "dare_server_ingest": ([_vp, _vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_double),
+                            _P(ctypes.c_double), ctypes.c_uint64], ctypes.c_int),
+    "dare_server_poll": ([_vp, _P(dare_completion), ctypes.c_int32, _P(ctypes.c_int32)], ctypes.c_int),
+    "dare_server_drain": ([_vp, ctypes.c_double], ctypes.c_int),
+    "dare_server_stats_get": ([_vp, _P(dare_server_stats)], ctypes.c_int),
+    "dare_server_destroy": ([_vp], ctypes.c_int),
     "dare_set_memory_budget": ([ctypes.c_int64], ctypes.c_int),
     "dare_memory_in_use": ([], ctypes.c_int64),
 }
@@ -483,6 +508,71 @@ class Plan:
                 _LIB.dare_plan_destroy(self._h)
         except Exception:
             pass
+
+
+class Server:
+    """Continuous-batching serving loop (dare_server_*)."""
+
+    def __init__(self, device=0, lanes=2, max_batch=64, params=None):
+        c = dare_server_config()
+        c.device, c.lanes, c.max_batch = int(device), int(lanes), int(max_batch)
+        c.params = params if params is not None else params_default()
+        self._h = ctypes.c_void_p()
+        check(lib().dare_server_create(ctypes.byref(c), ctypes.byref(self._h)), "dare_server_create")
+        self._req = dare_reslice_req()
+        self._keep = {}
+
+    def submit(self, session, image_to_world, out, mask, px_mm, tag):
+        H, W = (int(x) for x in out.shape)
+        r = self._req
+        r.session = session.handle.value
+        r.plane = make_plane(W, H, px_mm, image_to_world)
+        r.out = out.data_ptr()
+        r.mask = mask.data_ptr()
+        check(lib().dare_server_submit(self._h, ctypes.byref(r), ctypes.c_uint64(tag)), "dare_server_submit")
+
+    def ingest(self, session, frames_dev, poses, px_mm, tag):
+        n, H, W = (int(x) for x in frames_dev.shape)
+        poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(n, 16))
+        px = (ctypes.c_double * 2)(float(px_mm[0]), float(px_mm[1]))
+        self._keep[tag] = frames_dev  # valid until its completion is polled
+        check(lib().dare_server_ingest(self._h, session.handle, ctypes.c_void_p(frames_dev.data_ptr()), n, W, H, px,
+                                       poses.ctypes.data_as(_P(ctypes.c_double)), ctypes.c_uint64(tag)),
+              "dare_server_ingest")
+
+    def poll(self, capacity=4096):
+        arr = (dare_completion * capacity)()
+        n = ctypes.c_int32()
+        check(lib().dare_server_poll(self._h, arr, capacity, ctypes.byref(n)), "dare_server_poll")
+        out = [(arr[i].tag, arr[i].status, arr[i].kind, arr[i].submit_s, arr[i].done_s) for i in range(n.value)]
+        for t, _, kind, _, _ in out:
+            if kind == 1:
+                self._keep.pop(t, None)
+        return out
+
+    def drain(self, timeout_s=60.0):
+        check(lib().dare_server_drain(self._h, float(timeout_s)), "dare_server_drain")
+
+    def stats(self):
+        st = dare_server_stats()
+        check(lib().dare_server_stats_get(self._h, ctypes.byref(st)), "dare_server_stats_get")
+        return {k: getattr(st, k) for k, _ in st._fields_ if k != "reserved"}
+
+    def close(self):
+        if self._h and self._h.value:
+            check(lib().dare_server_destroy(self._h), "dare_server_destroy")
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            if self._h and self._h.value and _LIB is not None:
+                _LIB.dare_server_destroy(self._h)
+        except Exception:
+            pass
+
+
+def clock_seconds():
+    return float(lib().dare_clock_seconds())
 
 
 def unpack_mask(mask_words_np, width):

@@ -19,7 +19,7 @@ HEADER = os.path.join(ROOT, "include", "dare.h")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CU_SOURCES = ["kernels.cu", "kernels_tiled.cu", "kernels_build.cu", "noalloc.cu"]
-CPP_SOURCES = ["api.cpp"]
+CPP_SOURCES = ["api.cpp", "server.cpp"]
 
 
 def _sources():

@@ -423,6 +423,118 @@ bool use_tiled(const dare_params* p) { return p->path != DARE_PATH_PLAIN; }
 
 }  // namespace
 
+// ---------------------------------------------------------------- batch helpers (shared with the server)
+
+namespace dare {
+
+dare_status check_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params) {
+    dare_status rc = check_params(params);
+    if (rc != DARE_OK) return rc;
+    for (int32_t i = 0; i < n; ++i) {
+        const dare_reslice_req& r = reqs[i];
+        if (!r.session) return fail(DARE_E_INVALID, "request %d has no session", i);
+        if (r.session->cfg.device != reqs[0].session->cfg.device) return fail(DARE_E_INVALID, "requests span devices");
+        rc = check_plane(&r.plane);
+        if (rc != DARE_OK) return fail(rc, "request %d: %s", i, g_err.c_str());
+        if (!r.out || !r.mask) return fail(DARE_E_INVALID, "request %d: output pointers are NULL", i);
+        if (!affine_ok(r.session->cfg.grid.vol_to_world, r.session->cfg.grid.spacing_mm, r.plane.image_to_world,
+                       r.plane.width, r.plane.px_mm[0], r.plane.px_mm[1]))
+            return fail(DARE_E_INVALID, "request %d: plane too far from the grid", i);
+    }
+    return DARE_OK;
+}
+
+// Device workspace (weight tables + descriptors) and pinned descriptor bytes of a batch.
+void batch_sizes(const dare_reslice_req* reqs, int32_t n, const dare_params* params, size_t* ws_need,
+                 size_t* desc_bytes) {
+    const int wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
+    size_t o = 0;
+    for (int32_t i = 0; i < n; ++i) o = align_up(o + size_t(std::max(reqs[i].session->n_frames, 1)) * wb, 256);
+    const size_t o_tj = o;
+    const size_t o_rj = align_up(o_tj + size_t(n) * sizeof(TableJob), 256);
+    *ws_need = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    *desc_bytes = *ws_need - o_tj;
+}
+
+// Queue weight tables and reslice launches for a checked batch on `st`, using
+// device workspace `ws` and pinned staging `pin` (sized by batch_sizes).  No
+// ordering against the sessions' other work: the caller provides it.
+dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, cudaStream_t st,
+                        uint8_t* ws, uint8_t* pin) {
+    const int wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
+    std::vector<size_t> t_off(n);
+    size_t o = 0;
+    int max_frames = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        t_off[i] = o;
+        o = align_up(o + size_t(std::max(reqs[i].session->n_frames, 1)) * wb, 256);
+        max_frames = std::max(max_frames, reqs[i].session->n_frames);
+    }
+    const size_t o_tj = o;
+    const size_t o_rj = align_up(o_tj + size_t(n) * sizeof(TableJob), 256);
+    const size_t desc_bytes = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256) - o_tj;
+    auto* tjs = reinterpret_cast<TableJob*>(pin);
+    auto* rjs = reinterpret_cast<ResliceJob*>(pin + (o_rj - o_tj));
+    // order jobs by (K, dtype) so each launch covers one group
+    std::vector<int32_t> order(n);
+    for (int32_t i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        const auto* sa = reqs[a].session;
+        const auto* sb = reqs[b].session;
+        return sa->K != sb->K ? sa->K < sb->K : sa->dtype < sb->dtype;
+    });
+    int total_tiles = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        const dare_reslice_req& r = reqs[order[k]];
+        void* wtab = ws + t_off[order[k]];
+        TableJob tj{};
+        plane_vectors(r.session, &r.plane, params->normal_axis, &tj);
+        tj.frames = r.session->frames_dev;
+        tj.wtab = wtab;
+        tj.n_frames = r.session->n_frames;
+        tjs[k] = tj;
+        rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, params->unassigned);
+        rjs[k].tile_base = total_tiles;
+        total_tiles += tiles_of(&r.plane);
+    }
+    CUDA_TRY(cudaMemcpyAsync(ws + o_tj, pin, desc_bytes, cudaMemcpyHostToDevice, st));
+    const auto* tj_dev = reinterpret_cast<const TableJob*>(ws + o_tj);
+    const auto* rj_dev = reinterpret_cast<const ResliceJob*>(ws + o_rj);
+    if (max_frames > 0) {
+        KernelScope ks("weight_table", st, 1);
+        CUDA_TRY(launch_weight_tables(tj_dev, nullptr, n, max_frames, table_params(params), st));
+    }
+    const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
+    for (int32_t k0 = 0; k0 < n;) {
+        const auto* sg = reqs[order[k0]].session;
+        int32_t k1 = k0;
+        int max_w = 0, max_h = 0;
+        while (k1 < n && reqs[order[k1]].session->K == sg->K && reqs[order[k1]].session->dtype == sg->dtype) {
+            max_w = std::max(max_w, reqs[order[k1]].plane.width);
+            max_h = std::max(max_h, reqs[order[k1]].plane.height);
+            ++k1;
+        }
+        if (use_tiled(params)) {
+            const int base = rjs[k0].tile_base;
+            const int end = (k1 < n) ? rjs[k1].tile_base : total_tiles;
+            // same tile count for every job of the group: 2-D grid without a job search
+            const int per = tiles_of(&reqs[order[k0]].plane);
+            bool uniform = k1 - k0 <= 65535;
+            for (int32_t k = k0; uniform && k < k1; ++k) uniform = tiles_of(&reqs[order[k]].plane) == per;
+            KernelScope ks("reslice_tiled", st, 1);
+            CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base,
+                                          uniform ? 1 : 0, kTileH, sg->K, sg->dtype, half_w, st));
+        } else {
+            KernelScope ks("reslice_plain", st, 1);
+            CUDA_TRY(launch_reslice_plain(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
+        }
+        k0 = k1;
+    }
+    return DARE_OK;
+}
+
+}  // namespace dare
+
 // ---------------------------------------------------------------- ABI
 
 extern "C" {
@@ -814,20 +926,9 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
 dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream) {
     if (n < 0 || (n > 0 && !reqs)) return fail(DARE_E_INVALID, "bad request list");
     if (n == 0) return DARE_OK;
-    dare_status rc = check_params(params);
+    dare_status rc = dare::check_batch(reqs, n, params);
     if (rc != DARE_OK) return rc;
     dare_session s0 = reqs[0].session;
-    for (int32_t i = 0; i < n; ++i) {
-        const dare_reslice_req& r = reqs[i];
-        if (!r.session) return fail(DARE_E_INVALID, "request %d has no session", i);
-        if (r.session->cfg.device != s0->cfg.device) return fail(DARE_E_INVALID, "requests span devices");
-        rc = check_plane(&r.plane);
-        if (rc != DARE_OK) return fail(rc, "request %d: %s", i, g_err.c_str());
-        if (!r.out || !r.mask) return fail(DARE_E_INVALID, "request %d: output pointers are NULL", i);
-        if (!affine_ok(r.session->cfg.grid.vol_to_world, r.session->cfg.grid.spacing_mm, r.plane.image_to_world,
-                       r.plane.width, r.plane.px_mm[0], r.plane.px_mm[1]))
-            return fail(DARE_E_INVALID, "request %d: plane too far from the grid", i);
-    }
     DeviceGuard dg(s0->cfg.device);
     if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -839,85 +940,15 @@ dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const da
         rc = session_begin(s, st);
         if (rc != DARE_OK) return rc;
     }
-    const int wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
-    // workspace: tables, then table jobs, then reslice jobs
-    std::vector<size_t> t_off(n);
-    size_t o = 0;
-    int max_frames = 0;
-    for (int32_t i = 0; i < n; ++i) {
-        t_off[i] = o;
-        o = align_up(o + size_t(std::max(reqs[i].session->n_frames, 1)) * wb, 256);
-        max_frames = std::max(max_frames, reqs[i].session->n_frames);
-    }
-    const size_t o_tj = o;
-    const size_t o_rj = align_up(o_tj + size_t(n) * sizeof(TableJob), 256);
-    const size_t need = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256);
-    rc = ensure_workspace(s0, need, st);
+    size_t ws_need = 0, desc_bytes = 0;
+    dare::batch_sizes(reqs, n, params, &ws_need, &desc_bytes);
+    rc = ensure_workspace(s0, ws_need, st);
     if (rc != DARE_OK) return rc;
-    const size_t desc_bytes = need - o_tj;
     rc = ensure_pinned(s0, 1, desc_bytes);
     if (rc != DARE_OK) return rc;
-    uint8_t* ws = static_cast<uint8_t*>(s0->ws);
-    uint8_t* pin = static_cast<uint8_t*>(s0->pinned[1]);
-    auto* tjs = reinterpret_cast<TableJob*>(pin);
-    auto* rjs = reinterpret_cast<ResliceJob*>(pin + (o_rj - o_tj));
-    // order jobs by (K, dtype) so each launch covers one group
-    std::vector<int32_t> order(n);
-    for (int32_t i = 0; i < n; ++i) order[i] = i;
-    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
-        const auto* sa = reqs[a].session;
-        const auto* sb = reqs[b].session;
-        return sa->K != sb->K ? sa->K < sb->K : sa->dtype < sb->dtype;
-    });
-    int total_tiles = 0;
-    for (int32_t k = 0; k < n; ++k) {
-        const dare_reslice_req& r = reqs[order[k]];
-        void* wtab = ws + t_off[order[k]];
-        TableJob tj{};
-        plane_vectors(r.session, &r.plane, params->normal_axis, &tj);
-        tj.frames = r.session->frames_dev;
-        tj.wtab = wtab;
-        tj.n_frames = r.session->n_frames;
-        tjs[k] = tj;
-        rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, params->unassigned);
-        rjs[k].tile_base = total_tiles;
-        total_tiles += tiles_of(&r.plane);
-    }
-    CUDA_TRY(cudaMemcpyAsync(ws + o_tj, pin, desc_bytes, cudaMemcpyHostToDevice, st));
+    rc = dare::queue_batch(reqs, n, params, st, static_cast<uint8_t*>(s0->ws), static_cast<uint8_t*>(s0->pinned[1]));
+    if (rc != DARE_OK) return rc;
     CUDA_TRY(cudaEventRecord(s0->pinned_ev[1], st));
-    const auto* tj_dev = reinterpret_cast<const TableJob*>(ws + o_tj);
-    const auto* rj_dev = reinterpret_cast<const ResliceJob*>(ws + o_rj);
-    if (max_frames > 0) {
-        KernelScope ks("weight_table", st, 1);
-        CUDA_TRY(launch_weight_tables(tj_dev, nullptr, n, max_frames, table_params(params), st));
-    }
-    const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
-    for (int32_t k0 = 0; k0 < n;) {
-        const auto* sg = reqs[order[k0]].session;
-        int32_t k1 = k0;
-        int max_w = 0, max_h = 0;
-        while (k1 < n && reqs[order[k1]].session->K == sg->K && reqs[order[k1]].session->dtype == sg->dtype) {
-            max_w = std::max(max_w, reqs[order[k1]].plane.width);
-            max_h = std::max(max_h, reqs[order[k1]].plane.height);
-            ++k1;
-        }
-        if (use_tiled(params)) {
-            // tile bases restart per group
-            const int base = rjs[k0].tile_base;
-            const int end = (k1 < n) ? rjs[k1].tile_base : total_tiles;
-            // same tile count for every job of the group: 2-D grid without a job search
-            const int per = tiles_of(&reqs[order[k0]].plane);
-            bool uniform = k1 - k0 <= 65535;
-            for (int32_t k = k0; uniform && k < k1; ++k) uniform = tiles_of(&reqs[order[k]].plane) == per;
-            KernelScope ks("reslice_tiled", st, 1);
-            CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base, uniform ? 1 : 0,
-                                          kTileH, sg->K, sg->dtype, half_w, st));
-        } else {
-            KernelScope ks("reslice_plain", st, 1);
-            CUDA_TRY(launch_reslice_plain(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
-        }
-        k0 = k1;
-    }
     for (auto* s : sess) {
         rc = session_end(s, st);
         if (rc != DARE_OK) return rc;
@@ -1183,6 +1214,9 @@ dare_status dare_session_load(const dare_session_config* cfg, const char* path, 
 namespace dare {
 
 dare_status set_error(dare_status st, const char* msg) { return fail(st, "%s", msg); }
+
+dare_status reserve_bytes(int64_t bytes) { return admit(bytes); }
+void release_bytes(int64_t bytes) { g_in_use -= bytes; }
 
 int session_device(dare_session s) { return s ? s->cfg.device : -1; }
 

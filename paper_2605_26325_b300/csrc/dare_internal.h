@@ -100,6 +100,15 @@ cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* o
                                  int half_weights, cudaStream_t st);
 constexpr int kTileW = 32;
 
+// batch helpers and memory accounting (api.cpp), used by the server
+dare_status check_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params);
+void batch_sizes(const dare_reslice_req* reqs, int32_t n, const dare_params* params, size_t* ws_need,
+                 size_t* desc_bytes);
+dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, cudaStream_t st,
+                        uint8_t* ws, uint8_t* pin);
+dare_status reserve_bytes(int64_t bytes);
+void release_bytes(int64_t bytes);
+
 // allocation-free reslice support (api.cpp)
 dare_status set_error(dare_status st, const char* msg);
 int session_device(dare_session s);

@@ -1,0 +1,100 @@
+"""Serving loop (dare_server_*): continuous batching over stream lanes gives each
+request exactly what it gets resliced alone, and live ingestion is ordered
+with the requests around it."""
+import numpy as np
+import pytest
+import torch
+
+import paper_2605_26325_b300 as dare
+import synth
+from gpu_helpers import DEV, gpu_reslice, gpu_session, new_outputs
+
+pytestmark = pytest.mark.gpu
+
+
+def _wait_all(server, n, timeout=30.0):
+    server.drain(timeout)
+    got = []
+    while len(got) < n:
+        got += server.poll()
+    return got
+
+
+def test_server_mix_equals_alone(tiny):
+    s1 = gpu_session(tiny, dare.DARE_F32, 8)
+    s2 = gpu_session(tiny, dare.DARE_U8, 4)
+    server = dare.Server(lanes=3, max_batch=5)
+    rng = np.random.default_rng(0)
+    jobs = []
+    for i in range(48):
+        s = s1 if rng.random() < 0.5 else s2
+        W, H = int(rng.choice([37, 64, 128, 160])), int(rng.choice([23, 64, 128]))
+        T = synth.plane_pose_centred(tiny.reslice_poses[i % 12][:3, :3], rng.uniform(-2, 2, 3), W, H, *tiny.out_px)
+        out, mask = new_outputs(W, H)
+        jobs.append((s, T, out, mask))
+        server.submit(s, T, out, mask, tiny.out_px, tag=i)
+    done = _wait_all(server, len(jobs))
+    assert sorted(d[0] for d in done) == list(range(48))
+    assert all(d[1] == dare.DARE_OK and d[4] >= d[3] for d in done)
+    st = server.stats()
+    assert st["submitted"] == st["completed"] == 48 and st["batches"] >= 10 and st["max_batch_seen"] <= 5
+    for s, T, out, mask in jobs:
+        H, W = out.shape
+        o1, m1 = gpu_reslice(s, T, W, H, tiny.out_px, dare.params_default())
+        assert np.array_equal(mask.cpu().numpy(), m1)
+        cov = dare.unpack_mask(m1, W).astype(bool)
+        got = out.cpu().numpy()
+        assert np.all(np.abs(got[cov] - o1[cov]) <= 1e-5 * np.maximum(np.abs(o1[cov]), 1))
+        assert np.all(got[~cov] == o1[~cov])
+    server.close()
+    s1.close()
+    s2.close()
+
+
+def test_server_ingest_is_ordered(tiny):
+    """Requests submitted before an ingest see the old volume, requests after it
+    the grown one."""
+    live = gpu_session(tiny, dare.DARE_F16, 8, frames=tiny.frames[:100], poses=tiny.frame_poses[:100])
+    half = gpu_session(tiny, dare.DARE_F16, 8, frames=tiny.frames[:100], poses=tiny.frame_poses[:100])
+    full = gpu_session(tiny, dare.DARE_F16, 8)
+    more = torch.from_numpy(tiny.frames[100:]).to(DEV)
+    server = dare.Server(lanes=2, max_batch=4)
+    before, after = [], []
+    for i in range(8):
+        out, mask = new_outputs(96, 96)
+        T = tiny.reslice_poses[i]
+        before.append((T, out, mask))
+        server.submit(live, T, out, mask, tiny.out_px, tag=i)
+    server.ingest(live, more, tiny.frame_poses[100:], tiny.frame_px, tag=1000)
+    for i in range(8):
+        out, mask = new_outputs(96, 96)
+        T = tiny.reslice_poses[i]
+        after.append((T, out, mask))
+        server.submit(live, T, out, mask, tiny.out_px, tag=100 + i)
+    done = _wait_all(server, 17)
+    assert {d[0] for d in done} == set(range(8)) | set(range(100, 108)) | {1000}
+    assert all(d[1] == dare.DARE_OK for d in done)
+    p = dare.params_default()
+    for ref_session, group in ((half, before), (full, after)):
+        for T, out, mask in group:
+            o1, m1 = gpu_reslice(ref_session, T, 96, 96, tiny.out_px, p)
+            assert np.array_equal(mask.cpu().numpy(), m1)
+            assert np.allclose(out.cpu().numpy(), o1, rtol=1e-5, atol=1e-5)
+    assert live.info().n_frames == 200
+    server.close()
+    for s in (live, half, full):
+        s.close()
+
+
+def test_server_rejects_bad_requests(tiny, tmp_path):
+    s = gpu_session(tiny, dare.DARE_F32, 8)
+    server = dare.Server()
+    out, mask = new_outputs(16, 16)
+    bad = np.eye(4)
+    bad[0, 0] = 3.0
+    with pytest.raises(dare.DareError) as ei:
+        server.submit(s, bad, out, mask, tiny.out_px, tag=1)
+    assert ei.value.status == dare.DARE_E_INVALID
+    server.drain(5.0)
+    server.close()
+    s.close()
