@@ -357,7 +357,9 @@ def run_dare(args, dist):
 
 
 def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, params, line, step, P, W, H):
-    """End-to-end arm, per-slice latency, and the comparators (plain FP32 and scalar trilinear)."""
+    """End-to-end arm, per-slice latency, the comparators (plain FP32 and scalar
+    trilinear) and the L2-resident mode on a small volume."""
+    import synth
     # --- end to end through the public API with host buffers
     frames_h = torch.from_numpy(w.frames).pin_memory()
     outs_h = torch.empty(outs.shape, dtype=outs.dtype).pin_memory()
@@ -397,6 +399,17 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
         torch.cuda.synchronize()
         return a.elapsed_time(b) / reps
 
+    def timed_on(fn, reps, st):
+        fn()
+        st.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(st)
+        for _ in range(reps):
+            fn()
+        b.record(st)
+        st.synchronize()
+        return a.elapsed_time(b) / reps
+
     plain = dare.params_default(path=dare.DARE_PATH_PLAIN)
     tiled = dare.params_default(path=dare.DARE_PATH_TILED)
     ms_tiled = timed(lambda: dare.reslice_batch(reqs, tiled, stream), 5)
@@ -427,6 +440,23 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
             torch.cuda.synchronize()
             xs.append((time.perf_counter() - t) * 1e3)
         return {"p50_ms": percentile(xs, 50), "p99_ms": percentile(xs, 99), "samples": n}
+
+    # L2-resident mode: a 128^3 f16 K=8 volume (67 MB of records) built from the same frames
+    side = torch.cuda.Stream()
+    l2 = {}
+    for name, flags in (("default", 0), ("l2_persist", dare.DARE_SESSION_L2_PERSIST)):
+        g = synth.centred_grid((128, 128, 128), 0.8)
+        sm = dare.Session(g.dims, g.spacing, g.vol_to_world, dtype=dare.DARE_F16, max_slots=8, device=dist.local,
+                          flags=flags)
+        sm.build(frames_d, w.frame_poses, w.frame_px, stream)
+        torch.cuda.synchronize()
+        rq = dare.make_requests([(sm, w.reslice_poses[i], outs[i], masks[i], w.out_px) for i in range(P)])
+        with torch.cuda.stream(side):
+            l2[name] = timed_on(lambda: dare.reslice_batch(rq, tiled, side), 5, side)
+        l2["volume_mb"] = sm.info().record_bytes * 128 ** 3 / 1e6
+        sm.close()
+    line["l2_mode"] = {"volume_mb": l2["volume_mb"], "default_ms": l2["default"], "l2_persist_ms": l2["l2_persist"],
+                       "planes": P}
 
     line["latency"] = {"tiled": lat(tiled), "plain_fp32": lat(plain),
                        "note": "wall time from the host call to the 512x512 image and mask on the device, "

@@ -150,6 +150,14 @@ typedef struct {
 } dare_allocator;
 
 #define DARE_SESSION_SCALAR 1 /* also keep the mean-compounding totals (dare_reslice_scalar) */
+/* Keep the volume's records resident in L2 while this session is resliced: its
+ * reslice launches run under a persisting access-policy window over the
+ * records (up to the device's persisting-L2 size), so output writes stream past
+ * them.  Meant for volumes under about 100 MB.  The window is set on the
+ * caller's stream for the library's own launches and the stream's previous
+ * window is restored before the call returns.  Not applied on the legacy
+ * default (NULL) stream or inside plans. */
+#define DARE_SESSION_L2_PERSIST 2
 
 typedef struct {
     dare_grid grid;

@@ -192,6 +192,58 @@ struct KernelScope {
     }
 };
 
+// Persisting-L2 window over a record range for the launches between
+// construction and destruction (DARE_SESSION_L2_PERSIST).
+struct L2Window {
+    cudaStream_t st = nullptr;
+    bool set = false;
+    cudaStreamAttrValue prev{};
+    L2Window(const void* base, size_t bytes, cudaStream_t stream) {
+        if (!stream || !base || bytes == 0) return;
+        static std::mutex mu;
+        static int max_persist[64] = {}, max_window[64] = {};
+        static bool limit_set[64] = {};
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return;
+        {
+            std::lock_guard<std::mutex> lk(mu);
+            if (!max_window[dev]) {
+                cudaDeviceGetAttribute(&max_persist[dev], cudaDevAttrMaxPersistingL2CacheSize, dev);
+                cudaDeviceGetAttribute(&max_window[dev], cudaDevAttrMaxAccessPolicyWindowSize, dev);
+                if (!max_window[dev]) max_window[dev] = -1;
+            }
+            if (max_window[dev] <= 0 || max_persist[dev] <= 0) return;
+            if (!limit_set[dev]) {
+                if (cudaDeviceSetLimit(cudaLimitPersistingL2CacheSize, static_cast<size_t>(max_persist[dev])) != cudaSuccess) {
+                    cudaGetLastError();
+                    return;
+                }
+                limit_set[dev] = true;
+            }
+        }
+        if (cudaStreamGetAttribute(stream, cudaStreamAttributeAccessPolicyWindow, &prev) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        cudaStreamAttrValue v{};
+        const size_t n = std::min(bytes, static_cast<size_t>(max_window[dev]));
+        v.accessPolicyWindow.base_ptr = const_cast<void*>(base);
+        v.accessPolicyWindow.num_bytes = n;
+        v.accessPolicyWindow.hitRatio = std::min(1.0f, static_cast<float>(max_persist[dev]) / static_cast<float>(n));
+        v.accessPolicyWindow.hitProp = cudaAccessPropertyPersisting;
+        v.accessPolicyWindow.missProp = cudaAccessPropertyStreaming;
+        if (cudaStreamSetAttribute(stream, cudaStreamAttributeAccessPolicyWindow, &v) != cudaSuccess) {
+            cudaGetLastError();
+            return;
+        }
+        st = stream;
+        set = true;
+    }
+    ~L2Window() {
+        if (set) cudaStreamSetAttribute(st, cudaStreamAttributeAccessPolicyWindow, &prev);
+    }
+};
+
 }  // namespace
 
 // ---------------------------------------------------------------- session
@@ -912,6 +964,7 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
     }
     ResliceJob job = make_job(s, plane, s->ws, out_dev, mask_dev, params->unassigned);
     const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
+    L2Window l2((s->cfg.flags & DARE_SESSION_L2_PERSIST) ? s->rec : nullptr, size_t(s->n_vox) * s->rec_bytes, st);
     if (use_tiled(params)) {
         job.tile_base = 0;
         KernelScope ks("reslice_tiled", st, 1);
@@ -946,7 +999,12 @@ dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const da
     if (rc != DARE_OK) return rc;
     rc = ensure_pinned(s0, 1, desc_bytes);
     if (rc != DARE_OK) return rc;
-    rc = dare::queue_batch(reqs, n, params, st, static_cast<uint8_t*>(s0->ws), static_cast<uint8_t*>(s0->pinned[1]));
+    {
+        const bool one_l2 = sess.size() == 1 && (s0->cfg.flags & DARE_SESSION_L2_PERSIST);
+        L2Window l2(one_l2 ? s0->rec : nullptr, size_t(s0->n_vox) * s0->rec_bytes, st);
+        rc = dare::queue_batch(reqs, n, params, st, static_cast<uint8_t*>(s0->ws),
+                               static_cast<uint8_t*>(s0->pinned[1]));
+    }
     if (rc != DARE_OK) return rc;
     CUDA_TRY(cudaEventRecord(s0->pinned_ev[1], st));
     for (auto* s : sess) {

@@ -378,3 +378,30 @@ def test_plan_graph_replay(tiny, path):
     plan.close()
     s1.close()
     s2.close()
+
+
+def test_l2_persist_mode_same_results(tiny):
+    """DARE_SESSION_L2_PERSIST changes cache policy only: results on a side
+    stream equal those of an ordinary session, batch and single."""
+    a = gpu_session(tiny, dare.DARE_F32, 8, flags=dare.DARE_SESSION_L2_PERSIST)
+    b = gpu_session(tiny, dare.DARE_F32, 8)
+    side = torch.cuda.Stream()
+    p = dare.params_default()
+    for T in tiny.reslice_poses[[0, 4, 9]]:
+        oa, ma = new_outputs(128, 128)
+        with torch.cuda.stream(side):
+            a.reslice(T, oa, ma, tiny.out_px, p, stream=side)
+        side.synchronize()
+        ob, mb = gpu_reslice(b, T, 128, 128, tiny.out_px, p)
+        assert np.array_equal(ma.cpu().numpy(), mb) and np.array_equal(oa.cpu().numpy(), ob)
+    items = []
+    for T in tiny.reslice_poses[:6]:
+        o, m = new_outputs(128, 128)
+        items.append((a, T, o, m, tiny.out_px))
+    dare.reslice_batch(items, p, stream=side)
+    side.synchronize()
+    for (_, T, o, m, _) in items:
+        ob, mb = gpu_reslice(b, T, 128, 128, tiny.out_px, p)
+        assert np.array_equal(m.cpu().numpy(), mb) and np.array_equal(o.cpu().numpy(), ob)
+    a.close()
+    b.close()
