@@ -63,7 +63,9 @@ def _lib():
     global _LIB
     if _LIB is None:
         from . import _build
-        lib = ctypes.CDLL(_build.build())
+        # a test may point the oracle at a deliberately broken build to check that the pins catch it
+        override = os.environ.get("DARE_ORACLE_LIB")
+        lib = ctypes.CDLL(override if override else _build.build())
         i32p, i64p, dp, u8p = _P(ctypes.c_int32), _P(ctypes.c_int64), _P(ctypes.c_double), _P(ctypes.c_uint8)
         vp = ctypes.c_void_p
         lib.ora_pixel_affine.argtypes = [dp, ctypes.c_double, dp, ctypes.c_int32, ctypes.c_double, ctypes.c_double, i64p]

@@ -1,0 +1,85 @@
+"""The pins catch plausible mistakes: each case plants one mistake in a copy of
+the oracle's source (on the CPU), builds it, and runs the pin suite against it;
+at least one pin must fail.  The unmodified source must pass."""
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SRC = os.path.join(ROOT, "oracle", "dare_oracle.c")
+
+MUTANTS = {
+    "in-plane term without absolute value (Eq. 1)":
+        ("double d_inplane = fabs(x_s[0] * c->x_r[0] + x_s[1] * c->x_r[1] + x_s[2] * c->x_r[2]);",
+         "double d_inplane = (x_s[0] * c->x_r[0] + x_s[1] * c->x_r[1] + x_s[2] * c->x_r[2]);"),
+    "normal term with absolute value (Eq. 1)":
+        ("double d_normal = n_s[0] * c->n_r[0] + n_s[1] * c->n_r[1] + n_s[2] * c->n_r[2];",
+         "double d_normal = fabs(n_s[0] * c->n_r[0] + n_s[1] * c->n_r[1] + n_s[2] * c->n_r[2]);"),
+    "Eq. 2 constants swapped":
+        ("return exp(p->k_normal * (d_normal - 1.0) + p->k_inplane * (d_inplane - 1.0));",
+         "return exp(p->k_inplane * (d_normal - 1.0) + p->k_normal * (d_inplane - 1.0));"),
+    "Eq. 2 in-plane term dropped":
+        ("return exp(p->k_normal * (d_normal - 1.0) + p->k_inplane * (d_inplane - 1.0));",
+         "return exp(p->k_normal * (d_normal - 1.0));"),
+    "threshold on the wrong term":
+        ("if (c->use_thr_i && d_inplane < c->cos_i) return 0.0;",
+         "if (c->use_thr_i && d_normal < c->cos_i) return 0.0;"),
+    "trilinear weight reuses the x distance":
+        ("t = (1.0 - fabs(dx) / R) * (1.0 - fabs(dy) / R) * (1.0 - fabs(dz) / R);",
+         "t = (1.0 - fabs(dx) / R) * (1.0 - fabs(dx) / R) * (1.0 - fabs(dz) / R);"),
+    "TENT window one voxel too wide":
+        ("lo[a] = f - R + 1; hi[a] = f + R;\n        }\n    }\n    double num",
+         "lo[a] = f - R; hi[a] = f + R;\n        }\n    }\n    double num"),
+    "voxelisation floors instead of rounding":
+        ("c[a] = fix_floor(G + FIX_ONE / 2); /* nearest voxel, ties up */",
+         "c[a] = fix_floor(G); /* nearest voxel, ties up */"),
+    "beam read from the lateral column":
+        ("quat_axis(q, p->normal_axis == 1 ? 2 : 1, n_s);", "quat_axis(q, p->normal_axis == 1 ? 2 : 0, n_s);"),
+    "volume rotation not transposed":
+        ("R[3 * r + c] = V[0 * 4 + r] * T[0 * 4 + c] + V[1 * 4 + r] * T[1 * 4 + c] + V[2 * 4 + r] * T[2 * 4 + c];",
+         "R[3 * r + c] = V[r * 4 + 0] * T[0 * 4 + c] + V[r * 4 + 1] * T[1 * 4 + c] + V[r * 4 + 2] * T[2 * 4 + c];"),
+    "pixel centring term dropped":
+        ("out[r] = fix_round((tm[r] - half_w * c0[r]) / h);", "out[r] = fix_round(tm[r] / h);"),
+    "capacity tie-break reversed":
+        ("return x->frame < y->frame ? -1 : (x->frame > y->frame);",
+         "return x->frame > y->frame ? -1 : (x->frame < y->frame);"),
+    "bf16 storage truncates":
+        ("b = (b + 0x7FFFu + lsb) & 0xFFFF0000u;", "b = b & 0xFFFF0000u;"),
+    "unassigned when the numerator is zero":
+        ("    if (den > 0) {\n        *out = num / den;", "    if (num > 0) {\n        *out = num / den;"),
+}
+
+
+def _run_pins(lib_path):
+    env = dict(os.environ, DARE_ORACLE_LIB=lib_path)
+    r = subprocess.run([sys.executable, "-m", "pytest", "-q", "-x", "-p", "no:cacheprovider",
+                        os.path.join(ROOT, "tests", "test_oracle_pins.py")], cwd=ROOT, env=env,
+                       capture_output=True, text=True, timeout=600)
+    return r.returncode, r.stdout[-2000:]
+
+
+def _build(src_text, tmp_path, name):
+    c = tmp_path / f"{name}.c"
+    so = tmp_path / f"{name}.so"
+    c.write_text(src_text)
+    subprocess.run(["gcc", "-O1", "-fPIC", "-shared", "-fopenmp", "-std=gnu11", "-ffp-contract=off", "-o", str(so),
+                    str(c), "-lm"], check=True)
+    return str(so)
+
+
+@pytest.mark.slow
+def test_unmodified_oracle_passes(tmp_path):
+    rc, out = _run_pins(_build(open(SRC).read(), tmp_path, "clean"))
+    assert rc == 0, out
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_planted_mistake_is_caught(tmp_path, name):
+    old, new = MUTANTS[name]
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique: {name}"
+    rc, out = _run_pins(_build(src.replace(old, new), tmp_path, "mutant"))
+    assert rc != 0, f"no pin caught: {name}\n{out}"
