@@ -6,6 +6,7 @@ Floating point: |gpu - oracle| <= 1e-5 max(|oracle|, 1) for FP32 weight tables
 """
 import ctypes
 import math
+import types
 
 import numpy as np
 import pytest
@@ -65,6 +66,23 @@ def test_build_append_equals_one_call(tiny):
     assert a.info().version == 4 and b.info().version == 1
     a.close()
     b.close()
+
+
+def test_build_fine_pixels_coarse_voxels(tiny):
+    """Pixels far finer than voxels (0.1 mm pixels in 4 mm voxels: over a
+    thousand pixels of one frame in a voxel, and voxels beyond capacity):
+    npix, means and the capacity rule stay bit-exact."""
+    w = types.SimpleNamespace(grid=synth.centred_grid((9, 8, 7), 4.0), frames=tiny.frames[:60],
+                              frame_poses=tiny.frame_poses[:60], frame_px=(0.1, 0.12))
+    for dtype in (dare.DARE_F32, dare.DARE_U8):
+        s = gpu_session(w, dtype, 8)
+        ids, vals, npix, e = oracle_dense(oracle_volume(w, dtype, 8), 8, dtype)
+        assert e["npix"].max() > 255
+        g = s.read_records(npix=True)
+        assert np.array_equal(g["frame_ids"], ids)
+        assert np.array_equal(g["values"].view(np.uint8), vals.view(np.uint8))
+        assert np.array_equal(g["npix"], npix)
+        s.close()
 
 
 def test_build_frame_table(tiny, tiny_f32):
