@@ -56,25 +56,18 @@ __device__ __forceinline__ int find_job(const ResliceJob* jobs, int n_jobs, int 
     return lo;
 }
 
-// (A_c, B_c) of one voxel: reads only the 16-byte chunks that hold its
-// occupied slots (ids first, values after; empty ids sort last).
+// (A_c, B_c) of one voxel from its whole record, read in one round trip (ids
+// first, values after; empty ids sort last).
 template <int K, typename VT, typename WT>
 __device__ __forceinline__ float2 collapse_voxel(const uint8_t* rec, int64_t vi, const WT* wt) {
     using S = RecShape<K, VT>;
-    constexpr int kIdChunks = (2 * K + 15) / 16;
     const uint4* q = reinterpret_cast<const uint4*>(rec + vi * S::kBytes);
     uint4 r[S::kVec];
 #pragma unroll
-    for (int i = 0; i < kIdChunks; ++i) r[i] = __ldg(q + i);
+    for (int i = 0; i < S::kVec; ++i) r[i] = __ldg(q + i);
     int count = 0;
 #pragma unroll
     for (int w = 0; w < K / 2; ++w) count += __popc(__vcmpne2(word_of(r, w), 0xFFFFFFFFu)) >> 4;
-#pragma unroll
-    for (int i = kIdChunks; i < S::kVec; ++i) {
-        constexpr int vb = static_cast<int>(sizeof(VT));
-        const int first = (16 * i - 2 * K + vb - 1) / vb;  // first slot whose value starts in chunk i
-        r[i] = first < count ? __ldg(q + i) : make_uint4(0, 0, 0, 0);
-    }
     float A = 0.0f, B = 0.0f;
 #pragma unroll
     for (int s = 0; s < K; ++s) {
@@ -117,6 +110,7 @@ struct TileSetup {
     int u0, v0, u1, v1;      // pixel range of the tile
     int b1, b2, n1, n2;      // column box
     int direct;
+    int empty;               // no pixel of the tile reaches the grid
     int R1, R2, Rd;          // 20-bit remainders of the tile origin's coordinates
     int O1, O2, Od;          // integer parts, relative to the box (clamped far outside when irrelevant)
 };
@@ -124,19 +118,29 @@ struct TileSetup {
 template <int D>
 __device__ void tile_setup(const ResliceJob& J, int u0, int v0, int u1, int v1, TileSetup& T) {
     constexpr int E1 = Axes<D>::E1, E2 = Axes<D>::E2;
-    int64_t lo1 = INT64_MAX, hi1 = INT64_MIN, lo2 = INT64_MAX, hi2 = INT64_MIN;
+    int64_t lo1 = INT64_MAX, hi1 = INT64_MIN, lo2 = INT64_MAX, hi2 = INT64_MIN, lod = INT64_MAX, hid = INT64_MIN;
     for (int k = 0; k < 4; ++k) {
         const int u = (k & 1) ? u1 : u0, v = (k & 2) ? v1 : v0;
         const int64_t f1 = axis_fix(J, E1, u, v) >> kFixBits, f2 = axis_fix(J, E2, u, v) >> kFixBits;
+        const int64_t fd = axis_fix(J, D, u, v) >> kFixBits;
         lo1 = lmin(lo1, f1); hi1 = lmax(hi1, f1);
         lo2 = lmin(lo2, f2); hi2 = lmax(hi2, f2);
+        lod = lmin(lod, fd); hid = lmax(hid, fd);
     }
-    T.b1 = static_cast<int>(lmax(lmin(lo1, J.dims[E1]), 0));
-    T.b2 = static_cast<int>(lmax(lmin(lo2, J.dims[E2]), 0));
-    T.n1 = static_cast<int>(lmax(0, lmin(hi1 + 1, J.dims[E1] - 1) - T.b1 + 1));
-    T.n2 = static_cast<int>(lmax(0, lmin(hi2 + 1, J.dims[E2] - 1) - T.b2 + 1));
-    const int ncol = T.n1 * T.n2;
-    T.direct = J.direct || ncol > kColMax || ncol * J.levels > kSlotMax;
+    // a pixel reads floors f .. f + 1 on each axis; when on some axis that
+    // range misses the grid for every pixel of the tile, the tile is unassigned
+    T.empty = hi1 + 1 < 0 || lo1 > J.dims[E1] - 1 || hi2 + 1 < 0 || lo2 > J.dims[E2] - 1 || hid + 1 < 0 ||
+              lod > J.dims[D] - 1;
+    // The box is not clipped to the grid: by convexity every pixel's column
+    // (k1, k2) and its +1 neighbours lie inside it, so the pixel pass needs no
+    // bounds tests; columns outside the grid hold zeros.
+    const int64_t n1 = hi1 + 2 - lo1, n2 = hi2 + 2 - lo2;
+    T.direct = !T.empty && (J.direct || n1 > kColMax || n2 > kColMax || n1 * n2 > kColMax || n1 * n2 * J.levels > kSlotMax ||
+               lo1 < -(1 << 30) || lo2 < -(1 << 30) || hi1 > (1 << 30) || hi2 > (1 << 30));
+    T.b1 = static_cast<int>(lmax(lmin(lo1, 1 << 30), -(1 << 30)));
+    T.b2 = static_cast<int>(lmax(lmin(lo2, 1 << 30), -(1 << 30)));
+    T.n1 = T.direct || T.empty ? 0 : static_cast<int>(n1);
+    T.n2 = T.direct || T.empty ? 0 : static_cast<int>(n2);
     const int64_t G1 = axis_fix(J, E1, u0, v0), G2 = axis_fix(J, E2, u0, v0), Gd = axis_fix(J, D, u0, v0);
     T.R1 = static_cast<int>(G1 & (kFixOne - 1));
     T.R2 = static_cast<int>(G2 & (kFixOne - 1));
@@ -153,13 +157,15 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const WT* wt = static_cast<const WT*>(J.wtab);
     const int b1 = T.b1, b2 = T.b2, n1 = T.n1, n2 = T.n2, ncol = n1 * n2, L = J.levels;
-    const bool direct = T.direct != 0;
+    const bool direct = T.direct != 0, empty = T.empty != 0;
 
-    if (!direct) {
-        // (A) per column: level range, then one collapse per candidate voxel
-        const float inv_n1 = 1.0f / static_cast<float>(max(n1, 1));
+    if (!direct && !empty) {
+        // (A) per column: its lowest level, then L slots (A_c, B_c) of levels
+        // lo .. lo + L - 1; slots outside the grid, past the column's level
+        // range or of columns no pixel of the tile reaches hold zeros
+        const float inv_n1 = 1.0f / static_cast<float>(n1);
         const float sm = J.spread + kMargin;
-        const int dd = J.dims[D];
+        const int dd = J.dims[D], d1 = J.dims[E1], d2 = J.dims[E2];
         for (int c = threadIdx.x; c < ncol; c += kThreads) {
             const int k2 = static_cast<int>((static_cast<float>(c) + 0.5f) * inv_n1);
             const int k1 = c - k2 * n1;
@@ -169,19 +175,22 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
             const bool near = fabsf(uc - fminf(fmaxf(uc, static_cast<float>(u0)), static_cast<float>(u1))) <= J.hu &&
                               fabsf(vc - fminf(fmaxf(vc, static_cast<float>(v0)), static_cast<float>(v1))) <= J.hv;
             const float gd = J.alpha + J.beta1 * c1 + J.beta2 * c2;
-            int lo = 0, cnt = 0;
-            if (near && fabsf(gd) < 16384.0f) {
-                lo = max(static_cast<int>(floorf(gd - sm)), 0);
-                const int hi = min(static_cast<int>(floorf(gd + sm)) + 1, dd - 1);
-                cnt = max(0, min(hi - lo + 1, L));
+            int lo = 0, top = -1;  // levels lo .. top may be read
+            if (near && fabsf(gd) < 16384.0f && static_cast<unsigned>(c1) < static_cast<unsigned>(d1) &&
+                static_cast<unsigned>(c2) < static_cast<unsigned>(d2)) {
+                lo = static_cast<int>(floorf(gd - sm));
+                top = min(static_cast<int>(floorf(gd + sm)) + 1, dd - 1);
             }
-            sCol[c] = (lo & 0xFFFF) | (cnt << 16);
+            sCol[c] = lo;
             const int64_t base = (D == 0 ? 0 : c1) + static_cast<int64_t>(J.dims[0]) *
                                  ((D == 1 ? 0 : (E1 == 1 ? c1 : c2)) + static_cast<int64_t>(J.dims[1]) * (D == 2 ? 0 : c2));
             const int64_t step = D == 0 ? 1 : (D == 1 ? static_cast<int64_t>(J.dims[0])
                                                       : static_cast<int64_t>(J.dims[0]) * J.dims[1]);
-            for (int lev = 0; lev < cnt; ++lev)
-                sAB[c * L + lev] = collapse_voxel<K, VT, WT>(J.rec, base + (lo + lev) * step, wt);
+            for (int lev = 0; lev < L; ++lev) {
+                const int g = lo + lev;
+                sAB[c * L + lev] = (g >= 0 && g <= top) ? collapse_voxel<K, VT, WT>(J.rec, base + g * step, wt)
+                                                        : make_float2(0.0f, 0.0f);
+            }
         }
         __syncthreads();
     }
@@ -198,12 +207,14 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
         if (active) {
             if (direct) {
                 direct_pixel<K, VT, WT>(J, u, v, num, den);
-            } else {
+            } else if (!empty) {
                 const int du = u - u0, dv = v - v0;
                 const int r1 = T.R1 + du * A1 + dv * B1;
                 const int r2 = T.R2 + du * A2 + dv * B2;
                 const int rd = T.Rd + du * Ad + dv * Bd;
-                const int k1 = (r1 >> kFixBits) + T.O1, k2 = (r2 >> kFixBits) + T.O2, fd = (rd >> kFixBits) + T.Od;
+                // k1 in [0, n1 - 2], k2 in [0, n2 - 2] by construction of the box
+                const int c00 = (r1 >> kFixBits) + T.O1 + n1 * ((r2 >> kFixBits) + T.O2);
+                const int fd = (rd >> kFixBits) + T.Od;
                 const float p1 = static_cast<float>(r1 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
                 const float p2 = static_cast<float>(r2 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
                 const float pd = static_cast<float>(rd & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
@@ -211,22 +222,16 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
                 for (int j = 0; j < 2; ++j) {
 #pragma unroll
                     for (int i = 0; i < 2; ++i) {
-                        if (static_cast<unsigned>(k1 + i) >= static_cast<unsigned>(n1) ||
-                            static_cast<unsigned>(k2 + j) >= static_cast<unsigned>(n2))
-                            continue;
-                        const int c = k1 + i + n1 * (k2 + j);
-                        const int info = sCol[c];
-                        const int lev = fd - (info & 0xFFFF);
-                        const int cnt = info >> 16;
+                        const int c = c00 + i + n1 * j;
+                        // levels fd, fd + 1 lie in the column's range; the clamp only keeps reads in bounds
+                        const int lev = min(max(fd - sCol[c], 0), L - 2);
+                        const float2 a0 = sAB[c * L + lev], a1 = sAB[c * L + lev + 1];
                         const float wc = (i ? p1 : 1.0f - p1) * (j ? p2 : 1.0f - p2);
-#pragma unroll
-                        for (int k = 0; k < 2; ++k) {
-                            if (static_cast<unsigned>(lev + k) >= static_cast<unsigned>(cnt)) continue;
-                            const float2 ab = sAB[c * L + lev + k];
-                            const float t = wc * (k ? pd : 1.0f - pd);
-                            num = fmaf(t, ab.x, num);
-                            den = fmaf(t, ab.y, den);
-                        }
+                        const float t0 = wc * (1.0f - pd), t1 = wc * pd;
+                        num = fmaf(t0, a0.x, num);
+                        den = fmaf(t0, a0.y, den);
+                        num = fmaf(t1, a1.x, num);
+                        den = fmaf(t1, a1.y, den);
                     }
                 }
             }
@@ -239,40 +244,45 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
 
 // One CTA per tile.  With `uniform` every job has `n_tiles` tiles and the job
 // is blockIdx.y; otherwise blockIdx.x runs over all tiles of the launch and
-// thread 0 finds the job by binary search over tile_base.
+// the first warp finds the job by binary search over tile_base.
 template <int K, typename VT, typename WT, int TH>
 __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_tiled(const ResliceJob* __restrict__ jobs,
                                                                                    int n_jobs, int tile_offset,
                                                                                    int uniform,
                                                                                    const __grid_constant__ ResliceJob one) {
     __shared__ float2 sAB[kSlotMax];
-    __shared__ int sCol[kColMax];  // per column: lowest level | (level count << 16)
+    __shared__ int sCol[kColMax];  // per column: its lowest level (slot 0)
     __shared__ TileSetup T;
-    if (threadIdx.x == 0) {
-        int lt;
-        if (!jobs) {
-            T.job = 0;
-            lt = static_cast<int>(blockIdx.x);
-        } else if (uniform) {
-            T.job = static_cast<int>(blockIdx.y);
-            lt = static_cast<int>(blockIdx.x);
-        } else {
+    __shared__ ResliceJob sJob;  // the tile's job: one coalesced copy, then shared-memory reads
+    static_assert(sizeof(ResliceJob) % 4 == 0, "job copied as 32-bit words");
+    if (threadIdx.x < 32) {
+        int job = 0, lt = static_cast<int>(blockIdx.x);
+        if (jobs && uniform) {
+            job = static_cast<int>(blockIdx.y);
+        } else if (jobs) {
             const int tile = tile_offset + static_cast<int>(blockIdx.x);
-            T.job = find_job(jobs, n_jobs, tile);
-            lt = tile - __ldg(&jobs[T.job].tile_base);
+            job = find_job(jobs, n_jobs, tile);
+            lt = tile - __ldg(&jobs[job].tile_base);
         }
-        const ResliceJob& J0 = jobs ? jobs[T.job] : one;
-        const int ty = lt / J0.tiles_x, tx = lt - ty * J0.tiles_x;
-        T.u0 = tx * kTileW;
-        T.v0 = ty * TH;
-        T.u1 = min(T.u0 + kTileW, J0.width) - 1;
-        T.v1 = min(T.v0 + TH, J0.height) - 1;
-        if (J0.d == 0) tile_setup<0>(J0, T.u0, T.v0, T.u1, T.v1, T);
-        else if (J0.d == 1) tile_setup<1>(J0, T.u0, T.v0, T.u1, T.v1, T);
-        else tile_setup<2>(J0, T.u0, T.v0, T.u1, T.v1, T);
+        const uint32_t* src = reinterpret_cast<const uint32_t*>(jobs ? jobs + job : &one);
+        uint32_t* dst = reinterpret_cast<uint32_t*>(&sJob);
+        for (int i = threadIdx.x; i < static_cast<int>(sizeof(ResliceJob) / 4); i += 32) dst[i] = src[i];
+        __syncwarp();
+        if (threadIdx.x == 0) {
+            const ResliceJob& J0 = sJob;
+            T.job = job;
+            const int ty = lt / J0.tiles_x, tx = lt - ty * J0.tiles_x;
+            T.u0 = tx * kTileW;
+            T.v0 = ty * TH;
+            T.u1 = min(T.u0 + kTileW, J0.width) - 1;
+            T.v1 = min(T.v0 + TH, J0.height) - 1;
+            if (J0.d == 0) tile_setup<0>(J0, T.u0, T.v0, T.u1, T.v1, T);
+            else if (J0.d == 1) tile_setup<1>(J0, T.u0, T.v0, T.u1, T.v1, T);
+            else tile_setup<2>(J0, T.u0, T.v0, T.u1, T.v1, T);
+        }
     }
     __syncthreads();
-    const ResliceJob& J = jobs ? jobs[T.job] : one;
+    const ResliceJob& J = sJob;
     switch (J.d) {
     case 0: tile_body<K, VT, WT, 0, TH>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
     case 1: tile_body<K, VT, WT, 1, TH>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
