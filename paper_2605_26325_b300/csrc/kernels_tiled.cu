@@ -65,14 +65,12 @@ __device__ __forceinline__ float2 collapse_voxel(const uint8_t* rec, int64_t vi,
     uint4 r[S::kVec];
 #pragma unroll
     for (int i = 0; i < S::kVec; ++i) r[i] = __ldg(q + i);
-    int count = 0;
-#pragma unroll
-    for (int w = 0; w < K / 2; ++w) count += __popc(__vcmpne2(word_of(r, w), 0xFFFFFFFFu)) >> 4;
     float A = 0.0f, B = 0.0f;
 #pragma unroll
     for (int s = 0; s < K; ++s) {
-        if (s >= count) break;
-        const float w = weight_of(wt, static_cast<int>(slot_id<K, VT>(r, s)));
+        const uint32_t id = slot_id<K, VT>(r, s);
+        if (id == DARE_EMPTY_FRAME) break;  // empty slots come last
+        const float w = weight_of(wt, static_cast<int>(id));
         A = fmaf(w, slot_value<K, VT>(r, s), A);
         B += w;
     }
@@ -166,15 +164,21 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
         const float inv_n1 = 1.0f / static_cast<float>(n1);
         const float sm = J.spread + kMargin;
         const int dd = J.dims[D], d1 = J.dims[E1], d2 = J.dims[E2];
+        const float ou = J.ou, ov = J.ov, m00 = J.m00, m01 = J.m01, m10 = J.m10, m11 = J.m11, hu = J.hu, hv = J.hv;
+        const float alpha = J.alpha, beta1 = J.beta1, beta2 = J.beta2;
+        const float fu0 = static_cast<float>(u0), fu1 = static_cast<float>(u1);
+        const float fv0 = static_cast<float>(v0), fv1 = static_cast<float>(v1);
+        const uint8_t* const rec = J.rec;
+        const int64_t sx = 1, sy = J.dims[0], sz = static_cast<int64_t>(J.dims[0]) * J.dims[1];
+        const int64_t st1 = E1 == 0 ? sx : sy, st2 = E2 == 1 ? sy : sz, std_ = D == 0 ? sx : (D == 1 ? sy : sz);
         for (int c = threadIdx.x; c < ncol; c += kThreads) {
             const int k2 = static_cast<int>((static_cast<float>(c) + 0.5f) * inv_n1);
             const int k1 = c - k2 * n1;
             const int c1 = b1 + k1, c2 = b2 + k2;
-            const float uc = J.ou + J.m00 * c1 + J.m01 * c2;
-            const float vc = J.ov + J.m10 * c1 + J.m11 * c2;
-            const bool near = fabsf(uc - fminf(fmaxf(uc, static_cast<float>(u0)), static_cast<float>(u1))) <= J.hu &&
-                              fabsf(vc - fminf(fmaxf(vc, static_cast<float>(v0)), static_cast<float>(v1))) <= J.hv;
-            const float gd = J.alpha + J.beta1 * c1 + J.beta2 * c2;
+            const float uc = ou + m00 * c1 + m01 * c2;
+            const float vc = ov + m10 * c1 + m11 * c2;
+            const bool near = fabsf(uc - fminf(fmaxf(uc, fu0), fu1)) <= hu && fabsf(vc - fminf(fmaxf(vc, fv0), fv1)) <= hv;
+            const float gd = alpha + beta1 * c1 + beta2 * c2;
             int lo = 0, top = -1;  // levels lo .. top may be read
             if (near && fabsf(gd) < 16384.0f && static_cast<unsigned>(c1) < static_cast<unsigned>(d1) &&
                 static_cast<unsigned>(c2) < static_cast<unsigned>(d2)) {
@@ -182,39 +186,42 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
                 top = min(static_cast<int>(floorf(gd + sm)) + 1, dd - 1);
             }
             sCol[c] = lo;
-            const int64_t base = (D == 0 ? 0 : c1) + static_cast<int64_t>(J.dims[0]) *
-                                 ((D == 1 ? 0 : (E1 == 1 ? c1 : c2)) + static_cast<int64_t>(J.dims[1]) * (D == 2 ? 0 : c2));
-            const int64_t step = D == 0 ? 1 : (D == 1 ? static_cast<int64_t>(J.dims[0])
-                                                      : static_cast<int64_t>(J.dims[0]) * J.dims[1]);
+            const int64_t base = c1 * st1 + c2 * st2;
             for (int lev = 0; lev < L; ++lev) {
                 const int g = lo + lev;
-                sAB[c * L + lev] = (g >= 0 && g <= top) ? collapse_voxel<K, VT, WT>(J.rec, base + g * step, wt)
+                sAB[c * L + lev] = (g >= 0 && g <= top) ? collapse_voxel<K, VT, WT>(rec, base + g * std_, wt)
                                                         : make_float2(0.0f, 0.0f);
             }
         }
         __syncthreads();
     }
-    // (B) pixels: a warp walks the 32 pixels of a tile row; int32 steps from the tile origin
+    // (B) pixels: a warp walks the 32 pixels of a tile row; int32 steps from the tile origin.
+    // Everything the loop reads besides the slots sits in registers: the output
+    // stores go through generic pointers, which could otherwise alias the
+    // shared-memory copies and force reloads.
     const int A1 = static_cast<int>(J.a[E1]), B1 = static_cast<int>(J.b[E1]);
     const int A2 = static_cast<int>(J.a[E2]), B2 = static_cast<int>(J.b[E2]);
     const int Ad = static_cast<int>(J.a[D]), Bd = static_cast<int>(J.b[D]);
+    const int R1 = T.R1 + lane * A1, R2 = T.R2 + lane * A2, Rd = T.Rd + lane * Ad;
+    const int O1 = T.O1, O2 = T.O2, Od = T.Od;
+    float* const out = J.out;
+    uint32_t* const mask = J.mask;
+    const int64_t width = J.width, mstride = J.mask_stride;
+    const float unassigned = J.unassigned;
+    const int u = u0 + lane;
+    const bool active = u <= u1;
     for (int r = warp; r < TH; r += kThreads / 32) {
         const int v = v0 + r;
         if (v > v1) break;  // warp-uniform
-        const int u = u0 + lane;
-        const bool active = u <= u1;
         float num = 0.0f, den = 0.0f;
         if (active) {
             if (direct) {
                 direct_pixel<K, VT, WT>(J, u, v, num, den);
             } else if (!empty) {
-                const int du = u - u0, dv = v - v0;
-                const int r1 = T.R1 + du * A1 + dv * B1;
-                const int r2 = T.R2 + du * A2 + dv * B2;
-                const int rd = T.Rd + du * Ad + dv * Bd;
+                const int r1 = R1 + r * B1, r2 = R2 + r * B2, rd = Rd + r * Bd;
                 // k1 in [0, n1 - 2], k2 in [0, n2 - 2] by construction of the box
-                const int c00 = (r1 >> kFixBits) + T.O1 + n1 * ((r2 >> kFixBits) + T.O2);
-                const int fd = (rd >> kFixBits) + T.Od;
+                const int c00 = (r1 >> kFixBits) + O1 + n1 * ((r2 >> kFixBits) + O2);
+                const int fd = (rd >> kFixBits) + Od;
                 const float p1 = static_cast<float>(r1 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
                 const float p2 = static_cast<float>(r2 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
                 const float pd = static_cast<float>(rd & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
@@ -235,10 +242,10 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
                     }
                 }
             }
-            J.out[static_cast<int64_t>(v) * J.width + u] = den > 0.0f ? num / den : J.unassigned;
+            out[v * width + u] = den > 0.0f ? num / den : unassigned;
         }
         const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);
-        if (lane == 0) J.mask[static_cast<int64_t>(v) * J.mask_stride + u0 / 32] = bits;
+        if (lane == 0) mask[v * mstride + u0 / 32] = bits;
     }
 }
 
