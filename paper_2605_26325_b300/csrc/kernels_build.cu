@@ -6,11 +6,11 @@
 // Pipeline per chunk of frames:
 //   count  -- each CTA takes a 32 x 32 pixel tile of one frame and sums its
 //             pixels per voxel in a shared-memory hash table; every (voxel,
-//             tile) pair then bumps that voxel's counter once;
+//             tile) pair bumps that voxel's counter once and is appended to a
+//             pair list;
 //   scan   -- exclusive prefix sum of the counters (kernels.cu);
-//   place  -- the same tiles again; every (voxel, tile) pair writes one entry
-//             (frame id, npix, sum) into the voxel's range and returns the
-//             counter to zero;
+//   place  -- every pair writes its entry (frame id, npix, sum) into its
+//             voxel's range and returns the counter towards zero;
 //   finalize -- one thread per voxel groups its entries by frame id (a frame
 //             split across tiles has several), appends the new samples after
 //             the stored ones (their ids are all lower) and applies the
@@ -124,27 +124,86 @@ __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int 
     __syncthreads();
 }
 
-template <bool kPlace>
-__global__ void __launch_bounds__(kThreads) k_scatter_tiles(const __grid_constant__ ScatterArgs A, int32_t* count,
-                                                            const int32_t* __restrict__ offsets,
-                                                            unsigned long long* __restrict__ entries) {
+// A (voxel, tile) pair in the list: x = voxel, (w:z) = entry
+// (frame id << 48 | npix << 32 | sum).
+__global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constant__ ScatterArgs A,
+                                                            int32_t* __restrict__ count, uint4* __restrict__ pairs,
+                                                            unsigned long long* __restrict__ n_pairs) {
+    constexpr int kIters = kHash / kThreads, kWarps = kThreads / 32;
+    static_assert(kIters * kWarps == 64, "the range scan covers 64 counts with one warp");
     __shared__ int keys[kHash];
     __shared__ unsigned npx[kHash];
     __shared__ unsigned sums[kHash];
+    __shared__ int s_cnt[kIters * kWarps];  // occupied slots per (iteration, warp), then their offsets
+    __shared__ unsigned long long s_base;
     const int tiles_x = (A.width + kTile - 1) / kTile;
     const int f = blockIdx.y;
     const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
     aggregate_tile(A, f, u0, v0, keys, npx, sums);
-    const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
-    for (int i = threadIdx.x; i < kHash; i += kThreads) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    // pass 1: count the pairs, bump each voxel's counter once per pair
+    for (int it = 0; it < kIters; ++it) {
+        const int i = it * kThreads + threadIdx.x;
         const int vi = keys[i];
-        if (vi == kEmptyKey) continue;
-        if (kPlace) {
-            const int pos = offsets[vi] + atomicSub(count + vi, 1) - 1;
-            entries[pos] = fid | (static_cast<unsigned long long>(npx[i]) << 32) | sums[i];
-        } else {
-            atomicAdd(count + vi, 1);
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, vi != kEmptyKey);
+        if (vi != kEmptyKey) atomicAdd(count + vi, 1);
+        if (lane == 0) s_cnt[it * kWarps + warp] = __popc(bal);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        // exclusive scan of the kIters * kWarps (<= 64) counts, reserve the block's range
+        const int a = s_cnt[threadIdx.x], b = s_cnt[32 + threadIdx.x];
+        int ia = a, ib = b;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int ya = __shfl_up_sync(0xFFFFFFFFu, ia, o), yb = __shfl_up_sync(0xFFFFFFFFu, ib, o);
+            if (lane >= o) ia += ya, ib += yb;
         }
+        const int tot_a = __shfl_sync(0xFFFFFFFFu, ia, 31);
+        s_cnt[threadIdx.x] = ia - a;
+        s_cnt[32 + threadIdx.x] = tot_a + ib - b;
+        if (threadIdx.x == 31) s_base = atomicAdd(n_pairs, static_cast<unsigned long long>(tot_a + ib));
+    }
+    __syncthreads();
+    // pass 2: write the pairs, each warp into its reserved run
+    const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
+    const unsigned long long base = s_base;
+    for (int it = 0; it < kIters; ++it) {
+        const int i = it * kThreads + threadIdx.x;
+        const int vi = keys[i];
+        const unsigned bal = __ballot_sync(0xFFFFFFFFu, vi != kEmptyKey);
+        if (vi != kEmptyKey) {
+            const unsigned long long e = fid | (static_cast<unsigned long long>(npx[i]) << 32) | sums[i];
+            const int pos = s_cnt[it * kWarps + warp] + __popc(bal & ((1u << lane) - 1u));
+            pairs[base + pos] = make_uint4(static_cast<unsigned>(vi), 0u, static_cast<unsigned>(e),
+                                           static_cast<unsigned>(e >> 32));
+        }
+    }
+}
+
+constexpr int kPlaceUnroll = 4;  // pairs in flight per thread
+
+__global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__ pairs,
+                                                       const unsigned long long* __restrict__ n_pairs,
+                                                       int32_t* __restrict__ count, const int32_t* __restrict__ offsets,
+                                                       unsigned long long* __restrict__ entries) {
+    const int64_t n = static_cast<int64_t>(*n_pairs);
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    for (int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n;
+         i0 += stride * kPlaceUnroll) {
+        uint4 p[kPlaceUnroll];
+        int pos[kPlaceUnroll];
+#pragma unroll
+        for (int j = 0; j < kPlaceUnroll; ++j) {
+            const int64_t i = i0 + j * stride;
+            p[j] = i < n ? __ldg(pairs + i) : make_uint4(0, 0, 0, 0);
+        }
+#pragma unroll
+        for (int j = 0; j < kPlaceUnroll; ++j)
+            pos[j] = i0 + j * stride < n ? offsets[p[j].x] + atomicSub(count + p[j].x, 1) - 1 : -1;
+#pragma unroll
+        for (int j = 0; j < kPlaceUnroll; ++j)
+            if (pos[j] >= 0) entries[pos[j]] = (static_cast<unsigned long long>(p[j].w) << 32) | p[j].z;
     }
 }
 
@@ -350,16 +409,16 @@ dim3 scatter_grid(const ScatterArgs& a) {
 
 }  // namespace
 
-cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, cudaStream_t st) {
+cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, uint4* pairs, unsigned long long* n_pairs,
+                                 cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    k_scatter_tiles<false><<<scatter_grid(a), kThreads, 0, st>>>(a, count, nullptr, nullptr);
+    k_scatter_count<<<scatter_grid(a), kThreads, 0, st>>>(a, count, pairs, n_pairs);
     return cudaPeekAtLastError();
 }
 
-cudaError_t launch_scatter_place(const ScatterArgs& a, int32_t* count, const int32_t* offsets,
-                                 unsigned long long* entries, cudaStream_t st) {
-    if (a.n <= 0) return cudaSuccess;
-    k_scatter_tiles<true><<<scatter_grid(a), kThreads, 0, st>>>(a, count, offsets, entries);
+cudaError_t launch_scatter_place(const uint4* pairs, const unsigned long long* n_pairs, int32_t* count,
+                                 const int32_t* offsets, unsigned long long* entries, cudaStream_t st) {
+    k_scatter_place<<<148 * 16, 256, 0, st>>>(pairs, n_pairs, count, offsets, entries);
     return cudaPeekAtLastError();
 }
 
