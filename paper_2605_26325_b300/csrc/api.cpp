@@ -262,6 +262,7 @@ struct dare_session_s {
     std::vector<double> frames_host;       // n_frames x 9
     int32_t n_frames = 0;
     int64_t version = 0;
+    bool fresh = true;                     // no sample stored since create / reset: finalize skips reading records
     int64_t volume_bytes = 0;
     void* ws = nullptr;
     size_t ws_bytes = 0;
@@ -927,9 +928,11 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
             CUDA_TRY(launch_scatter_place(pairs, n_pairs, s->count, offsets, entries, st));
         }
         {
+            const int fresh = s->fresh ? 1 : 0;
+            s->fresh = false;  // from here on the records may hold samples
             KernelScope ks("finalize", st, 1);
             CUDA_TRY(launch_finalize(offsets, entries, s->n_vox, s->rec, s->npix, s->ssum, s->scnt, s->K, s->dtype,
-                                     s->overflow_dev, st));
+                                     fresh, s->overflow_dev, st));
         }
     }
     rc = session_end(s, st);
@@ -1099,6 +1102,7 @@ dare_status dare_session_reset(dare_session s, void* stream) {
     s->frames_host.clear();
     s->n_frames = 0;
     s->version = 0;
+    s->fresh = true;
     return DARE_OK;
 }
 
@@ -1267,6 +1271,7 @@ dare_status dare_session_load(const dare_session_config* cfg, const char* path, 
     s->frames_host = std::move(frames);
     s->n_frames = hd.n_frames;
     s->version = hd.version;
+    s->fresh = false;
     *out = s;
     return DARE_OK;
 }

@@ -88,8 +88,9 @@ cudaError_t launch_scatter_place(const uint4* pairs, const unsigned long long* n
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
                                   int64_t block_sums_len, cudaStream_t st);
 int64_t scan_block_sums_needed(int64_t n);
+// fresh != 0: the volume holds no sample (created or reset since): stored records are not read
 cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
-                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
+                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int fresh,
                             unsigned long long* overflow, cudaStream_t st);
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
                                   cudaStream_t st);

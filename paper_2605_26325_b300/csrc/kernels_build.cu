@@ -313,68 +313,99 @@ __device__ __noinline__ bool merge_general(const unsigned long long* entries, in
     return over;
 }
 
-constexpr int kRegEntries = 16;  // entries a voxel keeps in registers on the fast path
-
+// Fast path: new samples (ascending frame id) go after the stored ones; each
+// pass re-reads the voxel's entries (from L1) and takes the next frame.
+// Returns false when more than K samples exist (the capacity rule needs the
+// general merge).
 template <int K, typename VT>
+__device__ __forceinline__ bool append_in_order(const unsigned long long* __restrict__ entries, int s, int e,
+                                                int m_old, uint16_t* ids, VT* vals, uint16_t* np) {
+    int m = m_old, last = -1;
+    for (;;) {
+        int next = 0xFFFF, cnt = 0, sum = 0;
+        for (int i = s; i < e; ++i) {
+            const unsigned long long x = __ldg(entries + i);
+            const int f = ent_frame(x);
+            const bool lower = f > last && f < next;
+            const bool same = f == next;
+            cnt = lower ? ent_npix(x) : (same ? cnt + ent_npix(x) : cnt);
+            sum = lower ? ent_sum(x) : (same ? sum + ent_sum(x) : sum);
+            next = lower ? f : next;
+        }
+        if (next == 0xFFFF) return true;
+        if (m == K) return false;  // more than K samples: capacity rule
+        ids[m] = static_cast<uint16_t>(next);
+        vals[m] = round_store<VT>(sum, cnt);
+        np[m] = static_cast<uint16_t>(cnt < 65535 ? cnt : 65535);
+        ++m;
+        last = next;
+    }
+}
+
+// kFresh: the volume holds no sample at all (just created or reset), so the
+// stored records are known to be empty and are not read.
+template <int K, typename VT, bool kFresh>
 __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ offsets,
                                                   const unsigned long long* __restrict__ entries, int64_t n_vox,
                                                   uint8_t* __restrict__ rec, uint16_t* __restrict__ npix,
                                                   uint32_t* __restrict__ scal_sum, uint32_t* __restrict__ scal_cnt,
                                                   unsigned long long* overflow) {
     constexpr int RB = (2 * K + K * static_cast<int>(sizeof(VT)) + 15) / 16 * 16;
+    // each thread edits its voxel's record and npix row in shared memory and
+    // writes them back whole (full sectors, vector stores)
+    __shared__ uint4 s_rec[256 * RB / 16];
+    __shared__ uint2 s_np[256 * K / 4];
+    uint4* my_rec = s_rec + threadIdx.x * (RB / 16);
+    uint2* my_np = s_np + threadIdx.x * (K / 4);
     for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n_vox;
          v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int s = offsets[v], e = offsets[v + 1];
         if (s == e) continue;
-        uint16_t* ids = reinterpret_cast<uint16_t*>(rec + v * RB);
-        VT* vals = reinterpret_cast<VT*>(rec + v * RB + 2 * K);
-        uint16_t* np = npix + v * K;
-        int m_old = 0;
-        while (m_old < K && ids[m_old] != DARE_EMPTY_FRAME) ++m_old;
-        const int n = e - s;
-        uint32_t tot_sum = 0, tot_cnt = 0;
-        bool over = false;
-        bool done = false;
-        if (n <= kRegEntries) {
-            unsigned long long ent[kRegEntries];
+        uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
+        uint2* g_np = reinterpret_cast<uint2*>(npix + v * K);
+        if (kFresh) {
+            // empty record: ids 0xFFFF, values and npix 0
 #pragma unroll
-            for (int i = 0; i < kRegEntries; ++i) {
-                ent[i] = i < n ? __ldg(entries + s + i) : (0xFFFFull << 48);
-                tot_sum += static_cast<uint32_t>(ent_sum(ent[i]));
-                tot_cnt += static_cast<uint32_t>(ent_npix(ent[i]));
-            }
-            // fast path: new samples (ascending frame id) go after the stored ones
-            int m = m_old, last = -1;
-            done = true;
-            for (;;) {
-                int next = 0xFFFF, cnt = 0, sum = 0;
+            for (int i = 0; i < RB / 16; ++i) {
+                uint4 q = make_uint4(0u, 0u, 0u, 0u);
 #pragma unroll
-                for (int i = 0; i < kRegEntries; ++i) {
-                    const int f = ent_frame(ent[i]);
-                    const bool lower = f > last && f < next;
-                    const bool same = f == next;
-                    cnt = lower ? ent_npix(ent[i]) : (same ? cnt + ent_npix(ent[i]) : cnt);
-                    sum = lower ? ent_sum(ent[i]) : (same ? sum + ent_sum(ent[i]) : sum);
-                    next = lower ? f : next;
+                for (int w = 0; w < 4; ++w) {
+                    const int b = 16 * i + 4 * w;  // byte offset of this word
+                    uint32_t x = 0u;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h)
+                        if (b + 2 * h < 2 * K) x |= 0xFFFFu << (16 * h);
+                    (w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w) = x;
                 }
-                if (next == 0xFFFF) break;
-                if (m == K) {  // more than K samples: capacity rule
-                    done = false;
-                    break;
-                }
-                ids[m] = static_cast<uint16_t>(next);
-                vals[m] = round_store<VT>(sum, cnt);
-                np[m] = static_cast<uint16_t>(cnt < 65535 ? cnt : 65535);
-                ++m;
-                last = next;
+                my_rec[i] = q;
             }
+#pragma unroll
+            for (int i = 0; i < K / 4; ++i) my_np[i] = make_uint2(0u, 0u);
         } else {
-            for (int i = s; i < e; ++i) {
-                tot_sum += static_cast<uint32_t>(ent_sum(entries[i]));
-                tot_cnt += static_cast<uint32_t>(ent_npix(entries[i]));
-            }
+#pragma unroll
+            for (int i = 0; i < RB / 16; ++i) my_rec[i] = g_rec[i];
+#pragma unroll
+            for (int i = 0; i < K / 4; ++i) my_np[i] = g_np[i];
         }
-        if (!done) over = merge_general<K, VT>(entries, s, e, m_old, ids, vals, np);
+        uint16_t* ids = reinterpret_cast<uint16_t*>(my_rec);
+        VT* vals = reinterpret_cast<VT*>(reinterpret_cast<uint8_t*>(my_rec) + 2 * K);
+        uint16_t* np = reinterpret_cast<uint16_t*>(my_np);
+        int m_old = 0;
+        if (!kFresh)
+            while (m_old < K && ids[m_old] != DARE_EMPTY_FRAME) ++m_old;
+        uint32_t tot_sum = 0, tot_cnt = 0;
+        for (int i = s; i < e; ++i) {
+            const unsigned long long x = __ldg(entries + i);
+            tot_sum += static_cast<uint32_t>(ent_sum(x));
+            tot_cnt += static_cast<uint32_t>(ent_npix(x));
+        }
+        bool over = false;
+        if (!append_in_order<K, VT>(entries, s, e, m_old, ids, vals, np))
+            over = merge_general<K, VT>(entries, s, e, m_old, ids, vals, np);
+#pragma unroll
+        for (int i = 0; i < RB / 16; ++i) g_rec[i] = my_rec[i];
+#pragma unroll
+        for (int i = 0; i < K / 4; ++i) g_np[i] = my_np[i];
         if (scal_sum) {
             scal_sum[v] += tot_sum;
             scal_cnt[v] += tot_cnt;
@@ -383,23 +414,37 @@ __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ of
     }
 }
 
-template <int K>
-cudaError_t finalize_k(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
-                       uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, unsigned long long* ovf,
-                       cudaStream_t st) {
+template <int K, bool kFresh>
+cudaError_t finalize_kf(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
+                        uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, unsigned long long* ovf,
+                        cudaStream_t st) {
     const int threads = 256;
     const int64_t want = (n_vox + threads - 1) / threads;
     const int blocks = static_cast<int>(want < 148 * 64 ? want : 148 * 64);
     switch (dtype) {
-    case DARE_U8: k_finalize<K, uint8_t><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
-    case DARE_F16: k_finalize<K, __half><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
-    case DARE_BF16:
-        k_finalize<K, __nv_bfloat16><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+    case DARE_U8:
+        k_finalize<K, uint8_t, kFresh><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
-    case DARE_F32: k_finalize<K, float><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf); break;
+    case DARE_F16:
+        k_finalize<K, __half, kFresh><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        break;
+    case DARE_BF16:
+        k_finalize<K, __nv_bfloat16, kFresh><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        break;
+    case DARE_F32:
+        k_finalize<K, float, kFresh><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        break;
     default: return cudaErrorInvalidValue;
     }
     return cudaPeekAtLastError();
+}
+
+template <int K>
+cudaError_t finalize_k(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
+                       uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int fresh, unsigned long long* ovf,
+                       cudaStream_t st) {
+    return fresh ? finalize_kf<K, true>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st)
+                 : finalize_kf<K, false>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
 }
 
 dim3 scatter_grid(const ScatterArgs& a) {
@@ -423,13 +468,13 @@ cudaError_t launch_scatter_place(const uint4* pairs, const unsigned long long* n
 }
 
 cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
-                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
+                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int fresh,
                             unsigned long long* overflow, cudaStream_t st) {
     switch (K) {
-    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
-    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
-    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
-    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, overflow, st);
+    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, fresh, overflow, st);
+    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, fresh, overflow, st);
+    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, fresh, overflow, st);
+    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, fresh, overflow, st);
     }
     return cudaErrorInvalidValue;
 }
