@@ -852,7 +852,10 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
     if (int64_t(s->n_frames) + n > s->cfg.max_frames)
         return fail(DARE_E_CAPACITY, "%d frames + %d new exceed max_frames %d", s->n_frames, n, s->cfg.max_frames);
     const int64_t npx = int64_t(width) * height;
-    if (npx > kMaxPixelsPerChunk) return fail(DARE_E_INVALID, "frame too large");
+    // pair slots of a frame: one per pixel of its whole 32 x 32 tiles
+    const int64_t tiles_pf = int64_t((width + kScatterTile - 1) / kScatterTile) * ((height + kScatterTile - 1) / kScatterTile);
+    const int64_t slots_pf = tiles_pf * kScatterTile * kScatterTile;
+    if (slots_pf > kMaxPixelsPerChunk) return fail(DARE_E_INVALID, "frame too large");
     const double* V = s->cfg.grid.vol_to_world;
     const double h = s->cfg.grid.spacing_mm;
     std::vector<int64_t> aff(size_t(n) * 9);
@@ -868,17 +871,17 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
     DeviceGuard dg(s->cfg.device);
     if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int32_t chunk = static_cast<int32_t>(std::min<int64_t>(65535, std::max<int64_t>(1, kMaxPixelsPerChunk / npx)));
+    const int32_t chunk = static_cast<int32_t>(std::min<int64_t>(65535, std::max<int64_t>(1, kMaxPixelsPerChunk / slots_pf)));
     const int32_t n_chunk = std::min(n, chunk);
-    // workspace: offsets (n_vox + 1), scan block sums, entries, (voxel, entry) pairs,
-    // pair counter, affines; entries and pairs: at most one per pixel
+    // workspace: offsets (n_vox + 1), scan block sums, entries (at most one per pixel),
+    // (voxel, entry) pairs (one slot per pixel of the frame tiles), pairs per tile, affines
     const int64_t nbs = scan_block_sums_needed(s->n_vox);
     const size_t o_off = 0;
     const size_t o_bs = align_up(o_off + size_t(s->n_vox + 1) * 4, 256);
     const size_t o_ent = align_up(o_bs + size_t(nbs) * 4, 256);
     const size_t o_pairs = align_up(o_ent + size_t(n_chunk) * npx * 8, 256);
-    const size_t o_np = align_up(o_pairs + size_t(n_chunk) * npx * 16, 256);
-    const size_t o_aff = align_up(o_np + 8, 256);
+    const size_t o_np = align_up(o_pairs + size_t(n_chunk) * slots_pf * 16, 256);
+    const size_t o_aff = align_up(o_np + size_t(n_chunk) * tiles_pf * 4, 256);
     const size_t ws_need = align_up(o_aff + size_t(n) * 9 * 8, 256);
     dare_status rc = session_begin(s, st);
     if (rc != DARE_OK) return rc;
@@ -891,7 +894,7 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
     int32_t* bsums = reinterpret_cast<int32_t*>(ws + o_bs);
     auto* entries = reinterpret_cast<unsigned long long*>(ws + o_ent);
     auto* pairs = reinterpret_cast<uint4*>(ws + o_pairs);
-    auto* n_pairs = reinterpret_cast<unsigned long long*>(ws + o_np);
+    auto* n_pairs = reinterpret_cast<int32_t*>(ws + o_np);
     int64_t* aff_dev = reinterpret_cast<int64_t*>(ws + o_aff);
     uint8_t* pin = static_cast<uint8_t*>(s->pinned[0]);
     std::memcpy(pin, aff.data(), aff.size() * 8);
@@ -914,7 +917,6 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
         for (int32_t f = c0; f < c0 + nc; ++f)
             for (int k = 3; k < 9; ++k)
                 if (std::llabs(aff[9 * size_t(f) + k]) >= (int64_t(1) << 25)) a.small_steps = 0;
-        CUDA_TRY(cudaMemsetAsync(n_pairs, 0, 8, st));
         {
             KernelScope ks("scatter_count", st, 1);
             CUDA_TRY(launch_scatter_count(a, s->count, pairs, n_pairs, st));
@@ -925,7 +927,7 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
         }
         {
             KernelScope ks("scatter_place", st, 1);
-            CUDA_TRY(launch_scatter_place(pairs, n_pairs, s->count, offsets, entries, st));
+            CUDA_TRY(launch_scatter_place(a, pairs, n_pairs, s->count, offsets, entries, st));
         }
         {
             const int fresh = s->fresh ? 1 : 0;

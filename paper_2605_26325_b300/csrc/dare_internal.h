@@ -18,7 +18,8 @@ namespace dare {
 
 constexpr int kFixBits = DARE_FIX_BITS;
 constexpr int64_t kFixOne = int64_t(1) << kFixBits;
-constexpr int kMaxPixelsPerChunk = 1 << 28;  // pixels of one scatter pass (at most one 8-byte entry and one 16-byte pair per pixel)
+constexpr int kMaxPixelsPerChunk = 1 << 28;  // pixels of one scatter pass (one 8-byte entry and one 16-byte pair per pixel at most)
+constexpr int kScatterTile = 32;              // frame tiles of the scatter passes: 32 x 32 pixels
 
 inline int value_bytes(int dtype) { return dtype == DARE_U8 ? 1 : (dtype == DARE_F32 ? 4 : 2); }
 inline int record_bytes(int K, int dtype) { return (2 * K + K * value_bytes(dtype) + 15) / 16 * 16; }
@@ -79,11 +80,11 @@ cudaError_t launch_weight_tables(const TableJob* jobs_dev, const TableJob* one_j
                                  const TableParams& p, cudaStream_t st);
 cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int max_w,
                                  int max_h, int K, int dtype, int half_weights, cudaStream_t st);
-// count: per-voxel counters (zero on entry; place returns them to zero); pairs: room for one
-// 16-byte (voxel, entry) pair per pixel; n_pairs: zero on entry, the pairs written
-cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, uint4* pairs, unsigned long long* n_pairs,
+// count: per-voxel counters (zero on entry; place returns them to zero); pairs: kTile^2 16-byte
+// (voxel, entry) pairs per 32 x 32 frame tile; n_pairs: one int per tile
+cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, uint4* pairs, int32_t* n_pairs,
                                  cudaStream_t st);
-cudaError_t launch_scatter_place(const uint4* pairs, const unsigned long long* n_pairs, int32_t* count,
+cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const int32_t* n_pairs, int32_t* count,
                                  const int32_t* offsets, unsigned long long* entries, cudaStream_t st);
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
                                   int64_t block_sums_len, cudaStream_t st);

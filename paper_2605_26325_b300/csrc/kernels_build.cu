@@ -6,8 +6,8 @@
 // Pipeline per chunk of frames:
 //   count  -- each CTA takes a 32 x 32 pixel tile of one frame and sums its
 //             pixels per voxel in a shared-memory hash table; every (voxel,
-//             tile) pair bumps that voxel's counter once and is appended to a
-//             pair list;
+//             tile) pair bumps that voxel's counter once and goes to the
+//             tile's region of a pair list;
 //   scan   -- exclusive prefix sum of the counters (kernels.cu);
 //   place  -- every pair writes its entry (frame id, npix, sum) into its
 //             voxel's range and returns the counter towards zero;
@@ -26,7 +26,7 @@
 namespace dare {
 namespace {
 
-constexpr int kTile = 32;             // frame tile: 32 x 32 pixels
+constexpr int kTile = kScatterTile;   // frame tile: 32 x 32 pixels
 constexpr int kThreads = 256;         // 4 pixels per thread
 constexpr int kHash = 2048;           // >= 2 x pixels per tile: never full
 constexpr int kEmptyKey = -1;
@@ -126,16 +126,18 @@ __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int 
 
 // A (voxel, tile) pair in the list: x = voxel, (w:z) = entry
 // (frame id << 48 | npix << 32 | sum).
+// A (voxel, tile) pair: x = voxel, (w:z) = entry (frame id << 48 | npix << 32
+// | sum).  Tile t owns pairs[t * kTile^2, ...) (a tile has at most one pair per
+// pixel) and n_pairs[t] says how many it wrote.
 __global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constant__ ScatterArgs A,
                                                             int32_t* __restrict__ count, uint4* __restrict__ pairs,
-                                                            unsigned long long* __restrict__ n_pairs) {
+                                                            int32_t* __restrict__ n_pairs) {
     constexpr int kIters = kHash / kThreads, kWarps = kThreads / 32;
-    static_assert(kIters * kWarps == 64, "the range scan covers 64 counts with one warp");
+    static_assert(kIters * kWarps == 64, "the run scan covers 64 counts with one warp");
     __shared__ int keys[kHash];
     __shared__ unsigned npx[kHash];
     __shared__ unsigned sums[kHash];
     __shared__ int s_cnt[kIters * kWarps];  // occupied slots per (iteration, warp), then their offsets
-    __shared__ unsigned long long s_base;
     const int tiles_x = (A.width + kTile - 1) / kTile;
     const int f = blockIdx.y;
     const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
@@ -150,8 +152,9 @@ __global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constan
         if (lane == 0) s_cnt[it * kWarps + warp] = __popc(bal);
     }
     __syncthreads();
+    const int64_t tile = static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
     if (threadIdx.x < 32) {
-        // exclusive scan of the kIters * kWarps (<= 64) counts, reserve the block's range
+        // exclusive scan of the kIters * kWarps counts: each warp's run in the tile's region
         const int a = s_cnt[threadIdx.x], b = s_cnt[32 + threadIdx.x];
         int ia = a, ib = b;
 #pragma unroll
@@ -162,12 +165,12 @@ __global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constan
         const int tot_a = __shfl_sync(0xFFFFFFFFu, ia, 31);
         s_cnt[threadIdx.x] = ia - a;
         s_cnt[32 + threadIdx.x] = tot_a + ib - b;
-        if (threadIdx.x == 31) s_base = atomicAdd(n_pairs, static_cast<unsigned long long>(tot_a + ib));
+        if (threadIdx.x == 31) n_pairs[tile] = tot_a + ib;
     }
     __syncthreads();
-    // pass 2: write the pairs, each warp into its reserved run
+    // pass 2: write the pairs, each warp into its run
     const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
-    const unsigned long long base = s_base;
+    uint4* out = pairs + tile * (kTile * kTile);
     for (int it = 0; it < kIters; ++it) {
         const int i = it * kThreads + threadIdx.x;
         const int vi = keys[i];
@@ -175,36 +178,36 @@ __global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constan
         if (vi != kEmptyKey) {
             const unsigned long long e = fid | (static_cast<unsigned long long>(npx[i]) << 32) | sums[i];
             const int pos = s_cnt[it * kWarps + warp] + __popc(bal & ((1u << lane) - 1u));
-            pairs[base + pos] = make_uint4(static_cast<unsigned>(vi), 0u, static_cast<unsigned>(e),
-                                           static_cast<unsigned>(e >> 32));
+            out[pos] = make_uint4(static_cast<unsigned>(vi), 0u, static_cast<unsigned>(e), static_cast<unsigned>(e >> 32));
         }
     }
 }
 
-constexpr int kPlaceUnroll = 4;  // pairs in flight per thread
-
+// One CTA per tile region: each pair takes its slot from the voxel's counter
+// (returning it towards zero) and writes its entry into the voxel's range.
 __global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__ pairs,
-                                                       const unsigned long long* __restrict__ n_pairs,
+                                                       const int32_t* __restrict__ n_pairs,
                                                        int32_t* __restrict__ count, const int32_t* __restrict__ offsets,
                                                        unsigned long long* __restrict__ entries) {
-    const int64_t n = static_cast<int64_t>(*n_pairs);
-    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-    for (int64_t i0 = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i0 < n;
-         i0 += stride * kPlaceUnroll) {
-        uint4 p[kPlaceUnroll];
-        int pos[kPlaceUnroll];
+    const int64_t tile = blockIdx.x;
+    const int n = n_pairs[tile];
+    const uint4* in = pairs + tile * (kTile * kTile);
+    constexpr int kU = kTile * kTile / 256;
+    uint4 p[kU];
 #pragma unroll
-        for (int j = 0; j < kPlaceUnroll; ++j) {
-            const int64_t i = i0 + j * stride;
-            p[j] = i < n ? __ldg(pairs + i) : make_uint4(0, 0, 0, 0);
-        }
-#pragma unroll
-        for (int j = 0; j < kPlaceUnroll; ++j)
-            pos[j] = i0 + j * stride < n ? offsets[p[j].x] + atomicSub(count + p[j].x, 1) - 1 : -1;
-#pragma unroll
-        for (int j = 0; j < kPlaceUnroll; ++j)
-            if (pos[j] >= 0) entries[pos[j]] = (static_cast<unsigned long long>(p[j].w) << 32) | p[j].z;
+    for (int j = 0; j < kU; ++j) {
+        const int i = threadIdx.x + 256 * j;
+        p[j] = i < n ? __ldg(in + i) : make_uint4(0, 0, 0, 0);
     }
+    int pos[kU];
+#pragma unroll
+    for (int j = 0; j < kU; ++j) {
+        const int i = threadIdx.x + 256 * j;
+        pos[j] = i < n ? offsets[p[j].x] + atomicSub(count + p[j].x, 1) - 1 : -1;
+    }
+#pragma unroll
+    for (int j = 0; j < kU; ++j)
+        if (pos[j] >= 0) entries[pos[j]] = (static_cast<unsigned long long>(p[j].w) << 32) | p[j].z;
 }
 
 // ------------------------------------------------------------------ finalize
@@ -454,16 +457,18 @@ dim3 scatter_grid(const ScatterArgs& a) {
 
 }  // namespace
 
-cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, uint4* pairs, unsigned long long* n_pairs,
+cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, uint4* pairs, int32_t* n_pairs,
                                  cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     k_scatter_count<<<scatter_grid(a), kThreads, 0, st>>>(a, count, pairs, n_pairs);
     return cudaPeekAtLastError();
 }
 
-cudaError_t launch_scatter_place(const uint4* pairs, const unsigned long long* n_pairs, int32_t* count,
+cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const int32_t* n_pairs, int32_t* count,
                                  const int32_t* offsets, unsigned long long* entries, cudaStream_t st) {
-    k_scatter_place<<<148 * 16, 256, 0, st>>>(pairs, n_pairs, count, offsets, entries);
+    if (a.n <= 0) return cudaSuccess;
+    const dim3 g = scatter_grid(a);
+    k_scatter_place<<<g.x * g.y, 256, 0, st>>>(pairs, n_pairs, count, offsets, entries);
     return cudaPeekAtLastError();
 }
 
