@@ -27,7 +27,7 @@ namespace dare {
 namespace {
 
 constexpr int kTile = kScatterTile;   // frame tile: 32 x 32 pixels
-constexpr int kThreads = 256;         // 4 pixels per thread
+constexpr int kThreads = 256;         // a 2 x 2 pixel block per thread
 constexpr int kHash = 2048;           // >= 2 x pixels per tile: never full
 constexpr int kEmptyKey = -1;
 
@@ -49,7 +49,7 @@ __device__ __forceinline__ void hash_add(int* keys, unsigned* npx, unsigned* sum
     for (;;) {  // at most kTile^2 distinct keys in kHash slots: terminates
         const int k0 = atomicCAS(keys + h, kEmptyKey, vi);
         if (k0 == kEmptyKey || k0 == vi) {
-            atomicAdd(npx + h, n);
+            atomicAdd(npx + h, n);  // two 32-bit adds: faster here than one 64-bit shared-memory add
             atomicAdd(sums + h, s);
             return;
         }
@@ -57,22 +57,23 @@ __device__ __forceinline__ void hash_add(int* keys, unsigned* npx, unsigned* sum
     }
 }
 
-// Shared-memory aggregation of one frame tile: keys[h] = voxel, npx/sums[h] = its pixel count and sum.
-// Each thread owns the horizontal pixel pair (2 tx, 2 tx + 1) of rows ty, ty + 16; a pair that lands
-// in one voxel is combined before touching shared memory.
+// Shared-memory aggregation of one frame tile: keys[h] = voxel, npx/sums[h] =
+// its pixel count and sum.  Each thread owns a 2 x 2 pixel block; pixels of the
+// block that land in one voxel are combined before touching shared memory.
 __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int u0, int v0, int* keys,
                                                unsigned* npx, unsigned* sums) {
+    // npx and sums are the two halves of one 8-byte-aligned buffer: cleared with 8-byte stores
+    unsigned long long* both = reinterpret_cast<unsigned long long*>(npx);
     for (int i = threadIdx.x; i < kHash; i += kThreads) {
         keys[i] = kEmptyKey;
-        npx[i] = 0u;
-        sums[i] = 0u;
+        both[i] = 0ull;
     }
     __shared__ int64_t aff[9];
     if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
     __syncthreads();
     const uint8_t* img = A.frames + static_cast<int64_t>(f) * A.width * A.height;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int u = u0 + 2 * tx;
+    const int u = u0 + 2 * tx, v = v0 + 2 * ty;
     // int32 steps from the tile origin when |A|, |B| < 2^25 (host flag), else int64 per pixel
     int base[3] = {0, 0, 0}, ra[3] = {0, 0, 0}, rb[3] = {0, 0, 0}, r0[3] = {0, 0, 0};
     if (A.small_steps) {
@@ -87,45 +88,44 @@ __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int 
             rb[a] = static_cast<int>(aff[6 + a]);
         }
     }
+    int vi[4];
+    unsigned val[4];
 #pragma unroll
-    for (int k = 0; k < 2; ++k) {
-        const int v = v0 + ty + 16 * k;
-        if (v >= A.height) continue;
-        int vi[2];
-        unsigned val[2];
+    for (int q = 0; q < 4; ++q) {
+        const int uu = u + (q & 1), vv = v + (q >> 1);
+        vi[q] = -1;
+        val[q] = 0;
+        if (uu >= A.width || vv >= A.height) continue;
+        if (A.small_steps) {
+            const int du = uu - u0, dv = vv - v0;
+            int c[3];
+            bool in = true;
 #pragma unroll
-        for (int e = 0; e < 2; ++e) {
-            vi[e] = -1;
-            val[e] = 0;
-            const int uu = u + e;
-            if (uu >= A.width) continue;
-            if (A.small_steps) {
-                const int du = uu - u0, dv = v - v0;
-                int c[3];
-                bool in = true;
-#pragma unroll
-                for (int a = 0; a < 3; ++a) {
-                    c[a] = base[a] + ((r0[a] + du * ra[a] + dv * rb[a]) >> kFixBits);
-                    in = in && c[a] >= 0 && c[a] < A.dims[a];
-                }
-                if (in) vi[e] = c[0] + A.dims[0] * (c[1] + A.dims[1] * c[2]);
-            } else {
-                vi[e] = scatter_voxel(aff, A.dims, uu, v);
+            for (int a = 0; a < 3; ++a) {
+                c[a] = base[a] + ((r0[a] + du * ra[a] + dv * rb[a]) >> kFixBits);
+                in = in && c[a] >= 0 && c[a] < A.dims[a];
             }
-            if (vi[e] >= 0) val[e] = __ldg(img + static_cast<int64_t>(v) * A.width + uu);
-        }
-        if (vi[0] >= 0 && vi[0] == vi[1]) {
-            hash_add(keys, npx, sums, vi[0], 2u, val[0] + val[1]);
+            if (in) vi[q] = c[0] + A.dims[0] * (c[1] + A.dims[1] * c[2]);
         } else {
-            if (vi[0] >= 0) hash_add(keys, npx, sums, vi[0], 1u, val[0]);
-            if (vi[1] >= 0) hash_add(keys, npx, sums, vi[1], 1u, val[1]);
+            vi[q] = scatter_voxel(aff, A.dims, uu, vv);
         }
+        if (vi[q] >= 0) val[q] = __ldg(img + static_cast<int64_t>(vv) * A.width + uu);
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        bool first = vi[j] >= 0;  // the first pixel of the block in its voxel adds the block's share
+#pragma unroll
+        for (int k = 0; k < j; ++k) first = first && vi[k] != vi[j];
+        if (!first) continue;
+        unsigned n = 1u, sm = val[j];
+#pragma unroll
+        for (int k = j + 1; k < 4; ++k)
+            if (vi[k] == vi[j]) ++n, sm += val[k];
+        hash_add(keys, npx, sums, vi[j], n, sm);
     }
     __syncthreads();
 }
 
-// A (voxel, tile) pair in the list: x = voxel, (w:z) = entry
-// (frame id << 48 | npix << 32 | sum).
 // A (voxel, tile) pair: x = voxel, (w:z) = entry (frame id << 48 | npix << 32
 // | sum).  Tile t owns pairs[t * kTile^2, ...) (a tile has at most one pair per
 // pixel) and n_pairs[t] says how many it wrote.
@@ -135,9 +135,10 @@ __global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constan
     constexpr int kIters = kHash / kThreads, kWarps = kThreads / 32;
     static_assert(kIters * kWarps == 64, "the run scan covers 64 counts with one warp");
     __shared__ int keys[kHash];
-    __shared__ unsigned npx[kHash];
-    __shared__ unsigned sums[kHash];
-    __shared__ int s_cnt[kIters * kWarps];  // occupied slots per (iteration, warp), then their offsets
+    __shared__ unsigned long long acc_buf[kHash];  // npx, then sums: kHash 32-bit counters each
+    __shared__ int s_cnt[kIters * kWarps];
+    unsigned* npx = reinterpret_cast<unsigned*>(acc_buf);
+    unsigned* sums = npx + kHash;  // occupied slots per (iteration, warp), then their offsets
     const int tiles_x = (A.width + kTile - 1) / kTile;
     const int f = blockIdx.y;
     const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
