@@ -306,6 +306,41 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
 dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream);
 
 /*
+ * Host-buffer forms of the two calls above, for callers whose recorded
+ * frames sit in host memory (Sec. 2.1: the recorded stream is processed on
+ * the GPU after acquisition) and whose preview images go back to the host for
+ * display (Sec. 4: reslicing runs on the physician's side).  Results are
+ * those of the device-buffer calls, bit for bit.  Page-locked host buffers (cudaHostAlloc / cudaHostRegister) let the
+ * copies overlap the kernels; pageable buffers work, with the copies staged
+ * by the driver.  Both calls are asynchronous: the caller keeps the host
+ * buffers valid and unchanged until `stream` reaches the end of the call.
+ *
+ * dare_build_volume_host: frames_host is n x height x width uint8 in host
+ * memory.  The frames go to the device in slices of slice_frames frames (0:
+ * about 32 MB a slice) through a two-slot device ring owned by the session;
+ * a slice's upload runs on the session's upload stream and overlaps the
+ * scatter of the previous slice.  Uploads do not wait for earlier work on
+ * `stream` (they only write the ring), so they may also overlap the
+ * downloads of a previous dare_reslice_batch_host.  Errors as
+ * dare_build_volume; DARE_E_INVALID for slice_frames < 0.
+ *
+ * dare_reslice_batch_host: out and mask of every request are host pointers
+ * (layouts as in dare_reslice).  The requests are resliced in groups of
+ * group_planes planes (0: about 128 MB of output a group) into a device
+ * staging buffer of 2 to 8 group slots (about 1 GB at most) owned by the
+ * first request's session; groups are resliced ahead while earlier ones are
+ * copied back on the session's download stream.  Consecutive requests whose host outputs (or masks) are
+ * adjacent in memory are copied back in one transfer.  `stream` waits for the
+ * last copy, so once it is synchronised every output is in host memory.
+ * Errors as dare_reslice_batch; DARE_E_INVALID for group_planes < 0.
+ */
+dare_status dare_build_volume_host(dare_session s, const uint8_t* frames_host, int32_t n, int32_t width,
+                                   int32_t height, const double px_mm[2], const double* image_to_world,
+                                   int32_t slice_frames, void* stream);
+dare_status dare_reslice_batch_host(const dare_reslice_req* reqs, int32_t n, const dare_params* params,
+                                    int32_t group_planes, void* stream);
+
+/*
  * Reslice plans: a fixed set of requests (sessions, output sizes and buffers)
  * prepared once and replayed many times, for a stream of batches whose poses
  * change (the batched workloads behind Sec. 3's timing and a serving loop).

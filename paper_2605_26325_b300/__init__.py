@@ -141,6 +141,10 @@ _SIGNATURES = {
                            _P(ctypes.c_double), _vp], ctypes.c_int),
     "dare_reslice": ([_vp, _P(dare_plane), _P(dare_params), _vp, _vp, _vp], ctypes.c_int),
     "dare_reslice_batch": ([_P(dare_reslice_req), ctypes.c_int32, _P(dare_params), _vp], ctypes.c_int),
+    "dare_build_volume_host": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_double),
+                                _P(ctypes.c_double), ctypes.c_int32, _vp], ctypes.c_int),
+    "dare_reslice_batch_host": ([_P(dare_reslice_req), ctypes.c_int32, _P(dare_params), ctypes.c_int32, _vp],
+                                ctypes.c_int),
     "dare_reslice_noalloc": ([_vp, _P(dare_plane), _P(dare_params), _vp, _vp, _vp], ctypes.c_int),
     "dare_plan_create": ([_P(dare_reslice_req), ctypes.c_int32, _P(dare_params), _vp, _P(_vp)], ctypes.c_int),
     "dare_plan_set_poses": ([_vp, _P(ctypes.c_double)], ctypes.c_int),
@@ -266,6 +270,24 @@ def _stream_ptr(stream):
     if isinstance(stream, int):
         return ctypes.c_void_p(stream)
     return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _host_ptr(t, name, shape=None):
+    """Host buffer (numpy array or CPU torch tensor, contiguous) -> pointer."""
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name} must be contiguous")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+        return ctypes.c_void_p(t.ctypes.data)
+    import torch
+    if not isinstance(t, torch.Tensor) or t.is_cuda:
+        raise TypeError(f"expected a host array or CPU tensor for {name}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _dev_ptr(t, dtype_name, shape=None):
@@ -425,6 +447,18 @@ class Session:
                                       poses.ctypes.data_as(_P(ctypes.c_double)), _stream_ptr(stream)),
               "dare_build_volume")
 
+    def build_host(self, frames_host, poses, px_mm, stream=None, slice_frames=0):
+        """Append frames held in host memory (uint8 (n, H, W) numpy array or CPU
+        tensor; page-locked memory lets the uploads overlap the scatter)."""
+        n, H, W = (int(x) for x in frames_host.shape)
+        if str(frames_host.dtype) not in ("uint8", "torch.uint8"):
+            raise TypeError("frames must be uint8")
+        poses = np.ascontiguousarray(np.asarray(poses, dtype=np.float64).reshape(n, 16))
+        px = (ctypes.c_double * 2)(float(px_mm[0]), float(px_mm[1]))
+        check(lib().dare_build_volume_host(self._h, _host_ptr(frames_host, "frames"), n, W, H, px,
+                                           poses.ctypes.data_as(_P(ctypes.c_double)), int(slice_frames),
+                                           _stream_ptr(stream)), "dare_build_volume_host")
+
     # ---- reslicing
     def reslice(self, image_to_world, out, mask, px_mm, params=None, stream=None):
         """Reslice one plane into out (H, W) float32 and mask (H, ceil(W/32)) int32 device tensors."""
@@ -450,16 +484,18 @@ class Session:
         return np.array(counts[:], dtype=np.int64)
 
 
-def make_requests(items):
-    """items: iterable of (session, image_to_world, out, mask, px_mm) -> ctypes array of dare_reslice_req."""
+def make_requests(items, host=False):
+    """items: iterable of (session, image_to_world, out, mask, px_mm) -> ctypes array of dare_reslice_req.
+    host: out / mask are host buffers (for reslice_batch_host), else CUDA tensors."""
     items = list(items)
     arr = (dare_reslice_req * len(items))()
+    ptr = _host_ptr if host else _dev_ptr
     for i, (s, T, out, mask, px) in enumerate(items):
         H, W = (int(x) for x in out.shape)
         arr[i].session = s.handle.value
         arr[i].plane = make_plane(W, H, px, T)
-        arr[i].out = _dev_ptr(out, "out").value
-        arr[i].mask = _dev_ptr(mask, "mask", (H, mask_words(W))).value
+        arr[i].out = ptr(out, "out").value
+        arr[i].mask = ptr(mask, "mask", (H, mask_words(W))).value
     return arr
 
 
@@ -470,6 +506,15 @@ def reslice_batch(requests, params=None, stream=None):
     p = params if params is not None else params_default()
     check(lib().dare_reslice_batch(requests, len(requests), ctypes.byref(p), _stream_ptr(stream)),
           "dare_reslice_batch")
+
+
+def reslice_batch_host(requests, params=None, stream=None, group_planes=0):
+    """Like reslice_batch, with host outputs: requests from make_requests(..., host=True)."""
+    if not isinstance(requests, ctypes.Array):
+        requests = make_requests(requests, host=True)
+    p = params if params is not None else params_default()
+    check(lib().dare_reslice_batch_host(requests, len(requests), ctypes.byref(p), int(group_planes),
+                                        _stream_ptr(stream)), "dare_reslice_batch_host")
 
 
 class Plan:

@@ -266,12 +266,29 @@ struct dare_session_s {
     int64_t volume_bytes = 0;
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    // pinned host staging: [0] frame affines / rotations of a build, [1] batch descriptors
-    void* pinned[2] = {nullptr, nullptr};
-    size_t pinned_bytes[2] = {0, 0};
-    cudaEvent_t pinned_ev[2] = {nullptr, nullptr};  // last copy out of each staging buffer
+    // pinned host staging: [0] frame affines / rotations of a build, [1..8] batch
+    // descriptors, used in turn so the host can run a few batches ahead
+    static constexpr int kPinSlots = 9;
+    void* pinned[kPinSlots] = {};
+    size_t pinned_bytes[kPinSlots] = {};
+    cudaEvent_t pinned_ev[kPinSlots] = {};  // last copy out of each staging buffer
+    int next_desc = 0;
     cudaEvent_t order_ev = nullptr;        // end of the session's last queued call
     cudaStream_t last_stream = nullptr;
+    // host-buffer calls: a two-slot upload ring (build) and a two-slot download
+    // staging buffer (reslice), each with its own copy stream and slot events
+    uint8_t* ring = nullptr;
+    size_t ring_slot = 0;
+    int ring_n = 0;
+    static constexpr int kStageSlots = 8;  // download staging: up to 8 slots, about 1 GB in all
+    uint8_t* stage = nullptr;
+    size_t stage_slot = 0;
+    int stage_n = 0;
+    cudaStream_t up_st = nullptr, down_st = nullptr;
+    cudaEvent_t ring_free[2] = {nullptr, nullptr};   // last scatter count that read the slot
+    cudaEvent_t ring_full[2] = {nullptr, nullptr};   // upload into the slot done
+    cudaEvent_t stage_free[kStageSlots] = {};        // download out of the slot done
+    cudaEvent_t stage_full[kStageSlots] = {};        // reslices into the slot done
     std::vector<std::pair<void*, size_t>> allocs;
 
     void* dev_alloc(size_t bytes, cudaStream_t st) {
@@ -353,6 +370,51 @@ dare_status ensure_pinned(dare_session s, int slot, size_t bytes) {
     const size_t want = align_up(std::max(bytes, size_t(1) << 16), 4096);
     CUDA_TRY(cudaHostAlloc(&s->pinned[slot], want, cudaHostAllocDefault));
     s->pinned_bytes[slot] = want;
+    return DARE_OK;
+}
+
+// Copy streams and slot events of the host-buffer calls, made on first use.
+dare_status ensure_host_io(dare_session s) {
+    if (s->up_st) return DARE_OK;
+    CUDA_TRY(cudaStreamCreateWithFlags(&s->up_st, cudaStreamNonBlocking));
+    CUDA_TRY(cudaStreamCreateWithFlags(&s->down_st, cudaStreamNonBlocking));
+    std::vector<cudaEvent_t*> evs;
+    for (int k = 0; k < 2; ++k) evs.insert(evs.end(), {&s->ring_free[k], &s->ring_full[k]});
+    for (int k = 0; k < dare_session_s::kStageSlots; ++k) evs.insert(evs.end(), {&s->stage_free[k], &s->stage_full[k]});
+    for (cudaEvent_t* e : evs) {
+        CUDA_TRY(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+        CUDA_TRY(cudaEventRecord(*e, s->up_st));  // completes at once: every slot starts free
+    }
+    return DARE_OK;
+}
+
+// A device buffer of n_want slots of at least `slot` bytes; growing it first
+// waits (on the host) until no slot is in use (the events in_use).
+dare_status ensure_slots(dare_session s, uint8_t*& buf, size_t& have, int& n_have, size_t slot, int n_want,
+                         const std::vector<cudaEvent_t>& in_use, cudaStream_t st) {
+    if (have >= slot && n_have >= n_want) return DARE_OK;
+    for (cudaEvent_t e : in_use) CUDA_TRY(cudaEventSynchronize(e));
+    if (buf) {
+        s->dev_free(buf, size_t(n_have) * have, st);
+        g_in_use -= static_cast<int64_t>(size_t(n_have) * have);
+        buf = nullptr;
+    }
+    have = std::max(have, align_up(slot, size_t(1) << 20));
+    n_have = std::max(n_have, n_want);
+    const size_t bytes = size_t(n_have) * have;
+    dare_status a = admit(static_cast<int64_t>(bytes));
+    if (a != DARE_OK) {
+        have = 0;
+        n_have = 0;
+        return a;
+    }
+    buf = static_cast<uint8_t*>(s->dev_alloc(bytes, st));
+    if (!buf) {
+        g_in_use -= static_cast<int64_t>(bytes);
+        have = 0;
+        n_have = 0;
+        return fail(DARE_E_OOM, "staging allocation of %zu bytes failed", bytes);
+    }
     return DARE_OK;
 }
 
@@ -739,10 +801,11 @@ dare_status dare_session_create(const dare_session_config* cfg, dare_session* ou
         dare_session_destroy(s);
         return code;
     };
-    if (cudaEventCreateWithFlags(&s->order_ev, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->pinned_ev[0], cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&s->pinned_ev[1], cudaEventDisableTiming) != cudaSuccess)
+    if (cudaEventCreateWithFlags(&s->order_ev, cudaEventDisableTiming) != cudaSuccess)
         return bail(fail(DARE_E_CUDA, "event creation failed"));
+    for (int k = 0; k < dare_session_s::kPinSlots; ++k)
+        if (cudaEventCreateWithFlags(&s->pinned_ev[k], cudaEventDisableTiming) != cudaSuccess)
+            return bail(fail(DARE_E_CUDA, "event creation failed"));
     // clear: empty records, zero counters (synchronous)
     g_launches += 1;
     if (launch_fill_records(s->rec, n_vox, s->rec_bytes, s->K, nullptr) != cudaSuccess ||
@@ -752,9 +815,10 @@ dare_status dare_session_create(const dare_session_config* cfg, dare_session* ou
         cudaError_t e = cudaGetLastError();
         return bail(fail(DARE_E_CUDA, "clearing the volume failed: %s", cudaGetErrorString(e)));
     }
-    if (cudaEventRecord(s->order_ev, nullptr) != cudaSuccess || cudaEventRecord(s->pinned_ev[0], nullptr) != cudaSuccess ||
-        cudaEventRecord(s->pinned_ev[1], nullptr) != cudaSuccess)
-        return bail(fail(DARE_E_CUDA, "event record failed"));
+    bool rec_ok = cudaEventRecord(s->order_ev, nullptr) == cudaSuccess;
+    for (int k = 0; k < dare_session_s::kPinSlots; ++k)
+        rec_ok = rec_ok && cudaEventRecord(s->pinned_ev[k], nullptr) == cudaSuccess;
+    if (!rec_ok) return bail(fail(DARE_E_CUDA, "event record failed"));
     *out = s;
     return DARE_OK;
 }
@@ -763,7 +827,7 @@ dare_status dare_session_destroy(dare_session s) {
     if (!s) return DARE_OK;
     DeviceGuard dg(s->cfg.device);
     if (s->order_ev) cudaEventSynchronize(s->order_ev);
-    for (int k = 0; k < 2; ++k)
+    for (int k = 0; k < dare_session_s::kPinSlots; ++k)
         if (s->pinned_ev[k]) cudaEventSynchronize(s->pinned_ev[k]);
     if (s->ws) {
         s->dev_free(s->ws, s->ws_bytes, s->last_stream);
@@ -773,9 +837,30 @@ dare_status dare_session_destroy(dare_session s) {
         s->dev_free(a.first, a.second, s->last_stream);
         g_in_use -= static_cast<int64_t>(a.second);
     }
-    for (int k = 0; k < 2; ++k) {
+    for (int k = 0; k < dare_session_s::kPinSlots; ++k) {
         if (s->pinned[k]) cudaFreeHost(s->pinned[k]);
         if (s->pinned_ev[k]) cudaEventDestroy(s->pinned_ev[k]);
+    }
+    if (s->up_st) {
+        cudaStreamSynchronize(s->up_st);
+        cudaStreamSynchronize(s->down_st);
+        std::vector<cudaEvent_t> evs;
+        for (int k = 0; k < 2; ++k) evs.insert(evs.end(), {s->ring_free[k], s->ring_full[k]});
+        for (int k = 0; k < dare_session_s::kStageSlots; ++k) evs.insert(evs.end(), {s->stage_free[k], s->stage_full[k]});
+        for (cudaEvent_t e : evs) {
+            cudaEventSynchronize(e);
+            cudaEventDestroy(e);
+        }
+        cudaStreamDestroy(s->up_st);
+        cudaStreamDestroy(s->down_st);
+    }
+    if (s->ring) {
+        s->dev_free(s->ring, size_t(s->ring_n) * s->ring_slot, s->last_stream);
+        g_in_use -= static_cast<int64_t>(size_t(s->ring_n) * s->ring_slot);
+    }
+    if (s->stage) {
+        s->dev_free(s->stage, size_t(s->stage_n) * s->stage_slot, s->last_stream);
+        g_in_use -= static_cast<int64_t>(size_t(s->stage_n) * s->stage_slot);
     }
     if (s->order_ev) cudaEventDestroy(s->order_ev);
     delete s;
@@ -840,13 +925,21 @@ dare_status dare_session_read_frames(dare_session s, double* rotations) {
     return DARE_OK;
 }
 
-dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t n, int32_t width, int32_t height,
-                              const double px_mm[2], const double* image_to_world, void* stream) {
+}  // extern "C"
+
+namespace {
+
+// Reconstruction of n frames (Fig. 1).  host: frames are in host memory and go
+// through the session's upload ring in slices of slice_frames frames, each
+// slice's upload overlapping the scatter count of the previous one.
+dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t n, int32_t width, int32_t height,
+                       const double px_mm[2], const double* image_to_world, int32_t slice_frames, void* stream) {
     if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    if (slice_frames < 0) return fail(DARE_E_INVALID, "slice_frames must be >= 0");
     if (n < 0 || width < 1 || height < 1 || width > 65535 || height > 65535)
         return fail(DARE_E_INVALID, "bad frame count or size");
     if (n == 0) return DARE_OK;
-    if (!frames_dev || !image_to_world || !px_mm) return fail(DARE_E_INVALID, "NULL argument");
+    if (!frames || !image_to_world || !px_mm) return fail(DARE_E_INVALID, "NULL argument");
     if (!(px_mm[0] > 0 && px_mm[1] > 0) || !std::isfinite(px_mm[0]) || !std::isfinite(px_mm[1]))
         return fail(DARE_E_INVALID, "pixel spacing must be positive and finite");
     if (int64_t(s->n_frames) + n > s->cfg.max_frames)
@@ -883,10 +976,22 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
     const size_t o_np = align_up(o_pairs + size_t(n_chunk) * slots_pf * 16, 256);
     const size_t o_aff = align_up(o_np + size_t(n_chunk) * tiles_pf * 4, 256);
     const size_t ws_need = align_up(o_aff + size_t(n) * 9 * 8, 256);
+    // upload slices (host frames): about 32 MB each unless given
+    const int32_t slice = !host ? 0
+                                : static_cast<int32_t>(std::min<int64_t>(
+                                      n_chunk, slice_frames > 0 ? slice_frames
+                                                                : std::max<int64_t>(1, (int64_t(32) << 20) / npx)));
     dare_status rc = session_begin(s, st);
     if (rc != DARE_OK) return rc;
     rc = ensure_workspace(s, ws_need, st);
     if (rc != DARE_OK) return rc;
+    if (host) {
+        rc = ensure_host_io(s);
+        if (rc != DARE_OK) return rc;
+        rc = ensure_slots(s, s->ring, s->ring_slot, s->ring_n, size_t(slice) * npx, 2,
+                          {s->ring_free[0], s->ring_free[1], s->ring_full[0], s->ring_full[1]}, st);
+        if (rc != DARE_OK) return rc;
+    }
     rc = ensure_pinned(s, 0, size_t(n) * 9 * 8 * 2);
     if (rc != DARE_OK) return rc;
     uint8_t* ws = static_cast<uint8_t*>(s->ws);
@@ -906,7 +1011,7 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
     for (int32_t c0 = 0; c0 < n; c0 += n_chunk) {
         const int32_t nc = std::min(n_chunk, n - c0);
         ScatterArgs a{};
-        a.frames = frames_dev + size_t(c0) * npx;
+        a.frames = frames + size_t(c0) * npx;
         a.affines = aff_dev + size_t(c0) * 9;
         a.n = nc;
         a.width = width;
@@ -917,9 +1022,32 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
         for (int32_t f = c0; f < c0 + nc; ++f)
             for (int k = 3; k < 9; ++k)
                 if (std::llabs(aff[9 * size_t(f) + k]) >= (int64_t(1) << 25)) a.small_steps = 0;
-        {
+        if (!host) {
             KernelScope ks("scatter_count", st, 1);
             CUDA_TRY(launch_scatter_count(a, s->count, pairs, n_pairs, st));
+        } else {
+            for (int32_t j0 = 0, k = 0; j0 < nc; j0 += slice, ++k) {
+                const int b = k & 1;
+                const int32_t nj = std::min(slice, nc - j0);
+                uint8_t* slot = s->ring + size_t(b) * s->ring_slot;
+                // upload into a free slot, then count from it on the caller's stream
+                CUDA_TRY(cudaStreamWaitEvent(s->up_st, s->ring_free[b], 0));
+                CUDA_TRY(cudaMemcpyAsync(slot, frames + (size_t(c0) + j0) * npx, size_t(nj) * npx,
+                                         cudaMemcpyHostToDevice, s->up_st));
+                CUDA_TRY(cudaEventRecord(s->ring_full[b], s->up_st));
+                CUDA_TRY(cudaStreamWaitEvent(st, s->ring_full[b], 0));
+                ScatterArgs sa = a;
+                sa.frames = slot;
+                sa.affines = a.affines + size_t(j0) * 9;
+                sa.n = nj;
+                sa.frame_base = a.frame_base + j0;
+                sa.tile_base = int64_t(j0) * tiles_pf;
+                {
+                    KernelScope ks("scatter_count", st, 1);
+                    CUDA_TRY(launch_scatter_count(sa, s->count, pairs, n_pairs, st));
+                }
+                CUDA_TRY(cudaEventRecord(s->ring_free[b], st));
+            }
         }
         {
             KernelScope ks("exclusive_scan", st, 3);
@@ -944,6 +1072,22 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
     s->version += 1;
     return DARE_OK;
 }
+
+}  // namespace
+
+extern "C" {
+
+dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t n, int32_t width, int32_t height,
+                              const double px_mm[2], const double* image_to_world, void* stream) {
+    return build_impl(s, frames_dev, false, n, width, height, px_mm, image_to_world, 0, stream);
+}
+
+dare_status dare_build_volume_host(dare_session s, const uint8_t* frames_host, int32_t n, int32_t width,
+                                   int32_t height, const double px_mm[2], const double* image_to_world,
+                                   int32_t slice_frames, void* stream) {
+    return build_impl(s, frames_host, true, n, width, height, px_mm, image_to_world, slice_frames, stream);
+}
+
 
 dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
                          uint32_t* mask_dev, void* stream) {
@@ -1008,20 +1152,112 @@ dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const da
     dare::batch_sizes(reqs, n, params, &ws_need, &desc_bytes);
     rc = ensure_workspace(s0, ws_need, st);
     if (rc != DARE_OK) return rc;
-    rc = ensure_pinned(s0, 1, desc_bytes);
+    const int pin = 1 + (s0->next_desc++ & 7);  // descriptor slots 1..8 in turn
+    rc = ensure_pinned(s0, pin, desc_bytes);
     if (rc != DARE_OK) return rc;
     {
         const bool one_l2 = sess.size() == 1 && (s0->cfg.flags & DARE_SESSION_L2_PERSIST);
         L2Window l2(one_l2 ? s0->rec : nullptr, size_t(s0->n_vox) * s0->rec_bytes, st);
         rc = dare::queue_batch(reqs, n, params, st, static_cast<uint8_t*>(s0->ws),
-                               static_cast<uint8_t*>(s0->pinned[1]));
+                               static_cast<uint8_t*>(s0->pinned[pin]));
     }
     if (rc != DARE_OK) return rc;
-    CUDA_TRY(cudaEventRecord(s0->pinned_ev[1], st));
+    CUDA_TRY(cudaEventRecord(s0->pinned_ev[pin], st));
     for (auto* s : sess) {
         rc = session_end(s, st);
         if (rc != DARE_OK) return rc;
     }
+    return DARE_OK;
+}
+
+dare_status dare_reslice_batch_host(const dare_reslice_req* reqs, int32_t n, const dare_params* params,
+                                    int32_t group_planes, void* stream) {
+    if (n < 0 || (n > 0 && !reqs)) return fail(DARE_E_INVALID, "bad request list");
+    if (group_planes < 0) return fail(DARE_E_INVALID, "group_planes must be >= 0");
+    if (n == 0) return DARE_OK;
+    dare_status rc = dare::check_batch(reqs, n, params);
+    if (rc != DARE_OK) return rc;
+    dare_session s0 = reqs[0].session;
+    DeviceGuard dg(s0->cfg.device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    std::vector<size_t> ob(n), mb(n);  // staging bytes of each image and mask
+    for (int32_t i = 0; i < n; ++i) {
+        const dare_plane& pl = reqs[i].plane;
+        ob[i] = size_t(pl.width) * pl.height * 4;
+        mb[i] = size_t(pl.height) * ((pl.width + 31) / 32) * 4;
+    }
+    // groups of consecutive requests: group_planes planes, or about 128 MB of output
+    std::vector<int32_t> gs;  // first request of each group, then n
+    size_t slot_need = 0, cur = 0;
+    for (int32_t i = 0, cnt = 0; i < n; ++i) {
+        const bool full = group_planes > 0 ? cnt == group_planes : cur + ob[i] + mb[i] > (size_t(128) << 20);
+        if (cnt == 0 || full) {
+            gs.push_back(i);
+            cur = 0;
+            cnt = 0;
+        }
+        cur += ob[i] + mb[i];
+        ++cnt;
+        slot_need = std::max(slot_need, cur);
+    }
+    gs.push_back(n);
+    rc = ensure_host_io(s0);
+    if (rc != DARE_OK) return rc;
+    const int32_t ng = static_cast<int32_t>(gs.size()) - 1;
+    // slots: enough for the groups to run ahead of their downloads, within about 1 GB
+    const int n_slots = static_cast<int>(std::max<int64_t>(
+        2, std::min<int64_t>({int64_t(dare_session_s::kStageSlots), int64_t(ng),
+                              int64_t((size_t(1) << 30) / std::max<size_t>(slot_need, 1))})));
+    std::vector<cudaEvent_t> stage_ev;
+    for (int k = 0; k < dare_session_s::kStageSlots; ++k) stage_ev.insert(stage_ev.end(), {s0->stage_free[k], s0->stage_full[k]});
+    rc = ensure_slots(s0, s0->stage, s0->stage_slot, s0->stage_n, slot_need, n_slots, stage_ev, st);
+    if (rc != DARE_OK) return rc;
+    std::vector<dare_reslice_req> sub;
+    for (int32_t g = 0; g < ng; ++g) {
+        const int32_t a = gs[g], b = gs[g + 1];
+        const int sl = g % s0->stage_n;
+        uint8_t* base = s0->stage + size_t(sl) * s0->stage_slot;
+        // slot layout: the group's images in request order, then its masks
+        size_t out_total = 0;
+        for (int32_t i = a; i < b; ++i) out_total += ob[i];
+        sub.assign(reqs + a, reqs + b);
+        std::vector<uint8_t*> so(b - a), sm(b - a);
+        size_t oo = 0, mo = 0;
+        for (int32_t i = a; i < b; ++i) {
+            so[i - a] = base + oo;
+            sm[i - a] = base + out_total + mo;
+            sub[i - a].out = reinterpret_cast<float*>(so[i - a]);
+            sub[i - a].mask = reinterpret_cast<uint32_t*>(sm[i - a]);
+            oo += ob[i];
+            mo += mb[i];
+        }
+        CUDA_TRY(cudaStreamWaitEvent(st, s0->stage_free[sl], 0));
+        rc = dare_reslice_batch(sub.data(), b - a, params, st);
+        if (rc != DARE_OK) return rc;
+        CUDA_TRY(cudaEventRecord(s0->stage_full[sl], st));
+        CUDA_TRY(cudaStreamWaitEvent(s0->down_st, s0->stage_full[sl], 0));
+        // downloads; requests whose host buffers follow each other go in one copy
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int32_t i = a; i < b;) {
+                uint8_t* dst = pass == 0 ? reinterpret_cast<uint8_t*>(reqs[i].out) : reinterpret_cast<uint8_t*>(reqs[i].mask);
+                const uint8_t* src = pass == 0 ? so[i - a] : sm[i - a];
+                size_t bytes = pass == 0 ? ob[i] : mb[i];
+                int32_t j = i + 1;
+                for (; j < b; ++j) {
+                    const uint8_t* next = pass == 0 ? reinterpret_cast<const uint8_t*>(reqs[j].out)
+                                                    : reinterpret_cast<const uint8_t*>(reqs[j].mask);
+                    if (next != dst + bytes) break;
+                    bytes += pass == 0 ? ob[j] : mb[j];
+                }
+                CUDA_TRY(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s0->down_st));
+                i = j;
+            }
+        }
+        CUDA_TRY(cudaEventRecord(s0->stage_free[sl], s0->down_st));
+    }
+    // the caller's stream covers the downloads (in order on the download stream)
+    CUDA_TRY(cudaStreamWaitEvent(st, s0->stage_free[(ng - 1) % s0->stage_n], 0));
     return DARE_OK;
 }
 

@@ -73,6 +73,7 @@ struct ScatterArgs {
     int32_t dims[3];
     int32_t frame_base;       // global id of frame 0 of this chunk
     int32_t small_steps;      // every |A|, |B| < 2^25: tiles step pixels in int32
+    int64_t tile_base;        // pair-list tile of frame 0 (frames uploaded in slices)
 };
 
 // ------------------------------------------------------------ launchers (kernels.cu, kernels_build.cu)

@@ -153,7 +153,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constan
         if (lane == 0) s_cnt[it * kWarps + warp] = __popc(bal);
     }
     __syncthreads();
-    const int64_t tile = static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
+    const int64_t tile = A.tile_base + static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
     if (threadIdx.x < 32) {
         // exclusive scan of the kIters * kWarps counts: each warp's run in the tile's region
         const int a = s_cnt[threadIdx.x], b = s_cnt[32 + threadIdx.x];
