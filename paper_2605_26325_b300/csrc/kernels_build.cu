@@ -44,13 +44,16 @@ __device__ __forceinline__ int scatter_voxel(const int64_t* aff, const int* dims
     return c[0] + dims[0] * (c[1] + dims[1] * c[2]);
 }
 
-__device__ __forceinline__ void hash_add(int* keys, unsigned* npx, unsigned* sums, int vi, unsigned n, unsigned s) {
+// A new key also appends its slot to `list` (the tile's distinct voxels).
+__device__ __forceinline__ void hash_add(int* keys, unsigned* npx, unsigned* sums, int* list, int* n_list, int vi,
+                                         unsigned n, unsigned s) {
     unsigned h = (static_cast<unsigned>(vi) * 2654435761u) >> 21;  // 11-bit Fibonacci hash
     for (;;) {  // at most kTile^2 distinct keys in kHash slots: terminates
         const int k0 = atomicCAS(keys + h, kEmptyKey, vi);
         if (k0 == kEmptyKey || k0 == vi) {
             atomicAdd(npx + h, n);  // two 32-bit adds: faster here than one 64-bit shared-memory add
             atomicAdd(sums + h, s);
+            if (k0 == kEmptyKey) list[atomicAdd(n_list, 1)] = static_cast<int>(h);
             return;
         }
         h = (h + 1) & (kHash - 1);
@@ -61,13 +64,14 @@ __device__ __forceinline__ void hash_add(int* keys, unsigned* npx, unsigned* sum
 // its pixel count and sum.  Each thread owns a 2 x 2 pixel block; pixels of the
 // block that land in one voxel are combined before touching shared memory.
 __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int u0, int v0, int* keys,
-                                               unsigned* npx, unsigned* sums) {
+                                               unsigned* npx, unsigned* sums, int* list, int* n_list) {
     // npx and sums are the two halves of one 8-byte-aligned buffer: cleared with 8-byte stores
     unsigned long long* both = reinterpret_cast<unsigned long long*>(npx);
     for (int i = threadIdx.x; i < kHash; i += kThreads) {
         keys[i] = kEmptyKey;
         both[i] = 0ull;
     }
+    if (threadIdx.x == 0) *n_list = 0;
     __shared__ int64_t aff[9];
     if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
     __syncthreads();
@@ -121,7 +125,7 @@ __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int 
 #pragma unroll
         for (int k = j + 1; k < 4; ++k)
             if (vi[k] == vi[j]) ++n, sm += val[k];
-        hash_add(keys, npx, sums, vi[j], n, sm);
+        hash_add(keys, npx, sums, list, n_list, vi[j], n, sm);
     }
     __syncthreads();
 }
@@ -132,56 +136,29 @@ __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int 
 __global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constant__ ScatterArgs A,
                                                             int32_t* __restrict__ count, uint4* __restrict__ pairs,
                                                             int32_t* __restrict__ n_pairs) {
-    constexpr int kIters = kHash / kThreads, kWarps = kThreads / 32;
-    static_assert(kIters * kWarps == 64, "the run scan covers 64 counts with one warp");
     __shared__ int keys[kHash];
     __shared__ unsigned long long acc_buf[kHash];  // npx, then sums: kHash 32-bit counters each
-    __shared__ int s_cnt[kIters * kWarps];
+    __shared__ int list[kTile * kTile];            // slots of the tile's distinct voxels, in insertion order
+    __shared__ int n_list;
     unsigned* npx = reinterpret_cast<unsigned*>(acc_buf);
-    unsigned* sums = npx + kHash;  // occupied slots per (iteration, warp), then their offsets
+    unsigned* sums = npx + kHash;
     const int tiles_x = (A.width + kTile - 1) / kTile;
     const int f = blockIdx.y;
     const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
-    aggregate_tile(A, f, u0, v0, keys, npx, sums);
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    // pass 1: count the pairs, bump each voxel's counter once per pair
-    for (int it = 0; it < kIters; ++it) {
-        const int i = it * kThreads + threadIdx.x;
-        const int vi = keys[i];
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, vi != kEmptyKey);
-        if (vi != kEmptyKey) atomicAdd(count + vi, 1);
-        if (lane == 0) s_cnt[it * kWarps + warp] = __popc(bal);
-    }
-    __syncthreads();
+    aggregate_tile(A, f, u0, v0, keys, npx, sums, list, &n_list);
+    // one pair per distinct voxel, at its list position: bump the voxel's counter, write the pair
     const int64_t tile = A.tile_base + static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
-    if (threadIdx.x < 32) {
-        // exclusive scan of the kIters * kWarps counts: each warp's run in the tile's region
-        const int a = s_cnt[threadIdx.x], b = s_cnt[32 + threadIdx.x];
-        int ia = a, ib = b;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int ya = __shfl_up_sync(0xFFFFFFFFu, ia, o), yb = __shfl_up_sync(0xFFFFFFFFu, ib, o);
-            if (lane >= o) ia += ya, ib += yb;
-        }
-        const int tot_a = __shfl_sync(0xFFFFFFFFu, ia, 31);
-        s_cnt[threadIdx.x] = ia - a;
-        s_cnt[32 + threadIdx.x] = tot_a + ib - b;
-        if (threadIdx.x == 31) n_pairs[tile] = tot_a + ib;
-    }
-    __syncthreads();
-    // pass 2: write the pairs, each warp into its run
+    const int n = n_list;
     const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
     uint4* out = pairs + tile * (kTile * kTile);
-    for (int it = 0; it < kIters; ++it) {
-        const int i = it * kThreads + threadIdx.x;
-        const int vi = keys[i];
-        const unsigned bal = __ballot_sync(0xFFFFFFFFu, vi != kEmptyKey);
-        if (vi != kEmptyKey) {
-            const unsigned long long e = fid | (static_cast<unsigned long long>(npx[i]) << 32) | sums[i];
-            const int pos = s_cnt[it * kWarps + warp] + __popc(bal & ((1u << lane) - 1u));
-            out[pos] = make_uint4(static_cast<unsigned>(vi), 0u, static_cast<unsigned>(e), static_cast<unsigned>(e >> 32));
-        }
+    for (int j = threadIdx.x; j < n; j += kThreads) {
+        const int h = list[j];
+        const int vi = keys[h];
+        atomicAdd(count + vi, 1);
+        const unsigned long long e = fid | (static_cast<unsigned long long>(npx[h]) << 32) | sums[h];
+        out[j] = make_uint4(static_cast<unsigned>(vi), 0u, static_cast<unsigned>(e), static_cast<unsigned>(e >> 32));
     }
+    if (threadIdx.x == 0) n_pairs[tile] = n;
 }
 
 // One CTA per tile region: each pair takes its slot from the voxel's counter
