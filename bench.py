@@ -247,7 +247,11 @@ def run_reference(args, dist):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "poses": args.poses, "storage": "f64 (oracle)"},
+            "config": {"workload": WORKLOAD, "grid": "256^3 @ 0.4 mm", "frames": int(len(w.frames)),
+                       "frame_px": "256x512 @ 0.2 mm", "poses": args.poses, "out_px": f"{w.out_w}x{w.out_h} @ 0.2 mm",
+                       "storage": "f64 (oracle; f32-rounded stored values)", "slots": args.slots,
+                       "step": "reset + rebuild volume from all frames + reslice every pose",
+                       "parallelism": "host threads, rank 0 only"},
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
