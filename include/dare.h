@@ -176,10 +176,13 @@ typedef struct {
     double k_inplane;       /* Eq. 2, paper: 5 */
     double thr_normal_deg;  /* paper: 25 */
     double thr_inplane_deg; /* paper: 15 */
-    double k_dist;          /* rate of the EXP distance kernel */
+    double k_dist;          /* rate of the EXP distance kernel (>= 0) */
     float unassigned;       /* value of an unassigned pixel (default 0) */
-    int32_t radius_vox;     /* R, interpolation distance in voxels (default 1) */
-    int32_t dist_kernel;    /* dare_dist_kernel (default TENT) */
+    int32_t radius_vox;     /* R, interpolation distance in voxels, 1..16 (default 1) */
+    int32_t dist_kernel;    /* dare_dist_kernel (default TENT): a pixel at g reads, per axis,
+                               TENT: floor(g) - R + 1 .. floor(g) + R, t = prod (1 - |g - c| / R);
+                               BOX:  round(g) - R .. round(g) + R,    t = 1;
+                               EXP:  as TENT,                          t = exp(-k_dist |g - c| / R) */
     int32_t normal_axis;    /* dare_normal_axis (default BEAM) */
     int32_t weight_dtype;   /* dare_weight_dtype of the per-frame weight table */
     int32_t path;           /* dare_path: kernel choice */
@@ -292,8 +295,10 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
 
 /*
  * Reslicing (Sec. 2.1, Eq. 1, Eq. 2, Fig. 2) of one plane into out_dev /
- * mask_dev (see Layouts).  DARE_E_UNSUPPORTED for a radius or distance
- * kernel the chosen path does not implement.
+ * mask_dev (see Layouts).  Every distance kernel (TENT, BOX, EXP) runs on
+ * both paths for radius_vox 1..16 (the tiled kernel up to a support of 9
+ * voxels per axis, i.e. radius 4; planes beyond it, or whose tiles do not fit
+ * shared memory, gather per pixel).  DARE_E_UNSUPPORTED above radius 16.
  */
 dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
                          uint32_t* mask_dev, void* stream);

@@ -439,8 +439,8 @@ dare_status check_params(const dare_params* p) {
     if (p->normal_axis < 0 || p->normal_axis > 1) return fail(DARE_E_INVALID, "unknown normal axis");
     if (p->weight_dtype < 0 || p->weight_dtype > 1) return fail(DARE_E_INVALID, "unknown weight dtype");
     if (p->path < 0 || p->path > 2) return fail(DARE_E_INVALID, "unknown path");
-    if (p->radius_vox != 1 || p->dist_kernel != DARE_TENT)
-        return fail(DARE_E_UNSUPPORTED, "the CUDA path implements the TENT kernel at radius 1");
+    if (p->radius_vox > 16) return fail(DARE_E_UNSUPPORTED, "radius_vox above 16 is not implemented");
+    if (p->dist_kernel == DARE_EXP && !(p->k_dist >= 0)) return fail(DARE_E_INVALID, "k_dist must be >= 0");
     return DARE_OK;
 }
 
@@ -467,9 +467,18 @@ void plane_vectors(const dare_session s, const dare_plane* pl, int normal_axis, 
     }
 }
 
+// The distance kernel of params (TENT at radius 1 when NULL) goes into the job.
 ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab, float* out, uint32_t* mask,
-                    float unassigned) {
+                    float unassigned, const dare_params* params = nullptr) {
     ResliceJob j{};
+    const int R = params ? params->radius_vox : 1;
+    j.radius = R;
+    j.kernel = params ? params->dist_kernel : DARE_TENT;
+    j.k_dist = params ? static_cast<float>(params->k_dist) : 1.0f;
+    j.ext_lo = j.kernel == DARE_BOX ? R : R - 1;  // a pixel with floor f reads f - ext_lo .. f + ext_hi
+    j.ext_hi = j.kernel == DARE_BOX ? R + 1 : R;
+    // pixels reading a voxel column lie within `reach` voxels of it on each in-plane axis
+    const double reach = static_cast<double>(std::max(j.ext_hi, j.ext_lo + 1));
     int64_t aff[9];
     compose_affine(s->cfg.grid.vol_to_world, s->cfg.grid.spacing_mm, pl->image_to_world, pl->width, pl->px_mm[0],
                    pl->px_mm[1], aff);
@@ -517,7 +526,7 @@ ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab
     j.beta2 = static_cast<float>(b2);
     j.alpha = static_cast<float>(G0[d] - b1 * G0[e1] - b2 * G0[e2]);
     j.spread = static_cast<float>(spread);
-    j.levels = static_cast<int32_t>(std::floor(2.0 * spread + 0.05)) + 3;
+    j.levels = static_cast<int32_t>(std::floor((2.0 * spread + 0.05) * reach)) + j.ext_lo + j.ext_hi + 2;
     const double m00 = B[e2] / det, m01 = -B[e1] / det, m10 = -A[e2] / det, m11 = A[e1] / det;
     j.m00 = static_cast<float>(m00);
     j.m01 = static_cast<float>(m01);
@@ -525,9 +534,40 @@ ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab
     j.m11 = static_cast<float>(m11);
     j.ou = static_cast<float>(-(m00 * G0[e1] + m01 * G0[e2]));
     j.ov = static_cast<float>(-(m10 * G0[e1] + m11 * G0[e2]));
-    j.hu = static_cast<float>(std::fabs(m00) + std::fabs(m01) + 0.25);
-    j.hv = static_cast<float>(std::fabs(m10) + std::fabs(m11) + 0.25);
+    j.hu = static_cast<float>((std::fabs(m00) + std::fabs(m01)) * reach + 0.25);
+    j.hv = static_cast<float>((std::fabs(m10) + std::fabs(m11)) * reach + 0.25);
     return j;
+}
+
+// Any distance kernel but TENT at radius 1 runs on the general kernels (kernels_radius.cu).
+bool general_support(const dare_params* p) { return p->radius_vox != 1 || p->dist_kernel != DARE_TENT; }
+constexpr int kTileHGeneral = 32;  // tile rows of the general tiled kernel
+
+// Shared memory of the general tiled kernel for these jobs: a bound on any
+// tile's column box and (A, B) slots.  A plane whose tiles cannot fit gathers
+// per pixel (direct).
+void general_caps(ResliceJob* jobs, int n, int* col_cap, int* slot_cap) {
+    int64_t cols_max = 1, slots_max = 1;
+    for (int i = 0; i < n; ++i) {
+        ResliceJob& j = jobs[i];
+        if (j.direct) continue;
+        const int S = j.kernel == DARE_BOX ? 2 * j.radius + 1 : 2 * j.radius;
+        const int e1 = j.d == 0 ? 1 : 0, e2 = j.d == 2 ? 1 : 2;
+        const double sc = 1.0 / static_cast<double>(kFixOne);
+        const double x1 = (std::llabs(j.a[e1]) * double(kTileW - 1) + std::llabs(j.b[e1]) * double(kTileHGeneral - 1)) * sc;
+        const double x2 = (std::llabs(j.a[e2]) * double(kTileW - 1) + std::llabs(j.b[e2]) * double(kTileHGeneral - 1)) * sc;
+        const int64_t n1 = static_cast<int64_t>(x1) + 2 + j.ext_lo + j.ext_hi;
+        const int64_t n2 = static_cast<int64_t>(x2) + 2 + j.ext_lo + j.ext_hi;
+        const int64_t cols = n1 * n2, slots = cols * j.levels;
+        if (S > kMaxSupport || slots * 8 + cols * 4 > kGeneralSmemCap) {
+            j.direct = 1;
+            continue;
+        }
+        cols_max = std::max(cols_max, cols);
+        slots_max = std::max(slots_max, slots);
+    }
+    *col_cap = static_cast<int>(cols_max);
+    *slot_cap = static_cast<int>(slots_max);
 }
 
 int tiles_of(const dare_plane* pl, int tile_h = kTileH) {
@@ -535,6 +575,29 @@ int tiles_of(const dare_plane* pl, int tile_h = kTileH) {
 }
 
 bool use_tiled(const dare_params* p) { return p->path != DARE_PATH_PLAIN; }
+
+// One plane's reslice launch on the path params choose.
+cudaError_t launch_one(ResliceJob& job, const dare_plane* plane, const dare_params* params, int K, int dtype,
+                       int half_w, cudaStream_t st) {
+    job.tile_base = 0;
+    if (general_support(params)) {
+        if (use_tiled(params)) {
+            int col_cap = 0, slot_cap = 0;
+            general_caps(&job, 1, &col_cap, &slot_cap);
+            KernelScope ks("reslice_tiled_r", st, 1);
+            return launch_reslice_tiled_r(nullptr, &job, 1, 0, tiles_of(plane, kTileHGeneral), 0, col_cap, slot_cap, K,
+                                          dtype, half_w, st);
+        }
+        KernelScope ks("reslice_plain_r", st, 1);
+        return launch_reslice_plain_r(nullptr, &job, 1, plane->width, plane->height, K, dtype, half_w, st);
+    }
+    if (use_tiled(params)) {
+        KernelScope ks("reslice_tiled", st, 1);
+        return launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, kTileH, K, dtype, half_w, st);
+    }
+    KernelScope ks("reslice_plain", st, 1);
+    return launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, K, dtype, half_w, st);
+}
 
 }  // namespace
 
@@ -598,6 +661,8 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
         const auto* sb = reqs[b].session;
         return sa->K != sb->K ? sa->K < sb->K : sa->dtype < sb->dtype;
     });
+    const bool general = general_support(params);
+    const int th = general ? kTileHGeneral : kTileH;
     int total_tiles = 0;
     for (int32_t k = 0; k < n; ++k) {
         const dare_reslice_req& r = reqs[order[k]];
@@ -608,10 +673,12 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
         tj.wtab = wtab;
         tj.n_frames = r.session->n_frames;
         tjs[k] = tj;
-        rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, params->unassigned);
+        rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, params->unassigned, params);
         rjs[k].tile_base = total_tiles;
-        total_tiles += tiles_of(&r.plane);
+        total_tiles += tiles_of(&r.plane, th);
     }
+    int col_cap = 0, slot_cap = 0;
+    if (general) general_caps(rjs, n, &col_cap, &slot_cap);
     CUDA_TRY(cudaMemcpyAsync(ws + o_tj, pin, desc_bytes, cudaMemcpyHostToDevice, st));
     const auto* tj_dev = reinterpret_cast<const TableJob*>(ws + o_tj);
     const auto* rj_dev = reinterpret_cast<const ResliceJob*>(ws + o_rj);
@@ -633,12 +700,21 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
             const int base = rjs[k0].tile_base;
             const int end = (k1 < n) ? rjs[k1].tile_base : total_tiles;
             // same tile count for every job of the group: 2-D grid without a job search
-            const int per = tiles_of(&reqs[order[k0]].plane);
+            const int per = tiles_of(&reqs[order[k0]].plane, th);
             bool uniform = k1 - k0 <= 65535;
-            for (int32_t k = k0; uniform && k < k1; ++k) uniform = tiles_of(&reqs[order[k]].plane) == per;
-            KernelScope ks("reslice_tiled", st, 1);
-            CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base,
-                                          uniform ? 1 : 0, kTileH, sg->K, sg->dtype, half_w, st));
+            for (int32_t k = k0; uniform && k < k1; ++k) uniform = tiles_of(&reqs[order[k]].plane, th) == per;
+            if (general) {
+                KernelScope ks("reslice_tiled_r", st, 1);
+                CUDA_TRY(launch_reslice_tiled_r(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base,
+                                                uniform ? 1 : 0, col_cap, slot_cap, sg->K, sg->dtype, half_w, st));
+            } else {
+                KernelScope ks("reslice_tiled", st, 1);
+                CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base,
+                                              uniform ? 1 : 0, kTileH, sg->K, sg->dtype, half_w, st));
+            }
+        } else if (general) {
+            KernelScope ks("reslice_plain_r", st, 1);
+            CUDA_TRY(launch_reslice_plain_r(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
         } else {
             KernelScope ks("reslice_plain", st, 1);
             CUDA_TRY(launch_reslice_plain(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
@@ -1117,17 +1193,10 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
         KernelScope ks("weight_table", st, 1);
         CUDA_TRY(launch_weight_tables(nullptr, &tj, 1, s->n_frames, table_params(params), st));
     }
-    ResliceJob job = make_job(s, plane, s->ws, out_dev, mask_dev, params->unassigned);
+    ResliceJob job = make_job(s, plane, s->ws, out_dev, mask_dev, params->unassigned, params);
     const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
     L2Window l2((s->cfg.flags & DARE_SESSION_L2_PERSIST) ? s->rec : nullptr, size_t(s->n_vox) * s->rec_bytes, st);
-    if (use_tiled(params)) {
-        job.tile_base = 0;
-        KernelScope ks("reslice_tiled", st, 1);
-        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, kTileH, s->K, s->dtype, half_w, st));
-    } else {
-        KernelScope ks("reslice_plain", st, 1);
-        CUDA_TRY(launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, s->K, s->dtype, half_w, st));
-    }
+    CUDA_TRY(launch_one(job, plane, params, s->K, s->dtype, half_w, st));
     return session_end(s, st);
 }
 
@@ -1556,16 +1625,9 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
         KernelScope ks("weight_table", st, 1);
         CUDA_TRY(launch_weight_tables(nullptr, &tj, 1, s->n_frames, table_params(params), st));
     }
-    ResliceJob job = make_job(s, plane, wtab, out_dev, mask_dev, params->unassigned);
+    ResliceJob job = make_job(s, plane, wtab, out_dev, mask_dev, params->unassigned, params);
     const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
-    if (use_tiled(params)) {
-        job.tile_base = 0;
-        KernelScope ks("reslice_tiled", st, 1);
-        CUDA_TRY(launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, kTileH, s->K, s->dtype, half_w, st));
-    } else {
-        KernelScope ks("reslice_plain", st, 1);
-        CUDA_TRY(launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, s->K, s->dtype, half_w, st));
-    }
+    CUDA_TRY(launch_one(job, plane, params, s->K, s->dtype, half_w, st));
     return session_end(s, st);
 }
 
@@ -1580,6 +1642,7 @@ struct dare_plan_s {
         int choice = kTileH;      // 0 = plain, else tiled tile rows
         int max_w = 0, max_h = 0;
         float tune_ms[3] = {0, 0, 0};
+        int col_cap = 0, slot_cap = 0;  // general distance kernels: shared memory of the tiled kernel
     };
     std::vector<dare_reslice_req> reqs;
     dare_params params{};
@@ -1614,7 +1677,7 @@ void plan_fill(dare_plan p) {
     auto* tjs = reinterpret_cast<TableJob*>(pin);
     auto* rjs = reinterpret_cast<ResliceJob*>(pin + (p->o_rj - p->o_tj));
     uint8_t* ws = static_cast<uint8_t*>(p->ws);
-    for (const auto& g : p->groups) {
+    for (auto& g : p->groups) {
         int tile_base = 0;
         for (int32_t k = g.k0; k < g.k1; ++k) {
             const dare_reslice_req& r = p->reqs[p->order[k]];
@@ -1625,18 +1688,23 @@ void plan_fill(dare_plan p) {
             tj.wtab = wtab;
             tj.n_frames = r.session->n_frames;
             tjs[k] = tj;
-            rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, p->params.unassigned);
+            rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, p->params.unassigned, &p->params);
             rjs[k].tile_base = tile_base;
             tile_base += plan_tiles(&r.plane, g.choice);
         }
+        if (general_support(&p->params)) general_caps(rjs + g.k0, g.k1 - g.k0, &g.col_cap, &g.slot_cap);
     }
 }
 
 cudaError_t plan_group_launch(dare_plan p, const dare_plan_s::Group& g, cudaStream_t st) {
     const auto* rj_dev = reinterpret_cast<const ResliceJob*>(static_cast<uint8_t*>(p->ws) + p->o_rj);
     const int half_w = p->params.weight_dtype == DARE_WEIGHTS_F16;
+    const bool general = general_support(&p->params);
     if (g.choice == 0)
-        return launch_reslice_plain(rj_dev + g.k0, nullptr, g.k1 - g.k0, g.max_w, g.max_h, g.K, g.dtype, half_w, st);
+        return general ? launch_reslice_plain_r(rj_dev + g.k0, nullptr, g.k1 - g.k0, g.max_w, g.max_h, g.K, g.dtype,
+                                                half_w, st)
+                       : launch_reslice_plain(rj_dev + g.k0, nullptr, g.k1 - g.k0, g.max_w, g.max_h, g.K, g.dtype,
+                                              half_w, st);
     const int per = tiles_of(&p->reqs[p->order[g.k0]].plane, g.choice);
     bool uniform = g.k1 - g.k0 <= 65535;
     int total = 0;
@@ -1645,6 +1713,9 @@ cudaError_t plan_group_launch(dare_plan p, const dare_plan_s::Group& g, cudaStre
         uniform = uniform && t == per;
         total += t;
     }
+    if (general)
+        return launch_reslice_tiled_r(rj_dev + g.k0, nullptr, g.k1 - g.k0, 0, uniform ? per : total, uniform ? 1 : 0,
+                                      g.col_cap, g.slot_cap, g.K, g.dtype, half_w, st);
     return launch_reslice_tiled(rj_dev + g.k0, nullptr, g.k1 - g.k0, 0, uniform ? per : total, uniform ? 1 : 0,
                                 g.choice, g.K, g.dtype, half_w, st);
 }
@@ -1785,7 +1856,7 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
             ++k1;
         }
         g.k1 = k1;
-        g.choice = params->path == DARE_PATH_PLAIN ? 0 : kTileH;
+        g.choice = params->path == DARE_PATH_PLAIN ? 0 : (general_support(params) ? kTileHGeneral : kTileH);
         p->groups.push_back(g);
         k0 = k1;
     }
@@ -1820,7 +1891,7 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
     for (auto* s : p->sessions) {
         if (cudaStreamWaitEvent(p->cap, s->order_ev, 0) != cudaSuccess) return bail(fail(DARE_E_CUDA, "wait failed"));
     }
-    if (params->path == DARE_PATH_AUTO)
+    if (params->path == DARE_PATH_AUTO && !general_support(params))  // general kernels: tiled, no tuning
         for (auto& g : p->groups) {
             rc = plan_tune(p, g, p->cap);
             if (rc != DARE_OK) return bail(rc);

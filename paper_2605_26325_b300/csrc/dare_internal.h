@@ -46,6 +46,13 @@ struct ResliceJob {
     int32_t n_frames;           // entries of wtab
     float alpha, beta1, beta2, spread;
     float m00, m01, m10, m11, ou, ov, hu, hv;
+    // distance kernel (Sec. 2.1 "Reslicing"): radius R in voxels, TENT / BOX / EXP,
+    // EXP rate; a pixel with floor(g) = f reads voxels f - ext_lo .. f + ext_hi
+    // per axis at most (TENT, EXP: R - 1, R; BOX: R, R + 1)
+    int32_t radius, kernel;
+    int32_t ext_lo, ext_hi;
+    float k_dist;
+    int32_t reserved;
 };
 
 // Inputs of the per-(plane, frame) weight table of Eq. 1 / Eq. 2.
@@ -98,6 +105,16 @@ cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_su
                                   cudaStream_t st);
 cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned long long* count, cudaStream_t st);
 cudaError_t launch_fill_records(uint8_t* rec, int64_t n_vox, int rec_bytes, int K, cudaStream_t st);
+
+// any radius and distance kernel (kernels_radius.cu): per-pixel gather, and the
+// tiled kernel with col_cap columns and slot_cap (A, B) slots of dynamic shared memory
+cudaError_t launch_reslice_plain_r(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int max_w,
+                                   int max_h, int K, int dtype, int half_weights, cudaStream_t st);
+cudaError_t launch_reslice_tiled_r(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
+                                   int tile_offset, int n_tiles, int uniform, int col_cap, int slot_cap, int K,
+                                   int dtype, int half_weights, cudaStream_t st);
+constexpr int kMaxSupport = 9;           // tiled general path: support of at most 9 voxels per axis (R <= 4)
+constexpr int kGeneralSmemCap = 200 << 10;  // dynamic shared memory of the general tiled kernel, at most
 
 // tiled kernel (kernels_tiled.cu)
 // uniform != 0: every job has n_tiles tiles (2-D grid, no job search); tile_h: 32 or 64

@@ -60,6 +60,27 @@ __device__ __forceinline__ void load_record(const uint8_t* p, uint4 (&r)[RecShap
     for (int i = 0; i < RecShape<K, VT>::kVec; ++i) r[i] = __ldg(q + i);
 }
 
+// (A_c, B_c) of one voxel from its whole record, read in one round trip (ids
+// first, values after; empty ids sort last).
+template <int K, typename VT, typename WT>
+__device__ __forceinline__ float2 collapse_voxel(const uint8_t* rec, int64_t vi, const WT* wt) {
+    using S = RecShape<K, VT>;
+    const uint4* q = reinterpret_cast<const uint4*>(rec + vi * S::kBytes);
+    uint4 r[S::kVec];
+#pragma unroll
+    for (int i = 0; i < S::kVec; ++i) r[i] = __ldg(q + i);
+    float A = 0.0f, B = 0.0f;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const uint32_t id = slot_id<K, VT>(r, s);
+        if (id == DARE_EMPTY_FRAME) break;  // empty slots come last
+        const float w = weight_of(wt, static_cast<int>(id));
+        A = fmaf(w, slot_value<K, VT>(r, s), A);
+        B += w;
+    }
+    return make_float2(A, B);
+}
+
 // Fixed-point pixel coordinate: integer voxel part and 20-bit fraction.
 struct PixelCoord {
     int c0[3];

@@ -308,12 +308,12 @@ def test_frame_capacity(tiny):
     s.close()
 
 
-def test_unsupported_kernel_is_reported(tiny, tiny_f32):
+def test_unsupported_radius_is_reported(tiny, tiny_f32):
     s, _ = tiny_f32
     out, mask = new_outputs(8, 8)
-    for p in (dare.params_default(radius_vox=2), dare.params_default(dist_kernel=dare.DARE_BOX)):
+    for path in (dare.DARE_PATH_PLAIN, dare.DARE_PATH_TILED):
         with pytest.raises(dare.DareError) as ei:
-            s.reslice(tiny.reslice_poses[0], out, mask, tiny.out_px, p)
+            s.reslice(tiny.reslice_poses[0], out, mask, tiny.out_px, dare.params_default(radius_vox=17, path=path))
         assert ei.value.status == dare.DARE_E_UNSUPPORTED
 
 
