@@ -474,6 +474,22 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
     line["l2_mode"] = {"volume_mb": l2["volume_mb"], "default_ms": l2["default"], "l2_persist_ms": l2["l2_persist"],
                        "planes": P}
 
+    # --- the paper's timing axis (Sec. 3): interpolation radius.  BOX gives its
+    # cubic neighbourhoods (3^3, 5^3, 9^3 voxels); TENT the 2R-wide support
+    radius = {}
+    for kname, kern in (("box", dare.DARE_BOX), ("tent", dare.DARE_TENT)):
+        for R in (1, 2, 4):
+            pr = dare.params_default(path=dare.DARE_PATH_TILED, radius_vox=R, dist_kernel=kern)
+            n = P if R < 4 else min(P, 200)
+            rq = (dare.dare_reslice_req * n)(*reqs[:n])
+            ms = timed(lambda: dare.reslice_batch(rq, pr, stream), 3 if R < 4 else 2) / n
+            side_n = 2 * R + 1 if kern == dare.DARE_BOX else 2 * R
+            radius[f"{kname}_R{R}"] = {"neighbourhood": f"{side_n}^3", "ms_per_plane_batched": ms,
+                                       "mpix_s": W * H / (ms * 1e-3) / 1e6, "latency": lat(pr, 50)}
+    radius["note"] = ("tiled path, 512x512 planes from the resident 256^3 volume; the paper's laptop-GPU medians "
+                      "(image and volume size not stated) are 50 / 100 / 300 ms for 3^3 / 5^3 / 9^3")
+    line["radius_axis"] = radius
+
     line["latency"] = {"tiled": lat(tiled), "plain_fp32": lat(plain),
                        "note": "wall time from the host call to the 512x512 image and mask on the device, "
                                "one plane per call"}
