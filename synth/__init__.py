@@ -268,6 +268,7 @@ class Workload:
     out_px: tuple
     reslice_poses: np.ndarray   # (m, 4, 4)
     sweep_tilts: tuple
+    phantom: "Phantom" = None   # the scene the frames were rendered from (renders ground truth at any pose)
 
 
 def tiny_workload(seed=0, render=True):
@@ -285,7 +286,7 @@ def tiny_workload(seed=0, render=True):
     rp = np.concatenate([perturbed_poses(seed, poses, 8, 10.0, 3.0),
                          perturbed_poses(seed + 1000, poses, 4, 35.0, 3.0),
                          random_poses(seed, 4, W, H, sx, sy, 6.0)])
-    return Workload("dare_64cube_200f_128px", grid, W, H, (sx, sy), poses, frames, W, H, (sx, sy), rp, tilts)
+    return Workload("dare_64cube_200f_128px", grid, W, H, (sx, sy), poses, frames, W, H, (sx, sy), rp, tilts, ph)
 
 
 def working_workload(seed=1, n_poses=1000, render=True):
@@ -301,7 +302,8 @@ def working_workload(seed=1, n_poses=1000, render=True):
     ph = make_phantom(seed, float(grid.extent[0]), 8, 2)
     frames = render_frames(ph, poses, W, H, sx, sy) if render else None
     rp = smooth_trajectory(seed, n_poses, 1000.0, 512, 512, 0.2, 0.2, tilts)
-    return Workload("dare_256cube_1600f_512px", grid, W, H, (sx, sy), poses, frames, 512, 512, (0.2, 0.2), rp, tilts)
+    return Workload("dare_256cube_1600f_512px", grid, W, H, (sx, sy), poses, frames, 512, 512, (0.2, 0.2), rp, tilts,
+                    ph)
 
 
 @dataclass
