@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--dtype", choices=list(DTYPE_NAMES), default="f32")
     ap.add_argument("--slots", type=int, default=12)
     ap.add_argument("--path", choices=["tiled", "plain"], default="tiled")
+    ap.add_argument("--radius", type=int, default=1, help="interpolation radius in voxels (default 1)")
+    ap.add_argument("--kernel", choices=["tent", "box", "exp"], default="tent", help="distance kernel (default tent)")
     ap.add_argument("--workload", choices=["working", "batched", "serving"], default="working",
                     help="working: the 256^3 step (default); batched: 64 uneven volumes through a graph-replayed "
                          "plan; serving: 16 sessions under Poisson pose streams with live ingestion")
@@ -282,7 +284,8 @@ def run_dare(args, dist):
     masks = torch.empty((P, H, dare.mask_words(W)), dtype=torch.int32, device=device)
     reqs = dare.make_requests([(s, w.reslice_poses[i], outs[i], masks[i], w.out_px) for i in range(P)])
     path = dare.DARE_PATH_TILED if args.path == "tiled" else dare.DARE_PATH_PLAIN
-    params = dare.params_default(path=path)
+    params = dare.params_default(path=path, radius_vox=args.radius,
+                                 dist_kernel={"tent": dare.DARE_TENT, "box": dare.DARE_BOX, "exp": dare.DARE_EXP}[args.kernel])
 
     def step():
         s.reset(stream)
@@ -340,6 +343,7 @@ def run_dare(args, dist):
             "config": {"workload": WORKLOAD, "grid": "256^3 @ 0.4 mm", "frames": int(len(w.frames)),
                        "frame_px": "256x512 @ 0.2 mm", "poses": P, "out_px": f"{W}x{H} @ 0.2 mm",
                        "storage": args.dtype, "slots": args.slots, "path": args.path, "weights": "f32",
+                       "distance_kernel": f"{args.kernel} R={args.radius}",
                        "step": "reset + rebuild volume from all frames + reslice every pose",
                        "l2": "inputs larger than L2 (volume, frames and outputs each > 126 MB); no flush",
                        "parallelism": f"replicas x{dist.world}"},
