@@ -534,6 +534,23 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
     line["l2_mode"] = {"volume_mb": l2["volume_mb"], "default_ms": l2["default"], "l2_persist_ms": l2["l2_persist"],
                        "planes": P}
 
+    # --- the same volume in mapped host memory (DARE_SESSION_HOST_VOLUME): reset +
+    # rebuild and the 1000-plane reslice, every record access over the host link
+    hv = dare.Session(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, dtype=DTYPE_NAMES[args.dtype],
+                      max_slots=args.slots, device=dist.local, flags=dare.DARE_SESSION_HOST_VOLUME)
+
+    def hv_build():
+        hv.reset(stream)
+        hv.build(frames_d, w.frame_poses, w.frame_px, stream)
+
+    hv_build_ms = timed(hv_build, 2)
+    rq_hv = dare.make_requests([(hv, w.reslice_poses[i], outs[i], masks[i], w.out_px) for i in range(P)])
+    hv_res_ms = timed(lambda: dare.reslice_batch(rq_hv, params, stream), 2)
+    line["host_volume"] = {"host_bytes": int(hv.info().record_bytes) * int(np.prod(w.grid.dims)),
+                           "device_bytes": int(hv.info().volume_bytes), "build_ms": hv_build_ms,
+                           "reslice_ms_per_plane": hv_res_ms / P, "mpix_s": P * W * H / (hv_res_ms * 1e-3) / 1e6}
+    hv.close()
+
     # --- the paper's timing axis (Sec. 3): interpolation radius.  BOX gives its
     # cubic neighbourhoods (3^3, 5^3, 9^3 voxels); TENT the 2R-wide support
     radius = {}

@@ -158,6 +158,15 @@ typedef struct {
  * window is restored before the call returns.  Not applied on the legacy
  * default (NULL) stream or inside plans. */
 #define DARE_SESSION_L2_PERSIST 2
+/* Keep the records, npix and scalar totals in page-locked host memory mapped
+ * into the device's address space instead of device memory, for volumes
+ * beyond device memory (Sec. 4: growing datasets despite GPU memory limits).
+ * Every kernel reads and writes them in place over the host link, through the
+ * device's caches; results are those of a device-resident session, bit for
+ * bit.  The host memory is not counted by the device-memory budget
+ * (dare_set_memory_budget); the session's volume_bytes counts only its device
+ * part. */
+#define DARE_SESSION_HOST_VOLUME 4
 
 typedef struct {
     dare_grid grid;

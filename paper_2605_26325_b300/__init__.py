@@ -28,6 +28,7 @@ DARE_WEIGHTS_F32, DARE_WEIGHTS_F16 = 0, 1
 DARE_PATH_AUTO, DARE_PATH_PLAIN, DARE_PATH_TILED = 0, 1, 2
 DARE_SESSION_SCALAR = 1
 DARE_SESSION_L2_PERSIST = 2
+DARE_SESSION_HOST_VOLUME = 4
 DARE_EMPTY_FRAME = 0xFFFF
 DARE_FIX_BITS = 20
 DARE_NOALLOC_MAX_FRAMES = 16384

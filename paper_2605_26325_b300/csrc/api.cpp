@@ -264,6 +264,7 @@ struct dare_session_s {
     int64_t version = 0;
     bool fresh = true;                     // no sample stored since create / reset: finalize skips reading records
     int64_t volume_bytes = 0;
+    void* host_vol = nullptr;              // DARE_SESSION_HOST_VOLUME: the mapped host block
     void* ws = nullptr;
     size_t ws_bytes = 0;
     // pinned host staging: [0] frame affines / rotations of a build, [1..8] batch
@@ -843,30 +844,53 @@ dare_status dare_session_create(const dare_session_config* cfg, dare_session* ou
     const size_t b_cnt = align_up(size_t(n_vox) * 4, 256);
     const size_t b_fr = align_up(size_t(cfg->max_frames) * 9 * 8, 256);
     const size_t b_ovf = 256;
-    const size_t total = b_rec + b_np + 2 * b_sc + b_cnt + b_fr + b_ovf;
+    // records, npix and scalar totals: device memory, or mapped host memory (DARE_SESSION_HOST_VOLUME)
+    const bool host_vol = (cfg->flags & DARE_SESSION_HOST_VOLUME) != 0;
+    const size_t b_vol = b_rec + b_np + 2 * b_sc;
+    const size_t total = (host_vol ? 0 : b_vol) + b_cnt + b_fr + b_ovf;
+    uint8_t* vol = nullptr;
+    if (host_vol) {
+        void* h = nullptr;
+        if (cudaHostAlloc(&h, b_vol, cudaHostAllocMapped) != cudaSuccess) {
+            cudaGetLastError();
+            delete s;
+            return fail(DARE_E_OOM, "host volume allocation of %zu bytes failed", b_vol);
+        }
+        void* d = nullptr;
+        if (cudaHostGetDevicePointer(&d, h, 0) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFreeHost(h);
+            delete s;
+            return fail(DARE_E_CUDA, "host volume is not mapped into the device");
+        }
+        s->host_vol = h;
+        vol = static_cast<uint8_t*>(d);
+    }
     dare_status st = admit(static_cast<int64_t>(total));
     if (st != DARE_OK) {
+        if (s->host_vol) cudaFreeHost(s->host_vol);
         delete s;
         return st;
     }
     uint8_t* base = static_cast<uint8_t*>(s->dev_alloc(total, nullptr));
     if (!base) {
         g_in_use -= static_cast<int64_t>(total);
+        if (s->host_vol) cudaFreeHost(s->host_vol);
         delete s;
         return fail(DARE_E_OOM, "volume allocation of %zu bytes failed", total);
     }
     s->allocs.push_back({base, total});
     s->volume_bytes = static_cast<int64_t>(total);
     size_t off = 0;
-    s->rec = base + off;
-    off += b_rec;
-    s->npix = reinterpret_cast<uint16_t*>(base + off);
-    off += b_np;
+    if (!host_vol) {
+        vol = base;
+        off = b_vol;
+    }
+    s->rec = vol;
+    s->npix = reinterpret_cast<uint16_t*>(vol + b_rec);
     if (scalar) {
-        s->ssum = reinterpret_cast<uint32_t*>(base + off);
-        off += b_sc;
-        s->scnt = reinterpret_cast<uint32_t*>(base + off);
-        off += b_sc;
+        s->ssum = reinterpret_cast<uint32_t*>(vol + b_rec + b_np);
+        s->scnt = reinterpret_cast<uint32_t*>(vol + b_rec + b_np + b_sc);
     }
     s->count = reinterpret_cast<int32_t*>(base + off);
     off += b_cnt;
@@ -937,6 +961,10 @@ dare_status dare_session_destroy(dare_session s) {
     if (s->stage) {
         s->dev_free(s->stage, size_t(s->stage_n) * s->stage_slot, s->last_stream);
         g_in_use -= static_cast<int64_t>(size_t(s->stage_n) * s->stage_slot);
+    }
+    if (s->host_vol) {
+        cudaDeviceSynchronize();  // no kernel may still touch the mapped volume
+        cudaFreeHost(s->host_vol);
     }
     if (s->order_ev) cudaEventDestroy(s->order_ev);
     delete s;

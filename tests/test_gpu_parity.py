@@ -423,3 +423,27 @@ def test_l2_persist_mode_same_results(tiny):
         assert np.array_equal(m.cpu().numpy(), mb) and np.array_equal(o.cpu().numpy(), ob)
     a.close()
     b.close()
+
+
+def test_host_volume_session_equals_device(tiny):
+    """DARE_SESSION_HOST_VOLUME: records in mapped host memory give the
+    device-resident session's records and images bit for bit, and the device
+    holds only the session's small tables."""
+    dev = gpu_session(tiny, dare.DARE_F16, 8, flags=dare.DARE_SESSION_SCALAR)
+    host = gpu_session(tiny, dare.DARE_F16, 8, flags=dare.DARE_SESSION_SCALAR | dare.DARE_SESSION_HOST_VOLUME,
+                       chunks=[0, 77, 200])
+    ref = gpu_session(tiny, dare.DARE_F16, 8, flags=dare.DARE_SESSION_SCALAR, chunks=[0, 77, 200])
+    ra, rb = ref.read_records(npix=True, scalar=True), host.read_records(npix=True, scalar=True)
+    for k in ("frame_ids", "npix", "scalar_sum", "scalar_count"):
+        assert np.array_equal(ra[k], rb[k]), k
+    assert np.array_equal(ra["values"].view(np.uint16), rb["values"].view(np.uint16))
+    nv = int(np.prod(tiny.grid.dims))
+    assert dev.info().volume_bytes - host.info().volume_bytes >= nv * (dev.info().record_bytes + 2 * 8)
+    for path in (dare.DARE_PATH_PLAIN, dare.DARE_PATH_TILED):
+        p = dare.params_default(path=path)
+        for T in tiny.reslice_poses[[0, 4, 9]]:
+            o1, m1 = gpu_reslice(ref, T, 96, 80, tiny.out_px, p)
+            o2, m2 = gpu_reslice(host, T, 96, 80, tiny.out_px, p)
+            assert np.array_equal(m1, m2) and np.array_equal(o1, o2)
+    for s in (dev, host, ref):
+        s.close()
