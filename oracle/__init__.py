@@ -22,6 +22,7 @@ import numpy as np
 U8, F16, BF16, F32 = 0, 1, 2, 3
 TENT, BOX, EXP = 0, 1, 2
 BEAM, ELEVATION = 0, 1
+LINEAR, CURVILINEAR = 0, 1
 
 _LIB = None
 
@@ -31,13 +32,17 @@ class _Params(ctypes.Structure):
                 ("thr_normal_deg", ctypes.c_double), ("thr_inplane_deg", ctypes.c_double),
                 ("k_dist", ctypes.c_double), ("unassigned", ctypes.c_double),
                 ("radius", ctypes.c_int32), ("kernel", ctypes.c_int32),
-                ("normal_axis", ctypes.c_int32), ("use_exact", ctypes.c_int32)]
+                ("normal_axis", ctypes.c_int32), ("use_exact", ctypes.c_int32),
+                ("probe", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("apex_x", ctypes.c_double), ("apex_y", ctypes.c_double)]
 
 
 @dataclass
 class Params:
     """Reslicing parameters; defaults are the paper's (Sec. 2.1: k_normal 10,
-    k_inplane 5, thresholds 25 and 15 degrees) with radius 1 voxel."""
+    k_inplane 5, thresholds 25 and 15 degrees) with radius 1 voxel.  probe
+    CURVILINEAR makes the virtual plane a fan of beams from apex_mm (image
+    point, mm)."""
     k_normal: float = 10.0
     k_inplane: float = 5.0
     thr_normal_deg: float = 25.0
@@ -48,11 +53,14 @@ class Params:
     kernel: int = TENT
     normal_axis: int = BEAM
     use_exact: bool = False
+    probe: int = LINEAR
+    apex_mm: tuple = (0.0, 0.0)
 
     def _c(self):
         return _Params(self.k_normal, self.k_inplane, self.thr_normal_deg, self.thr_inplane_deg,
                        self.k_dist, self.unassigned, int(self.radius), int(self.kernel),
-                       int(self.normal_axis), int(bool(self.use_exact)))
+                       int(self.normal_axis), int(bool(self.use_exact)), int(self.probe), 0,
+                       float(self.apex_mm[0]), float(self.apex_mm[1]))
 
 
 def _P(t):
@@ -73,6 +81,8 @@ def _lib():
         lib.ora_build.argtypes = [i32p, ctypes.c_double, dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
                                   ctypes.c_double, ctypes.c_double, u8p, dp, ctypes.c_int32, ctypes.c_int32, u8p]
         lib.ora_build.restype = vp
+        lib.ora_build_probe.argtypes = lib.ora_build.argtypes + [i32p, dp, u8p]
+        lib.ora_build_probe.restype = vp
         lib.ora_volume_manual.argtypes = [i32p, ctypes.c_double, dp, ctypes.c_int64, i64p, i32p, dp, dp]
         lib.ora_volume_manual.restype = vp
         lib.ora_volume_free.argtypes = [vp]
@@ -173,8 +183,13 @@ class Volume:
         return d
 
 
-def build(dims, spacing, vol_to_world, frames, poses, px_mm, dtype=F32, kmax=16, voxel_filter=None):
-    """Reconstruct the directional volume from uint8 frames (n, H, W) and poses (n, 4, 4)."""
+def build(dims, spacing, vol_to_world, frames, poses, px_mm, dtype=F32, kmax=16, voxel_filter=None,
+          probe=None, apex_mm=None, pixel_mask=None):
+    """Reconstruct the directional volume from uint8 frames (n, H, W) and poses (n, 4, 4).
+
+    probe: per-frame LINEAR / CURVILINEAR (a scalar applies to every frame),
+    apex_mm: the fan apex of curvilinear frames, (2,) or (n, 2) image mm;
+    pixel_mask: (H, W), zero excludes that pixel of every frame."""
     frames = _arr(frames, np.uint8)
     n, H, W = frames.shape
     poses = _arr(poses, np.float64).reshape(n, 16)
@@ -185,10 +200,22 @@ def build(dims, spacing, vol_to_world, frames, poses, px_mm, dtype=F32, kmax=16,
         filt = _arr(voxel_filter, np.uint8).reshape(-1)
         if filt.size != int(np.prod(dims)):
             raise ValueError("voxel_filter size")
-    h = _lib().ora_build(_ptr(dims_a, ctypes.c_int32), float(spacing), _ptr(V, ctypes.c_double), n, W, H,
-                         float(px_mm[0]), float(px_mm[1]), _ptr(frames, ctypes.c_uint8),
-                         _ptr(poses, ctypes.c_double), int(dtype), int(kmax),
-                         _ptr(filt, ctypes.c_uint8) if filt is not None else None)
+    kinds = apex = pm = None
+    if probe is not None:
+        kinds = _arr(np.broadcast_to(np.asarray(probe, np.int32), (n,)), np.int32)
+        apex = _arr(np.broadcast_to(np.asarray(apex_mm if apex_mm is not None else (0.0, 0.0), np.float64),
+                                    (n, 2)), np.float64)
+    if pixel_mask is not None:
+        pm = _arr(pixel_mask, np.uint8)
+        if pm.shape != (H, W):
+            raise ValueError("pixel_mask shape")
+    h = _lib().ora_build_probe(_ptr(dims_a, ctypes.c_int32), float(spacing), _ptr(V, ctypes.c_double), n, W, H,
+                               float(px_mm[0]), float(px_mm[1]), _ptr(frames, ctypes.c_uint8),
+                               _ptr(poses, ctypes.c_double), int(dtype), int(kmax),
+                               _ptr(filt, ctypes.c_uint8) if filt is not None else None,
+                               _ptr(kinds, ctypes.c_int32) if kinds is not None else None,
+                               _ptr(apex, ctypes.c_double) if apex is not None else None,
+                               _ptr(pm, ctypes.c_uint8) if pm is not None else None)
     return Volume(h, dims, spacing, vol_to_world)
 
 

@@ -39,7 +39,21 @@
  *   - stored value: RN_fp32(sum/npix), then rounded to the storage type
  *     (u8: round-half-even, clamped to [0,255]; f16 and bf16: RN-even);
  *   - capacity: when a voxel holds more than kmax samples, keep the kmax with
- *     the largest npix (ties: lower frame id), ordered by frame id.
+ *     the largest npix (ties: lower frame id), ordered by frame id;
+ *   - curvilinear probes (an extension: the paper's probe is a linear array,
+ *     Sec. 2.2, whose beam is the image y axis everywhere): the beams fan out
+ *     from an apex a = (a_x, a_y) of the image plane.  The beam through image
+ *     point p runs along (p - a) / |p - a|, i.e. the image axes turned about
+ *     image z by alpha = atan2(-(p_x - a_x), p_y - a_y) (alpha = 0 at p = a).
+ *     A sample's acquisition orientation, the quaternion the paper stores per
+ *     sample, is its frame's quaternion times that turn, taken at the centre
+ *     of the sample's voxel expressed in the frame's image coordinates (the
+ *     in-plane part; the voxel centre lies within half a voxel diagonal of
+ *     the plane).  A curvilinear virtual plane turns its own axes the same
+ *     way at every output pixel, about its own apex.  Eq. 1 and Eq. 2 are
+ *     unchanged, applied to the turned axes;
+ *   - pixel mask: a build may exclude pixels (the dark corners outside a fan
+ *     image); an excluded pixel is never voxelised.
  *
  * Arithmetic is FP64 throughout except the storage rounding, which is the
  * storage type's own.  Compile with -ffp-contract=off.
@@ -58,6 +72,9 @@
 #define ORA_BOX 1
 #define ORA_EXP 2
 
+#define ORA_LINEAR 0
+#define ORA_CURVILINEAR 1
+
 #define FIX_BITS 20
 #define FIX_ONE ((int64_t)1 << FIX_BITS)
 
@@ -70,6 +87,9 @@ typedef struct {
     int32_t kernel;                    /* ORA_TENT / ORA_BOX / ORA_EXP */
     int32_t normal_axis;               /* 0 = beam (R y), 1 = plane normal (R z) */
     int32_t use_exact;                 /* 1: FP64 means instead of stored values */
+    int32_t probe;                     /* virtual probe: ORA_LINEAR / ORA_CURVILINEAR */
+    int32_t pad;
+    double apex_x, apex_y;             /* curvilinear virtual probe: fan apex, image point (mm) */
 } ora_params;
 
 typedef struct {
@@ -172,6 +192,26 @@ static void quat_axis(const double q[4], int axis, double v[3]) {
     }
 }
 
+/* Hamilton product a * b: the rotation b followed by a */
+static void quat_mul(const double a[4], const double b[4], double out[4]) {
+    out[0] = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
+    out[1] = a[0] * b[1] + a[1] * b[0] + a[2] * b[3] - a[3] * b[2];
+    out[2] = a[0] * b[2] - a[1] * b[3] + a[2] * b[0] + a[3] * b[1];
+    out[3] = a[0] * b[3] + a[1] * b[2] - a[2] * b[1] + a[3] * b[0];
+}
+
+/*
+ * Orientation of the beam of a curvilinear probe through image point
+ * (px, py): q turned about its image z axis by the steering angle from the
+ * apex (ax, ay).
+ */
+static void steer(const double q[4], double px, double py, double ax, double ay, double out[4]) {
+    double dx = px - ax, dy = py - ay;
+    double alpha = (dx == 0.0 && dy == 0.0) ? 0.0 : atan2(-dx, dy);
+    double turn[4] = {cos(0.5 * alpha), 0.0, 0.0, sin(0.5 * alpha)};
+    quat_mul(q, turn, out);
+}
+
 /* ------------------------------------------------------------ storage rounding */
 
 static float rn_f32_quotient(int64_t s, int64_t n) { return (float)s / (float)n; }
@@ -248,12 +288,17 @@ static int cmp_int32(const void* a, const void* b) {
  * Reconstruction (Sec. 2.1, Fig. 1).  frames: n x H x W uint8 row-major;
  * poses: n x 16 row-major image->world.  Frame k gets id k.  voxel_filter,
  * when non-NULL, keeps only voxels whose byte is non-zero (used to build the
- * neighbourhood of a few sampled pixels of a large workload).
+ * neighbourhood of a few sampled pixels of a large workload).  probe, when
+ * non-NULL, gives each frame's probe (ORA_LINEAR / ORA_CURVILINEAR) and apex
+ * holds its fan apex (n x 2, image mm); pixel_mask, when non-NULL, is H x W
+ * and a zero byte excludes that pixel of every frame.
  */
-ora_volume* ora_build(const int32_t* dims, double h, const double* V, int32_t n, int32_t W, int32_t H,
-                      double sx, double sy, const uint8_t* frames, const double* poses,
-                      int32_t dtype, int32_t kmax, const uint8_t* voxel_filter) {
+ora_volume* ora_build_probe(const int32_t* dims, double h, const double* V, int32_t n, int32_t W, int32_t H,
+                            double sx, double sy, const uint8_t* frames, const double* poses,
+                            int32_t dtype, int32_t kmax, const uint8_t* voxel_filter, const int32_t* probe,
+                            const double* apex, const uint8_t* pixel_mask) {
     if (dims[0] <= 0 || dims[1] <= 0 || dims[2] <= 0 || n < 0 || W <= 0 || H <= 0 || kmax <= 0) return NULL;
+    if (probe && !apex) return NULL;
     ora_volume* v = vol_alloc(dims, h, V, dtype, kmax);
     if (!v) return NULL;
     const int64_t nx = dims[0], ny = dims[1], nz = dims[2];
@@ -288,6 +333,7 @@ ora_volume* ora_build(const int32_t* dims, double h, const double* V, int32_t n,
             const uint8_t* img = frames + (size_t)f * W * H;
             for (int32_t y = 0; y < H; ++y) {
                 for (int32_t x = 0; x < W; ++x) {
+                    if (pixel_mask && !pixel_mask[(size_t)y * W + x]) continue;
                     int64_t c[3];
                     for (int a = 0; a < 3; ++a) {
                         int64_t G = G0[a] + (int64_t)x * A[a] + (int64_t)y * B[a];
@@ -364,7 +410,22 @@ ora_volume* ora_build(const int32_t* dims, double h, const double* V, int32_t n,
                     v->sum[out] = tmp_sum[j];
                     v->mean_exact[out] = (double)tmp_sum[j] / (double)tmp[j].npix;
                     v->stored[out] = to_stored(rn_f32_quotient(tmp_sum[j], tmp[j].npix), dtype);
-                    memcpy(v->quat + 4 * out, fq + 4 * (size_t)tmp[j].frame, 4 * sizeof(double));
+                    const int32_t fr = tmp[j].frame;
+                    if (probe && probe[fr] == ORA_CURVILINEAR) {
+                        /* voxel centre in world, then in the frame's image coordinates */
+                        const double* T = poses + 16 * (size_t)fr;
+                        double c[3] = {(double)(i % nx), (double)((i / nx) % ny), (double)(i / (nx * ny))};
+                        double w[3], p[2];
+                        for (int r = 0; r < 3; ++r)
+                            w[r] = V[4 * r + 0] * (h * c[0]) + V[4 * r + 1] * (h * c[1]) + V[4 * r + 2] * (h * c[2]) +
+                                   V[4 * r + 3];
+                        for (int k = 0; k < 2; ++k)
+                            p[k] = T[0 * 4 + k] * (w[0] - T[3]) + T[1 * 4 + k] * (w[1] - T[7]) +
+                                   T[2 * 4 + k] * (w[2] - T[11]);
+                        steer(fq + 4 * (size_t)fr, p[0], p[1], apex[2 * fr], apex[2 * fr + 1], v->quat + 4 * out);
+                    } else {
+                        memcpy(v->quat + 4 * out, fq + 4 * (size_t)fr, 4 * sizeof(double));
+                    }
                     ++out;
                 }
             }
@@ -376,6 +437,13 @@ ora_volume* ora_build(const int32_t* dims, double h, const double* V, int32_t n,
     }
     free(aff); free(fq); free(count);
     return v;
+}
+
+/* Reconstruction from linear-array frames, every pixel used. */
+ora_volume* ora_build(const int32_t* dims, double h, const double* V, int32_t n, int32_t W, int32_t H,
+                      double sx, double sy, const uint8_t* frames, const double* poses,
+                      int32_t dtype, int32_t kmax, const uint8_t* voxel_filter) {
+    return ora_build_probe(dims, h, V, n, W, H, sx, sy, frames, poses, dtype, kmax, voxel_filter, NULL, NULL, NULL);
 }
 
 /*
@@ -439,6 +507,8 @@ typedef struct {
     double n_r[3], x_r[3];
     double cos_n, cos_i;
     int use_thr_n, use_thr_i;
+    double q[4];             /* plane orientation in the volume frame */
+    double half_w, sx, sy;   /* pixel (u, v) sits at image point ((u - (W-1)/2) sx, v sy) */
 } plane_ctx;
 
 static void plane_setup(const ora_volume* v, const double* P, int32_t W, double sx, double sy,
@@ -447,6 +517,10 @@ static void plane_setup(const ora_volume* v, const double* P, int32_t W, double 
     double R[9], q[4];
     rel_rotation(v->vol_to_world, P, R);
     mat_to_quat(R, q);
+    memcpy(c->q, q, sizeof(q));
+    c->half_w = 0.5 * (double)(W - 1);
+    c->sx = sx;
+    c->sy = sy;
     quat_axis(q, p->normal_axis == 1 ? 2 : 1, c->n_r);
     quat_axis(q, 0, c->x_r);
     c->use_thr_n = p->thr_normal_deg < 180.0;
@@ -470,8 +544,17 @@ static double orientation_weight(const double* q, const plane_ctx* c, const ora_
     return exp(p->k_normal * (d_normal - 1.0) + p->k_inplane * (d_inplane - 1.0));
 }
 
-static void reslice_pixel(const ora_volume* v, const plane_ctx* c, const ora_params* p, int32_t x, int32_t y,
+static void reslice_pixel(const ora_volume* v, const plane_ctx* c0, const ora_params* p, int32_t x, int32_t y,
                           double* out, uint8_t* mask) {
+    plane_ctx cp = *c0;
+    const plane_ctx* c = &cp;
+    if (p->probe == ORA_CURVILINEAR) {
+        /* a curvilinear virtual plane: this pixel's beam and lateral axes */
+        double qp[4];
+        steer(c0->q, ((double)x - c0->half_w) * c0->sx, (double)y * c0->sy, p->apex_x, p->apex_y, qp);
+        quat_axis(qp, p->normal_axis == 1 ? 2 : 1, cp.n_r);
+        quat_axis(qp, 0, cp.x_r);
+    }
     double g[3];
     for (int a = 0; a < 3; ++a) {
         int64_t G = c->aff[a] + (int64_t)x * c->aff[3 + a] + (int64_t)y * c->aff[6 + a];

@@ -47,6 +47,31 @@ MUTANTS = {
          "return x->frame > y->frame ? -1 : (x->frame < y->frame);"),
     "bf16 storage truncates":
         ("b = (b + 0x7FFFu + lsb) & 0xFFFF0000u;", "b = b & 0xFFFF0000u;"),
+    "fan steering angle sign flipped":
+        ("double alpha = (dx == 0.0 && dy == 0.0) ? 0.0 : atan2(-dx, dy);",
+         "double alpha = (dx == 0.0 && dy == 0.0) ? 0.0 : atan2(dx, dy);"),
+    "fan turn applied before the frame rotation":
+        ("    quat_mul(q, turn, out);\n}", "    quat_mul(turn, q, out);\n}"),
+    "fan turn quaternion without the half angle":
+        ("double turn[4] = {cos(0.5 * alpha), 0.0, 0.0, sin(0.5 * alpha)};",
+         "double turn[4] = {cos(alpha), 0.0, 0.0, sin(alpha)};"),
+    "sample fan taken at the voxel index, not its centre":
+        ("w[r] = V[4 * r + 0] * (h * c[0]) + V[4 * r + 1] * (h * c[1]) + V[4 * r + 2] * (h * c[2]) +",
+         "w[r] = V[4 * r + 0] * c[0] + V[4 * r + 1] * c[1] + V[4 * r + 2] * c[2] +"),
+    "fan apex coordinates swapped":
+        ("steer(fq + 4 * (size_t)fr, p[0], p[1], apex[2 * fr], apex[2 * fr + 1], v->quat + 4 * out);",
+         "steer(fq + 4 * (size_t)fr, p[0], p[1], apex[2 * fr + 1], apex[2 * fr], v->quat + 4 * out);"),
+    "voxel centre rotated into the frame without transposing":
+        ("p[k] = T[0 * 4 + k] * (w[0] - T[3]) + T[1 * 4 + k] * (w[1] - T[7]) +\n"
+         "                                   T[2 * 4 + k] * (w[2] - T[11]);",
+         "p[k] = T[k * 4 + 0] * (w[0] - T[3]) + T[k * 4 + 1] * (w[1] - T[7]) +\n"
+         "                                   T[k * 4 + 2] * (w[2] - T[11]);"),
+    "virtual fan measured from the image corner":
+        ("steer(c0->q, ((double)x - c0->half_w) * c0->sx,", "steer(c0->q, (double)x * c0->sx,"),
+    "virtual fan leaves the lateral axis unturned":
+        ("quat_axis(qp, 0, cp.x_r);", "quat_axis(c0->q, 0, cp.x_r);"),
+    "pixel mask ignored":
+        ("if (pixel_mask && !pixel_mask[(size_t)y * W + x]) continue;", ""),
     "unassigned when the numerator is zero":
         ("    if (den > 0) {\n        *out = num / den;", "    if (num > 0) {\n        *out = num / den;"),
 }

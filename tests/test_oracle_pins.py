@@ -527,3 +527,242 @@ def test_scalar_comparator(tiny):
     ref = ndimage.map_coordinates(arr, gc.reshape(-1, 3).T, order=1).reshape(gc.shape[:2])
     assert np.max(np.abs(out - ref)[full]) < 1e-9
     assert np.all(mask[full] == 1)
+
+
+# ----------------------------------------------------------------- curvilinear probes
+#
+# A curvilinear probe's beams fan out from an apex of the image plane: the
+# beam through image point p runs along (p - a) / |p - a|.  These pins derive
+# the expected axes from positions and plain unit vectors (no angles, no
+# quaternion products), the oracle from steering angles and quaternions.
+
+FAN_APEX = (0.7, -12.0)
+
+
+def fan_beam(px, py, apex):
+    """unit beam direction(s) in image coordinates for a fan from apex"""
+    dx, dy = np.asarray(px, np.float64) - apex[0], np.asarray(py, np.float64) - apex[1]
+    r = np.hypot(dx, dy)
+    return dx / r, dy / r
+
+
+def voxel_centres(idx, dims, spacing, V):
+    c = np.stack([idx % dims[0], (idx // dims[0]) % dims[1], idx // (dims[0] * dims[1])], axis=-1)
+    return (V[:3, :3] @ (spacing * c.astype(np.float64)).T).T + V[:3, 3]
+
+
+def quat_matrices(q):
+    return Rotation.from_quat(np.stack([q[:, 1], q[:, 2], q[:, 3], q[:, 0]], axis=-1)).as_matrix()
+
+
+def test_curvilinear_sample_axes(tiny):
+    """Every sample of a curvilinear frame carries its frame's axes turned in
+    the image plane so that image y runs from the apex through the voxel
+    centre (projected into the frame): beam R (u_x, u_y, 0), lateral
+    R (u_y, -u_x, 0), elevation R z, in the volume frame.  Samples, npix and
+    sums are those of the linear build."""
+    w = tiny
+    n = 6
+    apex = (1.5, -25.0)
+    vol = oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames[:n], w.frame_poses[:n],
+                       w.frame_px, probe=oracle.CURVILINEAR, apex_mm=apex)
+    lin = oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames[:n], w.frame_poses[:n],
+                       w.frame_px)
+    e, el = vol.export(), lin.export()
+    for k in ("offsets", "frame_id", "npix", "sum", "stored"):
+        assert np.array_equal(e[k], el[k]), k
+    V = w.grid.vol_to_world
+    vox = np.repeat(np.arange(len(e["offsets"]) - 1), np.diff(e["offsets"]))
+    ctr = voxel_centres(vox, w.grid.dims, w.grid.spacing, V)
+    T = w.frame_poses[:n][e["frame_id"]]
+    p = np.einsum("nki,nk->ni", T[:, :3, :3], ctr - T[:, :3, 3])  # R_f^T (c - t_f)
+    ux, uy = fan_beam(p[:, 0], p[:, 1], apex)
+    zero = np.zeros_like(ux)
+    R = np.einsum("ji,njk->nik", V[:3, :3], T[:, :3, :3])        # R_v^T R_f
+    beam = np.einsum("nij,nj->ni", R, np.stack([ux, uy, zero], -1))
+    lat = np.einsum("nij,nj->ni", R, np.stack([uy, -ux, zero], -1))
+    M = quat_matrices(e["quat"])
+    assert vox.size > 1000
+    assert np.max(np.abs(M[:, :, 1] - beam)) < 1e-12
+    assert np.max(np.abs(M[:, :, 0] - lat)) < 1e-12
+    assert np.max(np.abs(M[:, :, 2] - R[:, :, 2])) < 1e-12
+    # the fan really turns the beams: tens of degrees across the frame
+    tilt = np.degrees(np.arccos(np.clip(np.einsum("ni,ni->n", M[:, :, 1], R[:, :, 1]), -1, 1)))
+    assert tilt.max() > 15.0
+
+
+def test_curvilinear_limits_and_mask_identity(tiny):
+    """A far apex is the linear probe; an all-ones pixel mask, and an explicit
+    LINEAR probe, change nothing."""
+    w = tiny
+    n = 4
+    args = (w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames[:n], w.frame_poses[:n], w.frame_px)
+    ref = oracle.build(*args).export()
+    far = oracle.build(*args, probe=oracle.CURVILINEAR, apex_mm=(0.0, -1e9)).export()
+    assert np.max(np.abs(quat_matrices(far["quat"]) - quat_matrices(ref["quat"]))) < 1e-7
+    H, W = w.frames.shape[1:]
+    for e in (oracle.build(*args, pixel_mask=np.ones((H, W), np.uint8)).export(),
+              oracle.build(*args, probe=oracle.LINEAR, apex_mm=(3.0, -5.0)).export()):
+        for k in ref:
+            assert np.array_equal(ref[k], e[k]), k
+
+
+def test_pixel_mask_voxelisation(tiny):
+    """Masked pixels are never voxelised: per-voxel totals and per-(voxel, frame)
+    samples equal a numpy group-by over the unmasked pixels only."""
+    w = tiny
+    n = 5
+    H, W = w.frames.shape[1:]
+    rng = np.random.default_rng(41)
+    pm = (rng.random((H, W)) < 0.6).astype(np.uint8)
+    vol = oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames[:n], w.frame_poses[:n],
+                       w.frame_px, pixel_mask=pm)
+    e = vol.export()
+    dims = w.grid.dims
+    nv = int(np.prod(dims))
+    tot_n, tot_s = np.zeros(nv, np.int64), np.zeros(nv, np.int64)
+    keys = {}
+    for f in range(n):
+        aff = oracle.pixel_affine(w.grid.vol_to_world, w.grid.spacing, w.frame_poses[f], W, w.frame_px)
+        G, _ = voxel_coords(aff, W, H)
+        c = np.floor_divide(G + 2**19, 2**20)
+        ok = np.all((c >= 0) & (c < np.array(dims)), axis=-1) & (pm > 0)
+        vi = flat_index(c, dims)[ok]
+        val = w.frames[f][ok].astype(np.int64)
+        np.add.at(tot_n, vi, 1)
+        np.add.at(tot_s, vi, val)
+        for a, b in zip(vi, val):
+            k = (int(a), f)
+            s = keys.setdefault(k, [0, 0])
+            s[0] += 1
+            s[1] += int(b)
+    assert np.array_equal(e["tot_npix"], tot_n)
+    assert np.array_equal(e["tot_sum"], tot_s)
+    vox = np.repeat(np.arange(nv), np.diff(e["offsets"]))
+    got = {(int(a), int(f)): [int(m), int(s)] for a, f, m, s in zip(vox, e["frame_id"], e["npix"], e["sum"])}
+    assert got == keys
+    assert tot_n.sum() < 0.7 * H * W * n
+
+
+def _coplanar_case(seed, frame_curv, out_curv):
+    """One random frame in a rotated 40^3 grid, resliced at its own pose."""
+    rng = np.random.default_rng(seed)
+    h, dims = 0.6, (40, 40, 40)
+    V = synth.make_pose(synth.random_rotation(rng), rng.uniform(-5, 5, 3))
+    W, H, px = 48, 40, (0.3, 0.3)
+    Rrel = synth.random_rotation(rng)
+    c0 = np.array([12.0, 12.0, 12.0]) + rng.uniform(-0.3, 0.3, 3)
+    Tv = synth.make_pose(Rrel, c0 - Rrel @ np.array([0.0, 6.0, 0.0]))
+    T = V @ Tv
+    frame = rng.integers(0, 256, (1, H, W)).astype(np.uint8)
+    vol = oracle.build(dims, h, V, frame, T[None], px, probe=oracle.CURVILINEAR if frame_curv else None,
+                       apex_mm=FAN_APEX)
+    return vol, V, T, W, H, px, dims, h
+
+
+@pytest.mark.parametrize("frame_curv,out_curv", [(True, False), (False, True), (True, True)])
+@pytest.mark.parametrize("normal_axis", [oracle.BEAM, oracle.ELEVATION])
+def test_curvilinear_coplanar_brute_force(frame_curv, out_curv, normal_axis):
+    """Frame and virtual plane share one pose, so every sample's axes and every
+    pixel's axes differ by a turn in the plane: d_normal = u_s . u_p (beam) or
+    1 (elevation), d_inplane = |u_s . u_p|, with u the unit beams of the fan
+    (u = (0, 1) for a linear probe).  Whole plane against a numpy brute force:
+    masks exact, values to 1e-12."""
+    vol, V, T, W, H, px, dims, h = _coplanar_case(500 + 2 * frame_curv + out_curv, frame_curv, out_curv)
+    p = oracle.Params(normal_axis=normal_axis, probe=oracle.CURVILINEAR if out_curv else oracle.LINEAR,
+                      apex_mm=FAN_APEX)
+    out, mask = oracle.reslice(vol, T, W, H, px, p)
+    e = vol.export()
+    aff = oracle.pixel_affine(V, h, T, W, px)
+    _, g = voxel_coords(aff, W, H)
+    # samples: value and beam per voxel (one frame: at most one sample per voxel)
+    nv = int(np.prod(dims))
+    cnt = np.diff(e["offsets"])
+    has = cnt > 0
+    val = np.zeros(nv)
+    val[has] = e["stored"][e["offsets"][:-1][has]]
+    us = np.zeros((nv, 2))
+    us[:, 1] = 1.0
+    if frame_curv:
+        idx = np.nonzero(has)[0]
+        ctr = voxel_centres(idx, dims, h, V)
+        q = (T[:3, :3].T @ (ctr - T[:3, 3]).T).T
+        us[idx] = np.stack(fan_beam(q[:, 0], q[:, 1], FAN_APEX), -1)
+    cn, ci = math.cos(math.radians(25.0)), math.cos(math.radians(15.0))
+    n_on = 0
+    for y in range(H):
+        for x in range(W):
+            up = (0.0, 1.0)
+            if out_curv:
+                up = fan_beam((x - 0.5 * (W - 1)) * px[0], y * px[1], FAN_APEX)
+            f = np.floor(g[y, x]).astype(np.int64)
+            num = den = 0.0
+            for k in range(8):
+                c = f + np.array([k & 1, (k >> 1) & 1, k >> 2])
+                if np.any(c < 0) or np.any(c >= dims):
+                    continue
+                vi = int(c[0] + dims[0] * (c[1] + dims[1] * c[2]))
+                if not has[vi]:
+                    continue
+                t = np.prod(1.0 - np.abs(g[y, x] - c))
+                cosd = us[vi, 0] * up[0] + us[vi, 1] * up[1]
+                dn = cosd if normal_axis == oracle.BEAM else 1.0
+                di = abs(cosd)
+                assert abs(dn - cn) > 1e-9 and abs(di - ci) > 1e-9
+                if dn < cn or di < ci:
+                    continue
+                wgt = math.exp(10.0 * (dn - 1.0) + 5.0 * (di - 1.0))
+                num += t * wgt * val[vi]
+                den += t * wgt
+            m = 1 if den > 0 else 0
+            assert mask[y, x] == m, (x, y)
+            n_on += m
+            if m:
+                assert abs(out[y, x] - num / den) < 1e-12 * 255
+    # one fan against a linear probe keeps and drops pixels; two matching fans keep all
+    assert n_on > 0.2 * W * H
+    assert (n_on < 0.95 * W * H) == (frame_curv != out_curv)
+
+
+@pytest.mark.parametrize("normal_axis,kernel,radius", [(oracle.BEAM, oracle.TENT, 1),
+                                                       (oracle.ELEVATION, oracle.BOX, 1),
+                                                       (oracle.BEAM, oracle.EXP, 2)])
+def test_curvilinear_plane_brute_force_8cube(normal_axis, kernel, radius):
+    """A curvilinear virtual plane in general position over hand-made samples:
+    each pixel's plane orientation is R_plane times the in-plane turn whose
+    columns are (u_y, -u_x, 0), (u_x, u_y, 0), z, built as a matrix and
+    handed to the every-voxel brute force."""
+    rng = np.random.default_rng(900 + 10 * normal_axis + kernel)
+    dims = (8, 8, 8)
+    nv = 512
+    counts = rng.integers(0, 3, nv)
+    voxel = np.repeat(np.arange(nv), counts)
+    base = synth.random_rotation(rng)
+    rots = [synth.rot_axis_angle(rng.normal(size=3), math.radians(rng.uniform(0, 40))) @ base
+            for _ in range(voxel.size)]
+    quats = np.array([quat_wxyz(R) for R in rots])
+    vals = rng.uniform(0, 255, voxel.size)
+    Vp = rigid(rng, 3.0)
+    vol = oracle.volume_from_samples(dims, 0.9, Vp, voxel, np.arange(voxel.size, dtype=np.int32), vals, quats)
+    apex = (0.4, -2.5)
+    p = oracle.Params(radius=radius, kernel=kernel, normal_axis=normal_axis, k_dist=0.7,
+                      probe=oracle.CURVILINEAR, apex_mm=apex)
+    W, H, px = 6, 5, (0.8, 0.7)
+    P = synth.make_pose(Vp[:3, :3] @ base, Vp[:3, :3] @ np.array([3.3, 3.6, 3.4]) * 0.9 + Vp[:3, 3])
+    out, mask = oracle.reslice(vol, P, W, H, px, p)
+    aff = oracle.pixel_affine(Vp, 0.9, P, W, px)
+    _, g = voxel_coords(aff, W, H)
+    samples = {}
+    for s, vi in enumerate(voxel):
+        samples.setdefault((vi % 8, (vi // 8) % 8, vi // 64), []).append((vals[s], tuple(quats[s])))
+    Rp = Vp[:3, :3].T @ P[:3, :3]
+    n_on = 0
+    for y in range(H):
+        for x in range(W):
+            ux, uy = fan_beam((x - 0.5 * (W - 1)) * px[0], y * px[1], apex)
+            turn = np.array([[uy, ux, 0.0], [-ux, uy, 0.0], [0.0, 0.0, 1.0]])
+            ref, m = _brute.reslice_pixel(dims, samples, g[y, x], tuple(quat_wxyz(Rp @ turn)), p)
+            assert mask[y, x] == m
+            n_on += m
+            assert abs(out[y, x] - ref) < 1e-12 * 255
+    assert n_on > 0
