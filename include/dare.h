@@ -60,7 +60,21 @@
  *     valid iff d_normal >= cos(thr_normal) and d_inplane >= cos(thr_inplane)
  *       (a threshold of 180 degrees or more is off)
  *     w_f = exp(k_normal (d_normal - 1) + k_inplane (d_inplane - 1))
- * The decisions are taken in FP64 once per (plane, frame).  With the TENT
+ * The decisions are taken in FP64 once per (plane, frame).
+ *
+ * Curvilinear probes (an extension: the paper's probe is a linear array,
+ * Sec. 2.2).  The beams fan out from an apex a = (a_x, a_y) of the image plane
+ * (image mm; a_y < 0 above the transducer face): the beam through image point
+ * p runs along u = (p - a) / |p - a| (u = (0, 1) at p = a), and the image axes
+ * there are turned about image z: beam R (u_x, u_y, 0), lateral
+ * R (u_y, -u_x, 0), elevation R z.  A sample of a curvilinear frame takes the
+ * turn at the centre of its voxel expressed in the frame's image coordinates
+ * (in-plane part); a curvilinear virtual plane (dare_params.probe) takes it at
+ * every output pixel.  Eq. 1 and Eq. 2 apply to the turned axes, so a
+ * session with curvilinear frames, or a curvilinear virtual probe, evaluates
+ * them per (pixel, sample): in FP32, with a threshold decision re-taken in
+ * FP64 whenever the FP32 dot product lies within its error bound of the
+ * cosine, so that every decision is the FP64 one.  With the TENT
  * distance kernel of radius R = 1 (the default; R is the interpolation
  * distance in voxels) a pixel at g reads the 8 voxels floor(g) + {0,1}^3
  * with trilinear weights t_c, and
@@ -103,7 +117,7 @@
 extern "C" {
 #endif
 
-#define DARE_ABI_VERSION 1
+#define DARE_ABI_VERSION 2
 #define DARE_FIX_BITS 20
 #define DARE_EMPTY_FRAME 0xFFFFu
 #define DARE_MAX_FRAMES 65535
@@ -126,6 +140,15 @@ typedef enum { DARE_TENT = 0, DARE_BOX = 1, DARE_EXP = 2 } dare_dist_kernel;
 typedef enum { DARE_NORMAL_BEAM = 0, DARE_NORMAL_ELEVATION = 1 } dare_normal_axis;
 typedef enum { DARE_WEIGHTS_F32 = 0, DARE_WEIGHTS_F16 = 1 } dare_weight_dtype;
 typedef enum { DARE_PATH_AUTO = 0, DARE_PATH_PLAIN = 1, DARE_PATH_TILED = 2 } dare_path;
+typedef enum { DARE_PROBE_LINEAR = 0, DARE_PROBE_CURVILINEAR = 1 } dare_probe_kind;
+
+/* Probe geometry (see "Curvilinear probes"): kind, and for a curvilinear
+ * probe the apex of its beam fan as an image point (x, y) in mm. */
+typedef struct {
+    int32_t kind;        /* dare_probe_kind */
+    int32_t reserved;
+    double apex_mm[2];
+} dare_probe;
 
 typedef struct dare_session_s* dare_session;
 
@@ -194,7 +217,8 @@ typedef struct {
                                EXP:  as TENT,                          t = exp(-k_dist |g - c| / R) */
     int32_t normal_axis;    /* dare_normal_axis (default BEAM) */
     int32_t weight_dtype;   /* dare_weight_dtype of the per-frame weight table */
-    int32_t path;           /* dare_path: kernel choice */
+    int32_t path;           /* dare_path: kernel choice (linear probes) */
+    dare_probe probe;       /* virtual probe of the planes (default linear) */
 } dare_params;
 
 /* A virtual image plane: output size, pixel spacing and pose. */
@@ -303,6 +327,18 @@ dare_status dare_build_volume(dare_session s, const uint8_t* frames_dev, int32_t
                               void* stream);
 
 /*
+ * Probe of the frames appended from now on (default: linear, every pixel).
+ * probe->kind DARE_PROBE_CURVILINEAR gives those frames the fan of apex
+ * probe->apex_mm.  pixel_mask (host, height x width bytes, row-major; NULL
+ * for none) excludes the pixels whose byte is 0 from voxelisation, e.g. the
+ * dark corners outside a fan image; later builds must then use frames of
+ * exactly width x height (DARE_E_INVALID otherwise).  The mask is copied
+ * before return.  Waits for the session's queued work (synchronous).
+ */
+dare_status dare_session_set_probe(dare_session s, const dare_probe* probe, const uint8_t* pixel_mask,
+                                   int32_t width, int32_t height);
+
+/*
  * Reslicing (Sec. 2.1, Eq. 1, Eq. 2, Fig. 2) of one plane into out_dev /
  * mask_dev (see Layouts).  Every distance kernel (TENT, BOX, EXP) runs on
  * both paths for radius_vox 1..16 (the tiled kernel up to a support of 9
@@ -370,7 +406,9 @@ dare_status dare_reslice_batch_host(const dare_reslice_req* reqs, int32_t n, con
  * dare_plan_launch replays the graph on `stream`; each result equals
  * dare_reslice of that request.  A session whose frame count changed since
  * the plan was created makes launch fail with DARE_E_STATE (re-create the
- * plan); rebuilding it to the same frame count is fine.
+ * plan); rebuilding it to the same frame count is fine.  Plans cover linear
+ * probes: a request whose session holds curvilinear frames, or a curvilinear
+ * params->probe, gives DARE_E_UNSUPPORTED (use dare_reslice_batch).
  */
 typedef struct dare_plan_s* dare_plan;
 
@@ -460,6 +498,8 @@ dare_status dare_server_destroy(dare_server sv);
  * looks up the array's device address on that device (no allocation); make
  * that first call before any stream capture.  The session, its volume and
  * the outputs must already exist; this call allocates nothing itself.
+ * Linear probes only: curvilinear frames or a curvilinear params->probe give
+ * DARE_E_UNSUPPORTED.
  */
 #define DARE_NOALLOC_MAX_FRAMES 16384
 dare_status dare_reslice_noalloc(dare_session s, const dare_plane* plane, const dare_params* params,

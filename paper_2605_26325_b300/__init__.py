@@ -26,6 +26,7 @@ DARE_TENT, DARE_BOX, DARE_EXP = 0, 1, 2
 DARE_NORMAL_BEAM, DARE_NORMAL_ELEVATION = 0, 1
 DARE_WEIGHTS_F32, DARE_WEIGHTS_F16 = 0, 1
 DARE_PATH_AUTO, DARE_PATH_PLAIN, DARE_PATH_TILED = 0, 1, 2
+DARE_PROBE_LINEAR, DARE_PROBE_CURVILINEAR = 0, 1
 DARE_SESSION_SCALAR = 1
 DARE_SESSION_L2_PERSIST = 2
 DARE_SESSION_HOST_VOLUME = 4
@@ -67,12 +68,16 @@ class dare_session_config(ctypes.Structure):
                 ("reserved", ctypes.c_int32), ("alloc", dare_allocator)]
 
 
+class dare_probe(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("reserved", ctypes.c_int32), ("apex_mm", ctypes.c_double * 2)]
+
+
 class dare_params(ctypes.Structure):
     _fields_ = [("k_normal", ctypes.c_double), ("k_inplane", ctypes.c_double),
                 ("thr_normal_deg", ctypes.c_double), ("thr_inplane_deg", ctypes.c_double),
                 ("k_dist", ctypes.c_double), ("unassigned", ctypes.c_float), ("radius_vox", ctypes.c_int32),
                 ("dist_kernel", ctypes.c_int32), ("normal_axis", ctypes.c_int32),
-                ("weight_dtype", ctypes.c_int32), ("path", ctypes.c_int32)]
+                ("weight_dtype", ctypes.c_int32), ("path", ctypes.c_int32), ("probe", dare_probe)]
 
 
 class dare_plane(ctypes.Structure):
@@ -136,6 +141,7 @@ _SIGNATURES = {
     "dare_session_query": ([_vp, _P(dare_session_info)], ctypes.c_int),
     "dare_session_read_records": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "dare_session_read_frames": ([_vp, _P(ctypes.c_double)], ctypes.c_int),
+    "dare_session_set_probe": ([_vp, _P(dare_probe), _vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "dare_session_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "dare_session_load": ([_P(dare_session_config), ctypes.c_char_p, _P(_vp)], ctypes.c_int),
     "dare_build_volume": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_double),
@@ -231,13 +237,24 @@ def make_plane(width, height, px_mm, image_to_world) -> dare_plane:
     return p
 
 
-def params_default(**overrides) -> dare_params:
+def make_probe(kind=DARE_PROBE_LINEAR, apex_mm=(0.0, 0.0)) -> dare_probe:
+    pr = dare_probe()
+    pr.kind = int(kind)
+    pr.apex_mm[0], pr.apex_mm[1] = float(apex_mm[0]), float(apex_mm[1])
+    return pr
+
+
+def params_default(probe_apex_mm=None, **overrides) -> dare_params:
+    """The paper's parameters with overrides by field name; probe_apex_mm=(x, y)
+    makes the virtual probe curvilinear with that fan apex (image mm)."""
     p = dare_params()
     check(lib().dare_params_default(ctypes.byref(p)), "dare_params_default")
     for k, v in overrides.items():
         if not hasattr(p, k):
             raise AttributeError(k)
         setattr(p, k, v)
+    if probe_apex_mm is not None:
+        p.probe = make_probe(DARE_PROBE_CURVILINEAR, probe_apex_mm)
     return p
 
 
@@ -408,6 +425,20 @@ class Session:
 
     def reset(self, stream=None):
         check(lib().dare_session_reset(self._h, _stream_ptr(stream)), "dare_session_reset")
+
+    def set_probe(self, kind=DARE_PROBE_LINEAR, apex_mm=(0.0, 0.0), pixel_mask=None):
+        """Probe of the frames built from now on: DARE_PROBE_CURVILINEAR fans the
+        beams from apex_mm (image x, y in mm); pixel_mask (H, W), zero bytes
+        excluded from voxelisation (e.g. outside the fan)."""
+        pr = make_probe(kind, apex_mm)
+        if pixel_mask is None:
+            check(lib().dare_session_set_probe(self._h, ctypes.byref(pr), None, 0, 0), "dare_session_set_probe")
+            return
+        m = np.ascontiguousarray(np.asarray(pixel_mask, dtype=np.uint8))
+        if m.ndim != 2:
+            raise ValueError("pixel_mask must be (H, W)")
+        check(lib().dare_session_set_probe(self._h, ctypes.byref(pr), m.ctypes.data_as(ctypes.c_void_p),
+                                           m.shape[1], m.shape[0]), "dare_session_set_probe")
 
     def read_records(self, npix=False, scalar=False):
         """Host copies of the volume: dict(frame_ids (n_vox, K) uint16, values (n_vox, K),

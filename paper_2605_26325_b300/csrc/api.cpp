@@ -101,6 +101,45 @@ void relative_rotation(const double* V, const double* T, double R[9]) {
             R[3 * r + c] = V[0 * 4 + r] * T[0 * 4 + c] + V[1 * 4 + r] * T[1 * 4 + c] + V[2 * 4 + r] * T[2 * 4 + c];
 }
 
+// Apex-relative image coordinates of voxel centres in a frame: for voxel c,
+// p_x = h sum_r R[r][0] c_r + off[0], p_y = h sum_r R[r][1] c_r + off[1], with
+// R = R_v^T R_f (row-major) and tm = R_v^T (t_f - t_v): p = R^T (h c - tm) - apex.
+void probe_offsets(const double* V, const double* T, const double R[9], const double apex[2], double off[2]) {
+    double d[3], tm[3];
+    for (int k = 0; k < 3; ++k) d[k] = T[4 * k + 3] - V[4 * k + 3];
+    for (int r = 0; r < 3; ++r) tm[r] = V[0 * 4 + r] * d[0] + V[1 * 4 + r] * d[1] + V[2 * 4 + r] * d[2];
+    for (int c = 0; c < 2; ++c) off[c] = -(R[c] * tm[0] + R[3 + c] * tm[1] + R[6 + c] * tm[2]) - apex[c];
+}
+
+// FP32 geometry row of a frame for the curvilinear kernel (layout in
+// dare_internal.h).  k1 = 17 eps S bounds the FP32 direction error times |p|,
+// S the largest operand sum of the point computation over the grid.
+void geometry_row(const dare_grid& g, const double R[9], int kind, const double off[2], float* row) {
+    const double h = g.spacing_mm;
+    std::fill(row, row + kGeomFloats, 0.0f);
+    if (kind == DARE_PROBE_CURVILINEAR) {
+        double S = 0.0;
+        for (int c = 0; c < 2; ++c) {
+            double sum = std::fabs(off[c]);
+            for (int r = 0; r < 3; ++r) {
+                row[4 * c + r] = static_cast<float>(h * R[3 * r + c]);
+                sum += std::fabs(h * R[3 * r + c]) * static_cast<double>(std::max(g.dims[r] - 1, 0));
+            }
+            row[4 * c + 3] = static_cast<float>(off[c]);
+            S = std::max(S, sum);
+        }
+        row[17] = static_cast<float>(17.0 * std::ldexp(1.0, -24) * S * (1.0 + 1e-6));
+        row[18] = 1.0f;
+    } else {
+        row[7] = 1.0f;  // p = (0, 1): the beam is image y
+    }
+    for (int r = 0; r < 3; ++r) {
+        row[8 + r] = static_cast<float>(R[3 * r + 0]);
+        row[11 + r] = static_cast<float>(R[3 * r + 1]);
+        row[14 + r] = static_cast<float>(R[3 * r + 2]);
+    }
+}
+
 // Largest coefficient magnitude that keeps g = G0 + u A + v B inside int64
 // for any u, v < 2^16 (and keeps voxel coordinates far from overflow).
 constexpr double kMaxFix = 9.0e15;
@@ -258,8 +297,16 @@ struct dare_session_s {
     uint32_t* scnt = nullptr;
     int32_t* count = nullptr;              // scatter counters, all zero between calls
     double* frames_dev = nullptr;          // max_frames x 9
+    float* geom_dev = nullptr;             // max_frames x kGeomFloats: probe geometry (curvilinear kernel)
+    double* geom_off_dev = nullptr;        // max_frames x 2: its FP64 apex-relative offsets
     unsigned long long* overflow_dev = nullptr;
     std::vector<double> frames_host;       // n_frames x 9
+    std::vector<double> probe_host;        // n_frames x 3: probe kind, FP64 offsets
+    int32_t n_curv = 0;                    // frames from a curvilinear probe
+    dare_probe probe{};                    // probe of the frames appended from now on
+    uint32_t* pix_mask = nullptr;          // its pixel mask (device bitmap), or NULL
+    size_t pix_mask_bytes = 0;
+    int32_t pm_w = 0, pm_h = 0;
     int32_t n_frames = 0;
     int64_t version = 0;
     bool fresh = true;                     // no sample stored since create / reset: finalize skips reading records
@@ -442,6 +489,9 @@ dare_status check_params(const dare_params* p) {
     if (p->path < 0 || p->path > 2) return fail(DARE_E_INVALID, "unknown path");
     if (p->radius_vox > 16) return fail(DARE_E_UNSUPPORTED, "radius_vox above 16 is not implemented");
     if (p->dist_kernel == DARE_EXP && !(p->k_dist >= 0)) return fail(DARE_E_INVALID, "k_dist must be >= 0");
+    if (p->probe.kind != DARE_PROBE_LINEAR && p->probe.kind != DARE_PROBE_CURVILINEAR)
+        return fail(DARE_E_INVALID, "unknown virtual probe kind %d", p->probe.kind);
+    if (!finite_all(p->probe.apex_mm, 2)) return fail(DARE_E_INVALID, "virtual probe apex is not finite");
     return DARE_OK;
 }
 
@@ -600,6 +650,48 @@ cudaError_t launch_one(ResliceJob& job, const dare_plane* plane, const dare_para
     return launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, K, dtype, half_w, st);
 }
 
+// Curvilinear kernel (kernels_curv.cu) for this session and params: the
+// session holds frames of a curvilinear probe, or the virtual probe is one.
+bool curv_path(const dare_session s, const dare_params* p) {
+    return s->n_curv > 0 || p->probe.kind == DARE_PROBE_CURVILINEAR;
+}
+
+CurvJob make_curv_job(const dare_session s, const dare_plane* pl, float* out, uint32_t* mask, const dare_params* p) {
+    CurvJob c{};
+    c.j = make_job(s, pl, nullptr, out, mask, p->unassigned, p);
+    c.geom = reinterpret_cast<const float4*>(s->geom_dev);
+    c.rot64 = s->frames_dev;
+    c.off64 = s->geom_off_dev;
+    relative_rotation(s->cfg.grid.vol_to_world, pl->image_to_world, c.R);
+    c.h = s->cfg.grid.spacing_mm;
+    c.half_w = 0.5 * static_cast<double>(pl->width - 1);
+    c.sx = pl->px_mm[0];
+    c.sy = pl->px_mm[1];
+    c.curv_out = p->probe.kind == DARE_PROBE_CURVILINEAR;
+    c.ax = c.curv_out ? p->probe.apex_mm[0] : 0.0;
+    c.ay = c.curv_out ? p->probe.apex_mm[1] : 0.0;
+    for (int i = 0; i < 9; ++i) c.Rf[i] = static_cast<float>(c.R[i]);
+    // pixel (u, v) relative to the virtual apex: (u sx + ox, v sy + oy)
+    const double ox = -c.half_w * c.sx - c.ax, oy = -c.ay;
+    c.oxf = static_cast<float>(ox);
+    c.oyf = static_cast<float>(oy);
+    c.sxf = static_cast<float>(c.sx);
+    c.syf = static_cast<float>(c.sy);
+    const double S = std::max(std::fabs(static_cast<double>(pl->width - 1) * c.sx) + std::fabs(ox),
+                              std::fabs(static_cast<double>(pl->height - 1) * c.sy) + std::fabs(oy));
+    c.k1p = c.curv_out ? static_cast<float>(17.0 * std::ldexp(1.0, -24) * S * (1.0 + 1e-6)) : 0.0f;
+    c.k_n = static_cast<float>(p->k_normal);
+    c.k_i = static_cast<float>(p->k_inplane);
+    c.use_n = p->thr_normal_deg < 180.0;
+    c.use_i = p->thr_inplane_deg < 180.0;
+    c.cos_n64 = std::cos(p->thr_normal_deg * (M_PI / 180.0));
+    c.cos_i64 = std::cos(p->thr_inplane_deg * (M_PI / 180.0));
+    c.cos_n = static_cast<float>(c.cos_n64);
+    c.cos_i = static_cast<float>(c.cos_i64);
+    c.elevation = p->normal_axis == DARE_NORMAL_ELEVATION;
+    return c;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- batch helpers (shared with the server)
@@ -631,7 +723,8 @@ void batch_sizes(const dare_reslice_req* reqs, int32_t n, const dare_params* par
     for (int32_t i = 0; i < n; ++i) o = align_up(o + size_t(std::max(reqs[i].session->n_frames, 1)) * wb, 256);
     const size_t o_tj = o;
     const size_t o_rj = align_up(o_tj + size_t(n) * sizeof(TableJob), 256);
-    *ws_need = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    const size_t o_cj = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    *ws_need = align_up(o_cj + size_t(n) * sizeof(CurvJob), 256);
     *desc_bytes = *ws_need - o_tj;
 }
 
@@ -651,17 +744,27 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
     }
     const size_t o_tj = o;
     const size_t o_rj = align_up(o_tj + size_t(n) * sizeof(TableJob), 256);
-    const size_t desc_bytes = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256) - o_tj;
+    const size_t o_cj = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    const size_t desc_bytes = align_up(o_cj + size_t(n) * sizeof(CurvJob), 256) - o_tj;
     auto* tjs = reinterpret_cast<TableJob*>(pin);
     auto* rjs = reinterpret_cast<ResliceJob*>(pin + (o_rj - o_tj));
-    // order jobs by (K, dtype) so each launch covers one group
+    auto* cjs = reinterpret_cast<CurvJob*>(pin + (o_cj - o_tj));
+    // order jobs by (kernel family, K, dtype) so each launch covers one group
     std::vector<int32_t> order(n);
-    for (int32_t i = 0; i < n; ++i) order[i] = i;
+    std::vector<char> curv(n);
+    for (int32_t i = 0; i < n; ++i) {
+        order[i] = i;
+        curv[i] = curv_path(reqs[i].session, params) ? 1 : 0;
+    }
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         const auto* sa = reqs[a].session;
         const auto* sb = reqs[b].session;
+        if (curv[a] != curv[b]) return curv[a] < curv[b];
         return sa->K != sb->K ? sa->K < sb->K : sa->dtype < sb->dtype;
     });
+    max_frames = 0;
+    for (int32_t i = 0; i < n; ++i)
+        if (!curv[i]) max_frames = std::max(max_frames, reqs[i].session->n_frames);
     const bool general = general_support(params);
     const int th = general ? kTileHGeneral : kTileH;
     int total_tiles = 0;
@@ -672,17 +775,19 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
         plane_vectors(r.session, &r.plane, params->normal_axis, &tj);
         tj.frames = r.session->frames_dev;
         tj.wtab = wtab;
-        tj.n_frames = r.session->n_frames;
+        tj.n_frames = curv[order[k]] ? 0 : r.session->n_frames;  // the curvilinear kernel needs no table
         tjs[k] = tj;
         rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, params->unassigned, params);
+        if (curv[order[k]]) cjs[k] = make_curv_job(r.session, &r.plane, r.out, r.mask, params);
         rjs[k].tile_base = total_tiles;
-        total_tiles += tiles_of(&r.plane, th);
+        if (!curv[order[k]]) total_tiles += tiles_of(&r.plane, th);
     }
     int col_cap = 0, slot_cap = 0;
     if (general) general_caps(rjs, n, &col_cap, &slot_cap);
     CUDA_TRY(cudaMemcpyAsync(ws + o_tj, pin, desc_bytes, cudaMemcpyHostToDevice, st));
     const auto* tj_dev = reinterpret_cast<const TableJob*>(ws + o_tj);
     const auto* rj_dev = reinterpret_cast<const ResliceJob*>(ws + o_rj);
+    const auto* cj_dev = reinterpret_cast<const CurvJob*>(ws + o_cj);
     if (max_frames > 0) {
         KernelScope ks("weight_table", st, 1);
         CUDA_TRY(launch_weight_tables(tj_dev, nullptr, n, max_frames, table_params(params), st));
@@ -692,12 +797,17 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
         const auto* sg = reqs[order[k0]].session;
         int32_t k1 = k0;
         int max_w = 0, max_h = 0;
-        while (k1 < n && reqs[order[k1]].session->K == sg->K && reqs[order[k1]].session->dtype == sg->dtype) {
+        const char cg = curv[order[k0]];
+        while (k1 < n && curv[order[k1]] == cg && reqs[order[k1]].session->K == sg->K &&
+               reqs[order[k1]].session->dtype == sg->dtype) {
             max_w = std::max(max_w, reqs[order[k1]].plane.width);
             max_h = std::max(max_h, reqs[order[k1]].plane.height);
             ++k1;
         }
-        if (use_tiled(params)) {
+        if (cg) {
+            KernelScope ks("reslice_curv", st, 1);
+            CUDA_TRY(launch_reslice_curv(cj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, st));
+        } else if (use_tiled(params)) {
             const int base = rjs[k0].tile_base;
             const int end = (k1 < n) ? rjs[k1].tile_base : total_tiles;
             // same tile count for every job of the group: 2-D grid without a job search
@@ -843,11 +953,13 @@ dare_status dare_session_create(const dare_session_config* cfg, dare_session* ou
     const size_t b_sc = scalar ? align_up(size_t(n_vox) * 4, 256) : 0;
     const size_t b_cnt = align_up(size_t(n_vox) * 4, 256);
     const size_t b_fr = align_up(size_t(cfg->max_frames) * 9 * 8, 256);
+    const size_t b_geo = align_up(size_t(cfg->max_frames) * kGeomFloats * 4, 256);
+    const size_t b_goff = align_up(size_t(cfg->max_frames) * 2 * 8, 256);
     const size_t b_ovf = 256;
     // records, npix and scalar totals: device memory, or mapped host memory (DARE_SESSION_HOST_VOLUME)
     const bool host_vol = (cfg->flags & DARE_SESSION_HOST_VOLUME) != 0;
     const size_t b_vol = b_rec + b_np + 2 * b_sc;
-    const size_t total = (host_vol ? 0 : b_vol) + b_cnt + b_fr + b_ovf;
+    const size_t total = (host_vol ? 0 : b_vol) + b_cnt + b_fr + b_geo + b_goff + b_ovf;
     uint8_t* vol = nullptr;
     if (host_vol) {
         void* h = nullptr;
@@ -896,6 +1008,10 @@ dare_status dare_session_create(const dare_session_config* cfg, dare_session* ou
     off += b_cnt;
     s->frames_dev = reinterpret_cast<double*>(base + off);
     off += b_fr;
+    s->geom_dev = reinterpret_cast<float*>(base + off);
+    off += b_geo;
+    s->geom_off_dev = reinterpret_cast<double*>(base + off);
+    off += b_goff;
     s->overflow_dev = reinterpret_cast<unsigned long long*>(base + off);
     auto bail = [&](dare_status code) {
         dare_session_destroy(s);
@@ -965,6 +1081,10 @@ dare_status dare_session_destroy(dare_session s) {
     if (s->host_vol) {
         cudaDeviceSynchronize();  // no kernel may still touch the mapped volume
         cudaFreeHost(s->host_vol);
+    }
+    if (s->pix_mask) {
+        s->dev_free(s->pix_mask, s->pix_mask_bytes, s->last_stream);
+        g_in_use -= static_cast<int64_t>(s->pix_mask_bytes);
     }
     if (s->order_ev) cudaEventDestroy(s->order_ev);
     delete s;
@@ -1053,10 +1173,16 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     const int64_t tiles_pf = int64_t((width + kScatterTile - 1) / kScatterTile) * ((height + kScatterTile - 1) / kScatterTile);
     const int64_t slots_pf = tiles_pf * kScatterTile * kScatterTile;
     if (slots_pf > kMaxPixelsPerChunk) return fail(DARE_E_INVALID, "frame too large");
+    if (s->pix_mask && (width != s->pm_w || height != s->pm_h))
+        return fail(DARE_E_INVALID, "frames are %dx%d but the pixel mask is %dx%d", width, height, s->pm_w, s->pm_h);
     const double* V = s->cfg.grid.vol_to_world;
     const double h = s->cfg.grid.spacing_mm;
     std::vector<int64_t> aff(size_t(n) * 9);
     std::vector<double> rot(size_t(n) * 9);
+    // probe geometry of the new frames: FP32 rows, FP64 offsets, (kind, offsets) for save / load
+    std::vector<float> grow(size_t(n) * kGeomFloats);
+    std::vector<double> goff(size_t(n) * 2), prow(size_t(n) * 3);
+    const int kind = s->probe.kind;
     for (int32_t f = 0; f < n; ++f) {
         const double* T = image_to_world + 16 * size_t(f);
         if (!rigid_ok(T)) return fail(DARE_E_INVALID, "frame pose %d is not a rigid transform", f);
@@ -1064,6 +1190,11 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
             return fail(DARE_E_INVALID, "frame %d too far from the grid for fixed-point coordinates", f);
         compose_affine(V, h, T, width, px_mm[0], px_mm[1], &aff[9 * size_t(f)]);
         relative_rotation(V, T, &rot[9 * size_t(f)]);
+        probe_offsets(V, T, &rot[9 * size_t(f)], s->probe.apex_mm, &goff[2 * size_t(f)]);
+        geometry_row(s->cfg.grid, &rot[9 * size_t(f)], kind, &goff[2 * size_t(f)], &grow[size_t(f) * kGeomFloats]);
+        prow[3 * size_t(f)] = kind;
+        prow[3 * size_t(f) + 1] = goff[2 * size_t(f)];
+        prow[3 * size_t(f) + 2] = goff[2 * size_t(f) + 1];
     }
     DeviceGuard dg(s->cfg.device);
     if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
@@ -1096,7 +1227,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                           {s->ring_free[0], s->ring_free[1], s->ring_full[0], s->ring_full[1]}, st);
         if (rc != DARE_OK) return rc;
     }
-    rc = ensure_pinned(s, 0, size_t(n) * 9 * 8 * 2);
+    rc = ensure_pinned(s, 0, size_t(n) * (9 * 8 * 2 + kGeomFloats * 4 + 2 * 8));
     if (rc != DARE_OK) return rc;
     uint8_t* ws = static_cast<uint8_t*>(s->ws);
     int32_t* offsets = reinterpret_cast<int32_t*>(ws + o_off);
@@ -1106,10 +1237,17 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     auto* n_pairs = reinterpret_cast<int32_t*>(ws + o_np);
     int64_t* aff_dev = reinterpret_cast<int64_t*>(ws + o_aff);
     uint8_t* pin = static_cast<uint8_t*>(s->pinned[0]);
+    const size_t p_rot = aff.size() * 8, p_geo = p_rot + rot.size() * 8, p_off = p_geo + grow.size() * 4;
     std::memcpy(pin, aff.data(), aff.size() * 8);
-    std::memcpy(pin + aff.size() * 8, rot.data(), rot.size() * 8);
+    std::memcpy(pin + p_rot, rot.data(), rot.size() * 8);
+    std::memcpy(pin + p_geo, grow.data(), grow.size() * 4);
+    std::memcpy(pin + p_off, goff.data(), goff.size() * 8);
     CUDA_TRY(cudaMemcpyAsync(aff_dev, pin, aff.size() * 8, cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaMemcpyAsync(s->frames_dev + size_t(s->n_frames) * 9, pin + aff.size() * 8, rot.size() * 8,
+    CUDA_TRY(cudaMemcpyAsync(s->frames_dev + size_t(s->n_frames) * 9, pin + p_rot, rot.size() * 8,
+                             cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(s->geom_dev + size_t(s->n_frames) * kGeomFloats, pin + p_geo, grow.size() * 4,
+                             cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaMemcpyAsync(s->geom_off_dev + size_t(s->n_frames) * 2, pin + p_off, goff.size() * 8,
                              cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaEventRecord(s->pinned_ev[0], st));
     for (int32_t c0 = 0; c0 < n; c0 += n_chunk) {
@@ -1122,6 +1260,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
         a.height = height;
         for (int k = 0; k < 3; ++k) a.dims[k] = s->cfg.grid.dims[k];
         a.frame_base = s->n_frames + c0;
+        a.pix_mask = s->pix_mask;
         a.small_steps = 1;
         for (int32_t f = c0; f < c0 + nc; ++f)
             for (int k = 3; k < 9; ++k)
@@ -1172,6 +1311,8 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     rc = session_end(s, st);
     if (rc != DARE_OK) return rc;
     s->frames_host.insert(s->frames_host.end(), rot.begin(), rot.end());
+    s->probe_host.insert(s->probe_host.end(), prow.begin(), prow.end());
+    if (kind == DARE_PROBE_CURVILINEAR) s->n_curv += n;
     s->n_frames += n;
     s->version += 1;
     return DARE_OK;
@@ -1192,6 +1333,53 @@ dare_status dare_build_volume_host(dare_session s, const uint8_t* frames_host, i
     return build_impl(s, frames_host, true, n, width, height, px_mm, image_to_world, slice_frames, stream);
 }
 
+dare_status dare_session_set_probe(dare_session s, const dare_probe* probe, const uint8_t* pixel_mask,
+                                   int32_t width, int32_t height) {
+    if (!s || !probe) return fail(DARE_E_INVALID, "NULL argument");
+    if (probe->kind != DARE_PROBE_LINEAR && probe->kind != DARE_PROBE_CURVILINEAR)
+        return fail(DARE_E_INVALID, "unknown probe kind %d", probe->kind);
+    if (!finite_all(probe->apex_mm, 2)) return fail(DARE_E_INVALID, "probe apex is not finite");
+    if (pixel_mask && (width < 1 || height < 1 || width > 65535 || height > 65535))
+        return fail(DARE_E_INVALID, "pixel mask size %dx%d outside [1, 65535]", width, height);
+    DeviceGuard dg(s->cfg.device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
+    CUDA_TRY(cudaEventSynchronize(s->order_ev));  // queued builds may still read the old mask
+    if (s->pix_mask) {
+        s->dev_free(s->pix_mask, s->pix_mask_bytes, s->last_stream);
+        g_in_use -= static_cast<int64_t>(s->pix_mask_bytes);
+        s->pix_mask = nullptr;
+        s->pix_mask_bytes = 0;
+        s->pm_w = s->pm_h = 0;
+    }
+    if (pixel_mask) {
+        const int words = (width + 31) / 32;
+        std::vector<uint32_t> bits(size_t(words) * height, 0u);
+        for (int32_t y = 0; y < height; ++y)
+            for (int32_t x = 0; x < width; ++x)
+                if (pixel_mask[size_t(y) * width + x]) bits[size_t(y) * words + x / 32] |= 1u << (x % 32);
+        const size_t bytes = align_up(bits.size() * 4, 256);
+        dare_status rc = admit(static_cast<int64_t>(bytes));
+        if (rc != DARE_OK) return rc;
+        auto* d = static_cast<uint32_t*>(s->dev_alloc(bytes, nullptr));
+        if (!d) {
+            g_in_use -= static_cast<int64_t>(bytes);
+            return fail(DARE_E_OOM, "pixel mask allocation failed");
+        }
+        if (cudaMemcpy(d, bits.data(), bits.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
+            cudaError_t e = cudaGetLastError();
+            s->dev_free(d, bytes, nullptr);
+            g_in_use -= static_cast<int64_t>(bytes);
+            return fail(DARE_E_CUDA, "pixel mask upload failed: %s", cudaGetErrorString(e));
+        }
+        s->pix_mask = d;
+        s->pix_mask_bytes = bytes;
+        s->pm_w = width;
+        s->pm_h = height;
+    }
+    s->probe = *probe;
+    return DARE_OK;
+}
+
 
 dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
                          uint32_t* mask_dev, void* stream) {
@@ -1209,6 +1397,13 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = session_begin(s, st);
     if (rc != DARE_OK) return rc;
+    if (curv_path(s, params)) {
+        const CurvJob cj = make_curv_job(s, plane, out_dev, mask_dev, params);
+        L2Window l2((s->cfg.flags & DARE_SESSION_L2_PERSIST) ? s->rec : nullptr, size_t(s->n_vox) * s->rec_bytes, st);
+        KernelScope ks("reslice_curv", st, 1);
+        CUDA_TRY(launch_reslice_curv(nullptr, &cj, 1, plane->width, plane->height, s->K, s->dtype, st));
+        return session_end(s, st);
+    }
     const int wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
     rc = ensure_workspace(s, align_up(size_t(std::max(s->n_frames, 1)) * wb, 256), st);
     if (rc != DARE_OK) return rc;
@@ -1435,6 +1630,8 @@ dare_status dare_session_reset(dare_session s, void* stream) {
     rc = session_end(s, st);
     if (rc != DARE_OK) return rc;
     s->frames_host.clear();
+    s->probe_host.clear();
+    s->n_curv = 0;
     s->n_frames = 0;
     s->version = 0;
     s->fresh = true;
@@ -1495,6 +1692,9 @@ struct FileHeader {
     uint32_t crc;           // CRC-32 of everything after the header
     uint32_t reserved;
 };
+// flags bit: a probe section (n_frames x 3 FP64: kind, apex-relative offsets)
+// follows the frame table; files without it hold linear-probe frames only
+constexpr int32_t kFileProbes = 1 << 8;
 }  // namespace
 
 dare_status dare_session_save(dare_session s, const char* path) {
@@ -1520,12 +1720,15 @@ dare_status dare_session_save(dare_session s, const char* path) {
     hd.slots = s->K;
     hd.max_frames = s->cfg.max_frames;
     hd.n_frames = s->n_frames;
-    hd.flags = s->cfg.flags & DARE_SESSION_SCALAR;
+    hd.flags = (s->cfg.flags & DARE_SESSION_SCALAR) | (s->n_curv > 0 ? kFileProbes : 0);
+    const std::vector<double> none;
+    const std::vector<double>& probes = s->n_curv > 0 ? s->probe_host : none;
     hd.rec_bytes = s->rec_bytes;
     hd.n_vox = s->n_vox;
     hd.version = s->version;
     uint32_t crc = 0;
     crc = crc32_update(crc, s->frames_host.data(), s->frames_host.size() * 8);
+    crc = crc32_update(crc, probes.data(), probes.size() * 8);
     crc = crc32_update(crc, rec.data(), rec.size());
     crc = crc32_update(crc, np.data(), np.size());
     crc = crc32_update(crc, sc.data(), sc.size());
@@ -1534,6 +1737,7 @@ dare_status dare_session_save(dare_session s, const char* path) {
     if (!fp) return fail(DARE_E_INVALID, "cannot open %s for writing", path);
     bool ok = std::fwrite(&hd, sizeof(hd), 1, fp) == 1;
     ok = ok && (s->frames_host.empty() || std::fwrite(s->frames_host.data(), 8, s->frames_host.size(), fp) == s->frames_host.size());
+    ok = ok && (probes.empty() || std::fwrite(probes.data(), 8, probes.size(), fp) == probes.size());
     ok = ok && std::fwrite(rec.data(), 1, rec.size(), fp) == rec.size();
     ok = ok && std::fwrite(np.data(), 1, np.size(), fp) == np.size();
     ok = ok && (sc.empty() || std::fwrite(sc.data(), 1, sc.size(), fp) == sc.size());
@@ -1554,16 +1758,18 @@ dare_status dare_session_load(const dare_session_config* cfg, const char* path, 
     };
     if (std::fread(&hd, sizeof(hd), 1, fp) != 1 || std::memcmp(hd.magic, "DAREVOL1", 8) != 0)
         return close_fail("not a DARE volume file");
-    if (hd.abi != DARE_ABI_VERSION) return close_fail("ABI version mismatch");
+    if (hd.abi != 1 && hd.abi != DARE_ABI_VERSION) return close_fail("ABI version mismatch");
     if (hd.n_frames < 0 || hd.n_frames > hd.max_frames || hd.max_frames > DARE_MAX_FRAMES ||
         hd.n_vox != int64_t(hd.dims[0]) * hd.dims[1] * hd.dims[2] || hd.n_vox <= 0 ||
         hd.rec_bytes != record_bytes(hd.slots, hd.dtype))
         return close_fail("inconsistent header");
     std::vector<double> frames(size_t(hd.n_frames) * 9);
+    std::vector<double> probes((hd.flags & kFileProbes) ? size_t(hd.n_frames) * 3 : 0);
     std::vector<uint8_t> rec(size_t(hd.n_vox) * hd.rec_bytes);
     std::vector<uint8_t> np(size_t(hd.n_vox) * hd.slots * 2);
     std::vector<uint8_t> sc((hd.flags & DARE_SESSION_SCALAR) ? size_t(hd.n_vox) * 8 : 0);
     bool ok = frames.empty() || std::fread(frames.data(), 8, frames.size(), fp) == frames.size();
+    ok = ok && (probes.empty() || std::fread(probes.data(), 8, probes.size(), fp) == probes.size());
     ok = ok && std::fread(rec.data(), 1, rec.size(), fp) == rec.size();
     ok = ok && std::fread(np.data(), 1, np.size(), fp) == np.size();
     ok = ok && (sc.empty() || std::fread(sc.data(), 1, sc.size(), fp) == sc.size());
@@ -1571,10 +1777,17 @@ dare_status dare_session_load(const dare_session_config* cfg, const char* path, 
     std::fclose(fp);
     uint32_t crc = 0;
     crc = crc32_update(crc, frames.data(), frames.size() * 8);
+    crc = crc32_update(crc, probes.data(), probes.size() * 8);
     crc = crc32_update(crc, rec.data(), rec.size());
     crc = crc32_update(crc, np.data(), np.size());
     crc = crc32_update(crc, sc.data(), sc.size());
     if (crc != hd.crc) return fail(DARE_E_INVALID, "%s: CRC mismatch (corrupted file)", path);
+    if (probes.empty()) probes.assign(size_t(hd.n_frames) * 3, 0.0);  // every frame linear
+    for (int32_t f = 0; f < hd.n_frames; ++f) {
+        const double k = probes[3 * size_t(f)];
+        if ((k != DARE_PROBE_LINEAR && k != DARE_PROBE_CURVILINEAR) || !finite_all(&probes[3 * size_t(f) + 1], 2))
+            return fail(DARE_E_INVALID, "%s: bad probe record of frame %d", path, f);
+    }
     dare_session_config c = *cfg;
     for (int a = 0; a < 3; ++a) c.grid.dims[a] = hd.dims[a];
     c.grid.spacing_mm = hd.spacing_mm;
@@ -1597,6 +1810,22 @@ dare_status dare_session_load(const dare_session_config* cfg, const char* path, 
     if (!frames.empty() &&
         (e = cudaMemcpy(s->frames_dev, frames.data(), frames.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
         return bail(e);
+    if (hd.n_frames > 0) {
+        // probe geometry rebuilt from the rotations and the (kind, offsets) records
+        std::vector<float> grow(size_t(hd.n_frames) * kGeomFloats);
+        std::vector<double> goff(size_t(hd.n_frames) * 2);
+        for (int32_t f = 0; f < hd.n_frames; ++f) {
+            const int kind = static_cast<int>(probes[3 * size_t(f)]);
+            goff[2 * size_t(f)] = probes[3 * size_t(f) + 1];
+            goff[2 * size_t(f) + 1] = probes[3 * size_t(f) + 2];
+            geometry_row(s->cfg.grid, &frames[9 * size_t(f)], kind, &goff[2 * size_t(f)], &grow[size_t(f) * kGeomFloats]);
+            if (kind == DARE_PROBE_CURVILINEAR) s->n_curv += 1;
+        }
+        if ((e = cudaMemcpy(s->geom_dev, grow.data(), grow.size() * 4, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e);
+        if ((e = cudaMemcpy(s->geom_off_dev, goff.data(), goff.size() * 8, cudaMemcpyHostToDevice)) != cudaSuccess)
+            return bail(e);
+    }
     if (!sc.empty()) {
         if ((e = cudaMemcpy(s->ssum, sc.data(), size_t(hd.n_vox) * 4, cudaMemcpyHostToDevice)) != cudaSuccess) return bail(e);
         if ((e = cudaMemcpy(s->scnt, sc.data() + size_t(hd.n_vox) * 4, size_t(hd.n_vox) * 4, cudaMemcpyHostToDevice)) !=
@@ -1604,6 +1833,7 @@ dare_status dare_session_load(const dare_session_config* cfg, const char* path, 
             return bail(e);
     }
     s->frames_host = std::move(frames);
+    s->probe_host = std::move(probes);
     s->n_frames = hd.n_frames;
     s->version = hd.version;
     s->fresh = false;
@@ -1637,6 +1867,8 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
     if (!affine_ok(s->cfg.grid.vol_to_world, s->cfg.grid.spacing_mm, plane->image_to_world, plane->width,
                    plane->px_mm[0], plane->px_mm[1]))
         return fail(DARE_E_INVALID, "plane too far from the grid for fixed-point coordinates");
+    if (curv_path(s, params))
+        return fail(DARE_E_UNSUPPORTED, "the allocation-free reslice covers linear probes only (use dare_reslice)");
     const size_t wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
     if (s->n_frames > max_frames || size_t(s->n_frames) * wb > wtab_bytes)
         return fail(DARE_E_INVALID, "the allocation-free reslice holds weights for at most %d frames; "
@@ -1842,6 +2074,8 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
     for (int32_t i = 0; i < n; ++i) {
         const dare_reslice_req& r = reqs[i];
         if (!r.session) return fail(DARE_E_INVALID, "request %d has no session", i);
+        if (curv_path(r.session, params))
+            return fail(DARE_E_UNSUPPORTED, "request %d: plans cover linear probes only (use dare_reslice_batch)", i);
         if (r.session->cfg.device != reqs[0].session->cfg.device) return fail(DARE_E_INVALID, "requests span devices");
         rc = check_plane(&r.plane);
         if (rc != DARE_OK) return fail(rc, "request %d: %s", i, g_err.c_str());

@@ -81,6 +81,42 @@ struct ScatterArgs {
     int32_t frame_base;       // global id of frame 0 of this chunk
     int32_t small_steps;      // every |A|, |B| < 2^25: tiles step pixels in int32
     int64_t tile_base;        // pair-list tile of frame 0 (frames uploaded in slices)
+    const uint32_t* pix_mask; // H rows of ceil(W / 32) words, bit set = pixel used; NULL: every pixel
+};
+
+// Per-frame probe geometry for curvilinear reslicing, kGeomFloats floats per
+// frame (five float4): the voxel -> apex-relative image point rows
+// tx, ty (p_x = tx . (i, j, k, 1), likewise p_y), the frame's image axes in
+// the volume frame c0 (lateral), c1 (beam), c2 (elevation), the sample side of
+// the FP32 error bound k1 (the direction error is at most k1 / |p|), and kind
+// (0 linear: tx = 0, ty = (0, 0, 0, 1), k1 = 0; 1 curvilinear).
+constexpr int kGeomFloats = 20;
+
+// One plane of a curvilinear reslice (any session whose frames include a
+// curvilinear probe, or a curvilinear virtual probe).  Eq. 1 / Eq. 2 are
+// evaluated per (pixel, sample) in FP32; a threshold decision within the FP32
+// error bound of its cosine is re-taken in FP64 from rot64 / off64.
+struct CurvJob {
+    ResliceJob j;             // pixel -> voxel map, records, outputs, support (wtab unused)
+    const float4* geom;       // per-frame FP32 geometry, 5 float4 per frame
+    const double* rot64;      // per-frame rotations in the volume frame (9 FP64, row-major)
+    const double* off64;      // per-frame apex-relative offsets (ox, oy) FP64; with rot64 and h:
+                              //   p_x = h sum_r R[r][0] c_r + ox, p_y = h sum_r R[r][1] c_r + oy
+    double R[9];              // plane rotation in the volume frame, row-major
+    double h;                 // grid spacing
+    double half_w, sx, sy;    // pixel (u, v) at image point ((u - half_w) sx, v sy)
+    double ax, ay;            // virtual fan apex (image mm)
+    double cos_n64, cos_i64;  // thresholds
+    float Rf[9];
+    float oxf, oyf;           // FP32: p = (u sx + oxf, v sy + oyf) relative to the virtual apex
+    float sxf, syf;
+    float k1p;                // pixel side of the FP32 error bound
+    float k_n, k_i;           // Eq. 2
+    float cos_n, cos_i;       // thresholds, FP32 copies
+    int32_t use_n, use_i;     // thresholds active
+    int32_t elevation;        // 1: Eq. 1's normal is the elevation axis
+    int32_t curv_out;         // 1: curvilinear virtual probe
+    int32_t pad;
 };
 
 // ------------------------------------------------------------ launchers (kernels.cu, kernels_build.cu)
@@ -113,6 +149,9 @@ cudaError_t launch_reslice_plain_r(const ResliceJob* jobs_dev, const ResliceJob*
 cudaError_t launch_reslice_tiled_r(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
                                    int tile_offset, int n_tiles, int uniform, int col_cap, int slot_cap, int K,
                                    int dtype, int half_weights, cudaStream_t st);
+// curvilinear probes (kernels_curv.cu): per-pixel gather with in-kernel Eq. 1 / Eq. 2
+cudaError_t launch_reslice_curv(const CurvJob* jobs_dev, const CurvJob* one_job, int n_jobs, int max_w, int max_h,
+                                int K, int dtype, cudaStream_t st);
 constexpr int kMaxSupport = 9;           // tiled general path: support of at most 9 voxels per axis (R <= 4)
 constexpr int kGeneralSmemCap = 200 << 10;  // dynamic shared memory of the general tiled kernel, at most
 

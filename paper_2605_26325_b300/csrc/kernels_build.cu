@@ -100,6 +100,8 @@ __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int 
         vi[q] = -1;
         val[q] = 0;
         if (uu >= A.width || vv >= A.height) continue;
+        if (A.pix_mask && !((__ldg(A.pix_mask + static_cast<int64_t>(vv) * ((A.width + 31) >> 5) + (uu >> 5)) >> (uu & 31)) & 1u))
+            continue;  // excluded by the probe's pixel mask
         if (A.small_steps) {
             const int du = uu - u0, dv = vv - v0;
             int c[3];

@@ -1,0 +1,295 @@
+// DARE reslicing (Sec. 2.1 "Reslicing", Eq. 1, Eq. 2) for curvilinear
+// probes on sm_103a.
+//
+// The paper's probe is a linear array: a frame's beam is its image y axis
+// everywhere, so Eq. 1 depends only on (plane, frame) and the other kernels
+// read it from a per-frame weight table.  A curvilinear probe's beams fan out
+// from an apex: the beam through image point p runs along (p - a) / |p - a|,
+// the frame's image axes turned about image z.  A stored sample's axes are
+// its frame's turned toward the centre of its voxel (projected into the
+// frame); a curvilinear virtual plane turns its own axes at every output
+// pixel.  The weight then depends on (pixel, voxel, frame) and no longer
+// factors through a per-voxel sum, so this kernel gathers per pixel and
+// evaluates Eq. 1 and Eq. 2 for every sample it reads:
+//   u_s = (p_s - a_s) / |p_s - a_s|, b_s = R_f (u_s,x, u_s,y, 0), x_s = R_f (u_s,y, -u_s,x, 0)
+//   d_normal = n_s . n_p (n = b, or the elevation axis R z), d_inplane = |x_s . x_p|
+//   w = exp(-k_normal |n_s - n_p|^2 / 2 - k_inplane |x_s -+ x_p|^2 / 2)
+// (1 - n_s . n_p = |n_s - n_p|^2 / 2 for unit vectors: the form that keeps its
+// accuracy where the weight is large).
+//
+// Thresholds: a sample passes iff d >= cos(threshold), decided exactly.  The
+// FP32 dot products carry an error of at most
+//   E = 4 (k1_s / |p_s| + k1_p / |p_p|) + 96 eps
+// (k1 = 17 eps S, S a bound on the FP32 point computation's operands, from the
+// host); a decision with |d - cos| <= E is re-taken in FP64 from the FP64
+// geometry (a filtered predicate: FP32 speed, FP64 decisions).
+#include <cfloat>
+
+#include "dare_internal.h"
+#include "device_common.cuh"
+
+namespace dare {
+namespace {
+
+using namespace dev;
+
+constexpr float kEps = 5.9604645e-8f;  // 2^-24, FP32 unit roundoff
+
+__device__ __forceinline__ float tent_factor(float d, float R) { return 1.0f - __fdiv_rn(fabsf(d), R); }
+__device__ __forceinline__ float exp_weight(float d2, float kr) { return expf(-kr * sqrtf(d2)); }
+
+struct V3 {
+    float x, y, z;
+};
+
+// a p + b q
+__device__ __forceinline__ V3 comb(float a, V3 p, float b, V3 q) {
+    return {fmaf(a, p.x, b * q.x), fmaf(a, p.y, b * q.y), fmaf(a, p.z, b * q.z)};
+}
+__device__ __forceinline__ float dot(V3 a, V3 b) { return fmaf(a.x, b.x, fmaf(a.y, b.y, a.z * b.z)); }
+// |a - s b|^2 / 2
+__device__ __forceinline__ float half_gap2(V3 a, V3 b, float s) {
+    const float dx = fmaf(-s, b.x, a.x), dy = fmaf(-s, b.y, a.y), dz = fmaf(-s, b.z, a.z);
+    return 0.5f * fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+}
+
+// The output pixel's axes (volume frame) and its part of the error bound.
+struct PixelAxes {
+    V3 n, x;   // Eq. 1 normal (beam or elevation) and lateral axis
+    float e;   // k1_p / |p_p|; infinite at the apex (every decision in FP64)
+};
+
+__device__ __forceinline__ PixelAxes pixel_axes(const CurvJob& C, int u, int v) {
+    float ux = 0.0f, uy = 1.0f, e = 0.0f;
+    if (C.curv_out) {
+        const float px = fmaf(static_cast<float>(u), C.sxf, C.oxf);
+        const float py = fmaf(static_cast<float>(v), C.syf, C.oyf);
+        const float r2 = fmaf(px, px, py * py);
+        if (r2 > 0.0f) {
+            const float inv = rsqrtf(r2);
+            ux = px * inv;
+            uy = py * inv;
+            e = C.k1p * inv;
+        } else {
+            e = INFINITY;
+        }
+    }
+    const V3 c0 = {C.Rf[0], C.Rf[3], C.Rf[6]}, c1 = {C.Rf[1], C.Rf[4], C.Rf[7]};
+    PixelAxes P;
+    P.x = comb(uy, c0, -ux, c1);
+    P.n = C.elevation ? V3{C.Rf[2], C.Rf[5], C.Rf[8]} : comb(ux, c0, uy, c1);
+    P.e = e;
+    return P;
+}
+
+// Unit fan direction (ux, uy) of an apex-relative point, FP64; (0, 1) at the apex.
+__device__ __forceinline__ void fan64(double px, double py, double& ux, double& uy) {
+    const double r = sqrt(px * px + py * py);
+    if (r > 0.0) {
+        ux = px / r;
+        uy = py / r;
+    } else {
+        ux = 0.0;
+        uy = 1.0;
+    }
+}
+
+// Threshold decisions of one (pixel, sample) pair in FP64: bit 0 normal
+// passes, bit 1 in-plane passes.  Off the hot path (a few per million).
+__device__ __noinline__ int decide64(const CurvJob& C, int f, float ci, float cj, float ck, int u, int v) {
+    const double* R = C.rot64 + 9 * static_cast<int64_t>(f);
+    double sux = 0.0, suy = 1.0;
+    if (__ldg(&C.geom[5 * f + 4].z) != 0.0f) {
+        const double* o = C.off64 + 2 * static_cast<int64_t>(f);
+        const double hi = C.h * ci, hj = C.h * cj, hk = C.h * ck;
+        fan64(R[0] * hi + R[3] * hj + R[6] * hk + o[0], R[1] * hi + R[4] * hj + R[7] * hk + o[1], sux, suy);
+    }
+    double pux = 0.0, puy = 1.0;
+    if (C.curv_out)
+        fan64((static_cast<double>(u) - C.half_w) * C.sx - C.ax, static_cast<double>(v) * C.sy - C.ay, pux, puy);
+    double dn = 0.0, dx = 0.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        const double bs = sux * R[3 * r] + suy * R[3 * r + 1], xs = suy * R[3 * r] - sux * R[3 * r + 1];
+        const double bp = pux * C.R[3 * r] + puy * C.R[3 * r + 1], xp = puy * C.R[3 * r] - pux * C.R[3 * r + 1];
+        dn += C.elevation ? R[3 * r + 2] * C.R[3 * r + 2] : bs * bp;
+        dx += xs * xp;
+    }
+    return (dn >= C.cos_n64 ? 1 : 0) | (fabs(dx) >= C.cos_i64 ? 2 : 0);
+}
+
+// Eq. 1 / Eq. 2 weight of frame f's sample in voxel (ci, cj, ck) for this
+// pixel, 0 when a threshold discards it.
+__device__ __forceinline__ float sample_weight(const CurvJob& C, const PixelAxes& P, int f, float ci, float cj,
+                                               float ck, int u, int v) {
+    const float4* G = C.geom + 5 * static_cast<int64_t>(f);
+    const float4 g2 = __ldg(G + 2), g3 = __ldg(G + 3), g4 = __ldg(G + 4);
+    float ux = 0.0f, uy = 1.0f, es = 0.0f;
+    if (g4.z != 0.0f) {  // curvilinear frame: turn toward the voxel centre
+        const float4 g0 = __ldg(G), g1 = __ldg(G + 1);
+        const float px = fmaf(g0.x, ci, fmaf(g0.y, cj, fmaf(g0.z, ck, g0.w)));
+        const float py = fmaf(g1.x, ci, fmaf(g1.y, cj, fmaf(g1.z, ck, g1.w)));
+        const float r2 = fmaf(px, px, py * py);
+        if (r2 > 0.0f) {
+            const float inv = rsqrtf(r2);
+            ux = px * inv;
+            uy = py * inv;
+            es = g4.y * inv;
+        } else {
+            es = INFINITY;
+        }
+    }
+    const V3 c0 = {g2.x, g2.y, g2.z}, c1 = {g2.w, g3.x, g3.y};
+    const V3 xs = comb(uy, c0, -ux, c1);
+    const V3 ns = C.elevation ? V3{g3.z, g3.w, g4.x} : comb(ux, c0, uy, c1);
+    const float dn = dot(ns, P.n), dx = dot(xs, P.x), di = fabsf(dx);
+    bool pass_n = !C.use_n || dn >= C.cos_n;
+    bool pass_i = !C.use_i || di >= C.cos_i;
+    const float E = fmaf(4.0f, es + P.e, 96.0f * kEps);
+    if ((C.use_n && fabsf(dn - C.cos_n) <= E) || (C.use_i && fabsf(di - C.cos_i) <= E)) {
+        const int d = decide64(C, f, ci, cj, ck, u, v);
+        pass_n = !C.use_n || (d & 1);
+        pass_i = !C.use_i || (d & 2);
+    }
+    if (!(pass_n && pass_i)) return 0.0f;
+    const float en = half_gap2(ns, P.n, 1.0f), ei = half_gap2(xs, P.x, dx < 0.0f ? -1.0f : 1.0f);
+    return expf(-fmaf(C.k_n, en, C.k_i * ei));
+}
+
+// One voxel's (A, B) = (sum w I, sum w) for this pixel.
+template <int K, typename VT>
+__device__ __forceinline__ float2 curv_voxel(const CurvJob& C, const PixelAxes& P, int64_t vi, float ci, float cj,
+                                             float ck, int u, int v) {
+    using S = RecShape<K, VT>;
+    uint4 r[S::kVec];
+    load_record<K, VT>(C.j.rec + vi * S::kBytes, r);
+    float A = 0.0f, B = 0.0f;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const uint32_t id = slot_id<K, VT>(r, s);
+        if (id == DARE_EMPTY_FRAME) break;  // empty slots come last
+        const float w = sample_weight(C, P, static_cast<int>(id), ci, cj, ck, u, v);
+        A = fmaf(w, slot_value<K, VT>(r, s), A);
+        B += w;
+    }
+    return make_float2(A, B);
+}
+
+// The pixel's support (as in the linear-probe kernels) with per-sample weights.
+template <int K, typename VT>
+__device__ __noinline__ void gather_pixel_curv(const CurvJob& C, int u, int v, float& num, float& den) {
+    const ResliceJob& J = C.j;
+    const int R = J.radius;
+    const bool box = J.kernel == DARE_BOX;
+    const int S = box ? 2 * R + 1 : 2 * R;
+    int64_t lo[3];
+    float fr[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int64_t G = J.g0[a] + static_cast<int64_t>(u) * J.a[a] + static_cast<int64_t>(v) * J.b[a];
+        const int64_t f = G >> kFixBits;
+        fr[a] = static_cast<float>(static_cast<int32_t>(G & (kFixOne - 1))) * (1.0f / static_cast<float>(kFixOne));
+        lo[a] = box ? f + (fr[a] >= 0.5f ? 1 : 0) - R : f - R + 1;
+        if (lo[a] + S - 1 < 0 || lo[a] > J.dims[a] - 1) return;  // the support misses the grid
+        fr[a] -= static_cast<float>(lo[a] - f);                   // g - lo, exact
+    }
+    const PixelAxes P = pixel_axes(C, u, v);
+    const float Rf = static_cast<float>(R), kr = J.k_dist / Rf;
+    for (int jz = 0; jz < S; ++jz) {
+        const int64_t cz = lo[2] + jz;
+        if (cz < 0 || cz >= J.dims[2]) continue;
+        const float dz = fr[2] - static_cast<float>(jz);
+        const float tz = J.kernel == DARE_TENT ? tent_factor(dz, Rf) : 1.0f;
+        for (int jy = 0; jy < S; ++jy) {
+            const int64_t cy = lo[1] + jy;
+            if (cy < 0 || cy >= J.dims[1]) continue;
+            const float dy = fr[1] - static_cast<float>(jy);
+            const float tyz = J.kernel == DARE_TENT ? tent_factor(dy, Rf) * tz : 1.0f;
+            for (int jx = 0; jx < S; ++jx) {
+                const int64_t cx = lo[0] + jx;
+                if (cx < 0 || cx >= J.dims[0]) continue;
+                const float dx = fr[0] - static_cast<float>(jx);
+                float t;
+                if (J.kernel == DARE_TENT)
+                    t = tent_factor(dx, Rf) * tyz;
+                else if (box)
+                    t = 1.0f;
+                else
+                    t = exp_weight(dx * dx + dy * dy + dz * dz, kr);
+                const int64_t vi = cx + static_cast<int64_t>(J.dims[0]) * (cy + static_cast<int64_t>(J.dims[1]) * cz);
+                const float2 ab = curv_voxel<K, VT>(C, P, vi, static_cast<float>(cx), static_cast<float>(cy),
+                                                    static_cast<float>(cz), u, v);
+                num = fmaf(t, ab.x, num);
+                den = fmaf(t, ab.y, den);
+            }
+        }
+    }
+}
+
+// 32 x 8 pixels per CTA, one per thread; a warp writes one mask word.
+template <int K, typename VT>
+__device__ __forceinline__ void curv_body(const CurvJob& C) {
+    const ResliceJob& J = C.j;
+    const int lane = threadIdx.x;
+    const int u = blockIdx.x * 32 + lane;
+    const int v = blockIdx.y * 8 + threadIdx.y;
+    if (v >= J.height || static_cast<int>(blockIdx.x) * 32 >= J.width) return;  // warp-uniform
+    const bool active = u < J.width;
+    float num = 0.0f, den = 0.0f;
+    if (active) {
+        gather_pixel_curv<K, VT>(C, u, v, num, den);
+        J.out[static_cast<int64_t>(v) * J.width + u] = den > 0.0f ? num / den : J.unassigned;
+    }
+    const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);
+    if (lane == 0) J.mask[static_cast<int64_t>(v) * J.mask_stride + blockIdx.x] = bits;
+}
+
+template <int K, typename VT>
+__global__ void __launch_bounds__(256) k_reslice_curv_one(const __grid_constant__ CurvJob C) {
+    curv_body<K, VT>(C);
+}
+
+template <int K, typename VT>
+__global__ void __launch_bounds__(256) k_reslice_curv_batch(const CurvJob* __restrict__ jobs) {
+    curv_body<K, VT>(jobs[blockIdx.z]);
+}
+
+template <int K, typename VT>
+cudaError_t launch_c(const CurvJob* jobs_dev, const CurvJob* one, int n_jobs, int max_w, int max_h, cudaStream_t st) {
+    const dim3 block(32, 8);
+    const dim3 grid((max_w + 31) / 32, (max_h + 7) / 8, one ? 1 : n_jobs);
+    if (one)
+        k_reslice_curv_one<K, VT><<<grid, block, 0, st>>>(*one);
+    else
+        k_reslice_curv_batch<K, VT><<<grid, block, 0, st>>>(jobs_dev);
+    return cudaPeekAtLastError();
+}
+
+template <int K>
+cudaError_t launch_c_k(const CurvJob* jobs_dev, const CurvJob* one, int n_jobs, int max_w, int max_h, int dtype,
+                       cudaStream_t st) {
+    switch (dtype) {
+    case DARE_U8: return launch_c<K, uint8_t>(jobs_dev, one, n_jobs, max_w, max_h, st);
+    case DARE_F16: return launch_c<K, __half>(jobs_dev, one, n_jobs, max_w, max_h, st);
+    case DARE_BF16: return launch_c<K, __nv_bfloat16>(jobs_dev, one, n_jobs, max_w, max_h, st);
+    case DARE_F32: return launch_c<K, float>(jobs_dev, one, n_jobs, max_w, max_h, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_reslice_curv(const CurvJob* jobs_dev, const CurvJob* one_job, int n_jobs, int max_w, int max_h,
+                                int K, int dtype, cudaStream_t st) {
+    if (n_jobs <= 0 || max_w <= 0 || max_h <= 0) return cudaSuccess;
+    if (!one_job && n_jobs > 65535) return cudaErrorInvalidValue;
+    switch (K) {
+    case 4: return launch_c_k<4>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, st);
+    case 8: return launch_c_k<8>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, st);
+    case 12: return launch_c_k<12>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, st);
+    case 16: return launch_c_k<16>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace dare

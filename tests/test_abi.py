@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_abi_version():
-    assert dare.lib().dare_abi_version() == 1
+    assert dare.lib().dare_abi_version() == 2
 
 
 def test_struct_layouts_match_c(tmp_path):
@@ -47,7 +47,7 @@ def test_struct_layouts_match_c(tmp_path):
         "dare_grid": dare.dare_grid, "dare_allocator": dare.dare_allocator,
         "dare_session_config": dare.dare_session_config, "dare_params": dare.dare_params,
         "dare_plane": dare.dare_plane, "dare_reslice_req": dare.dare_reslice_req,
-        "dare_session_info": dare.dare_session_info,
+        "dare_session_info": dare.dare_session_info, "dare_probe": dare.dare_probe,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
     for name, cls in structs.items():
