@@ -567,6 +567,39 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
                       "(image and volume size not stated) are 50 / 100 / 300 ms for 3^3 / 5^3 / 9^3")
     line["radius_axis"] = radius
 
+    # --- curvilinear probes: the same frames as a fan from an apex 40 mm above the
+    # transducer face, resliced by a curvilinear virtual probe (per-sample Eq. 1 /
+    # Eq. 2 kernel); and the linear volume under the curvilinear virtual probe
+    apex = (0.0, -40.0)
+    cs = dare.Session(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, dtype=DTYPE_NAMES[args.dtype],
+                      max_slots=args.slots, device=dist.local)
+    cs.set_probe(dare.DARE_PROBE_CURVILINEAR, apex)
+
+    def cs_build():
+        cs.reset(stream)
+        cs.build(frames_d, w.frame_poses, w.frame_px, stream)
+
+    c_build_ms = timed(cs_build, 2)
+    pc = dare.params_default(probe_apex_mm=apex)
+    rq_c = dare.make_requests([(cs, w.reslice_poses[i], outs[i], masks[i], w.out_px) for i in range(P)])
+    c_ms = timed(lambda: dare.reslice_batch(rq_c, pc, stream), 2)
+    v_ms = timed(lambda: dare.reslice_batch(reqs, pc, stream), 2)
+    c_lat = []
+    for i in range(50):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        cs.reslice(w.reslice_poses[i % P], outs[0], masks[0], w.out_px, pc, stream=stream)
+        torch.cuda.synchronize()
+        c_lat.append((time.perf_counter() - t) * 1e3)
+    line["curvilinear"] = {"apex_mm": list(apex), "build_ms": c_build_ms, "reslice_ms": c_ms,
+                           "mpix_s": P * W * H / (c_ms * 1e-3) / 1e6,
+                           "virtual_probe_only_mpix_s": P * W * H / (v_ms * 1e-3) / 1e6,
+                           "latency": {"p50_ms": percentile(c_lat, 50), "p99_ms": percentile(c_lat, 99),
+                                       "samples": len(c_lat)},
+                           "note": "curvilinear frames and virtual probe; the second figure is the linear "
+                                   "volume under the curvilinear virtual probe; both gather per pixel"}
+    cs.close()
+
     # --- image quality on synthetic ground truth (the paper's Sec. 3 comparison,
     # NCC / SSIM against the acquired image, on rendered data): the phantom
     # rendered at the virtual probe's pose vs DARE and the mean-compounding
