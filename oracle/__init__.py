@@ -101,6 +101,13 @@ def _lib():
         lib.ora_reslice_scalar.argtypes = [vp, dp, ctypes.c_int32, ctypes.c_int32, ctypes.c_double,
                                            ctypes.c_double, ctypes.c_double, dp, u8p]
         lib.ora_reslice_scalar.restype = ctypes.c_int
+        lib.ora_compounded.argtypes = [vp, dp]
+        lib.ora_compounded.restype = None
+        lib.ora_fill_holes.argtypes = [vp, dp, ctypes.c_int32, ctypes.c_int32, dp]
+        lib.ora_fill_holes.restype = None
+        lib.ora_reslice_values.argtypes = [i32p, ctypes.c_double, dp, dp, dp, ctypes.c_int32, ctypes.c_int32,
+                                           ctypes.c_double, ctypes.c_double, ctypes.c_double, dp, u8p]
+        lib.ora_reslice_values.restype = ctypes.c_int
         lib.ora_footprint.argtypes = [i32p, ctypes.c_double, dp, dp, ctypes.c_int32, ctypes.c_int32,
                                       ctypes.c_double, ctypes.c_double, ctypes.c_int32, ctypes.c_int32]
         lib.ora_footprint.restype = ctypes.c_int64
@@ -268,6 +275,41 @@ def reslice_scalar(vol: Volume, image_to_world, width, height, px_mm, unassigned
     mask = np.zeros((height, width), np.uint8)
     _lib().ora_reslice_scalar(vol._h, _ptr(T, ctypes.c_double), int(width), int(height), float(px_mm[0]),
                               float(px_mm[1]), float(unassigned), _ptr(out, ctypes.c_double),
+                              _ptr(mask, ctypes.c_uint8))
+    return out, mask
+
+
+def compounded(vol: Volume):
+    """Mean-compounded value per voxel (flat, x fastest): RN_fp32(sum / npix) over
+    every pixel that landed in it, NaN where none did."""
+    out = np.zeros(int(np.prod(vol.dims)), np.float64)
+    _lib().ora_compounded(vol._h, _ptr(out, ctypes.c_double))
+    return out
+
+
+def fill_holes(vol: Volume, values, radius=1, min_neighbours=1):
+    """Hole filling of a compounded volume (the PLUS baseline's, Sec. 2.2): each
+    empty voxel takes the 1/distance-weighted mean of the occupied voxels of its
+    (2 radius + 1)^3 cube when at least min_neighbours are occupied."""
+    values = _arr(values, np.float64).reshape(-1)
+    out = np.zeros_like(values)
+    _lib().ora_fill_holes(vol._h, _ptr(values, ctypes.c_double), int(radius), int(min_neighbours),
+                          _ptr(out, ctypes.c_double))
+    return out
+
+
+def reslice_values(dims, spacing, vol_to_world, values, image_to_world, width, height, px_mm, unassigned=0.0):
+    """Trilinear reslice of a scalar volume (NaN = empty), renormalised over the
+    non-empty corners: (out (H, W), mask (H, W))."""
+    dims_a = _arr(dims, np.int32)
+    V = _arr(vol_to_world, np.float64).reshape(16)
+    T = _arr(image_to_world, np.float64).reshape(16)
+    values = _arr(values, np.float64).reshape(-1)
+    out = np.zeros((height, width), np.float64)
+    mask = np.zeros((height, width), np.uint8)
+    _lib().ora_reslice_values(_ptr(dims_a, ctypes.c_int32), float(spacing), _ptr(V, ctypes.c_double),
+                              _ptr(values, ctypes.c_double), _ptr(T, ctypes.c_double), int(width), int(height),
+                              float(px_mm[0]), float(px_mm[1]), float(unassigned), _ptr(out, ctypes.c_double),
                               _ptr(mask, ctypes.c_uint8))
     return out, mask
 

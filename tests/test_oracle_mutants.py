@@ -72,6 +72,20 @@ MUTANTS = {
         ("quat_axis(qp, 0, cp.x_r);", "quat_axis(c0->q, 0, cp.x_r);"),
     "pixel mask ignored":
         ("if (pixel_mask && !pixel_mask[(size_t)y * W + x]) continue;", ""),
+    "hole weights without the square root":
+        ("const double w = 1.0 / sqrt((double)(dx * dx + dy * dy + dz * dz));",
+         "const double w = 1.0 / (double)(dx * dx + dy * dy + dz * dz);"),
+    "hole filling ignores min_neighbours":
+        ("filled[i] = (n >= min_neighbours && n > 0) ? num / den : NAN;", "filled[i] = n > 0 ? num / den : NAN;"),
+    "hole filling cube one voxel short":
+        ("        for (int64_t dz = -r; dz <= r; ++dz)\n            for (int64_t dy = -r; dy <= r; ++dy)\n"
+         "                for (int64_t dx = -r; dx <= r; ++dx) {",
+         "        for (int64_t dz = -r; dz < r; ++dz)\n            for (int64_t dy = -r; dy <= r; ++dy)\n"
+         "                for (int64_t dx = -r; dx <= r; ++dx) {"),
+    "scalar-volume reslice blends empty corners as zero":
+        ("const double S = values[cx + (int64_t)dims[0] * (cy + (int64_t)dims[1] * cz)];\n                if (isnan(S)) continue;",
+         "const double S0 = values[cx + (int64_t)dims[0] * (cy + (int64_t)dims[1] * cz)];\n"
+         "                const double S = isnan(S0) ? 0.0 : S0;"),
     "unassigned when the numerator is zero":
         ("    if (den > 0) {\n        *out = num / den;", "    if (num > 0) {\n        *out = num / den;"),
 }

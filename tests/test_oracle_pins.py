@@ -529,6 +529,95 @@ def test_scalar_comparator(tiny):
     assert np.all(mask[full] == 1)
 
 
+# ----------------------------------------------------------------- hole filling (comparator)
+
+def test_compounded_and_values_reslice(tiny):
+    """The compounded volume is the RN_fp32 mean of every voxel's pixels (NaN
+    where empty), and the scalar-volume reslice of it is the mean-compounding
+    comparator exactly."""
+    g = tiny.grid
+    vol = oracle.build(g.dims, g.spacing, g.vol_to_world, tiny.frames[:80], tiny.frame_poses[:80], tiny.frame_px)
+    e = vol.export()
+    occ = e["tot_npix"] > 0
+    vals = oracle.compounded(vol)
+    assert np.array_equal(np.isnan(vals), ~occ)
+    assert np.array_equal(vals[occ], (np.float32(e["tot_sum"][occ]) / np.float32(e["tot_npix"][occ])).astype(np.float64))
+    for P in tiny.reslice_poses[[0, 6, 13]]:
+        a, am = oracle.reslice_scalar(vol, P, tiny.out_w, tiny.out_h, tiny.out_px, unassigned=-3.0)
+        b, bm = oracle.reslice_values(g.dims, g.spacing, g.vol_to_world, vals, P, tiny.out_w, tiny.out_h,
+                                      tiny.out_px, unassigned=-3.0)
+        assert np.array_equal(am, bm)
+        assert np.max(np.abs(a - b)) < 1e-12
+
+
+def _empty_volume(dims):
+    return oracle.volume_from_samples(dims, 1.0, np.eye(4), np.zeros(0, np.int64), np.zeros(0, np.int32),
+                                      np.zeros(0), np.zeros((0, 4)))
+
+
+def test_fill_holes_closed_forms():
+    """Hand-computed fills: one occupied voxel fills its 26 neighbours with its
+    value; between two occupied voxels the 1/distance weights give the plain
+    mean at equal distances and (10 + 40/sqrt 5)/(1 + 1/sqrt 5) at distances 1
+    and sqrt 5; min_neighbours leaves a voxel with fewer occupied neighbours
+    empty; occupied voxels keep their value."""
+    dims = (7, 7, 7)
+    vol = _empty_volume(dims)
+    idx = lambda x, y, z: x + 7 * (y + 7 * z)
+    one = np.full(343, np.nan)
+    one[idx(3, 3, 3)] = 10.0
+    f = oracle.fill_holes(vol, one, 1, 1)
+    cube = np.zeros(343, bool)
+    for d in np.ndindex(3, 3, 3):
+        cube[idx(2 + d[0], 2 + d[1], 2 + d[2])] = True
+    assert np.all(f[cube] == 10.0)
+    assert np.all(np.isnan(f[~cube]))
+    two = np.full(343, np.nan)
+    two[idx(2, 3, 3)], two[idx(4, 3, 3)] = 10.0, 40.0
+    f1 = oracle.fill_holes(vol, two, 1, 1)
+    assert f1[idx(2, 3, 3)] == 10.0 and f1[idx(4, 3, 3)] == 40.0
+    assert abs(f1[idx(3, 3, 3)] - 25.0) < 1e-13
+    assert abs(f1[idx(3, 4, 3)] - 25.0) < 1e-13
+    assert f1[idx(2, 4, 3)] == 10.0          # only the near voxel lies in its 3^3 cube
+    f2 = oracle.fill_holes(vol, two, 2, 1)
+    r5 = 1.0 / math.sqrt(5.0)
+    assert abs(f2[idx(2, 4, 3)] - (10.0 + 40.0 * r5) / (1.0 + r5)) < 1e-13
+    fm = oracle.fill_holes(vol, two, 1, 2)
+    assert np.isnan(fm[idx(2, 4, 3)]) and abs(fm[idx(3, 3, 3)] - 25.0) < 1e-13
+
+
+@pytest.mark.parametrize("radius,min_nb", [(1, 1), (1, 5), (2, 1), (2, 9)])
+def test_fill_holes_convolution(radius, min_nb):
+    """Whole-volume check by convolution (scipy): filled = conv(S occ, K) /
+    conv(occ, K) with K = 1/distance (0 at the centre), where conv(occ, 1) >=
+    min_neighbours; occupied voxels unchanged, the rest empty."""
+    rng = np.random.default_rng(70 + 3 * radius + min_nb)
+    dims = (12, 10, 9)
+    n = int(np.prod(dims))
+    occ = rng.random(n) < 0.12
+    vals = np.where(occ, rng.uniform(0, 255, n), np.nan)
+    got = oracle.fill_holes(_empty_volume(dims), vals, radius, min_nb)
+    k = 2 * radius + 1
+    dz, dy, dx = np.meshgrid(*(np.arange(k) - radius,) * 3, indexing="ij")
+    d = np.sqrt(dx * dx + dy * dy + dz * dz)
+    K = np.where(d > 0, 1.0 / np.where(d > 0, d, 1.0), 0.0)
+    ones = (d > 0).astype(np.float64)
+    occ3 = occ.reshape(dims[2], dims[1], dims[0]).astype(np.float64)
+    S3 = np.where(occ, vals, 0.0).reshape(dims[2], dims[1], dims[0])
+    num = ndimage.convolve(S3 * occ3, K, mode="constant", cval=0.0).reshape(-1)
+    den = ndimage.convolve(occ3, K, mode="constant", cval=0.0).reshape(-1)
+    cnt = np.rint(ndimage.convolve(occ3, ones, mode="constant", cval=0.0)).reshape(-1)
+    fill = (~occ) & (cnt >= max(min_nb, 1))
+    ref = np.where(occ, vals, np.nan)
+    ref[fill] = num[fill] / den[fill]
+    assert np.array_equal(np.isnan(got), np.isnan(ref))
+    ok = ~np.isnan(ref)
+    assert np.max(np.abs(got[ok] - ref[ok])) < 1e-10
+    assert fill.sum() > 50
+    if (radius, min_nb) != (2, 1):  # a 5^3 cube always holds an occupied voxel here
+        assert (~occ & ~fill).sum() > 5
+
+
 # ----------------------------------------------------------------- curvilinear probes
 #
 # A curvilinear probe's beams fan out from an apex of the image plane: the
