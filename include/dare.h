@@ -515,6 +515,29 @@ dare_status dare_reslice_scalar(dare_session s, const dare_plane* plane, float u
                                 uint32_t* mask_dev, void* stream);
 
 /*
+ * Hole filling of the compounded volume (the PLUS baseline of Sec. 2.2 runs
+ * mean compounding "with hole-filling"; one pass, this library's reading):
+ * every voxel with pixels keeps RN_fp32(total / count); an empty voxel takes
+ * the mean of the occupied voxels of the (2 radius_vox + 1)^3 cube around it,
+ * each weighted by 1 / its Euclidean distance in voxels, when at least
+ * min_neighbours of them are occupied, and stays empty otherwise.  The result
+ * (FP32 per voxel, NaN = empty) is kept in the session (allocated on first
+ * use, n_vox x 4 bytes) until the next build or reset makes it stale.
+ * radius_vox 1..8, min_neighbours 0..(2 radius_vox + 1)^3 - 1.  Needs
+ * DARE_SESSION_SCALAR (DARE_E_STATE otherwise).  Asynchronous on `stream`.
+ */
+dare_status dare_fill_holes(dare_session s, int32_t radius_vox, int32_t min_neighbours, void* stream);
+
+/* The comparator's trilinear reslice (as dare_reslice_scalar) of the
+ * hole-filled volume: non-empty corners only, renormalised.  DARE_E_STATE
+ * without a current dare_fill_holes result. */
+dare_status dare_reslice_scalar_filled(dare_session s, const dare_plane* plane, float unassigned, float* out_dev,
+                                       uint32_t* mask_dev, void* stream);
+
+/* Host copy of the hole-filled volume, n_vox FP32 (NaN = empty); synchronous. */
+dare_status dare_session_read_filled(dare_session s, float* values);
+
+/*
  * Footprint: for each of n planes, the number of distinct in-grid voxels in
  * the TENT support of radius 1 of any pixel -- the voxel records a reslice
  * must read at least once.  counts: n int64 on the host.  Synchronous.

@@ -142,6 +142,9 @@ _SIGNATURES = {
     "dare_session_read_records": ([_vp, _vp, _vp, _vp, _vp, _vp], ctypes.c_int),
     "dare_session_read_frames": ([_vp, _P(ctypes.c_double)], ctypes.c_int),
     "dare_session_set_probe": ([_vp, _P(dare_probe), _vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
+    "dare_fill_holes": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp], ctypes.c_int),
+    "dare_reslice_scalar_filled": ([_vp, _P(dare_plane), ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
+    "dare_session_read_filled": ([_vp, _vp], ctypes.c_int),
     "dare_session_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
     "dare_session_load": ([_P(dare_session_config), ctypes.c_char_p, _P(_vp)], ctypes.c_int),
     "dare_build_volume": ([_vp, _vp, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P(ctypes.c_double),
@@ -506,6 +509,24 @@ class Session:
         check(lib().dare_reslice_scalar(self._h, ctypes.byref(pl), float(unassigned), _dev_ptr(out, "out"),
                                         _dev_ptr(mask, "mask", (H, mask_words(W))), _stream_ptr(stream)),
               "dare_reslice_scalar")
+
+    def fill_holes(self, radius_vox=1, min_neighbours=1, stream=None):
+        """Hole filling of the compounded volume (the comparator's, Sec. 2.2)."""
+        check(lib().dare_fill_holes(self._h, int(radius_vox), int(min_neighbours), _stream_ptr(stream)),
+              "dare_fill_holes")
+
+    def reslice_scalar_filled(self, image_to_world, out, mask, px_mm, unassigned=0.0, stream=None):
+        H, W = (int(x) for x in out.shape)
+        pl = make_plane(W, H, px_mm, image_to_world)
+        check(lib().dare_reslice_scalar_filled(self._h, ctypes.byref(pl), float(unassigned), _dev_ptr(out, "out"),
+                                               _dev_ptr(mask, "mask", (H, mask_words(W))), _stream_ptr(stream)),
+              "dare_reslice_scalar_filled")
+
+    def read_filled(self):
+        """Host copy of the hole-filled volume, flat (x fastest), NaN = empty."""
+        out = np.empty(int(np.prod(self.info().dims[:])), np.float32)
+        check(lib().dare_session_read_filled(self._h, out.ctypes.data_as(ctypes.c_void_p)), "dare_session_read_filled")
+        return out
 
     def footprint(self, poses, width, height, px_mm, stream=None):
         poses = np.asarray(poses, dtype=np.float64).reshape(-1, 4, 4)

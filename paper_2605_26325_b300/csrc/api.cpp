@@ -305,6 +305,9 @@ struct dare_session_s {
     int32_t n_curv = 0;                    // frames from a curvilinear probe
     dare_probe probe{};                    // probe of the frames appended from now on
     uint32_t* pix_mask = nullptr;          // its pixel mask (device bitmap), or NULL
+    float* filled = nullptr;               // hole-filled compounded volume (NaN = empty), or NULL
+    size_t filled_bytes = 0;
+    int64_t filled_version = -1;           // session version it was computed at
     size_t pix_mask_bytes = 0;
     int32_t pm_w = 0, pm_h = 0;
     int32_t n_frames = 0;
@@ -1086,6 +1089,10 @@ dare_status dare_session_destroy(dare_session s) {
         s->dev_free(s->pix_mask, s->pix_mask_bytes, s->last_stream);
         g_in_use -= static_cast<int64_t>(s->pix_mask_bytes);
     }
+    if (s->filled) {
+        s->dev_free(s->filled, s->filled_bytes, s->last_stream);
+        g_in_use -= static_cast<int64_t>(s->filled_bytes);
+    }
     if (s->order_ev) cudaEventDestroy(s->order_ev);
     delete s;
     return DARE_OK;
@@ -1575,6 +1582,70 @@ dare_status dare_reslice_scalar(dare_session s, const dare_plane* plane, float u
     return session_end(s, st);
 }
 
+dare_status dare_fill_holes(dare_session s, int32_t radius_vox, int32_t min_neighbours, void* stream) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    if (!s->ssum) return fail(DARE_E_STATE, "session was created without DARE_SESSION_SCALAR");
+    if (radius_vox < 1 || radius_vox > 8) return fail(DARE_E_INVALID, "radius_vox must be in [1, 8]");
+    const int cube = (2 * radius_vox + 1) * (2 * radius_vox + 1) * (2 * radius_vox + 1) - 1;
+    if (min_neighbours < 0 || min_neighbours > cube)
+        return fail(DARE_E_INVALID, "min_neighbours must be in [0, %d]", cube);
+    DeviceGuard dg(s->cfg.device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    dare_status rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    if (!s->filled) {
+        const size_t bytes = align_up(size_t(s->n_vox) * 4, 256);
+        rc = admit(static_cast<int64_t>(bytes));
+        if (rc != DARE_OK) return rc;
+        s->filled = static_cast<float*>(s->dev_alloc(bytes, st));
+        if (!s->filled) {
+            g_in_use -= static_cast<int64_t>(bytes);
+            return fail(DARE_E_OOM, "hole-filled volume allocation of %zu bytes failed", bytes);
+        }
+        s->filled_bytes = bytes;
+    }
+    {
+        KernelScope ks("fill_holes", st, 1);
+        CUDA_TRY(launch_fill_holes(s->cfg.grid.dims, radius_vox, min_neighbours, s->ssum, s->scnt, s->filled, st));
+    }
+    s->filled_version = s->version;
+    return session_end(s, st);
+}
+
+dare_status dare_reslice_scalar_filled(dare_session s, const dare_plane* plane, float unassigned, float* out_dev,
+                                       uint32_t* mask_dev, void* stream) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    dare_status rc = check_plane(plane);
+    if (rc != DARE_OK) return rc;
+    if (!s->filled || s->filled_version != s->version)
+        return fail(DARE_E_STATE, "no hole-filled volume for the session's current frames (call dare_fill_holes)");
+    if (!out_dev || !mask_dev) return fail(DARE_E_INVALID, "output pointers are NULL");
+    if (!affine_ok(s->cfg.grid.vol_to_world, s->cfg.grid.spacing_mm, plane->image_to_world, plane->width,
+                   plane->px_mm[0], plane->px_mm[1]))
+        return fail(DARE_E_INVALID, "plane too far from the grid for fixed-point coordinates");
+    DeviceGuard dg(s->cfg.device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    ResliceJob job = make_job(s, plane, nullptr, out_dev, mask_dev, unassigned);
+    {
+        KernelScope ks("reslice_values", st, 1);
+        CUDA_TRY(launch_reslice_values(job, s->filled, st));
+    }
+    return session_end(s, st);
+}
+
+dare_status dare_session_read_filled(dare_session s, float* values) {
+    if (!s || !values) return fail(DARE_E_INVALID, "NULL argument");
+    if (!s->filled || s->filled_version != s->version)
+        return fail(DARE_E_STATE, "no hole-filled volume for the session's current frames (call dare_fill_holes)");
+    DeviceGuard dg(s->cfg.device);
+    CUDA_TRY(cudaEventSynchronize(s->order_ev));
+    CUDA_TRY(cudaMemcpy(values, s->filled, size_t(s->n_vox) * 4, cudaMemcpyDeviceToHost));
+    return DARE_OK;
+}
+
 dare_status dare_footprint(dare_session s, const dare_plane* planes, int32_t n, int64_t* counts, void* stream) {
     if (!s || (n > 0 && (!planes || !counts)) || n < 0) return fail(DARE_E_INVALID, "bad arguments");
     for (int32_t i = 0; i < n; ++i) {
@@ -1632,6 +1703,7 @@ dare_status dare_session_reset(dare_session s, void* stream) {
     s->frames_host.clear();
     s->probe_host.clear();
     s->n_curv = 0;
+    s->filled_version = -1;
     s->n_frames = 0;
     s->version = 0;
     s->fresh = true;

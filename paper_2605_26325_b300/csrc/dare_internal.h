@@ -140,6 +140,10 @@ cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* en
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
                                   cudaStream_t st);
 cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned long long* count, cudaStream_t st);
+// hole filling of the compounded volume (NaN = still empty) and the trilinear reslice of such a volume
+cudaError_t launch_fill_holes(const int32_t dims[3], int radius, int min_neighbours, const uint32_t* scal_sum,
+                              const uint32_t* scal_cnt, float* out, cudaStream_t st);
+cudaError_t launch_reslice_values(const ResliceJob& job, const float* values, cudaStream_t st);
 cudaError_t launch_fill_records(uint8_t* rec, int64_t n_vox, int rec_bytes, int K, cudaStream_t st);
 
 // any radius and distance kernel (kernels_radius.cu): per-pixel gather, and the

@@ -9,6 +9,7 @@
 #include <cuda_fp16.h>
 
 #include <cfloat>
+#include <algorithm>
 #include <climits>
 
 #include "dare_internal.h"
@@ -253,6 +254,80 @@ __global__ void __launch_bounds__(256) k_reslice_scalar(const __grid_constant__ 
     if (lane == 0) J.mask[static_cast<int64_t>(v) * J.mask_stride + blockIdx.x] = bits;
 }
 
+// Hole filling of the compounded volume (the PLUS baseline of Sec. 2.2 runs
+// mean compounding "with hole-filling"): an occupied voxel keeps its mean, an
+// empty one takes the 1/distance-weighted mean of the occupied voxels of its
+// (2r+1)^3 cube when at least min_nb are occupied, else NaN (empty).
+__global__ void __launch_bounds__(256) k_fill_holes(int3 dims, int r, int min_nb, const uint32_t* __restrict__ ssum,
+                                                    const uint32_t* __restrict__ scnt, float* __restrict__ out) {
+    const int64_t n = static_cast<int64_t>(dims.x) * dims.y * dims.z;
+    for (int64_t vi = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; vi < n;
+         vi += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint32_t c = __ldg(scnt + vi);
+        if (c > 0) {
+            out[vi] = __fdiv_rn(static_cast<float>(__ldg(ssum + vi)), static_cast<float>(c));
+            continue;
+        }
+        const int x = static_cast<int>(vi % dims.x), y = static_cast<int>((vi / dims.x) % dims.y);
+        const int z = static_cast<int>(vi / (static_cast<int64_t>(dims.x) * dims.y));
+        float num = 0.0f, den = 0.0f;
+        int cnt = 0;
+        for (int dz = -r; dz <= r; ++dz) {
+            const int cz = z + dz;
+            if (cz < 0 || cz >= dims.z) continue;
+            for (int dy = -r; dy <= r; ++dy) {
+                const int cy = y + dy;
+                if (cy < 0 || cy >= dims.y) continue;
+                const int64_t row = dims.x * (cy + static_cast<int64_t>(dims.y) * cz);
+                for (int dx = -r; dx <= r; ++dx) {
+                    const int cx = x + dx;
+                    if (cx < 0 || cx >= dims.x) continue;
+                    const uint32_t cc = __ldg(scnt + row + cx);
+                    if (cc == 0) continue;  // also the voxel itself
+                    const float S = __fdiv_rn(static_cast<float>(__ldg(ssum + row + cx)), static_cast<float>(cc));
+                    const float w = __frsqrt_rn(static_cast<float>(dx * dx + dy * dy + dz * dz));
+                    num = fmaf(w, S, num);
+                    den += w;
+                    ++cnt;
+                }
+            }
+        }
+        out[vi] = (cnt >= min_nb && cnt > 0) ? num / den : __int_as_float(0x7fc00000);
+    }
+}
+
+// Trilinear reslice of a scalar volume (NaN = empty voxel), renormalised over
+// the non-empty corners: the comparator's blend on the hole-filled volume.
+__global__ void __launch_bounds__(256) k_reslice_values(const __grid_constant__ ResliceJob J,
+                                                        const float* __restrict__ values) {
+    const int lane = threadIdx.x;
+    const int u = blockIdx.x * 32 + lane;
+    const int v = blockIdx.y * 8 + threadIdx.y;
+    if (v >= J.height) return;
+    const bool active = u < J.width;
+    float num = 0.0f, den = 0.0f;
+    if (active) {
+        const PixelCoord pc = pixel_coord(J, u, v);
+        if (pc.any) {
+            for (int corner = 0; corner < 8; ++corner) {
+                const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
+                const int cx = pc.c0[0] + dx, cy = pc.c0[1] + dy, cz = pc.c0[2] + dz;
+                if (cx < 0 || cy < 0 || cz < 0 || cx >= J.dims[0] || cy >= J.dims[1] || cz >= J.dims[2]) continue;
+                const int64_t vi = cx + static_cast<int64_t>(J.dims[0]) * (cy + static_cast<int64_t>(J.dims[1]) * cz);
+                const float S = __ldg(values + vi);
+                if (isnan(S)) continue;
+                const float t = (dx ? pc.fr[0] : 1.0f - pc.fr[0]) * (dy ? pc.fr[1] : 1.0f - pc.fr[1]) *
+                                (dz ? pc.fr[2] : 1.0f - pc.fr[2]);
+                num = fmaf(t, S, num);
+                den += t;
+            }
+        }
+        J.out[static_cast<int64_t>(v) * J.width + u] = den > 0.0f ? num / den : J.unassigned;
+    }
+    const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);
+    if (lane == 0) J.mask[static_cast<int64_t>(v) * J.mask_stride + blockIdx.x] = bits;
+}
+
 __global__ void __launch_bounds__(256) k_footprint(const __grid_constant__ ResliceJob J, uint32_t* bitmap,
                                                    unsigned long long* count) {
     const int u = blockIdx.x * 32 + threadIdx.x;
@@ -328,6 +403,22 @@ cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, in
     k_scan_reduce<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums);
     k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb);
     k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums, out);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_fill_holes(const int32_t dims[3], int radius, int min_neighbours, const uint32_t* scal_sum,
+                              const uint32_t* scal_cnt, float* out, cudaStream_t st) {
+    const int64_t n = int64_t(dims[0]) * dims[1] * dims[2];
+    if (n <= 0) return cudaSuccess;
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, 148 * 64);
+    k_fill_holes<<<static_cast<unsigned>(blocks), 256, 0, st>>>(make_int3(dims[0], dims[1], dims[2]), radius,
+                                                                 min_neighbours, scal_sum, scal_cnt, out);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_reslice_values(const ResliceJob& job, const float* values, cudaStream_t st) {
+    dim3 grid((job.width + 31) / 32, (job.height + 7) / 8);
+    k_reslice_values<<<grid, dim3(32, 8), 0, st>>>(job, values);
     return cudaPeekAtLastError();
 }
 
