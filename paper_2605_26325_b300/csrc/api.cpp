@@ -313,6 +313,8 @@ struct dare_session_s {
     int32_t n_frames = 0;
     int64_t version = 0;
     bool fresh = true;                     // no sample stored since create / reset: finalize skips reading records
+    bool pending_clear = false;            // reset but not yet cleared: the next build writes every voxel,
+                                           // any other call clears the volume first
     int64_t volume_bytes = 0;
     void* host_vol = nullptr;              // DARE_SESSION_HOST_VOLUME: the mapped host block
     void* ws = nullptr;
@@ -374,9 +376,30 @@ dare_status admit(int64_t bytes) {
     }
 }
 
+// Empty volume on st: empty records, zero npix and scalar totals.
+dare_status clear_volume(dare_session s, cudaStream_t st) {
+    {
+        KernelScope ks("fill_records", st, 1);
+        CUDA_TRY(launch_fill_records(s->rec, s->n_vox, s->rec_bytes, s->K, st));
+    }
+    CUDA_TRY(cudaMemsetAsync(s->npix, 0, size_t(s->n_vox) * s->K * 2, st));
+    if (s->ssum) {
+        CUDA_TRY(cudaMemsetAsync(s->ssum, 0, size_t(s->n_vox) * 4, st));
+        CUDA_TRY(cudaMemsetAsync(s->scnt, 0, size_t(s->n_vox) * 4, st));
+    }
+    return DARE_OK;
+}
+
 // Order a call after the session's previous one, whatever stream that used.
-dare_status session_begin(dare_session s, cudaStream_t st) {
+// A clear deferred by dare_session_reset is queued first, unless the caller
+// takes it over (a build: its first finalize writes every voxel).
+dare_status session_begin(dare_session s, cudaStream_t st, bool settle = true) {
     CUDA_TRY(cudaStreamWaitEvent(st, s->order_ev, 0));
+    if (settle && s->pending_clear) {
+        dare_status rc = clear_volume(s, st);
+        if (rc != DARE_OK) return rc;
+        s->pending_clear = false;
+    }
     return DARE_OK;
 }
 
@@ -384,6 +407,15 @@ dare_status session_end(dare_session s, cudaStream_t st) {
     CUDA_TRY(cudaEventRecord(s->order_ev, st));
     s->last_stream = st;
     return DARE_OK;
+}
+
+// A deferred clear queued now (legacy stream) for the synchronous calls and
+// for callers with their own ordering; they then wait for order_ev.
+dare_status settle_now(dare_session s) {
+    if (!s->pending_clear) return DARE_OK;
+    dare_status rc = session_begin(s, nullptr);
+    if (rc != DARE_OK) return rc;
+    return session_end(s, nullptr);
 }
 
 dare_status ensure_workspace(dare_session s, size_t bytes, cudaStream_t st) {
@@ -1132,6 +1164,8 @@ dare_status dare_session_read_records(dare_session s, uint16_t* frame_ids, void*
     if (!s) return fail(DARE_E_INVALID, "session is NULL");
     if ((scalar_sum || scalar_count) && !s->ssum) return fail(DARE_E_STATE, "session keeps no scalar totals");
     DeviceGuard dg(s->cfg.device);
+    dare_status rc = settle_now(s);
+    if (rc != DARE_OK) return rc;
     CUDA_TRY(cudaEventSynchronize(s->order_ev));
     const int vb = value_bytes(s->dtype);
     if (frame_ids || values) {
@@ -1223,7 +1257,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                                 : static_cast<int32_t>(std::min<int64_t>(
                                       n_chunk, slice_frames > 0 ? slice_frames
                                                                 : std::max<int64_t>(1, (int64_t(32) << 20) / npx)));
-    dare_status rc = session_begin(s, st);
+    dare_status rc = session_begin(s, st, false);  // a pending clear is left to the first finalize
     if (rc != DARE_OK) return rc;
     rc = ensure_workspace(s, ws_need, st);
     if (rc != DARE_OK) return rc;
@@ -1308,11 +1342,12 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
             CUDA_TRY(launch_scatter_place(a, pairs, n_pairs, s->count, offsets, entries, st));
         }
         {
-            const int fresh = s->fresh ? 1 : 0;
-            s->fresh = false;  // from here on the records may hold samples
+            const int mode = s->pending_clear ? 2 : (s->fresh ? 1 : 0);
+            s->pending_clear = false;  // this finalize writes every voxel
+            s->fresh = false;          // from here on the records may hold samples
             KernelScope ks("finalize", st, 1);
             CUDA_TRY(launch_finalize(offsets, entries, s->n_vox, s->rec, s->npix, s->ssum, s->scnt, s->K, s->dtype,
-                                     fresh, s->overflow_dev, st));
+                                     mode, s->overflow_dev, st));
         }
     }
     rc = session_end(s, st);
@@ -1686,20 +1721,14 @@ dare_status dare_session_reset(dare_session s, void* stream) {
     if (!s) return fail(DARE_E_INVALID, "session is NULL");
     DeviceGuard dg(s->cfg.device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    dare_status rc = session_begin(s, st);
+    // the volume itself is cleared lazily: by the next build's finalize, which
+    // writes every voxel, or before any other call that reads it
+    dare_status rc = session_begin(s, st, false);
     if (rc != DARE_OK) return rc;
-    {
-        KernelScope ks("fill_records", st, 1);
-        CUDA_TRY(launch_fill_records(s->rec, s->n_vox, s->rec_bytes, s->K, st));
-    }
-    CUDA_TRY(cudaMemsetAsync(s->npix, 0, size_t(s->n_vox) * s->K * 2, st));
-    if (s->ssum) {
-        CUDA_TRY(cudaMemsetAsync(s->ssum, 0, size_t(s->n_vox) * 4, st));
-        CUDA_TRY(cudaMemsetAsync(s->scnt, 0, size_t(s->n_vox) * 4, st));
-    }
     CUDA_TRY(cudaMemsetAsync(s->overflow_dev, 0, sizeof(unsigned long long), st));
     rc = session_end(s, st);
     if (rc != DARE_OK) return rc;
+    s->pending_clear = true;
     s->frames_host.clear();
     s->probe_host.clear();
     s->n_curv = 0;
@@ -1772,6 +1801,8 @@ constexpr int32_t kFileProbes = 1 << 8;
 dare_status dare_session_save(dare_session s, const char* path) {
     if (!s || !path) return fail(DARE_E_INVALID, "NULL argument");
     DeviceGuard dg(s->cfg.device);
+    dare_status rc0 = settle_now(s);
+    if (rc0 != DARE_OK) return rc0;
     CUDA_TRY(cudaEventSynchronize(s->order_ev));
     std::vector<uint8_t> rec(size_t(s->n_vox) * s->rec_bytes);
     std::vector<uint8_t> np(size_t(s->n_vox) * s->K * 2);
@@ -1920,6 +1951,14 @@ dare_status dare_session_load(const dare_session_config* cfg, const char* path, 
 namespace dare {
 
 dare_status set_error(dare_status st, const char* msg) { return fail(st, "%s", msg); }
+
+dare_status settle_session(dare_session s, cudaStream_t st) {
+    if (!s->pending_clear) return DARE_OK;
+    dare_status rc = settle_now(s);
+    if (rc != DARE_OK) return rc;
+    CUDA_TRY(cudaStreamWaitEvent(st, s->order_ev, 0));
+    return DARE_OK;
+}
 
 dare_status reserve_bytes(int64_t bytes) { return admit(bytes); }
 void release_bytes(int64_t bytes) { g_in_use -= bytes; }
@@ -2223,6 +2262,8 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
     }
     // tuning and capture run on the plan's own stream, after the sessions' queued work
     for (auto* s : p->sessions) {
+        rc = settle_now(s);
+        if (rc != DARE_OK) return bail(rc);
         if (cudaStreamWaitEvent(p->cap, s->order_ev, 0) != cudaSuccess) return bail(fail(DARE_E_CUDA, "wait failed"));
     }
     if (params->path == DARE_PATH_AUTO && !general_support(params))  // general kernels: tiled, no tuning

@@ -133,9 +133,11 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
                                   int64_t block_sums_len, cudaStream_t st);
 int64_t scan_block_sums_needed(int64_t n);
-// fresh != 0: the volume holds no sample (created or reset since): stored records are not read
+// mode 0: merge into the stored records; 1: the volume holds no sample (created or
+// reset since), stored records are not read; 2: as 1 and not cleared since a reset:
+// every voxel's record, npix row and scalar totals are written (empty where no entry)
 cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
-                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int fresh,
+                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode,
                             unsigned long long* overflow, cudaStream_t st);
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
                                   cudaStream_t st);
@@ -174,6 +176,9 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
                         uint8_t* ws, uint8_t* pin);
 dare_status reserve_bytes(int64_t bytes);
 void release_bytes(int64_t bytes);
+
+// a clear deferred by dare_session_reset, queued and ordered before work on st (server batches)
+dare_status settle_session(dare_session s, cudaStream_t st);
 
 // allocation-free reslice support (api.cpp)
 dare_status set_error(dare_status st, const char* msg);

@@ -325,9 +325,12 @@ __device__ __forceinline__ bool append_in_order(const unsigned long long* __rest
     }
 }
 
-// kFresh: the volume holds no sample at all (just created or reset), so the
-// stored records are known to be empty and are not read.
-template <int K, typename VT, bool kFresh>
+// kMode 0: merge into the stored records.  1 (fresh): the volume holds no
+// sample at all, so the stored records are known to be empty and are not read.
+// 2 (full): as 1, and the volume has not been cleared since a reset: every
+// voxel is written, empty ones with the empty record, zero npix and zero
+// scalar totals, which spares the reset a pass over the whole volume.
+template <int K, typename VT, int kMode>
 __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ offsets,
                                                   const unsigned long long* __restrict__ entries, int64_t n_vox,
                                                   uint8_t* __restrict__ rec, uint16_t* __restrict__ npix,
@@ -340,12 +343,37 @@ __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ of
     __shared__ uint2 s_np[256 * K / 4];
     uint4* my_rec = s_rec + threadIdx.x * (RB / 16);
     uint2* my_np = s_np + threadIdx.x * (K / 4);
+    constexpr bool kFresh = kMode != 0;
     for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n_vox;
          v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int s = offsets[v], e = offsets[v + 1];
-        if (s == e) continue;
         uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
         uint2* g_np = reinterpret_cast<uint2*>(npix + v * K);
+        if (s == e) {
+            if (kMode == 2) {
+#pragma unroll
+                for (int i = 0; i < RB / 16; ++i) {
+                    uint4 q = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+                    for (int w = 0; w < 4; ++w) {
+                        const int b = 16 * i + 4 * w;
+                        uint32_t x = 0u;
+#pragma unroll
+                        for (int h = 0; h < 2; ++h)
+                            if (b + 2 * h < 2 * K) x |= 0xFFFFu << (16 * h);
+                        (w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w) = x;
+                    }
+                    g_rec[i] = q;
+                }
+#pragma unroll
+                for (int i = 0; i < K / 4; ++i) g_np[i] = make_uint2(0u, 0u);
+                if (scal_sum) {
+                    scal_sum[v] = 0u;
+                    scal_cnt[v] = 0u;
+                }
+            }
+            continue;
+        }
         if (kFresh) {
             // empty record: ids 0xFFFF, values and npix 0
 #pragma unroll
@@ -390,14 +418,14 @@ __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ of
 #pragma unroll
         for (int i = 0; i < K / 4; ++i) g_np[i] = my_np[i];
         if (scal_sum) {
-            scal_sum[v] += tot_sum;
-            scal_cnt[v] += tot_cnt;
+            scal_sum[v] = kMode == 2 ? tot_sum : scal_sum[v] + tot_sum;
+            scal_cnt[v] = kMode == 2 ? tot_cnt : scal_cnt[v] + tot_cnt;
         }
         if (over) atomicAdd(overflow, 1ull);
     }
 }
 
-template <int K, bool kFresh>
+template <int K, int kMode>
 cudaError_t finalize_kf(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
                         uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, unsigned long long* ovf,
                         cudaStream_t st) {
@@ -406,16 +434,16 @@ cudaError_t finalize_kf(const int32_t* off, const unsigned long long* ent, int64
     const int blocks = static_cast<int>(want < 148 * 64 ? want : 148 * 64);
     switch (dtype) {
     case DARE_U8:
-        k_finalize<K, uint8_t, kFresh><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, uint8_t, kMode><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
     case DARE_F16:
-        k_finalize<K, __half, kFresh><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, __half, kMode><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
     case DARE_BF16:
-        k_finalize<K, __nv_bfloat16, kFresh><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, __nv_bfloat16, kMode><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
     case DARE_F32:
-        k_finalize<K, float, kFresh><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, float, kMode><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -424,10 +452,14 @@ cudaError_t finalize_kf(const int32_t* off, const unsigned long long* ent, int64
 
 template <int K>
 cudaError_t finalize_k(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
-                       uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int fresh, unsigned long long* ovf,
+                       uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int mode, unsigned long long* ovf,
                        cudaStream_t st) {
-    return fresh ? finalize_kf<K, true>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st)
-                 : finalize_kf<K, false>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
+    switch (mode) {
+    case 0: return finalize_kf<K, 0>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
+    case 1: return finalize_kf<K, 1>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
+    case 2: return finalize_kf<K, 2>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 dim3 scatter_grid(const ScatterArgs& a) {
@@ -453,13 +485,13 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
 }
 
 cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
-                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int fresh,
+                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode,
                             unsigned long long* overflow, cudaStream_t st) {
     switch (K) {
-    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, fresh, overflow, st);
-    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, fresh, overflow, st);
-    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, fresh, overflow, st);
-    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, fresh, overflow, st);
+    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, overflow, st);
+    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, overflow, st);
+    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, overflow, st);
+    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, overflow, st);
     }
     return cudaErrorInvalidValue;
 }

@@ -159,6 +159,7 @@ void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& b
     for (auto& r : reqs) {
         auto it = sv->write_ev.find(r.session);
         if (it != sv->write_ev.end()) cudaStreamWaitEvent(L.st, it->second, 0);
+        dare::settle_session(r.session, L.st);  // a reset volume not yet cleared
     }
     dare_status rc = dare::queue_batch(reqs.data(), n, &sv->cfg.params, L.st, static_cast<uint8_t*>(L.ws),
                                        static_cast<uint8_t*>(L.pin));

@@ -447,3 +447,60 @@ def test_host_volume_session_equals_device(tiny):
             assert np.array_equal(m1, m2) and np.array_equal(o1, o2)
     for s in (dev, host, ref):
         s.close()
+
+
+@pytest.mark.parametrize("flags", [dare.DARE_SESSION_SCALAR, dare.DARE_SESSION_SCALAR | dare.DARE_SESSION_HOST_VOLUME])
+def test_reset_is_cleared_by_the_next_call(tiny, tmp_path, flags):
+    """dare_session_reset defers the clear: the next build's finalize writes
+    every voxel (records, npix, scalar totals), and any other call clears the
+    volume first.  Each route gives exactly the volume (or the unassigned
+    image) of a session that never held the old frames."""
+    ft = torch.from_numpy(tiny.frames).to(DEV)
+    a, b = slice(0, 120), slice(80, 200)
+    fresh = gpu_session(tiny, dare.DARE_F16, 8, flags=flags, frames=tiny.frames[b], poses=tiny.frame_poses[b])
+    ref = fresh.read_records(npix=True, scalar=True)
+    s = gpu_session(tiny, dare.DARE_F16, 8, flags=flags, frames=tiny.frames[a], poses=tiny.frame_poses[a])
+    # reset + build: the full-write finalize
+    s.reset()
+    s.build(ft[b], tiny.frame_poses[b], tiny.frame_px)
+    got = s.read_records(npix=True, scalar=True)
+    for k in ("frame_ids", "npix", "scalar_sum", "scalar_count"):
+        assert np.array_equal(got[k], ref[k]), k
+    assert np.array_equal(got["values"].view(np.uint16), ref["values"].view(np.uint16))
+    T = tiny.reslice_poses[3]
+    o1, m1 = gpu_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, dare.params_default())
+    o2, m2 = gpu_reslice(fresh, T, tiny.out_w, tiny.out_h, tiny.out_px, dare.params_default())
+    assert np.array_equal(m1, m2) and np.array_equal(o1, o2)
+    # reset + every reading call: an empty volume
+    for route in ("reslice", "batch", "scalar", "holes", "save"):
+        s.reset()
+        out, mask = new_outputs(40, 30)
+        if route == "reslice":
+            s.reslice(T, out, mask, tiny.out_px)
+        elif route == "batch":
+            dare.reslice_batch([(s, T, out, mask, tiny.out_px)])
+        elif route == "scalar":
+            s.reslice_scalar(T, out, mask, tiny.out_px)
+        elif route == "holes":
+            s.fill_holes(1, 1)
+            assert np.all(np.isnan(s.read_filled()))
+            s.reslice_scalar_filled(T, out, mask, tiny.out_px)
+        else:
+            path = str(tmp_path / "reset.dare")
+            s.save(path)
+            r = dare.Session.load(path)
+            e = r.read_records(npix=True, scalar=True)
+            assert np.all(e["frame_ids"] == 0xFFFF) and not e["npix"].any() and not e["scalar_count"].any()
+            r.close()
+            s.reslice(T, out, mask, tiny.out_px)
+        torch.cuda.synchronize()
+        assert not mask.cpu().numpy().any(), route
+        assert np.all(out.cpu().numpy() == 0.0), route
+        e = s.read_records(npix=True, scalar=True)
+        assert np.all(e["frame_ids"] == 0xFFFF) and not e["npix"].any() and not e["scalar_sum"].any()
+        s.build(ft[b], tiny.frame_poses[b], tiny.frame_px)  # merge into the cleared volume: as fresh
+        got = s.read_records(npix=True, scalar=True)
+        assert np.array_equal(got["frame_ids"], ref["frame_ids"]) and np.array_equal(got["npix"], ref["npix"])
+        assert np.array_equal(got["scalar_sum"], ref["scalar_sum"])
+    s.close()
+    fresh.close()
