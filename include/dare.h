@@ -545,9 +545,12 @@ dare_status dare_session_read_filled(dare_session s, float* values);
 dare_status dare_footprint(dare_session s, const dare_plane* planes, int32_t n, int64_t* counts, void* stream);
 
 /*
- * Empty the volume (all samples, frame ids and scalar totals) on `stream`,
- * keeping its allocation, grid and configuration; the next build starts at
- * frame id 0.  Asynchronous.
+ * Empty the volume (all samples, frame ids and scalar totals), keeping its
+ * allocation, grid and configuration; the next build starts at frame id 0.
+ * Asynchronous.  The device-side clear is deferred: the next build writes
+ * every voxel in its finalize pass (so a reset + rebuild costs no separate
+ * pass over the volume), and any other call that reads the volume first
+ * queues the clear on its own stream.  Every call sees an empty volume.
  */
 dare_status dare_session_reset(dare_session s, void* stream);
 
