@@ -34,7 +34,8 @@ class _Params(ctypes.Structure):
                 ("radius", ctypes.c_int32), ("kernel", ctypes.c_int32),
                 ("normal_axis", ctypes.c_int32), ("use_exact", ctypes.c_int32),
                 ("probe", ctypes.c_int32), ("pad", ctypes.c_int32),
-                ("apex_x", ctypes.c_double), ("apex_y", ctypes.c_double)]
+                ("apex_x", ctypes.c_double), ("apex_y", ctypes.c_double),
+                ("sample_weight", ctypes.c_int32), ("pad2", ctypes.c_int32)]
 
 
 @dataclass
@@ -55,12 +56,13 @@ class Params:
     use_exact: bool = False
     probe: int = LINEAR
     apex_mm: tuple = (0.0, 0.0)
+    per_pixel: bool = False   # every pixel its own sample: merged samples weighted by npix
 
     def _c(self):
         return _Params(self.k_normal, self.k_inplane, self.thr_normal_deg, self.thr_inplane_deg,
                        self.k_dist, self.unassigned, int(self.radius), int(self.kernel),
                        int(self.normal_axis), int(bool(self.use_exact)), int(self.probe), 0,
-                       float(self.apex_mm[0]), float(self.apex_mm[1]))
+                       float(self.apex_mm[0]), float(self.apex_mm[1]), int(bool(self.per_pixel)), 0)
 
 
 def _P(t):

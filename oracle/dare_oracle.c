@@ -53,7 +53,12 @@
  *     way at every output pixel, about its own apex.  Eq. 1 and Eq. 2 are
  *     unchanged, applied to the turned axes;
  *   - pixel mask: a build may exclude pixels (the dark corners outside a fan
- *     image); an excluded pixel is never voxelised.
+ *     image); an excluded pixel is never voxelised;
+ *   - per-pixel samples (the other reading of Sec. 2.1's storage, where every
+ *     pixel is kept as its own sample with its frame's orientation): all of a
+ *     frame's pixels in a voxel share the orientation weight, so their sum
+ *     w * sum(I) equals the merged sample's w * npix * mean; sample_weight 1
+ *     weights each merged sample by its npix, which is that reading exactly.
  *
  * Arithmetic is FP64 throughout except the storage rounding, which is the
  * storage type's own.  Compile with -ffp-contract=off.
@@ -90,6 +95,8 @@ typedef struct {
     int32_t probe;                     /* virtual probe: ORA_LINEAR / ORA_CURVILINEAR */
     int32_t pad;
     double apex_x, apex_y;             /* curvilinear virtual probe: fan apex, image point (mm) */
+    int32_t sample_weight;             /* 0: one sample per (voxel, frame); 1: per pixel (see below) */
+    int32_t pad2;
 } ora_params;
 
 typedef struct {
@@ -589,8 +596,9 @@ static void reslice_pixel(const ora_volume* v, const plane_ctx* c0, const ora_pa
                 for (int64_t s = v->offsets[vi]; s < v->offsets[vi + 1]; ++s) {
                     double w = orientation_weight(v->quat + 4 * s, c, p);
                     double I = p->use_exact ? v->mean_exact[s] : v->stored[s];
-                    num += t * w * I;
-                    den += t * w;
+                    double m = p->sample_weight ? (double)v->npix[s] : 1.0;
+                    num += t * w * m * I;
+                    den += t * w * m;
                 }
             }
     if (den > 0) {

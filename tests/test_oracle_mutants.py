@@ -86,6 +86,8 @@ MUTANTS = {
         ("const double S = values[cx + (int64_t)dims[0] * (cy + (int64_t)dims[1] * cz)];\n                if (isnan(S)) continue;",
          "const double S0 = values[cx + (int64_t)dims[0] * (cy + (int64_t)dims[1] * cz)];\n"
          "                const double S = isnan(S0) ? 0.0 : S0;"),
+    "per-pixel weight missing from the denominator":
+        ("                    den += t * w * m;", "                    den += t * w;"),
     "unassigned when the numerator is zero":
         ("    if (den > 0) {\n        *out = num / den;", "    if (num > 0) {\n        *out = num / den;"),
 }
