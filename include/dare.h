@@ -141,6 +141,13 @@ typedef enum { DARE_NORMAL_BEAM = 0, DARE_NORMAL_ELEVATION = 1 } dare_normal_axi
 typedef enum { DARE_WEIGHTS_F32 = 0, DARE_WEIGHTS_F16 = 1 } dare_weight_dtype;
 typedef enum { DARE_PATH_AUTO = 0, DARE_PATH_PLAIN = 1, DARE_PATH_TILED = 2 } dare_path;
 typedef enum { DARE_PROBE_LINEAR = 0, DARE_PROBE_CURVILINEAR = 1 } dare_probe_kind;
+/* What a stored sample stands for (Sec. 2.1 stores "the intensity values at
+ * that voxel"): MEAN, one sample per (voxel, frame), the mean of that frame's
+ * pixels in the voxel (default); PIXELS, every pixel its own sample with its
+ * frame's orientation, which is the stored sample weighted by its pixel count
+ * (the frame's pixels in a voxel share one orientation weight).  PIXELS runs
+ * on the general kernels. */
+typedef enum { DARE_SAMPLE_MEAN = 0, DARE_SAMPLE_PIXELS = 1 } dare_sample_weight;
 
 /* Probe geometry (see "Curvilinear probes"): kind, and for a curvilinear
  * probe the apex of its beam fan as an image point (x, y) in mm. */
@@ -219,6 +226,8 @@ typedef struct {
     int32_t weight_dtype;   /* dare_weight_dtype of the per-frame weight table */
     int32_t path;           /* dare_path: kernel choice (linear probes) */
     dare_probe probe;       /* virtual probe of the planes (default linear) */
+    int32_t sample_weight;  /* dare_sample_weight (default MEAN) */
+    int32_t reserved;
 } dare_params;
 
 /* A virtual image plane: output size, pixel spacing and pose. */

@@ -27,6 +27,7 @@ DARE_NORMAL_BEAM, DARE_NORMAL_ELEVATION = 0, 1
 DARE_WEIGHTS_F32, DARE_WEIGHTS_F16 = 0, 1
 DARE_PATH_AUTO, DARE_PATH_PLAIN, DARE_PATH_TILED = 0, 1, 2
 DARE_PROBE_LINEAR, DARE_PROBE_CURVILINEAR = 0, 1
+DARE_SAMPLE_MEAN, DARE_SAMPLE_PIXELS = 0, 1
 DARE_SESSION_SCALAR = 1
 DARE_SESSION_L2_PERSIST = 2
 DARE_SESSION_HOST_VOLUME = 4
@@ -77,7 +78,8 @@ class dare_params(ctypes.Structure):
                 ("thr_normal_deg", ctypes.c_double), ("thr_inplane_deg", ctypes.c_double),
                 ("k_dist", ctypes.c_double), ("unassigned", ctypes.c_float), ("radius_vox", ctypes.c_int32),
                 ("dist_kernel", ctypes.c_int32), ("normal_axis", ctypes.c_int32),
-                ("weight_dtype", ctypes.c_int32), ("path", ctypes.c_int32), ("probe", dare_probe)]
+                ("weight_dtype", ctypes.c_int32), ("path", ctypes.c_int32), ("probe", dare_probe),
+                ("sample_weight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class dare_plane(ctypes.Structure):

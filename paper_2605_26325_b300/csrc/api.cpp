@@ -527,6 +527,8 @@ dare_status check_params(const dare_params* p) {
     if (p->probe.kind != DARE_PROBE_LINEAR && p->probe.kind != DARE_PROBE_CURVILINEAR)
         return fail(DARE_E_INVALID, "unknown virtual probe kind %d", p->probe.kind);
     if (!finite_all(p->probe.apex_mm, 2)) return fail(DARE_E_INVALID, "virtual probe apex is not finite");
+    if (p->sample_weight != DARE_SAMPLE_MEAN && p->sample_weight != DARE_SAMPLE_PIXELS)
+        return fail(DARE_E_INVALID, "unknown sample weighting %d", p->sample_weight);
     return DARE_OK;
 }
 
@@ -574,6 +576,7 @@ ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab
         j.b[a] = aff[6 + a];
     }
     j.rec = s->rec;
+    j.npix = (params && params->sample_weight == DARE_SAMPLE_PIXELS) ? s->npix : nullptr;
     j.wtab = wtab;
     j.out = out;
     j.mask = mask;
@@ -626,7 +629,9 @@ ResliceJob make_job(const dare_session s, const dare_plane* pl, const void* wtab
 }
 
 // Any distance kernel but TENT at radius 1 runs on the general kernels (kernels_radius.cu).
-bool general_support(const dare_params* p) { return p->radius_vox != 1 || p->dist_kernel != DARE_TENT; }
+bool general_support(const dare_params* p) {
+    return p->radius_vox != 1 || p->dist_kernel != DARE_TENT || p->sample_weight == DARE_SAMPLE_PIXELS;
+}
 constexpr int kTileHGeneral = 32;  // tile rows of the general tiled kernel
 
 // Shared memory of the general tiled kernel for these jobs: a bound on any

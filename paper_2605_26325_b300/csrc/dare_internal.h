@@ -53,6 +53,7 @@ struct ResliceJob {
     int32_t ext_lo, ext_hi;
     float k_dist;
     int32_t reserved;
+    const uint16_t* npix;       // per-pixel samples: weight each sample by its npix (general kernels); NULL: 1
 };
 
 // Inputs of the per-(plane, frame) weight table of Eq. 1 / Eq. 2.

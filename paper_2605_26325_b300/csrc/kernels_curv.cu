@@ -163,12 +163,23 @@ __device__ __forceinline__ float2 curv_voxel(const CurvJob& C, const PixelAxes& 
     using S = RecShape<K, VT>;
     uint4 r[S::kVec];
     load_record<K, VT>(C.j.rec + vi * S::kBytes, r);
+    // per-pixel samples: each merged sample counts npix times (its pixels share the weight)
+    uint2 n[K / 4];
+    if (C.j.npix) {
+        const uint2* q = reinterpret_cast<const uint2*>(C.j.npix + vi * K);
+#pragma unroll
+        for (int i = 0; i < K / 4; ++i) n[i] = __ldg(q + i);
+    }
     float A = 0.0f, B = 0.0f;
 #pragma unroll
     for (int s = 0; s < K; ++s) {
         const uint32_t id = slot_id<K, VT>(r, s);
         if (id == DARE_EMPTY_FRAME) break;  // empty slots come last
-        const float w = sample_weight(C, P, static_cast<int>(id), ci, cj, ck, u, v);
+        float w = sample_weight(C, P, static_cast<int>(id), ci, cj, ck, u, v);
+        if (C.j.npix) {
+            const uint32_t word = (s & 2) ? n[s >> 2].y : n[s >> 2].x;
+            w *= static_cast<float>((word >> (16 * (s & 1))) & 0xFFFFu);
+        }
         A = fmaf(w, slot_value<K, VT>(r, s), A);
         B += w;
     }

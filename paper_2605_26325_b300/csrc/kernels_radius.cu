@@ -33,6 +33,39 @@ constexpr float kMargin = 0.02f; // voxel; > FP32 error of the plane height for 
 __device__ __forceinline__ float tent_factor(float d, float R) { return 1.0f - __fdiv_rn(fabsf(d), R); }
 __device__ __forceinline__ float exp_weight(float d2, float kr) { return expf(-kr * sqrtf(d2)); }
 
+// npix of slot s from a voxel's npix row held as K/4 uint2
+template <int K>
+__device__ __forceinline__ float slot_npix(const uint2 (&n)[K / 4], int s) {
+    const uint2 q = n[s >> 2];
+    const uint32_t w = (s & 2) ? q.y : q.x;
+    return static_cast<float>((w >> (16 * (s & 1))) & 0xFFFFu);
+}
+
+// (A_c, B_c) of one voxel with every sample weighted by its pixel count: the
+// per-pixel reading of the storage (each pixel a sample with its frame's
+// orientation), exactly, since a frame's pixels in a voxel share one weight.
+template <int K, typename VT, typename WT>
+__device__ __forceinline__ float2 collapse_voxel_px(const uint8_t* rec, const uint16_t* npix, int64_t vi,
+                                                    const WT* wt) {
+    using S = RecShape<K, VT>;
+    uint4 r[S::kVec];
+    load_record<K, VT>(rec + vi * S::kBytes, r);
+    uint2 n[K / 4];
+    const uint2* q = reinterpret_cast<const uint2*>(npix + vi * K);
+#pragma unroll
+    for (int i = 0; i < K / 4; ++i) n[i] = __ldg(q + i);
+    float A = 0.0f, B = 0.0f;
+#pragma unroll
+    for (int s = 0; s < K; ++s) {
+        const uint32_t id = slot_id<K, VT>(r, s);
+        if (id == DARE_EMPTY_FRAME) break;
+        const float w = weight_of(wt, static_cast<int>(id)) * slot_npix<K>(n, s);
+        A = fmaf(w, slot_value<K, VT>(r, s), A);
+        B += w;
+    }
+    return make_float2(A, B);
+}
+
 // Per-pixel gather over the kernel's support (records read from global memory).
 template <int K, typename VT, typename WT>
 __device__ __noinline__ void gather_pixel_r(const ResliceJob& J, int u, int v, float& num, float& den) {
@@ -74,7 +107,8 @@ __device__ __noinline__ void gather_pixel_r(const ResliceJob& J, int u, int v, f
                 else
                     t = exp_weight(dx * dx + dy * dy + dz * dz, kr);
                 const int64_t vi = cx + static_cast<int64_t>(J.dims[0]) * (cy + static_cast<int64_t>(J.dims[1]) * cz);
-                const float2 ab = collapse_voxel<K, VT, WT>(J.rec, vi, wt);
+                const float2 ab = J.npix ? collapse_voxel_px<K, VT, WT>(J.rec, J.npix, vi, wt)
+                                         : collapse_voxel<K, VT, WT>(J.rec, vi, wt);
                 num = fmaf(t, ab.x, num);
                 den = fmaf(t, ab.y, den);
             }
@@ -202,6 +236,7 @@ __device__ __forceinline__ void tile_body_r(const ResliceJob& J, const TileSetup
         const float fu0 = static_cast<float>(u0), fu1 = static_cast<float>(u1);
         const float fv0 = static_cast<float>(v0), fv1 = static_cast<float>(v1);
         const uint8_t* const rec = J.rec;
+        const uint16_t* const npx = J.npix;
         const int64_t sx = 1, sy = J.dims[0], sz = static_cast<int64_t>(J.dims[0]) * J.dims[1];
         const int64_t st1 = E1 == 0 ? sx : sy, st2 = E2 == 1 ? sy : sz, std_ = D == 0 ? sx : (D == 1 ? sy : sz);
         for (int c = threadIdx.x; c < ncol; c += kThreads) {
@@ -222,8 +257,10 @@ __device__ __forceinline__ void tile_body_r(const ResliceJob& J, const TileSetup
             const int64_t base = c1 * st1 + c2 * st2;
             for (int lev = 0; lev < L; ++lev) {
                 const int g = lo + lev;
-                sAB[c * L + lev] = (g >= 0 && g <= top) ? collapse_voxel<K, VT, WT>(rec, base + g * std_, wt)
-                                                        : make_float2(0.0f, 0.0f);
+                sAB[c * L + lev] = (g >= 0 && g <= top)
+                                       ? (npx ? collapse_voxel_px<K, VT, WT>(rec, npx, base + g * std_, wt)
+                                              : collapse_voxel<K, VT, WT>(rec, base + g * std_, wt))
+                                       : make_float2(0.0f, 0.0f);
             }
         }
         __syncthreads();

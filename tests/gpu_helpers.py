@@ -61,7 +61,8 @@ def oracle_dense(vol, K, dtype):
 def ora_params(p):
     return oracle.Params(k_normal=p.k_normal, k_inplane=p.k_inplane, thr_normal_deg=p.thr_normal_deg,
                          thr_inplane_deg=p.thr_inplane_deg, k_dist=p.k_dist, unassigned=float(p.unassigned),
-                         radius=p.radius_vox, kernel=p.dist_kernel, normal_axis=p.normal_axis)
+                         radius=p.radius_vox, kernel=p.dist_kernel, normal_axis=p.normal_axis,
+                         per_pixel=p.sample_weight == dare.DARE_SAMPLE_PIXELS)
 
 
 def new_outputs(W, H):

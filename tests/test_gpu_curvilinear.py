@@ -119,6 +119,13 @@ def test_both_curvilinear_kernels_and_radii(tiny, curv_pair, kernel, R):
     assert covered > 0
 
 
+def test_curvilinear_per_pixel_samples(tiny, curv_pair):
+    """Per-pixel samples (npix-weighted) under a curvilinear virtual probe."""
+    s, vol = curv_pair
+    p = dare.params_default(probe_apex_mm=APEX, sample_weight=dare.DARE_SAMPLE_PIXELS)
+    assert _run(tiny, s, vol, p, APEX, tiny.reslice_poses[[1, 8]])[0] > 0
+
+
 def test_curvilinear_thresholds_off_and_nan(tiny, curv_pair):
     s, vol = curv_pair
     for p in (dare.params_default(thr_normal_deg=180.0, thr_inplane_deg=180.0, probe_apex_mm=APEX),

@@ -110,3 +110,40 @@ def test_radius_limits(tiny, f32_pair):
         s.reslice(tiny.reslice_poses[0], out, mask, tiny.out_px,
                   dare.params_default(dist_kernel=dare.DARE_EXP, k_dist=-1.0))
     assert ei.value.status == dare.DARE_E_INVALID
+
+
+@pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("kernel,R", [(dare.DARE_TENT, 1), (dare.DARE_BOX, 2), (dare.DARE_EXP, 1)])
+def test_per_pixel_samples_parity(tiny, f32_pair, path, kernel, R):
+    """DARE_SAMPLE_PIXELS (every pixel its own sample: stored samples weighted
+    by their npix) on both general kernels against the oracle's reading."""
+    s, vol = f32_pair
+    p = dare.params_default(path=path, radius_vox=R, dist_kernel=kernel, sample_weight=dare.DARE_SAMPLE_PIXELS)
+    assert _check(tiny, s, vol, p, tiny.reslice_poses[[0, 6, 11]]) > 0
+
+
+def test_per_pixel_samples_u8_batch_and_plan(tiny):
+    """Reduced storage, and batches / plans / single calls bit for bit."""
+    s = gpu_session(tiny, dare.DARE_U8, 4)
+    vol = oracle_volume(tiny, dare.DARE_U8, 4)
+    p = dare.params_default(sample_weight=dare.DARE_SAMPLE_PIXELS)
+    _check(tiny, s, vol, p, tiny.reslice_poses[[2, 9]])
+    outs = [new_outputs(64, 48) for _ in range(5)]
+    items = [(s, tiny.reslice_poses[i], o, m, tiny.out_px) for i, (o, m) in enumerate(outs)]
+    dare.reslice_batch(items, p)
+    torch.cuda.synchronize()
+    got = [(o.cpu().numpy(), m.cpu().numpy()) for o, m in outs]
+    plan = dare.Plan(items, p)
+    for o, m in outs:
+        o.fill_(-1.0)
+    plan.launch()
+    torch.cuda.synchronize()
+    for i, ((o, m), (go, gm)) in enumerate(zip(outs, got)):
+        o1, m1 = gpu_reslice(s, tiny.reslice_poses[i], 64, 48, tiny.out_px, p)
+        assert np.array_equal(gm, m1) and np.array_equal(go, o1)
+        assert np.array_equal(m.cpu().numpy(), m1) and np.array_equal(o.cpu().numpy(), o1)
+    plan.close()
+    with pytest.raises(dare.DareError) as ei:
+        s.reslice(tiny.reslice_poses[0], outs[0][0], outs[0][1], tiny.out_px, dare.params_default(sample_weight=5))
+    assert ei.value.status == dare.DARE_E_INVALID
+    s.close()
