@@ -348,6 +348,27 @@ dare_status dare_session_set_probe(dare_session s, const dare_probe* probe, cons
                                    int32_t width, int32_t height);
 
 /*
+ * Brick cache for a DARE_SESSION_HOST_VOLUME session (Sec. 4: growing
+ * datasets despite GPU memory limits): `bytes` of device memory hold whole
+ * bricks of 8 x 8 x 8 voxels' records (512 x record_bytes each).  Before each
+ * plane of dare_reslice / dare_reslice_batch (linear probes, per-(voxel,
+ * frame) samples) the bricks its support can reach are paged in from the host
+ * volume unless resident, replacing bricks in clock order that the plane does
+ * not use; the plane then reads resident bricks from device memory and any
+ * other from the host volume.  Results are bit-identical whatever the cache
+ * holds.  A build or reset makes every cached brick stale.  bytes = 0 frees
+ * the cache.  DARE_E_STATE for a device-resident session.  Synchronous.
+ * dare_reslice_batch runs the planes of such sessions one by one;
+ * dare_reslice_batch_host, plans, the server and the allocation-free call
+ * refuse them (DARE_E_UNSUPPORTED).
+ */
+dare_status dare_session_set_cache(dare_session s, int64_t bytes);
+
+/* Brick cache counters: out[0] slots, out[1] resident bricks, out[2] bricks
+ * paged in, out[3] bricks found resident, since dare_session_set_cache. */
+dare_status dare_session_cache_stats(dare_session s, int64_t out[4]);
+
+/*
  * Reslicing (Sec. 2.1, Eq. 1, Eq. 2, Fig. 2) of one plane into out_dev /
  * mask_dev (see Layouts).  Every distance kernel (TENT, BOX, EXP) runs on
  * both paths for radius_vox 1..16 (the tiled kernel up to a support of 9

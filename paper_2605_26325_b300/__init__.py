@@ -145,6 +145,8 @@ _SIGNATURES = {
     "dare_session_read_frames": ([_vp, _P(ctypes.c_double)], ctypes.c_int),
     "dare_session_set_probe": ([_vp, _P(dare_probe), _vp, ctypes.c_int32, ctypes.c_int32], ctypes.c_int),
     "dare_fill_holes": ([_vp, ctypes.c_int32, ctypes.c_int32, _vp], ctypes.c_int),
+    "dare_session_set_cache": ([_vp, ctypes.c_int64], ctypes.c_int),
+    "dare_session_cache_stats": ([_vp, _P(ctypes.c_int64)], ctypes.c_int),
     "dare_reslice_scalar_filled": ([_vp, _P(dare_plane), ctypes.c_float, _vp, _vp, _vp], ctypes.c_int),
     "dare_session_read_filled": ([_vp, _vp], ctypes.c_int),
     "dare_session_save": ([_vp, ctypes.c_char_p], ctypes.c_int),
@@ -511,6 +513,16 @@ class Session:
         check(lib().dare_reslice_scalar(self._h, ctypes.byref(pl), float(unassigned), _dev_ptr(out, "out"),
                                         _dev_ptr(mask, "mask", (H, mask_words(W))), _stream_ptr(stream)),
               "dare_reslice_scalar")
+
+    def set_cache(self, nbytes):
+        """Brick cache of a host-volume session (0 frees it)."""
+        check(lib().dare_session_set_cache(self._h, int(nbytes)), "dare_session_set_cache")
+
+    def cache_stats(self):
+        """dict(slots, resident, paged_in, hits) of the brick cache."""
+        out = (ctypes.c_int64 * 4)()
+        check(lib().dare_session_cache_stats(self._h, out), "dare_session_cache_stats")
+        return dict(slots=out[0], resident=out[1], paged_in=out[2], hits=out[3])
 
     def fill_holes(self, radius_vox=1, min_neighbours=1, stream=None):
         """Hole filling of the compounded volume (the comparator's, Sec. 2.2)."""

@@ -18,7 +18,8 @@ OUT = os.path.join(PKG, "libdare.so")
 HEADER = os.path.join(ROOT, "include", "dare.h")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-CU_SOURCES = ["kernels.cu", "kernels_tiled.cu", "kernels_radius.cu", "kernels_curv.cu", "kernels_build.cu", "noalloc.cu"]
+CU_SOURCES = ["kernels.cu", "kernels_tiled.cu", "kernels_radius.cu", "kernels_curv.cu", "kernels_paged.cu",
+              "kernels_build.cu", "noalloc.cu"]
 CPP_SOURCES = ["api.cpp", "server.cpp"]
 
 

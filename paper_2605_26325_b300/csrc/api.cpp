@@ -305,6 +305,19 @@ struct dare_session_s {
     int32_t n_curv = 0;                    // frames from a curvilinear probe
     dare_probe probe{};                    // probe of the frames appended from now on
     uint32_t* pix_mask = nullptr;          // its pixel mask (device bitmap), or NULL
+    // brick cache (dare_session_set_cache, host volumes): slots of 8^3-voxel bricks of records
+    uint8_t* cache = nullptr;
+    size_t cache_bytes = 0;
+    int32_t n_slots = 0;
+    int32_t* brick_table = nullptr;        // per brick: slot or -1 (device)
+    size_t table_bytes = 0;
+    int32_t nb[3] = {0, 0, 0};
+    std::vector<int32_t> slot_of_brick, brick_of_slot;
+    std::vector<int64_t> slot_stamp;       // plane count at the slot's last use
+    std::vector<uint8_t> brick_mark;       // scratch of plane_bricks
+    int64_t stamp = 0;
+    int32_t hand = 0;                      // next eviction candidate (clock)
+    int64_t pages_in = 0, page_hits = 0;
     float* filled = nullptr;               // hole-filled compounded volume (NaN = empty), or NULL
     size_t filled_bytes = 0;
     int64_t filled_version = -1;           // session version it was computed at
@@ -376,8 +389,20 @@ dare_status admit(int64_t bytes) {
     }
 }
 
+// Every cached brick is stale once the records change (a build or a clear).
+dare_status invalidate_cache(dare_session s, cudaStream_t st) {
+    if (!s->cache) return DARE_OK;
+    CUDA_TRY(cudaMemsetAsync(s->brick_table, 0xFF, s->table_bytes, st));
+    std::fill(s->slot_of_brick.begin(), s->slot_of_brick.end(), -1);
+    std::fill(s->brick_of_slot.begin(), s->brick_of_slot.end(), -1);
+    std::fill(s->slot_stamp.begin(), s->slot_stamp.end(), 0);
+    return DARE_OK;
+}
+
 // Empty volume on st: empty records, zero npix and scalar totals.
 dare_status clear_volume(dare_session s, cudaStream_t st) {
+    dare_status rc0 = invalidate_cache(s, st);
+    if (rc0 != DARE_OK) return rc0;
     {
         KernelScope ks("fill_records", st, 1);
         CUDA_TRY(launch_fill_records(s->rec, s->n_vox, s->rec_bytes, s->K, st));
@@ -732,18 +757,122 @@ CurvJob make_curv_job(const dare_session s, const dare_plane* pl, float* out, ui
     return c;
 }
 
+// Bricks whose records a plane's support can read: a conservative cover from
+// 8 x 8-pixel cells (inside a cell g lies between its values at the cell's
+// corners, g being affine in the pixel), each cell's voxel box widened by the
+// support's extent below and above floor(g).
+void plane_bricks(const dare_session s, const ResliceJob& j, std::vector<uint8_t>& mark, std::vector<int32_t>& out) {
+    const int64_t n_b = int64_t(s->nb[0]) * s->nb[1] * s->nb[2];
+    mark.assign(size_t(n_b), 0);
+    out.clear();
+    for (int v0 = 0; v0 < j.height; v0 += 8)
+        for (int u0 = 0; u0 < j.width; u0 += 8) {
+            const int u1 = std::min(u0 + 7, j.width - 1), v1 = std::min(v0 + 7, j.height - 1);
+            int blo[3], bhi[3];
+            bool empty = false;
+            for (int a = 0; a < 3 && !empty; ++a) {
+                const int64_t c[4] = {j.g0[a] + u0 * j.a[a] + v0 * j.b[a], j.g0[a] + u1 * j.a[a] + v0 * j.b[a],
+                                      j.g0[a] + u0 * j.a[a] + v1 * j.b[a], j.g0[a] + u1 * j.a[a] + v1 * j.b[a]};
+                const int64_t gmin = std::min(std::min(c[0], c[1]), std::min(c[2], c[3]));
+                const int64_t gmax = std::max(std::max(c[0], c[1]), std::max(c[2], c[3]));
+                const int64_t lo = std::max<int64_t>((gmin >> kFixBits) - j.ext_lo, 0);
+                const int64_t hi = std::min<int64_t>((gmax >> kFixBits) + j.ext_hi, j.dims[a] - 1);
+                if (lo > hi) {
+                    empty = true;
+                } else {
+                    blo[a] = static_cast<int>(lo / kBrickSide);
+                    bhi[a] = static_cast<int>(hi / kBrickSide);
+                }
+            }
+            if (empty) continue;
+            for (int bz = blo[2]; bz <= bhi[2]; ++bz)
+                for (int by = blo[1]; by <= bhi[1]; ++by)
+                    for (int bx = blo[0]; bx <= bhi[0]; ++bx) {
+                        const int32_t id = bx + s->nb[0] * (by + s->nb[1] * bz);
+                        if (!mark[size_t(id)]) {
+                            mark[size_t(id)] = 1;
+                            out.push_back(id);
+                        }
+                    }
+        }
+}
+
+// Make the bricks of `need` resident: hits keep their slots, misses take the
+// next slots (clock order) that this plane does not use; the copies and table
+// updates are queued on st from `lists` (device workspace).  A plane needing
+// more bricks than the cache has slots pages nothing and reads the missing
+// bricks over the host link.
+dare_status page_bricks(dare_session s, const std::vector<int32_t>& need, uint8_t* lists, cudaStream_t st) {
+    s->stamp += 1;
+    if (int64_t(need.size()) > s->n_slots) return DARE_OK;
+    std::vector<int32_t> miss;
+    for (int32_t b : need) {
+        const int32_t sl = s->slot_of_brick[size_t(b)];
+        if (sl >= 0) {
+            s->slot_stamp[size_t(sl)] = s->stamp;
+            s->page_hits += 1;
+        } else {
+            miss.push_back(b);
+        }
+    }
+    if (miss.empty()) return DARE_OK;
+    std::vector<int2> lst;  // table updates (evictions, then insertions), then page copies
+    std::vector<int2> ins;
+    lst.reserve(2 * miss.size());
+    for (int32_t b : miss) {
+        int32_t sl = s->hand;
+        while (s->slot_stamp[size_t(sl)] == s->stamp) sl = (sl + 1) % s->n_slots;  // need <= n_slots: ends
+        s->hand = (sl + 1) % s->n_slots;
+        const int32_t old = s->brick_of_slot[size_t(sl)];
+        if (old >= 0) {
+            s->slot_of_brick[size_t(old)] = -1;
+            lst.push_back(make_int2(old, -1));
+        }
+        s->brick_of_slot[size_t(sl)] = b;
+        s->slot_of_brick[size_t(b)] = sl;
+        s->slot_stamp[size_t(sl)] = s->stamp;
+        ins.push_back(make_int2(b, sl));
+    }
+    const int n_upd = static_cast<int>(lst.size() + ins.size());
+    lst.insert(lst.end(), ins.begin(), ins.end());  // insertions double as the page list
+    const size_t bytes = lst.size() * sizeof(int2);
+    const int pin = 1 + (s->next_desc++ & 7);
+    dare_status rc = ensure_pinned(s, pin, bytes);
+    if (rc != DARE_OK) return rc;
+    std::memcpy(s->pinned[pin], lst.data(), bytes);
+    CUDA_TRY(cudaMemcpyAsync(lists, s->pinned[pin], bytes, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaEventRecord(s->pinned_ev[pin], st));
+    const auto* dl = reinterpret_cast<const int2*>(lists);
+    {
+        KernelScope ks("page_in", st, 2);
+        CUDA_TRY(launch_page_in(dl, n_upd, dl + (n_upd - int(ins.size())), static_cast<int>(ins.size()), s->rec,
+                                s->cache, s->cfg.grid.dims, s->nb, s->rec_bytes, s->brick_table, st));
+    }
+    s->pages_in += static_cast<int64_t>(ins.size());
+    return DARE_OK;
+}
+
+// The paged reslice applies to a session with a brick cache, linear probes
+// and per-(voxel, frame) samples; other reslices of such a session read the
+// host volume directly.
+bool paged_path(const dare_session s, const dare_params* p) {
+    return s->cache && !curv_path(s, p) && p->sample_weight == DARE_SAMPLE_MEAN;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------- batch helpers (shared with the server)
 
 namespace dare {
 
-dare_status check_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params) {
+dare_status check_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, bool allow_paged) {
     dare_status rc = check_params(params);
     if (rc != DARE_OK) return rc;
     for (int32_t i = 0; i < n; ++i) {
         const dare_reslice_req& r = reqs[i];
         if (!r.session) return fail(DARE_E_INVALID, "request %d has no session", i);
+        if (r.session->cache && !allow_paged)
+            return fail(DARE_E_UNSUPPORTED, "request %d: a session with a brick cache (use dare_reslice_batch)", i);
         if (r.session->cfg.device != reqs[0].session->cfg.device) return fail(DARE_E_INVALID, "requests span devices");
         rc = check_plane(&r.plane);
         if (rc != DARE_OK) return fail(rc, "request %d: %s", i, g_err.c_str());
@@ -1130,6 +1259,10 @@ dare_status dare_session_destroy(dare_session s) {
         s->dev_free(s->filled, s->filled_bytes, s->last_stream);
         g_in_use -= static_cast<int64_t>(s->filled_bytes);
     }
+    if (s->cache) {
+        s->dev_free(s->cache, s->cache_bytes + s->table_bytes, s->last_stream);
+        g_in_use -= static_cast<int64_t>(s->cache_bytes + s->table_bytes);
+    }
     if (s->order_ev) cudaEventDestroy(s->order_ev);
     delete s;
     return DARE_OK;
@@ -1347,6 +1480,10 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
             CUDA_TRY(launch_scatter_place(a, pairs, n_pairs, s->count, offsets, entries, st));
         }
         {
+            if (c0 == 0) {
+                rc = invalidate_cache(s, st);  // the records are about to change
+                if (rc != DARE_OK) return rc;
+            }
             const int mode = s->pending_clear ? 2 : (s->fresh ? 1 : 0);
             s->pending_clear = false;  // this finalize writes every voxel
             s->fresh = false;          // from here on the records may hold samples
@@ -1378,6 +1515,66 @@ dare_status dare_build_volume_host(dare_session s, const uint8_t* frames_host, i
                                    int32_t height, const double px_mm[2], const double* image_to_world,
                                    int32_t slice_frames, void* stream) {
     return build_impl(s, frames_host, true, n, width, height, px_mm, image_to_world, slice_frames, stream);
+}
+
+dare_status dare_session_set_cache(dare_session s, int64_t bytes) {
+    if (!s) return fail(DARE_E_INVALID, "session is NULL");
+    if (!s->host_vol) return fail(DARE_E_STATE, "a brick cache needs DARE_SESSION_HOST_VOLUME");
+    if (bytes < 0) return fail(DARE_E_INVALID, "cache bytes must be >= 0");
+    DeviceGuard dg(s->cfg.device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
+    CUDA_TRY(cudaEventSynchronize(s->order_ev));  // queued reslices may still read the old cache
+    if (s->cache) {
+        s->dev_free(s->cache, s->cache_bytes + s->table_bytes, s->last_stream);
+        g_in_use -= static_cast<int64_t>(s->cache_bytes + s->table_bytes);
+        s->cache = nullptr;
+        s->brick_table = nullptr;
+        s->cache_bytes = s->table_bytes = 0;
+        s->n_slots = 0;
+    }
+    if (bytes == 0) return DARE_OK;
+    for (int a = 0; a < 3; ++a) s->nb[a] = (s->cfg.grid.dims[a] + kBrickSide - 1) / kBrickSide;
+    const int64_t n_b = int64_t(s->nb[0]) * s->nb[1] * s->nb[2];
+    const size_t slot_bytes = size_t(kBrickVoxels) * s->rec_bytes;
+    const int64_t slots = std::min<int64_t>(bytes / static_cast<int64_t>(slot_bytes), n_b);
+    if (slots < 1) return fail(DARE_E_INVALID, "cache of %lld bytes holds no brick of %zu bytes", (long long)bytes, slot_bytes);
+    if (slots > INT32_MAX / kBrickVoxels) return fail(DARE_E_INVALID, "cache too large");
+    const size_t cbytes = align_up(size_t(slots) * slot_bytes, 256), tbytes = align_up(size_t(n_b) * 4, 256);
+    dare_status rc = admit(static_cast<int64_t>(cbytes + tbytes));
+    if (rc != DARE_OK) return rc;
+    auto* base = static_cast<uint8_t*>(s->dev_alloc(cbytes + tbytes, nullptr));
+    if (!base) {
+        g_in_use -= static_cast<int64_t>(cbytes + tbytes);
+        return fail(DARE_E_OOM, "brick cache allocation of %zu bytes failed", cbytes + tbytes);
+    }
+    if (cudaMemset(base + cbytes, 0xFF, tbytes) != cudaSuccess) {
+        cudaGetLastError();
+        s->dev_free(base, cbytes + tbytes, nullptr);
+        g_in_use -= static_cast<int64_t>(cbytes + tbytes);
+        return fail(DARE_E_CUDA, "brick table clear failed");
+    }
+    s->cache = base;
+    s->cache_bytes = cbytes;
+    s->brick_table = reinterpret_cast<int32_t*>(base + cbytes);
+    s->table_bytes = tbytes;
+    s->n_slots = static_cast<int32_t>(slots);
+    s->slot_of_brick.assign(size_t(n_b), -1);
+    s->brick_of_slot.assign(size_t(slots), -1);
+    s->slot_stamp.assign(size_t(slots), 0);
+    s->hand = 0;
+    s->pages_in = s->page_hits = 0;
+    return DARE_OK;
+}
+
+dare_status dare_session_cache_stats(dare_session s, int64_t out[4]) {
+    if (!s || !out) return fail(DARE_E_INVALID, "NULL argument");
+    int64_t resident = 0;
+    for (int32_t b : s->brick_of_slot) resident += b >= 0;
+    out[0] = s->n_slots;
+    out[1] = resident;
+    out[2] = s->pages_in;
+    out[3] = s->page_hits;
+    return DARE_OK;
 }
 
 dare_status dare_session_set_probe(dare_session s, const dare_probe* probe, const uint8_t* pixel_mask,
@@ -1444,6 +1641,38 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     rc = session_begin(s, st);
     if (rc != DARE_OK) return rc;
+    if (paged_path(s, params)) {
+        const int wbp = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
+        const size_t wt_bytes = align_up(size_t(std::max(s->n_frames, 1)) * wbp, 256);
+        std::vector<int32_t> need;
+        {
+            const ResliceJob probe_job = make_job(s, plane, nullptr, out_dev, mask_dev, params->unassigned, params);
+            plane_bricks(s, probe_job, s->brick_mark, need);
+        }
+        rc = ensure_workspace(s, wt_bytes + (2 * need.size() + 2) * sizeof(int2), st);
+        if (rc != DARE_OK) return rc;
+        TableJob tjp{};
+        plane_vectors(s, plane, params->normal_axis, &tjp);
+        tjp.frames = s->frames_dev;
+        tjp.wtab = s->ws;
+        tjp.n_frames = s->n_frames;
+        if (s->n_frames > 0) {
+            KernelScope ks("weight_table", st, 1);
+            CUDA_TRY(launch_weight_tables(nullptr, &tjp, 1, s->n_frames, table_params(params), st));
+        }
+        rc = page_bricks(s, need, static_cast<uint8_t*>(s->ws) + wt_bytes, st);
+        if (rc != DARE_OK) return rc;
+        PagedJob pj{};
+        pj.j = make_job(s, plane, s->ws, out_dev, mask_dev, params->unassigned, params);
+        pj.cache = s->cache;
+        pj.table = s->brick_table;
+        for (int a = 0; a < 3; ++a) pj.nb[a] = s->nb[a];
+        {
+            KernelScope ks("reslice_paged", st, 1);
+            CUDA_TRY(launch_reslice_paged(pj, s->K, s->dtype, params->weight_dtype == DARE_WEIGHTS_F16, st));
+        }
+        return session_end(s, st);
+    }
     if (curv_path(s, params)) {
         const CurvJob cj = make_curv_job(s, plane, out_dev, mask_dev, params);
         L2Window l2((s->cfg.flags & DARE_SESSION_L2_PERSIST) ? s->rec : nullptr, size_t(s->n_vox) * s->rec_bytes, st);
@@ -1473,8 +1702,17 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
 dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream) {
     if (n < 0 || (n > 0 && !reqs)) return fail(DARE_E_INVALID, "bad request list");
     if (n == 0) return DARE_OK;
-    dare_status rc = dare::check_batch(reqs, n, params);
+    dare_status rc = dare::check_batch(reqs, n, params, true);
     if (rc != DARE_OK) return rc;
+    for (int32_t i = 0; i < n; ++i)
+        if (reqs[i].session->cache) {
+            // sessions with a brick cache page per plane: every request in order, one plane at a time
+            for (int32_t k = 0; k < n; ++k) {
+                rc = dare_reslice(reqs[k].session, &reqs[k].plane, params, reqs[k].out, reqs[k].mask, stream);
+                if (rc != DARE_OK) return rc;
+            }
+            return DARE_OK;
+        }
     dare_session s0 = reqs[0].session;
     DeviceGuard dg(s0->cfg.device);
     if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device");
@@ -1985,6 +2223,7 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
         return fail(DARE_E_INVALID, "plane too far from the grid for fixed-point coordinates");
     if (curv_path(s, params))
         return fail(DARE_E_UNSUPPORTED, "the allocation-free reslice covers linear probes only (use dare_reslice)");
+    if (s->cache) return fail(DARE_E_UNSUPPORTED, "a session with a brick cache pages per call (use dare_reslice)");
     const size_t wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
     if (s->n_frames > max_frames || size_t(s->n_frames) * wb > wtab_bytes)
         return fail(DARE_E_INVALID, "the allocation-free reslice holds weights for at most %d frames; "
@@ -2192,6 +2431,8 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
         if (!r.session) return fail(DARE_E_INVALID, "request %d has no session", i);
         if (curv_path(r.session, params))
             return fail(DARE_E_UNSUPPORTED, "request %d: plans cover linear probes only (use dare_reslice_batch)", i);
+        if (r.session->cache)
+            return fail(DARE_E_UNSUPPORTED, "request %d: a session with a brick cache (use dare_reslice_batch)", i);
         if (r.session->cfg.device != reqs[0].session->cfg.device) return fail(DARE_E_INVALID, "requests span devices");
         rc = check_plane(&r.plane);
         if (rc != DARE_OK) return fail(rc, "request %d: %s", i, g_err.c_str());

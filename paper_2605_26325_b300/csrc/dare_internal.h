@@ -156,6 +156,22 @@ cudaError_t launch_reslice_plain_r(const ResliceJob* jobs_dev, const ResliceJob*
 cudaError_t launch_reslice_tiled_r(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
                                    int tile_offset, int n_tiles, int uniform, int col_cap, int slot_cap, int K,
                                    int dtype, int half_weights, cudaStream_t st);
+// brick paging (kernels_paged.cu): 8^3-voxel bricks of records in a device cache
+constexpr int kBrickSide = 8;
+constexpr int kBrickVoxels = kBrickSide * kBrickSide * kBrickSide;
+struct PagedJob {
+    ResliceJob j;             // rec = the mapped host records (bricks that are not resident)
+    const uint8_t* cache;     // slots of kBrickVoxels records, voxel x fastest within the brick
+    const int32_t* table;     // per brick: its slot, or -1
+    int32_t nb[3];            // bricks per axis
+    int32_t pad;
+};
+// updates: (brick, slot or -1) table writes; pages: (brick, slot) copies host -> cache
+cudaError_t launch_page_in(const int2* updates, int n_updates, const int2* pages, int n_pages, const uint8_t* host_rec,
+                           uint8_t* cache, const int32_t dims[3], const int32_t nb[3], int rec_bytes, int32_t* table,
+                           cudaStream_t st);
+cudaError_t launch_reslice_paged(const PagedJob& job, int K, int dtype, int half_weights, cudaStream_t st);
+
 // curvilinear probes (kernels_curv.cu): per-pixel gather with in-kernel Eq. 1 / Eq. 2
 cudaError_t launch_reslice_curv(const CurvJob* jobs_dev, const CurvJob* one_job, int n_jobs, int max_w, int max_h,
                                 int K, int dtype, cudaStream_t st);
@@ -170,7 +186,8 @@ cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* o
 constexpr int kTileW = 32;
 
 // batch helpers and memory accounting (api.cpp), used by the server
-dare_status check_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params);
+// allow_paged: sessions with a brick cache are accepted (dare_reslice_batch runs them plane by plane)
+dare_status check_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, bool allow_paged = false);
 void batch_sizes(const dare_reslice_req* reqs, int32_t n, const dare_params* params, size_t* ws_need,
                  size_t* desc_bytes);
 dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, cudaStream_t st,
