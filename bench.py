@@ -564,6 +564,20 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
     line["host_volume"] = {"host_bytes": int(hv.info().record_bytes) * int(np.prod(w.grid.dims)),
                            "device_bytes": int(hv.info().volume_bytes), "build_ms": hv_build_ms,
                            "reslice_ms_per_plane": hv_res_ms / P, "mpix_s": P * W * H / (hv_res_ms * 1e-3) / 1e6}
+    # the same host volume with a device brick cache of a quarter of its bytes:
+    # bricks of each plane's footprint paged in as the trajectory moves
+    cache_bytes = int(hv.info().record_bytes) * int(np.prod(w.grid.dims)) // 4
+    hv.set_cache(cache_bytes)
+    n_pg = min(P, 500)
+    rq_pg = (dare.dare_reslice_req * n_pg)(*rq_hv[:n_pg])
+    pg_ms = timed(lambda: dare.reslice_batch(rq_pg, params, stream), 2)
+    stats = hv.cache_stats()
+    line["host_volume"]["paged"] = {"cache_bytes": cache_bytes, "planes": n_pg,
+                                    "reslice_ms_per_plane": pg_ms / n_pg,
+                                    "mpix_s": n_pg * W * H / (pg_ms * 1e-3) / 1e6, "cache": stats,
+                                    "note": "dare_session_set_cache: 8^3-voxel bricks of the plane footprints paged "
+                                            "into device memory, the per-pixel gather reading the cache; one plane "
+                                            "per launch"}
     hv.close()
 
     # --- the paper's timing axis (Sec. 3): interpolation radius.  BOX gives its
