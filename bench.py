@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--path", choices=["tiled", "plain"], default="tiled")
     ap.add_argument("--radius", type=int, default=1, help="interpolation radius in voxels (default 1)")
     ap.add_argument("--kernel", choices=["tent", "box", "exp"], default="tent", help="distance kernel (default tent)")
+    ap.add_argument("--probe", choices=["linear", "curvilinear"], default="linear",
+                    help="probe of the frames and of the virtual planes (curvilinear: a fan from 40 mm above the face)")
     ap.add_argument("--workload", choices=["working", "batched", "serving"], default="working",
                     help="working: the 256^3 step (default); batched: 64 uneven volumes through a graph-replayed "
                          "plan; serving: 16 sessions under Poisson pose streams with live ingestion")
@@ -278,13 +280,16 @@ def run_dare(args, dist):
     dtype = DTYPE_NAMES[args.dtype]
     s = dare.Session(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, dtype=dtype, max_slots=args.slots,
                      device=dev, flags=0 if args.quick else dare.DARE_SESSION_SCALAR)
+    curv_apex = (0.0, -40.0) if args.probe == "curvilinear" else None
+    if curv_apex is not None:
+        s.set_probe(dare.DARE_PROBE_CURVILINEAR, curv_apex)
     stream = torch.cuda.current_stream()
     frames_d = torch.from_numpy(w.frames).to(device)
     outs = torch.empty((P, H, W), dtype=torch.float32, device=device)
     masks = torch.empty((P, H, dare.mask_words(W)), dtype=torch.int32, device=device)
     reqs = dare.make_requests([(s, w.reslice_poses[i], outs[i], masks[i], w.out_px) for i in range(P)])
     path = dare.DARE_PATH_TILED if args.path == "tiled" else dare.DARE_PATH_PLAIN
-    params = dare.params_default(path=path, radius_vox=args.radius,
+    params = dare.params_default(path=path, radius_vox=args.radius, probe_apex_mm=curv_apex,
                                  dist_kernel={"tent": dare.DARE_TENT, "box": dare.DARE_BOX, "exp": dare.DARE_EXP}[args.kernel])
 
     def step():
@@ -329,6 +334,8 @@ def run_dare(args, dist):
     rec_bytes = info.record_bytes
     reslice_alg = float(fp.sum() * rec_bytes + P * (W * H * 4 + H * dare.mask_words(W) * 4) + P * info.n_frames * 4)
     alg = {"reslice_tiled": reslice_alg, "reslice_plain": reslice_alg}
+    if args.radius == 1 and args.kernel == "tent":  # the footprint counts the TENT R = 1 support
+        alg["reslice_curv"] = reslice_alg
     peak, peak_kind = peaks()
     roof = None
     if top[0] in alg:
@@ -343,7 +350,7 @@ def run_dare(args, dist):
             "config": {"workload": WORKLOAD, "grid": "256^3 @ 0.4 mm", "frames": int(len(w.frames)),
                        "frame_px": "256x512 @ 0.2 mm", "poses": P, "out_px": f"{W}x{H} @ 0.2 mm",
                        "storage": args.dtype, "slots": args.slots, "path": args.path, "weights": "f32",
-                       "distance_kernel": f"{args.kernel} R={args.radius}",
+                       "distance_kernel": f"{args.kernel} R={args.radius}", "probe": args.probe,
                        "step": "reset + rebuild volume from all frames + reslice every pose",
                        "l2": "inputs larger than L2 (volume, frames and outputs each > 126 MB); no flush",
                        "parallelism": f"replicas x{dist.world}"},
