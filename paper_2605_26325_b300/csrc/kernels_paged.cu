@@ -65,7 +65,7 @@ __device__ __noinline__ void gather_pixel_paged(const PagedJob& P, int u, int v,
         fr[a] = static_cast<float>(static_cast<int32_t>(G & (kFixOne - 1))) * (1.0f / static_cast<float>(kFixOne));
         lo[a] = box ? f + (fr[a] >= 0.5f ? 1 : 0) - R : f - R + 1;
         if (lo[a] + S - 1 < 0 || lo[a] > J.dims[a] - 1) return;  // the support misses the grid
-        fr[a] -= static_cast<float>(lo[a] - f);                   // g - lo, exact
+        fr[a] -= static_cast<float>(static_cast<int>(lo[a] - f));  // g - lo, exact (int32: a fast conversion)
     }
     const WT* wt = static_cast<const WT*>(J.wtab);
     const float Rf = static_cast<float>(R), kr = J.k_dist / Rf;
