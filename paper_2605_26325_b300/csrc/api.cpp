@@ -1489,7 +1489,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
             s->fresh = false;          // from here on the records may hold samples
             KernelScope ks("finalize", st, 1);
             CUDA_TRY(launch_finalize(offsets, entries, s->n_vox, s->rec, s->npix, s->ssum, s->scnt, s->K, s->dtype,
-                                     mode, s->overflow_dev, st));
+                                     mode, s->host_vol ? 0 : 1, s->overflow_dev, st));
         }
     }
     rc = session_end(s, st);

@@ -137,9 +137,10 @@ int64_t scan_block_sums_needed(int64_t n);
 // mode 0: merge into the stored records; 1: the volume holds no sample (created or
 // reset since), stored records are not read; 2: as 1 and not cleared since a reset:
 // every voxel's record, npix row and scalar totals are written (empty where no entry)
+// bulk: records and npix in device memory, so mode 2 may store whole runs with bulk copies
 cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
                             uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode,
-                            unsigned long long* overflow, cudaStream_t st);
+                            int bulk, unsigned long long* overflow, cudaStream_t st);
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
                                   cudaStream_t st);
 cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned long long* count, cudaStream_t st);

@@ -425,6 +425,111 @@ __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ of
     }
 }
 
+// Empty record of a voxel: ids 0xFFFF, values 0.
+template <int K, int RB>
+__device__ __forceinline__ void empty_record(uint4* r) {
+#pragma unroll
+    for (int i = 0; i < RB / 16; ++i) {
+        uint4 q = make_uint4(0u, 0u, 0u, 0u);
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int b = 16 * i + 4 * w;
+            uint32_t x = 0u;
+#pragma unroll
+            for (int h = 0; h < 2; ++h)
+                if (b + 2 * h < 2 * K) x |= 0xFFFFu << (16 * h);
+            (w == 0 ? q.x : w == 1 ? q.y : w == 2 ? q.z : q.w) = x;
+        }
+        r[i] = q;
+    }
+}
+
+// Shared -> global bulk copy (the asynchronous copy engine), one thread.
+__device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_t bytes) {
+    const uint32_t saddr = static_cast<uint32_t>(__cvta_generic_to_shared(ssrc));
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;"
+                 :: "l"(gdst), "r"(saddr), "r"(bytes) : "memory");
+}
+
+// Finalize writing every voxel (mode 2: the volume has not been cleared since
+// a reset) with records and npix rows in device memory.  A CTA takes runs of
+// 256 consecutive voxels; each thread builds its voxel's record and npix row
+// in shared memory (the empty ones too), and one thread sends the whole run
+// (20 KB of f32 K=12 records) to global memory with two bulk copies.  A run
+// shorter than 256 voxels (the grid's tail) is stored thread by thread.
+template <int K, typename VT>
+__global__ void __launch_bounds__(256) k_finalize_full(const int32_t* __restrict__ offsets,
+                                                       const unsigned long long* __restrict__ entries,
+                                                       int64_t n_vox, uint8_t* __restrict__ rec,
+                                                       uint16_t* __restrict__ npix, uint32_t* __restrict__ scal_sum,
+                                                       uint32_t* __restrict__ scal_cnt,
+                                                       unsigned long long* overflow) {
+    constexpr int RB = (2 * K + K * static_cast<int>(sizeof(VT)) + 15) / 16 * 16;
+    __shared__ __align__(128) uint4 s_rec[256 * RB / 16];
+    __shared__ __align__(128) uint2 s_np[256 * K / 4];
+    uint4* my_rec = s_rec + threadIdx.x * (RB / 16);
+    uint2* my_np = s_np + threadIdx.x * (K / 4);
+    for (int64_t v0 = static_cast<int64_t>(blockIdx.x) * 256; v0 < n_vox; v0 += static_cast<int64_t>(gridDim.x) * 256) {
+        const int64_t v = v0 + threadIdx.x;
+        const bool whole = n_vox - v0 >= 256;  // block-uniform
+        if (v < n_vox) {
+            empty_record<K, RB>(my_rec);
+#pragma unroll
+            for (int i = 0; i < K / 4; ++i) my_np[i] = make_uint2(0u, 0u);
+            const int s = offsets[v], e = offsets[v + 1];
+            uint32_t tot_sum = 0, tot_cnt = 0;
+            bool over = false;
+            if (s < e) {
+                uint16_t* ids = reinterpret_cast<uint16_t*>(my_rec);
+                VT* vals = reinterpret_cast<VT*>(reinterpret_cast<uint8_t*>(my_rec) + 2 * K);
+                uint16_t* np = reinterpret_cast<uint16_t*>(my_np);
+                for (int i = s; i < e; ++i) {
+                    const unsigned long long x = __ldg(entries + i);
+                    tot_sum += static_cast<uint32_t>(ent_sum(x));
+                    tot_cnt += static_cast<uint32_t>(ent_npix(x));
+                }
+                if (!append_in_order<K, VT>(entries, s, e, 0, ids, vals, np))
+                    over = merge_general<K, VT>(entries, s, e, 0, ids, vals, np);
+            }
+            if (!whole) {
+                uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
+                uint2* g_np = reinterpret_cast<uint2*>(npix + v * K);
+#pragma unroll
+                for (int i = 0; i < RB / 16; ++i) g_rec[i] = my_rec[i];
+#pragma unroll
+                for (int i = 0; i < K / 4; ++i) g_np[i] = my_np[i];
+            }
+            if (scal_sum) {
+                scal_sum[v] = tot_sum;
+                scal_cnt[v] = tot_cnt;
+            }
+            if (over) atomicAdd(overflow, 1ull);
+        }
+        if (whole) {
+            __syncthreads();  // the run's records and npix rows are in shared memory
+            if (threadIdx.x == 0) {
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                // offsets are multiples of 256 records and 256 npix rows: 16-byte aligned, sizes multiples of 16
+                bulk_store(rec + v0 * RB, s_rec, 256u * RB);
+                bulk_store(npix + v0 * K, s_np, 256u * K * 2u);
+                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // shared memory free again
+            }
+            __syncthreads();
+        }
+    }
+    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+}
+
+template <int K, typename VT>
+cudaError_t finalize_full_v(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
+                            uint16_t* npix, uint32_t* ss, uint32_t* sc, unsigned long long* ovf, cudaStream_t st) {
+    const int64_t want = (n_vox + 255) / 256;
+    const int blocks = static_cast<int>(want < (1 << 30) ? want : (1 << 30));  // one run per CTA
+    k_finalize_full<K, VT><<<blocks, 256, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+    return cudaPeekAtLastError();
+}
+
 template <int K, int kMode>
 cudaError_t finalize_kf(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
                         uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, unsigned long long* ovf,
@@ -452,8 +557,17 @@ cudaError_t finalize_kf(const int32_t* off, const unsigned long long* ent, int64
 
 template <int K>
 cudaError_t finalize_k(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
-                       uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int mode, unsigned long long* ovf,
-                       cudaStream_t st) {
+                       uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int mode, int bulk,
+                       unsigned long long* ovf, cudaStream_t st) {
+    if (mode == 2 && bulk) {
+        switch (dtype) {
+        case DARE_U8: return finalize_full_v<K, uint8_t>(off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        case DARE_F16: return finalize_full_v<K, __half>(off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        case DARE_BF16: return finalize_full_v<K, __nv_bfloat16>(off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        case DARE_F32: return finalize_full_v<K, float>(off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        }
+        return cudaErrorInvalidValue;
+    }
     switch (mode) {
     case 0: return finalize_kf<K, 0>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
     case 1: return finalize_kf<K, 1>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
@@ -486,12 +600,12 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
 
 cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
                             uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode,
-                            unsigned long long* overflow, cudaStream_t st) {
+                            int bulk, unsigned long long* overflow, cudaStream_t st) {
     switch (K) {
-    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, overflow, st);
-    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, overflow, st);
-    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, overflow, st);
-    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, overflow, st);
+    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
+    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
+    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
+    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
     }
     return cudaErrorInvalidValue;
 }
