@@ -98,3 +98,37 @@ def test_server_rejects_bad_requests(tiny, tmp_path):
     server.drain(5.0)
     server.close()
     s.close()
+
+
+def test_server_curvilinear_and_paged_sessions(tiny):
+    """A curvilinear session served next to a linear one (the batch groups
+    them by kernel family) gives what each request gets alone; a session with
+    a brick cache is refused at submission."""
+    curv = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, dtype=dare.DARE_F32, max_slots=8)
+    curv.set_probe(dare.DARE_PROBE_CURVILINEAR, (0.0, -20.0))
+    curv.build(torch.from_numpy(np.ascontiguousarray(tiny.frames)).to(DEV), tiny.frame_poses, tiny.frame_px)
+    lin = gpu_session(tiny, dare.DARE_F32, 8)
+    server = dare.Server(lanes=2, max_batch=6)
+    jobs = []
+    for i in range(24):
+        s = curv if i % 3 else lin
+        W, H = (64, 48) if i % 2 else (96, 80)
+        out, mask = new_outputs(W, H)
+        jobs.append((s, tiny.reslice_poses[i % 16], out, mask))
+        server.submit(s, tiny.reslice_poses[i % 16], out, mask, tiny.out_px, tag=i)
+    done = _wait_all(server, len(jobs))
+    assert all(d[1] == dare.DARE_OK for d in done)
+    for s, T, out, mask in jobs:
+        H, W = out.shape
+        o1, m1 = gpu_reslice(s, T, W, H, tiny.out_px, dare.params_default())
+        assert np.array_equal(mask.cpu().numpy(), m1) and np.array_equal(out.cpu().numpy(), o1)
+    hv = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, dtype=dare.DARE_U8, max_slots=4,
+                      flags=dare.DARE_SESSION_HOST_VOLUME)
+    hv.set_cache(1 << 22)
+    out, mask = new_outputs(16, 16)
+    with pytest.raises(dare.DareError) as ei:
+        server.submit(hv, tiny.reslice_poses[0], out, mask, tiny.out_px, tag=99)
+    assert ei.value.status == dare.DARE_E_UNSUPPORTED
+    server.close()
+    for x in (curv, lin, hv):
+        x.close()
