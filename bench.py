@@ -583,8 +583,8 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
                                     "reslice_ms_per_plane": pg_ms / n_pg,
                                     "mpix_s": n_pg * W * H / (pg_ms * 1e-3) / 1e6, "cache": stats,
                                     "note": "dare_session_set_cache: 8^3-voxel bricks of the plane footprints paged "
-                                            "into device memory, the per-pixel gather reading the cache; one plane "
-                                            "per launch"}
+                                            "into device memory, the per-pixel gather reading the cache; planes in "
+                                            "groups of up to 64 whose bricks fit the cache, one launch per group"}
     hv.close()
 
     # --- the paper's timing axis (Sec. 3): interpolation radius.  BOX gives its

@@ -358,9 +358,10 @@ dare_status dare_session_set_probe(dare_session s, const dare_probe* probe, cons
  * other from the host volume.  Results are bit-identical whatever the cache
  * holds.  A build or reset makes every cached brick stale.  bytes = 0 frees
  * the cache.  DARE_E_STATE for a device-resident session.  Synchronous.
- * dare_reslice_batch runs the planes of such sessions one by one;
- * dare_reslice_batch_host, plans, the server and the allocation-free call
- * refuse them (DARE_E_UNSUPPORTED).
+ * dare_reslice_batch takes consecutive planes of such a session in groups
+ * (up to 64 planes whose bricks fit the cache: one paging pass and one launch
+ * per group); dare_reslice_batch_host, plans, the server and the
+ * allocation-free call refuse them (DARE_E_UNSUPPORTED).
  */
 dare_status dare_session_set_cache(dare_session s, int64_t bytes);
 

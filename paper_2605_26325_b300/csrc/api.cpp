@@ -758,16 +758,18 @@ CurvJob make_curv_job(const dare_session s, const dare_plane* pl, float* out, ui
 }
 
 // Bricks whose records a plane's support can read: a conservative cover from
-// 8 x 8-pixel cells (inside a cell g lies between its values at the cell's
+// 32 x 32-pixel cells (inside a cell g lies between its values at the cell's
 // corners, g being affine in the pixel), each cell's voxel box widened by the
-// support's extent below and above floor(g).
+// support's extent below and above floor(g).  Coarser cells cost fewer host
+// cycles per plane and add a few boundary bricks to the cover.
 void plane_bricks(const dare_session s, const ResliceJob& j, std::vector<uint8_t>& mark, std::vector<int32_t>& out) {
     const int64_t n_b = int64_t(s->nb[0]) * s->nb[1] * s->nb[2];
     mark.assign(size_t(n_b), 0);
     out.clear();
-    for (int v0 = 0; v0 < j.height; v0 += 8)
-        for (int u0 = 0; u0 < j.width; u0 += 8) {
-            const int u1 = std::min(u0 + 7, j.width - 1), v1 = std::min(v0 + 7, j.height - 1);
+    constexpr int kCell = 32;
+    for (int v0 = 0; v0 < j.height; v0 += kCell)
+        for (int u0 = 0; u0 < j.width; u0 += kCell) {
+            const int u1 = std::min(u0 + kCell - 1, j.width - 1), v1 = std::min(v0 + kCell - 1, j.height - 1);
             int blo[3], bhi[3];
             bool empty = false;
             for (int a = 0; a < 3 && !empty; ++a) {
@@ -857,6 +859,63 @@ dare_status page_bricks(dare_session s, const std::vector<int32_t>& need, uint8_
 // host volume directly.
 bool paged_path(const dare_session s, const dare_params* p) {
     return s->cache && !curv_path(s, p) && p->sample_weight == DARE_SAMPLE_MEAN;
+}
+
+// n planes of one paged session in one go: the union of their bricks paged in
+// once, their weight tables in one launch, one launch of the paged kernel.
+// Each plane's result is that of dare_reslice.
+dare_status paged_group(dare_session s, const dare_reslice_req* reqs, int n, const std::vector<int32_t>& bricks,
+                        const dare_params* params, cudaStream_t st) {
+    const int wb = params->weight_dtype == DARE_WEIGHTS_F16 ? 2 : 4;
+    const size_t wt = align_up(size_t(std::max(s->n_frames, 1)) * wb, 256);
+    const size_t o_tj = wt * size_t(n);
+    const size_t o_pj = align_up(o_tj + size_t(n) * sizeof(TableJob), 256);
+    const size_t o_ls = align_up(o_pj + size_t(n) * sizeof(PagedJob), 256);
+    const size_t need = o_ls + (2 * bricks.size() + 2) * sizeof(int2);
+    dare_status rc = session_begin(s, st);
+    if (rc != DARE_OK) return rc;
+    rc = ensure_workspace(s, need, st);
+    if (rc != DARE_OK) return rc;
+    uint8_t* ws = static_cast<uint8_t*>(s->ws);
+    const int pin = 1 + (s->next_desc++ & 7);
+    const size_t desc = o_ls - o_tj;
+    rc = ensure_pinned(s, pin, desc);
+    if (rc != DARE_OK) return rc;
+    uint8_t* pinned = static_cast<uint8_t*>(s->pinned[pin]);
+    auto* tjs = reinterpret_cast<TableJob*>(pinned);
+    auto* pjs = reinterpret_cast<PagedJob*>(pinned + (o_pj - o_tj));
+    int max_w = 0, max_h = 0;
+    for (int k = 0; k < n; ++k) {
+        TableJob tj{};
+        plane_vectors(s, &reqs[k].plane, params->normal_axis, &tj);
+        tj.frames = s->frames_dev;
+        tj.wtab = ws + size_t(k) * wt;
+        tj.n_frames = s->n_frames;
+        tjs[k] = tj;
+        PagedJob pj{};
+        pj.j = make_job(s, &reqs[k].plane, ws + size_t(k) * wt, reqs[k].out, reqs[k].mask, params->unassigned, params);
+        pj.cache = s->cache;
+        pj.table = s->brick_table;
+        for (int a = 0; a < 3; ++a) pj.nb[a] = s->nb[a];
+        pjs[k] = pj;
+        max_w = std::max(max_w, reqs[k].plane.width);
+        max_h = std::max(max_h, reqs[k].plane.height);
+    }
+    CUDA_TRY(cudaMemcpyAsync(ws + o_tj, pinned, desc, cudaMemcpyHostToDevice, st));
+    CUDA_TRY(cudaEventRecord(s->pinned_ev[pin], st));
+    if (s->n_frames > 0) {
+        KernelScope ks("weight_table", st, 1);
+        CUDA_TRY(launch_weight_tables(reinterpret_cast<const TableJob*>(ws + o_tj), nullptr, n, s->n_frames,
+                                      table_params(params), st));
+    }
+    rc = page_bricks(s, bricks, ws + o_ls, st);
+    if (rc != DARE_OK) return rc;
+    {
+        KernelScope ks("reslice_paged", st, 1);
+        CUDA_TRY(launch_reslice_paged(reinterpret_cast<const PagedJob*>(ws + o_pj), nullptr, n, max_w, max_h, s->K,
+                                      s->dtype, params->weight_dtype == DARE_WEIGHTS_F16, st));
+    }
+    return session_end(s, st);
 }
 
 }  // namespace
@@ -1669,7 +1728,8 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
         for (int a = 0; a < 3; ++a) pj.nb[a] = s->nb[a];
         {
             KernelScope ks("reslice_paged", st, 1);
-            CUDA_TRY(launch_reslice_paged(pj, s->K, s->dtype, params->weight_dtype == DARE_WEIGHTS_F16, st));
+            CUDA_TRY(launch_reslice_paged(nullptr, &pj, 1, plane->width, plane->height, s->K, s->dtype,
+                                          params->weight_dtype == DARE_WEIGHTS_F16, st));
         }
         return session_end(s, st);
     }
@@ -1706,10 +1766,41 @@ dare_status dare_reslice_batch(const dare_reslice_req* reqs, int32_t n, const da
     if (rc != DARE_OK) return rc;
     for (int32_t i = 0; i < n; ++i)
         if (reqs[i].session->cache) {
-            // sessions with a brick cache page per plane: every request in order, one plane at a time
-            for (int32_t k = 0; k < n; ++k) {
-                rc = dare_reslice(reqs[k].session, &reqs[k].plane, params, reqs[k].out, reqs[k].mask, stream);
+            // sessions with a brick cache page per group of planes: consecutive requests of one such
+            // session whose bricks fit its cache together (at most 64) go as one group; any other
+            // request runs alone, in order
+            DeviceGuard dgp(reqs[0].session->cfg.device);
+            cudaStream_t sp = static_cast<cudaStream_t>(stream);
+            std::vector<uint8_t> umark;
+            std::vector<int32_t> uni, need;
+            for (int32_t k = 0; k < n;) {
+                dare_session s = reqs[k].session;
+                if (!paged_path(s, params)) {
+                    rc = dare_reslice(s, &reqs[k].plane, params, reqs[k].out, reqs[k].mask, stream);
+                    if (rc != DARE_OK) return rc;
+                    ++k;
+                    continue;
+                }
+                umark.assign(size_t(s->nb[0]) * s->nb[1] * s->nb[2], 0);
+                uni.clear();
+                int32_t j = k;
+                while (j < n && j - k < 64 && reqs[j].session == s) {
+                    const ResliceJob pj = make_job(s, &reqs[j].plane, nullptr, reqs[j].out, reqs[j].mask,
+                                                   params->unassigned, params);
+                    plane_bricks(s, pj, s->brick_mark, need);
+                    size_t add = 0;
+                    for (int32_t b : need) add += umark[size_t(b)] ? 0 : 1;
+                    if (j > k && int64_t(uni.size() + add) > s->n_slots) break;
+                    for (int32_t b : need)
+                        if (!umark[size_t(b)]) {
+                            umark[size_t(b)] = 1;
+                            uni.push_back(b);
+                        }
+                    ++j;
+                }
+                rc = paged_group(s, reqs + k, j - k, uni, params, sp);
                 if (rc != DARE_OK) return rc;
+                k = j;
             }
             return DARE_OK;
         }

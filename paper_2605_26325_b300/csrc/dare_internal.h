@@ -171,7 +171,9 @@ struct PagedJob {
 cudaError_t launch_page_in(const int2* updates, int n_updates, const int2* pages, int n_pages, const uint8_t* host_rec,
                            uint8_t* cache, const int32_t dims[3], const int32_t nb[3], int rec_bytes, int32_t* table,
                            cudaStream_t st);
-cudaError_t launch_reslice_paged(const PagedJob& job, int K, int dtype, int half_weights, cudaStream_t st);
+// one plane (one_job) or n_jobs planes of a paged group (jobs_dev, grid z)
+cudaError_t launch_reslice_paged(const PagedJob* jobs_dev, const PagedJob* one_job, int n_jobs, int max_w, int max_h,
+                                 int K, int dtype, int half_weights, cudaStream_t st);
 
 // curvilinear probes (kernels_curv.cu): per-pixel gather with in-kernel Eq. 1 / Eq. 2
 cudaError_t launch_reslice_curv(const CurvJob* jobs_dev, const CurvJob* one_job, int n_jobs, int max_w, int max_h,

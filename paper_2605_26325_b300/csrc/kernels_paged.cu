@@ -131,24 +131,39 @@ __global__ void __launch_bounds__(256) k_reslice_paged(const __grid_constant__ P
     paged_body<K, VT, WT>(P);
 }
 
+// planes of one paged group (their bricks paged in together), one per grid z
+template <int K, typename VT, typename WT>
+__global__ void __launch_bounds__(256) k_reslice_paged_batch(const PagedJob* __restrict__ jobs) {
+    paged_body<K, VT, WT>(jobs[blockIdx.z]);
+}
+
 template <int K, typename VT>
-cudaError_t launch_p(const PagedJob& P, int half_w, cudaStream_t st) {
+cudaError_t launch_p(const PagedJob* jobs_dev, const PagedJob* one, int n_jobs, int max_w, int max_h, int half_w,
+                     cudaStream_t st) {
     const dim3 block(32, 8);
-    const dim3 grid((P.j.width + 31) / 32, (P.j.height + 7) / 8);
-    if (half_w)
-        k_reslice_paged<K, VT, __half><<<grid, block, 0, st>>>(P);
-    else
-        k_reslice_paged<K, VT, float><<<grid, block, 0, st>>>(P);
+    const dim3 grid((max_w + 31) / 32, (max_h + 7) / 8, one ? 1 : n_jobs);
+    if (one) {
+        if (half_w)
+            k_reslice_paged<K, VT, __half><<<grid, block, 0, st>>>(*one);
+        else
+            k_reslice_paged<K, VT, float><<<grid, block, 0, st>>>(*one);
+    } else {
+        if (half_w)
+            k_reslice_paged_batch<K, VT, __half><<<grid, block, 0, st>>>(jobs_dev);
+        else
+            k_reslice_paged_batch<K, VT, float><<<grid, block, 0, st>>>(jobs_dev);
+    }
     return cudaPeekAtLastError();
 }
 
 template <int K>
-cudaError_t launch_p_k(const PagedJob& P, int dtype, int half_w, cudaStream_t st) {
+cudaError_t launch_p_k(const PagedJob* jobs_dev, const PagedJob* one, int n_jobs, int max_w, int max_h, int dtype,
+                       int half_w, cudaStream_t st) {
     switch (dtype) {
-    case DARE_U8: return launch_p<K, uint8_t>(P, half_w, st);
-    case DARE_F16: return launch_p<K, __half>(P, half_w, st);
-    case DARE_BF16: return launch_p<K, __nv_bfloat16>(P, half_w, st);
-    case DARE_F32: return launch_p<K, float>(P, half_w, st);
+    case DARE_U8: return launch_p<K, uint8_t>(jobs_dev, one, n_jobs, max_w, max_h, half_w, st);
+    case DARE_F16: return launch_p<K, __half>(jobs_dev, one, n_jobs, max_w, max_h, half_w, st);
+    case DARE_BF16: return launch_p<K, __nv_bfloat16>(jobs_dev, one, n_jobs, max_w, max_h, half_w, st);
+    case DARE_F32: return launch_p<K, float>(jobs_dev, one, n_jobs, max_w, max_h, half_w, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -169,13 +184,15 @@ cudaError_t launch_page_in(const int2* updates, int n_updates, const int2* pages
     return cudaPeekAtLastError();
 }
 
-cudaError_t launch_reslice_paged(const PagedJob& job, int K, int dtype, int half_weights, cudaStream_t st) {
-    if (job.j.width <= 0 || job.j.height <= 0) return cudaSuccess;
+cudaError_t launch_reslice_paged(const PagedJob* jobs_dev, const PagedJob* one_job, int n_jobs, int max_w, int max_h,
+                                 int K, int dtype, int half_weights, cudaStream_t st) {
+    if (n_jobs <= 0 || max_w <= 0 || max_h <= 0) return cudaSuccess;
+    if (!one_job && n_jobs > 65535) return cudaErrorInvalidValue;
     switch (K) {
-    case 4: return launch_p_k<4>(job, dtype, half_weights, st);
-    case 8: return launch_p_k<8>(job, dtype, half_weights, st);
-    case 12: return launch_p_k<12>(job, dtype, half_weights, st);
-    case 16: return launch_p_k<16>(job, dtype, half_weights, st);
+    case 4: return launch_p_k<4>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, half_weights, st);
+    case 8: return launch_p_k<8>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, half_weights, st);
+    case 12: return launch_p_k<12>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, half_weights, st);
+    case 16: return launch_p_k<16>(jobs_dev, one_job, n_jobs, max_w, max_h, dtype, half_weights, st);
     }
     return cudaErrorInvalidValue;
 }
