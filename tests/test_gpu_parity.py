@@ -528,3 +528,44 @@ def test_reset_rebuild_odd_grid_matches_oracle(tiny):
     assert np.array_equal(got["scalar_count"], e["tot_npix"].astype(np.uint32))
     assert np.array_equal(got["scalar_sum"], e["tot_sum"].astype(np.uint32))
     s.close()
+
+
+@pytest.mark.parametrize("path", PATHS)
+def test_reslice_maximum_plane_sizes(tiny, tiny_f32, path):
+    """Planes at the largest accepted size along one axis (65535 pixels wide,
+    or tall) against the oracle; one past it is refused."""
+    s, vol = tiny_f32
+    p = dare.params_default(path=path)
+    px = (0.0005, 0.0005)  # 65535 pixels span 33 mm: across the whole grid
+    for W, H in ((65535, 2), (3, 65535)):
+        T = synth.plane_pose_centred(tiny.reslice_poses[4][:3, :3], np.zeros(3), W, H, *px)
+        out, mw = gpu_reslice(s, T, W, H, px, p)
+        ref, rm = oracle.reslice(vol, T, W, H, px, ora_params(p))
+        assert rm.sum() > 1000
+        assert_parity(out, mw, ref, rm, W)
+    out, mask = new_outputs(8, 8)
+    with pytest.raises(dare.DareError) as ei:
+        s.reslice(tiny.reslice_poses[0], torch.empty((1, 65536), device=DEV), torch.empty((1, 2048), dtype=torch.int32,
+                                                                                        device=DEV), tiny.out_px, p)
+    assert ei.value.status == dare.DARE_E_INVALID
+
+
+@pytest.mark.parametrize("W,H", [(1, 1), (37, 29), (33, 64), (130, 7)])
+def test_build_ragged_frame_sizes(tiny, W, H):
+    """Frames that are not whole 32 x 32 scatter tiles (down to one pixel):
+    records bit-exact against the oracle."""
+    rng = np.random.default_rng(W * 131 + H)
+    frames = rng.integers(0, 256, (60, H, W)).astype(np.uint8)
+    px = (0.3, 0.3)
+    poses = np.stack([synth.plane_pose_centred(tiny.frame_poses[i][:3, :3], rng.uniform(-4, 4, 3), W, H, *px)
+                      for i in range(0, 120, 2)])
+    s = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, dtype=dare.DARE_F32, max_slots=8)
+    s.build(torch.from_numpy(frames).to(DEV), poses, px)
+    got = s.read_records(npix=True)
+    vol = oracle.build(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, frames, poses, px, oracle.F32, 8)
+    ids, vals, npix, e = oracle_dense(vol, 8, dare.DARE_F32)
+    assert e["npix"].sum() > 0
+    assert np.array_equal(got["frame_ids"], ids)
+    assert np.array_equal(got["values"].view(np.uint32), vals.view(np.uint32))
+    assert np.array_equal(got["npix"], npix)
+    s.close()
