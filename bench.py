@@ -166,10 +166,21 @@ def peaks():
 
 
 def kernel_source_hash():
+    """Hash of what the tiled reslice kernel is built from: its source, the
+    device helpers, and the parts of the internal header it uses (the job
+    layout and the fixed-point / tile constants); other declarations in that
+    header do not change the kernel."""
+    csrc = os.path.join(ROOT, "paper_2605_26325_b300", "csrc")
     h = hashlib.sha256()
-    for f in ("kernels_tiled.cu", "device_common.cuh", "dare_internal.h"):
-        with open(os.path.join(ROOT, "paper_2605_26325_b300", "csrc", f), "rb") as fh:
+    for f in ("kernels_tiled.cu", "device_common.cuh"):
+        with open(os.path.join(csrc, f), "rb") as fh:
             h.update(fh.read())
+    hdr = open(os.path.join(csrc, "dare_internal.h")).read()
+    a = hdr.index("struct ResliceJob {")
+    h.update(hdr[a:hdr.index("};", a) + 2].encode())
+    for line in hdr.splitlines():
+        if line.startswith("constexpr") and any(k in line for k in ("kFixBits", "kFixOne", "kTileW", "kTileH")):
+            h.update(line.encode())
     return h.hexdigest()[:16]
 
 
