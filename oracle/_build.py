@@ -1,6 +1,6 @@
 """Compile the CPU oracle (plain C, FP64, OpenMP over pixels) in place.
 
-Test infrastructure: building the checker is not using it.
+Test infrastructure: building the oracle is not using it.
 """
 import os
 import subprocess
