@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--duration", type=float, default=10.0, help="seconds of the serving run")
     ap.add_argument("--volumes", type=int, default=64, help="volumes of the batched workload")
     ap.add_argument("--quick", action="store_true", help="main timed loop only (for profiler runs)")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="build from the first N frames only (profiler runs on a smaller build; 0 = all 1600)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     return ap.parse_args()
 
@@ -286,6 +288,8 @@ def run_dare(args, dist):
     seed = 1 + dist.rank
     t0 = time.perf_counter()
     w = synth.working_workload(seed, n_poses=args.poses)
+    if args.frames > 0:
+        w.frames, w.frame_poses = w.frames[:args.frames], w.frame_poses[:args.frames]
     log(f"rank {dist.rank}: workload ready in {time.perf_counter() - t0:.1f} s")
     P, W, H = args.poses, w.out_w, w.out_h
     dtype = DTYPE_NAMES[args.dtype]
