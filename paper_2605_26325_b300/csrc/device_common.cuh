@@ -60,9 +60,19 @@ __device__ __forceinline__ void load_record(const uint8_t* p, uint4 (&r)[RecShap
     for (int i = 0; i < RecShape<K, VT>::kVec; ++i) r[i] = __ldg(q + i);
 }
 
+// Slots per group of weight lookups in collapse_voxel: half the record, at least 4
+// (out-of-line callers, where registers are scarcer, pass 1).
+template <int K>
+struct SlotGroup {
+    static constexpr int G = K / 2 > 4 ? K / 2 : (K < 4 ? K : 4);
+};
+
 // (A_c, B_c) of one voxel from its whole record, read in one round trip (ids
-// first, values after; empty ids sort last).
-template <int K, typename VT, typename WT>
+// first, values after; empty ids sort last).  The weight-table lookups go in
+// groups of G slots whose loads issue together (each predicated on its slot
+// being used), so a record waits on about K / G table round trips instead of
+// one per sample; the sums keep slot order, so the result does not depend on G.
+template <int K, typename VT, typename WT, int G = SlotGroup<K>::G>
 __device__ __forceinline__ float2 collapse_voxel(const uint8_t* rec, int64_t vi, const WT* wt) {
     using S = RecShape<K, VT>;
     const uint4* q = reinterpret_cast<const uint4*>(rec + vi * S::kBytes);
@@ -71,12 +81,21 @@ __device__ __forceinline__ float2 collapse_voxel(const uint8_t* rec, int64_t vi,
     for (int i = 0; i < S::kVec; ++i) r[i] = __ldg(q + i);
     float A = 0.0f, B = 0.0f;
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-        const uint32_t id = slot_id<K, VT>(r, s);
-        if (id == DARE_EMPTY_FRAME) break;  // empty slots come last
-        const float w = weight_of(wt, static_cast<int>(id));
-        A = fmaf(w, slot_value<K, VT>(r, s), A);
-        B += w;
+    for (int g = 0; g < K; g += G) {
+        uint32_t id[G];
+        float w[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) id[j] = g + j < K ? slot_id<K, VT>(r, g + j) : DARE_EMPTY_FRAME;
+        if (id[0] == DARE_EMPTY_FRAME) break;  // empty slots come last
+#pragma unroll
+        for (int j = 0; j < G; ++j) w[j] = id[j] != DARE_EMPTY_FRAME ? weight_of(wt, static_cast<int>(id[j])) : 0.0f;
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            if (id[j] != DARE_EMPTY_FRAME) {
+                A = fmaf(w[j], slot_value<K, VT>(r, g + j), A);
+                B += w[j];
+            }
+        if (id[G - 1] == DARE_EMPTY_FRAME) break;
     }
     return make_float2(A, B);
 }

@@ -68,7 +68,7 @@ __device__ __noinline__ void direct_pixel(const ResliceJob& J, int u, int v, flo
         const float t = (dx ? pc.fr[0] : 1.0f - pc.fr[0]) * (dy ? pc.fr[1] : 1.0f - pc.fr[1]) *
                         (dz ? pc.fr[2] : 1.0f - pc.fr[2]);
         const int64_t vi = cx + static_cast<int64_t>(J.dims[0]) * (cy + static_cast<int64_t>(J.dims[1]) * cz);
-        const float2 ab = collapse_voxel<K, VT, WT>(J.rec, vi, wt);
+        const float2 ab = collapse_voxel<K, VT, WT, 1>(J.rec, vi, wt);
         num = fmaf(t, ab.x, num);
         den = fmaf(t, ab.y, den);
     }
