@@ -55,13 +55,24 @@ __device__ __forceinline__ float2 collapse_voxel_px(const uint8_t* rec, const ui
 #pragma unroll
     for (int i = 0; i < K / 4; ++i) n[i] = __ldg(q + i);
     float A = 0.0f, B = 0.0f;
+    constexpr int G = SlotGroup<K>::G;  // table lookups in groups, as in collapse_voxel
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-        const uint32_t id = slot_id<K, VT>(r, s);
-        if (id == DARE_EMPTY_FRAME) break;
-        const float w = weight_of(wt, static_cast<int>(id)) * slot_npix<K>(n, s);
-        A = fmaf(w, slot_value<K, VT>(r, s), A);
-        B += w;
+    for (int g = 0; g < K; g += G) {
+        uint32_t id[G];
+        float wf[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) id[j] = g + j < K ? slot_id<K, VT>(r, g + j) : DARE_EMPTY_FRAME;
+        if (id[0] == DARE_EMPTY_FRAME) break;
+#pragma unroll
+        for (int j = 0; j < G; ++j) wf[j] = id[j] != DARE_EMPTY_FRAME ? weight_of(wt, static_cast<int>(id[j])) : 0.0f;
+#pragma unroll
+        for (int j = 0; j < G; ++j)
+            if (id[j] != DARE_EMPTY_FRAME) {
+                const float w = wf[j] * slot_npix<K>(n, g + j);
+                A = fmaf(w, slot_value<K, VT>(r, g + j), A);
+                B += w;
+            }
+        if (id[G - 1] == DARE_EMPTY_FRAME) break;
     }
     return make_float2(A, B);
 }
