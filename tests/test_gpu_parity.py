@@ -132,6 +132,38 @@ def test_reslice_variants(tiny, tiny_f32, path):
 
 
 @pytest.mark.parametrize("path", PATHS)
+@pytest.mark.parametrize("K", [4, 8, 12, 16])
+def test_reslice_every_record_fill(tiny, K, path):
+    """Records holding every sample count from 1 to K, full ones included: 3 mm
+    voxels over every 1st, 2nd, 3rd and 5th tiny frame at 0.1 x 0.12 mm pixels
+    put 1 to 16 frames in a voxel.  The reslice kernels look the weights of a
+    record's samples up in groups of slots and stop at the first empty slot, so
+    each count stops at a different place inside or between groups; checked on
+    the TENT R = 1 kernels, the general-radius kernels (BOX R = 2) and per-pixel
+    sample weighting."""
+    g = synth.centred_grid((12, 10, 9), 3.0)
+    seen = set()
+    for stride in (1, 2, 3, 5):
+        w = types.SimpleNamespace(grid=g, frames=tiny.frames[::stride], frame_poses=tiny.frame_poses[::stride],
+                                  frame_px=(0.1, 0.12))
+        s = gpu_session(w, dare.DARE_F32, K)
+        vol = oracle_volume(w, dare.DARE_F32, K)
+        seen |= set(np.diff(vol.export()["offsets"]).tolist())
+        for p in (dare.params_default(path=path),
+                  dare.params_default(path=path, radius_vox=2, dist_kernel=dare.DARE_BOX),
+                  dare.params_default(path=path, sample_weight=dare.DARE_SAMPLE_PIXELS)):
+            covered = 0
+            for T in tiny.reslice_poses[[0, 3, 5, 12]]:
+                out, mw = gpu_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, p)
+                ref, rm = oracle.reslice(vol, T, tiny.out_w, tiny.out_h, tiny.out_px, ora_params(p))
+                assert_parity(out, mw, ref, rm, tiny.out_w)
+                covered += int(rm.sum())
+            assert covered > 0
+        s.close()
+    assert set(range(1, K + 1)) <= seen
+
+
+@pytest.mark.parametrize("path", PATHS)
 def test_reslice_fp16_weights(tiny, path):
     """FP16 weight table: masks stay bit-exact; values within the bound of a
     relative weight error eps = 2^-11: |d out| <= 2 eps / (1 - eps) (max I - min I)."""
