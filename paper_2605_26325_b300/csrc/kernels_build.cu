@@ -65,12 +65,13 @@ __device__ __forceinline__ void hash_add(int* keys, unsigned* npx, unsigned* sum
 // block that land in one voxel are combined before touching shared memory.
 __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int u0, int v0, int* keys,
                                                unsigned* npx, unsigned* sums, int* list, int* n_list) {
-    // npx and sums are the two halves of one 8-byte-aligned buffer: cleared with 8-byte stores
-    unsigned long long* both = reinterpret_cast<unsigned long long*>(npx);
-    for (int i = threadIdx.x; i < kHash; i += kThreads) {
-        keys[i] = kEmptyKey;
-        both[i] = 0ull;
-    }
+    // keys and the npx / sums buffer (its two halves) are declared 16-byte
+    // aligned by the kernel: cleared with 16-byte stores
+    uint4* keys4 = reinterpret_cast<uint4*>(keys);
+    uint4* both4 = reinterpret_cast<uint4*>(npx);
+    static_assert(kEmptyKey == -1, "keys cleared to all-ones words");
+    for (int i = threadIdx.x; i < kHash / 4; i += kThreads) keys4[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
+    for (int i = threadIdx.x; i < kHash / 2; i += kThreads) both4[i] = make_uint4(0u, 0u, 0u, 0u);
     if (threadIdx.x == 0) *n_list = 0;
     __shared__ int64_t aff[9];
     if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
@@ -138,8 +139,8 @@ __device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int 
 __global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constant__ ScatterArgs A,
                                                             int32_t* __restrict__ count, uint4* __restrict__ pairs,
                                                             int32_t* __restrict__ n_pairs) {
-    __shared__ int keys[kHash];
-    __shared__ unsigned long long acc_buf[kHash];  // npx, then sums: kHash 32-bit counters each
+    __shared__ __align__(16) int keys[kHash];
+    __shared__ __align__(16) unsigned long long acc_buf[kHash];  // npx, then sums: kHash 32-bit counters each
     __shared__ int list[kTile * kTile];            // slots of the tile's distinct voxels, in insertion order
     __shared__ int n_list;
     unsigned* npx = reinterpret_cast<unsigned*>(acc_buf);
