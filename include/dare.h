@@ -171,7 +171,10 @@ typedef struct {
  * Device-memory allocator used by a session for its volume and workspace.
  * alloc returns device memory of at least `bytes` (256-byte aligned) or NULL;
  * free releases it.  `stream` is the stream of the call that allocates (may
- * be NULL).  Both NULL: the library uses cudaMalloc / cudaFree.
+ * be NULL).  Both NULL: the library uses cudaMalloc / cudaFree.  A block that
+ * is not 256-byte aligned is handed back to free at once and the call that
+ * wanted it fails with DARE_E_OOM (the kernels use 16-byte vector and bulk
+ * copies on it).
  */
 typedef struct {
     void* (*alloc)(size_t bytes, void* stream, void* ctx);

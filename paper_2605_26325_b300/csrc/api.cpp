@@ -365,6 +365,11 @@ struct dare_session_s {
             cudaGetLastError();
             p = nullptr;
         }
+        if (p && (reinterpret_cast<uintptr_t>(p) & 255u) != 0) {
+            // a caller-supplied allocator broke the 256-byte alignment the kernels rely on
+            dev_free(p, bytes, st);
+            p = nullptr;
+        }
         return p;
     }
     void dev_free(void* p, size_t bytes, cudaStream_t st) {

@@ -137,9 +137,11 @@ cudaError_t plain_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, in
 
 // ------------------------------------------------------------------ exclusive scan (3 passes)
 
-constexpr int kScanThreads = 1024;
-constexpr int kScanItems = 8;
-constexpr int kScanTile = kScanThreads * kScanItems;
+constexpr int kScanThreads = 256;                       // reduce and down passes
+constexpr int kScanVec = 4;                             // 16-byte loads per thread
+constexpr int kScanItems = 4 * kScanVec;                // counters per thread
+constexpr int kScanTile = kScanThreads * kScanItems;    // counters per block
+constexpr int kScanTopThreads = 1024;                   // the one block that scans the block sums
 
 __device__ __forceinline__ int block_exclusive_scan(int x, int* smem, int* total) {
     // warp scan
@@ -168,25 +170,46 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* smem, int* total
     return warp_off + incl - x;
 }
 
+// A thread's kScanItems counters; whole groups (every one but the array's
+// tail) with 16-byte loads: `in` is 256-byte aligned and base a multiple of 16.
+__device__ __forceinline__ void scan_load(const int32_t* __restrict__ in, int64_t n, int64_t base,
+                                          int (&v)[kScanItems]) {
+    if (base + kScanItems <= n) {
+        const int4* q = reinterpret_cast<const int4*>(in + base);
+#pragma unroll
+        for (int i = 0; i < kScanVec; ++i) {
+            const int4 x = __ldg(q + i);
+            v[4 * i] = x.x;
+            v[4 * i + 1] = x.y;
+            v[4 * i + 2] = x.z;
+            v[4 * i + 3] = x.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i) v[i] = base + i < n ? in[base + i] : 0;
+    }
+}
+
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __restrict__ in, int64_t n,
                                                               int32_t* __restrict__ block_sums) {
     __shared__ int smem[32];
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
+    int v[kScanItems];
+    scan_load(in, n, base, v);
     int s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i)
-        if (base + i < n) s += in[base + i];
+    for (int i = 0; i < kScanItems; ++i) s += v[i];
     int total;
     block_exclusive_scan(s, smem, &total);
     if (threadIdx.x == 0) block_sums[blockIdx.x] = total;
 }
 
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(int32_t* block_sums, int64_t nb) {
+__global__ void __launch_bounds__(kScanTopThreads) k_scan_top(int32_t* block_sums, int64_t nb) {
     __shared__ int smem[32];
     __shared__ int carry;
     if (threadIdx.x == 0) carry = 0;
     __syncthreads();
-    for (int64_t base = 0; base < nb; base += kScanThreads) {
+    for (int64_t base = 0; base < nb; base += kScanTopThreads) {
         const int64_t i = base + threadIdx.x;
         const int x = i < nb ? block_sums[i] : 0;
         int total;
@@ -204,18 +227,26 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t* __res
     __shared__ int smem[32];
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
     int vals[kScanItems];
+    scan_load(in, n, base, vals);
     int s = 0;
 #pragma unroll
-    for (int i = 0; i < kScanItems; ++i) {
-        vals[i] = base + i < n ? in[base + i] : 0;
-        s += vals[i];
-    }
+    for (int i = 0; i < kScanItems; ++i) s += vals[i];
     int total;
     int run = block_sums[blockIdx.x] + block_exclusive_scan(s, smem, &total);
+    int ex[kScanItems];
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
-        if (base + i < n) out[base + i] = run;
+        ex[i] = run;
         run += vals[i];
+    }
+    if (base + kScanItems <= n) {  // `out` is 256-byte aligned too
+        int4* q = reinterpret_cast<int4*>(out + base);
+#pragma unroll
+        for (int i = 0; i < kScanVec; ++i) q[i] = make_int4(ex[4 * i], ex[4 * i + 1], ex[4 * i + 2], ex[4 * i + 3]);
+    } else {
+#pragma unroll
+        for (int i = 0; i < kScanItems; ++i)
+            if (base + i < n) out[base + i] = ex[i];
     }
     if (blockIdx.x == gridDim.x - 1 && threadIdx.x == blockDim.x - 1) out[n] = run;
 }
@@ -401,7 +432,7 @@ cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, in
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb + 1 > block_sums_len || nb > INT_MAX) return cudaErrorInvalidValue;
     k_scan_reduce<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums);
-    k_scan_top<<<1, kScanThreads, 0, st>>>(block_sums, nb);
+    k_scan_top<<<1, kScanTopThreads, 0, st>>>(block_sums, nb);
     k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums, out);
     return cudaPeekAtLastError();
 }

@@ -313,6 +313,52 @@ def test_allocator_hook_and_oom(tiny):
     assert len(alloc.live) == 0
 
 
+class _ShiftedAllocator:
+    """Caller allocator whose blocks start `shift` bytes past a 256-byte boundary."""
+
+    def __init__(self, shift):
+        self.shift, self.live, self.freed = shift, {}, []
+
+        def _alloc(nbytes, stream, ctx):
+            t = torch.empty(int(nbytes) + 512, dtype=torch.uint8, device=DEV)
+            p = (t.data_ptr() + 255) // 256 * 256 + self.shift
+            self.live[p] = t
+            return p
+
+        def _free(ptr, nbytes, stream, ctx):
+            self.freed.append(ptr)
+            self.live.pop(ptr, None)
+
+        self._a, self._f = dare._ALLOC_FN(_alloc), dare._FREE_FN(_free)
+
+    def as_struct(self):
+        a = dare.dare_allocator()
+        a.alloc, a.free, a.ctx = self._a, self._f, None
+        return a
+
+
+def test_allocator_misaligned_block_refused(tiny):
+    """A block off the 256-byte alignment the header asks of a caller allocator
+    goes straight back to its free and the call fails with DARE_E_OOM, before
+    any kernel could touch it; aligned blocks from the same allocator work."""
+    bad = _ShiftedAllocator(16)
+    with pytest.raises(dare.DareError) as ei:
+        dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, allocator=bad)
+    assert ei.value.status == dare.DARE_E_OOM
+    assert len(bad.freed) == 1 and not bad.live
+    good = _ShiftedAllocator(0)
+    s = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, allocator=good)
+    s.build(torch.from_numpy(tiny.frames).to(DEV), tiny.frame_poses, tiny.frame_px)
+    ref = gpu_session(tiny, dare.DARE_F32, 8)
+    p = dare.params_default()
+    a = gpu_reslice(s, tiny.reslice_poses[2], 64, 64, tiny.out_px, p)
+    b = gpu_reslice(ref, tiny.reslice_poses[2], 64, 64, tiny.out_px, p)
+    assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
+    s.close()
+    ref.close()
+    assert not good.live
+
+
 def test_memory_budget_admission(tiny):
     base = dare.memory_in_use()
     dare.set_memory_budget(base + 1024)
