@@ -171,7 +171,8 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* smem, int* total
 }
 
 // A thread's kScanItems counters; whole groups (every one but the array's
-// tail) with 16-byte loads: `in` is 256-byte aligned and base a multiple of 16.
+// tail) with 16-byte loads: the launcher checks that `in` and `out` are 16-byte
+// aligned, and base is a multiple of 16 counters.
 __device__ __forceinline__ void scan_load(const int32_t* __restrict__ in, int64_t n, int64_t base,
                                           int (&v)[kScanItems]) {
     if (base + kScanItems <= n) {
@@ -239,7 +240,7 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t* __res
         ex[i] = run;
         run += vals[i];
     }
-    if (base + kScanItems <= n) {  // `out` is 256-byte aligned too
+    if (base + kScanItems <= n) {  // `out` is 16-byte aligned too
         int4* q = reinterpret_cast<int4*>(out + base);
 #pragma unroll
         for (int i = 0; i < kScanVec; ++i) q[i] = make_int4(ex[4 * i], ex[4 * i + 1], ex[4 * i + 2], ex[4 * i + 3]);
@@ -431,6 +432,8 @@ cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, in
                                   int64_t block_sums_len, cudaStream_t st) {
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb + 1 > block_sums_len || nb > INT_MAX) return cudaErrorInvalidValue;
+    // the passes move 16-byte groups of counters
+    if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return cudaErrorInvalidValue;
     k_scan_reduce<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums);
     k_scan_top<<<1, kScanTopThreads, 0, st>>>(block_sums, nb);
     k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums, out);
