@@ -3,12 +3,15 @@ despite GPU memory limits): a DARE_SESSION_HOST_VOLUME session with a device
 cache of 8^3-voxel bricks.  Results must not depend on what the cache holds
 (one slot, a few, all of them: bit-identical), must match the FP64 oracle
 (masks exact, values 1e-5 relative), and must follow builds and resets."""
+import types
+
 import numpy as np
 import pytest
 import torch
 
 import oracle
 import paper_2605_26325_b300 as dare
+import synth
 from gpu_helpers import DEV, ORA_DTYPE, assert_parity, gpu_reslice, new_outputs, ora_params, oracle_volume
 
 pytestmark = pytest.mark.gpu
@@ -105,3 +108,27 @@ def test_cache_arguments(tiny):
     h.set_cache(1 << 40)  # more than the volume: one slot per brick
     assert h.cache_stats()["slots"] == 512
     h.close()
+
+
+@pytest.mark.parametrize("K", [8, 12, 16])
+def test_paged_every_record_fill(tiny, K):
+    """The paged gather on records of every fill from 1 to K (3 mm voxels over
+    strided frame subsets, as in the device-resident parity test): a 2-brick
+    cache (most records over the host link) and a cache of every brick give
+    the same bits, and both match the oracle."""
+    g = synth.centred_grid((12, 10, 9), 3.0)
+    p = dare.params_default()
+    for stride in (1, 3, 5):
+        w = types.SimpleNamespace(grid=g, frames=tiny.frames[::stride], frame_poses=tiny.frame_poses[::stride],
+                                  frame_px=(0.1, 0.12))
+        small = host_session(w, dare.DARE_F32, K, cache_bricks=2)
+        full = host_session(w, dare.DARE_F32, K, cache_bricks=1 << 12)
+        vol = oracle.build(g.dims, g.spacing, g.vol_to_world, w.frames, w.frame_poses, w.frame_px, oracle.F32, K)
+        for T in tiny.reslice_poses[[0, 3, 5]]:
+            a = gpu_reslice(small, T, tiny.out_w, tiny.out_h, tiny.out_px, p)
+            b = gpu_reslice(full, T, tiny.out_w, tiny.out_h, tiny.out_px, p)
+            assert np.array_equal(a[1], b[1]) and np.array_equal(a[0], b[0])
+            ref, rm = oracle.reslice(vol, T, tiny.out_w, tiny.out_h, tiny.out_px, ora_params(p))
+            assert_parity(a[0], a[1], ref, rm, tiny.out_w)
+        small.close()
+        full.close()
