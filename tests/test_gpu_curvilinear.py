@@ -13,6 +13,7 @@ value and a weighted mean within 2e-6 of the sample span (<= 255):
 |gpu - oracle| <= 1e-5 max(|oracle|, 1) + 5e-4."""
 import ctypes
 import math
+import types
 
 import numpy as np
 import pytest
@@ -259,3 +260,24 @@ def test_probe_argument_errors(tiny, linear_pair):
     with pytest.raises(dare.DareError) as ei:
         s.reslice(tiny.reslice_poses[0], o, m, tiny.out_px, p)
     assert ei.value.status == dare.DARE_E_INVALID
+
+
+@pytest.mark.parametrize("K", [12, 16])
+def test_curvilinear_every_record_fill(tiny, K):
+    """Curvilinear frames and virtual probe on records of every fill from 1 to
+    K (3 mm voxels over every 1st, 2nd, 3rd and 5th tiny frame at 0.1 x 0.12 mm
+    pixels): the per-sample loop runs to every stopping point, full records
+    included; masks exact, values within the bound above."""
+    g = synth.centred_grid((12, 10, 9), 3.0)
+    p = dare.params_default(probe_apex_mm=APEX)
+    seen = set()
+    for stride in (1, 2, 3, 5):
+        w = types.SimpleNamespace(grid=g, frames=tiny.frames[::stride], frame_poses=tiny.frame_poses[::stride],
+                                  frame_px=(0.1, 0.12))
+        s = curv_session(w, K=K)
+        vol = curv_oracle(w, K=K)
+        seen |= set(np.diff(vol.export()["offsets"]).tolist())
+        covered, _ = _run(tiny, s, vol, p, APEX, tiny.reslice_poses[[0, 3, 5]])
+        assert covered > 0
+        s.close()
+    assert set(range(1, K + 1)) <= seen
