@@ -33,6 +33,7 @@ sys.path.insert(0, ROOT)
 METRIC = "resliced Mpix/s and p50/p99 slice latency (512² from 256³) vs plain FP32 path"
 WORKLOAD = "dare_256cube_1600f_512px"
 DTYPE_NAMES = {"u8": 0, "f16": 1, "bf16": 2, "f32": 3}
+VALUE_BYTES = {"u8": 1, "f16": 2, "bf16": 2, "f32": 4}
 
 
 def log(*a):
@@ -57,6 +58,8 @@ def parse():
                     help="working: the 256^3 step (default); batched: 64 uneven volumes through a graph-replayed "
                          "plan; serving: 16 sessions under Poisson pose streams with live ingestion")
     ap.add_argument("--duration", type=float, default=10.0, help="seconds of the serving run")
+    ap.add_argument("--coalesce-us", type=int, default=300,
+                    help="serving: a batch that is not full waits until its oldest request is this old")
     ap.add_argument("--volumes", type=int, default=64, help="volumes of the batched workload")
     ap.add_argument("--quick", action="store_true", help="main timed loop only (for profiler runs)")
     ap.add_argument("--frames", type=int, default=0,
@@ -186,9 +189,10 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(kernel, n_slices):
-    """DRAM bytes per launch from the committed ncu summary, scaled per slice;
-    None when the kernel source changed since the counters were taken."""
+def profiled_counters(kernel, n_slices):
+    """Per-launch DRAM and L2 bytes from the committed ncu summary of the tiled
+    kernel, scaled per slice to n_slices; None when the kernel's sources changed
+    since the counters were taken."""
     path = os.path.join(ROOT, "profiles", "reslice_tiled_dram_traffic.txt")
     try:
         kv = dict(line.split("=", 1) for line in open(path).read().split("\n") if "=" in line and not line.startswith("#"))
@@ -196,10 +200,41 @@ def profiled_traffic(kernel, n_slices):
         return None
     if kv.get("kernel", "").strip() != kernel or kv.get("src_sha256_16", "").strip() != kernel_source_hash():
         return None
+    out = {}
+    for key, name in (("dram_bytes_per_slice", "dram"), ("l2_bytes_per_slice", "l2")):
+        try:
+            out[name] = float(kv[key]) * n_slices
+        except (KeyError, ValueError):
+            out[name] = None
+    return out
+
+
+def host_cores():
+    """Host threads this process may run on (its CPU affinity), as nproc reports."""
     try:
-        return float(kv["dram_bytes_per_slice"]) * n_slices
-    except (KeyError, ValueError):
-        return None
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def omp_threads(n):
+    """Thread count of the oracle's OpenMP loops (libgomp's own setting)."""
+    import ctypes
+    try:
+        ctypes.CDLL("libgomp.so.1").omp_set_num_threads(int(n))
+    except OSError:
+        pass
+
+
+def workload_config(args, n_frames, P, W, H, world):
+    """The working workload's config, identical in both arms."""
+    return {"workload": WORKLOAD, "grid": "256^3 @ 0.4 mm", "frames": int(n_frames),
+            "frame_px": "256x512 @ 0.2 mm", "poses": P, "out_px": f"{W}x{H} @ 0.2 mm",
+            "storage": args.dtype, "slots": args.slots, "path": args.path, "weights": "f32",
+            "distance_kernel": f"{args.kernel} R={args.radius}", "probe": args.probe,
+            "step": "reset + rebuild volume from all frames + reslice every pose",
+            "l2": "inputs larger than L2 (volume, frames and outputs each > 126 MB); no flush",
+            "parallelism": f"replicas x{world}"}
 
 
 def percentile(xs, q):
@@ -208,69 +243,116 @@ def percentile(xs, q):
 
 # ---------------------------------------------------------------- CPU oracle (baseline / reference arm)
 
-def cpu_baseline(w, n_poses, slots, n_res=8):
+def cpu_baseline(w, n_poses, slots, n_sub=16):
+    """The FP64 oracle on the host: the tiny workload in full (200 frames of
+    128 x 128 into 64^3, 16 planes of 128 x 128), and the working workload's
+    full reconstruction plus a fixed subset of n_sub of its planes (every
+    (n_poses / n_sub)-th), each reslice set single-threaded and on every core
+    this process may use.  The reconstruction loop is sequential in the
+    oracle.  value: the working step (rebuild + n_poses planes) at the
+    measured all-core reslice rate."""
     import oracle
+    import synth
+    cores = host_cores()
+    out = {"cores": cores, "kind": "oracle", "unit": "Mpix/s"}
+    tiny = synth.tiny_workload(0)
+    t = time.perf_counter()
+    tv = oracle.build(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, tiny.frames, tiny.frame_poses,
+                      tiny.frame_px, oracle.F32, 8)
+    tb = time.perf_counter() - t
+    tiny_res = {}
+    for threads in (1, cores):
+        omp_threads(threads)
+        t = time.perf_counter()
+        for T in tiny.reslice_poses:
+            oracle.reslice(tv, T, tiny.out_w, tiny.out_h, tiny.out_px)
+        tiny_res[threads] = (time.perf_counter() - t) / len(tiny.reslice_poses)
+    px_t = len(tiny.reslice_poses) * tiny.out_w * tiny.out_h
+    out["tiny_full"] = {"build_s": tb, "ms_per_slice_1_thread": tiny_res[1] * 1e3,
+                        "ms_per_slice_all_cores": tiny_res[cores] * 1e3,
+                        "mpix_s_all_cores": px_t / (tb + len(tiny.reslice_poses) * tiny_res[cores]) / 1e6,
+                        "mpix_s_1_thread": px_t / (tb + len(tiny.reslice_poses) * tiny_res[1]) / 1e6}
+    del tv
     t = time.perf_counter()
     vol = oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames, w.frame_poses, w.frame_px,
                        oracle.F32, slots)
     t_build = time.perf_counter() - t
-    t = time.perf_counter()
-    for T in w.reslice_poses[:n_res]:
-        oracle.reslice(vol, T, w.out_w, w.out_h, w.out_px)
-    t_res = (time.perf_counter() - t) / n_res
-    full = t_build + n_poses * t_res
+    sub = w.reslice_poses[::max(1, n_poses // n_sub)][:n_sub]
+    res = {}
+    for threads in (1, cores):
+        omp_threads(threads)
+        t = time.perf_counter()
+        for T in sub:
+            oracle.reslice(vol, T, w.out_w, w.out_h, w.out_px)
+        res[threads] = (time.perf_counter() - t) / len(sub)
+    omp_threads(cores)
     px = n_poses * w.out_w * w.out_h
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": px / full / 1e6, "unit": "Mpix/s", "cores": cores, "kind": "oracle",
-            "sample": (f"FP64 oracle on the host: full reconstruction of the {len(w.frames)} frames "
-                       f"(single-threaded, {t_build:.1f} s) + {n_res} of the {n_poses} 512x512 reslices "
-                       f"({t_res * 1e3:.0f} ms each, OpenMP over {cores} threads), extrapolated to one step"),
-            "ms_per_step": full * 1e3}, vol
+    full = t_build + n_poses * res[cores]
+    out["working"] = {"build_s_1_thread": t_build, "planes_timed": len(sub),
+                      "ms_per_slice_1_thread": res[1] * 1e3, "ms_per_slice_all_cores": res[cores] * 1e3,
+                      "mpix_s_reslice_only_all_cores": w.out_w * w.out_h / res[cores] / 1e6,
+                      "mpix_s_reslice_only_1_thread": w.out_w * w.out_h / res[1] / 1e6}
+    out["value"] = px / full / 1e6
+    out["ms_per_step"] = full * 1e3
+    out["sample"] = (f"FP64 oracle on the host ({cores} cores by CPU affinity): the tiny workload in full "
+                     f"(build {tb:.2f} s, {len(tiny.reslice_poses)} planes of 128x128) and the working workload's full "
+                     f"reconstruction of {len(w.frames)} frames (single-threaded, {t_build:.1f} s) + {len(sub)} of its "
+                     f"{n_poses} 512x512 planes (every {max(1, n_poses // n_sub)}th; {res[cores] * 1e3:.0f} ms each on "
+                     f"{cores} threads, {res[1] * 1e3:.0f} ms on 1); value = one working step at those rates")
+    return out
 
 
 def run_reference(args, dist):
+    """The reference arm: the FP64 oracle as it stands, on the host cores.  Each
+    step is 1/16 of the working step with the same frames-to-planes ratio: a
+    fresh reconstruction of 100 consecutive frames (1600 / 16) and the reslice
+    of 62 or 63 planes (1000 / 16) on the full volume, built once before timing.
+    value = planes resliced x 512^2 / step time."""
     if dist.rank != 0:
         return
     import oracle
     import synth
     w = synth.working_workload(1, n_poses=args.poses)
+    cores = host_cores()
+    omp_threads(cores)
     log("reference: building the full oracle volume (untimed)")
     vol = oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames, w.frame_poses, w.frame_px,
                        oracle.F32, args.slots)
-    n_res, sub = 4, 400
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    parts = 16
+    nf = len(w.frames) // parts
 
     def step(k):
+        j = k % parts
+        a = j * nf
+        planes = range(j * args.poses // parts, (j + 1) * args.poses // parts)
         t = time.perf_counter()
-        a = (k * sub) % len(w.frames)
-        oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames[a:a + sub], w.frame_poses[a:a + sub],
+        oracle.build(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, w.frames[a:a + nf], w.frame_poses[a:a + nf],
                      w.frame_px, oracle.F32, args.slots)
-        t_b = (time.perf_counter() - t) * len(w.frames) / sub
-        t = time.perf_counter()
-        for j in range(n_res):
-            oracle.reslice(vol, w.reslice_poses[(k * n_res + j) % args.poses], w.out_w, w.out_h, w.out_px)
-        t_r = (time.perf_counter() - t) / n_res
-        return t_b + args.poses * t_r
+        for i in planes:
+            oracle.reslice(vol, w.reslice_poses[i], w.out_w, w.out_h, w.out_px)
+        return time.perf_counter() - t, len(planes)
 
     for k in range(args.warmup):
         step(k)
-    times = [step(args.warmup + k) for k in range(args.steps)]
-    full = sum(times) / len(times)
-    px = args.poses * w.out_w * w.out_h
-    value = px / full / 1e6
-    sample = (f"each step: FP64 oracle reconstruction of {sub} of the {len(w.frames)} frames (x{len(w.frames)//sub}) "
-              f"+ {n_res} of the {args.poses} 512x512 reslices (x{args.poses // n_res}) on the full oracle volume, "
-              f"on {cores} host threads")
+    times, planes = [], 0
+    for k in range(args.steps):
+        dt, n = step(args.warmup + k)
+        times.append(dt)
+        planes += n
+    total = sum(times)
+    value = planes * w.out_w * w.out_h / total / 1e6
+    sample = (f"each step: the FP64 oracle's fresh reconstruction of {nf} consecutive frames of the {len(w.frames)} "
+              f"(single-threaded) + the reslice of {args.poses // parts} or {args.poses // parts + 1} of the "
+              f"{args.poses} 512x512 planes (OpenMP over {cores} threads) on the full oracle volume built before "
+              f"timing: 1/{parts} of a working step; successive steps take successive sixteenths")
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": full * 1e3, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "256^3 @ 0.4 mm", "frames": int(len(w.frames)),
-                       "frame_px": "256x512 @ 0.2 mm", "poses": args.poses, "out_px": f"{w.out_w}x{w.out_h} @ 0.2 mm",
-                       "storage": "f64 (oracle; f32-rounded stored values)", "slots": args.slots,
-                       "step": "reset + rebuild volume from all frames + reslice every pose",
-                       "parallelism": "host threads, rank 0 only"},
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": total / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, len(w.frames), args.poses, w.out_w, w.out_h, dist.world),
             "cpu_baseline": {"value": value, "unit": "Mpix/s", "cores": cores, "kind": "oracle", "sample": sample},
-            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+            "e2e": {"value": value, "unit": "Mpix/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "work_per_step": {"frames_built": nf, "planes_resliced": planes / args.steps,
+                              "fraction_of_working_step": 1.0 / parts}}
     print(json.dumps(line), flush=True)
 
 
@@ -321,6 +403,7 @@ def run_dare(args, dist):
     dist.barrier()
     torch.cuda.synchronize()
     dare.trace_read()
+    dare.trace_counters(reset=True)
     dare.trace_enable(True)
     clocks = ClockSampler(dev)
     clocks.start()
@@ -336,54 +419,170 @@ def run_dare(args, dist):
     clk = clocks.stop()
     dare.trace_enable(False)
     trace = dare.trace_read()
+    counters = dare.trace_counters(reset=True)
     dist.barrier()
     ms_total = dist.max(e0.elapsed_time(e1))
     ms_step = ms_total / args.steps
     px_step = P * W * H * dist.world
     value = px_step / (ms_step * 1e-3) / 1e6
 
-    # roofline of the dominant kernel
+    # roofline of the dominant kernel.  Algorithmic bytes per plane: every record of
+    # its footprint read once (the record's data, 2 B id + value per slot; the
+    # 16-byte stride's padding is layout, not the method's bytes), the image and
+    # mask written, the weight table read.
     top = max(trace.items(), key=lambda kv: kv[1][1])
     per_launch_ms = {k: v[1] / max(v[0], 1) for k, v in trace.items()}
     fp = s.footprint(w.reslice_poses, W, H, w.out_px)
-    rec_bytes = info.record_bytes
-    reslice_alg = float(fp.sum() * rec_bytes + P * (W * H * 4 + H * dare.mask_words(W) * 4) + P * info.n_frames * 4)
+    rec_stride = info.record_bytes
+    rec_data = args.slots * (2 + VALUE_BYTES[args.dtype])
+    out_bytes = P * (W * H * 4 + H * dare.mask_words(W) * 4)
+    reslice_alg = float(fp.sum() * rec_data + out_bytes + P * info.n_frames * 4)
     alg = {"reslice_tiled": reslice_alg, "reslice_plain": reslice_alg}
     if args.radius == 1 and args.kernel == "tent":  # the footprint counts the TENT R = 1 support
         alg["reslice_curv"] = reslice_alg
     peak, peak_kind = peaks()
     roof = None
     if top[0] in alg:
-        achieved = alg[top[0]] / (per_launch_ms[top[0]] * 1e-3) / 1e9
+        t_launch = per_launch_ms[top[0]] * 1e-3
+        achieved = alg[top[0]] / t_launch / 1e9
+        prof = profiled_counters(top[0], P) or {}
+        dram, l2b = prof.get("dram"), prof.get("l2")
         roof = {"kernel": top[0], "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": profiled_traffic(top[0], P),
+                "frac": achieved / peak, "peak_kind": peak_kind, "traffic": dram,
                 "algorithmic_bytes_per_launch": alg[top[0]], "launch_ms": per_launch_ms[top[0]],
-                "footprint_voxels_per_slice": float(fp.mean()), "record_bytes": rec_bytes}
+                "footprint_voxels_per_slice": float(fp.mean()), "record_bytes": rec_data,
+                "record_stride_bytes": rec_stride,
+                "note": "achieved/frac: algorithmic bytes (each plane's footprint read once, cold) over the "
+                        "launch time; dram_*: bytes DRAM actually moved (ncu, scaled per plane); l2: bytes "
+                        "through L2 (ncu lts__t_bytes) against the measured L2 read bandwidth"}
+        if dram:
+            roof["dram_achieved"] = dram / t_launch / 1e9
+            roof["dram_frac"] = roof["dram_achieved"] / peak
+        l2_peak = None
+        try:
+            l2_peak = dare.measure_l2_bandwidth(dev, 32 << 20, 200)
+        except dare.DareError as e:
+            log(f"L2 bandwidth measurement failed: {e}")
+        roof["l2"] = {"peak_gbs": l2_peak, "peak_kind": "measured: dare_measure_l2_bandwidth, 32 MiB x 200 passes",
+                      "bytes_per_launch": l2b}
+        if l2b and l2_peak:
+            roof["l2"]["achieved_gbs"] = l2b / t_launch / 1e9
+            roof["l2"]["frac"] = roof["l2"]["achieved_gbs"] / l2_peak
+        t_hbm = alg[top[0]] / (peak * 1e9)
+        t_l2 = l2b / (l2_peak * 1e9) if (l2b and l2_peak) else 0.0
+        roof["roofline_ms"] = max(t_hbm, t_l2) * 1e3
+        roof["binding_term"] = "l2" if t_l2 > t_hbm else "hbm"
+        roof["roofline_frac"] = max(t_hbm, t_l2) / t_launch
+    # the reconstruction as a whole (count + scan + place + finalize): its method's
+    # bytes are the frames read and every voxel's record data and npix row written
+    build_kernels = ("scatter_count", "exclusive_scan", "scatter_place", "finalize")
+    build_ms = sum(trace[k][1] for k in build_kernels if k in trace) / args.steps
+    n_vox = int(np.prod(w.grid.dims))
+    build_bytes = float(w.frames.size + n_vox * rec_data + n_vox * args.slots * 2)
+    build_roof = {"ms_per_step": build_ms, "bytes": build_bytes,
+                  "achieved": build_bytes / (build_ms * 1e-3) / 1e9 if build_ms > 0 else None, "peak": peak,
+                  "unit": "GB/s", "kernels": list(build_kernels),
+                  "note": "frames read + record data and npix of every voxel written (a reset volume is rewritten "
+                          "whole); intermediate pair and entry lists are not the method's bytes"}
+    if build_roof["achieved"]:
+        build_roof["frac"] = build_roof["achieved"] / peak
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "grid": "256^3 @ 0.4 mm", "frames": int(len(w.frames)),
-                       "frame_px": "256x512 @ 0.2 mm", "poses": P, "out_px": f"{W}x{H} @ 0.2 mm",
-                       "storage": args.dtype, "slots": args.slots, "path": args.path, "weights": "f32",
-                       "distance_kernel": f"{args.kernel} R={args.radius}", "probe": args.probe,
-                       "step": "reset + rebuild volume from all frames + reslice every pose",
-                       "l2": "inputs larger than L2 (volume, frames and outputs each > 126 MB); no flush",
-                       "parallelism": f"replicas x{dist.world}"},
+            "config": workload_config(args, len(w.frames), P, W, H, dist.world),
             "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
                        "samples": clk["samples"], "power_w_max": clk.get("power_w_max")},
             "gpu_launches": int(launches),
             "roofline": roof,
+            "build_roofline": build_roof,
+            "path_counters": counters,
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(trace.items())}}
 
     if not args.quick:
         extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, params, line, step, P, W, H)
+        # the other configurations of the workload family: storage precision against
+        # the FP64 oracle, the uneven batch through a graph-replayed plan, the serving loop
+        line["precision"] = precision_leg(dare, torch, w, frames_d, outs, masks, stream, P, W, H, args.slots)
+        bres, bclk = batched_leg(args, dist, 300, args.warmup)
+        bres["clocks"] = {"sm_mhz": bclk["sm_mhz"], "sm_max_mhz": bclk["sm_max_mhz"], "reasons": bclk["reasons"]}
+        line["batched"] = bres
+        sres, sclk = serving_leg(args, dist, args.duration, args.coalesce_us)
+        sres["clocks"] = {"sm_mhz": sclk["sm_mhz"], "sm_max_mhz": sclk["sm_max_mhz"], "reasons": sclk["reasons"]}
+        line["serving"] = sres
         if dist.rank == 0 and dist.world == 1 and not args.no_cpu:
             del s
             torch.cuda.synchronize()
-            cb, _ = cpu_baseline(w, P, args.slots)
+            cb = cpu_baseline(w, P, args.slots)
             line["cpu_baseline"] = cb
     if dist.rank == 0:
         print(json.dumps(line), flush=True)
+
+
+def workload_hash(w):
+    """Digest of the working workload's grid, frames, frame poses and planes (the
+    stored FP64 reference values of the precision sweep name the workload they
+    were computed on by this digest)."""
+    h = hashlib.sha256()
+    h.update(np.asarray(w.grid.dims, np.int64).tobytes())
+    h.update(np.float64(w.grid.spacing).tobytes())
+    h.update(np.ascontiguousarray(w.grid.vol_to_world, np.float64).tobytes())
+    h.update(np.ascontiguousarray(w.frames).tobytes())
+    h.update(np.ascontiguousarray(w.frame_poses, np.float64).tobytes())
+    h.update(np.asarray(w.frame_px, np.float64).tobytes())
+    h.update(np.ascontiguousarray(w.reslice_poses, np.float64).tobytes())
+    h.update(np.asarray([w.out_w, w.out_h], np.int64).tobytes())
+    h.update(np.asarray(w.out_px, np.float64).tobytes())
+    return h.hexdigest()[:32]
+
+
+# storage half-ulp for values in [128, 256) plus FP32 accumulation of a convex combination of values
+# <= 255 (a few ulp of 255); the FP16 weight table adds 2 eps / (1 - eps) (max I - min I), eps = 2^-11
+PRECISION_BOUND = {"u8": 0.5 + 4e-5, "f16": 0.0625 + 4e-5, "bf16": 0.5 + 4e-5, "f32": 2.0 ** -17 + 4e-5}
+
+
+def precision_leg(dare, torch, w, frames_d, outs, masks, stream, P, W, H, slots):
+    """Storage precision on the working workload: every plane resliced from
+    volumes stored as u8, f16, bf16 (FP16 weight tables) and f32 (FP32 weights),
+    compared at 64 covered pixels of each plane with the FP64 oracle's values on
+    the exact, unrounded means (tests/golden/precision_working.npz, written by
+    tests/golden/make_precision_reference.py from the oracle alone)."""
+    path = os.path.join(ROOT, "tests", "golden", "precision_working.npz")
+    try:
+        g = np.load(path)
+    except OSError:
+        return {"unavailable": "no stored reference values"}
+    if str(g["workload"]) != workload_hash(w) or g["uv"].shape[0] != P:
+        return {"unavailable": "the stored reference values were computed on another workload"}
+    uv, ref, cnt = g["uv"].astype(np.int64), g["value"], g["count"]
+    pidx = np.repeat(np.arange(P), uv.shape[1])
+    keep = (np.arange(uv.shape[1])[None, :] < cnt[:, None]).reshape(-1)
+    pi, u, v = pidx[keep], uv[:, :, 0].reshape(-1)[keep], uv[:, :, 1].reshape(-1)[keep]
+    refv = ref.reshape(-1)[keep]
+    ti = torch.from_numpy(pi).to(outs.device)
+    tv = torch.from_numpy(v).to(outs.device)
+    tu = torch.from_numpy(u).to(outs.device)
+    eps = 2.0 ** -11
+    res = {"planes": P, "pixels": int(keep.sum()), "pixels_per_plane": int(uv.shape[1]),
+           "reference": "FP64 oracle on exact per-(voxel, frame) means (tests/golden/precision_working.npz)"}
+    for name in ("u8", "f16", "bf16", "f32"):
+        wd = dare.DARE_WEIGHTS_F32 if name == "f32" else dare.DARE_WEIGHTS_F16
+        sp = dare.Session(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, dtype=DTYPE_NAMES[name], max_slots=slots,
+                          device=outs.device.index)
+        sp.build(frames_d, w.frame_poses, w.frame_px, stream)
+        rq = dare.make_requests([(sp, w.reslice_poses[i], outs[i], masks[i], w.out_px) for i in range(P)])
+        dare.reslice_batch(rq, dare.params_default(weight_dtype=wd), stream)
+        torch.cuda.synchronize()
+        got = outs[ti, tv, tu].double().cpu().numpy()
+        words = masks[ti, tv, tu // 32].cpu().numpy().view(np.uint32)
+        covered = ((words >> (u % 32).astype(np.uint32)) & 1).astype(bool)
+        e = np.abs(got - refv)
+        bound = PRECISION_BOUND[name] + (0.0 if name == "f32" else 2 * eps / (1 - eps) * 255.0)
+        res[name] = {"max_abs": float(e.max()), "psnr_db": float(10 * np.log10(255.0 ** 2 / max(np.mean(e ** 2), 1e-30))),
+                     "mean_abs": float(e.mean()), "bound": bound, "within_bound": bool(e.max() <= bound),
+                     "mask_agrees": bool(covered.all()), "weights": "f32" if name == "f32" else "f16",
+                     "overflow_voxels": int(sp.info().overflow_voxels)}
+        sp.close()
+    return res
 
 
 def _ssim_map(a, b):
@@ -662,9 +861,11 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
                                "one plane per call"}
 
 
-def run_batched(args, dist):
-    """Uneven batch: every plane of 64 volumes of different sizes resliced by one
-    autotuned plan replayed through a CUDA graph (volumes built untimed)."""
+def batched_leg(args, dist, steps, warmup):
+    """Uneven batch (64 volumes of dims U(96..384, 96..384, 96..256), 8-32
+    planes each of 128^2 .. 640^2): every plane through one autotuned plan
+    replayed as a CUDA graph (volumes built untimed).  Returns the measurements
+    and the clock record."""
     import torch
 
     import paper_2605_26325_b300 as dare
@@ -699,7 +900,7 @@ def run_batched(args, dist):
     tune_s = time.perf_counter() - t
 
     def timed(fn, reps):
-        for _ in range(max(args.warmup, 3)):
+        for _ in range(max(warmup, 3)):
             fn()
         torch.cuda.synchronize()
         dist.barrier()
@@ -714,40 +915,57 @@ def run_batched(args, dist):
     clocks = ClockSampler(dev)
     clocks.start()
     n0 = dare.launch_count()
-    reps = max(args.steps, 300)  # about a second of replays, long enough for the clock sampler
-    ms_plan = timed(lambda: plan.launch(stream), reps)
-    launches = (dare.launch_count() - n0) // (reps + max(args.warmup, 3))
+    ms_plan = timed(lambda: plan.launch(stream), steps)
+    launches = (dare.launch_count() - n0) // (steps + max(warmup, 3))
     clk = clocks.stop()
-    ms_batch = timed(lambda: dare.reslice_batch(reqs, dare.params_default(), stream), args.steps)
-    ms_plain = timed(lambda: dare.reslice_batch(reqs, dare.params_default(path=dare.DARE_PATH_PLAIN), stream), 3)
+    dare.trace_counters(reset=True)
+    ms_batch = timed(lambda: dare.reslice_batch(reqs, dare.params_default(), stream), 20)
+    counters = dare.trace_counters(reset=True)
+    ms_plain = timed(lambda: dare.reslice_batch(reqs, dare.params_default(path=dare.DARE_PATH_PLAIN), stream), 5)
     info = plan.info()
-    line = {"metric": "resliced Mpix/s, uneven batch of 64 volumes through one graph-replayed plan",
-            "value": px * dist.world / ms_plan / 1e3, "unit": "Mpix/s", "n_gpus": dist.world, "steps": reps,
-            "warmup": args.warmup, "ms_per_step": ms_plan, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"dare_batch_{len(vols)}vol_uneven", "volumes": len(vols), "planes": len(items),
-                       "out_mpix": px / 1e6, "storage": "f16", "slots": 8,
-                       "dims": "U(96..384, 96..384, 96..256) @ 0.4 mm", "sizes": "{128,256,512,640}^2",
-                       "overflow_voxels": int(overflow)},
-            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
-            "gpu_launches": int(launches),
-            "plan": {"groups": info["n_groups"], "choice": info["choice"], "tune_ms": info["tune_ms"],
-                     "tune_s": tune_s},
-            "paths_mpix_s": {"plan_graph": px / ms_plan / 1e3, "batch_call_tiled": px / ms_batch / 1e3,
-                             "batch_call_plain": px / ms_plain / 1e3}}
-    if dist.rank == 0:
-        print(json.dumps(line), flush=True)
+    pitch = [max(v.plane_px) / v.grid.spacing for v in vols]
+    res = {"mpix_s": px * dist.world / ms_plan / 1e3, "ms_per_replay": ms_plan, "replays": steps,
+           "volumes": len(vols), "planes": len(items), "out_mpix": px / 1e6, "overflow_voxels": int(overflow),
+           "pixel_pitch_vox": [min(pitch), max(pitch)],
+           "plan": {"groups": info["n_groups"], "choice": info["choice"],
+                    "tune_ms": {"plain": info["tune_ms"][0][0], "tiled_rows_le_64": info["tune_ms"][0][1],
+                                "tiled_rows_le_32": info["tune_ms"][0][2], "tiled_rows_le_16": info["tune_ms"][0][3]},
+                    "tune_s": tune_s, "kernel": "persistent tiled (work queue over every plane's tiles)"
+                    if info["choice"] and info["choice"][0] else "plain"},
+           "gpu_launches_per_replay": int(launches),
+           "paths_mpix_s": {"plan_graph": px / ms_plan / 1e3, "batch_call_tiled": px / ms_batch / 1e3,
+                            "batch_call_plain": px / ms_plain / 1e3},
+           "batch_call_path_counters": {k: v // (max(warmup, 3) + 20) for k, v in counters.items()}}
     plan.close()
     for s in sessions:
         s.close()
+    return res, clk
 
 
-def run_serving(args, dist):
+def run_batched(args, dist):
+    reps = max(args.steps, 300)  # about a second of replays, long enough for the clock sampler
+    res, clk = batched_leg(args, dist, reps, args.warmup)
+    line = {"metric": "resliced Mpix/s, uneven batch of 64 volumes through one graph-replayed plan",
+            "value": res["mpix_s"], "unit": "Mpix/s", "n_gpus": dist.world, "steps": reps,
+            "warmup": args.warmup, "ms_per_step": res["ms_per_replay"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"dare_batch_{res['volumes']}vol_uneven", "volumes": res["volumes"],
+                       "planes": res["planes"], "out_mpix": res["out_mpix"], "storage": "f16", "slots": 8,
+                       "dims": "U(96..384, 96..384, 96..256) @ 0.4 mm", "sizes": "{128,256,512,640}^2",
+                       "overflow_voxels": res["overflow_voxels"]},
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]},
+            "gpu_launches": res["gpu_launches_per_replay"], "plan": res["plan"], "paths_mpix_s": res["paths_mpix_s"],
+            "batch_call_path_counters": res["batch_call_path_counters"]}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def serving_leg(args, dist, duration, coalesce_us):
     """16 sessions (dims 128^3 .. 512x512x384, u8/f16) admitted under a 120 GB
     device-memory budget; each session's poses arrive as a Poisson stream at
     60-1000 Hz with a fixed output size in 256^2 .. 640^2; two sessions ingest
-    new sweep frames live (30 frames/s in batches of 3).  Reports throughput
-    and submit-to-done latency percentiles."""
+    new sweep frames live (30 frames/s in batches of 3).  Returns throughput,
+    submit-to-done latency percentiles, batching figures and the clocks."""
     import torch
 
     import paper_2605_26325_b300 as dare
@@ -784,12 +1002,12 @@ def run_serving(args, dist):
         del frames
         live = None
         if len(meta) < 2:  # the first two admitted sessions get a live sweep
-            lp = synth.sweep_poses(vseed, 99, int(30 * args.duration) + 6, H, 0.4, float(rng.uniform(-40, 40)),
+            lp = synth.sweep_poses(vseed, 99, int(30 * duration) + 6, H, 0.4, float(rng.uniform(-40, 40)),
                                    float(ext[1]))
             live = (torch.from_numpy(synth.render_frames(ph, lp, W, H, 0.4, 0.4)).to(device), lp)
         size = int(rng.choice([256, 320, 384, 448, 512, 576, 640]))
         rate = float(rng.uniform(60, 1000))
-        traj = synth.smooth_trajectory(vseed, int(args.duration * 1000) + 10, 1000.0, size, size, 0.3, 0.3, tilts,
+        traj = synth.smooth_trajectory(vseed, int(duration * 1000) + 10, 1000.0, size, size, 0.3, 0.3, tilts,
                                        pos_sigma_mm=0.15 * float(min(ext)))
         sessions.append(s)
         meta.append({"dims": dims, "dtype": "u8" if dtype == dare.DARE_U8 else "f16", "size": size, "rate": rate,
@@ -802,7 +1020,7 @@ def run_serving(args, dist):
         t = 0.0
         while True:
             t += float(rng.exponential(1.0 / m["rate"]))
-            if t >= args.duration:
+            if t >= duration:
                 break
             arrivals.append((t, i))
     arrivals.sort()
@@ -811,7 +1029,7 @@ def run_serving(args, dist):
               torch.empty((m["size"], dare.mask_words(m["size"])), dtype=torch.int32, device=device))
              for _ in range(ring)] for m in meta]
     free = [list(range(ring)) for _ in meta]
-    server = dare.Server(device=dev, lanes=3, max_batch=64)
+    server = dare.Server(device=dev, lanes=3, max_batch=64, coalesce_us=coalesce_us)
     tag_of = {}
     lat, ingest_lat, px_done, dropped = [], [], 0, 0
 
@@ -866,7 +1084,7 @@ def run_serving(args, dist):
             server.submit(sessions[i], traj[min(int(t_arr * 1000), len(traj) - 1)], out, mask, (0.3, 0.3), tag)
             tag_of[tag] = (i, b)
             tag += 1
-        while now >= next_ingest and next_ingest < args.duration:
+        while now >= next_ingest and next_ingest < duration:
             for j in range(min(2, len(meta))):
                 fr, lp = meta[j]["live"]
                 a = ingest_idx[j]
@@ -887,28 +1105,38 @@ def run_serving(args, dist):
     st = server.stats()
     server.close()
     lat = np.asarray(lat)
-    line = {"metric": "serving: resliced Mpix/s and submit-to-done latency over 16 sessions",
-            "value": px_done / wall / 1e6 * dist.world, "unit": "Mpix/s", "n_gpus": dist.world,
-            "steps": len(lat), "warmup": 0, "ms_per_step": float(np.mean(lat)) if lat.size else None,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "dare_serving_16sessions", "duration_s": args.duration,
-                       "sessions": len(sessions), "rejected_by_budget": rejected, "budget_gb": 120,
-                       "device_gb_in_use": dare.memory_in_use() / 1e9,
-                       "rates_hz": [round(m["rate"]) for m in meta], "sizes": [m["size"] for m in meta],
-                       "dims": [m["dims"] for m in meta], "storage": [m["dtype"] for m in meta],
-                       "live_ingest_sessions": min(2, len(meta)), "lanes": 3, "max_batch": 64},
-            "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "p99.9": percentile(lat, 99.9),
-                           "max": float(lat.max())},
-            "ingest_latency_ms": {"p50": percentile(ingest_lat, 50), "max": float(max(ingest_lat))}
-            if ingest_lat else None,
-            "requests": int(lat.size), "dropped_no_buffer": int(dropped),
-            "server": {k2: int(v) for k2, v in st.items()},
-            "mean_batch": st["completed"] / max(st["batches"], 1),
-            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"]}}
-    if dist.rank == 0:
-        print(json.dumps(line), flush=True)
+    res = {"mpix_s": px_done / wall / 1e6 * dist.world, "duration_s": duration, "wall_s": wall,
+           "requests": int(lat.size), "dropped_no_buffer": int(dropped),
+           "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "p99.9": percentile(lat, 99.9),
+                          "max": float(lat.max()), "mean": float(lat.mean())},
+           "ingest_latency_ms": {"p50": percentile(ingest_lat, 50), "max": float(max(ingest_lat))}
+           if ingest_lat else None,
+           "server": {k2: int(v) for k2, v in st.items()},
+           "mean_batch": (st["completed"] - st["ingests"]) / max(st["batches"], 1),
+           "coalesce_us": coalesce_us, "lanes": 3, "max_batch": 64,
+           "sessions": len(sessions), "rejected_by_budget": rejected, "budget_gb": 120,
+           "device_gb_in_use": dare.memory_in_use() / 1e9,
+           "rates_hz": [round(m["rate"]) for m in meta], "sizes": [m["size"] for m in meta],
+           "dims": [m["dims"] for m in meta], "storage": [m["dtype"] for m in meta],
+           "live_ingest_sessions": min(2, len(meta))}
     for s in sessions:
         s.close()
+    return res, clk
+
+
+def run_serving(args, dist):
+    res, clk = serving_leg(args, dist, args.duration, args.coalesce_us)
+    line = {"metric": "serving: resliced Mpix/s and submit-to-done latency over 16 sessions",
+            "value": res["mpix_s"], "unit": "Mpix/s", "n_gpus": dist.world, "steps": res["requests"], "warmup": 0,
+            "ms_per_step": res["latency_ms"]["mean"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "dare_serving_16sessions", "duration_s": args.duration,
+                       "coalesce_us": args.coalesce_us},
+            "serving": res,
+            "clocks": {"sm_mhz": clk["sm_mhz"], "sm_max_mhz": clk["sm_max_mhz"], "reasons": clk["reasons"],
+                       "samples": clk["samples"]}}
+    if dist.rank == 0:
+        print(json.dumps(line), flush=True)
 
 
 def main():

@@ -117,7 +117,7 @@
 extern "C" {
 #endif
 
-#define DARE_ABI_VERSION 2
+#define DARE_ABI_VERSION 3
 #define DARE_FIX_BITS 20
 #define DARE_EMPTY_FRAME 0xFFFFu
 #define DARE_MAX_FRAMES 65535
@@ -139,7 +139,14 @@ typedef enum { DARE_U8 = 0, DARE_F16 = 1, DARE_BF16 = 2, DARE_F32 = 3 } dare_dty
 typedef enum { DARE_TENT = 0, DARE_BOX = 1, DARE_EXP = 2 } dare_dist_kernel;
 typedef enum { DARE_NORMAL_BEAM = 0, DARE_NORMAL_ELEVATION = 1 } dare_normal_axis;
 typedef enum { DARE_WEIGHTS_F32 = 0, DARE_WEIGHTS_F16 = 1 } dare_weight_dtype;
-typedef enum { DARE_PATH_AUTO = 0, DARE_PATH_PLAIN = 1, DARE_PATH_TILED = 2 } dare_path;
+/* Kernel choice for linear probes: AUTO (tiled for single planes and batches;
+ * plans time the candidates), PLAIN (one thread per pixel, every record read
+ * per pixel), TILED (per-voxel reduction in shared-memory tiles whose height
+ * follows dare_params.tile_rows), TILED_FIXED (the tiled kernel with exactly
+ * tile_rows rows, 64 when 0, for every plane: tiles whose voxel-column box does
+ * not fit shared memory gather per pixel inside the kernel and are counted by
+ * dare_trace_counters_read; for measurements and tests). */
+typedef enum { DARE_PATH_AUTO = 0, DARE_PATH_PLAIN = 1, DARE_PATH_TILED = 2, DARE_PATH_TILED_FIXED = 3 } dare_path;
 typedef enum { DARE_PROBE_LINEAR = 0, DARE_PROBE_CURVILINEAR = 1 } dare_probe_kind;
 /* What a stored sample stands for (Sec. 2.1 stores "the intensity values at
  * that voxel"): MEAN, one sample per (voxel, frame), the mean of that frame's
@@ -230,7 +237,13 @@ typedef struct {
     int32_t path;           /* dare_path: kernel choice (linear probes) */
     dare_probe probe;       /* virtual probe of the planes (default linear) */
     int32_t sample_weight;  /* dare_sample_weight (default MEAN) */
-    int32_t reserved;
+    int32_t tile_rows;      /* tiled kernel (TENT, R = 1): rows of its 32-pixel-wide tiles.  0 (default):
+                               per plane, the largest of 64, 32, 16, 8 for which every tile's
+                               voxel-column box fits the kernel's shared memory (the box grows with
+                               the pixel-to-voxel pitch and the in-plane rotation); 8, 16, 32, 64: the
+                               same choice, capped at that value.  A plane for which no height fits
+                               goes to the per-pixel kernel (counted).  DARE_PATH_TILED_FIXED: exactly
+                               this many rows. */
 } dare_params;
 
 /* A virtual image plane: output size, pixel spacing and pose. */
@@ -428,13 +441,21 @@ dare_status dare_reslice_batch_host(const dare_reslice_req* reqs, int32_t n, con
  * Reslice plans: a fixed set of requests (sessions, output sizes and buffers)
  * prepared once and replayed many times, for a stream of batches whose poses
  * change (the batched workloads behind Sec. 3's timing and a serving loop).
- * dare_plan_create groups the requests by storage type and slot count,
- * chooses each group's kernel (with params->path == DARE_PATH_AUTO by timing
- * the plain kernel and the tiled kernel with 32- and 64-row tiles on these
- * very requests; results are cached per shape for the process), allocates
- * the plan's device workspace and pinned staging, and captures the
- * descriptor upload, the weight tables and the reslice launches into one CUDA
- * graph (synchronous; writes the outputs while tuning).
+ * dare_plan_create groups the requests by storage type and slot count and
+ * chooses each group's kernel: with params->path == DARE_PATH_AUTO by timing,
+ * on these very requests, the plain kernel and the persistent tiled kernel
+ * with tiles of at most 64, 32 and 16 rows (each plane then takes the largest
+ * height up to that cap whose tiles fit shared memory, recomputed for every
+ * new pose; a plane that no height fits is gathered per pixel inside the
+ * persistent kernel).  The persistent tiled kernel runs one CTA per resident
+ * slot of the device and takes tiles from a work queue over every plane of
+ * the group.  Choices are cached per shape (storage type, K, weights, output
+ * pixels and planes rounded to powers of two, median pixel-to-voxel pitch in
+ * eighths of a voxel, L2 mode, frame count, SM count) for the process, and in
+ * the file named by dare_tune_cache_file when one is set.  The plan then
+ * allocates its device workspace and pinned staging and captures the
+ * descriptor upload, the weight tables and the reslice launches into one
+ * CUDA graph (synchronous; writes the outputs while tuning).
  * dare_plan_set_poses replaces every request's image_to_world (n x 16 host
  * FP64, copied; waits for the previous launch's upload to finish).
  * dare_plan_launch replays the graph on `stream`; each result equals
@@ -449,10 +470,16 @@ typedef struct dare_plan_s* dare_plan;
 typedef struct {
     int32_t n_requests;
     int32_t n_groups;        /* launches per replay (one per storage type / K) */
-    int32_t choice[8];       /* per group: 0 = plain kernel, 32 or 64 = tiled, tile rows */
-    float tune_ms[8][3];     /* per group: measured plain, tiled-32, tiled-64 (0 if not timed) */
+    int32_t choice[8];       /* per group: 0 = plain kernel, else the tiled kernel's largest tile height */
+    float tune_ms[8][4];     /* per group: measured plain, tiled <= 64, <= 32, <= 16 rows (0 if not timed) */
     int64_t workspace_bytes;
 } dare_plan_info;
+
+/* File (JSON object of "shape key": choice) that plan tuning reads now and
+ * rewrites after each new choice; NULL or "" stops using a file.  A file that
+ * cannot be read is treated as empty; DARE_E_INVALID if a later write fails
+ * (reported by the dare_plan_create that tuned). */
+dare_status dare_tune_cache_file(const char* path);
 
 dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream,
                              dare_plan* out);
@@ -464,29 +491,40 @@ dare_status dare_plan_destroy(dare_plan p);
 /*
  * Serving loop: many sessions' reslice requests arriving over time (the
  * expert console's haptic pose stream, Sec. 1) plus live frame ingestion
- * (incremental integration, Sec. 4).  A dispatcher thread batches every
- * pending request whenever one of `lanes` streams is free (continuous
- * batching: requests arriving while others run join the next batch), so the
- * batches of different lanes overlap on the device.  A batch waits only for
- * the ingests of the sessions it reads; an ingest waits for the reslices in
- * flight, then runs dare_build_volume on the server's ingest stream.  Every
- * result equals dare_reslice of that request against the volume as of its
- * submission.  Completions are stamped by a host callback on the stream that
- * finishes them, on the clock of dare_clock_seconds.
+ * (incremental integration, Sec. 4).  A dispatcher thread batches the pending
+ * requests whenever one of `lanes` streams is free (continuous batching:
+ * requests arriving while others run join the next batch), so the batches of
+ * different lanes overlap on the device; requests of different sessions and
+ * output sizes go out in one dare_reslice_batch.  With coalesce_us > 0 a batch
+ * that is not full waits until its oldest request is coalesce_us old before it
+ * is issued, so that more requests join it (fewer launches for a bounded added
+ * latency); an ingest queued behind it, or a stop, issues it at once.  A batch
+ * waits only for the ingests of the sessions it reads; an ingest waits for
+ * the reslices in flight, then runs dare_build_volume on the server's ingest
+ * stream.  Every result equals dare_reslice of that request against the
+ * volume as of its submission.  Completions are stamped by a host callback on
+ * the stream that finishes them, on the clock of dare_clock_seconds.
  *
  * Sessions given to a server must be idle (dare_session_sync) and must not be
  * used outside the server until dare_server_drain returns.  frames_dev of an
  * ingest must stay valid until its completion is polled.  Submission is
- * thread-safe; the server allocates its per-lane workspace itself.
+ * thread-safe.  dare_server_create allocates every lane's device workspace
+ * and pinned staging for max_batch requests of sessions with up to
+ * max_frames frames (counted by the device-memory budget; DARE_E_ADMISSION or
+ * DARE_E_OOM when that fails), so the dispatcher never allocates; a request
+ * whose session allows more frames (its max_frames) is refused by submit
+ * with DARE_E_INVALID.
  */
 typedef struct dare_server_s* dare_server;
 
 typedef struct {
     int32_t device;
-    int32_t lanes;      /* batches in flight at once, 1..8 (default 2 when 0) */
-    int32_t max_batch;  /* requests per batch (default 64 when 0) */
-    int32_t reserved;
+    int32_t lanes;        /* batches in flight at once, 1..8 (default 2 when 0) */
+    int32_t max_batch;    /* requests per batch, 1..4096 (default 64 when 0) */
+    int32_t coalesce_us;  /* coalescing window of a batch, 0..1000000 microseconds (0: none) */
     dare_params params;
+    int32_t max_frames;   /* largest max_frames of the sessions served (0: DARE_MAX_FRAMES) */
+    int32_t reserved;
 } dare_server_config;
 
 typedef struct {
@@ -529,9 +567,13 @@ dare_status dare_server_destroy(dare_server sv);
  * loads the library keeps the array until the process exits.  All calls
  * share it: calls that overlap on the GPU (unordered streams) race and give
  * wrong images; order them or use dare_reslice.  The first call on a device
- * looks up the array's device address on that device (no allocation); make
- * that first call before any stream capture.  The session, its volume and
- * the outputs must already exist; this call allocates nothing itself.
+ * looks up the array's device address on that device.  That lookup asks for
+ * no memory itself, but under CUDA's lazy module loading (the default) it is
+ * what loads the part of the library that holds the array, and loading takes
+ * device memory; so make the first call during set-up, before the phase that
+ * must not allocate and before any stream capture.  The session, its volume
+ * and the outputs must already exist; after that first call, calls allocate
+ * nothing.
  * Linear probes only: curvilinear frames or a curvilinear params->probe give
  * DARE_E_UNSUPPORTED.
  */
@@ -604,6 +646,34 @@ typedef struct {
 dare_status dare_trace_enable(int32_t on);
 dare_status dare_trace_read(dare_kernel_time* out, int32_t capacity, int32_t* n_out);
 int64_t dare_launch_count(void);
+
+/*
+ * Path counters of the reslice kernels, counted whether tracing is on or not:
+ * tiled_planes, planes given to the tiled kernels; per_pixel_planes, planes
+ * that the automatic tile choice sent to the per-pixel kernels because no
+ * tile height fits them (or the plane is degenerate); fallback_tiles, tiles
+ * of the tiled kernels that gathered per pixel inside the kernel because
+ * their voxel-column box did not fit shared memory (0 unless
+ * DARE_PATH_TILED_FIXED forces a tile height).  fallback_tiles is read from
+ * the current device (synchronous: waits for that device's queued work).
+ * reset != 0 sets the counters back to 0 after reading.
+ */
+typedef struct {
+    int64_t tiled_planes;
+    int64_t per_pixel_planes;
+    int64_t fallback_tiles;
+} dare_trace_counters;
+
+dare_status dare_trace_counters_read(dare_trace_counters* out, int32_t reset);
+
+/*
+ * Measurement aid for the roofline of the reslice kernels, whose gathers L2
+ * serves for the most part: the device's L2-to-SM read bandwidth in GB/s, from
+ * 16-byte loads that bypass L1 over a buffer of `bytes` (1 MiB .. 1 GiB; keep
+ * it well under the L2 size) read `reps` times by 8 CTAs of 256 threads per
+ * SM after one warm-up pass.  Allocates and frees its own buffer; synchronous.
+ */
+dare_status dare_measure_l2_bandwidth(int32_t device, int64_t bytes, int32_t reps, double* read_gbs);
 
 /* Device-memory budget (bytes) shared by all sessions of this process;
  * 0 = unlimited.  Sessions that would exceed it fail with DARE_E_ADMISSION. */

@@ -25,7 +25,7 @@ DARE_U8, DARE_F16, DARE_BF16, DARE_F32 = 0, 1, 2, 3
 DARE_TENT, DARE_BOX, DARE_EXP = 0, 1, 2
 DARE_NORMAL_BEAM, DARE_NORMAL_ELEVATION = 0, 1
 DARE_WEIGHTS_F32, DARE_WEIGHTS_F16 = 0, 1
-DARE_PATH_AUTO, DARE_PATH_PLAIN, DARE_PATH_TILED = 0, 1, 2
+DARE_PATH_AUTO, DARE_PATH_PLAIN, DARE_PATH_TILED, DARE_PATH_TILED_FIXED = 0, 1, 2, 3
 DARE_PROBE_LINEAR, DARE_PROBE_CURVILINEAR = 0, 1
 DARE_SAMPLE_MEAN, DARE_SAMPLE_PIXELS = 0, 1
 DARE_SESSION_SCALAR = 1
@@ -79,7 +79,7 @@ class dare_params(ctypes.Structure):
                 ("k_dist", ctypes.c_double), ("unassigned", ctypes.c_float), ("radius_vox", ctypes.c_int32),
                 ("dist_kernel", ctypes.c_int32), ("normal_axis", ctypes.c_int32),
                 ("weight_dtype", ctypes.c_int32), ("path", ctypes.c_int32), ("probe", dare_probe),
-                ("sample_weight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("sample_weight", ctypes.c_int32), ("tile_rows", ctypes.c_int32)]
 
 
 class dare_plane(ctypes.Structure):
@@ -102,12 +102,13 @@ class dare_session_info(ctypes.Structure):
 
 class dare_plan_info(ctypes.Structure):
     _fields_ = [("n_requests", ctypes.c_int32), ("n_groups", ctypes.c_int32), ("choice", ctypes.c_int32 * 8),
-                ("tune_ms", (ctypes.c_float * 3) * 8), ("workspace_bytes", ctypes.c_int64)]
+                ("tune_ms", (ctypes.c_float * 4) * 8), ("workspace_bytes", ctypes.c_int64)]
 
 
 class dare_server_config(ctypes.Structure):
     _fields_ = [("device", ctypes.c_int32), ("lanes", ctypes.c_int32), ("max_batch", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("params", dare_params)]
+                ("coalesce_us", ctypes.c_int32), ("params", dare_params), ("max_frames", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class dare_completion(ctypes.Structure):
@@ -119,6 +120,11 @@ class dare_server_stats(ctypes.Structure):
     _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64), ("batches", ctypes.c_int64),
                 ("ingests", ctypes.c_int64), ("max_batch_seen", ctypes.c_int64), ("lanes", ctypes.c_int32),
                 ("reserved", ctypes.c_int32)]
+
+
+class dare_trace_counters(ctypes.Structure):
+    _fields_ = [("tiled_planes", ctypes.c_int64), ("per_pixel_planes", ctypes.c_int64),
+                ("fallback_tiles", ctypes.c_int64)]
 
 
 class dare_kernel_time(ctypes.Structure):
@@ -171,6 +177,10 @@ _SIGNATURES = {
     "dare_trace_enable": ([ctypes.c_int32], ctypes.c_int),
     "dare_trace_read": ([_P(dare_kernel_time), ctypes.c_int32, _P(ctypes.c_int32)], ctypes.c_int),
     "dare_launch_count": ([], ctypes.c_int64),
+    "dare_trace_counters_read": ([_P(dare_trace_counters), ctypes.c_int32], ctypes.c_int),
+    "dare_tune_cache_file": ([ctypes.c_char_p], ctypes.c_int),
+    "dare_measure_l2_bandwidth": ([ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P(ctypes.c_double)],
+                                  ctypes.c_int),
     "dare_clock_seconds": ([], ctypes.c_double),
     "dare_server_create": ([_P(dare_server_config), _P(_vp)], ctypes.c_int),
     "dare_server_submit": ([_vp, _P(dare_reslice_req), ctypes.c_uint64], ctypes.c_int),
@@ -341,6 +351,26 @@ def trace_read():
 
 def launch_count():
     return int(lib().dare_launch_count())
+
+
+def trace_counters(reset=False):
+    """{tiled_planes, per_pixel_planes, fallback_tiles} (dare_trace_counters_read)."""
+    c = dare_trace_counters()
+    check(lib().dare_trace_counters_read(ctypes.byref(c), 1 if reset else 0), "dare_trace_counters_read")
+    return {k: int(getattr(c, k)) for k, _ in c._fields_}
+
+
+def measure_l2_bandwidth(device=0, nbytes=32 << 20, reps=200):
+    """L2-to-SM read bandwidth of the device in GB/s (dare_measure_l2_bandwidth)."""
+    g = ctypes.c_double()
+    check(lib().dare_measure_l2_bandwidth(int(device), int(nbytes), int(reps), ctypes.byref(g)),
+          "dare_measure_l2_bandwidth")
+    return float(g.value)
+
+
+def tune_cache_file(path):
+    """Plan tuning choices read from and written to this JSON file (None: no file)."""
+    check(lib().dare_tune_cache_file(None if path is None else os.fsencode(path)), "dare_tune_cache_file")
 
 
 def set_memory_budget(nbytes):
@@ -626,9 +656,10 @@ class Plan:
 class Server:
     """Continuous-batching serving loop (dare_server_*)."""
 
-    def __init__(self, device=0, lanes=2, max_batch=64, params=None):
+    def __init__(self, device=0, lanes=2, max_batch=64, params=None, coalesce_us=0, max_frames=0):
         c = dare_server_config()
         c.device, c.lanes, c.max_batch = int(device), int(lanes), int(max_batch)
+        c.coalesce_us, c.max_frames = int(coalesce_us), int(max_frames)
         c.params = params if params is not None else params_default()
         self._h = ctypes.c_void_p()
         check(lib().dare_server_create(ctypes.byref(c), ctypes.byref(self._h)), "dare_server_create")

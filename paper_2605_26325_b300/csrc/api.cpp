@@ -182,6 +182,7 @@ size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 // ---------------------------------------------------------------- tracing
 
 std::atomic<int64_t> g_launches{0};
+std::atomic<int64_t> g_tiled_planes{0}, g_per_pixel_planes{0};
 std::atomic<bool> g_trace_on{false};
 std::mutex g_trace_mu;
 struct TraceRec {
@@ -551,7 +552,9 @@ dare_status check_params(const dare_params* p) {
     if (p->dist_kernel < 0 || p->dist_kernel > 2) return fail(DARE_E_INVALID, "unknown distance kernel");
     if (p->normal_axis < 0 || p->normal_axis > 1) return fail(DARE_E_INVALID, "unknown normal axis");
     if (p->weight_dtype < 0 || p->weight_dtype > 1) return fail(DARE_E_INVALID, "unknown weight dtype");
-    if (p->path < 0 || p->path > 2) return fail(DARE_E_INVALID, "unknown path");
+    if (p->path < 0 || p->path > 3) return fail(DARE_E_INVALID, "unknown path");
+    if (p->tile_rows != 0 && p->tile_rows != 8 && p->tile_rows != 16 && p->tile_rows != 32 && p->tile_rows != 64)
+        return fail(DARE_E_INVALID, "tile_rows must be 0, 8, 16, 32 or 64");
     if (p->radius_vox > 16) return fail(DARE_E_UNSUPPORTED, "radius_vox above 16 is not implemented");
     if (p->dist_kernel == DARE_EXP && !(p->k_dist >= 0)) return fail(DARE_E_INVALID, "k_dist must be >= 0");
     if (p->probe.kind != DARE_PROBE_LINEAR && p->probe.kind != DARE_PROBE_CURVILINEAR)
@@ -691,11 +694,38 @@ void general_caps(ResliceJob* jobs, int n, int* col_cap, int* slot_cap) {
     *slot_cap = static_cast<int>(slots_max);
 }
 
-int tiles_of(const dare_plane* pl, int tile_h = kTileH) {
+int tiles_of(const dare_plane* pl, int tile_h) {
     return ((pl->width + kTileW - 1) / kTileW) * ((pl->height + tile_h - 1) / tile_h);
 }
 
 bool use_tiled(const dare_params* p) { return p->path != DARE_PATH_PLAIN; }
+
+// Rows of the tiled kernel's tiles for a plane (TENT, R = 1).  A tile of 32 x th
+// pixels has corner coordinates that differ by at most D = |a| 31 + |b| (th - 1)
+// (fixed point) along each in-plane voxel axis, so its floors differ by at most
+// floor(D / 2^20) + 1 and the kernel's column box (floors + 2) is at most
+// floor(D / 2^20) + 3 wide: the largest th <= cap whose bound fits the kernel's
+// columns and (A, B) slots makes every tile fit.  0: none fits (per-pixel kernel).
+int tile_rows_fit(const ResliceJob& j, int cap) {
+    if (j.direct) return 0;
+    const int e1 = j.d == 0 ? 1 : 0, e2 = j.d == 2 ? 1 : 2;
+    for (int th = kTileH; th >= 8; th /= 2) {
+        if (th > cap) continue;
+        const int64_t D1 = std::llabs(j.a[e1]) * (kTileW - 1) + std::llabs(j.b[e1]) * (th - 1);
+        const int64_t D2 = std::llabs(j.a[e2]) * (kTileW - 1) + std::llabs(j.b[e2]) * (th - 1);
+        const int64_t n1 = (D1 >> kFixBits) + 3, n2 = (D2 >> kFixBits) + 3;
+        if (n1 <= kTiledColMax && n2 <= kTiledColMax && n1 * n2 <= kTiledColMax && n1 * n2 * j.levels <= kTiledSlotMax)
+            return th;
+    }
+    return 0;
+}
+
+// Tile rows of a job on the tiled path of params (TENT, R = 1): the fit above
+// (capped by params->tile_rows), or exactly tile_rows with DARE_PATH_TILED_FIXED.
+int tile_rows_for(const ResliceJob& j, const dare_params* p) {
+    if (p->path == DARE_PATH_TILED_FIXED) return p->tile_rows ? p->tile_rows : kTileH;
+    return tile_rows_fit(j, p->tile_rows ? p->tile_rows : kTileH);
+}
 
 // One plane's reslice launch on the path params choose.
 cudaError_t launch_one(ResliceJob& job, const dare_plane* plane, const dare_params* params, int K, int dtype,
@@ -705,16 +735,26 @@ cudaError_t launch_one(ResliceJob& job, const dare_plane* plane, const dare_para
         if (use_tiled(params)) {
             int col_cap = 0, slot_cap = 0;
             general_caps(&job, 1, &col_cap, &slot_cap);
-            KernelScope ks("reslice_tiled_r", st, 1);
-            return launch_reslice_tiled_r(nullptr, &job, 1, 0, tiles_of(plane, kTileHGeneral), 0, col_cap, slot_cap, K,
-                                          dtype, half_w, st);
+            if (!job.direct) {
+                g_tiled_planes += 1;
+                KernelScope ks("reslice_tiled_r", st, 1);
+                return launch_reslice_tiled_r(nullptr, &job, 1, 0, tiles_of(plane, kTileHGeneral), 0, col_cap,
+                                              slot_cap, K, dtype, half_w, st);
+            }
+            g_per_pixel_planes += 1;
         }
         KernelScope ks("reslice_plain_r", st, 1);
         return launch_reslice_plain_r(nullptr, &job, 1, plane->width, plane->height, K, dtype, half_w, st);
     }
     if (use_tiled(params)) {
-        KernelScope ks("reslice_tiled", st, 1);
-        return launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane), 0, kTileH, K, dtype, half_w, st);
+        const int th = tile_rows_for(job, params);
+        if (th > 0) {
+            job.tile_h = th;
+            g_tiled_planes += 1;
+            KernelScope ks("reslice_tiled", st, 1);
+            return launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane, th), 0, K, dtype, half_w, st);
+        }
+        g_per_pixel_planes += 1;
     }
     KernelScope ks("reslice_plain", st, 1);
     return launch_reslice_plain(nullptr, &job, 1, plane->width, plane->height, K, dtype, half_w, st);
@@ -961,6 +1001,16 @@ void batch_sizes(const dare_reslice_req* reqs, int32_t n, const dare_params* par
     *desc_bytes = *ws_need - o_tj;
 }
 
+// A bound on batch_sizes for any batch of n requests whose sessions hold at most
+// max_frames frames each.
+void batch_sizes_bound(int32_t n, int32_t max_frames, size_t* ws_need, size_t* desc_bytes) {
+    const size_t o_tj = size_t(n) * align_up(size_t(std::max(max_frames, 1)) * 4, 256);
+    const size_t o_rj = align_up(o_tj + size_t(n) * sizeof(TableJob), 256);
+    const size_t o_cj = align_up(o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    *ws_need = align_up(o_cj + size_t(n) * sizeof(CurvJob), 256);
+    *desc_bytes = *ws_need - o_tj;
+}
+
 // Queue weight tables and reslice launches for a checked batch on `st`, using
 // device workspace `ws` and pinned staging `pin` (sized by batch_sizes).  No
 // ordering against the sessions' other work: the caller provides it.
@@ -982,41 +1032,69 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
     auto* tjs = reinterpret_cast<TableJob*>(pin);
     auto* rjs = reinterpret_cast<ResliceJob*>(pin + (o_rj - o_tj));
     auto* cjs = reinterpret_cast<CurvJob*>(pin + (o_cj - o_tj));
+    const bool general = general_support(params);
+    const bool tiled = use_tiled(params);
+    // every request's job and route: 0 tiled kernel, 1 per-pixel kernel (the plain
+    // path, or a plane no tile fits), 2 curvilinear kernel
+    std::vector<ResliceJob> jobs(n);
+    std::vector<char> route(n);
+    for (int32_t i = 0; i < n; ++i) {
+        const dare_reslice_req& r = reqs[i];
+        jobs[i] = make_job(r.session, &r.plane, ws + t_off[i], r.out, r.mask, params->unassigned, params);
+        if (curv_path(r.session, params)) {
+            route[i] = 2;
+        } else if (!tiled) {
+            route[i] = 1;
+        } else if (!general) {
+            jobs[i].tile_h = tile_rows_for(jobs[i], params);
+            route[i] = jobs[i].tile_h > 0 ? 0 : 1;
+        }
+    }
+    int col_cap = 0, slot_cap = 0;
+    if (general && tiled) {
+        std::vector<int32_t> idx;
+        std::vector<ResliceJob> gj;
+        for (int32_t i = 0; i < n; ++i)
+            if (route[i] != 2) {
+                idx.push_back(i);
+                gj.push_back(jobs[i]);
+            }
+        general_caps(gj.data(), static_cast<int>(gj.size()), &col_cap, &slot_cap);
+        for (size_t k = 0; k < idx.size(); ++k) {
+            jobs[idx[k]] = gj[k];
+            route[idx[k]] = gj[k].direct ? 1 : 0;
+        }
+    }
     // order jobs by (kernel family, K, dtype) so each launch covers one group
     std::vector<int32_t> order(n);
-    std::vector<char> curv(n);
-    for (int32_t i = 0; i < n; ++i) {
-        order[i] = i;
-        curv[i] = curv_path(reqs[i].session, params) ? 1 : 0;
-    }
+    for (int32_t i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
         const auto* sa = reqs[a].session;
         const auto* sb = reqs[b].session;
-        if (curv[a] != curv[b]) return curv[a] < curv[b];
-        return sa->K != sb->K ? sa->K < sb->K : sa->dtype < sb->dtype;
+        if ((route[a] == 2) != (route[b] == 2)) return route[a] < route[b];
+        if (sa->K != sb->K) return sa->K < sb->K;
+        if (sa->dtype != sb->dtype) return sa->dtype < sb->dtype;
+        return route[a] < route[b];
     });
     max_frames = 0;
     for (int32_t i = 0; i < n; ++i)
-        if (!curv[i]) max_frames = std::max(max_frames, reqs[i].session->n_frames);
-    const bool general = general_support(params);
-    const int th = general ? kTileHGeneral : kTileH;
+        if (route[i] != 2) max_frames = std::max(max_frames, reqs[i].session->n_frames);
+    const int th_general = kTileHGeneral;
     int total_tiles = 0;
     for (int32_t k = 0; k < n; ++k) {
-        const dare_reslice_req& r = reqs[order[k]];
-        void* wtab = ws + t_off[order[k]];
+        const int32_t i = order[k];
+        const dare_reslice_req& r = reqs[i];
         TableJob tj{};
         plane_vectors(r.session, &r.plane, params->normal_axis, &tj);
         tj.frames = r.session->frames_dev;
-        tj.wtab = wtab;
-        tj.n_frames = curv[order[k]] ? 0 : r.session->n_frames;  // the curvilinear kernel needs no table
+        tj.wtab = ws + t_off[i];
+        tj.n_frames = route[i] == 2 ? 0 : r.session->n_frames;  // the curvilinear kernel needs no table
         tjs[k] = tj;
-        rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, params->unassigned, params);
-        if (curv[order[k]]) cjs[k] = make_curv_job(r.session, &r.plane, r.out, r.mask, params);
+        rjs[k] = jobs[i];
+        if (route[i] == 2) cjs[k] = make_curv_job(r.session, &r.plane, r.out, r.mask, params);
         rjs[k].tile_base = total_tiles;
-        if (!curv[order[k]]) total_tiles += tiles_of(&r.plane, th);
+        if (route[i] == 0) total_tiles += tiles_of(&r.plane, general ? th_general : rjs[k].tile_h);
     }
-    int col_cap = 0, slot_cap = 0;
-    if (general) general_caps(rjs, n, &col_cap, &slot_cap);
     CUDA_TRY(cudaMemcpyAsync(ws + o_tj, pin, desc_bytes, cudaMemcpyHostToDevice, st));
     const auto* tj_dev = reinterpret_cast<const TableJob*>(ws + o_tj);
     const auto* rj_dev = reinterpret_cast<const ResliceJob*>(ws + o_rj);
@@ -1027,26 +1105,29 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
     }
     const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
     for (int32_t k0 = 0; k0 < n;) {
-        const auto* sg = reqs[order[k0]].session;
+        const int32_t i0 = order[k0];
+        const auto* sg = reqs[i0].session;
+        const char rg = route[i0];
         int32_t k1 = k0;
         int max_w = 0, max_h = 0;
-        const char cg = curv[order[k0]];
-        while (k1 < n && curv[order[k1]] == cg && reqs[order[k1]].session->K == sg->K &&
+        while (k1 < n && route[order[k1]] == rg && reqs[order[k1]].session->K == sg->K &&
                reqs[order[k1]].session->dtype == sg->dtype) {
             max_w = std::max(max_w, reqs[order[k1]].plane.width);
             max_h = std::max(max_h, reqs[order[k1]].plane.height);
             ++k1;
         }
-        if (cg) {
+        if (rg == 2) {
             KernelScope ks("reslice_curv", st, 1);
             CUDA_TRY(launch_reslice_curv(cj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, st));
-        } else if (use_tiled(params)) {
+        } else if (rg == 0) {
+            g_tiled_planes += k1 - k0;
             const int base = rjs[k0].tile_base;
-            const int end = (k1 < n) ? rjs[k1].tile_base : total_tiles;
+            const int end = (k1 < n && route[order[k1]] == 0) ? rjs[k1].tile_base : total_tiles;
             // same tile count for every job of the group: 2-D grid without a job search
-            const int per = tiles_of(&reqs[order[k0]].plane, th);
+            const int per = tiles_of(&reqs[i0].plane, general ? th_general : rjs[k0].tile_h);
             bool uniform = k1 - k0 <= 65535;
-            for (int32_t k = k0; uniform && k < k1; ++k) uniform = tiles_of(&reqs[order[k]].plane, th) == per;
+            for (int32_t k = k0; uniform && k < k1; ++k)
+                uniform = tiles_of(&reqs[order[k]].plane, general ? th_general : rjs[k].tile_h) == per;
             if (general) {
                 KernelScope ks("reslice_tiled_r", st, 1);
                 CUDA_TRY(launch_reslice_tiled_r(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base,
@@ -1054,14 +1135,19 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
             } else {
                 KernelScope ks("reslice_tiled", st, 1);
                 CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base,
-                                              uniform ? 1 : 0, kTileH, sg->K, sg->dtype, half_w, st));
+                                              uniform ? 1 : 0, sg->K, sg->dtype, half_w, st));
             }
-        } else if (general) {
-            KernelScope ks("reslice_plain_r", st, 1);
-            CUDA_TRY(launch_reslice_plain_r(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
         } else {
-            KernelScope ks("reslice_plain", st, 1);
-            CUDA_TRY(launch_reslice_plain(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w, st));
+            if (tiled) g_per_pixel_planes += k1 - k0;
+            if (general) {
+                KernelScope ks("reslice_plain_r", st, 1);
+                CUDA_TRY(launch_reslice_plain_r(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w,
+                                                st));
+            } else {
+                KernelScope ks("reslice_plain", st, 1);
+                CUDA_TRY(launch_reslice_plain(rj_dev + k0, nullptr, k1 - k0, max_w, max_h, sg->K, sg->dtype, half_w,
+                                              st));
+            }
         }
         k0 = k1;
     }
@@ -2117,6 +2203,63 @@ dare_status dare_trace_read(dare_kernel_time* out, int32_t capacity, int32_t* n_
 
 int64_t dare_launch_count(void) { return g_launches.load(); }
 
+dare_status dare_measure_l2_bandwidth(int32_t device, int64_t bytes, int32_t reps, double* read_gbs) {
+    if (!read_gbs || bytes < (int64_t(1) << 20) || bytes > (int64_t(1) << 30) || reps < 1 || reps > 100000)
+        return fail(DARE_E_INVALID, "bytes must be 1 MiB .. 1 GiB and reps 1 .. 100000");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(DARE_E_INVALID, "device %d not available", device);
+    }
+    DeviceGuard dg(device);
+    if (!dg.ok) return fail(DARE_E_CUDA, "cannot select device %d", device);
+    int sms = 0;
+    CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+    const int64_t n = bytes / 16 * 16;
+    void* buf = nullptr;
+    void* sink = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaMalloc(&buf, size_t(n));
+    if (e == cudaSuccess) e = cudaMalloc(&sink, 16);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = cudaMemsetAsync(buf, 0x5A, size_t(n), st);
+    const int blocks = sms * 8;
+    if (e == cudaSuccess) e = launch_l2_read(buf, n, 2, sink, blocks, st);  // warm-up: the buffer into L2
+    if (e == cudaSuccess) e = cudaEventRecord(a, st);
+    if (e == cudaSuccess) e = launch_l2_read(buf, n, reps, sink, blocks, st);
+    if (e == cudaSuccess) e = cudaEventRecord(b, st);
+    if (e == cudaSuccess) e = cudaEventSynchronize(b);
+    float ms = 0.0f;
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, a, b);
+    if (e != cudaSuccess) cudaGetLastError();
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    if (st) cudaStreamDestroy(st);
+    if (buf) cudaFree(buf);
+    if (sink) cudaFree(sink);
+    if (e != cudaSuccess) return fail(DARE_E_CUDA, "L2 bandwidth measurement: %s", cudaGetErrorString(e));
+    g_launches += 2;
+    *read_gbs = double(n) * reps / (double(ms) * 1e-3) / 1e9;
+    return DARE_OK;
+}
+
+dare_status dare_trace_counters_read(dare_trace_counters* out, int32_t reset) {
+    if (!out) return fail(DARE_E_INVALID, "out is NULL");
+    unsigned long long ft = 0, fg = 0;
+    if (read_fallback_tiles_tiled(&ft, reset != 0) != cudaSuccess ||
+        read_fallback_tiles_general(&fg, reset != 0) != cudaSuccess) {
+        cudaError_t e = cudaGetLastError();
+        return fail(DARE_E_CUDA, "reading the fallback counters: %s", cudaGetErrorString(e));
+    }
+    out->tiled_planes = reset ? g_tiled_planes.exchange(0) : g_tiled_planes.load();
+    out->per_pixel_planes = reset ? g_per_pixel_planes.exchange(0) : g_per_pixel_planes.load();
+    out->fallback_tiles = static_cast<int64_t>(ft + fg);
+    return DARE_OK;
+}
+
 // ---------------------------------------------------------------- checkpoint
 
 namespace {
@@ -2303,6 +2446,7 @@ dare_status reserve_bytes(int64_t bytes) { return admit(bytes); }
 void release_bytes(int64_t bytes) { g_in_use -= bytes; }
 
 int session_device(dare_session s) { return s ? s->cfg.device : -1; }
+int session_max_frames(dare_session s) { return s ? s->cfg.max_frames : 0; }
 
 // dare_reslice with a caller-provided weight table of wtab_bytes bytes on the
 // session's device; queues the same kernels and allocates nothing.
@@ -2338,6 +2482,7 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
     }
     ResliceJob job = make_job(s, plane, wtab, out_dev, mask_dev, params->unassigned, params);
     const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
+    L2Window l2((s->cfg.flags & DARE_SESSION_L2_PERSIST) ? s->rec : nullptr, size_t(s->n_vox) * s->rec_bytes, st);
     CUDA_TRY(launch_one(job, plane, params, s->K, s->dtype, half_w, st));
     return session_end(s, st);
 }
@@ -2347,13 +2492,15 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
 // ---------------------------------------------------------------- plans (graph-replayed batches, autotuned)
 
 struct dare_plan_s {
+    static constexpr int kCands = 4;  // plain, tiled with at most 64, 32, 16 rows
     struct Group {
         int32_t k0 = 0, k1 = 0;   // range in `order`
         int K = 0, dtype = 0;
-        int choice = kTileH;      // 0 = plain, else tiled tile rows
+        int choice = kTileH;      // 0 = plain, else the largest tile height of the tiled kernel
         int max_w = 0, max_h = 0;
-        float tune_ms[3] = {0, 0, 0};
+        float tune_ms[kCands] = {0, 0, 0, 0};
         int col_cap = 0, slot_cap = 0;  // general distance kernels: shared memory of the tiled kernel
+        std::string key;          // tuning-cache key
     };
     std::vector<dare_reslice_req> reqs;
     dare_params params{};
@@ -2364,7 +2511,7 @@ struct dare_plan_s {
     std::vector<Group> groups;
     int device = 0;
     int max_frames = 0;
-    size_t o_tj = 0, o_rj = 0, desc_bytes = 0;
+    size_t o_tj = 0, o_rj = 0, o_q = 0, desc_bytes = 0;
     void* ws = nullptr;
     size_t ws_bytes = 0;
     void* pinned = nullptr;
@@ -2376,19 +2523,71 @@ struct dare_plan_s {
 
 namespace {
 
+// ---- tuning cache: choices per shape, in the process and optionally in a JSON file
 std::mutex g_tune_mu;
 std::map<std::string, int> g_tune_cache;
+std::string g_tune_file;
 
-int plan_tiles(const dare_plane* pl, int choice) { return choice == 0 ? 0 : tiles_of(pl, choice); }
+// The file is one flat JSON object {"key": choice, ...} written by this library.
+void tune_file_load(const std::string& path) {
+    FILE* f = std::fopen(path.c_str(), "rb");
+    if (!f) return;
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+    std::fclose(f);
+    size_t i = 0;
+    for (;;) {
+        const size_t k0 = text.find('"', i);
+        if (k0 == std::string::npos) break;
+        const size_t k1 = text.find('"', k0 + 1);
+        if (k1 == std::string::npos) break;
+        const size_t colon = text.find(':', k1);
+        if (colon == std::string::npos) break;
+        char* end = nullptr;
+        const long v = std::strtol(text.c_str() + colon + 1, &end, 10);
+        if (end == text.c_str() + colon + 1) break;
+        if (v == 0 || v == 16 || v == 32 || v == 64) g_tune_cache[text.substr(k0 + 1, k1 - k0 - 1)] = static_cast<int>(v);
+        i = static_cast<size_t>(end - text.c_str());
+    }
+}
+
+bool tune_file_save() {
+    if (g_tune_file.empty()) return true;
+    const std::string tmp = g_tune_file + ".tmp";
+    FILE* f = std::fopen(tmp.c_str(), "wb");
+    if (!f) return false;
+    std::fputs("{\n", f);
+    size_t k = 0;
+    for (auto& kv : g_tune_cache) std::fprintf(f, "  \"%s\": %d%s\n", kv.first.c_str(), kv.second, ++k < g_tune_cache.size() ? "," : "");
+    std::fputs("}\n", f);
+    const bool ok = std::fclose(f) == 0;
+    return ok && std::rename(tmp.c_str(), g_tune_file.c_str()) == 0;
+}
+
+// Pixel-to-voxel pitch of a plane: the longer of its two in-plane pixel steps, in voxels.
+double plane_pitch(const dare_reslice_req& r) {
+    const double h = r.session->cfg.grid.spacing_mm;
+    return std::max(r.plane.px_mm[0], r.plane.px_mm[1]) / h;
+}
+
+// Tiles of a job in a plan group: its own tile height (tiled), none (plain).
+int plan_tiles(const dare_plane* pl, const ResliceJob& j, int choice) {
+    return choice == 0 ? 0 : tiles_of(pl, j.tile_h);
+}
 
 // Descriptors of every request for the plan's current poses and kernel choices,
-// written to its pinned staging buffer.
+// written to its pinned staging buffer: tables, jobs, one work queue per group.
 void plan_fill(dare_plan p) {
     uint8_t* pin = static_cast<uint8_t*>(p->pinned);
     auto* tjs = reinterpret_cast<TableJob*>(pin);
     auto* rjs = reinterpret_cast<ResliceJob*>(pin + (p->o_rj - p->o_tj));
+    auto* qs = reinterpret_cast<TileQueue*>(pin + (p->o_q - p->o_tj));
     uint8_t* ws = static_cast<uint8_t*>(p->ws);
-    for (auto& g : p->groups) {
+    const bool general = general_support(&p->params);
+    for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+        auto& g = p->groups[gi];
         int tile_base = 0;
         for (int32_t k = g.k0; k < g.k1; ++k) {
             const dare_reslice_req& r = p->reqs[p->order[k]];
@@ -2399,16 +2598,34 @@ void plan_fill(dare_plan p) {
             tj.wtab = wtab;
             tj.n_frames = r.session->n_frames;
             tjs[k] = tj;
-            rjs[k] = make_job(r.session, &r.plane, wtab, r.out, r.mask, p->params.unassigned, &p->params);
-            rjs[k].tile_base = tile_base;
-            tile_base += plan_tiles(&r.plane, g.choice);
+            ResliceJob j = make_job(r.session, &r.plane, wtab, r.out, r.mask, p->params.unassigned, &p->params);
+            if (general) {
+                j.tile_h = kTileHGeneral;
+            } else if (g.choice > 0 && p->params.path == DARE_PATH_TILED_FIXED) {
+                j.tile_h = g.choice;
+            } else if (g.choice > 0) {
+                // the persistent tiled kernel: the plane's own tile height, or per-pixel tiles
+                // (32 rows each) when none fits
+                j.tile_h = tile_rows_fit(j, g.choice);
+                if (j.tile_h == 0) {
+                    j.direct = 1;
+                    j.tile_h = 32;
+                }
+            }
+            j.tile_base = tile_base;
+            rjs[k] = j;
+            tile_base += plan_tiles(&r.plane, j, g.choice);
         }
-        if (general_support(&p->params)) general_caps(rjs + g.k0, g.k1 - g.k0, &g.col_cap, &g.slot_cap);
+        qs[gi] = TileQueue{tile_base, 0, {0, 0}};
+        if (general) general_caps(rjs + g.k0, g.k1 - g.k0, &g.col_cap, &g.slot_cap);
     }
 }
 
-cudaError_t plan_group_launch(dare_plan p, const dare_plan_s::Group& g, cudaStream_t st) {
-    const auto* rj_dev = reinterpret_cast<const ResliceJob*>(static_cast<uint8_t*>(p->ws) + p->o_rj);
+cudaError_t plan_group_launch(dare_plan p, size_t gi, cudaStream_t st) {
+    const dare_plan_s::Group& g = p->groups[gi];
+    uint8_t* ws = static_cast<uint8_t*>(p->ws);
+    const auto* rj_dev = reinterpret_cast<const ResliceJob*>(ws + p->o_rj);
+    auto* q_dev = reinterpret_cast<TileQueue*>(ws + p->o_q) + gi;
     const int half_w = p->params.weight_dtype == DARE_WEIGHTS_F16;
     const bool general = general_support(&p->params);
     if (g.choice == 0)
@@ -2416,19 +2633,20 @@ cudaError_t plan_group_launch(dare_plan p, const dare_plan_s::Group& g, cudaStre
                                                 half_w, st)
                        : launch_reslice_plain(rj_dev + g.k0, nullptr, g.k1 - g.k0, g.max_w, g.max_h, g.K, g.dtype,
                                               half_w, st);
-    const int per = tiles_of(&p->reqs[p->order[g.k0]].plane, g.choice);
-    bool uniform = g.k1 - g.k0 <= 65535;
-    int total = 0;
-    for (int32_t k = g.k0; k < g.k1; ++k) {
-        const int t = tiles_of(&p->reqs[p->order[k]].plane, g.choice);
-        uniform = uniform && t == per;
-        total += t;
-    }
-    if (general)
+    if (general) {
+        // fixed 32-row tiles: the tile count does not depend on the poses
+        const int per = tiles_of(&p->reqs[p->order[g.k0]].plane, kTileHGeneral);
+        bool uniform = g.k1 - g.k0 <= 65535;
+        int total = 0;
+        for (int32_t k = g.k0; k < g.k1; ++k) {
+            const int t = tiles_of(&p->reqs[p->order[k]].plane, kTileHGeneral);
+            uniform = uniform && t == per;
+            total += t;
+        }
         return launch_reslice_tiled_r(rj_dev + g.k0, nullptr, g.k1 - g.k0, 0, uniform ? per : total, uniform ? 1 : 0,
                                       g.col_cap, g.slot_cap, g.K, g.dtype, half_w, st);
-    return launch_reslice_tiled(rj_dev + g.k0, nullptr, g.k1 - g.k0, 0, uniform ? per : total, uniform ? 1 : 0,
-                                g.choice, g.K, g.dtype, half_w, st);
+    }
+    return launch_reslice_tiled_persistent(rj_dev + g.k0, g.k1 - g.k0, q_dev, g.K, g.dtype, half_w, st);
 }
 
 cudaError_t plan_tables_launch(dare_plan p, cudaStream_t st) {
@@ -2437,48 +2655,67 @@ cudaError_t plan_tables_launch(dare_plan p, cudaStream_t st) {
                                 table_params(&p->params), st);
 }
 
+// Tuning key of a group: storage type, K, weight type, output pixels (rounded to
+// a power of two) and planes, median pixel-to-voxel pitch (eighths of a voxel),
+// L2 mode, frame count (rounded to a power of two) and the device's SM count.
 std::string tune_key(dare_plan p, const dare_plan_s::Group& g) {
     long long px = 0;
-    for (int32_t k = g.k0; k < g.k1; ++k) px += int64_t(p->reqs[p->order[k]].plane.width) * p->reqs[p->order[k]].plane.height;
-    char buf[160];
-    std::snprintf(buf, sizeof(buf), "d%d K%d t%d n%d w%d h%d px%lld f%d hw%d", p->device, g.K, g.dtype, g.k1 - g.k0,
-                  g.max_w, g.max_h, px, p->max_frames, p->params.weight_dtype);
+    std::vector<double> pitch;
+    bool l2 = true;
+    for (int32_t k = g.k0; k < g.k1; ++k) {
+        const dare_reslice_req& r = p->reqs[p->order[k]];
+        px += int64_t(r.plane.width) * r.plane.height;
+        pitch.push_back(plane_pitch(r));
+        l2 = l2 && (r.session->cfg.flags & DARE_SESSION_L2_PERSIST);
+    }
+    std::nth_element(pitch.begin(), pitch.begin() + pitch.size() / 2, pitch.end());
+    auto pow2 = [](long long x) {
+        int e = 0;
+        while ((1LL << e) < x) ++e;
+        return e;
+    };
+    int sms = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device);
+    char buf[200];
+    std::snprintf(buf, sizeof(buf), "sm%d t%d K%d w%d px2^%d n2^%d pitch%d l2%d f2^%d", sms, g.dtype, g.K,
+                  p->params.weight_dtype, pow2(px), pow2(g.k1 - g.k0),
+                  static_cast<int>(std::lround(pitch[pitch.size() / 2] * 8.0)), l2 ? 1 : 0, pow2(p->max_frames));
     return buf;
 }
 
 // Time one group's candidate kernels on the plan's own requests; keep the fastest.
-dare_status plan_tune(dare_plan p, dare_plan_s::Group& g, cudaStream_t st) {
-    const std::string key = tune_key(p, g);
+dare_status plan_tune(dare_plan p, size_t gi, cudaStream_t st) {
+    auto& g = p->groups[gi];
+    g.key = tune_key(p, g);
     {
         std::lock_guard<std::mutex> lk(g_tune_mu);
-        auto it = g_tune_cache.find(key);
+        auto it = g_tune_cache.find(g.key);
         if (it != g_tune_cache.end()) {
             g.choice = it->second;
             return DARE_OK;
         }
     }
-    const int cands[3] = {0, 32, 64};
+    const int cands[dare_plan_s::kCands] = {0, 64, 32, 16};
     cudaEvent_t a = nullptr, b = nullptr;
     CUDA_TRY(cudaEventCreate(&a));
     CUDA_TRY(cudaEventCreate(&b));
     float best = 1e30f;
     int best_c = kTileH;
-    for (int ci = 0; ci < 3; ++ci) {
+    for (int ci = 0; ci < dare_plan_s::kCands; ++ci) {
         g.choice = cands[ci];
         plan_fill(p);
-        CUDA_TRY(cudaMemcpyAsync(static_cast<uint8_t*>(p->ws) + p->o_tj, p->pinned, p->desc_bytes,
-                                 cudaMemcpyHostToDevice, st));
-        CUDA_TRY(plan_tables_launch(p, st));
-        CUDA_TRY(plan_group_launch(p, g, st));  // warm-up
         float ms = 1e30f;
-        for (int rep = 0; rep < 3; ++rep) {
+        for (int rep = 0; rep < 4; ++rep) {  // the first is a warm-up
+            CUDA_TRY(cudaMemcpyAsync(static_cast<uint8_t*>(p->ws) + p->o_tj, p->pinned, p->desc_bytes,
+                                     cudaMemcpyHostToDevice, st));
+            CUDA_TRY(plan_tables_launch(p, st));
             CUDA_TRY(cudaEventRecord(a, st));
-            CUDA_TRY(plan_group_launch(p, g, st));
+            CUDA_TRY(plan_group_launch(p, gi, st));
             CUDA_TRY(cudaEventRecord(b, st));
             CUDA_TRY(cudaEventSynchronize(b));
             float t = 0;
             CUDA_TRY(cudaEventElapsedTime(&t, a, b));
-            ms = std::min(ms, t);
+            if (rep > 0) ms = std::min(ms, t);
         }
         g.tune_ms[ci] = ms;
         if (ms < best) {
@@ -2490,13 +2727,21 @@ dare_status plan_tune(dare_plan p, dare_plan_s::Group& g, cudaStream_t st) {
     cudaEventDestroy(b);
     g.choice = best_c;
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    g_tune_cache[key] = best_c;
+    g_tune_cache[g.key] = best_c;
+    if (!tune_file_save()) return fail(DARE_E_INVALID, "cannot write the tuning file %s", g_tune_file.c_str());
     return DARE_OK;
 }
 
 }  // namespace
 
 extern "C" {
+
+dare_status dare_tune_cache_file(const char* path) {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    g_tune_file = path ? path : "";
+    if (!g_tune_file.empty()) tune_file_load(g_tune_file);
+    return DARE_OK;
+}
 
 dare_status dare_plan_destroy(dare_plan p) {
     if (!p) return DARE_OK;
@@ -2571,7 +2816,10 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
             ++k1;
         }
         g.k1 = k1;
-        g.choice = params->path == DARE_PATH_PLAIN ? 0 : (general_support(params) ? kTileHGeneral : kTileH);
+        g.choice = params->path == DARE_PATH_PLAIN ? 0
+                   : general_support(params)       ? kTileHGeneral
+                   : params->tile_rows             ? params->tile_rows
+                                                   : kTileH;
         p->groups.push_back(g);
         k0 = k1;
     }
@@ -2586,7 +2834,8 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
     }
     p->o_tj = o;
     p->o_rj = align_up(p->o_tj + size_t(n) * sizeof(TableJob), 256);
-    const size_t need = align_up(p->o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    p->o_q = align_up(p->o_rj + size_t(n) * sizeof(ResliceJob), 256);
+    const size_t need = align_up(p->o_q + p->groups.size() * sizeof(TileQueue), 256);
     p->desc_bytes = need - p->o_tj;
     rc = admit(static_cast<int64_t>(need));
     if (rc != DARE_OK) return bail(rc);
@@ -2609,19 +2858,25 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
         if (cudaStreamWaitEvent(p->cap, s->order_ev, 0) != cudaSuccess) return bail(fail(DARE_E_CUDA, "wait failed"));
     }
     if (params->path == DARE_PATH_AUTO && !general_support(params))  // general kernels: tiled, no tuning
-        for (auto& g : p->groups) {
-            rc = plan_tune(p, g, p->cap);
+        for (size_t gi = 0; gi < p->groups.size(); ++gi) {
+            rc = plan_tune(p, gi, p->cap);
             if (rc != DARE_OK) return bail(rc);
         }
     plan_fill(p);
     if (cudaStreamSynchronize(p->cap) != cudaSuccess) return bail(fail(DARE_E_CUDA, "plan tuning failed"));
+    for (auto& g : p->groups)
+        if (g.choice > 0 && !general_support(params) &&
+            prepare_reslice_tiled_persistent(g.K, g.dtype, params->weight_dtype == DARE_WEIGHTS_F16) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(fail(DARE_E_CUDA, "persistent kernel set-up failed"));
+        }
     cudaError_t e = cudaStreamBeginCapture(p->cap, cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
         cudaError_t e1 = cudaMemcpyAsync(static_cast<uint8_t*>(p->ws) + p->o_tj, p->pinned, p->desc_bytes,
                                          cudaMemcpyHostToDevice, p->cap);
         if (e1 == cudaSuccess && p->max_frames > 0) e1 = plan_tables_launch(p, p->cap);
-        for (auto& g : p->groups)
-            if (e1 == cudaSuccess) e1 = plan_group_launch(p, g, p->cap);
+        for (size_t gi = 0; gi < p->groups.size(); ++gi)
+            if (e1 == cudaSuccess) e1 = plan_group_launch(p, gi, p->cap);
         e = cudaStreamEndCapture(p->cap, &p->graph);
         if (e == cudaSuccess) e = e1;
     }
@@ -2683,7 +2938,7 @@ dare_status dare_plan_query(dare_plan p, dare_plan_info* out) {
     out->n_groups = static_cast<int32_t>(p->groups.size());
     for (size_t g = 0; g < p->groups.size() && g < 8; ++g) {
         out->choice[g] = p->groups[g].choice;
-        for (int c = 0; c < 3; ++c) out->tune_ms[g][c] = p->groups[g].tune_ms[c];
+        for (int c = 0; c < dare_plan_s::kCands; ++c) out->tune_ms[g][c] = p->groups[g].tune_ms[c];
     }
     out->workspace_bytes = static_cast<int64_t>(p->ws_bytes);
     return DARE_OK;

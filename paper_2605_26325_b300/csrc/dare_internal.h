@@ -42,7 +42,7 @@ struct ResliceJob {
     // g_d = alpha + beta1 g_e1 + beta2 g_e2; (u, v) = (ou, ov) + M (g_e1, g_e2).
     int32_t d;                  // 0, 1, 2
     int32_t levels;             // level slots per column, floor(2 spread + 0.05) + 3
-    int32_t direct;             // 1: degenerate plane, every pixel gathers directly
+    int32_t direct;             // 1: every pixel gathers directly (degenerate plane, or no tile height fits)
     int32_t n_frames;           // entries of wtab
     float alpha, beta1, beta2, spread;
     float m00, m01, m10, m11, ou, ov, hu, hv;
@@ -52,7 +52,7 @@ struct ResliceJob {
     int32_t radius, kernel;
     int32_t ext_lo, ext_hi;
     float k_dist;
-    int32_t reserved;
+    int32_t tile_h;             // rows of the tiled kernel's tiles for this plane (8, 16, 32 or 64)
     const uint16_t* npix;       // per-pixel samples: weight each sample by its npix (general kernels); NULL: 1
 };
 
@@ -149,6 +149,8 @@ cudaError_t launch_fill_holes(const int32_t dims[3], int radius, int min_neighbo
                               const uint32_t* scal_cnt, float* out, cudaStream_t st);
 cudaError_t launch_reslice_values(const ResliceJob& job, const float* values, cudaStream_t st);
 cudaError_t launch_fill_records(uint8_t* rec, int64_t n_vox, int rec_bytes, int K, cudaStream_t st);
+// L2 read-bandwidth measurement: `reps` passes over `bytes` (multiple of 16) of buf, `blocks` CTAs of 256
+cudaError_t launch_l2_read(const void* buf, int64_t bytes, int reps, void* sink, int blocks, cudaStream_t st);
 
 // any radius and distance kernel (kernels_radius.cu): per-pixel gather, and the
 // tiled kernel with col_cap columns and slot_cap (A, B) slots of dynamic shared memory
@@ -181,18 +183,40 @@ cudaError_t launch_reslice_curv(const CurvJob* jobs_dev, const CurvJob* one_job,
 constexpr int kMaxSupport = 9;           // tiled general path: support of at most 9 voxels per axis (R <= 4)
 constexpr int kGeneralSmemCap = 200 << 10;  // dynamic shared memory of the general tiled kernel, at most
 
-// tiled kernel (kernels_tiled.cu)
-// uniform != 0: every job has n_tiles tiles (2-D grid, no job search); tile_h: 32 or 64
-cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
-                                 int tile_offset, int n_tiles, int uniform, int tile_h, int K, int dtype,
-                                 int half_weights, cudaStream_t st);
+// tiled kernel (kernels_tiled.cu): 32 x tile_h pixel tiles (tile_h per job); a tile's voxel-column
+// box must fit kTiledColMax columns and kTiledSlotMax (A, B) slots of shared memory, or it gathers
+// per pixel (counted by read_fallback_tiles)
 constexpr int kTileW = 32;
+constexpr int kTiledColMax = 1024;
+constexpr int kTiledSlotMax = 4096;
+// uniform != 0: every job has n_tiles tiles (2-D grid, no job search)
+cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
+                                 int tile_offset, int n_tiles, int uniform, int K, int dtype, int half_weights,
+                                 cudaStream_t st);
+// Work queue of the persistent tiled kernel, in device memory: `total` tiles over the jobs'
+// tile_base ranges; `next` counts the tiles handed out beyond the first grid-size ones (0 at launch).
+struct TileQueue {
+    int32_t total;
+    int32_t next;
+    int32_t pad[2];
+};
+// persistent form: one CTA per resident slot of the device, tiles taken from the queue
+cudaError_t launch_reslice_tiled_persistent(const ResliceJob* jobs_dev, int n_jobs, TileQueue* queue, int K,
+                                            int dtype, int half_weights, cudaStream_t st);
+// sizes (and loads) the persistent kernel for (K, dtype, weights): before a stream capture launches it
+cudaError_t prepare_reslice_tiled_persistent(int K, int dtype, int half_weights);
+// tiles that gathered per pixel inside the tiled kernels (kernels_tiled.cu, kernels_radius.cu) since
+// the last reset, on the current device
+cudaError_t read_fallback_tiles_tiled(unsigned long long* out, bool reset);
+cudaError_t read_fallback_tiles_general(unsigned long long* out, bool reset);
 
 // batch helpers and memory accounting (api.cpp), used by the server
 // allow_paged: sessions with a brick cache are accepted (dare_reslice_batch runs them plane by plane)
 dare_status check_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, bool allow_paged = false);
 void batch_sizes(const dare_reslice_req* reqs, int32_t n, const dare_params* params, size_t* ws_need,
                  size_t* desc_bytes);
+void batch_sizes_bound(int32_t n, int32_t max_frames, size_t* ws_need, size_t* desc_bytes);
+int session_max_frames(dare_session s);
 dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_params* params, cudaStream_t st,
                         uint8_t* ws, uint8_t* pin);
 dare_status reserve_bytes(int64_t bytes);
@@ -206,6 +230,6 @@ dare_status set_error(dare_status st, const char* msg);
 int session_device(dare_session s);
 dare_status reslice_with_table(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
                                uint32_t* mask_dev, void* stream, void* wtab, size_t wtab_bytes, int max_frames);
-constexpr int kTileH = 64;  // default tile height; plans may autotune 32 or 64
+constexpr int kTileH = 64;  // largest tile height of the tiled kernel
 
 }  // namespace dare

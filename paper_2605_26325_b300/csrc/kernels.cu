@@ -400,6 +400,31 @@ __global__ void k_fill_records(uint4* rec, int64_t n_vec, int vec_per_rec, int i
     }
 }
 
+// ------------------------------------------------------------------ L2 read bandwidth (measurement)
+
+// Reads a buffer that fits L2 `reps` times with 16-byte loads that bypass L1
+// (ld.global.cg), four independent loads in flight per thread.  The XOR of the
+// words reaches `sink` only if it equals an unlikely value, so no load is dead.
+__global__ void __launch_bounds__(256) k_l2_read(const uint4* __restrict__ buf, int64_t n_vec, int reps,
+                                                 uint4* __restrict__ sink) {
+    uint32_t acc = 0;
+    const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+    const int64_t first = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    for (int r = 0; r < reps; ++r) {
+        int64_t i = first;
+        for (; i + 3 * stride < n_vec; i += 4 * stride) {
+            const uint4 a = __ldcg(buf + i), b = __ldcg(buf + i + stride);
+            const uint4 c = __ldcg(buf + i + 2 * stride), d = __ldcg(buf + i + 3 * stride);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w ^ b.x ^ b.y ^ b.z ^ b.w ^ c.x ^ c.y ^ c.z ^ c.w ^ d.x ^ d.y ^ d.z ^ d.w;
+        }
+        for (; i < n_vec; i += stride) {
+            const uint4 a = __ldcg(buf + i);
+            acc ^= a.x ^ a.y ^ a.z ^ a.w;
+        }
+    }
+    if (acc == 0x9E3779B9u) sink[0] = make_uint4(acc, 0u, 0u, 0u);
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------ launchers
@@ -475,6 +500,12 @@ cudaError_t launch_fill_records(uint8_t* rec, int64_t n_vox, int rec_bytes, int 
     const int blocks = static_cast<int>(want < 148 * 32 ? want : 148 * 32);
     if (blocks <= 0) return cudaSuccess;
     k_fill_records<<<blocks, 256, 0, st>>>(reinterpret_cast<uint4*>(rec), n_vec, rec_bytes / 16, 2 * K);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_l2_read(const void* buf, int64_t bytes, int reps, void* sink, int blocks, cudaStream_t st) {
+    if (bytes < 16 || reps < 1 || blocks < 1) return cudaErrorInvalidValue;
+    k_l2_read<<<blocks, 256, 0, st>>>(static_cast<const uint4*>(buf), bytes / 16, reps, static_cast<uint4*>(sink));
     return cudaPeekAtLastError();
 }
 

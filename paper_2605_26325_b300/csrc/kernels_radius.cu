@@ -27,6 +27,9 @@ using namespace dev;
 
 constexpr int kThreads = 256;
 constexpr int kTH = 32;          // tile rows of the general tiled kernel (tile 32 x 32)
+
+// tiles that gathered per pixel because their column box did not fit shared memory
+__device__ unsigned long long g_fallback_tiles_r;
 constexpr float kMargin = 0.02f; // voxel; > FP32 error of the plane height for |g| < 2^14
 
 // distance weights: TENT factor of one axis, EXP of the squared distance
@@ -378,6 +381,7 @@ __global__ void __launch_bounds__(kThreads) k_reslice_tiled_r(const ResliceJob* 
             if (J0.d == 0) tile_setup_r<0>(J0, T.u0, T.v0, T.u1, T.v1, col_cap, slot_cap, T);
             else if (J0.d == 1) tile_setup_r<1>(J0, T.u0, T.v0, T.u1, T.v1, col_cap, slot_cap, T);
             else tile_setup_r<2>(J0, T.u0, T.v0, T.u1, T.v1, col_cap, slot_cap, T);
+            if (T.direct && !J0.direct) atomicAdd(&g_fallback_tiles_r, 1ull);
         }
     }
     __syncthreads();
@@ -477,6 +481,13 @@ cudaError_t launch_reslice_tiled_r(const ResliceJob* jobs_dev, const ResliceJob*
     if (n_jobs <= 0 || n_tiles <= 0) return cudaSuccess;
     return launch_r_any(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, max(col_cap, 1), max(slot_cap, 1),
                         0, 0, true, K, dtype, half_weights, st);
+}
+
+cudaError_t read_fallback_tiles_general(unsigned long long* out, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_fallback_tiles_r, sizeof(*out));
+    if (e != cudaSuccess || !reset) return e;
+    const unsigned long long zero = 0;
+    return cudaMemcpyToSymbol(g_fallback_tiles_r, &zero, sizeof(zero));
 }
 
 }  // namespace dare

@@ -1,4 +1,6 @@
-// Tiled DARE reslice (sm_103a): one CTA per 32 x TH pixel tile (TH = 32 or 64).
+// Tiled DARE reslice (sm_103a): one CTA per 32 x TH pixel tile (TH = 8, 16, 32 or
+// 64, chosen per plane on the host so that the tile's voxel-column box fits
+// shared memory).
 //
 // For a plane r the orientation weight w_f of Eq. 2 depends only on the
 // sample's frame f, so the weighted average of Sec. 2.1 with TENT weights t_c
@@ -19,7 +21,13 @@
 // pixel rectangle.  The plane coefficients come from the host (FP64) as FP32
 // with margins far above FP32 rounding, so any error only adds work.  Every
 // shared-memory read is range-checked.  A tile whose box does not fit in
-// shared memory gathers per pixel instead, with the same result.
+// shared memory gathers per pixel instead, with the same result, and is counted.
+//
+// Two launch forms: a grid of one CTA per tile, and a persistent grid of one
+// CTA per resident slot that takes tiles from a work queue in device memory
+// (its tile count is read on the device, so a captured graph stays valid when
+// new poses change the planes' tile heights).
+#include <algorithm>
 #include <cfloat>
 
 #include "dare_internal.h"
@@ -31,12 +39,15 @@ namespace {
 using namespace dev;
 
 constexpr int kThreads = 256;
-constexpr int kColMax = 1024;
-constexpr int kSlotMax = 4096;   // (A, B) float2 slots: 32 KB
+constexpr int kColMax = kTiledColMax;
+constexpr int kSlotMax = kTiledSlotMax;   // (A, B) float2 slots: 32 KB
 #ifndef DARE_TILED_MIN_BLOCKS
 #define DARE_TILED_MIN_BLOCKS 4
 #endif
 constexpr float kMargin = 0.02f; // voxel; > FP32 error of the plane height for |g| < 2^14
+
+// tiles that gathered per pixel because their column box did not fit shared memory
+__device__ unsigned long long g_fallback_tiles;
 
 template <int D>
 struct Axes {
@@ -127,7 +138,7 @@ __device__ void tile_setup(const ResliceJob& J, int u0, int v0, int u1, int v1, 
     T.Od = static_cast<int>(lmax(lmin(Gd >> kFixBits, 1 << 24), -(1 << 24)));
 }
 
-template <int K, typename VT, typename WT, int D, int TH>
+template <int K, typename VT, typename WT, int D>
 __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& T, int u0, int v0, int u1, int v1,
                                           float2* sAB, int* sCol) {
     constexpr int E1 = Axes<D>::E1, E2 = Axes<D>::E2;
@@ -189,9 +200,9 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
     const float unassigned = J.unassigned;
     const int u = u0 + lane;
     const bool active = u <= u1;
-    for (int r = warp; r < TH; r += kThreads / 32) {
+    const int rows = v1 - v0 + 1;
+    for (int r = warp; r < rows; r += kThreads / 32) {
         const int v = v0 + r;
-        if (v > v1) break;  // warp-uniform
         float num = 0.0f, den = 0.0f;
         if (active) {
             if (direct) {
@@ -228,10 +239,43 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
     }
 }
 
+// Warp 0: copy the tile's job into shared memory (one coalesced pass), then
+// thread 0 sets the tile up; lt is the tile's index within its job.
+__device__ __forceinline__ void tile_start(const ResliceJob* src, int job, int lt, ResliceJob& sJob, TileSetup& T) {
+    static_assert(sizeof(ResliceJob) % 4 == 0, "job copied as 32-bit words");
+    const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
+    uint32_t* d32 = reinterpret_cast<uint32_t*>(&sJob);
+    for (int i = threadIdx.x; i < static_cast<int>(sizeof(ResliceJob) / 4); i += 32) d32[i] = s32[i];
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        const ResliceJob& J0 = sJob;
+        const int th = J0.tile_h;
+        T.job = job;
+        const int ty = lt / J0.tiles_x, tx = lt - ty * J0.tiles_x;
+        T.u0 = tx * kTileW;
+        T.v0 = ty * th;
+        T.u1 = min(T.u0 + kTileW, J0.width) - 1;
+        T.v1 = min(T.v0 + th, J0.height) - 1;
+        if (J0.d == 0) tile_setup<0>(J0, T.u0, T.v0, T.u1, T.v1, T);
+        else if (J0.d == 1) tile_setup<1>(J0, T.u0, T.v0, T.u1, T.v1, T);
+        else tile_setup<2>(J0, T.u0, T.v0, T.u1, T.v1, T);
+        if (T.direct && !J0.direct) atomicAdd(&g_fallback_tiles, 1ull);
+    }
+}
+
+template <int K, typename VT, typename WT>
+__device__ __forceinline__ void tile_run(const ResliceJob& J, const TileSetup& T, float2* sAB, int* sCol) {
+    switch (J.d) {
+    case 0: tile_body<K, VT, WT, 0>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    case 1: tile_body<K, VT, WT, 1>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    default: tile_body<K, VT, WT, 2>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    }
+}
+
 // One CTA per tile.  With `uniform` every job has `n_tiles` tiles and the job
 // is blockIdx.y; otherwise blockIdx.x runs over all tiles of the launch and
 // the first warp finds the job by binary search over tile_base.
-template <int K, typename VT, typename WT, int TH>
+template <int K, typename VT, typename WT>
 __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_tiled(const ResliceJob* __restrict__ jobs,
                                                                                    int n_jobs, int tile_offset,
                                                                                    int uniform,
@@ -240,7 +284,6 @@ __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_til
     __shared__ int sCol[kColMax];  // per column: its lowest level (slot 0)
     __shared__ TileSetup T;
     __shared__ ResliceJob sJob;  // the tile's job: one coalesced copy, then shared-memory reads
-    static_assert(sizeof(ResliceJob) % 4 == 0, "job copied as 32-bit words");
     if (threadIdx.x < 32) {
         int job = 0, lt = static_cast<int>(blockIdx.x);
         if (jobs && uniform) {
@@ -250,69 +293,125 @@ __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_til
             job = find_job(jobs, n_jobs, tile);
             lt = tile - __ldg(&jobs[job].tile_base);
         }
-        const uint32_t* src = reinterpret_cast<const uint32_t*>(jobs ? jobs + job : &one);
-        uint32_t* dst = reinterpret_cast<uint32_t*>(&sJob);
-        for (int i = threadIdx.x; i < static_cast<int>(sizeof(ResliceJob) / 4); i += 32) dst[i] = src[i];
-        __syncwarp();
-        if (threadIdx.x == 0) {
-            const ResliceJob& J0 = sJob;
-            T.job = job;
-            const int ty = lt / J0.tiles_x, tx = lt - ty * J0.tiles_x;
-            T.u0 = tx * kTileW;
-            T.v0 = ty * TH;
-            T.u1 = min(T.u0 + kTileW, J0.width) - 1;
-            T.v1 = min(T.v0 + TH, J0.height) - 1;
-            if (J0.d == 0) tile_setup<0>(J0, T.u0, T.v0, T.u1, T.v1, T);
-            else if (J0.d == 1) tile_setup<1>(J0, T.u0, T.v0, T.u1, T.v1, T);
-            else tile_setup<2>(J0, T.u0, T.v0, T.u1, T.v1, T);
-        }
+        tile_start(jobs ? jobs + job : &one, job, lt, sJob, T);
     }
     __syncthreads();
-    const ResliceJob& J = sJob;
-    switch (J.d) {
-    case 0: tile_body<K, VT, WT, 0, TH>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
-    case 1: tile_body<K, VT, WT, 1, TH>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
-    default: tile_body<K, VT, WT, 2, TH>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    tile_run<K, VT, WT>(sJob, T, sAB, sCol);
+}
+
+// Persistent form: CTA b first takes tile b, then tiles gridDim.x + k for the
+// values k of an atomic counter (taken while the current tile runs), until
+// the queue's total is reached.  The queue is written by the host with the
+// job descriptors before every launch, so `next` starts at 0.
+template <int K, typename VT, typename WT>
+__global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS)
+    k_reslice_tiled_persistent(const ResliceJob* __restrict__ jobs, int n_jobs, TileQueue* __restrict__ queue) {
+    __shared__ float2 sAB[kSlotMax];
+    __shared__ int sCol[kColMax];
+    __shared__ TileSetup T;
+    __shared__ ResliceJob sJob;
+    __shared__ int sNext;
+    const int total = *reinterpret_cast<volatile int32_t*>(&queue->total);
+    int tile = static_cast<int>(blockIdx.x);
+    while (tile < total) {  // CTA-uniform
+        if (threadIdx.x < 32) {
+            int next = 0;
+            if (threadIdx.x == 0) next = atomicAdd(&queue->next, 1) + static_cast<int>(gridDim.x);
+            const int job = find_job(jobs, n_jobs, tile);
+            tile_start(jobs + job, job, tile - __ldg(&jobs[job].tile_base), sJob, T);
+            if (threadIdx.x == 0) sNext = next;
+        }
+        __syncthreads();
+        tile_run<K, VT, WT>(sJob, T, sAB, sCol);
+        tile = sNext;
+        __syncthreads();  // shared memory is free for the next tile
     }
 }
 
-// n_tiles: tiles of the whole launch, or per job when `uniform`.
+// Resident CTAs per SM of a kernel (queried once per kernel and device) times the SM count.
+template <typename F>
+int persistent_grid(F kernel) {
+    static int grid[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+    if (!grid[dev]) {
+        int per_sm = 0, sms = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kThreads, 0) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            return 0;
+        grid[dev] = std::max(per_sm, 1) * std::max(sms, 1);
+    }
+    return grid[dev];
+}
+
+// n_tiles: tiles of the whole launch, or per job when `uniform`; queue: persistent form.
 template <int K, typename VT, typename WT>
 cudaError_t tiled_launch(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                         int n_tiles, int uniform, int tile_h, cudaStream_t st) {
+                         int n_tiles, int uniform, TileQueue* queue, cudaStream_t st) {
+    if (queue) {
+        const int grid = persistent_grid(k_reslice_tiled_persistent<K, VT, WT>);
+        if (grid <= 0) return cudaErrorInvalidValue;
+        k_reslice_tiled_persistent<K, VT, WT><<<grid, kThreads, 0, st>>>(jobs_dev, n_jobs, queue);
+        return cudaPeekAtLastError();
+    }
     ResliceJob dummy{};
     const dim3 grid(n_tiles, (one || !uniform) ? 1 : n_jobs);
-    if (tile_h == 32)
-        k_reslice_tiled<K, VT, WT, 32><<<grid, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset,
-                                                                 uniform, one ? *one : dummy);
-    else if (tile_h == 64)
-        k_reslice_tiled<K, VT, WT, 64><<<grid, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset,
-                                                                 uniform, one ? *one : dummy);
-    else
-        return cudaErrorInvalidValue;
+    k_reslice_tiled<K, VT, WT><<<grid, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset, uniform,
+                                                         one ? *one : dummy);
     return cudaPeekAtLastError();
 }
 
 template <int K, typename VT>
 cudaError_t tiled_launch_w(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                           int n_tiles, int uniform, int tile_h, int half_w, cudaStream_t st) {
-    return half_w ? tiled_launch<K, VT, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, st)
-                  : tiled_launch<K, VT, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, st);
+                           int n_tiles, int uniform, TileQueue* queue, int half_w, cudaStream_t st) {
+    return half_w ? tiled_launch<K, VT, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, st)
+                  : tiled_launch<K, VT, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, st);
 }
 
 template <int K>
 cudaError_t tiled_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                           int n_tiles, int uniform, int tile_h, int dtype, int half_w, cudaStream_t st) {
+                           int n_tiles, int uniform, TileQueue* queue, int dtype, int half_w, cudaStream_t st) {
     switch (dtype) {
     case DARE_U8:
-        return tiled_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, half_w, st);
+        return tiled_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, st);
     case DARE_F16:
-        return tiled_launch_w<K, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, half_w, st);
+        return tiled_launch_w<K, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, st);
     case DARE_BF16:
-        return tiled_launch_w<K, __nv_bfloat16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, half_w,
+        return tiled_launch_w<K, __nv_bfloat16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w,
                                                 st);
     case DARE_F32:
-        return tiled_launch_w<K, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, tile_h, half_w, st);
+        return tiled_launch_w<K, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// The persistent kernel's grid for (K, dtype, weights), queried once per device
+// (loads the kernel): call before a stream capture that launches it.
+template <int K, typename VT>
+cudaError_t persistent_prepare_w(int half_w) {
+    const int g = half_w ? persistent_grid(k_reslice_tiled_persistent<K, VT, __half>)
+                         : persistent_grid(k_reslice_tiled_persistent<K, VT, float>);
+    return g > 0 ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <int K>
+cudaError_t persistent_prepare_k(int dtype, int half_w) {
+    switch (dtype) {
+    case DARE_U8: return persistent_prepare_w<K, uint8_t>(half_w);
+    case DARE_F16: return persistent_prepare_w<K, __half>(half_w);
+    case DARE_BF16: return persistent_prepare_w<K, __nv_bfloat16>(half_w);
+    case DARE_F32: return persistent_prepare_w<K, float>(half_w);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t tiled_any(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset, int n_tiles,
+                      int uniform, TileQueue* queue, int K, int dtype, int hw, cudaStream_t st) {
+    switch (K) {
+    case 4: return tiled_launch_k<4>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, st);
+    case 8: return tiled_launch_k<8>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, st);
+    case 12: return tiled_launch_k<12>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, st);
+    case 16: return tiled_launch_k<16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -320,17 +419,33 @@ cudaError_t tiled_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, in
 }  // namespace
 
 cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int tile_offset,
-                                 int n_tiles, int uniform, int tile_h, int K, int dtype, int half_weights,
-                                 cudaStream_t st) {
+                                 int n_tiles, int uniform, int K, int dtype, int half_weights, cudaStream_t st) {
     if (n_jobs <= 0 || n_tiles <= 0) return cudaSuccess;
-    const int u = uniform, th = tile_h, hw = half_weights;
+    return tiled_any(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, nullptr, K, dtype, half_weights, st);
+}
+
+cudaError_t launch_reslice_tiled_persistent(const ResliceJob* jobs_dev, int n_jobs, TileQueue* queue, int K,
+                                            int dtype, int half_weights, cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    if (!jobs_dev || !queue) return cudaErrorInvalidValue;
+    return tiled_any(jobs_dev, nullptr, n_jobs, 0, 0, 0, queue, K, dtype, half_weights, st);
+}
+
+cudaError_t prepare_reslice_tiled_persistent(int K, int dtype, int half_weights) {
     switch (K) {
-    case 4: return tiled_launch_k<4>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, u, th, dtype, hw, st);
-    case 8: return tiled_launch_k<8>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, u, th, dtype, hw, st);
-    case 12: return tiled_launch_k<12>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, u, th, dtype, hw, st);
-    case 16: return tiled_launch_k<16>(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, u, th, dtype, hw, st);
+    case 4: return persistent_prepare_k<4>(dtype, half_weights);
+    case 8: return persistent_prepare_k<8>(dtype, half_weights);
+    case 12: return persistent_prepare_k<12>(dtype, half_weights);
+    case 16: return persistent_prepare_k<16>(dtype, half_weights);
     }
     return cudaErrorInvalidValue;
+}
+
+cudaError_t read_fallback_tiles_tiled(unsigned long long* out, bool reset) {
+    cudaError_t e = cudaMemcpyFromSymbol(out, g_fallback_tiles, sizeof(*out));
+    if (e != cudaSuccess || !reset) return e;
+    const unsigned long long zero = 0;
+    return cudaMemcpyToSymbol(g_fallback_tiles, &zero, sizeof(zero));
 }
 
 }  // namespace dare

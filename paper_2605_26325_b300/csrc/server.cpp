@@ -14,6 +14,7 @@
 #include <cstring>
 #include <deque>
 #include <map>
+#include <string>
 #include <mutex>
 #include <thread>
 #include <vector>
@@ -109,35 +110,24 @@ void CUDART_CB on_done(void* p) {
 // Completes requests that never reached the GPU.
 void complete_now(dare_server sv, DoneBatch* d) { on_done(d); }
 
-bool grow(dare_server_s::Lane& L, size_t ws_need, size_t pin_need) {
-    if (L.ws_bytes < ws_need) {
-        if (L.ws) {
-            cudaFree(L.ws);
-            dare::release_bytes(static_cast<int64_t>(L.ws_bytes));
-            L.ws = nullptr;
-            L.ws_bytes = 0;
-        }
-        const size_t want = std::max(ws_need, size_t(4) << 20);
-        if (dare::reserve_bytes(static_cast<int64_t>(want)) != DARE_OK) return false;
-        if (cudaMalloc(&L.ws, want) != cudaSuccess) {
-            cudaGetLastError();
-            dare::release_bytes(static_cast<int64_t>(want));
-            return false;
-        }
-        L.ws_bytes = want;
+// A lane's device workspace and pinned staging, allocated once at server creation.
+dare_status lane_alloc(dare_server_s::Lane& L, size_t ws_need, size_t pin_need) {
+    dare_status rc = dare::reserve_bytes(static_cast<int64_t>(ws_need));
+    if (rc != DARE_OK) return rc;
+    if (cudaMalloc(&L.ws, ws_need) != cudaSuccess) {
+        cudaGetLastError();
+        dare::release_bytes(static_cast<int64_t>(ws_need));
+        L.ws = nullptr;
+        return dare::set_error(DARE_E_OOM, "server lane workspace allocation failed");
     }
-    if (L.pin_bytes < pin_need) {
-        if (L.pin) cudaFreeHost(L.pin);
+    L.ws_bytes = ws_need;
+    if (cudaHostAlloc(&L.pin, pin_need, cudaHostAllocDefault) != cudaSuccess) {
+        cudaGetLastError();
         L.pin = nullptr;
-        L.pin_bytes = 0;
-        const size_t want = std::max(pin_need, size_t(1) << 20);
-        if (cudaHostAlloc(&L.pin, want, cudaHostAllocDefault) != cudaSuccess) {
-            cudaGetLastError();
-            return false;
-        }
-        L.pin_bytes = want;
+        return dare::set_error(DARE_E_OOM, "server lane staging allocation failed");
     }
-    return true;
+    L.pin_bytes = pin_need;
+    return DARE_OK;
 }
 
 void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& batch) {
@@ -151,8 +141,8 @@ void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& b
     const int32_t n = static_cast<int32_t>(reqs.size());
     size_t ws_need = 0, pin_need = 0;
     dare::batch_sizes(reqs.data(), n, &sv->cfg.params, &ws_need, &pin_need);
-    if (!grow(L, ws_need, pin_need)) {
-        d->status = DARE_E_OOM;
+    if (ws_need > L.ws_bytes || pin_need > L.pin_bytes) {  // excluded by the checks at submission
+        d->status = DARE_E_STATE;
         complete_now(sv, d);
         return;
     }
@@ -172,6 +162,7 @@ void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& b
     }
     cudaEventRecord(L.ev, L.st);
     L.busy = true;
+    std::lock_guard<std::mutex> lk(sv->done_mu);
     sv->stats.batches += 1;
     sv->stats.max_batch_seen = std::max<int64_t>(sv->stats.max_batch_seen, n);
 }
@@ -190,11 +181,28 @@ void run_ingest(dare_server sv, Ingest& g) {
         d->status = DARE_E_CUDA;
         complete_now(sv, d);
     }
+    std::lock_guard<std::mutex> lk(sv->done_mu);
     sv->stats.ingests += 1;
+}
+
+// Requests at the front of the queue that can go out as one batch: consecutive,
+// up to max_batch, stopping at an ingest.
+size_t front_batch(dare_server sv, bool* ingest_follows) {
+    size_t n = 0;
+    *ingest_follows = false;
+    for (const Item& it : sv->queue) {
+        if (it.is_ingest) {
+            *ingest_follows = true;
+            break;
+        }
+        if (++n == static_cast<size_t>(sv->cfg.max_batch)) break;
+    }
+    return n;
 }
 
 void worker_main(dare_server sv) {
     cudaSetDevice(sv->cfg.device);
+    const double window = sv->cfg.coalesce_us * 1e-6;
     std::unique_lock<std::mutex> lk(sv->mu);
     for (;;) {
         bool any_busy = false;
@@ -213,12 +221,22 @@ void worker_main(dare_server sv) {
             lk.lock();
             did = true;
         }
+        double wake = 0.0;  // when the front batch's coalescing window closes
         for (auto& L : sv->lanes) {
             if (L.busy || sv->queue.empty() || sv->queue.front().is_ingest) continue;
-            // the consecutive requests at the front, up to max_batch
+            // coalescing: a batch that is not full waits until its oldest request is
+            // `window` old, unless an ingest behind it or a stop ends the wait
+            bool ingest_follows = false;
+            const size_t n = front_batch(sv, &ingest_follows);
+            const double close = sv->queue.front().req.submit_s + window;
+            if (window > 0 && n < static_cast<size_t>(sv->cfg.max_batch) && !ingest_follows && !sv->stop &&
+                now_s() < close) {
+                wake = close;
+                break;
+            }
             std::vector<Pending> batch;
-            while (!sv->queue.empty() && !sv->queue.front().is_ingest &&
-                   batch.size() < static_cast<size_t>(sv->cfg.max_batch)) {
+            batch.reserve(n);
+            for (size_t k = 0; k < n; ++k) {
                 batch.push_back(sv->queue.front().req);
                 sv->queue.pop_front();
             }
@@ -228,7 +246,11 @@ void worker_main(dare_server sv) {
             did = true;
         }
         if (did) continue;
-        if (any_busy) {
+        if (wake > 0) {
+            // a batch is coalescing: wait for its window (new work or a stop ends the wait early)
+            const double dt = std::min(wake - now_s(), any_busy ? 20e-6 : 1.0);
+            if (dt > 0) sv->cv.wait_for(lk, std::chrono::duration<double>(dt));
+        } else if (any_busy) {
             // lanes still running: poll again shortly (a free lane or new work ends the wait)
             sv->cv.wait_for(lk, std::chrono::microseconds(20));
         } else {
@@ -251,9 +273,13 @@ dare_status dare_server_create(const dare_server_config* cfg, dare_server* out) 
     dare_server_config c = *cfg;
     if (c.lanes == 0) c.lanes = 2;
     if (c.max_batch == 0) c.max_batch = 64;
-    if (c.lanes < 1 || c.lanes > 8 || c.max_batch < 1) return err(DARE_E_INVALID, "lanes must be 1..8, max_batch >= 1");
-    dare_reslice_req probe{};
-    (void)probe;
+    if (c.lanes < 1 || c.lanes > 8 || c.max_batch < 1 || c.max_batch > 4096)
+        return err(DARE_E_INVALID, "lanes must be 1..8, max_batch 1..4096");
+    if (c.coalesce_us < 0 || c.coalesce_us > 1000000) return err(DARE_E_INVALID, "coalesce_us must be 0..1000000");
+    if (c.max_frames == 0) c.max_frames = DARE_MAX_FRAMES;
+    if (c.max_frames < 1 || c.max_frames > DARE_MAX_FRAMES) return err(DARE_E_INVALID, "max_frames must be 0..65535");
+    dare_status prc = dare::check_batch(nullptr, 0, &c.params);
+    if (prc != DARE_OK) return prc;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || c.device < 0 || c.device >= ndev) {
         cudaGetLastError();
@@ -271,11 +297,23 @@ dare_status dare_server_create(const dare_server_config* cfg, dare_server* out) 
         ok = ok && cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) == cudaSuccess;
     }
+    dare_status arc = DARE_OK;
+    if (ok) {
+        size_t ws_b = 0, pin_b = 0;
+        dare::batch_sizes_bound(c.max_batch, c.max_frames, &ws_b, &pin_b);
+        for (auto& L : sv->lanes)
+            if (arc == DARE_OK) arc = lane_alloc(L, ws_b, pin_b);
+    }
     if (prev != c.device) cudaSetDevice(prev);
     if (!ok) {
         cudaGetLastError();
         dare_server_destroy(sv);
         return err(DARE_E_CUDA, "server stream/event creation failed");
+    }
+    if (arc != DARE_OK) {
+        const std::string msg = dare_last_error();
+        dare_server_destroy(sv);
+        return err(arc, msg.c_str());
     }
     sv->worker = std::thread(worker_main, sv);
     *out = sv;
@@ -287,11 +325,16 @@ dare_status dare_server_submit(dare_server sv, const dare_reslice_req* req, uint
     dare_status rc = dare::check_batch(req, 1, &sv->cfg.params);
     if (rc != DARE_OK) return rc;
     if (dare::session_device(req->session) != sv->cfg.device) return err(DARE_E_INVALID, "session on another device");
+    if (dare::session_max_frames(req->session) > sv->cfg.max_frames)
+        return err(DARE_E_INVALID, "the session allows more frames than the server's lanes were sized for");
     {
         std::lock_guard<std::mutex> lk(sv->mu);
         if (sv->stop) return err(DARE_E_STATE, "server is stopping");
         sv->queue.push_back(Item{false, Pending{*req, tag, now_s()}, Ingest{}});
         sv->in_flight += 1;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->done_mu);
         sv->stats.submitted += 1;
     }
     sv->cv.notify_all();
@@ -310,6 +353,9 @@ dare_status dare_server_ingest(dare_server sv, dare_session s, const uint8_t* fr
         if (sv->stop) return err(DARE_E_STATE, "server is stopping");
         sv->queue.push_back(Item{true, Pending{}, std::move(g)});
         sv->in_flight += 1;
+    }
+    {
+        std::lock_guard<std::mutex> lk(sv->done_mu);
         sv->stats.submitted += 1;
     }
     sv->cv.notify_all();

@@ -39,7 +39,7 @@ def test_library_exports_every_declared_symbol():
 
 
 def test_abi_version():
-    assert dare.lib().dare_abi_version() == 2
+    assert dare.lib().dare_abi_version() == 3
 
 
 def test_struct_layouts_match_c(tmp_path):
@@ -48,6 +48,8 @@ def test_struct_layouts_match_c(tmp_path):
         "dare_session_config": dare.dare_session_config, "dare_params": dare.dare_params,
         "dare_plane": dare.dare_plane, "dare_reslice_req": dare.dare_reslice_req,
         "dare_session_info": dare.dare_session_info, "dare_probe": dare.dare_probe,
+        "dare_plan_info": dare.dare_plan_info, "dare_trace_counters": dare.dare_trace_counters,
+        "dare_server_config": dare.dare_server_config, "dare_server_stats": dare.dare_server_stats,
     }
     lines = ['#include <stdio.h>', '#include <stddef.h>', f'#include "{HEADER}"', "int main(void) {"]
     for name, cls in structs.items():

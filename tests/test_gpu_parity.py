@@ -452,7 +452,7 @@ def test_plan_graph_replay(tiny, path):
     info = plan.info()
     assert info["n_groups"] == 2 and info["n_requests"] == len(sizes)
     if path == dare.DARE_PATH_AUTO:
-        assert all(c in (0, 32, 64) for c in info["choice"])
+        assert all(c in (0, 16, 32, 64) for c in info["choice"])
     for poses in (poses_a, poses_b):
         plan.set_poses(np.stack(poses))
         for _, _, out, mask, _ in items:

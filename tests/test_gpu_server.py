@@ -132,3 +132,45 @@ def test_server_curvilinear_and_paged_sessions(tiny):
     server.close()
     for x in (curv, lin, hv):
         x.close()
+
+
+def test_server_coalesces_within_its_window(tiny):
+    """With a coalescing window, requests of different sessions and output sizes
+    submitted close together go out in few batches (here far fewer than one per
+    request), and each result still equals dare_reslice of that request alone."""
+    s1 = gpu_session(tiny, dare.DARE_F32, 8)
+    s2 = gpu_session(tiny, dare.DARE_F16, 8)
+    server = dare.Server(lanes=2, max_batch=64, coalesce_us=200000)
+    jobs = []
+    for i in range(24):
+        s = (s1, s2)[i % 2]
+        W, H = (64, 96, 128)[i % 3], (48, 128)[i % 2]
+        T = synth.plane_pose_centred(tiny.reslice_poses[i % 16][:3, :3], np.zeros(3), W, H, *tiny.out_px)
+        out, mask = new_outputs(W, H)
+        jobs.append((s, T, out, mask))
+        server.submit(s, T, out, mask, tiny.out_px, tag=i)
+    done = _wait_all(server, len(jobs))
+    assert sorted(d[0] for d in done) == list(range(24)) and all(d[1] == dare.DARE_OK for d in done)
+    st = server.stats()
+    assert st["completed"] == 24 and st["batches"] <= 4 and st["max_batch_seen"] >= 8
+    for s, T, out, mask in jobs:
+        H, W = out.shape
+        o1, m1 = gpu_reslice(s, T, W, H, tiny.out_px, dare.params_default())
+        assert np.array_equal(mask.cpu().numpy(), m1)
+        np.testing.assert_array_equal(out.cpu().numpy(), o1)
+    server.close()
+    s1.close()
+    s2.close()
+
+
+def test_server_refuses_sessions_beyond_its_frame_budget(tiny):
+    """Lane workspaces are sized at creation for sessions of up to max_frames
+    frames; a session that allows more is refused at submission."""
+    s = gpu_session(tiny, dare.DARE_F32, 8)  # max_frames 65535
+    server = dare.Server(lanes=1, max_batch=4, max_frames=1000)
+    out, mask = new_outputs(32, 32)
+    with pytest.raises(dare.DareError) as ei:
+        server.submit(s, tiny.reslice_poses[0], out, mask, tiny.out_px, tag=1)
+    assert ei.value.status == dare.DARE_E_INVALID
+    server.close()
+    s.close()

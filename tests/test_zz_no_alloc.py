@@ -19,9 +19,9 @@ from gpu_helpers import DEV, gpu_reslice, gpu_session, new_outputs
 pytestmark = pytest.mark.gpu
 
 
-def noalloc_reslice(s, T, W, H, px, params):
-    """Call the entry point through the C ABI."""
-    out, mask = new_outputs(W, H)
+def noalloc_reslice(s, T, W, H, px, params, bufs=None):
+    """Call the entry point through the C ABI (into bufs = (out, mask) when given)."""
+    out, mask = bufs if bufs is not None else new_outputs(W, H)
     plane = dare.make_plane(W, H, px, T)
     status = dare.lib().dare_reslice_noalloc(s.handle, ctypes.byref(plane), ctypes.byref(params),
                                              ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(mask.data_ptr()),
@@ -38,16 +38,23 @@ def test_noalloc_matches_reslice_twice(tiny, path, weights):
     s = gpu_session(tiny, dare.DARE_F32, 8, allocator=alloc)
     p = dare.params_default(path=path, weight_dtype=weights)
     gpu_reslice(s, tiny.reslice_poses[0], tiny.out_w, tiny.out_h, tiny.out_px, p)  # workspace exists already
+    # set-up call: the first call on a device looks up the array's address, which
+    # may load the library's module that holds it (device memory)
+    noalloc_reslice(s, tiny.reslice_poses[3], tiny.out_w, tiny.out_h, tiny.out_px, p)
     live, in_use = len(alloc.live), dare.memory_in_use()
-    for T in tiny.reslice_poses[[0, 9]]:  # two calls in a row, different planes
-        a_out, a_mask = noalloc_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, p)
-        assert len(alloc.live) == live and dare.memory_in_use() == in_use
-        b_out, b_mask = gpu_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, p)
-        assert np.array_equal(a_mask, b_mask)
-        cov = dare.unpack_mask(b_mask, tiny.out_w).astype(bool)
-        assert cov.sum() > 1000
-        assert np.all(np.abs(a_out[cov] - b_out[cov]) <= 1e-5 * np.maximum(np.abs(b_out[cov]), 1.0))
-        assert np.all(a_out[~cov] == b_out[~cov])
+    refs = [gpu_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, p) for T in tiny.reslice_poses[[0, 9]]]
+    bufs = [new_outputs(tiny.out_w, tiny.out_h) for _ in range(2)]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    outs = [noalloc_reslice(s, T, tiny.out_w, tiny.out_h, tiny.out_px, p, b)  # two calls in a row, different planes
+            for T, b in zip(tiny.reslice_poses[[0, 9]], bufs)]
+    assert torch.cuda.mem_get_info()[0] == free0
+    assert len(alloc.live) == live and dare.memory_in_use() == in_use
+    for (a_out, a_mask), (b_out, b_mask) in zip(outs, refs):
+        # same weight-table and reslice kernels with the same launch set-up: bit for bit
+        np.testing.assert_array_equal(a_mask, b_mask)
+        np.testing.assert_array_equal(a_out, b_out)
+        assert dare.unpack_mask(b_mask, tiny.out_w).sum() > 1000
     s.close()
 
 
