@@ -65,6 +65,9 @@ def parse():
     ap.add_argument("--frames", type=int, default=0,
                     help="build from the first N frames only (profiler runs on a smaller build; 0 = all 1600)")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--build-chunk", type=int, default=0,
+                    help="append the frames in calls of this many frames (same volume, smaller build workspace; "
+                         "for profiler runs that must stay small); 0 = one call")
     return ap.parse_args()
 
 
@@ -184,7 +187,8 @@ def kernel_source_hash():
     a = hdr.index("struct ResliceJob {")
     h.update(hdr[a:hdr.index("};", a) + 2].encode())
     for line in hdr.splitlines():
-        if line.startswith("constexpr") and any(k in line for k in ("kFixBits", "kFixOne", "kTileW", "kTileH")):
+        if line.startswith("constexpr") and any(k in line for k in ("kFixBits", "kFixOne", "kTileW", "kTileH",
+                                                                      "kTiledColMax", "kTiledSlotMax")):
             h.update(line.encode())
     return h.hexdigest()[:16]
 
@@ -389,9 +393,12 @@ def run_dare(args, dist):
     params = dare.params_default(path=path, radius_vox=args.radius, probe_apex_mm=curv_apex,
                                  dist_kernel={"tent": dare.DARE_TENT, "box": dare.DARE_BOX, "exp": dare.DARE_EXP}[args.kernel])
 
+    chunk = args.build_chunk if args.build_chunk > 0 else len(w.frames)
+
     def step():
         s.reset(stream)
-        s.build(frames_d, w.frame_poses, w.frame_px, stream)
+        for a in range(0, len(w.frames), chunk):
+            s.build(frames_d[a:a + chunk], w.frame_poses[a:a + chunk], w.frame_px, stream)
         dare.reslice_batch(reqs, params, stream)
 
     for _ in range(max(args.warmup, 3)):
