@@ -1530,13 +1530,15 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int32_t chunk = static_cast<int32_t>(std::min<int64_t>(65535, std::max<int64_t>(1, kMaxPixelsPerChunk / slots_pf)));
     const int32_t n_chunk = std::min(n, chunk);
-    // workspace: offsets (n_vox + 1), scan block sums, entries (at most one per pixel),
-    // (voxel, entry) pairs (one slot per pixel of the frame tiles), pairs per tile, affines
+    // workspace: offsets (n_vox + 1), scan block sums, overflow entries (at most one per pixel),
+    // buckets (kBucket entries per voxel), overflow (voxel, entry) pairs (one slot per pixel of the
+    // frame tiles), overflow pairs per tile, affines
     const int64_t nbs = scan_block_sums_needed(s->n_vox);
     const size_t o_off = 0;
     const size_t o_bs = align_up(o_off + size_t(s->n_vox + 1) * 4, 256);
     const size_t o_ent = align_up(o_bs + size_t(nbs) * 4, 256);
-    const size_t o_pairs = align_up(o_ent + size_t(n_chunk) * npx * 8, 256);
+    const size_t o_bk = align_up(o_ent + size_t(n_chunk) * npx * 8, 256);
+    const size_t o_pairs = align_up(o_bk + size_t(s->n_vox) * kBucket * 8, 256);
     const size_t o_np = align_up(o_pairs + size_t(n_chunk) * slots_pf * 16, 256);
     const size_t o_aff = align_up(o_np + size_t(n_chunk) * tiles_pf * 4, 256);
     const size_t ws_need = align_up(o_aff + size_t(n) * 9 * 8, 256);
@@ -1562,6 +1564,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     int32_t* offsets = reinterpret_cast<int32_t*>(ws + o_off);
     int32_t* bsums = reinterpret_cast<int32_t*>(ws + o_bs);
     auto* entries = reinterpret_cast<unsigned long long*>(ws + o_ent);
+    auto* buckets = reinterpret_cast<unsigned long long*>(ws + o_bk);
     auto* pairs = reinterpret_cast<uint4*>(ws + o_pairs);
     auto* n_pairs = reinterpret_cast<int32_t*>(ws + o_np);
     int64_t* aff_dev = reinterpret_cast<int64_t*>(ws + o_aff);
@@ -1596,7 +1599,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                 if (std::llabs(aff[9 * size_t(f) + k]) >= (int64_t(1) << 25)) a.small_steps = 0;
         if (!host) {
             KernelScope ks("scatter_count", st, 1);
-            CUDA_TRY(launch_scatter_count(a, s->count, pairs, n_pairs, st));
+            CUDA_TRY(launch_scatter_count(a, s->count, buckets, pairs, n_pairs, st));
         } else {
             for (int32_t j0 = 0, k = 0; j0 < nc; j0 += slice, ++k) {
                 const int b = k & 1;
@@ -1616,14 +1619,14 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                 sa.tile_base = int64_t(j0) * tiles_pf;
                 {
                     KernelScope ks("scatter_count", st, 1);
-                    CUDA_TRY(launch_scatter_count(sa, s->count, pairs, n_pairs, st));
+                    CUDA_TRY(launch_scatter_count(sa, s->count, buckets, pairs, n_pairs, st));
                 }
                 CUDA_TRY(cudaEventRecord(s->ring_free[b], st));
             }
         }
         {
             KernelScope ks("exclusive_scan", st, 3);
-            CUDA_TRY(launch_exclusive_scan(s->count, offsets, s->n_vox, bsums, nbs, st));
+            CUDA_TRY(launch_exclusive_scan(s->count, offsets, s->n_vox, bsums, nbs, kBucket, st));
         }
         {
             KernelScope ks("scatter_place", st, 1);
@@ -1638,8 +1641,8 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
             s->pending_clear = false;  // this finalize writes every voxel
             s->fresh = false;          // from here on the records may hold samples
             KernelScope ks("finalize", st, 1);
-            CUDA_TRY(launch_finalize(offsets, entries, s->n_vox, s->rec, s->npix, s->ssum, s->scnt, s->K, s->dtype,
-                                     mode, s->host_vol ? 0 : 1, s->overflow_dev, st));
+            CUDA_TRY(launch_finalize(s->count, buckets, offsets, entries, s->n_vox, s->rec, s->npix, s->ssum, s->scnt,
+                                     s->K, s->dtype, mode, s->host_vol ? 0 : 1, s->overflow_dev, st));
         }
     }
     rc = session_end(s, st);

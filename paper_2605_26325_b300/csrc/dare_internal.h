@@ -20,6 +20,7 @@ constexpr int kFixBits = DARE_FIX_BITS;
 constexpr int64_t kFixOne = int64_t(1) << kFixBits;
 constexpr int kMaxPixelsPerChunk = 1 << 28;  // pixels of one scatter pass (one 8-byte entry and one 16-byte pair per pixel at most)
 constexpr int kScatterTile = 32;              // frame tiles of the scatter passes: 32 x 32 pixels
+constexpr int kBucket = 8;                    // entries per voxel the count pass stores in place (8 bytes each)
 
 inline int value_bytes(int dtype) { return dtype == DARE_U8 ? 1 : (dtype == DARE_F32 ? 4 : 2); }
 inline int record_bytes(int K, int dtype) { return (2 * K + K * value_bytes(dtype) + 15) / 16 * 16; }
@@ -125,22 +126,29 @@ cudaError_t launch_weight_tables(const TableJob* jobs_dev, const TableJob* one_j
                                  const TableParams& p, cudaStream_t st);
 cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int max_w,
                                  int max_h, int K, int dtype, int half_weights, cudaStream_t st);
-// count: per-voxel counters (zero on entry; place returns them to zero); pairs: kTile^2 16-byte
-// (voxel, entry) pairs per 32 x 32 frame tile; n_pairs: one int per tile
-cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, uint4* pairs, int32_t* n_pairs,
-                                 cudaStream_t st);
+// count: per-voxel entry counters (zero on entry; finalize returns them to zero); buckets: kBucket
+// 8-byte entries per voxel; pairs: kTile^2 16-byte (voxel, entry) overflow pairs per 32 x 32 frame
+// tile; n_pairs: overflow pairs per tile
+cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, unsigned long long* buckets, uint4* pairs,
+                                 int32_t* n_pairs, cudaStream_t st);
+// overflow pairs into their voxels' ranges (offsets: scan of max(count - kBucket, 0)); leaves
+// min(count, kBucket) in the counters
 cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const int32_t* n_pairs, int32_t* count,
                                  const int32_t* offsets, unsigned long long* entries, cudaStream_t st);
+// out[i] = sum_{j < i} max(in[j] - bias, 0), out[n] the total
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
-                                  int64_t block_sums_len, cudaStream_t st);
+                                  int64_t block_sums_len, int bias, cudaStream_t st);
 int64_t scan_block_sums_needed(int64_t n);
 // mode 0: merge into the stored records; 1: the volume holds no sample (created or
 // reset since), stored records are not read; 2: as 1 and not cleared since a reset:
 // every voxel's record, npix row and scalar totals are written (empty where no entry)
 // bulk: records and npix in device memory, so mode 2 may store whole runs with bulk copies
-cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
-                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode,
-                            int bulk, unsigned long long* overflow, cudaStream_t st);
+// a voxel's entries: count[v] (<= kBucket) in its bucket, then entries[offsets[v], offsets[v + 1]);
+// count is returned to zero
+cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, const int32_t* offsets,
+                            const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
+                            uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
+                            unsigned long long* overflow, cudaStream_t st);
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
                                   cudaStream_t st);
 cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned long long* count, cudaStream_t st);

@@ -174,7 +174,7 @@ __device__ __forceinline__ int block_exclusive_scan(int x, int* smem, int* total
 // tail) with 16-byte loads: the launcher checks that `in` and `out` are 16-byte
 // aligned, and base is a multiple of 16 counters.
 __device__ __forceinline__ void scan_load(const int32_t* __restrict__ in, int64_t n, int64_t base,
-                                          int (&v)[kScanItems]) {
+                                          int (&v)[kScanItems], int bias) {
     if (base + kScanItems <= n) {
         const int4* q = reinterpret_cast<const int4*>(in + base);
 #pragma unroll
@@ -189,14 +189,16 @@ __device__ __forceinline__ void scan_load(const int32_t* __restrict__ in, int64_
 #pragma unroll
         for (int i = 0; i < kScanItems; ++i) v[i] = base + i < n ? in[base + i] : 0;
     }
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) v[i] = max(v[i] - bias, 0);  // counts above `bias` only
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_reduce(const int32_t* __restrict__ in, int64_t n,
-                                                              int32_t* __restrict__ block_sums) {
+                                                              int32_t* __restrict__ block_sums, int bias) {
     __shared__ int smem[32];
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
     int v[kScanItems];
-    scan_load(in, n, base, v);
+    scan_load(in, n, base, v, bias);
     int s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) s += v[i];
@@ -224,11 +226,11 @@ __global__ void __launch_bounds__(kScanTopThreads) k_scan_top(int32_t* block_sum
 
 __global__ void __launch_bounds__(kScanThreads) k_scan_down(const int32_t* __restrict__ in, int64_t n,
                                                             const int32_t* __restrict__ block_sums,
-                                                            int32_t* __restrict__ out) {
+                                                            int32_t* __restrict__ out, int bias) {
     __shared__ int smem[32];
     const int64_t base = static_cast<int64_t>(blockIdx.x) * kScanTile + static_cast<int64_t>(threadIdx.x) * kScanItems;
     int vals[kScanItems];
-    scan_load(in, n, base, vals);
+    scan_load(in, n, base, vals, bias);
     int s = 0;
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) s += vals[i];
@@ -454,14 +456,15 @@ cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* o
 int64_t scan_block_sums_needed(int64_t n) { return (n + kScanTile - 1) / kScanTile + 1; }
 
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
-                                  int64_t block_sums_len, cudaStream_t st) {
+                                  int64_t block_sums_len, int bias, cudaStream_t st) {
     const int64_t nb = (n + kScanTile - 1) / kScanTile;
     if (nb + 1 > block_sums_len || nb > INT_MAX) return cudaErrorInvalidValue;
     // the passes move 16-byte groups of counters
     if ((reinterpret_cast<uintptr_t>(in) | reinterpret_cast<uintptr_t>(out)) & 15u) return cudaErrorInvalidValue;
-    k_scan_reduce<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums);
+    if (bias < 0) return cudaErrorInvalidValue;
+    k_scan_reduce<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums, bias);
     k_scan_top<<<1, kScanTopThreads, 0, st>>>(block_sums, nb);
-    k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums, out);
+    k_scan_down<<<static_cast<unsigned>(nb), kScanThreads, 0, st>>>(in, n, block_sums, out, bias);
     return cudaPeekAtLastError();
 }
 

@@ -5,16 +5,21 @@
 //
 // Pipeline per chunk of frames:
 //   count  -- each CTA takes a 32 x 32 pixel tile of one frame and sums its
-//             pixels per voxel in a shared-memory hash table; every (voxel,
-//             tile) pair bumps that voxel's counter once and goes to the
-//             tile's region of a pair list;
-//   scan   -- exclusive prefix sum of the counters (kernels.cu);
-//   place  -- every pair writes its entry (frame id, npix, sum) into its
-//             voxel's range and returns the counter towards zero;
-//   finalize -- one thread per voxel groups its entries by frame id (a frame
-//             split across tiles has several), appends the new samples after
-//             the stored ones (their ids are all lower) and applies the
-//             capacity rule when more than K samples exist.
+//             pixels per voxel in shared memory: a direct-mapped box of the
+//             tile's voxels (one packed 32-bit add per voxel a thread's 2 x 2
+//             pixel block reaches) when that box is small, a hash table
+//             otherwise.  Every (voxel, tile) entry takes a slot from the
+//             voxel's counter; the first kBucket entries of a voxel go straight
+//             into its bucket, later ones (rare) to the tile's overflow list;
+//   scan   -- exclusive prefix sum of the overflow counts max(count - kBucket, 0)
+//             (kernels.cu);
+//   place  -- every overflow pair writes its entry into its voxel's overflow
+//             range (tiles without overflow return at once);
+//   finalize -- one thread per voxel groups its entries (bucket, then overflow
+//             range) by frame id (a frame split across tiles has several),
+//             appends the new samples after the stored ones (their ids are all
+//             lower), applies the capacity rule when more than K samples exist,
+//             and returns the counter to zero.
 // Integer sums make the result independent of scheduling order.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -28,20 +33,95 @@ namespace {
 
 constexpr int kTile = kScatterTile;   // frame tile: 32 x 32 pixels
 constexpr int kThreads = 256;         // a 2 x 2 pixel block per thread
+#ifndef DARE_COUNT_MIN_BLOCKS
+#define DARE_COUNT_MIN_BLOCKS 4
+#endif
 constexpr int kHash = 2048;           // >= 2 x pixels per tile: never full
 constexpr int kEmptyKey = -1;
+#ifndef DARE_BOX_CELLS
+#define DARE_BOX_CELLS 4096
+#endif
+constexpr int kBoxCells = DARE_BOX_CELLS;  // largest direct-mapped voxel box of a tile (16 KB)
+constexpr int kSmemWords = 3 * kHash + kTile * kTile;  // hash keys, counts, sums, list; or the box
+static_assert(kBoxCells >= 0 && kBoxCells <= kSmemWords, "the box fits the shared buffer");
+// packed per-voxel accumulator of the box: npix (<= 1024) above bit 18, sum (<= 1024 x 255 < 2^18) below
+constexpr int kPackShift = 18;
 
-// Nearest voxel of pixel (u, v) (floor(g + 1/2) per axis), or -1 outside the grid.
-__device__ __forceinline__ int scatter_voxel(const int64_t* aff, const int* dims, int u, int v) {
-    int c[3];
+// Nearest voxels of a thread's 2 x 2 pixel block: q-th pixel's coordinates
+// (in-grid flag) and value.  int32 steps from the tile origin when |A|, |B| <
+// 2^25 (host flag), else int64 per pixel.
+struct BlockPixels {
+    int c[4][3];
+    bool in[4];
+    unsigned val[4];
+};
+
+__device__ __forceinline__ void block_pixels(const ScatterArgs& A, const int64_t* aff, int f, int u0, int v0,
+                                             BlockPixels& P) {
+    const uint8_t* img = A.frames + static_cast<int64_t>(f) * A.width * A.height;
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int u = u0 + 2 * tx, v = v0 + 2 * ty;
+    int base[3] = {0, 0, 0}, ra[3] = {0, 0, 0}, rb[3] = {0, 0, 0}, r0[3] = {0, 0, 0};
+    if (A.small_steps) {
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        const int64_t G = aff[a] + static_cast<int64_t>(u) * aff[3 + a] + static_cast<int64_t>(v) * aff[6 + a];
-        const int64_t q = (G + kFixOne / 2) >> kFixBits;
-        if (q < 0 || q >= dims[a]) return -1;
-        c[a] = static_cast<int>(q);
+        for (int a = 0; a < 3; ++a) {
+            const int64_t G = aff[a] + static_cast<int64_t>(u0) * aff[3 + a] + static_cast<int64_t>(v0) * aff[6 + a] +
+                              kFixOne / 2;
+            const int64_t F = G >> kFixBits;
+            base[a] = static_cast<int>(F < -(1 << 24) ? -(1 << 24) : (F > (1 << 24) ? (1 << 24) : F));
+            r0[a] = static_cast<int>(G & (kFixOne - 1));
+            ra[a] = static_cast<int>(aff[3 + a]);
+            rb[a] = static_cast<int>(aff[6 + a]);
+        }
     }
-    return c[0] + dims[0] * (c[1] + dims[1] * c[2]);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const int uu = u + (q & 1), vv = v + (q >> 1);
+        P.in[q] = false;
+        P.val[q] = 0;
+        P.c[q][0] = P.c[q][1] = P.c[q][2] = 0;
+        if (uu >= A.width || vv >= A.height) continue;
+        if (A.pix_mask && !((__ldg(A.pix_mask + static_cast<int64_t>(vv) * ((A.width + 31) >> 5) + (uu >> 5)) >> (uu & 31)) & 1u))
+            continue;  // excluded by the probe's pixel mask
+        bool in = true;
+        if (A.small_steps) {
+            const int du = uu - u0, dv = vv - v0;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                P.c[q][a] = base[a] + ((r0[a] + du * ra[a] + dv * rb[a]) >> kFixBits);
+                in = in && P.c[q][a] >= 0 && P.c[q][a] < A.dims[a];
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const int64_t G = aff[a] + static_cast<int64_t>(uu) * aff[3 + a] + static_cast<int64_t>(vv) * aff[6 + a];
+                const int64_t qq = (G + kFixOne / 2) >> kFixBits;
+                in = in && qq >= 0 && qq < A.dims[a];
+                P.c[q][a] = in ? static_cast<int>(qq) : 0;
+            }
+        }
+        P.in[q] = in;
+        if (in) P.val[q] = __ldg(img + static_cast<int64_t>(vv) * A.width + uu);
+    }
+}
+
+// Sums the block's pixels per distinct key (pixels of the block that share a
+// voxel are combined before touching shared memory) and hands each distinct
+// key with its pixel count and sum to `add`.
+template <typename Add>
+__device__ __forceinline__ void block_combine(const int (&key)[4], const unsigned (&val)[4], Add add) {
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        bool first = key[j] >= 0;
+#pragma unroll
+        for (int k = 0; k < j; ++k) first = first && key[k] != key[j];
+        if (!first) continue;
+        unsigned n = 1u, sm = val[j];
+#pragma unroll
+        for (int k = j + 1; k < 4; ++k)
+            if (key[k] == key[j]) ++n, sm += val[k];
+        add(key[j], n, sm);
+    }
 }
 
 // A new key also appends its slot to `list` (the tile's distinct voxels).
@@ -60,115 +140,166 @@ __device__ __forceinline__ void hash_add(int* keys, unsigned* npx, unsigned* sum
     }
 }
 
-// Shared-memory aggregation of one frame tile: keys[h] = voxel, npx/sums[h] =
-// its pixel count and sum.  Each thread owns a 2 x 2 pixel block; pixels of the
-// block that land in one voxel are combined before touching shared memory.
-__device__ __forceinline__ void aggregate_tile(const ScatterArgs& A, int f, int u0, int v0, int* keys,
-                                               unsigned* npx, unsigned* sums, int* list, int* n_list) {
-    // keys and the npx / sums buffer (its two halves) are declared 16-byte
-    // aligned by the kernel: cleared with 16-byte stores
-    uint4* keys4 = reinterpret_cast<uint4*>(keys);
-    uint4* both4 = reinterpret_cast<uint4*>(npx);
-    static_assert(kEmptyKey == -1, "keys cleared to all-ones words");
-    for (int i = threadIdx.x; i < kHash / 4; i += kThreads) keys4[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
-    for (int i = threadIdx.x; i < kHash / 2; i += kThreads) both4[i] = make_uint4(0u, 0u, 0u, 0u);
-    if (threadIdx.x == 0) *n_list = 0;
-    __shared__ int64_t aff[9];
-    if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
-    __syncthreads();
-    const uint8_t* img = A.frames + static_cast<int64_t>(f) * A.width * A.height;
-    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
-    const int u = u0 + 2 * tx, v = v0 + 2 * ty;
-    // int32 steps from the tile origin when |A|, |B| < 2^25 (host flag), else int64 per pixel
-    int base[3] = {0, 0, 0}, ra[3] = {0, 0, 0}, rb[3] = {0, 0, 0}, r0[3] = {0, 0, 0};
-    if (A.small_steps) {
+// The nearest-voxel box of a tile: by convexity its corner pixels bound every
+// pixel's nearest voxel on each axis; clipped to the grid.  cells = 0 when no
+// pixel of the tile can land in the grid.
+struct TileBox {
+    int b[3];
+    int n[3];
+    int cells;  // n0 n1 n2, or INT_MAX when above kBoxCells
+};
+
+__device__ void tile_box(const int64_t* aff, const int* dims, int u0, int v0, int u1, int v1, TileBox& B) {
+    int64_t cells = 1;
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int64_t G = aff[a] + static_cast<int64_t>(u0) * aff[3 + a] + static_cast<int64_t>(v0) * aff[6 + a] +
-                              kFixOne / 2;
-            const int64_t F = G >> kFixBits;
-            base[a] = static_cast<int>(F < -(1 << 24) ? -(1 << 24) : (F > (1 << 24) ? (1 << 24) : F));
-            r0[a] = static_cast<int>(G & (kFixOne - 1));
-            ra[a] = static_cast<int>(aff[3 + a]);
-            rb[a] = static_cast<int>(aff[6 + a]);
+    for (int a = 0; a < 3; ++a) {
+        int64_t lo = INT64_MAX, hi = INT64_MIN;
+        for (int k = 0; k < 4; ++k) {
+            const int u = (k & 1) ? u1 : u0, v = (k & 2) ? v1 : v0;
+            const int64_t G = aff[a] + static_cast<int64_t>(u) * aff[3 + a] + static_cast<int64_t>(v) * aff[6 + a];
+            const int64_t q = (G + kFixOne / 2) >> kFixBits;
+            lo = q < lo ? q : lo;
+            hi = q > hi ? q : hi;
         }
+        lo = lo < 0 ? 0 : lo;
+        hi = hi > dims[a] - 1 ? dims[a] - 1 : hi;
+        const int64_t n = hi >= lo ? hi - lo + 1 : 0;
+        B.b[a] = static_cast<int>(lo < dims[a] ? lo : 0);
+        B.n[a] = static_cast<int>(n);
+        cells *= n;
     }
-    int vi[4];
-    unsigned val[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const int uu = u + (q & 1), vv = v + (q >> 1);
-        vi[q] = -1;
-        val[q] = 0;
-        if (uu >= A.width || vv >= A.height) continue;
-        if (A.pix_mask && !((__ldg(A.pix_mask + static_cast<int64_t>(vv) * ((A.width + 31) >> 5) + (uu >> 5)) >> (uu & 31)) & 1u))
-            continue;  // excluded by the probe's pixel mask
-        if (A.small_steps) {
-            const int du = uu - u0, dv = vv - v0;
-            int c[3];
-            bool in = true;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                c[a] = base[a] + ((r0[a] + du * ra[a] + dv * rb[a]) >> kFixBits);
-                in = in && c[a] >= 0 && c[a] < A.dims[a];
-            }
-            if (in) vi[q] = c[0] + A.dims[0] * (c[1] + A.dims[1] * c[2]);
-        } else {
-            vi[q] = scatter_voxel(aff, A.dims, uu, vv);
-        }
-        if (vi[q] >= 0) val[q] = __ldg(img + static_cast<int64_t>(vv) * A.width + uu);
-    }
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        bool first = vi[j] >= 0;  // the first pixel of the block in its voxel adds the block's share
-#pragma unroll
-        for (int k = 0; k < j; ++k) first = first && vi[k] != vi[j];
-        if (!first) continue;
-        unsigned n = 1u, sm = val[j];
-#pragma unroll
-        for (int k = j + 1; k < 4; ++k)
-            if (vi[k] == vi[j]) ++n, sm += val[k];
-        hash_add(keys, npx, sums, list, n_list, vi[j], n, sm);
-    }
-    __syncthreads();
+    B.cells = cells > kBoxCells ? INT_MAX : static_cast<int>(cells);
 }
 
-// A (voxel, tile) pair: x = voxel, (w:z) = entry (frame id << 48 | npix << 32
-// | sum).  Tile t owns pairs[t * kTile^2, ...) (a tile has at most one pair per
-// pixel) and n_pairs[t] says how many it wrote.
-__global__ void __launch_bounds__(kThreads) k_scatter_count(const __grid_constant__ ScatterArgs A,
-                                                            int32_t* __restrict__ count, uint4* __restrict__ pairs,
-                                                            int32_t* __restrict__ n_pairs) {
-    __shared__ __align__(16) int keys[kHash];
-    __shared__ __align__(16) unsigned long long acc_buf[kHash];  // npx, then sums: kHash 32-bit counters each
-    __shared__ int list[kTile * kTile];            // slots of the tile's distinct voxels, in insertion order
-    __shared__ int n_list;
-    unsigned* npx = reinterpret_cast<unsigned*>(acc_buf);
-    unsigned* sums = npx + kHash;
+// Up to four (voxel, entry) results per thread and round: counter slots are
+// taken with four returning atomics in flight; the first kBucket entries of a
+// voxel go to its bucket (kBucket consecutive entries per voxel), later ones to
+// the tile's overflow region.
+__device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long long (&e)[4], int32_t* count,
+                                      unsigned long long* buckets, uint4* ovf, int* n_ovf) {
+    int slot[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) slot[j] = vi[j] >= 0 ? atomicAdd(count + vi[j], 1) : 0;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        if (vi[j] < 0) continue;
+        if (slot[j] < kBucket) {
+            buckets[static_cast<int64_t>(vi[j]) * kBucket + slot[j]] = e[j];
+        } else {
+            const int k = atomicAdd(n_ovf, 1);  // at most one pair per pixel of the tile
+            ovf[k] = make_uint4(static_cast<unsigned>(vi[j]), 0u, static_cast<unsigned>(e[j]),
+                                static_cast<unsigned>(e[j] >> 32));
+        }
+    }
+}
+
+// One CTA per 32 x 32 frame tile (blockIdx.y = frame): per-voxel sums of the
+// tile's pixels, then one (voxel, entry) per distinct voxel, entry = frame id
+// << 48 | npix << 32 | sum.  Tile t owns pairs[t * kTile^2, ...) for its
+// overflow pairs and n_pairs[t] says how many it wrote.
+__global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_count(const __grid_constant__ ScatterArgs A,
+                                                            int32_t* __restrict__ count,
+                                                            unsigned long long* __restrict__ buckets,
+                                                            uint4* __restrict__ pairs, int32_t* __restrict__ n_pairs) {
+    __shared__ __align__(16) unsigned smem[kSmemWords];
+    __shared__ int64_t aff[9];
+    __shared__ TileBox B;
+    __shared__ int n_list, n_ovf;
     const int tiles_x = (A.width + kTile - 1) / kTile;
     const int f = blockIdx.y;
     const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
-    aggregate_tile(A, f, u0, v0, keys, npx, sums, list, &n_list);
-    // one pair per distinct voxel, at its list position: bump the voxel's counter, write the pair
     const int64_t tile = A.tile_base + static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
-    const int n = n_list;
-    const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
-    uint4* out = pairs + tile * (kTile * kTile);
-    for (int j = threadIdx.x; j < n; j += kThreads) {
-        const int h = list[j];
-        const int vi = keys[h];
-        atomicAdd(count + vi, 1);
-        const unsigned long long e = fid | (static_cast<unsigned long long>(npx[h]) << 32) | sums[h];
-        out[j] = make_uint4(static_cast<unsigned>(vi), 0u, static_cast<unsigned>(e), static_cast<unsigned>(e >> 32));
+    if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        tile_box(aff, A.dims, u0, v0, min(u0 + kTile, A.width) - 1, min(v0 + kTile, A.height) - 1, B);
+        n_list = 0;
+        n_ovf = 0;
     }
-    if (threadIdx.x == 0) n_pairs[tile] = n;
+    __syncthreads();
+    const int cells = B.cells;
+    if (cells == 0) {  // no pixel of the tile lands in the grid
+        if (threadIdx.x == 0) n_pairs[tile] = 0;
+        return;
+    }
+    const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
+    uint4* ovf = pairs + tile * (kTile * kTile);
+    BlockPixels P;
+    if (cells <= kBoxCells) {
+        // direct-mapped box: one packed counter per voxel of the box
+        uint4* c4 = reinterpret_cast<uint4*>(smem);
+        for (int i = threadIdx.x; i < (cells + 3) / 4; i += kThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+        block_pixels(A, aff, f, u0, v0, P);
+        const int b0 = B.b[0], b1 = B.b[1], b2 = B.b[2], n0 = B.n[0], n1 = B.n[1];
+        int key[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) key[q] = P.in[q] ? (P.c[q][0] - b0) + n0 * ((P.c[q][1] - b1) + n1 * (P.c[q][2] - b2)) : -1;
+        __syncthreads();  // box cleared
+        block_combine(key, P.val, [&](int k, unsigned n, unsigned sm) { atomicAdd(smem + k, (n << kPackShift) | sm); });
+        __syncthreads();
+        const int64_t d0 = A.dims[0], d01 = static_cast<int64_t>(A.dims[0]) * A.dims[1];
+        for (int r = 0; r < cells; r += 4 * kThreads) {
+            int vi[4];
+            unsigned long long e[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int idx = r + j * kThreads + threadIdx.x;
+                const unsigned x = idx < cells ? smem[idx] : 0u;
+                vi[j] = -1;
+                e[j] = 0;
+                if (x) {
+                    const int i2 = idx / (n0 * n1), rem = idx - i2 * (n0 * n1);
+                    const int i1 = rem / n0, i0 = rem - i1 * n0;
+                    vi[j] = static_cast<int>((b0 + i0) + d0 * (b1 + i1) + d01 * (b2 + i2));
+                    e[j] = fid | (static_cast<unsigned long long>(x >> kPackShift) << 32) | (x & ((1u << kPackShift) - 1));
+                }
+            }
+            emit4(vi, e, count, buckets, ovf, &n_ovf);
+        }
+    } else {
+        // hash table over voxel indices
+        int* keys = reinterpret_cast<int*>(smem);
+        unsigned* npx = smem + kHash;
+        unsigned* sums = smem + 2 * kHash;
+        int* list = reinterpret_cast<int*>(smem + 3 * kHash);
+        uint4* keys4 = reinterpret_cast<uint4*>(keys);
+        uint4* both4 = reinterpret_cast<uint4*>(npx);
+        static_assert(kEmptyKey == -1, "keys cleared to all-ones words");
+        for (int i = threadIdx.x; i < kHash / 4; i += kThreads) keys4[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
+        for (int i = threadIdx.x; i < kHash / 2; i += kThreads) both4[i] = make_uint4(0u, 0u, 0u, 0u);
+        block_pixels(A, aff, f, u0, v0, P);
+        int key[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) key[q] = P.in[q] ? P.c[q][0] + A.dims[0] * (P.c[q][1] + A.dims[1] * P.c[q][2]) : -1;
+        __syncthreads();  // table cleared
+        block_combine(key, P.val, [&](int k, unsigned n, unsigned sm) { hash_add(keys, npx, sums, list, &n_list, k, n, sm); });
+        __syncthreads();
+        const int n = n_list;
+        for (int r = 0; r < n; r += 4 * kThreads) {
+            int vi[4];
+            unsigned long long e[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = r + j * kThreads + threadIdx.x;
+                vi[j] = -1;
+                e[j] = 0;
+                if (i < n) {
+                    const int h = list[i];
+                    vi[j] = keys[h];
+                    e[j] = fid | (static_cast<unsigned long long>(npx[h]) << 32) | sums[h];
+                }
+            }
+            emit4(vi, e, count, buckets, ovf, &n_ovf);
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) n_pairs[tile] = n_ovf;
 }
 
-// One CTA per tile region: each pair takes its slot from the voxel's counter
-// (returning it towards zero) and writes its entry into the voxel's range.
-// Regions go tile position first: consecutive CTAs take the same tile of
-// consecutive frames, which cover nearly the same voxels, so their counters
-// and offsets stay in L2 (0.81 against 0.84 ms frame by frame).
+// Overflow pairs (entries of a voxel beyond its bucket): one CTA per tile
+// region; each pair takes a position in its voxel's overflow range from the
+// voxel's counter, which counts back down to kBucket.  Regions go tile
+// position first: consecutive CTAs take the same tile of consecutive frames.
 __global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__ pairs,
                                                        const int32_t* __restrict__ n_pairs,
                                                        int32_t* __restrict__ count, const int32_t* __restrict__ offsets,
@@ -177,23 +308,13 @@ __global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__
     const int64_t tt = blockIdx.x / n_frames, f = blockIdx.x - tt * n_frames;
     const int64_t tile = f * tiles_pf + tt;
     const int n = n_pairs[tile];
+    if (n == 0) return;
     const uint4* in = pairs + tile * (kTile * kTile);
-    constexpr int kU = kTile * kTile / 256;
-    uint4 p[kU];
-#pragma unroll
-    for (int j = 0; j < kU; ++j) {
-        const int i = threadIdx.x + 256 * j;
-        p[j] = i < n ? __ldg(in + i) : make_uint4(0, 0, 0, 0);
+    for (int i = threadIdx.x; i < n; i += 256) {
+        const uint4 p = __ldg(in + i);
+        const int pos = offsets[p.x] + atomicSub(count + p.x, 1) - 1 - kBucket;
+        entries[pos] = (static_cast<unsigned long long>(p.w) << 32) | p.z;
     }
-    int pos[kU];
-#pragma unroll
-    for (int j = 0; j < kU; ++j) {
-        const int i = threadIdx.x + 256 * j;
-        pos[j] = i < n ? offsets[p[j].x] + atomicSub(count + p[j].x, 1) - 1 : -1;
-    }
-#pragma unroll
-    for (int j = 0; j < kU; ++j)
-        if (pos[j] >= 0) entries[pos[j]] = (static_cast<unsigned long long>(p[j].w) << 32) | p[j].z;
 }
 
 // ------------------------------------------------------------------ finalize
@@ -222,11 +343,50 @@ __device__ __forceinline__ int ent_frame(unsigned long long e) { return static_c
 __device__ __forceinline__ int ent_npix(unsigned long long e) { return static_cast<int>((e >> 32) & 0xFFFFu); }
 __device__ __forceinline__ int ent_sum(unsigned long long e) { return static_cast<int>(e & 0xFFFFFFFFu); }
 
+// A voxel's entries: c in its bucket, then its overflow range [s, s + n - c).
+struct VoxelEntries {
+    const unsigned long long* bucket;
+    const unsigned long long* ovf;
+    int c, s, n;
+    __device__ __forceinline__ unsigned long long at(int i) const {
+        return i < c ? __ldg(bucket + i) : __ldg(ovf + s + (i - c));
+    }
+};
+
+// The c <= kBucket entries of a voxel without overflow, from its bucket with
+// 16-byte loads (only the loads that hold entries), the rest all ones (they
+// sort last), sorted ascending: by frame id, the entry's top 16 bits.
+__device__ __forceinline__ void bucket_sorted(const unsigned long long* bucket, int c,
+                                              unsigned long long (&e)[kBucket]) {
+    static_assert(kBucket == 8, "sorting network for 8 entries");
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(bucket);
+#pragma unroll
+    for (int i = 0; i < kBucket / 2; ++i) {
+        const ulonglong2 x = 2 * i < c ? __ldg(q + i) : make_ulonglong2(~0ull, ~0ull);
+        e[2 * i] = 2 * i < c ? x.x : ~0ull;
+        e[2 * i + 1] = 2 * i + 1 < c ? x.y : ~0ull;
+    }
+    // Batcher's odd-even merge sort, 19 compare-exchanges
+#define DARE_CX(a, b)                                        \
+    {                                                        \
+        const unsigned long long lo = e[a] < e[b] ? e[a] : e[b]; \
+        const unsigned long long hi = e[a] < e[b] ? e[b] : e[a]; \
+        e[a] = lo;                                           \
+        e[b] = hi;                                           \
+    }
+    DARE_CX(0, 1) DARE_CX(2, 3) DARE_CX(4, 5) DARE_CX(6, 7)
+    DARE_CX(0, 2) DARE_CX(1, 3) DARE_CX(4, 6) DARE_CX(5, 7)
+    DARE_CX(1, 2) DARE_CX(5, 6)
+    DARE_CX(0, 4) DARE_CX(1, 5) DARE_CX(2, 6) DARE_CX(3, 7)
+    DARE_CX(2, 4) DARE_CX(3, 5)
+    DARE_CX(1, 2) DARE_CX(3, 4) DARE_CX(5, 6)
+#undef DARE_CX
+}
+
 // General merge: the m_old stored samples plus the new entries grouped by
 // frame; more than K samples keep the K of largest npix (ties: lower id).
 template <int K, typename VT>
-__device__ __noinline__ bool merge_general(const unsigned long long* entries, int s, int e, int m_old, uint16_t* ids,
-                                           VT* vals, uint16_t* np) {
+__device__ __noinline__ bool merge_general(const VoxelEntries E, int m_old, uint16_t* ids, VT* vals, uint16_t* np) {
     int Lid[K], Lnp[K], Lcnt[K], Lsum[K];
     VT Lraw[K];
     bool Lnew[K];
@@ -243,8 +403,8 @@ __device__ __noinline__ bool merge_general(const unsigned long long* entries, in
     int last = -1;
     for (;;) {
         int next = 0xFFFF, cnt = 0, sum = 0;
-        for (int i = s; i < e; ++i) {
-            const unsigned long long x = entries[i];
+        for (int i = 0; i < E.n; ++i) {
+            const unsigned long long x = E.at(i);
             const int f = ent_frame(x);
             if (f > last && f < next) {
                 next = f;
@@ -307,13 +467,13 @@ __device__ __noinline__ bool merge_general(const unsigned long long* entries, in
 // Returns false when more than K samples exist (the capacity rule needs the
 // general merge).
 template <int K, typename VT>
-__device__ __forceinline__ bool append_in_order(const unsigned long long* __restrict__ entries, int s, int e,
-                                                int m_old, uint16_t* ids, VT* vals, uint16_t* np) {
+__device__ __forceinline__ bool append_in_order(const VoxelEntries& E, int m_old, uint16_t* ids, VT* vals,
+                                                uint16_t* np) {
     int m = m_old, last = -1;
     for (;;) {
         int next = 0xFFFF, cnt = 0, sum = 0;
-        for (int i = s; i < e; ++i) {
-            const unsigned long long x = __ldg(entries + i);
+        for (int i = 0; i < E.n; ++i) {
+            const unsigned long long x = E.at(i);
             const int f = ent_frame(x);
             const bool lower = f > last && f < next;
             const bool same = f == next;
@@ -331,13 +491,75 @@ __device__ __forceinline__ bool append_in_order(const unsigned long long* __rest
     }
 }
 
+// Sorted entries (frame id ascending, all-ones padding last) appended after
+// the m_old stored samples, entries of one frame merged.  Returns the new
+// sample count, or -1 when more than K samples exist (the general merge then
+// redoes the voxel from its stored samples).
+template <int K, typename VT>
+__device__ __forceinline__ int append_sorted(const unsigned long long (&e)[kBucket], int m_old, uint16_t* ids,
+                                             VT* vals, uint16_t* np) {
+    int m = m_old, cur = -1, cnt = 0, sum = 0;
+#pragma unroll
+    for (int j = 0; j <= kBucket; ++j) {
+        const bool end = j == kBucket || e[j] == ~0ull;
+        const int f = end ? -2 : ent_frame(e[j]);
+        if (f != cur) {
+            if (cur >= 0) {
+                if (m == K) return -1;
+                ids[m] = static_cast<uint16_t>(cur);
+                vals[m] = round_store<VT>(sum, cnt);
+                np[m] = static_cast<uint16_t>(cnt < 65535 ? cnt : 65535);
+                ++m;
+            }
+            if (end) break;
+            cur = f;
+            cnt = 0;
+            sum = 0;
+        }
+        cnt += ent_npix(e[j]);
+        sum += ent_sum(e[j]);
+    }
+    return m;
+}
+
+// A voxel's new samples after its m_old stored ones, and the totals of its
+// entries (mean-compounding comparator).  Returns true when the capacity rule
+// dropped samples.
+template <int K, typename VT>
+__device__ __forceinline__ bool voxel_merge(const VoxelEntries& E, int m_old, uint16_t* ids, VT* vals, uint16_t* np,
+                                            uint32_t& tot_sum, uint32_t& tot_cnt) {
+    tot_sum = 0;
+    tot_cnt = 0;
+    if (E.n == E.c) {  // every entry in the bucket: sorted in registers
+        unsigned long long ev[kBucket];
+        bucket_sorted(E.bucket, E.c, ev);
+#pragma unroll
+        for (int j = 0; j < kBucket; ++j)
+            if (j < E.c) {
+                tot_sum += static_cast<uint32_t>(ent_sum(ev[j]));
+                tot_cnt += static_cast<uint32_t>(ent_npix(ev[j]));
+            }
+        if (append_sorted<K, VT>(ev, m_old, ids, vals, np) >= 0) return false;
+    } else {
+        for (int i = 0; i < E.n; ++i) {
+            const unsigned long long x = E.at(i);
+            tot_sum += static_cast<uint32_t>(ent_sum(x));
+            tot_cnt += static_cast<uint32_t>(ent_npix(x));
+        }
+        if (append_in_order<K, VT>(E, m_old, ids, vals, np)) return false;
+    }
+    return merge_general<K, VT>(E, m_old, ids, vals, np);
+}
+
 // kMode 0: merge into the stored records.  1 (fresh): the volume holds no
 // sample at all, so the stored records are known to be empty and are not read.
 // 2 (full): as 1, and the volume has not been cleared since a reset: every
 // voxel is written, empty ones with the empty record, zero npix and zero
 // scalar totals, which spares the reset a pass over the whole volume.
 template <int K, typename VT, int kMode>
-__global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ offsets,
+__global__ void __launch_bounds__(256) k_finalize(int32_t* __restrict__ count,
+                                                  const unsigned long long* __restrict__ buckets,
+                                                  const int32_t* __restrict__ offsets,
                                                   const unsigned long long* __restrict__ entries, int64_t n_vox,
                                                   uint8_t* __restrict__ rec, uint16_t* __restrict__ npix,
                                                   uint32_t* __restrict__ scal_sum, uint32_t* __restrict__ scal_cnt,
@@ -352,10 +574,10 @@ __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ of
     constexpr bool kFresh = kMode != 0;
     for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n_vox;
          v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int s = offsets[v], e = offsets[v + 1];
+        const int s = offsets[v], e = offsets[v + 1], c = count[v];
         uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
         uint2* g_np = reinterpret_cast<uint2*>(npix + v * K);
-        if (s == e) {
+        if (c == 0) {  // no entry (the overflow range is empty too)
             if (kMode == 2) {
 #pragma unroll
                 for (int i = 0; i < RB / 16; ++i) {
@@ -410,15 +632,10 @@ __global__ void __launch_bounds__(256) k_finalize(const int32_t* __restrict__ of
         int m_old = 0;
         if (!kFresh)
             while (m_old < K && ids[m_old] != DARE_EMPTY_FRAME) ++m_old;
-        uint32_t tot_sum = 0, tot_cnt = 0;
-        for (int i = s; i < e; ++i) {
-            const unsigned long long x = __ldg(entries + i);
-            tot_sum += static_cast<uint32_t>(ent_sum(x));
-            tot_cnt += static_cast<uint32_t>(ent_npix(x));
-        }
-        bool over = false;
-        if (!append_in_order<K, VT>(entries, s, e, m_old, ids, vals, np))
-            over = merge_general<K, VT>(entries, s, e, m_old, ids, vals, np);
+        const VoxelEntries E{buckets + v * kBucket, entries, c, s, c + (e - s)};
+        count[v] = 0;
+        uint32_t tot_sum, tot_cnt;
+        const bool over = voxel_merge<K, VT>(E, m_old, ids, vals, np, tot_sum, tot_cnt);
 #pragma unroll
         for (int i = 0; i < RB / 16; ++i) g_rec[i] = my_rec[i];
 #pragma unroll
@@ -464,7 +681,9 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
 // (20 KB of f32 K=12 records) to global memory with two bulk copies.  A run
 // shorter than 256 voxels (the grid's tail) is stored thread by thread.
 template <int K, typename VT>
-__global__ void __launch_bounds__(256) k_finalize_full(const int32_t* __restrict__ offsets,
+__global__ void __launch_bounds__(256) k_finalize_full(int32_t* __restrict__ count,
+                                                       const unsigned long long* __restrict__ buckets,
+                                                       const int32_t* __restrict__ offsets,
                                                        const unsigned long long* __restrict__ entries,
                                                        int64_t n_vox, uint8_t* __restrict__ rec,
                                                        uint16_t* __restrict__ npix, uint32_t* __restrict__ scal_sum,
@@ -482,20 +701,17 @@ __global__ void __launch_bounds__(256) k_finalize_full(const int32_t* __restrict
             empty_record<K, RB>(my_rec);
 #pragma unroll
             for (int i = 0; i < K / 4; ++i) my_np[i] = make_uint2(0u, 0u);
-            const int s = offsets[v], e = offsets[v + 1];
+            const int c = count[v];
             uint32_t tot_sum = 0, tot_cnt = 0;
             bool over = false;
-            if (s < e) {
+            if (c > 0) {
+                const int s = offsets[v], e = offsets[v + 1];
+                const VoxelEntries E{buckets + v * kBucket, entries, c, s, c + (e - s)};
+                count[v] = 0;
                 uint16_t* ids = reinterpret_cast<uint16_t*>(my_rec);
                 VT* vals = reinterpret_cast<VT*>(reinterpret_cast<uint8_t*>(my_rec) + 2 * K);
                 uint16_t* np = reinterpret_cast<uint16_t*>(my_np);
-                for (int i = s; i < e; ++i) {
-                    const unsigned long long x = __ldg(entries + i);
-                    tot_sum += static_cast<uint32_t>(ent_sum(x));
-                    tot_cnt += static_cast<uint32_t>(ent_npix(x));
-                }
-                if (!append_in_order<K, VT>(entries, s, e, 0, ids, vals, np))
-                    over = merge_general<K, VT>(entries, s, e, 0, ids, vals, np);
+                over = voxel_merge<K, VT>(E, 0, ids, vals, np, tot_sum, tot_cnt);
             }
             if (!whole) {
                 uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
@@ -528,33 +744,34 @@ __global__ void __launch_bounds__(256) k_finalize_full(const int32_t* __restrict
 }
 
 template <int K, typename VT>
-cudaError_t finalize_full_v(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
-                            uint16_t* npix, uint32_t* ss, uint32_t* sc, unsigned long long* ovf, cudaStream_t st) {
+cudaError_t finalize_full_v(int32_t* cnt, const unsigned long long* bk, const int32_t* off,
+                            const unsigned long long* ent, int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss,
+                            uint32_t* sc, unsigned long long* ovf, cudaStream_t st) {
     const int64_t want = (n_vox + 255) / 256;
     const int blocks = static_cast<int>(want < (1 << 30) ? want : (1 << 30));  // one run per CTA
-    k_finalize_full<K, VT><<<blocks, 256, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+    k_finalize_full<K, VT><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
     return cudaPeekAtLastError();
 }
 
 template <int K, int kMode>
-cudaError_t finalize_kf(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
-                        uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, unsigned long long* ovf,
-                        cudaStream_t st) {
+cudaError_t finalize_kf(int32_t* cnt, const unsigned long long* bk, const int32_t* off,
+                        const unsigned long long* ent, int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss,
+                        uint32_t* sc, int dtype, unsigned long long* ovf, cudaStream_t st) {
     const int threads = 256;
     const int64_t want = (n_vox + threads - 1) / threads;
     const int blocks = static_cast<int>(want < 148 * 64 ? want : 148 * 64);
     switch (dtype) {
     case DARE_U8:
-        k_finalize<K, uint8_t, kMode><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, uint8_t, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
     case DARE_F16:
-        k_finalize<K, __half, kMode><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, __half, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
     case DARE_BF16:
-        k_finalize<K, __nv_bfloat16, kMode><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, __nv_bfloat16, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
     case DARE_F32:
-        k_finalize<K, float, kMode><<<blocks, threads, 0, st>>>(off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, float, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -562,22 +779,22 @@ cudaError_t finalize_kf(const int32_t* off, const unsigned long long* ent, int64
 }
 
 template <int K>
-cudaError_t finalize_k(const int32_t* off, const unsigned long long* ent, int64_t n_vox, uint8_t* rec,
-                       uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int mode, int bulk,
-                       unsigned long long* ovf, cudaStream_t st) {
+cudaError_t finalize_k(int32_t* cnt, const unsigned long long* bk, const int32_t* off, const unsigned long long* ent,
+                       int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int mode,
+                       int bulk, unsigned long long* ovf, cudaStream_t st) {
     if (mode == 2 && bulk) {
         switch (dtype) {
-        case DARE_U8: return finalize_full_v<K, uint8_t>(off, ent, n_vox, rec, npix, ss, sc, ovf, st);
-        case DARE_F16: return finalize_full_v<K, __half>(off, ent, n_vox, rec, npix, ss, sc, ovf, st);
-        case DARE_BF16: return finalize_full_v<K, __nv_bfloat16>(off, ent, n_vox, rec, npix, ss, sc, ovf, st);
-        case DARE_F32: return finalize_full_v<K, float>(off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        case DARE_U8: return finalize_full_v<K, uint8_t>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        case DARE_F16: return finalize_full_v<K, __half>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        case DARE_BF16: return finalize_full_v<K, __nv_bfloat16>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        case DARE_F32: return finalize_full_v<K, float>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
         }
         return cudaErrorInvalidValue;
     }
     switch (mode) {
-    case 0: return finalize_kf<K, 0>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
-    case 1: return finalize_kf<K, 1>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
-    case 2: return finalize_kf<K, 2>(off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
+    case 0: return finalize_kf<K, 0>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
+    case 1: return finalize_kf<K, 1>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
+    case 2: return finalize_kf<K, 2>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -589,10 +806,10 @@ dim3 scatter_grid(const ScatterArgs& a) {
 
 }  // namespace
 
-cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, uint4* pairs, int32_t* n_pairs,
-                                 cudaStream_t st) {
+cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, unsigned long long* buckets, uint4* pairs,
+                                 int32_t* n_pairs, cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    k_scatter_count<<<scatter_grid(a), kThreads, 0, st>>>(a, count, pairs, n_pairs);
+    k_scatter_count<<<scatter_grid(a), kThreads, 0, st>>>(a, count, buckets, pairs, n_pairs);
     return cudaPeekAtLastError();
 }
 
@@ -604,14 +821,15 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
     return cudaPeekAtLastError();
 }
 
-cudaError_t launch_finalize(const int32_t* offsets, const unsigned long long* entries, int64_t n_vox, uint8_t* rec,
-                            uint16_t* npix, uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode,
-                            int bulk, unsigned long long* overflow, cudaStream_t st) {
+cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, const int32_t* offsets,
+                            const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
+                            uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
+                            unsigned long long* overflow, cudaStream_t st) {
     switch (K) {
-    case 4: return finalize_k<4>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
-    case 8: return finalize_k<8>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
-    case 12: return finalize_k<12>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
-    case 16: return finalize_k<16>(offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
+    case 4: return finalize_k<4>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
+    case 8: return finalize_k<8>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
+    case 12: return finalize_k<12>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
+    case 16: return finalize_k<16>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
     }
     return cudaErrorInvalidValue;
 }
