@@ -246,12 +246,19 @@ def make_grid(dims, spacing_mm, vol_to_world) -> dare_grid:
     return g
 
 
-def make_plane(width, height, px_mm, image_to_world) -> dare_plane:
-    p = dare_plane()
+def fill_plane(p, width, height, px_mm, image_to_world):
+    """Write a plane's size, spacing and pose into an existing dare_plane."""
+    T = np.ascontiguousarray(image_to_world, dtype=np.float64)
+    if T.size != 16:
+        raise ValueError("image_to_world must hold 16 values")
     p.width, p.height = int(width), int(height)
     p.px_mm[0], p.px_mm[1] = float(px_mm[0]), float(px_mm[1])
-    p.image_to_world = _mat16(image_to_world)
+    ctypes.memmove(ctypes.addressof(p.image_to_world), T.ctypes.data, 128)
     return p
+
+
+def make_plane(width, height, px_mm, image_to_world) -> dare_plane:
+    return fill_plane(dare_plane(), width, height, px_mm, image_to_world)
 
 
 def make_probe(kind=DARE_PROBE_LINEAR, apex_mm=(0.0, 0.0)) -> dare_probe:
@@ -532,7 +539,10 @@ class Session:
     def reslice(self, image_to_world, out, mask, px_mm, params=None, stream=None):
         """Reslice one plane into out (H, W) float32 and mask (H, ceil(W/32)) int32 device tensors."""
         H, W = (int(x) for x in out.shape)
-        pl = make_plane(W, H, px_mm, image_to_world)
+        pl = self.__dict__.get("_plane")
+        if pl is None:
+            pl = self._plane = dare_plane()  # reused: a session is driven by one thread at a time
+        fill_plane(pl, W, H, px_mm, image_to_world)
         p = params if params is not None else params_default()
         check(lib().dare_reslice(self._h, ctypes.byref(pl), ctypes.byref(p), _dev_ptr(out, "out"),
                                  _dev_ptr(mask, "mask", (H, mask_words(W))), _stream_ptr(stream)), "dare_reslice")

@@ -727,9 +727,37 @@ int tile_rows_for(const ResliceJob& j, const dare_params* p) {
     return tile_rows_fit(j, p->tile_rows ? p->tile_rows : kTileH);
 }
 
-// One plane's reslice launch on the path params choose.
+// Multiprocessors of the current device (queried once per device).
+int sm_count() {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+        cudaGetLastError();
+        return 148;
+    }
+    return sms[dev];
+}
+
+// A single plane's tile height for low latency: its tiles must spread over the
+// device (at least two per multiprocessor where 8 rows allow it) rather than
+// take one large tile per multiprocessor, so the automatic choice is capped at
+// the largest height that still gives that many tiles.
+int tile_rows_single(const ResliceJob& j, const dare_plane* pl, const dare_params* p) {
+    if (p->path == DARE_PATH_TILED_FIXED || p->tile_rows != 0) return tile_rows_for(j, p);
+    int cap = 8;
+    for (int th = kTileH; th > 8; th /= 2)
+        if (tiles_of(pl, th) >= 2 * sm_count()) {
+            cap = th;
+            break;
+        }
+    return tile_rows_fit(j, cap);
+}
+
+// One plane's reslice launch on the path params choose; after_table: the
+// plane's weight table was launched just before on `st`.
 cudaError_t launch_one(ResliceJob& job, const dare_plane* plane, const dare_params* params, int K, int dtype,
-                       int half_w, cudaStream_t st) {
+                       int half_w, int after_table, cudaStream_t st) {
     job.tile_base = 0;
     if (general_support(params)) {
         if (use_tiled(params)) {
@@ -747,12 +775,14 @@ cudaError_t launch_one(ResliceJob& job, const dare_plane* plane, const dare_para
         return launch_reslice_plain_r(nullptr, &job, 1, plane->width, plane->height, K, dtype, half_w, st);
     }
     if (use_tiled(params)) {
-        const int th = tile_rows_for(job, params);
+        const int th = tile_rows_single(job, plane, params);
         if (th > 0) {
             job.tile_h = th;
             g_tiled_planes += 1;
             KernelScope ks("reslice_tiled", st, 1);
-            return launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane, th), 0, K, dtype, half_w, st);
+            // while tracing, the event recorded between the two launches keeps them apart
+            return launch_reslice_tiled(nullptr, &job, 1, 0, tiles_of(plane, th), 0, K, dtype, half_w,
+                                        after_table && !g_trace_on.load(), st);
         }
         g_per_pixel_planes += 1;
     }
@@ -1135,7 +1165,8 @@ dare_status queue_batch(const dare_reslice_req* reqs, int32_t n, const dare_para
             } else {
                 KernelScope ks("reslice_tiled", st, 1);
                 CUDA_TRY(launch_reslice_tiled(rj_dev + k0, nullptr, k1 - k0, base, uniform ? per : end - base,
-                                              uniform ? 1 : 0, sg->K, sg->dtype, half_w, st));
+                                              uniform ? 1 : 0, sg->K, sg->dtype, half_w,
+                                              k0 == 0 && max_frames > 0 && !g_trace_on.load(), st));
             }
         } else {
             if (tiled) g_per_pixel_planes += k1 - k0;
@@ -1849,7 +1880,7 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
     ResliceJob job = make_job(s, plane, s->ws, out_dev, mask_dev, params->unassigned, params);
     const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
     L2Window l2((s->cfg.flags & DARE_SESSION_L2_PERSIST) ? s->rec : nullptr, size_t(s->n_vox) * s->rec_bytes, st);
-    CUDA_TRY(launch_one(job, plane, params, s->K, s->dtype, half_w, st));
+    CUDA_TRY(launch_one(job, plane, params, s->K, s->dtype, half_w, s->n_frames > 0, st));
     return session_end(s, st);
 }
 
@@ -2486,7 +2517,7 @@ dare_status reslice_with_table(dare_session s, const dare_plane* plane, const da
     ResliceJob job = make_job(s, plane, wtab, out_dev, mask_dev, params->unassigned, params);
     const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
     L2Window l2((s->cfg.flags & DARE_SESSION_L2_PERSIST) ? s->rec : nullptr, size_t(s->n_vox) * s->rec_bytes, st);
-    CUDA_TRY(launch_one(job, plane, params, s->K, s->dtype, half_w, st));
+    CUDA_TRY(launch_one(job, plane, params, s->K, s->dtype, half_w, s->n_frames > 0, st));
     return session_end(s, st);
 }
 

@@ -197,10 +197,12 @@ constexpr int kGeneralSmemCap = 200 << 10;  // dynamic shared memory of the gene
 constexpr int kTileW = 32;
 constexpr int kTiledColMax = 1024;
 constexpr int kTiledSlotMax = 4096;
-// uniform != 0: every job has n_tiles tiles (2-D grid, no job search)
+// uniform != 0: every job has n_tiles tiles (2-D grid, no job search); after_table != 0: the launch
+// directly follows the weight-table kernel on `st` and overlaps its set-up with it (programmatic
+// dependent launch; the kernel waits for the table before reading it)
 cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs,
                                  int tile_offset, int n_tiles, int uniform, int K, int dtype, int half_weights,
-                                 cudaStream_t st);
+                                 int after_table, cudaStream_t st);
 // Work queue of the persistent tiled kernel, in device memory: `total` tiles over the jobs'
 // tile_base ranges; `next` counts the tiles handed out beyond the first grid-size ones (0 at launch).
 struct TileQueue {

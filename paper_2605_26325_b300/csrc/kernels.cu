@@ -25,6 +25,9 @@ using namespace dev;
 
 __global__ void __launch_bounds__(256) k_weight_table(const TableJob* __restrict__ jobs,
                                                       const __grid_constant__ TableJob one, TableParams p) {
+    // a reslice launched after this kernel with programmatic serialization may
+    // start its set-up now; it waits for this grid's results before reading them
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
     const TableJob& J = jobs ? jobs[blockIdx.y] : one;
     const int n = J.n_frames;
     const double n0 = J.n_r[0], n1 = J.n_r[1], n2 = J.n_r[2];

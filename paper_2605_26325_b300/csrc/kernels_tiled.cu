@@ -296,6 +296,9 @@ __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_til
         tile_start(jobs ? jobs + job : &one, job, lt, sJob, T);
     }
     __syncthreads();
+    // launched with programmatic serialization after the weight-table kernel: its
+    // table is complete and visible from here (no effect on an ordinary launch)
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     tile_run<K, VT, WT>(sJob, T, sAB, sCol);
 }
 
@@ -347,7 +350,7 @@ int persistent_grid(F kernel) {
 // n_tiles: tiles of the whole launch, or per job when `uniform`; queue: persistent form.
 template <int K, typename VT, typename WT>
 cudaError_t tiled_launch(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                         int n_tiles, int uniform, TileQueue* queue, cudaStream_t st) {
+                         int n_tiles, int uniform, TileQueue* queue, int pdl, cudaStream_t st) {
     if (queue) {
         const int grid = persistent_grid(k_reslice_tiled_persistent<K, VT, WT>);
         if (grid <= 0) return cudaErrorInvalidValue;
@@ -356,31 +359,40 @@ cudaError_t tiled_launch(const ResliceJob* jobs_dev, const ResliceJob* one, int 
     }
     ResliceJob dummy{};
     const dim3 grid(n_tiles, (one || !uniform) ? 1 : n_jobs);
-    k_reslice_tiled<K, VT, WT><<<grid, kThreads, 0, st>>>(one ? nullptr : jobs_dev, n_jobs, tile_offset, uniform,
-                                                         one ? *one : dummy);
-    return cudaPeekAtLastError();
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(kThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, k_reslice_tiled<K, VT, WT>, one ? nullptr : jobs_dev, n_jobs, tile_offset, uniform,
+                              one ? *one : dummy);
 }
 
 template <int K, typename VT>
 cudaError_t tiled_launch_w(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                           int n_tiles, int uniform, TileQueue* queue, int half_w, cudaStream_t st) {
-    return half_w ? tiled_launch<K, VT, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, st)
-                  : tiled_launch<K, VT, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, st);
+                           int n_tiles, int uniform, TileQueue* queue, int half_w, int pdl, cudaStream_t st) {
+    return half_w ? tiled_launch<K, VT, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, pdl, st)
+                  : tiled_launch<K, VT, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, pdl, st);
 }
 
 template <int K>
 cudaError_t tiled_launch_k(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset,
-                           int n_tiles, int uniform, TileQueue* queue, int dtype, int half_w, cudaStream_t st) {
+                           int n_tiles, int uniform, TileQueue* queue, int dtype, int half_w, int pdl, cudaStream_t st) {
     switch (dtype) {
     case DARE_U8:
-        return tiled_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, st);
+        return tiled_launch_w<K, uint8_t>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, pdl, st);
     case DARE_F16:
-        return tiled_launch_w<K, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, st);
+        return tiled_launch_w<K, __half>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, pdl, st);
     case DARE_BF16:
         return tiled_launch_w<K, __nv_bfloat16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w,
-                                                st);
+                                                pdl, st);
     case DARE_F32:
-        return tiled_launch_w<K, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, st);
+        return tiled_launch_w<K, float>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, half_w, pdl, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -406,12 +418,12 @@ cudaError_t persistent_prepare_k(int dtype, int half_w) {
 }
 
 cudaError_t tiled_any(const ResliceJob* jobs_dev, const ResliceJob* one, int n_jobs, int tile_offset, int n_tiles,
-                      int uniform, TileQueue* queue, int K, int dtype, int hw, cudaStream_t st) {
+                      int uniform, TileQueue* queue, int K, int dtype, int hw, int pdl, cudaStream_t st) {
     switch (K) {
-    case 4: return tiled_launch_k<4>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, st);
-    case 8: return tiled_launch_k<8>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, st);
-    case 12: return tiled_launch_k<12>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, st);
-    case 16: return tiled_launch_k<16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, st);
+    case 4: return tiled_launch_k<4>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, pdl, st);
+    case 8: return tiled_launch_k<8>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, pdl, st);
+    case 12: return tiled_launch_k<12>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, pdl, st);
+    case 16: return tiled_launch_k<16>(jobs_dev, one, n_jobs, tile_offset, n_tiles, uniform, queue, dtype, hw, pdl, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -419,16 +431,18 @@ cudaError_t tiled_any(const ResliceJob* jobs_dev, const ResliceJob* one, int n_j
 }  // namespace
 
 cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int tile_offset,
-                                 int n_tiles, int uniform, int K, int dtype, int half_weights, cudaStream_t st) {
+                                 int n_tiles, int uniform, int K, int dtype, int half_weights, int after_table,
+                                 cudaStream_t st) {
     if (n_jobs <= 0 || n_tiles <= 0) return cudaSuccess;
-    return tiled_any(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, nullptr, K, dtype, half_weights, st);
+    return tiled_any(jobs_dev, one_job, n_jobs, tile_offset, n_tiles, uniform, nullptr, K, dtype, half_weights,
+                     after_table, st);
 }
 
 cudaError_t launch_reslice_tiled_persistent(const ResliceJob* jobs_dev, int n_jobs, TileQueue* queue, int K,
                                             int dtype, int half_weights, cudaStream_t st) {
     if (n_jobs <= 0) return cudaSuccess;
     if (!jobs_dev || !queue) return cudaErrorInvalidValue;
-    return tiled_any(jobs_dev, nullptr, n_jobs, 0, 0, 0, queue, K, dtype, half_weights, st);
+    return tiled_any(jobs_dev, nullptr, n_jobs, 0, 0, 0, queue, K, dtype, half_weights, 0, st);
 }
 
 cudaError_t prepare_reslice_tiled_persistent(int K, int dtype, int half_weights) {
