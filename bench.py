@@ -612,12 +612,20 @@ def _ncc(a, b):
 def quality(dare, torch, s, w, stream, params, n=16, fill=(2, 1)):
     """Median NCC and SSIM of DARE, of the scalar comparator and of the scalar
     comparator after hole filling (radius, min_neighbours = fill) against the
-    phantom rendered at n poses spread over the trajectory."""
+    phantom rendered at n poses spread over the trajectory: over every pixel
+    DARE and the unfilled comparator both cover, and over the specular pixels
+    among them -- where the phantom's direction-dependent echo, rendered alone
+    at the virtual pose (no speckle), is at least 10 of its 200 (dilated by
+    one pixel) -- which is where orientation weighting can differ from mean
+    compounding."""
+    import dataclasses
+
     import synth
-    from scipy.ndimage import binary_erosion
+    from scipy.ndimage import binary_dilation, binary_erosion
     W, H = w.out_w, w.out_h
     poses = w.reslice_poses[np.linspace(0, len(w.reslice_poses) - 1, n).astype(int)]
     gt = synth.render_frames(w.phantom, poses, W, H, *w.out_px).astype(np.float64)
+    spec = synth.render_frames(dataclasses.replace(w.phantom, sigma=0.0), poses, W, H, *w.out_px)
     out = torch.empty((H, W), dtype=torch.float32, device=stream.device)
     mask = torch.empty((H, dare.mask_words(W)), dtype=torch.int32, device=stream.device)
     torch.cuda.synchronize()
@@ -626,8 +634,8 @@ def quality(dare, torch, s, w, stream, params, n=16, fill=(2, 1)):
     torch.cuda.synchronize()
     fill_ms = (time.perf_counter() - t0) * 1e3
     names = ("dare", "scalar", "scalar_filled")
-    res = {k: {"ncc": [], "ssim": []} for k in names}
-    cover = []
+    res = {k: {"ncc": [], "ssim": [], "ncc_spec": [], "ssim_spec": []} for k in names}
+    cover, spec_share = [], []
     cov_each = {k: [] for k in names}
     for k, T in enumerate(poses):
         imgs = {}
@@ -645,22 +653,34 @@ def quality(dare, torch, s, w, stream, params, n=16, fill=(2, 1)):
         cover.append(float(both.mean()))
         if both.sum() < 1000:
             continue
+        sp = binary_dilation(spec[k] >= 10, np.ones((3, 3), bool)) & both
+        spec_share.append(float(sp.sum() / both.sum()))
         inner = binary_erosion(both, np.ones((7, 7), bool))
         for name, (img, _) in imgs.items():
             res[name]["ncc"].append(_ncc(img[both], gt[k][both]))
-            if inner.any():
-                res[name]["ssim"].append(float(_ssim_map(np.where(both, img, 0.0), np.where(both, gt[k], 0.0))[inner].mean()))
+            smap = _ssim_map(np.where(both, img, 0.0), np.where(both, gt[k], 0.0)) if inner.any() else None
+            if smap is not None:
+                res[name]["ssim"].append(float(smap[inner].mean()))
+            if sp.sum() >= 200:
+                res[name]["ncc_spec"].append(_ncc(img[sp], gt[k][sp]))
+                if smap is not None and (sp & inner).sum() >= 100:
+                    res[name]["ssim_spec"].append(float(smap[sp & inner].mean()))
     med = lambda xs: float(np.median(xs)) if xs else None
     return {"ncc_median": {k: med(v["ncc"]) for k, v in res.items()},
             "ssim_median": {k: med(v["ssim"]) for k, v in res.items()},
+            "specular": {"ncc_median": {k: med(v["ncc_spec"]) for k, v in res.items()},
+                         "ssim_median": {k: med(v["ssim_spec"]) for k, v in res.items()},
+                         "poses_scored": len(res["dare"]["ncc_spec"]),
+                         "share_of_covered_pixels_median": med(spec_share)},
             "poses": n, "scored": len(res["dare"]["ncc"]), "coverage_median": med(cover),
             "coverage_each_median": {k: med(v) for k, v in cov_each.items()},
             "hole_fill": {"radius_vox": fill[0], "min_neighbours": fill[1], "ms": fill_ms},
             "note": "ground truth: the phantom rendered at each virtual probe pose (speckle + specular echoes "
                     "that depend on the beam direction); scalar = mean compounding with trilinear interpolation, "
                     "scalar_filled = the same after hole filling (the PLUS baseline's configuration); scored over "
-                    "the pixels DARE and the unfilled comparator both cover; the paper's medians on its own data: "
-                    "SSIM 0.465 vs 0.430, NCC 0.376 vs 0.215 (DARE vs PLUS)"}
+                    "the pixels DARE and the unfilled comparator both cover, and over the specular ones among "
+                    "them; the paper's medians on its own data: SSIM 0.465 vs 0.430, NCC 0.376 vs 0.215 (DARE "
+                    "vs PLUS)"}
 
 
 def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, params, line, step, P, W, H):
@@ -1040,9 +1060,11 @@ def serving_leg(args, dist, duration, coalesce_us):
     tag_of = {}
     lat, ingest_lat, px_done, dropped = [], [], 0, 0
 
+    detail = []  # per request: latency, queue wait, on-stream time, batch, session (ms)
+
     def collect():
         nonlocal px_done
-        for tag, status, kind, t_sub, t_done in server.poll():
+        for tag, status, kind, t_sub, t_done, t_iss, nb, lane in server.poll():
             if status != dare.DARE_OK:
                 raise RuntimeError(f"request {tag} failed with status {status}")
             if kind == 1:
@@ -1051,6 +1073,7 @@ def serving_leg(args, dist, duration, coalesce_us):
             i, b = tag_of.pop(tag)
             free[i].append(b)
             lat.append((t_done - t_sub) * 1e3)
+            detail.append(((t_done - t_sub) * 1e3, (t_iss - t_sub) * 1e3, (t_done - t_iss) * 1e3, nb, i))
             px_done += meta[i]["size"] ** 2
 
     # untimed warm-up: every session's kernels once (CUDA loads kernels lazily on first launch) and one
@@ -1112,6 +1135,16 @@ def serving_leg(args, dist, duration, coalesce_us):
     st = server.stats()
     server.close()
     lat = np.asarray(lat)
+    det = np.asarray(detail) if detail else np.zeros((0, 5))
+    slow = det[det[:, 0] >= np.percentile(det[:, 0], 99.9)] if det.size else det
+    tail = {"requests": int(slow.shape[0]),
+            "queue_wait_ms_median": float(np.median(slow[:, 1])) if slow.size else None,
+            "on_stream_ms_median": float(np.median(slow[:, 2])) if slow.size else None,
+            "batch_median": float(np.median(slow[:, 3])) if slow.size else None,
+            "live_session_share": float(np.mean(slow[:, 4] < 2)) if slow.size else None,
+            "note": "requests at or above the p99.9 latency: time queued before the dispatcher issued them, time "
+                    "from issue to completion on their lane, their batch size, and the share that belongs to the "
+                    "two sessions ingesting live"}
     res = {"mpix_s": px_done / wall / 1e6 * dist.world, "duration_s": duration, "wall_s": wall,
            "requests": int(lat.size), "dropped_no_buffer": int(dropped),
            "latency_ms": {"p50": percentile(lat, 50), "p99": percentile(lat, 99), "p99.9": percentile(lat, 99.9),
@@ -1120,6 +1153,9 @@ def serving_leg(args, dist, duration, coalesce_us):
            if ingest_lat else None,
            "server": {k2: int(v) for k2, v in st.items()},
            "mean_batch": (st["completed"] - st["ingests"]) / max(st["batches"], 1),
+           "queue_wait_ms": {"p50": percentile(det[:, 1], 50), "p99": percentile(det[:, 1], 99)} if det.size else None,
+           "on_stream_ms": {"p50": percentile(det[:, 2], 50), "p99": percentile(det[:, 2], 99)} if det.size else None,
+           "tail": tail,
            "coalesce_us": coalesce_us, "lanes": 3, "max_batch": 64,
            "sessions": len(sessions), "rejected_by_budget": rejected, "budget_gb": 120,
            "device_gb_in_use": dare.memory_in_use() / 1e9,

@@ -476,9 +476,10 @@ typedef struct {
 } dare_plan_info;
 
 /* File (JSON object of "shape key": choice) that plan tuning reads now and
- * rewrites after each new choice; NULL or "" stops using a file.  A file that
- * cannot be read is treated as empty; DARE_E_INVALID if a later write fails
- * (reported by the dare_plan_create that tuned). */
+ * rewrites, with every choice known to the process, now and after each new
+ * choice; NULL or "" stops using a file.  A file that cannot be read is treated
+ * as empty; DARE_E_INVALID if it cannot be written (then, or later from the
+ * dare_plan_create that tuned).  Synchronous, host only. */
 dare_status dare_tune_cache_file(const char* path);
 
 dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare_params* params, void* stream,
@@ -533,6 +534,9 @@ typedef struct {
     int32_t kind;       /* 0 reslice, 1 ingest */
     double submit_s;    /* dare_clock_seconds at submission */
     double done_s;      /* dare_clock_seconds when its stream finished it */
+    double issue_s;     /* dare_clock_seconds when the dispatcher queued it on a stream */
+    int32_t batch;      /* requests in the batch it went out with (1 for an ingest) */
+    int32_t lane;       /* stream lane of that batch (-1 for an ingest) */
 } dare_completion;
 
 typedef struct {

@@ -113,7 +113,8 @@ class dare_server_config(ctypes.Structure):
 
 class dare_completion(ctypes.Structure):
     _fields_ = [("tag", ctypes.c_uint64), ("status", ctypes.c_int32), ("kind", ctypes.c_int32),
-                ("submit_s", ctypes.c_double), ("done_s", ctypes.c_double)]
+                ("submit_s", ctypes.c_double), ("done_s", ctypes.c_double), ("issue_s", ctypes.c_double),
+                ("batch", ctypes.c_int32), ("lane", ctypes.c_int32)]
 
 
 class dare_server_stats(ctypes.Structure):
@@ -698,8 +699,9 @@ class Server:
         arr = (dare_completion * capacity)()
         n = ctypes.c_int32()
         check(lib().dare_server_poll(self._h, arr, capacity, ctypes.byref(n)), "dare_server_poll")
-        out = [(arr[i].tag, arr[i].status, arr[i].kind, arr[i].submit_s, arr[i].done_s) for i in range(n.value)]
-        for t, _, kind, _, _ in out:
+        out = [(arr[i].tag, arr[i].status, arr[i].kind, arr[i].submit_s, arr[i].done_s, arr[i].issue_s,
+                arr[i].batch, arr[i].lane) for i in range(n.value)]
+        for t, _, kind, *_ in out:
             if kind == 1:
                 self._keep.pop(t, None)
         return out

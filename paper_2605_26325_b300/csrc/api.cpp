@@ -2773,7 +2773,9 @@ extern "C" {
 dare_status dare_tune_cache_file(const char* path) {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     g_tune_file = path ? path : "";
-    if (!g_tune_file.empty()) tune_file_load(g_tune_file);
+    if (g_tune_file.empty()) return DARE_OK;
+    tune_file_load(g_tune_file);
+    if (!tune_file_save()) return fail(DARE_E_INVALID, "cannot write the tuning file %s", g_tune_file.c_str());
     return DARE_OK;
 }
 

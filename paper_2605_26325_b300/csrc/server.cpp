@@ -88,6 +88,8 @@ struct DoneBatch {
     std::vector<std::pair<uint64_t, double>> items;  // tag, submit time
     int32_t kind;
     int32_t status;
+    double issue_s = 0.0;
+    int32_t lane = -1;
 };
 
 void CUDART_CB on_done(void* p) {
@@ -95,7 +97,9 @@ void CUDART_CB on_done(void* p) {
     const double t = now_s();
     {
         std::lock_guard<std::mutex> lk(d->sv->done_mu);
-        for (auto& it : d->items) d->sv->done.push_back({it.first, d->status, d->kind, it.second, t});
+        for (auto& it : d->items)
+            d->sv->done.push_back({it.first, d->status, d->kind, it.second, t, d->issue_s,
+                                   static_cast<int32_t>(d->items.size()), d->lane});
         d->sv->stats.completed += static_cast<int64_t>(d->items.size());
     }
     {
@@ -132,6 +136,8 @@ dare_status lane_alloc(dare_server_s::Lane& L, size_t ws_need, size_t pin_need) 
 
 void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& batch) {
     auto* d = new DoneBatch{sv, {}, 0, DARE_OK};
+    d->issue_s = now_s();
+    d->lane = static_cast<int32_t>(&L - sv->lanes.data());
     std::vector<dare_reslice_req> reqs;
     reqs.reserve(batch.size());
     for (auto& p : batch) {
@@ -169,6 +175,7 @@ void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& b
 
 void run_ingest(dare_server sv, Ingest& g) {
     auto* d = new DoneBatch{sv, {{g.tag, g.submit_s}}, 1, DARE_OK};
+    d->issue_s = now_s();
     for (auto& L : sv->lanes)
         if (L.busy) cudaStreamWaitEvent(sv->ingest_st, L.ev, 0);
     dare_status rc = dare_build_volume(g.s, g.frames, g.n, g.w, g.h, g.px, g.poses.data(), sv->ingest_st);

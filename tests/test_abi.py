@@ -131,3 +131,19 @@ def test_argument_errors_without_a_device():
     assert lib.dare_set_memory_budget(-1) == dare.DARE_E_INVALID
     with pytest.raises(dare.DareError):
         dare.check(dare.DARE_E_INVALID, "x")
+
+
+def test_tune_cache_file_host_side(tmp_path):
+    """dare_tune_cache_file (host only): the file is written at once as a JSON
+    object of the choices known to the process; a path that cannot be written
+    is refused; None stops using a file."""
+    import json
+    path = tmp_path / "tune.json"
+    path.write_text('{"sm148 t3 K12 w0 px2^20 n2^4 pitch4 l20 f2^11": 32, "broken": "x"}')
+    dare.tune_cache_file(str(path))
+    got = json.loads(path.read_text())
+    assert got.get("sm148 t3 K12 w0 px2^20 n2^4 pitch4 l20 f2^11") == 32 and "broken" not in got
+    with pytest.raises(dare.DareError) as ei:
+        dare.tune_cache_file(str(tmp_path / "no_such_dir" / "tune.json"))
+    assert ei.value.status == dare.DARE_E_INVALID
+    dare.tune_cache_file(None)

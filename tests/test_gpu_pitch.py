@@ -189,3 +189,49 @@ def test_plan_per_pixel_planes(tiny, vols):
         ref, rm = oracle.reslice(vol, T, W, H, px, ora_params(p))
         assert_parity(out.cpu().numpy(), mask.cpu().numpy(), ref, rm, W)
     plan.close()
+
+
+def test_tuning_choices_persist_in_a_file(tiny, vols, tmp_path):
+    """Plan tuning writes its choice per shape to the JSON file named by
+    dare_tune_cache_file; a later plan of the same shape takes the choice from
+    the file (here edited to the plain kernel) without timing anything, and its
+    replay still equals dare_reslice."""
+    import json
+    s, _ = vols
+    path = tmp_path / "tune.json"
+    px = 0.5 * H_VOX
+    W, H = 96, 80
+    items = []
+    for k in range(3):
+        T = synth.plane_pose_centred(synth.probe_rotation(30.0 + 3 * k), np.array([0.0, 0.3 * k, 0.0]), W, H, px, px)
+        out, mask = new_outputs(W, H)
+        items.append((s, T, out, mask, (px, px)))
+    dare.tune_cache_file(str(path))  # writes the choices known so far
+    try:
+        before = json.loads(path.read_text())
+        plan = dare.Plan(items, dare.params_default(path=dare.DARE_PATH_AUTO))
+        info = plan.info()
+        plan.close()
+        assert all(t > 0 for t in info["tune_ms"][0])  # a shape no other test uses: timed now
+        saved = json.loads(path.read_text())
+        new_keys = set(saved) - set(before)
+        assert len(new_keys) == 1
+        key = new_keys.pop()
+        assert saved[key] == info["choice"][0] in (0, 16, 32, 64)
+        saved[key] = 0 if info["choice"][0] != 0 else 32
+        path.write_text(json.dumps(saved))
+        dare.tune_cache_file(str(path))  # reload
+        plan = dare.Plan(items, dare.params_default(path=dare.DARE_PATH_AUTO))
+        info2 = plan.info()
+        assert info2["choice"][0] == saved[key] and not any(t > 0 for t in info2["tune_ms"][0])
+        plan.launch()
+        torch.cuda.synchronize()
+        for (_, T, out, mask, _) in items:
+            o1, m1 = gpu_reslice(s, T, W, H, (px, px), dare.params_default())
+            assert np.array_equal(mask.cpu().numpy(), m1)
+            cov = dare.unpack_mask(m1, W).astype(bool)
+            got = out.cpu().numpy()
+            assert np.all(np.abs(got[cov] - o1[cov]) <= 1e-5 * np.maximum(np.abs(o1[cov]), 1))
+        plan.close()
+    finally:
+        dare.tune_cache_file(None)
