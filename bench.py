@@ -1137,7 +1137,10 @@ def serving_leg(args, dist, duration, coalesce_us):
     lat = np.asarray(lat)
     det = np.asarray(detail) if detail else np.zeros((0, 5))
     slow = det[det[:, 0] >= np.percentile(det[:, 0], 99.9)] if det.size else det
+    worst = det[np.argsort(det[:, 0])[-8:][::-1]] if det.size else det
     tail = {"requests": int(slow.shape[0]),
+            "worst": [{"latency_ms": float(r[0]), "queue_wait_ms": float(r[1]), "on_stream_ms": float(r[2]),
+                       "batch": int(r[3]), "session": int(r[4])} for r in worst],
             "queue_wait_ms_median": float(np.median(slow[:, 1])) if slow.size else None,
             "on_stream_ms_median": float(np.median(slow[:, 2])) if slow.size else None,
             "batch_median": float(np.median(slow[:, 3])) if slow.size else None,

@@ -502,7 +502,9 @@ dare_status dare_plan_destroy(dare_plan p);
  * latency); an ingest queued behind it, or a stop, issues it at once.  A batch
  * waits only for the ingests of the sessions it reads; an ingest waits for
  * the reslices in flight, then runs dare_build_volume on the server's ingest
- * stream.  Every result equals dare_reslice of that request against the
+ * stream, which has the device's lowest stream priority (the lanes the
+ * highest), so a build does not hold up the reslices that follow it on other
+ * sessions.  Every result equals dare_reslice of that request against the
  * volume as of its submission.  Completions are stamped by a host callback on
  * the stream that finishes them, on the clock of dare_clock_seconds.
  *

@@ -103,18 +103,29 @@ struct TileSetup {
     int O1, O2, Od;          // integer parts, relative to the box (clamped far outside when irrelevant)
 };
 
+// Per-tile set-up by the 32 lanes of warp 0: lanes 0-11 take the fixed-point
+// coordinate of one (corner, axis) and lanes 12-14 the tile origin's on one
+// axis, in parallel; lanes 0-2 reduce their axis over the four corners; lane 0
+// writes the result.
 template <int D>
 __device__ void tile_setup(const ResliceJob& J, int u0, int v0, int u1, int v1, TileSetup& T) {
     constexpr int E1 = Axes<D>::E1, E2 = Axes<D>::E2;
-    int64_t lo1 = INT64_MAX, hi1 = INT64_MIN, lo2 = INT64_MAX, hi2 = INT64_MIN, lod = INT64_MAX, hid = INT64_MIN;
-    for (int k = 0; k < 4; ++k) {
-        const int u = (k & 1) ? u1 : u0, v = (k & 2) ? v1 : v0;
-        const int64_t f1 = axis_fix(J, E1, u, v) >> kFixBits, f2 = axis_fix(J, E2, u, v) >> kFixBits;
-        const int64_t fd = axis_fix(J, D, u, v) >> kFixBits;
-        lo1 = lmin(lo1, f1); hi1 = lmax(hi1, f1);
-        lo2 = lmin(lo2, f2); hi2 = lmax(hi2, f2);
-        lod = lmin(lod, fd); hid = lmax(hid, fd);
-    }
+    const int lane = threadIdx.x & 31;
+    const int ai = lane < 12 ? lane % 3 : lane - 12;  // 0: e1, 1: e2, 2: d
+    const int ax = ai == 0 ? E1 : (ai == 1 ? E2 : D);
+    const int k = lane / 3;
+    const int u = lane < 12 ? ((k & 1) ? u1 : u0) : u0, v = lane < 12 ? ((k & 2) ? v1 : v0) : v0;
+    const int64_t G = lane < 15 ? axis_fix(J, ax < 3 ? ax : 0, u, v) : 0;
+    const int64_t f = G >> kFixBits;
+    const int64_t f3 = __shfl_down_sync(0xFFFFFFFFu, f, 3), f6 = __shfl_down_sync(0xFFFFFFFFu, f, 6);
+    const int64_t f9 = __shfl_down_sync(0xFFFFFFFFu, f, 9);
+    const int64_t lo = lmin(lmin(f, f3), lmin(f6, f9)), hi = lmax(lmax(f, f3), lmax(f6, f9));  // lanes 0-2
+    const int64_t lo1 = __shfl_sync(0xFFFFFFFFu, lo, 0), hi1 = __shfl_sync(0xFFFFFFFFu, hi, 0);
+    const int64_t lo2 = __shfl_sync(0xFFFFFFFFu, lo, 1), hi2 = __shfl_sync(0xFFFFFFFFu, hi, 1);
+    const int64_t lod = __shfl_sync(0xFFFFFFFFu, lo, 2), hid = __shfl_sync(0xFFFFFFFFu, hi, 2);
+    const int64_t G1 = __shfl_sync(0xFFFFFFFFu, G, 12), G2 = __shfl_sync(0xFFFFFFFFu, G, 13);
+    const int64_t Gd = __shfl_sync(0xFFFFFFFFu, G, 14);
+    if (lane != 0) return;
     // a pixel reads floors f .. f + 1 on each axis; when on some axis that
     // range misses the grid for every pixel of the tile, the tile is unassigned
     T.empty = hi1 + 1 < 0 || lo1 > J.dims[E1] - 1 || hi2 + 1 < 0 || lo2 > J.dims[E2] - 1 || hid + 1 < 0 ||
@@ -129,7 +140,6 @@ __device__ void tile_setup(const ResliceJob& J, int u0, int v0, int u1, int v1, 
     T.b2 = static_cast<int>(lmax(lmin(lo2, 1 << 30), -(1 << 30)));
     T.n1 = T.direct || T.empty ? 0 : static_cast<int>(n1);
     T.n2 = T.direct || T.empty ? 0 : static_cast<int>(n2);
-    const int64_t G1 = axis_fix(J, E1, u0, v0), G2 = axis_fix(J, E2, u0, v0), Gd = axis_fix(J, D, u0, v0);
     T.R1 = static_cast<int>(G1 & (kFixOne - 1));
     T.R2 = static_cast<int>(G2 & (kFixOne - 1));
     T.Rd = static_cast<int>(Gd & (kFixOne - 1));
@@ -240,27 +250,30 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
 }
 
 // Warp 0: copy the tile's job into shared memory (one coalesced pass), then
-// thread 0 sets the tile up; lt is the tile's index within its job.
+// set the tile up (all 32 lanes); lt is the tile's index within its job.
 __device__ __forceinline__ void tile_start(const ResliceJob* src, int job, int lt, ResliceJob& sJob, TileSetup& T) {
     static_assert(sizeof(ResliceJob) % 4 == 0, "job copied as 32-bit words");
     const uint32_t* s32 = reinterpret_cast<const uint32_t*>(src);
     uint32_t* d32 = reinterpret_cast<uint32_t*>(&sJob);
     for (int i = threadIdx.x; i < static_cast<int>(sizeof(ResliceJob) / 4); i += 32) d32[i] = s32[i];
     __syncwarp();
+    const ResliceJob& J0 = sJob;
+    const int th = J0.tile_h;
+    const int ty = lt / J0.tiles_x, tx = lt - ty * J0.tiles_x;
+    const int u0 = tx * kTileW, v0 = ty * th;
+    const int u1 = min(u0 + kTileW, J0.width) - 1, v1 = min(v0 + th, J0.height) - 1;
     if (threadIdx.x == 0) {
-        const ResliceJob& J0 = sJob;
-        const int th = J0.tile_h;
         T.job = job;
-        const int ty = lt / J0.tiles_x, tx = lt - ty * J0.tiles_x;
-        T.u0 = tx * kTileW;
-        T.v0 = ty * th;
-        T.u1 = min(T.u0 + kTileW, J0.width) - 1;
-        T.v1 = min(T.v0 + th, J0.height) - 1;
-        if (J0.d == 0) tile_setup<0>(J0, T.u0, T.v0, T.u1, T.v1, T);
-        else if (J0.d == 1) tile_setup<1>(J0, T.u0, T.v0, T.u1, T.v1, T);
-        else tile_setup<2>(J0, T.u0, T.v0, T.u1, T.v1, T);
-        if (T.direct && !J0.direct) atomicAdd(&g_fallback_tiles, 1ull);
+        T.u0 = u0;
+        T.v0 = v0;
+        T.u1 = u1;
+        T.v1 = v1;
     }
+    const int d = J0.d;  // warp-uniform
+    if (d == 0) tile_setup<0>(J0, u0, v0, u1, v1, T);
+    else if (d == 1) tile_setup<1>(J0, u0, v0, u1, v1, T);
+    else tile_setup<2>(J0, u0, v0, u1, v1, T);
+    if (threadIdx.x == 0 && T.direct && !J0.direct) atomicAdd(&g_fallback_tiles, 1ull);
 }
 
 template <int K, typename VT, typename WT>

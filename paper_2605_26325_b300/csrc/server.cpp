@@ -299,9 +299,16 @@ dare_status dare_server_create(const dare_server_config* cfg, dare_server* out) 
     sv->cfg = c;
     sv->stats.lanes = c.lanes;
     sv->lanes.resize(c.lanes);
-    bool ok = cudaStreamCreateWithFlags(&sv->ingest_st, cudaStreamNonBlocking) == cudaSuccess;
+    // reslices outrank ingestion: the block scheduler starts a lane's waiting CTAs
+    // before the ingest's, so a large build does not hold up preview requests
+    int prio_low = 0, prio_high = 0;
+    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
+        cudaGetLastError();
+        prio_low = prio_high = 0;
+    }
+    bool ok = cudaStreamCreateWithPriority(&sv->ingest_st, cudaStreamNonBlocking, prio_low) == cudaSuccess;
     for (auto& L : sv->lanes) {
-        ok = ok && cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithPriority(&L.st, cudaStreamNonBlocking, prio_high) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) == cudaSuccess;
     }
     dare_status arc = DARE_OK;
