@@ -502,11 +502,12 @@ dare_status dare_plan_destroy(dare_plan p);
  * latency); an ingest queued behind it, or a stop, issues it at once.  A batch
  * waits only for the ingests of the sessions it reads; an ingest waits for
  * the reslices in flight, then runs dare_build_volume on the server's ingest
- * stream, which has the device's lowest stream priority (the lanes the
- * highest), so a build does not hold up the reslices that follow it on other
- * sessions.  Every result equals dare_reslice of that request against the
- * volume as of its submission.  Completions are stamped by a host callback on
- * the stream that finishes them, on the clock of dare_clock_seconds.
+ * stream; requests of a session whose ingest is still running go out in a
+ * batch of their own, so an ingest holds up only its own session's requests.
+ * Every result equals dare_reslice of that request against the
+ * volume as of its submission.  The dispatcher thread completes requests when
+ * it sees their stream reach them (no host callbacks on the lanes), on the
+ * clock of dare_clock_seconds.
  *
  * Sessions given to a server must be idle (dare_session_sync) and must not be
  * used outside the server until dare_server_drain returns.  frames_dev of an
@@ -535,7 +536,8 @@ typedef struct {
     int32_t status;     /* dare_status of the request */
     int32_t kind;       /* 0 reslice, 1 ingest */
     double submit_s;    /* dare_clock_seconds at submission */
-    double done_s;      /* dare_clock_seconds when its stream finished it */
+    double done_s;      /* dare_clock_seconds when the dispatcher saw its stream finish it (it polls
+                           every 20 us while work is in flight) */
     double issue_s;     /* dare_clock_seconds when the dispatcher queued it on a stream */
     int32_t batch;      /* requests in the batch it went out with (1 for an ingest) */
     int32_t lane;       /* stream lane of that batch (-1 for an ingest) */

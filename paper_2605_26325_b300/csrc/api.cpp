@@ -1571,8 +1571,16 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     const size_t o_bk = align_up(o_ent + size_t(n_chunk) * npx * 8, 256);
     const size_t o_pairs = align_up(o_bk + size_t(s->n_vox) * kBucket * 8, 256);
     const size_t o_np = align_up(o_pairs + size_t(n_chunk) * slots_pf * 16, 256);
+    // appends that reach few voxels (a chunk of fewer pixels than a quarter of the
+    // grid's voxels) list the voxels they touch and finalize only those: touched
+    // list, voxel -> list position, list overflow counts, list length
+    const int64_t max_t = std::min<int64_t>(s->n_vox, int64_t(n_chunk) * npx);
     const size_t o_aff = align_up(o_np + size_t(n_chunk) * tiles_pf * 4, 256);
-    const size_t ws_need = align_up(o_aff + size_t(n) * 9 * 8, 256);
+    const size_t o_tl = align_up(o_aff + size_t(n) * 9 * 8, 256);
+    const size_t o_ti = align_up(o_tl + size_t(max_t) * 4, 256);
+    const size_t o_tc = align_up(o_ti + size_t(s->n_vox) * 4, 256);
+    const size_t o_tn = align_up(o_tc + size_t(max_t) * 4, 256);
+    const size_t ws_need = align_up(o_tn + 16, 256);
     // upload slices (host frames): about 32 MB each unless given
     const int32_t slice = !host ? 0
                                 : static_cast<int32_t>(std::min<int64_t>(
@@ -1599,6 +1607,10 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     auto* pairs = reinterpret_cast<uint4*>(ws + o_pairs);
     auto* n_pairs = reinterpret_cast<int32_t*>(ws + o_np);
     int64_t* aff_dev = reinterpret_cast<int64_t*>(ws + o_aff);
+    int32_t* t_list = reinterpret_cast<int32_t*>(ws + o_tl);
+    int32_t* t_index = reinterpret_cast<int32_t*>(ws + o_ti);
+    int32_t* t_ovf = reinterpret_cast<int32_t*>(ws + o_tc);
+    int32_t* t_n = reinterpret_cast<int32_t*>(ws + o_tn);
     uint8_t* pin = static_cast<uint8_t*>(s->pinned[0]);
     const size_t p_rot = aff.size() * 8, p_geo = p_rot + rot.size() * 8, p_off = p_geo + grow.size() * 4;
     std::memcpy(pin, aff.data(), aff.size() * 8);
@@ -1628,9 +1640,15 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
         for (int32_t f = c0; f < c0 + nc; ++f)
             for (int k = 3; k < 9; ++k)
                 if (std::llabs(aff[9 * size_t(f) + k]) >= (int64_t(1) << 25)) a.small_steps = 0;
+        const int mode = s->pending_clear ? 2 : (s->fresh ? 1 : 0);
+        const bool listed = mode != 2 && int64_t(nc) * npx * 4 < s->n_vox;
+        int32_t* tl = listed ? t_list : nullptr;
+        int32_t* ti = listed ? t_index : nullptr;
+        int32_t* tn = listed ? t_n : nullptr;
+        if (listed) CUDA_TRY(cudaMemsetAsync(t_n, 0, sizeof(int32_t), st));
         if (!host) {
             KernelScope ks("scatter_count", st, 1);
-            CUDA_TRY(launch_scatter_count(a, s->count, buckets, pairs, n_pairs, st));
+            CUDA_TRY(launch_scatter_count(a, s->count, buckets, pairs, n_pairs, tl, ti, tn, st));
         } else {
             for (int32_t j0 = 0, k = 0; j0 < nc; j0 += slice, ++k) {
                 const int b = k & 1;
@@ -1650,30 +1668,33 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                 sa.tile_base = int64_t(j0) * tiles_pf;
                 {
                     KernelScope ks("scatter_count", st, 1);
-                    CUDA_TRY(launch_scatter_count(sa, s->count, buckets, pairs, n_pairs, st));
+                    CUDA_TRY(launch_scatter_count(sa, s->count, buckets, pairs, n_pairs, tl, ti, tn, st));
                 }
                 CUDA_TRY(cudaEventRecord(s->ring_free[b], st));
             }
         }
-        {
+        if (listed) {
+            KernelScope ks("exclusive_scan", st, 4);
+            CUDA_TRY(launch_touched_overflow(s->count, t_list, t_n, max_t, t_ovf, st));
+            CUDA_TRY(launch_exclusive_scan(t_ovf, offsets, max_t, bsums, nbs, 0, st));
+        } else {
             KernelScope ks("exclusive_scan", st, 3);
             CUDA_TRY(launch_exclusive_scan(s->count, offsets, s->n_vox, bsums, nbs, kBucket, st));
         }
         {
             KernelScope ks("scatter_place", st, 1);
-            CUDA_TRY(launch_scatter_place(a, pairs, n_pairs, s->count, offsets, entries, st));
+            CUDA_TRY(launch_scatter_place(a, pairs, n_pairs, s->count, offsets, ti, entries, st));
         }
         {
             if (c0 == 0) {
                 rc = invalidate_cache(s, st);  // the records are about to change
                 if (rc != DARE_OK) return rc;
             }
-            const int mode = s->pending_clear ? 2 : (s->fresh ? 1 : 0);
-            s->pending_clear = false;  // this finalize writes every voxel
+            s->pending_clear = false;  // a full-write finalize (mode 2) writes every voxel
             s->fresh = false;          // from here on the records may hold samples
             KernelScope ks("finalize", st, 1);
             CUDA_TRY(launch_finalize(s->count, buckets, offsets, entries, s->n_vox, s->rec, s->npix, s->ssum, s->scnt,
-                                     s->K, s->dtype, mode, s->host_vol ? 0 : 1, s->overflow_dev, st));
+                                     s->K, s->dtype, mode, s->host_vol ? 0 : 1, s->overflow_dev, tl, tn, max_t, st));
         }
     }
     rc = session_end(s, st);

@@ -129,12 +129,19 @@ cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* o
 // count: per-voxel entry counters (zero on entry; finalize returns them to zero); buckets: kBucket
 // 8-byte entries per voxel; pairs: kTile^2 16-byte (voxel, entry) overflow pairs per 32 x 32 frame
 // tile; n_pairs: overflow pairs per tile
+// touched (optional): voxels reached for the first time are listed, touched[i] = v and tindex[v] = i
+// for i < *n_touched (zero on entry)
 cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, unsigned long long* buckets, uint4* pairs,
-                                 int32_t* n_pairs, cudaStream_t st);
-// overflow pairs into their voxels' ranges (offsets: scan of max(count - kBucket, 0)); leaves
-// min(count, kBucket) in the counters
+                                 int32_t* n_pairs, int32_t* touched, int32_t* tindex, int32_t* n_touched,
+                                 cudaStream_t st);
+// ovf_cnt[i] = max(count[touched[i]] - kBucket, 0) for i < *n_touched, 0 up to max_t
+cudaError_t launch_touched_overflow(const int32_t* count, const int32_t* touched, const int32_t* n_touched,
+                                    int64_t max_t, int32_t* ovf_cnt, cudaStream_t st);
+// overflow pairs into their voxels' ranges (offsets: scan of the overflow counts by voxel, or by
+// touched-list position when tindex is given); leaves min(count, kBucket) in the counters
 cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const int32_t* n_pairs, int32_t* count,
-                                 const int32_t* offsets, unsigned long long* entries, cudaStream_t st);
+                                 const int32_t* offsets, const int32_t* tindex, unsigned long long* entries,
+                                 cudaStream_t st);
 // out[i] = sum_{j < i} max(in[j] - bias, 0), out[n] the total
 cudaError_t launch_exclusive_scan(const int32_t* in, int32_t* out, int64_t n, int32_t* block_sums,
                                   int64_t block_sums_len, int bias, cudaStream_t st);
@@ -145,10 +152,12 @@ int64_t scan_block_sums_needed(int64_t n);
 // bulk: records and npix in device memory, so mode 2 may store whole runs with bulk copies
 // a voxel's entries: count[v] (<= kBucket) in its bucket, then entries[offsets[v], offsets[v + 1]);
 // count is returned to zero
+// touched / n_touched (modes 0 and 1): only the listed voxels, offsets by list position, at most max_t
 cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, const int32_t* offsets,
                             const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
                             uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
-                            unsigned long long* overflow, cudaStream_t st);
+                            unsigned long long* overflow, const int32_t* touched, const int32_t* n_touched,
+                            int64_t max_t, cudaStream_t st);
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
                                   cudaStream_t st);
 cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned long long* count, cudaStream_t st);

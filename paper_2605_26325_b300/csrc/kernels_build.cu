@@ -174,9 +174,10 @@ __device__ void tile_box(const int64_t* aff, const int* dims, int u0, int v0, in
 // Up to four (voxel, entry) results per thread and round: counter slots are
 // taken with four returning atomics in flight; the first kBucket entries of a
 // voxel go to its bucket (kBucket consecutive entries per voxel), later ones to
-// the tile's overflow region.
+// the tile's overflow region.  With s_new, a voxel whose first entry this is
+// (slot 0) is also listed as touched by this build.
 __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long long (&e)[4], int32_t* count,
-                                      unsigned long long* buckets, uint4* ovf, int* n_ovf) {
+                                      unsigned long long* buckets, uint4* ovf, int* n_ovf, int* s_new, int* s_n_new) {
     int slot[4];
 #pragma unroll
     for (int j = 0; j < 4; ++j) slot[j] = vi[j] >= 0 ? atomicAdd(count + vi[j], 1) : 0;
@@ -185,6 +186,7 @@ __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long lo
         if (vi[j] < 0) continue;
         if (slot[j] < kBucket) {
             buckets[static_cast<int64_t>(vi[j]) * kBucket + slot[j]] = e[j];
+            if (s_new && slot[j] == 0) s_new[atomicAdd(s_n_new, 1)] = vi[j];  // one per distinct voxel of the tile
         } else {
             const int k = atomicAdd(n_ovf, 1);  // at most one pair per pixel of the tile
             ovf[k] = make_uint4(static_cast<unsigned>(vi[j]), 0u, static_cast<unsigned>(e[j]),
@@ -196,15 +198,20 @@ __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long lo
 // One CTA per 32 x 32 frame tile (blockIdx.y = frame): per-voxel sums of the
 // tile's pixels, then one (voxel, entry) per distinct voxel, entry = frame id
 // << 48 | npix << 32 | sum.  Tile t owns pairs[t * kTile^2, ...) for its
-// overflow pairs and n_pairs[t] says how many it wrote.
+// overflow pairs and n_pairs[t] says how many it wrote.  With `touched`, the
+// voxels this build reaches for the first time are listed: touched[i], and
+// tindex[v] = i, i < *n_touched.
 __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_count(const __grid_constant__ ScatterArgs A,
                                                             int32_t* __restrict__ count,
                                                             unsigned long long* __restrict__ buckets,
-                                                            uint4* __restrict__ pairs, int32_t* __restrict__ n_pairs) {
+                                                            uint4* __restrict__ pairs, int32_t* __restrict__ n_pairs,
+                                                            int32_t* __restrict__ touched, int32_t* __restrict__ tindex,
+                                                            int32_t* __restrict__ n_touched) {
     __shared__ __align__(16) unsigned smem[kSmemWords];
     __shared__ int64_t aff[9];
     __shared__ TileBox B;
-    __shared__ int n_list, n_ovf;
+    __shared__ int n_list, n_ovf, n_new, new_base;
+    __shared__ int s_new[kTile * kTile];  // voxels whose first entry this tile made
     const int tiles_x = (A.width + kTile - 1) / kTile;
     const int f = blockIdx.y;
     const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
@@ -215,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
         tile_box(aff, A.dims, u0, v0, min(u0 + kTile, A.width) - 1, min(v0 + kTile, A.height) - 1, B);
         n_list = 0;
         n_ovf = 0;
+        n_new = 0;
     }
     __syncthreads();
     const int cells = B.cells;
@@ -254,7 +262,7 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
                     e[j] = fid | (static_cast<unsigned long long>(x >> kPackShift) << 32) | (x & ((1u << kPackShift) - 1));
                 }
             }
-            emit4(vi, e, count, buckets, ovf, &n_ovf);
+            emit4(vi, e, count, buckets, ovf, &n_ovf, touched ? s_new : nullptr, &n_new);
         }
     } else {
         // hash table over voxel indices
@@ -289,20 +297,45 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
                     e[j] = fid | (static_cast<unsigned long long>(npx[h]) << 32) | sums[h];
                 }
             }
-            emit4(vi, e, count, buckets, ovf, &n_ovf);
+            emit4(vi, e, count, buckets, ovf, &n_ovf, touched ? s_new : nullptr, &n_new);
         }
     }
     __syncthreads();
-    if (threadIdx.x == 0) n_pairs[tile] = n_ovf;
+    if (threadIdx.x == 0) {
+        n_pairs[tile] = n_ovf;
+        if (touched) new_base = n_new ? atomicAdd(n_touched, n_new) : 0;
+    }
+    if (touched) {
+        __syncthreads();
+        for (int k = threadIdx.x; k < n_new; k += kThreads) {
+            const int v = s_new[k];
+            touched[new_base + k] = v;
+            tindex[v] = new_base + k;
+        }
+    }
+}
+
+// Overflow counts of the touched voxels, max(count - kBucket, 0), in list order;
+// zeros from *n_touched up to max_t (the scan that follows covers max_t).
+__global__ void __launch_bounds__(256) k_touched_overflow(const int32_t* __restrict__ count,
+                                                          const int32_t* __restrict__ touched,
+                                                          const int32_t* __restrict__ n_touched, int64_t max_t,
+                                                          int32_t* __restrict__ ovf_cnt) {
+    const int64_t n = *n_touched;
+    for (int64_t i = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; i < max_t;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        ovf_cnt[i] = i < n ? max(count[touched[i]] - kBucket, 0) : 0;
 }
 
 // Overflow pairs (entries of a voxel beyond its bucket): one CTA per tile
-// region; each pair takes a position in its voxel's overflow range from the
-// voxel's counter, which counts back down to kBucket.  Regions go tile
+// region; each pair takes a position in its voxel's overflow range (by voxel,
+// or by its place in the touched list with tindex) from the voxel's counter,
+// which counts back down to kBucket.  Regions go tile
 // position first: consecutive CTAs take the same tile of consecutive frames.
 __global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__ pairs,
                                                        const int32_t* __restrict__ n_pairs,
                                                        int32_t* __restrict__ count, const int32_t* __restrict__ offsets,
+                                                       const int32_t* __restrict__ tindex,
                                                        unsigned long long* __restrict__ entries, int n_frames) {
     const int64_t tiles_pf = gridDim.x / n_frames;  // the grid is n_frames x tiles_pf regions
     const int64_t tt = blockIdx.x / n_frames, f = blockIdx.x - tt * n_frames;
@@ -312,7 +345,7 @@ __global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__
     const uint4* in = pairs + tile * (kTile * kTile);
     for (int i = threadIdx.x; i < n; i += 256) {
         const uint4 p = __ldg(in + i);
-        const int pos = offsets[p.x] + atomicSub(count + p.x, 1) - 1 - kBucket;
+        const int pos = offsets[tindex ? tindex[p.x] : p.x] + atomicSub(count + p.x, 1) - 1 - kBucket;
         entries[pos] = (static_cast<unsigned long long>(p.w) << 32) | p.z;
     }
 }
@@ -556,6 +589,9 @@ __device__ __forceinline__ bool voxel_merge(const VoxelEntries& E, int m_old, ui
 // 2 (full): as 1, and the volume has not been cleared since a reset: every
 // voxel is written, empty ones with the empty record, zero npix and zero
 // scalar totals, which spares the reset a pass over the whole volume.
+// With `touched` (modes 0 and 1) only the listed voxels are visited, item i
+// being voxel touched[i] with overflow range offsets[i] .. offsets[i + 1]; else
+// every voxel v with offsets[v] .. offsets[v + 1].
 template <int K, typename VT, int kMode>
 __global__ void __launch_bounds__(256) k_finalize(int32_t* __restrict__ count,
                                                   const unsigned long long* __restrict__ buckets,
@@ -563,7 +599,8 @@ __global__ void __launch_bounds__(256) k_finalize(int32_t* __restrict__ count,
                                                   const unsigned long long* __restrict__ entries, int64_t n_vox,
                                                   uint8_t* __restrict__ rec, uint16_t* __restrict__ npix,
                                                   uint32_t* __restrict__ scal_sum, uint32_t* __restrict__ scal_cnt,
-                                                  unsigned long long* overflow) {
+                                                  unsigned long long* overflow, const int32_t* __restrict__ touched,
+                                                  const int32_t* __restrict__ n_touched) {
     constexpr int RB = (2 * K + K * static_cast<int>(sizeof(VT)) + 15) / 16 * 16;
     // each thread edits its voxel's record and npix row in shared memory and
     // writes them back whole (full sectors, vector stores)
@@ -572,9 +609,11 @@ __global__ void __launch_bounds__(256) k_finalize(int32_t* __restrict__ count,
     uint4* my_rec = s_rec + threadIdx.x * (RB / 16);
     uint2* my_np = s_np + threadIdx.x * (K / 4);
     constexpr bool kFresh = kMode != 0;
-    for (int64_t v = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; v < n_vox;
-         v += static_cast<int64_t>(gridDim.x) * blockDim.x) {
-        const int s = offsets[v], e = offsets[v + 1], c = count[v];
+    const int64_t n_items = touched ? static_cast<int64_t>(*n_touched) : n_vox;
+    for (int64_t it = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; it < n_items;
+         it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t v = touched ? static_cast<int64_t>(touched[it]) : it;
+        const int s = offsets[it], e = offsets[it + 1], c = count[v];
         uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
         uint2* g_np = reinterpret_cast<uint2*>(npix + v * K);
         if (c == 0) {  // no entry (the overflow range is empty too)
@@ -756,22 +795,27 @@ cudaError_t finalize_full_v(int32_t* cnt, const unsigned long long* bk, const in
 template <int K, int kMode>
 cudaError_t finalize_kf(int32_t* cnt, const unsigned long long* bk, const int32_t* off,
                         const unsigned long long* ent, int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss,
-                        uint32_t* sc, int dtype, unsigned long long* ovf, cudaStream_t st) {
+                        uint32_t* sc, int dtype, unsigned long long* ovf, const int32_t* tl, const int32_t* tn,
+                        int64_t max_t, cudaStream_t st) {
     const int threads = 256;
-    const int64_t want = (n_vox + threads - 1) / threads;
+    const int64_t want = ((tl ? max_t : n_vox) + threads - 1) / threads;
     const int blocks = static_cast<int>(want < 148 * 64 ? want : 148 * 64);
     switch (dtype) {
     case DARE_U8:
-        k_finalize<K, uint8_t, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, uint8_t, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, tl,
+                                                               tn);
         break;
     case DARE_F16:
-        k_finalize<K, __half, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, __half, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, tl,
+                                                               tn);
         break;
     case DARE_BF16:
-        k_finalize<K, __nv_bfloat16, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, __nv_bfloat16, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, tl,
+                                                               tn);
         break;
     case DARE_F32:
-        k_finalize<K, float, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize<K, float, kMode><<<blocks, threads, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, tl,
+                                                               tn);
         break;
     default: return cudaErrorInvalidValue;
     }
@@ -781,7 +825,9 @@ cudaError_t finalize_kf(int32_t* cnt, const unsigned long long* bk, const int32_
 template <int K>
 cudaError_t finalize_k(int32_t* cnt, const unsigned long long* bk, const int32_t* off, const unsigned long long* ent,
                        int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int mode,
-                       int bulk, unsigned long long* ovf, cudaStream_t st) {
+                       int bulk, unsigned long long* ovf, const int32_t* tl, const int32_t* tn, int64_t max_t,
+                       cudaStream_t st) {
+    if (mode == 2 && tl) return cudaErrorInvalidValue;  // a full write visits every voxel
     if (mode == 2 && bulk) {
         switch (dtype) {
         case DARE_U8: return finalize_full_v<K, uint8_t>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
@@ -792,9 +838,9 @@ cudaError_t finalize_k(int32_t* cnt, const unsigned long long* bk, const int32_t
         return cudaErrorInvalidValue;
     }
     switch (mode) {
-    case 0: return finalize_kf<K, 0>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
-    case 1: return finalize_kf<K, 1>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
-    case 2: return finalize_kf<K, 2>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, st);
+    case 0: return finalize_kf<K, 0>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, tl, tn, max_t, st);
+    case 1: return finalize_kf<K, 1>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, tl, tn, max_t, st);
+    case 2: return finalize_kf<K, 2>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, dtype, ovf, nullptr, nullptr, 0, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -807,29 +853,44 @@ dim3 scatter_grid(const ScatterArgs& a) {
 }  // namespace
 
 cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, unsigned long long* buckets, uint4* pairs,
-                                 int32_t* n_pairs, cudaStream_t st) {
+                                 int32_t* n_pairs, int32_t* touched, int32_t* tindex, int32_t* n_touched,
+                                 cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    k_scatter_count<<<scatter_grid(a), kThreads, 0, st>>>(a, count, buckets, pairs, n_pairs);
+    k_scatter_count<<<scatter_grid(a), kThreads, 0, st>>>(a, count, buckets, pairs, n_pairs, touched, tindex,
+                                                          n_touched);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_touched_overflow(const int32_t* count, const int32_t* touched, const int32_t* n_touched,
+                                    int64_t max_t, int32_t* ovf_cnt, cudaStream_t st) {
+    if (max_t <= 0) return cudaSuccess;
+    const int64_t want = (max_t + 255) / 256;
+    const int blocks = static_cast<int>(want < 148 * 16 ? want : 148 * 16);
+    k_touched_overflow<<<blocks, 256, 0, st>>>(count, touched, n_touched, max_t, ovf_cnt);
     return cudaPeekAtLastError();
 }
 
 cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const int32_t* n_pairs, int32_t* count,
-                                 const int32_t* offsets, unsigned long long* entries, cudaStream_t st) {
+                                 const int32_t* offsets, const int32_t* tindex, unsigned long long* entries,
+                                 cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     const dim3 g = scatter_grid(a);
-    k_scatter_place<<<g.x * g.y, 256, 0, st>>>(pairs, n_pairs, count, offsets, entries, a.n);
+    k_scatter_place<<<g.x * g.y, 256, 0, st>>>(pairs, n_pairs, count, offsets, tindex, entries, a.n);
     return cudaPeekAtLastError();
 }
 
 cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, const int32_t* offsets,
                             const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
                             uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
-                            unsigned long long* overflow, cudaStream_t st) {
+                            unsigned long long* overflow, const int32_t* touched, const int32_t* n_touched,
+                            int64_t max_t, cudaStream_t st) {
+    const int32_t* tl = touched;
+    const int32_t* tn = n_touched;
     switch (K) {
-    case 4: return finalize_k<4>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
-    case 8: return finalize_k<8>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
-    case 12: return finalize_k<12>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
-    case 16: return finalize_k<16>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, st);
+    case 4: return finalize_k<4>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, st);
+    case 8: return finalize_k<8>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, st);
+    case 12: return finalize_k<12>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, st);
+    case 16: return finalize_k<16>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, st);
     }
     return cudaErrorInvalidValue;
 }

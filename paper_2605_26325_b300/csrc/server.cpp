@@ -1,6 +1,7 @@
 // Serving loop for many reslice sessions (dare_server_*): continuous batching
-// over a few stream lanes, live frame ingestion on its own stream, completion
-// stamps from host callbacks.
+// over a few stream lanes, live frame ingestion on its own stream; the
+// dispatcher thread stamps each completion when it sees the stream's event
+// (polled every 20 us while work is in flight).
 //
 // Ordering.  Each lane runs one batch at a time; a batch first waits on the
 // "last ingest" event of every session it reads.  An ingest first waits on
@@ -51,7 +52,7 @@ struct Item {
     Ingest ingest;
 };
 
-struct DoneBatch;  // callback payload
+struct DoneBatch;  // a batch or ingest in flight
 
 }  // namespace
 
@@ -65,10 +66,13 @@ struct dare_server_s {
         void* pin = nullptr;
         size_t pin_bytes = 0;
         bool busy = false;
+        DoneBatch* pending = nullptr;  // the batch in flight on this lane
     };
     std::vector<Lane> lanes;
     cudaStream_t ingest_st = nullptr;
     std::map<dare_session, cudaEvent_t> write_ev;
+    std::deque<std::pair<cudaEvent_t, DoneBatch*>> ingests_in_flight;  // in stream order
+    std::vector<cudaEvent_t> spare_events;
     std::thread worker;
     std::mutex mu;
     std::condition_variable cv;
@@ -92,9 +96,9 @@ struct DoneBatch {
     int32_t lane = -1;
 };
 
-void CUDART_CB on_done(void* p) {
-    auto* d = static_cast<DoneBatch*>(p);
-    const double t = now_s();
+// Hands a finished batch's completions to dare_server_poll; t is when the
+// dispatcher saw its stream reach the end of it.  Called without sv->mu held.
+void finish(DoneBatch* d, double t) {
     {
         std::lock_guard<std::mutex> lk(d->sv->done_mu);
         for (auto& it : d->items)
@@ -112,7 +116,10 @@ void CUDART_CB on_done(void* p) {
 }
 
 // Completes requests that never reached the GPU.
-void complete_now(dare_server sv, DoneBatch* d) { on_done(d); }
+void complete_now(dare_server sv, DoneBatch* d) {
+    (void)sv;
+    finish(d, now_s());
+}
 
 // A lane's device workspace and pinned staging, allocated once at server creation.
 dare_status lane_alloc(dare_server_s::Lane& L, size_t ws_need, size_t pin_need) {
@@ -134,7 +141,15 @@ dare_status lane_alloc(dare_server_s::Lane& L, size_t ws_need, size_t pin_need) 
     return DARE_OK;
 }
 
-void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& batch) {
+// The session's last ingest is still running on the device.
+bool ingest_running(dare_server sv, dare_session s) {
+    auto it = sv->write_ev.find(s);
+    return it != sv->write_ev.end() && cudaEventQuery(it->second) == cudaErrorNotReady;
+}
+
+// wait_ingests: the batch holds requests of sessions whose last ingest may still
+// be running; the lane waits for those ingests first.
+void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& batch, bool wait_ingests) {
     auto* d = new DoneBatch{sv, {}, 0, DARE_OK};
     d->issue_s = now_s();
     d->lane = static_cast<int32_t>(&L - sv->lanes.data());
@@ -153,20 +168,23 @@ void issue_batch(dare_server sv, dare_server_s::Lane& L, std::vector<Pending>& b
         return;
     }
     for (auto& r : reqs) {
-        auto it = sv->write_ev.find(r.session);
-        if (it != sv->write_ev.end()) cudaStreamWaitEvent(L.st, it->second, 0);
+        if (wait_ingests) {
+            auto it = sv->write_ev.find(r.session);
+            if (it != sv->write_ev.end()) cudaStreamWaitEvent(L.st, it->second, 0);
+        }
         dare::settle_session(r.session, L.st);  // a reset volume not yet cleared
     }
     dare_status rc = dare::queue_batch(reqs.data(), n, &sv->cfg.params, L.st, static_cast<uint8_t*>(L.ws),
                                        static_cast<uint8_t*>(L.pin));
     if (rc != DARE_OK) d->status = rc;
-    if (cudaLaunchHostFunc(L.st, on_done, d) != cudaSuccess) {
+    if (cudaEventRecord(L.ev, L.st) != cudaSuccess) {
         cudaGetLastError();
         d->status = DARE_E_CUDA;
+        cudaStreamSynchronize(L.st);
         complete_now(sv, d);
         return;
     }
-    cudaEventRecord(L.ev, L.st);
+    L.pending = d;  // the dispatcher completes it when L.ev is reached
     L.busy = true;
     std::lock_guard<std::mutex> lk(sv->done_mu);
     sv->stats.batches += 1;
@@ -183,10 +201,22 @@ void run_ingest(dare_server sv, Ingest& g) {
     cudaEvent_t& ev = sv->write_ev[g.s];
     if (!ev) cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     cudaEventRecord(ev, sv->ingest_st);
-    if (cudaLaunchHostFunc(sv->ingest_st, on_done, d) != cudaSuccess) {
+    cudaEvent_t done_ev = nullptr;
+    if (!sv->spare_events.empty()) {
+        done_ev = sv->spare_events.back();
+        sv->spare_events.pop_back();
+    } else if (cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
+        done_ev = nullptr;
+    }
+    if (!done_ev || cudaEventRecord(done_ev, sv->ingest_st) != cudaSuccess) {
+        cudaGetLastError();
+        if (done_ev) sv->spare_events.push_back(done_ev);
         d->status = DARE_E_CUDA;
+        cudaStreamSynchronize(sv->ingest_st);
         complete_now(sv, d);
+    } else {
+        sv->ingests_in_flight.push_back({done_ev, d});
     }
     std::lock_guard<std::mutex> lk(sv->done_mu);
     sv->stats.ingests += 1;
@@ -211,11 +241,30 @@ void worker_main(dare_server sv) {
     cudaSetDevice(sv->cfg.device);
     const double window = sv->cfg.coalesce_us * 1e-6;
     std::unique_lock<std::mutex> lk(sv->mu);
+    std::vector<DoneBatch*> finished;
     for (;;) {
+        // completions: lanes and ingests whose streams have reached their events
         bool any_busy = false;
         for (auto& L : sv->lanes) {
-            if (L.busy && cudaEventQuery(L.ev) == cudaSuccess) L.busy = false;
+            if (L.busy && cudaEventQuery(L.ev) == cudaSuccess) {
+                L.busy = false;
+                finished.push_back(L.pending);
+                L.pending = nullptr;
+            }
             any_busy = any_busy || L.busy;
+        }
+        while (!sv->ingests_in_flight.empty() && cudaEventQuery(sv->ingests_in_flight.front().first) == cudaSuccess) {
+            finished.push_back(sv->ingests_in_flight.front().second);
+            sv->spare_events.push_back(sv->ingests_in_flight.front().first);
+            sv->ingests_in_flight.pop_front();
+        }
+        any_busy = any_busy || !sv->ingests_in_flight.empty();
+        if (!finished.empty()) {
+            const double t = now_s();
+            lk.unlock();
+            for (DoneBatch* d : finished) finish(d, t);
+            lk.lock();
+            finished.clear();
         }
         if (sv->stop && sv->queue.empty() && !any_busy) break;
         bool did = false;
@@ -241,14 +290,23 @@ void worker_main(dare_server sv) {
                 wake = close;
                 break;
             }
-            std::vector<Pending> batch;
-            batch.reserve(n);
+            // requests of a session whose last ingest is still running must wait for it;
+            // the others go out at once in a batch of their own, so that an ingest
+            // holds up only its own session's requests
+            std::vector<Pending> ready, waiting;
             for (size_t k = 0; k < n; ++k) {
-                batch.push_back(sv->queue.front().req);
+                Pending& p = sv->queue.front().req;
+                (ingest_running(sv, p.req.session) ? waiting : ready).push_back(p);
                 sv->queue.pop_front();
             }
+            dare_server_s::Lane* lw = ready.empty() ? &L : nullptr;
+            for (auto& L2 : sv->lanes)
+                if (!lw && &L2 != &L && !L2.busy) lw = &L2;
+            if (!waiting.empty() && !lw)  // no second lane free: back to the front, in order
+                for (auto it = waiting.rbegin(); it != waiting.rend(); ++it) sv->queue.push_front(Item{false, *it, Ingest{}});
             lk.unlock();
-            issue_batch(sv, L, batch);
+            if (!ready.empty()) issue_batch(sv, L, ready, false);
+            if (!waiting.empty() && lw) issue_batch(sv, *lw, waiting, true);
             lk.lock();
             did = true;
         }
@@ -299,16 +357,9 @@ dare_status dare_server_create(const dare_server_config* cfg, dare_server* out) 
     sv->cfg = c;
     sv->stats.lanes = c.lanes;
     sv->lanes.resize(c.lanes);
-    // reslices outrank ingestion: the block scheduler starts a lane's waiting CTAs
-    // before the ingest's, so a large build does not hold up preview requests
-    int prio_low = 0, prio_high = 0;
-    if (cudaDeviceGetStreamPriorityRange(&prio_low, &prio_high) != cudaSuccess) {
-        cudaGetLastError();
-        prio_low = prio_high = 0;
-    }
-    bool ok = cudaStreamCreateWithPriority(&sv->ingest_st, cudaStreamNonBlocking, prio_low) == cudaSuccess;
+    bool ok = cudaStreamCreateWithFlags(&sv->ingest_st, cudaStreamNonBlocking) == cudaSuccess;
     for (auto& L : sv->lanes) {
-        ok = ok && cudaStreamCreateWithPriority(&L.st, cudaStreamNonBlocking, prio_high) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithFlags(&L.st, cudaStreamNonBlocking) == cudaSuccess;
         ok = ok && cudaEventCreateWithFlags(&L.ev, cudaEventDisableTiming) == cudaSuccess;
     }
     dare_status arc = DARE_OK;
@@ -427,6 +478,7 @@ dare_status dare_server_destroy(dare_server sv) {
         if (L.st) cudaStreamDestroy(L.st);
     }
     for (auto& kv : sv->write_ev) cudaEventDestroy(kv.second);
+    for (cudaEvent_t e : sv->spare_events) cudaEventDestroy(e);
     if (sv->ingest_st) cudaStreamDestroy(sv->ingest_st);
     if (prev != sv->cfg.device) cudaSetDevice(prev);
     delete sv;

@@ -85,6 +85,33 @@ def test_build_fine_pixels_coarse_voxels(tiny):
         s.close()
 
 
+@pytest.mark.parametrize("case", ["tiny_grid", "coarse_grid"])
+def test_build_small_appends_touch_only_their_voxels(tiny, case):
+    """Appends of 1 to 4 frames into an existing volume (incremental
+    integration, Sec. 4) finalize only the voxels they reach (the listed path):
+    records, npix and scalar totals equal one call over all frames, bit for
+    bit, including voxels whose entries overflow their bucket (coarse grid:
+    each frame splits a voxel over up to four tiles, 4-frame appends give it up
+    to 16 entries) and the capacity rule (K = 4)."""
+    if case == "tiny_grid":
+        w = tiny
+        bounds = [0, 40] + list(range(41, 81)) + [80, 200]
+    else:
+        w = types.SimpleNamespace(grid=synth.centred_grid((9, 8, 7), 4.0), frames=tiny.frames[:60],
+                                  frame_poses=tiny.frame_poses[:60], frame_px=(0.1, 0.12))
+        bounds = [0, 4, 8, 9, 11, 14, 18, 22, 26, 30, 34, 38, 42, 46, 50, 54, 58, 60]
+    bounds = sorted(set(bounds))
+    for dtype, K in ((dare.DARE_F32, 8), (dare.DARE_U8, 4)):
+        a = gpu_session(w, dtype, K, flags=dare.DARE_SESSION_SCALAR, chunks=bounds)
+        b = gpu_session(w, dtype, K, flags=dare.DARE_SESSION_SCALAR)
+        ra, rb = a.read_records(npix=True, scalar=True), b.read_records(npix=True, scalar=True)
+        for k in ("frame_ids", "npix", "scalar_sum", "scalar_count"):
+            assert np.array_equal(ra[k], rb[k]), k
+        assert np.array_equal(ra["values"].view(np.uint8), rb["values"].view(np.uint8))
+        a.close()
+        b.close()
+
+
 def test_build_frame_table(tiny, tiny_f32):
     s, _ = tiny_f32
     R = s.read_frames()
