@@ -34,7 +34,7 @@ namespace {
 constexpr int kTile = kScatterTile;   // frame tile: 32 x 32 pixels
 constexpr int kThreads = 256;         // a 2 x 2 pixel block per thread
 #ifndef DARE_COUNT_MIN_BLOCKS
-#define DARE_COUNT_MIN_BLOCKS 4
+#define DARE_COUNT_MIN_BLOCKS 5
 #endif
 constexpr int kHash = 2048;           // >= 2 x pixels per tile: never full
 constexpr int kEmptyKey = -1;
@@ -149,23 +149,34 @@ struct TileBox {
     int cells;  // n0 n1 n2, or INT_MAX when above kBoxCells
 };
 
+// Computed by the 32 lanes of one warp: lanes 0-11 take one (corner, axis)
+// each, lanes 0-2 reduce their axis over the corners, lane 0 writes B.
 __device__ void tile_box(const int64_t* aff, const int* dims, int u0, int v0, int u1, int v1, TileBox& B) {
+    const int lane = threadIdx.x & 31;
+    const int k = lane / 3, a = lane < 12 ? lane % 3 : 0;
+    const int u = (k & 1) ? u1 : u0, v = (k & 2) ? v1 : v0;
+    const int64_t q = lane < 12
+                          ? (aff[a] + static_cast<int64_t>(u) * aff[3 + a] + static_cast<int64_t>(v) * aff[6 + a] +
+                             kFixOne / 2) >> kFixBits
+                          : 0;
+    const int64_t q3 = __shfl_down_sync(0xFFFFFFFFu, q, 3), q6 = __shfl_down_sync(0xFFFFFFFFu, q, 6);
+    const int64_t q9 = __shfl_down_sync(0xFFFFFFFFu, q, 9);
+    const int64_t lo_a = min(min(q, q3), min(q6, q9)), hi_a = max(max(q, q3), max(q6, q9));  // lanes 0-2
+    int64_t lo[3], hi[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = __shfl_sync(0xFFFFFFFFu, lo_a, i);
+        hi[i] = __shfl_sync(0xFFFFFFFFu, hi_a, i);
+    }
+    if (lane != 0) return;
     int64_t cells = 1;
 #pragma unroll
-    for (int a = 0; a < 3; ++a) {
-        int64_t lo = INT64_MAX, hi = INT64_MIN;
-        for (int k = 0; k < 4; ++k) {
-            const int u = (k & 1) ? u1 : u0, v = (k & 2) ? v1 : v0;
-            const int64_t G = aff[a] + static_cast<int64_t>(u) * aff[3 + a] + static_cast<int64_t>(v) * aff[6 + a];
-            const int64_t q = (G + kFixOne / 2) >> kFixBits;
-            lo = q < lo ? q : lo;
-            hi = q > hi ? q : hi;
-        }
-        lo = lo < 0 ? 0 : lo;
-        hi = hi > dims[a] - 1 ? dims[a] - 1 : hi;
-        const int64_t n = hi >= lo ? hi - lo + 1 : 0;
-        B.b[a] = static_cast<int>(lo < dims[a] ? lo : 0);
-        B.n[a] = static_cast<int>(n);
+    for (int i = 0; i < 3; ++i) {
+        const int64_t l = lo[i] < 0 ? 0 : lo[i];
+        const int64_t h = hi[i] > dims[i] - 1 ? dims[i] - 1 : hi[i];
+        const int64_t n = h >= l ? h - l + 1 : 0;
+        B.b[i] = static_cast<int>(l < dims[i] ? l : 0);
+        B.n[i] = static_cast<int>(n);
         cells *= n;
     }
     B.cells = cells > kBoxCells ? INT_MAX : static_cast<int>(cells);
@@ -217,13 +228,19 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
     const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
     const int64_t tile = A.tile_base + static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
     if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
-    __syncthreads();
     if (threadIdx.x == 0) {
-        tile_box(aff, A.dims, u0, v0, min(u0 + kTile, A.width) - 1, min(v0 + kTile, A.height) - 1, B);
         n_list = 0;
         n_ovf = 0;
         n_new = 0;
     }
+    // the box of the direct-mapped path, cleared while the affine arrives
+    uint4* c4 = reinterpret_cast<uint4*>(smem);
+    for (int i = threadIdx.x; i < kBoxCells / 4; i += kThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (threadIdx.x < 32)
+        tile_box(aff, A.dims, u0, v0, min(u0 + kTile, A.width) - 1, min(v0 + kTile, A.height) - 1, B);
+    BlockPixels P;
+    block_pixels(A, aff, f, u0, v0, P);  // (the other warps meanwhile)
     __syncthreads();
     const int cells = B.cells;
     if (cells == 0) {  // no pixel of the tile lands in the grid
@@ -232,20 +249,17 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
     }
     const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
     uint4* ovf = pairs + tile * (kTile * kTile);
-    BlockPixels P;
     if (cells <= kBoxCells) {
         // direct-mapped box: one packed counter per voxel of the box
-        uint4* c4 = reinterpret_cast<uint4*>(smem);
-        for (int i = threadIdx.x; i < (cells + 3) / 4; i += kThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
-        block_pixels(A, aff, f, u0, v0, P);
         const int b0 = B.b[0], b1 = B.b[1], b2 = B.b[2], n0 = B.n[0], n1 = B.n[1];
         int key[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) key[q] = P.in[q] ? (P.c[q][0] - b0) + n0 * ((P.c[q][1] - b1) + n1 * (P.c[q][2] - b2)) : -1;
-        __syncthreads();  // box cleared
         block_combine(key, P.val, [&](int k, unsigned n, unsigned sm) { atomicAdd(smem + k, (n << kPackShift) | sm); });
         __syncthreads();
         const int64_t d0 = A.dims[0], d01 = static_cast<int64_t>(A.dims[0]) * A.dims[1];
+        // cell -> (i0, i1, i2) by FP32 reciprocals: exact for indices below 2^12
+        const float inv01 = 1.0f / static_cast<float>(n0 * n1), inv0 = 1.0f / static_cast<float>(n0);
         for (int r = 0; r < cells; r += 4 * kThreads) {
             int vi[4];
             unsigned long long e[4];
@@ -256,8 +270,9 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
                 vi[j] = -1;
                 e[j] = 0;
                 if (x) {
-                    const int i2 = idx / (n0 * n1), rem = idx - i2 * (n0 * n1);
-                    const int i1 = rem / n0, i0 = rem - i1 * n0;
+                    const int i2 = static_cast<int>((static_cast<float>(idx) + 0.5f) * inv01);
+                    const int rem = idx - i2 * (n0 * n1);
+                    const int i1 = static_cast<int>((static_cast<float>(rem) + 0.5f) * inv0), i0 = rem - i1 * n0;
                     vi[j] = static_cast<int>((b0 + i0) + d0 * (b1 + i1) + d01 * (b2 + i2));
                     e[j] = fid | (static_cast<unsigned long long>(x >> kPackShift) << 32) | (x & ((1u << kPackShift) - 1));
                 }
@@ -275,7 +290,6 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
         static_assert(kEmptyKey == -1, "keys cleared to all-ones words");
         for (int i = threadIdx.x; i < kHash / 4; i += kThreads) keys4[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
         for (int i = threadIdx.x; i < kHash / 2; i += kThreads) both4[i] = make_uint4(0u, 0u, 0u, 0u);
-        block_pixels(A, aff, f, u0, v0, P);
         int key[4];
 #pragma unroll
         for (int q = 0; q < 4; ++q) key[q] = P.in[q] ? P.c[q][0] + A.dims[0] * (P.c[q][1] + A.dims[1] * P.c[q][2]) : -1;
