@@ -607,7 +607,7 @@ __device__ __forceinline__ bool voxel_merge(const VoxelEntries& E, int m_old, ui
 // being voxel touched[i] with overflow range offsets[i] .. offsets[i + 1]; else
 // every voxel v with offsets[v] .. offsets[v + 1].
 template <int K, typename VT, int kMode>
-__global__ void __launch_bounds__(256) k_finalize(int32_t* __restrict__ count,
+__global__ void __launch_bounds__(256, kMode == 2 ? 6 : 4) k_finalize(int32_t* __restrict__ count,
                                                   const unsigned long long* __restrict__ buckets,
                                                   const int32_t* __restrict__ offsets,
                                                   const unsigned long long* __restrict__ entries, int64_t n_vox,
@@ -728,12 +728,14 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
 }
 
 // Finalize writing every voxel (mode 2: the volume has not been cleared since
-// a reset) with records and npix rows in device memory.  A CTA takes runs of
-// 256 consecutive voxels; each thread builds its voxel's record and npix row
-// in shared memory (the empty ones too), and one thread sends the whole run
-// (20 KB of f32 K=12 records) to global memory with two bulk copies.  A run
-// shorter than 256 voxels (the grid's tail) is stored thread by thread.
-template <int K, typename VT>
+// a reset).  A CTA takes runs of 256 consecutive voxels; each thread builds its
+// voxel's record and npix row in shared memory (the empty ones too), then the
+// whole run (20 KB of f32 K=12 records) goes out in one piece: with kBulk (the
+// volume in device memory) by two bulk copies from one thread, otherwise (a
+// volume in mapped host memory) by all threads in consecutive 16-byte stores,
+// so the host link sees whole lines.  A run shorter than 256 voxels (the
+// grid's tail) is stored thread by thread.
+template <int K, typename VT, bool kBulk>
 __global__ void __launch_bounds__(256) k_finalize_full(int32_t* __restrict__ count,
                                                        const unsigned long long* __restrict__ buckets,
                                                        const int32_t* __restrict__ offsets,
@@ -782,27 +784,38 @@ __global__ void __launch_bounds__(256) k_finalize_full(int32_t* __restrict__ cou
         }
         if (whole) {
             __syncthreads();  // the run's records and npix rows are in shared memory
-            if (threadIdx.x == 0) {
-                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                // offsets are multiples of 256 records and 256 npix rows: 16-byte aligned, sizes multiples of 16
-                bulk_store(rec + v0 * RB, s_rec, 256u * RB);
-                bulk_store(npix + v0 * K, s_np, 256u * K * 2u);
-                asm volatile("cp.async.bulk.commit_group;" ::: "memory");
-                asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // shared memory free again
+            if constexpr (kBulk) {
+                if (threadIdx.x == 0) {
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    // offsets are multiples of 256 records and 256 npix rows: 16-byte aligned, sizes multiples of 16
+                    bulk_store(rec + v0 * RB, s_rec, 256u * RB);
+                    bulk_store(npix + v0 * K, s_np, 256u * K * 2u);
+                    asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+                    asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");  // shared memory free again
+                }
+            } else {
+                uint4* g_rec = reinterpret_cast<uint4*>(rec + v0 * RB);
+                for (int i = threadIdx.x; i < 256 * RB / 16; i += 256) g_rec[i] = s_rec[i];
+                uint4* g_np = reinterpret_cast<uint4*>(npix + v0 * K);
+                const uint4* s_np4 = reinterpret_cast<const uint4*>(s_np);
+                for (int i = threadIdx.x; i < 256 * K * 2 / 16; i += 256) g_np[i] = s_np4[i];
             }
             __syncthreads();
         }
     }
-    if (threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    if (kBulk && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
 }
 
 template <int K, typename VT>
 cudaError_t finalize_full_v(int32_t* cnt, const unsigned long long* bk, const int32_t* off,
                             const unsigned long long* ent, int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss,
-                            uint32_t* sc, unsigned long long* ovf, cudaStream_t st) {
+                            uint32_t* sc, unsigned long long* ovf, bool bulk, cudaStream_t st) {
     const int64_t want = (n_vox + 255) / 256;
     const int blocks = static_cast<int>(want < (1 << 30) ? want : (1 << 30));  // one run per CTA
-    k_finalize_full<K, VT><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
+    if (bulk)
+        k_finalize_full<K, VT, true><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
+    else
+        k_finalize_full<K, VT, false><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
     return cudaPeekAtLastError();
 }
 
@@ -842,12 +855,13 @@ cudaError_t finalize_k(int32_t* cnt, const unsigned long long* bk, const int32_t
                        int bulk, unsigned long long* ovf, const int32_t* tl, const int32_t* tn, int64_t max_t,
                        cudaStream_t st) {
     if (mode == 2 && tl) return cudaErrorInvalidValue;  // a full write visits every voxel
-    if (mode == 2 && bulk) {
+    if (mode == 2) {
+        const bool b = bulk != 0;
         switch (dtype) {
-        case DARE_U8: return finalize_full_v<K, uint8_t>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
-        case DARE_F16: return finalize_full_v<K, __half>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
-        case DARE_BF16: return finalize_full_v<K, __nv_bfloat16>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
-        case DARE_F32: return finalize_full_v<K, float>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, st);
+        case DARE_U8: return finalize_full_v<K, uint8_t>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, st);
+        case DARE_F16: return finalize_full_v<K, __half>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, st);
+        case DARE_BF16: return finalize_full_v<K, __nv_bfloat16>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, st);
+        case DARE_F32: return finalize_full_v<K, float>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, st);
         }
         return cudaErrorInvalidValue;
     }
