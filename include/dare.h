@@ -464,6 +464,9 @@ dare_status dare_reslice_batch_host(const dare_reslice_req* reqs, int32_t n, con
  * plan); rebuilding it to the same frame count is fine.  Plans cover linear
  * probes: a request whose session holds curvilinear frames, or a curvilinear
  * params->probe, gives DARE_E_UNSUPPORTED (use dare_reslice_batch).
+ * The plan's workspace comes from the first request's session allocator (a
+ * copy of it is kept), so dare_plan_destroy touches no session and may follow
+ * the sessions' destruction; set_poses and launch need every session alive.
  */
 typedef struct dare_plan_s* dare_plan;
 

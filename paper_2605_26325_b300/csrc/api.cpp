@@ -288,6 +288,16 @@ struct L2Window {
 
 // ---------------------------------------------------------------- session
 
+// Hands a device block back through the allocator it came from (cudaFree
+// when the caller supplied none).
+static void allocator_free(const dare_allocator& a, void* p, size_t bytes, cudaStream_t st) {
+    if (!p) return;
+    if (a.free)
+        a.free(p, bytes, st, a.ctx);
+    else if (!a.alloc)
+        cudaFree(p);
+}
+
 struct dare_session_s {
     dare_session_config cfg{};
     int64_t n_vox = 0;
@@ -373,13 +383,7 @@ struct dare_session_s {
         }
         return p;
     }
-    void dev_free(void* p, size_t bytes, cudaStream_t st) {
-        if (!p) return;
-        if (cfg.alloc.free)
-            cfg.alloc.free(p, bytes, st, cfg.alloc.ctx);
-        else if (!cfg.alloc.alloc)
-            cudaFree(p);
-    }
+    void dev_free(void* p, size_t bytes, cudaStream_t st) { allocator_free(cfg.alloc, p, bytes, st); }
 };
 
 namespace {
@@ -2569,6 +2573,7 @@ struct dare_plan_s {
     size_t o_tj = 0, o_rj = 0, o_q = 0, desc_bytes = 0;
     void* ws = nullptr;
     size_t ws_bytes = 0;
+    dare_allocator ws_alloc{};  // the allocator ws came from (a copy: destroy needs no live session)
     void* pinned = nullptr;
     cudaStream_t cap = nullptr;
     cudaEvent_t done_ev = nullptr;
@@ -2809,8 +2814,8 @@ dare_status dare_plan_destroy(dare_plan p) {
     if (p->cap) cudaStreamDestroy(p->cap);
     if (p->done_ev) cudaEventDestroy(p->done_ev);
     if (p->pinned) cudaFreeHost(p->pinned);
-    if (p->ws && !p->sessions.empty()) {
-        p->sessions[0]->dev_free(p->ws, p->ws_bytes, nullptr);
+    if (p->ws) {
+        allocator_free(p->ws_alloc, p->ws, p->ws_bytes, nullptr);
         g_in_use -= static_cast<int64_t>(p->ws_bytes);
     }
     delete p;
@@ -2896,6 +2901,7 @@ dare_status dare_plan_create(const dare_reslice_req* reqs, int32_t n, const dare
     p->desc_bytes = need - p->o_tj;
     rc = admit(static_cast<int64_t>(need));
     if (rc != DARE_OK) return bail(rc);
+    p->ws_alloc = p->sessions[0]->cfg.alloc;
     p->ws = p->sessions[0]->dev_alloc(need, static_cast<cudaStream_t>(stream));
     if (!p->ws) {
         g_in_use -= static_cast<int64_t>(need);

@@ -18,6 +18,31 @@ __device__ __forceinline__ float to_f(float v) { return v; }
 __device__ __forceinline__ float weight_of(const float* w, int id) { return __ldg(w + id); }
 __device__ __forceinline__ float weight_of(const __half* w, int id) { return __half2float(__ldg(w + id)); }
 
+// Packed FP32 pairs (sm_100 and later): two independent IEEE round-to-nearest
+// operations per instruction, bit-identical to the scalar ones.
+__device__ __forceinline__ unsigned long long f2_bits(float2 a) {
+    return (static_cast<unsigned long long>(__float_as_uint(a.y)) << 32) | __float_as_uint(a.x);
+}
+__device__ __forceinline__ float2 f2_of(unsigned long long b) {
+    return make_float2(__uint_as_float(static_cast<uint32_t>(b)), __uint_as_float(static_cast<uint32_t>(b >> 32)));
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+    unsigned long long d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)));
+    return f2_of(d);
+}
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(f2_bits(a)), "l"(f2_bits(b)), "l"(f2_bits(c)));
+    return f2_of(d);
+}
+// (1 - t) a + t b on both halves, for a, b >= 0 (t and 1 - t each hold the same
+// weight twice).  Unlike a + t (b - a), a sum of non-negative products: no
+// cancellation when a and b differ by orders of magnitude.
+__device__ __forceinline__ float2 f2_mix(float2 a, float2 b, float2 omt, float2 t) {
+    return f2_fma(omt, a, f2_mul(t, b));
+}
+
 template <int K, typename VT>
 struct RecShape {
     static constexpr int kBytes = (2 * K + K * int(sizeof(VT)) + 15) / 16 * 16;

@@ -24,6 +24,7 @@
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 
+#include <algorithm>
 #include <climits>
 
 #include "dare_internal.h"
@@ -341,26 +342,56 @@ __global__ void __launch_bounds__(256) k_touched_overflow(const int32_t* __restr
         ovf_cnt[i] = i < n ? max(count[touched[i]] - kBucket, 0) : 0;
 }
 
-// Overflow pairs (entries of a voxel beyond its bucket): one CTA per tile
-// region; each pair takes a position in its voxel's overflow range (by voxel,
-// or by its place in the touched list with tindex) from the voxel's counter,
-// which counts back down to kBucket.  Regions go tile
-// position first: consecutive CTAs take the same tile of consecutive frames.
+// Overflow pairs (entries of a voxel beyond its bucket).  Few tiles have any,
+// so a CTA takes 256 consecutive tile regions at once: a block scan of their
+// pair counts, then its threads share out all of their pairs (each finds its
+// region by binary search over the scan).  Each pair takes a position in its
+// voxel's overflow range (by voxel, or by its place in the touched list with
+// tindex) from the voxel's counter, which counts back down to kBucket.
 __global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__ pairs,
-                                                       const int32_t* __restrict__ n_pairs,
+                                                       const int32_t* __restrict__ n_pairs, int64_t n_tiles,
                                                        int32_t* __restrict__ count, const int32_t* __restrict__ offsets,
                                                        const int32_t* __restrict__ tindex,
-                                                       unsigned long long* __restrict__ entries, int n_frames) {
-    const int64_t tiles_pf = gridDim.x / n_frames;  // the grid is n_frames x tiles_pf regions
-    const int64_t tt = blockIdx.x / n_frames, f = blockIdx.x - tt * n_frames;
-    const int64_t tile = f * tiles_pf + tt;
-    const int n = n_pairs[tile];
-    if (n == 0) return;
-    const uint4* in = pairs + tile * (kTile * kTile);
-    for (int i = threadIdx.x; i < n; i += 256) {
-        const uint4 p = __ldg(in + i);
-        const int pos = offsets[tindex ? tindex[p.x] : p.x] + atomicSub(count + p.x, 1) - 1 - kBucket;
-        entries[pos] = (static_cast<unsigned long long>(p.w) << 32) | p.z;
+                                                       unsigned long long* __restrict__ entries) {
+    __shared__ int s_incl[256];
+    __shared__ int s_warp[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * 256; t0 < n_tiles;
+         t0 += static_cast<int64_t>(gridDim.x) * 256) {  // block-uniform
+        const int n = t0 + threadIdx.x < n_tiles ? __ldg(n_pairs + t0 + threadIdx.x) : 0;
+        if (!__syncthreads_or(n > 0)) continue;
+        int x = n;  // inclusive scan: warps, then the warp totals
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (warp == 0) {
+            int w = lane < 8 ? s_warp[lane] : 0;
+#pragma unroll
+            for (int d = 1; d < 8; d <<= 1) {
+                const int y = __shfl_up_sync(0xFFFFFFFFu, w, d);
+                if (lane >= d) w += y;
+            }
+            if (lane < 8) s_warp[lane] = w;
+        }
+        __syncthreads();
+        s_incl[threadIdx.x] = x + (warp ? s_warp[warp - 1] : 0);
+        __syncthreads();
+        const int total = s_incl[255];
+        for (int k = threadIdx.x; k < total; k += 256) {
+            int j = 0;  // the region of pair k: the number of regions whose inclusive count is <= k
+#pragma unroll
+            for (int step = 128; step >= 1; step >>= 1)
+                if (s_incl[j + step - 1] <= k) j += step;
+            const int i = k - (j ? s_incl[j - 1] : 0);
+            const uint4 p = __ldg(pairs + (t0 + j) * (kTile * kTile) + i);
+            const int pos = offsets[tindex ? tindex[p.x] : p.x] + atomicSub(count + p.x, 1) - 1 - kBucket;
+            entries[pos] = (static_cast<unsigned long long>(p.w) << 32) | p.z;
+        }
+        __syncthreads();  // s_incl and s_warp are rewritten by the next round
     }
 }
 
@@ -400,18 +431,22 @@ struct VoxelEntries {
     }
 };
 
-// The c <= kBucket entries of a voxel without overflow, from its bucket with
-// 16-byte loads (only the loads that hold entries), the rest all ones (they
-// sort last), sorted ascending: by frame id, the entry's top 16 bits.
-__device__ __forceinline__ void bucket_sorted(const unsigned long long* bucket, int c,
-                                              unsigned long long (&e)[kBucket]) {
-    static_assert(kBucket == 8, "sorting network for 8 entries");
+// All four 16-byte pieces of a voxel's bucket, loaded together (entries past
+// the voxel's count are stale and ignored).
+__device__ __forceinline__ void bucket_load(const unsigned long long* bucket, ulonglong2 (&b)[kBucket / 2]) {
     const ulonglong2* q = reinterpret_cast<const ulonglong2*>(bucket);
 #pragma unroll
+    for (int i = 0; i < kBucket / 2; ++i) b[i] = __ldg(q + i);
+}
+
+// Sorts the c <= kBucket entries held in b ascending, by frame id (the
+// entry's top 16 bits); the slots past c become all ones and sort last.
+__device__ __forceinline__ void bucket_sort(const ulonglong2 (&b)[kBucket / 2], int c, unsigned long long (&e)[kBucket]) {
+    static_assert(kBucket == 8, "sorting network for 8 entries");
+#pragma unroll
     for (int i = 0; i < kBucket / 2; ++i) {
-        const ulonglong2 x = 2 * i < c ? __ldg(q + i) : make_ulonglong2(~0ull, ~0ull);
-        e[2 * i] = 2 * i < c ? x.x : ~0ull;
-        e[2 * i + 1] = 2 * i + 1 < c ? x.y : ~0ull;
+        e[2 * i] = 2 * i < c ? b[i].x : ~0ull;
+        e[2 * i + 1] = 2 * i + 1 < c ? b[i].y : ~0ull;
     }
     // Batcher's odd-even merge sort, 19 compare-exchanges
 #define DARE_CX(a, b)                                        \
@@ -428,6 +463,17 @@ __device__ __forceinline__ void bucket_sorted(const unsigned long long* bucket, 
     DARE_CX(2, 4) DARE_CX(3, 5)
     DARE_CX(1, 2) DARE_CX(3, 4) DARE_CX(5, 6)
 #undef DARE_CX
+}
+
+// The c <= kBucket entries of a voxel without overflow, sorted; only the
+// 16-byte loads that hold entries are issued.
+__device__ __forceinline__ void bucket_sorted(const unsigned long long* bucket, int c,
+                                              unsigned long long (&e)[kBucket]) {
+    const ulonglong2* q = reinterpret_cast<const ulonglong2*>(bucket);
+    ulonglong2 b[kBucket / 2];
+#pragma unroll
+    for (int i = 0; i < kBucket / 2; ++i) b[i] = 2 * i < c ? __ldg(q + i) : make_ulonglong2(~0ull, ~0ull);
+    bucket_sort(b, c, e);
 }
 
 // General merge: the m_old stored samples plus the new entries grouped by
@@ -573,6 +619,22 @@ __device__ __forceinline__ int append_sorted(const unsigned long long (&e)[kBuck
 // entries (mean-compounding comparator).  Returns true when the capacity rule
 // dropped samples.
 template <int K, typename VT>
+__device__ __forceinline__ bool voxel_merge_sorted(const VoxelEntries& E, const unsigned long long (&ev)[kBucket],
+                                                   int m_old, uint16_t* ids, VT* vals, uint16_t* np,
+                                                   uint32_t& tot_sum, uint32_t& tot_cnt) {
+    tot_sum = 0;
+    tot_cnt = 0;
+#pragma unroll
+    for (int j = 0; j < kBucket; ++j)
+        if (j < E.c) {
+            tot_sum += static_cast<uint32_t>(ent_sum(ev[j]));
+            tot_cnt += static_cast<uint32_t>(ent_npix(ev[j]));
+        }
+    if (append_sorted<K, VT>(ev, m_old, ids, vals, np) >= 0) return false;
+    return merge_general<K, VT>(E, m_old, ids, vals, np);
+}
+
+template <int K, typename VT>
 __device__ __forceinline__ bool voxel_merge(const VoxelEntries& E, int m_old, uint16_t* ids, VT* vals, uint16_t* np,
                                             uint32_t& tot_sum, uint32_t& tot_cnt) {
     tot_sum = 0;
@@ -580,13 +642,7 @@ __device__ __forceinline__ bool voxel_merge(const VoxelEntries& E, int m_old, ui
     if (E.n == E.c) {  // every entry in the bucket: sorted in registers
         unsigned long long ev[kBucket];
         bucket_sorted(E.bucket, E.c, ev);
-#pragma unroll
-        for (int j = 0; j < kBucket; ++j)
-            if (j < E.c) {
-                tot_sum += static_cast<uint32_t>(ent_sum(ev[j]));
-                tot_cnt += static_cast<uint32_t>(ent_npix(ev[j]));
-            }
-        if (append_sorted<K, VT>(ev, m_old, ids, vals, np) >= 0) return false;
+        return voxel_merge_sorted<K, VT>(E, ev, m_old, ids, vals, np, tot_sum, tot_cnt);
     } else {
         for (int i = 0; i < E.n; ++i) {
             const unsigned long long x = E.at(i);
@@ -756,17 +812,32 @@ __global__ void __launch_bounds__(256) k_finalize_full(int32_t* __restrict__ cou
             empty_record<K, RB>(my_rec);
 #pragma unroll
             for (int i = 0; i < K / 4; ++i) my_np[i] = make_uint2(0u, 0u);
+            // the counter and the whole bucket in one round trip; after the
+            // place pass c = min(entries, kBucket), and a voxel has overflow
+            // entries (its offsets differ) only when its bucket is full
             const int c = count[v];
+            ulonglong2 b[kBucket / 2];
+            bucket_load(buckets + v * kBucket, b);
             uint32_t tot_sum = 0, tot_cnt = 0;
             bool over = false;
             if (c > 0) {
-                const int s = offsets[v], e = offsets[v + 1];
+                int s = 0, e = 0;
+                if (c == kBucket) {
+                    s = offsets[v];
+                    e = offsets[v + 1];
+                }
                 const VoxelEntries E{buckets + v * kBucket, entries, c, s, c + (e - s)};
                 count[v] = 0;
                 uint16_t* ids = reinterpret_cast<uint16_t*>(my_rec);
                 VT* vals = reinterpret_cast<VT*>(reinterpret_cast<uint8_t*>(my_rec) + 2 * K);
                 uint16_t* np = reinterpret_cast<uint16_t*>(my_np);
-                over = voxel_merge<K, VT>(E, 0, ids, vals, np, tot_sum, tot_cnt);
+                if (E.n == c) {
+                    unsigned long long ev[kBucket];
+                    bucket_sort(b, c, ev);
+                    over = voxel_merge_sorted<K, VT>(E, ev, 0, ids, vals, np, tot_sum, tot_cnt);
+                } else {
+                    over = voxel_merge<K, VT>(E, 0, ids, vals, np, tot_sum, tot_cnt);
+                }
             }
             if (!whole) {
                 uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
@@ -803,7 +874,8 @@ __global__ void __launch_bounds__(256) k_finalize_full(int32_t* __restrict__ cou
             __syncthreads();
         }
     }
-    if (kBulk && threadIdx.x == 0) asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");
+    // Each run already waited until its copies had read shared memory; their
+    // global writes complete with the grid, so the CTA exits without waiting.
 }
 
 template <int K, typename VT>
@@ -903,7 +975,15 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
                                  cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     const dim3 g = scatter_grid(a);
-    k_scatter_place<<<g.x * g.y, 256, 0, st>>>(pairs, n_pairs, count, offsets, tindex, entries, a.n);
+    const int64_t n_tiles = int64_t(g.x) * g.y;
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    const int64_t want = (n_tiles + 255) / 256;  // a CTA per 256 tile regions
+    const int blocks = static_cast<int>(std::min<int64_t>(want, int64_t(sms[dev]) * 8));
+    k_scatter_place<<<blocks, 256, 0, st>>>(pairs, n_pairs, n_tiles, count, offsets, tindex, entries);
     return cudaPeekAtLastError();
 }
 

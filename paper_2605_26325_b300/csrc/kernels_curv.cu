@@ -205,7 +205,8 @@ __device__ __forceinline__ float2 curv_voxel(const CurvJob& C, const PixelAxes& 
 
 // The pixel's support (as in the linear-probe kernels) with per-sample weights.
 template <int K, typename VT>
-__device__ __noinline__ void gather_pixel_curv(const CurvJob& C, int u, int v, float& num, float& den) {
+__device__ __noinline__ float2 gather_pixel_curv(const CurvJob& C, int u, int v) {
+    float num = 0.0f, den = 0.0f;
     const ResliceJob& J = C.j;
     const int R = J.radius;
     const bool box = J.kernel == DARE_BOX;
@@ -218,7 +219,7 @@ __device__ __noinline__ void gather_pixel_curv(const CurvJob& C, int u, int v, f
         const int64_t f = G >> kFixBits;
         fr[a] = static_cast<float>(static_cast<int32_t>(G & (kFixOne - 1))) * (1.0f / static_cast<float>(kFixOne));
         lo[a] = box ? f + (fr[a] >= 0.5f ? 1 : 0) - R : f - R + 1;
-        if (lo[a] + S - 1 < 0 || lo[a] > J.dims[a] - 1) return;  // the support misses the grid
+        if (lo[a] + S - 1 < 0 || lo[a] > J.dims[a] - 1) return make_float2(num, den);  // the support misses the grid
         fr[a] -= static_cast<float>(static_cast<int>(lo[a] - f));  // g - lo, exact (int32: a fast conversion)
     }
     const PixelAxes P = pixel_axes(C, u, v);
@@ -254,6 +255,7 @@ __device__ __noinline__ void gather_pixel_curv(const CurvJob& C, int u, int v, f
             }
         }
     }
+    return make_float2(num, den);
 }
 
 // 32 x 8 pixels per CTA, one per thread; a warp writes one mask word.
@@ -267,7 +269,9 @@ __device__ __forceinline__ void curv_body(const CurvJob& C) {
     const bool active = u < J.width;
     float num = 0.0f, den = 0.0f;
     if (active) {
-        gather_pixel_curv<K, VT>(C, u, v, num, den);
+        const float2 nd = gather_pixel_curv<K, VT>(C, u, v);
+        num = nd.x;
+        den = nd.y;
         J.out[static_cast<int64_t>(v) * J.width + u] = den > 0.0f ? num / den : J.unassigned;
     }
     const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);

@@ -51,7 +51,8 @@ __global__ void __launch_bounds__(256) k_page_in(const int2* __restrict__ pages,
 // Per-pixel gather over the support, records from the brick cache (or the
 // mapped host volume for bricks that are not resident).
 template <int K, typename VT, typename WT>
-__device__ __noinline__ void gather_pixel_paged(const PagedJob& P, int u, int v, float& num, float& den) {
+__device__ __noinline__ float2 gather_pixel_paged(const PagedJob& P, int u, int v) {
+    float num = 0.0f, den = 0.0f;
     const ResliceJob& J = P.j;
     const int R = J.radius;
     const bool box = J.kernel == DARE_BOX;
@@ -64,7 +65,7 @@ __device__ __noinline__ void gather_pixel_paged(const PagedJob& P, int u, int v,
         const int64_t f = G >> kFixBits;
         fr[a] = static_cast<float>(static_cast<int32_t>(G & (kFixOne - 1))) * (1.0f / static_cast<float>(kFixOne));
         lo[a] = box ? f + (fr[a] >= 0.5f ? 1 : 0) - R : f - R + 1;
-        if (lo[a] + S - 1 < 0 || lo[a] > J.dims[a] - 1) return;  // the support misses the grid
+        if (lo[a] + S - 1 < 0 || lo[a] > J.dims[a] - 1) return make_float2(num, den);  // the support misses the grid
         fr[a] -= static_cast<float>(static_cast<int>(lo[a] - f));  // g - lo, exact (int32: a fast conversion)
     }
     const WT* wt = static_cast<const WT*>(J.wtab);
@@ -107,6 +108,7 @@ __device__ __noinline__ void gather_pixel_paged(const PagedJob& P, int u, int v,
             }
         }
     }
+    return make_float2(num, den);
 }
 
 template <int K, typename VT, typename WT>
@@ -119,7 +121,9 @@ __device__ __forceinline__ void paged_body(const PagedJob& P) {
     const bool active = u < J.width;
     float num = 0.0f, den = 0.0f;
     if (active) {
-        gather_pixel_paged<K, VT, WT>(P, u, v, num, den);
+        const float2 nd = gather_pixel_paged<K, VT, WT>(P, u, v);
+        num = nd.x;
+        den = nd.y;
         J.out[static_cast<int64_t>(v) * J.width + u] = den > 0.0f ? num / den : J.unassigned;
     }
     const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);

@@ -82,7 +82,8 @@ __device__ __forceinline__ float2 collapse_voxel_px(const uint8_t* rec, const ui
 
 // Per-pixel gather over the kernel's support (records read from global memory).
 template <int K, typename VT, typename WT>
-__device__ __noinline__ void gather_pixel_r(const ResliceJob& J, int u, int v, float& num, float& den) {
+__device__ __noinline__ float2 gather_pixel_r(const ResliceJob& J, int u, int v) {
+    float num = 0.0f, den = 0.0f;
     const int R = J.radius;
     const bool box = J.kernel == DARE_BOX;
     const int S = box ? 2 * R + 1 : 2 * R;
@@ -94,7 +95,7 @@ __device__ __noinline__ void gather_pixel_r(const ResliceJob& J, int u, int v, f
         const int64_t f = G >> kFixBits;
         fr[a] = static_cast<float>(static_cast<int32_t>(G & (kFixOne - 1))) * (1.0f / static_cast<float>(kFixOne));
         lo[a] = box ? f + (fr[a] >= 0.5f ? 1 : 0) - R : f - R + 1;
-        if (lo[a] + S - 1 < 0 || lo[a] > J.dims[a] - 1) return;  // the support misses the grid
+        if (lo[a] + S - 1 < 0 || lo[a] > J.dims[a] - 1) return make_float2(num, den);  // the support misses the grid
         fr[a] -= static_cast<float>(static_cast<int>(lo[a] - f));  // g - lo, exact (int32: a fast conversion)
     }
     const WT* wt = static_cast<const WT*>(J.wtab);
@@ -128,6 +129,7 @@ __device__ __noinline__ void gather_pixel_r(const ResliceJob& J, int u, int v, f
             }
         }
     }
+    return make_float2(num, den);
 }
 
 template <int K, typename VT, typename WT>
@@ -139,7 +141,9 @@ __device__ __forceinline__ void plain_r_body(const ResliceJob& J) {
     const bool active = u < J.width;
     float num = 0.0f, den = 0.0f;
     if (active) {
-        gather_pixel_r<K, VT, WT>(J, u, v, num, den);
+        const float2 nd = gather_pixel_r<K, VT, WT>(J, u, v);
+        num = nd.x;
+        den = nd.y;
         J.out[static_cast<int64_t>(v) * J.width + u] = den > 0.0f ? num / den : J.unassigned;
     }
     const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);
@@ -299,7 +303,9 @@ __device__ __forceinline__ void tile_body_r(const ResliceJob& J, const TileSetup
         float num = 0.0f, den = 0.0f;
         if (active) {
             if (direct) {
-                gather_pixel_r<K, VT, WT>(J, u, v, num, den);
+                const float2 nd = gather_pixel_r<K, VT, WT>(J, u, v);
+                num = nd.x;
+                den = nd.y;
             } else if (!empty) {
                 const int r1 = Rr1 + r * B1, r2 = Rr2 + r * B2, rd = Rrd + r * Bd;
                 const float p1 = static_cast<float>(r1 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));

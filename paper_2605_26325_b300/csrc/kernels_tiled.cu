@@ -42,7 +42,7 @@ constexpr int kThreads = 256;
 constexpr int kColMax = kTiledColMax;
 constexpr int kSlotMax = kTiledSlotMax;   // (A, B) float2 slots: 32 KB
 #ifndef DARE_TILED_MIN_BLOCKS
-#define DARE_TILED_MIN_BLOCKS 4
+#define DARE_TILED_MIN_BLOCKS 5  // 48 registers, a few spills: faster than 4 CTAs without spills
 #endif
 constexpr float kMargin = 0.02f; // voxel; > FP32 error of the plane height for |g| < 2^14
 
@@ -67,10 +67,13 @@ __device__ __forceinline__ int find_job(const ResliceJob* jobs, int n_jobs, int 
     return lo;
 }
 
+// Returned by value: sums passed by reference would live in the caller's
+// stack frame, and the pixel loop would store them to local memory every row.
 template <int K, typename VT, typename WT>
-__device__ __noinline__ void direct_pixel(const ResliceJob& J, int u, int v, float& num, float& den) {
+__device__ __noinline__ float2 direct_pixel(const ResliceJob& J, int u, int v) {
+    float num = 0.0f, den = 0.0f;
     const PixelCoord pc = pixel_coord(J, u, v);
-    if (!pc.any) return;
+    if (!pc.any) return make_float2(num, den);
     const WT* wt = static_cast<const WT*>(J.wtab);
     for (int corner = 0; corner < 8; ++corner) {
         const int dx = corner & 1, dy = (corner >> 1) & 1, dz = corner >> 2;
@@ -83,6 +86,14 @@ __device__ __noinline__ void direct_pixel(const ResliceJob& J, int u, int v, flo
         num = fmaf(t, ab.x, num);
         den = fmaf(t, ab.y, den);
     }
+    return make_float2(num, den);
+}
+
+// (r mod 2^20) / 2^20, exactly: the 20-bit fraction placed in the mantissa of
+// a float in [1, 2), minus one (integer operations instead of a conversion)
+__device__ __forceinline__ float frac20(int r) {
+    static_assert(kFixBits == 20, "20-bit fixed point");
+    return __int_as_float(0x3F800000 | ((r << 3) & 0x007FFFF8)) - 1.0f;
 }
 
 __device__ __forceinline__ int64_t lmin(int64_t a, int64_t b) { return a < b ? a : b; }
@@ -199,11 +210,6 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
     // Everything the loop reads besides the slots sits in registers: the output
     // stores go through generic pointers, which could otherwise alias the
     // shared-memory copies and force reloads.
-    const int A1 = static_cast<int>(J.a[E1]), B1 = static_cast<int>(J.b[E1]);
-    const int A2 = static_cast<int>(J.a[E2]), B2 = static_cast<int>(J.b[E2]);
-    const int Ad = static_cast<int>(J.a[D]), Bd = static_cast<int>(J.b[D]);
-    const int R1 = T.R1 + lane * A1, R2 = T.R2 + lane * A2, Rd = T.Rd + lane * Ad;
-    const int O1 = T.O1, O2 = T.O2, Od = T.Od;
     float* const out = J.out;
     uint32_t* const mask = J.mask;
     const int64_t width = J.width, mstride = J.mask_stride;
@@ -211,38 +217,65 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
     const int u = u0 + lane;
     const bool active = u <= u1;
     const int rows = v1 - v0 + 1;
+    if (direct || empty) {
+        for (int r = warp; r < rows; r += kThreads / 32) {
+            const int v = v0 + r;
+            float num = 0.0f, den = 0.0f;
+            if (active) {
+                if (direct) {
+                    const float2 nd = direct_pixel<K, VT, WT>(J, u, v);
+                    num = nd.x;
+                    den = nd.y;
+                }
+                out[v * width + u] = den > 0.0f ? num / den : unassigned;
+            }
+            const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);
+            if (lane == 0) mask[v * mstride + u0 / 32] = bits;
+        }
+        return;
+    }
+    const int A1 = static_cast<int>(J.a[E1]), B1 = static_cast<int>(J.b[E1]);
+    const int A2 = static_cast<int>(J.a[E2]), B2 = static_cast<int>(J.b[E2]);
+    const int Ad = static_cast<int>(J.a[D]), Bd = static_cast<int>(J.b[D]);
+    const int R1 = T.R1 + lane * A1, R2 = T.R2 + lane * A2, Rd = T.Rd + lane * Ad;
+    const int O1 = T.O1, O2 = T.O2, Od = T.Od;
     for (int r = warp; r < rows; r += kThreads / 32) {
         const int v = v0 + r;
         float num = 0.0f, den = 0.0f;
         if (active) {
-            if (direct) {
-                direct_pixel<K, VT, WT>(J, u, v, num, den);
-            } else if (!empty) {
-                const int r1 = R1 + r * B1, r2 = R2 + r * B2, rd = Rd + r * Bd;
-                // k1 in [0, n1 - 2], k2 in [0, n2 - 2] by construction of the box
-                const int c00 = (r1 >> kFixBits) + O1 + n1 * ((r2 >> kFixBits) + O2);
-                const int fd = (rd >> kFixBits) + Od;
-                const float p1 = static_cast<float>(r1 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
-                const float p2 = static_cast<float>(r2 & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
-                const float pd = static_cast<float>(rd & (kFixOne - 1)) * (1.0f / static_cast<float>(kFixOne));
+            const int r1 = R1 + r * B1, r2 = R2 + r * B2, rd = Rd + r * Bd;
+            // k1 in [0, n1 - 2], k2 in [0, n2 - 2] by construction of the box
+            const int c00 = (r1 >> kFixBits) + O1 + n1 * ((r2 >> kFixBits) + O2);
+            const int fd = (rd >> kFixBits) + Od;
+            const float p1 = frac20(r1), p2 = frac20(r2), pd = frac20(rd);
+            // TENT weights are separable: (A, B) pairs mixed along the depth
+            // axis, then e1, then e2, with packed pair arithmetic (1 - p is
+            // exact for a 20-bit fraction)
+            const float2 wd = make_float2(pd, pd), wd0 = make_float2(1.0f - pd, 1.0f - pd);
+            float2 q[2];
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
+            for (int j = 0; j < 2; ++j) {
+                float2 col[2];
 #pragma unroll
-                    for (int i = 0; i < 2; ++i) {
-                        const int c = c00 + i + n1 * j;
-                        // levels fd, fd + 1 lie in the column's range; the clamp only keeps reads in bounds
-                        const int lev = min(max(fd - sCol[c], 0), L - 2);
-                        const float2 a0 = sAB[c * L + lev], a1 = sAB[c * L + lev + 1];
-                        const float wc = (i ? p1 : 1.0f - p1) * (j ? p2 : 1.0f - p2);
-                        const float t0 = wc * (1.0f - pd), t1 = wc * pd;
-                        num = fmaf(t0, a0.x, num);
-                        den = fmaf(t0, a0.y, den);
-                        num = fmaf(t1, a1.x, num);
-                        den = fmaf(t1, a1.y, den);
-                    }
+                for (int i = 0; i < 2; ++i) {
+                    // Levels fd, fd + 1 lie in the column's range wherever the
+                    // column's weight is not zero.  The clamp keeps every read
+                    // among the column's own (written, finite) slots: a pixel
+                    // also reads its zero-weight neighbours, and 0 x NaN from
+                    // stale shared memory would not be zero.
+                    const int c = c00 + i + n1 * j;
+                    const int lev = min(max(fd - sCol[c], 0), L - 2);
+                    col[i] = f2_mix(sAB[c * L + lev], sAB[c * L + lev + 1], wd0, wd);
                 }
+                q[j] = f2_mix(col[0], col[1], make_float2(1.0f - p1, 1.0f - p1), make_float2(p1, p1));
             }
-            out[v * width + u] = den > 0.0f ? num / den : unassigned;
+            const float2 nd = f2_mix(q[0], q[1], make_float2(1.0f - p2, 1.0f - p2), make_float2(p2, p2));
+            num = nd.x;
+            den = nd.y;
+            // The fast division (2 ulp, far below the path's tolerance) holds
+            // for den in [2^-126, 2^126]; tiny weights (thresholds opened
+            // wide) can leave den below that, where the IEEE division runs.
+            out[v * width + u] = den > 0.0f ? (den >= 0x1p-100f ? __fdividef(num, den) : num / den) : unassigned;
         }
         const unsigned bits = __ballot_sync(0xFFFFFFFFu, active && den > 0.0f);
         if (lane == 0) mask[v * mstride + u0 / 32] = bits;

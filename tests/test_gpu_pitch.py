@@ -127,7 +127,7 @@ def test_tile_rows_rejects_other_values(tiny, vols):
     assert ei.value.status == dare.DARE_E_INVALID
 
 
-@pytest.mark.parametrize("path", [dare.DARE_PATH_AUTO, dare.DARE_PATH_TILED])
+@pytest.mark.parametrize("path", [dare.DARE_PATH_AUTO, dare.DARE_PATH_TILED, dare.DARE_PATH_PLAIN])
 def test_plan_replays_follow_tile_rows_of_new_poses(tiny, vols, path):
     """A plan's persistent tiled kernel reads each replay's tile count from the
     work queue: poses that change the planes' tile heights (aligned 0.5-voxel
@@ -170,6 +170,22 @@ def test_plan_replays_follow_tile_rows_of_new_poses(tiny, vols, path):
                 assert np.all(np.abs(got[cov] - o1[cov]) <= 1e-5 * np.maximum(np.abs(o1[cov]), 1))
             assert np.all(got[~cov] == 0.0)
     plan.close()
+
+
+@pytest.mark.parametrize("path", [dare.DARE_PATH_PLAIN, dare.DARE_PATH_TILED])
+def test_thresholds_open_parity(tiny, vols, path):
+    """Eq. 1's thresholds opened to 180 degrees: every stored sample counts and
+    Eq. 2's weights span orders of magnitude between neighbouring voxels, which
+    a blend that subtracts neighbouring (A, B) sums would lose to cancellation.
+    Both kernels stay within the path's tolerance of the oracle at every
+    pitch of this file."""
+    s, vol = vols
+    p = dare.params_default(path=path, thr_normal_deg=180.0, thr_inplane_deg=180.0)
+    for name, T, W, H, px in _planes(tiny):
+        out, mw = gpu_reslice(s, T, W, H, px, p)
+        ref, rm = oracle.reslice(vol, T, W, H, px, ora_params(p))
+        assert rm.sum() > 0.05 * W * H, name
+        assert_parity(out, mw, ref, rm, W)
 
 
 def test_plan_per_pixel_planes(tiny, vols):
@@ -235,3 +251,24 @@ def test_tuning_choices_persist_in_a_file(tiny, vols, tmp_path):
         plan.close()
     finally:
         dare.tune_cache_file(None)
+
+
+def test_plan_destroyed_after_its_session(tiny):
+    """A plan may outlive its sessions' handles at destruction: dare_plan_destroy
+    frees the plan's workspace through the allocator it recorded at creation and
+    touches no session."""
+    s = gpu_session(tiny, dare.DARE_F32, 8)
+    out, mask = new_outputs(64, 48)
+    plan = dare.Plan([(s, tiny.reslice_poses[3], out, mask, tiny.out_px)], dare.params_default())
+    plan.launch()
+    torch.cuda.synchronize()
+    s.close()
+    plan.close()
+    alloc = dare.TorchAllocator(0)
+    s = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, allocator=alloc)
+    s.build(torch.from_numpy(tiny.frames).to("cuda"), tiny.frame_poses, tiny.frame_px)
+    plan = dare.Plan([(s, tiny.reslice_poses[3], out, mask, tiny.out_px)], dare.params_default())
+    s.close()
+    assert len(alloc.live) == 1  # the plan's workspace, taken from the session's allocator
+    plan.close()
+    assert len(alloc.live) == 0
