@@ -35,7 +35,7 @@ namespace {
 constexpr int kTile = kScatterTile;   // frame tile: 32 x 32 pixels
 constexpr int kThreads = 256;         // a 2 x 2 pixel block per thread
 #ifndef DARE_COUNT_MIN_BLOCKS
-#define DARE_COUNT_MIN_BLOCKS 5
+#define DARE_COUNT_MIN_BLOCKS 6  // 40 registers, 8 bytes of spill: faster than 5 CTAs at 46
 #endif
 constexpr int kHash = 2048;           // >= 2 x pixels per tile: never full
 constexpr int kEmptyKey = -1;
@@ -48,51 +48,75 @@ static_assert(kBoxCells >= 0 && kBoxCells <= kSmemWords, "the box fits the share
 // packed per-voxel accumulator of the box: npix (<= 1024) above bit 18, sum (<= 1024 x 255 < 2^18) below
 constexpr int kPackShift = 18;
 
-// Nearest voxels of a thread's 2 x 2 pixel block: q-th pixel's coordinates
-// (in-grid flag) and value.  int32 steps from the tile origin when |A|, |B| <
-// 2^25 (host flag), else int64 per pixel.
+// A thread's 2 x 2 pixel block.  The values are loaded first (they need only
+// the frame and the pixel positions, so the loads overlap the CTA's set-up);
+// the nearest voxels follow once the tile origin is known.  q-th pixel: its
+// coordinates, in-grid flag and value.
 struct BlockPixels {
     int c[4][3];
     bool in[4];
     unsigned val[4];
 };
 
-__device__ __forceinline__ void block_pixels(const ScatterArgs& A, const int64_t* aff, int f, int u0, int v0,
-                                             BlockPixels& P) {
+// In-image (and in-mask) flags and raw values of the block's pixels.  With an
+// even width and an even frames address a pixel pair (u, u + 1) is one aligned
+// 16-bit load.
+__device__ __forceinline__ void block_values(const ScatterArgs& A, int f, int u0, int v0, BlockPixels& P) {
     const uint8_t* img = A.frames + static_cast<int64_t>(f) * A.width * A.height;
     const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
     const int u = u0 + 2 * tx, v = v0 + 2 * ty;
-    int base[3] = {0, 0, 0}, ra[3] = {0, 0, 0}, rb[3] = {0, 0, 0}, r0[3] = {0, 0, 0};
-    if (A.small_steps) {
-#pragma unroll
-        for (int a = 0; a < 3; ++a) {
-            const int64_t G = aff[a] + static_cast<int64_t>(u0) * aff[3 + a] + static_cast<int64_t>(v0) * aff[6 + a] +
-                              kFixOne / 2;
-            const int64_t F = G >> kFixBits;
-            base[a] = static_cast<int>(F < -(1 << 24) ? -(1 << 24) : (F > (1 << 24) ? (1 << 24) : F));
-            r0[a] = static_cast<int>(G & (kFixOne - 1));
-            ra[a] = static_cast<int>(aff[3 + a]);
-            rb[a] = static_cast<int>(aff[6 + a]);
-        }
-    }
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
         const int uu = u + (q & 1), vv = v + (q >> 1);
-        P.in[q] = false;
-        P.val[q] = 0;
-        P.c[q][0] = P.c[q][1] = P.c[q][2] = 0;
-        if (uu >= A.width || vv >= A.height) continue;
-        if (A.pix_mask && !((__ldg(A.pix_mask + static_cast<int64_t>(vv) * ((A.width + 31) >> 5) + (uu >> 5)) >> (uu & 31)) & 1u))
-            continue;  // excluded by the probe's pixel mask
-        bool in = true;
-        if (A.small_steps) {
-            const int du = uu - u0, dv = vv - v0;
+        bool ok = uu < A.width && vv < A.height;
+        if (ok && A.pix_mask)
+            ok = (__ldg(A.pix_mask + static_cast<int64_t>(vv) * ((A.width + 31) >> 5) + (uu >> 5)) >> (uu & 31)) & 1u;
+        P.in[q] = ok;
+    }
+    const bool pairs = ((reinterpret_cast<uintptr_t>(A.frames) | static_cast<uintptr_t>(A.width)) & 1u) == 0;
 #pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                P.c[q][a] = base[a] + ((r0[a] + du * ra[a] + dv * rb[a]) >> kFixBits);
-                in = in && P.c[q][a] >= 0 && P.c[q][a] < A.dims[a];
-            }
+    for (int h = 0; h < 2; ++h) {
+        const uint8_t* row = img + static_cast<int64_t>(v + h) * A.width + u;
+        if (pairs) {
+            const unsigned pair = P.in[2 * h] || P.in[2 * h + 1] ? __ldg(reinterpret_cast<const unsigned short*>(row)) : 0u;
+            P.val[2 * h] = pair & 0xFFu;
+            P.val[2 * h + 1] = pair >> 8;
         } else {
+            P.val[2 * h] = P.in[2 * h] ? __ldg(row) : 0u;
+            P.val[2 * h + 1] = P.in[2 * h + 1] ? __ldg(row + 1) : 0u;
+        }
+    }
+}
+
+// Nearest voxels of the block's pixels; in[q] becomes "in the image and in the
+// grid".  With small steps (|A|, |B| < 2^25, host flag) the tile origin's
+// coordinates come from org (per axis: integer part, 20-bit remainder, steps
+// per u and per v, set once per CTA) and each pixel adds int32 steps to them;
+// otherwise int64 per pixel.
+__device__ __forceinline__ void block_voxels(const ScatterArgs& A, const int64_t* aff, const int4* org, int u0, int v0,
+                                             BlockPixels& P) {
+    const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+    const int u = u0 + 2 * tx, v = v0 + 2 * ty;
+    if (A.small_steps) {
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const int4 o = org[a];
+            const int r00 = o.y + (2 * tx) * o.z + (2 * ty) * o.w, r10 = r00 + o.z, r01 = r00 + o.w, r11 = r10 + o.w;
+            P.c[0][a] = o.x + (r00 >> kFixBits);
+            P.c[1][a] = o.x + (r10 >> kFixBits);
+            P.c[2][a] = o.x + (r01 >> kFixBits);
+            P.c[3][a] = o.x + (r11 >> kFixBits);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+            P.in[q] = P.in[q] && static_cast<unsigned>(P.c[q][0]) < static_cast<unsigned>(A.dims[0]) &&
+                      static_cast<unsigned>(P.c[q][1]) < static_cast<unsigned>(A.dims[1]) &&
+                      static_cast<unsigned>(P.c[q][2]) < static_cast<unsigned>(A.dims[2]);
+    } else {
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const int uu = u + (q & 1), vv = v + (q >> 1);
+            bool in = P.in[q];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
                 const int64_t G = aff[a] + static_cast<int64_t>(uu) * aff[3 + a] + static_cast<int64_t>(vv) * aff[6 + a];
@@ -100,10 +124,12 @@ __device__ __forceinline__ void block_pixels(const ScatterArgs& A, const int64_t
                 in = in && qq >= 0 && qq < A.dims[a];
                 P.c[q][a] = in ? static_cast<int>(qq) : 0;
             }
+            P.in[q] = in;
         }
-        P.in[q] = in;
-        if (in) P.val[q] = __ldg(img + static_cast<int64_t>(vv) * A.width + uu);
     }
+#pragma unroll
+    for (int q = 0; q < 4; ++q)
+        if (!P.in[q]) P.val[q] = 0u;
 }
 
 // Sums the block's pixels per distinct key (pixels of the block that share a
@@ -152,14 +178,21 @@ struct TileBox {
 
 // Computed by the 32 lanes of one warp: lanes 0-11 take one (corner, axis)
 // each, lanes 0-2 reduce their axis over the corners, lane 0 writes B.
-__device__ void tile_box(const int64_t* aff, const int* dims, int u0, int v0, int u1, int v1, TileBox& B) {
+__device__ void tile_box(const int64_t* aff, const int4* org, bool small_steps, const int* dims, int u0, int v0, int u1,
+                         int v1, TileBox& B) {
     const int lane = threadIdx.x & 31;
     const int k = lane / 3, a = lane < 12 ? lane % 3 : 0;
     const int u = (k & 1) ? u1 : u0, v = (k & 2) ? v1 : v0;
-    const int64_t q = lane < 12
-                          ? (aff[a] + static_cast<int64_t>(u) * aff[3 + a] + static_cast<int64_t>(v) * aff[6 + a] +
-                             kFixOne / 2) >> kFixBits
-                          : 0;
+    int64_t q = 0;
+    if (lane < 12) {
+        if (small_steps) {  // the corner from the tile origin in int32 steps, as the pixels do
+            const int4 o = org[a];
+            q = o.x + ((o.y + (u - u0) * o.z + (v - v0) * o.w) >> kFixBits);
+        } else {
+            q = (aff[a] + static_cast<int64_t>(u) * aff[3 + a] + static_cast<int64_t>(v) * aff[6 + a] + kFixOne / 2) >>
+                kFixBits;
+        }
+    }
     const int64_t q3 = __shfl_down_sync(0xFFFFFFFFu, q, 3), q6 = __shfl_down_sync(0xFFFFFFFFu, q, 6);
     const int64_t q9 = __shfl_down_sync(0xFFFFFFFFu, q, 9);
     const int64_t lo_a = min(min(q, q3), min(q6, q9)), hi_a = max(max(q, q3), max(q6, q9));  // lanes 0-2
@@ -207,7 +240,7 @@ __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long lo
     }
 }
 
-// One CTA per 32 x 32 frame tile (blockIdx.y = frame): per-voxel sums of the
+// One CTA per 32 x 32 frame tile (blockIdx.z = frame): per-voxel sums of the
 // tile's pixels, then one (voxel, entry) per distinct voxel, entry = frame id
 // << 48 | npix << 32 | sum.  Tile t owns pairs[t * kTile^2, ...) for its
 // overflow pairs and n_pairs[t] says how many it wrote.  With `touched`, the
@@ -221,27 +254,39 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
                                                             int32_t* __restrict__ n_touched) {
     __shared__ __align__(16) unsigned smem[kSmemWords];
     __shared__ int64_t aff[9];
+    __shared__ int4 org[3];  // small steps: the tile origin per axis (integer part, remainder, steps)
     __shared__ TileBox B;
     __shared__ int n_list, n_ovf, n_new, new_base;
     __shared__ int s_new[kTile * kTile];  // voxels whose first entry this tile made
-    const int tiles_x = (A.width + kTile - 1) / kTile;
-    const int f = blockIdx.y;
-    const int u0 = (blockIdx.x % tiles_x) * kTile, v0 = (blockIdx.x / tiles_x) * kTile;
-    const int64_t tile = A.tile_base + static_cast<int64_t>(blockIdx.y) * gridDim.x + blockIdx.x;
+    const int f = blockIdx.z;
+    const int u0 = blockIdx.x * kTile, v0 = blockIdx.y * kTile;
+    const int64_t tile =
+        A.tile_base + (static_cast<int64_t>(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
+    if (A.small_steps && threadIdx.x >= 32 && threadIdx.x < 35) {  // (warp 0 sets up the box later)
+        const int a = threadIdx.x - 32;
+        const int64_t* af = A.affines + 9 * static_cast<int64_t>(f);
+        const int64_t ga = af[3 + a], gb = af[6 + a];
+        const int64_t G = af[a] + static_cast<int64_t>(u0) * ga + static_cast<int64_t>(v0) * gb + kFixOne / 2;
+        const int64_t F = G >> kFixBits;
+        org[a] = make_int4(static_cast<int>(F < -(1 << 24) ? -(1 << 24) : (F > (1 << 24) ? (1 << 24) : F)),
+                           static_cast<int>(G & (kFixOne - 1)), static_cast<int>(ga), static_cast<int>(gb));
+    }
     if (threadIdx.x == 0) {
         n_list = 0;
         n_ovf = 0;
         n_new = 0;
     }
     // the box of the direct-mapped path, cleared while the affine arrives
+    BlockPixels P;
+    block_values(A, f, u0, v0, P);  // in flight during the set-up
     uint4* c4 = reinterpret_cast<uint4*>(smem);
     for (int i = threadIdx.x; i < kBoxCells / 4; i += kThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
     __syncthreads();
     if (threadIdx.x < 32)
-        tile_box(aff, A.dims, u0, v0, min(u0 + kTile, A.width) - 1, min(v0 + kTile, A.height) - 1, B);
-    BlockPixels P;
-    block_pixels(A, aff, f, u0, v0, P);  // (the other warps meanwhile)
+        tile_box(aff, org, A.small_steps != 0, A.dims, u0, v0, min(u0 + kTile, A.width) - 1,
+                 min(v0 + kTile, A.height) - 1, B);
+    block_voxels(A, aff, org, u0, v0, P);  // (the other warps meanwhile)
     __syncthreads();
     const int cells = B.cells;
     if (cells == 0) {  // no pixel of the tile lands in the grid
@@ -945,9 +990,9 @@ cudaError_t finalize_k(int32_t* cnt, const unsigned long long* bk, const int32_t
     return cudaErrorInvalidValue;
 }
 
+// (tile column, tile row, frame); tiles numbered in that order
 dim3 scatter_grid(const ScatterArgs& a) {
-    const int tiles = ((a.width + kTile - 1) / kTile) * ((a.height + kTile - 1) / kTile);
-    return dim3(tiles, a.n);
+    return dim3((a.width + kTile - 1) / kTile, (a.height + kTile - 1) / kTile, a.n);
 }
 
 }  // namespace
@@ -975,7 +1020,7 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
                                  cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
     const dim3 g = scatter_grid(a);
-    const int64_t n_tiles = int64_t(g.x) * g.y;
+    const int64_t n_tiles = int64_t(g.x) * g.y * g.z;
     static int sms[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;

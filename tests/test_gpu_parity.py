@@ -674,3 +674,30 @@ def test_build_ragged_frame_sizes(tiny, W, H):
     assert np.array_equal(got["values"].view(np.uint32), vals.view(np.uint32))
     assert np.array_equal(got["npix"], npix)
     s.close()
+
+
+@pytest.mark.parametrize("W,H", [(130, 37), (64, 64)])
+def test_build_frames_at_odd_address(tiny, W, H):
+    """Even frame widths let the count pass read a pixel pair with one 16-bit
+    load; frames that start at an odd device address take the byte loads.
+    Both give the oracle's records bit for bit."""
+    rng = np.random.default_rng(W + 7 * H)
+    frames = rng.integers(0, 256, (40, H, W)).astype(np.uint8)
+    px = (0.3, 0.3)
+    poses = np.stack([synth.plane_pose_centred(tiny.frame_poses[i][:3, :3], rng.uniform(-4, 4, 3), W, H, *px)
+                      for i in range(0, 120, 3)])
+    buf = torch.empty(frames.size + 1, dtype=torch.uint8, device=DEV)
+    odd = buf[1:].view(frames.shape)
+    odd.copy_(torch.from_numpy(frames))
+    assert odd.data_ptr() % 2 == 1
+    vol = oracle.build(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, frames, poses, px, oracle.F32, 8)
+    ids, vals, npix, e = oracle_dense(vol, 8, dare.DARE_F32)
+    assert e["npix"].sum() > 0
+    for src in (torch.from_numpy(frames).to(DEV), odd):
+        s = dare.Session(tiny.grid.dims, tiny.grid.spacing, tiny.grid.vol_to_world, dtype=dare.DARE_F32, max_slots=8)
+        s.build(src, poses, px)
+        got = s.read_records(npix=True)
+        assert np.array_equal(got["frame_ids"], ids)
+        assert np.array_equal(got["values"].view(np.uint32), vals.view(np.uint32))
+        assert np.array_equal(got["npix"], npix)
+        s.close()
