@@ -1566,8 +1566,8 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     const int32_t chunk = static_cast<int32_t>(std::min<int64_t>(65535, std::max<int64_t>(1, kMaxPixelsPerChunk / slots_pf)));
     const int32_t n_chunk = std::min(n, chunk);
     // workspace: offsets (n_vox + 1), scan block sums, overflow entries (at most one per pixel),
-    // buckets (kBucket entries per voxel), overflow (voxel, entry) pairs (one slot per pixel of the
-    // frame tiles), overflow pairs per tile, affines
+    // buckets (kBucket entries per voxel), the overflow (voxel, entry) pair list (one slot per pixel
+    // of the frame tiles) and its length, affines
     const int64_t nbs = scan_block_sums_needed(s->n_vox);
     const size_t o_off = 0;
     const size_t o_bs = align_up(o_off + size_t(s->n_vox + 1) * 4, 256);
@@ -1579,7 +1579,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     // grid's voxels) list the voxels they touch and finalize only those: touched
     // list, voxel -> list position, list overflow counts, list length
     const int64_t max_t = std::min<int64_t>(s->n_vox, int64_t(n_chunk) * npx);
-    const size_t o_aff = align_up(o_np + size_t(n_chunk) * tiles_pf * 4, 256);
+    const size_t o_aff = align_up(o_np + 16, 256);
     const size_t o_tl = align_up(o_aff + size_t(n) * 9 * 8, 256);
     const size_t o_ti = align_up(o_tl + size_t(max_t) * 4, 256);
     const size_t o_tc = align_up(o_ti + size_t(s->n_vox) * 4, 256);
@@ -1650,6 +1650,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
         int32_t* ti = listed ? t_index : nullptr;
         int32_t* tn = listed ? t_n : nullptr;
         if (listed) CUDA_TRY(cudaMemsetAsync(t_n, 0, sizeof(int32_t), st));
+        CUDA_TRY(cudaMemsetAsync(n_pairs, 0, sizeof(int32_t), st));  // the chunk's overflow list starts empty
         if (!host) {
             KernelScope ks("scatter_count", st, 1);
             CUDA_TRY(launch_scatter_count(a, s->count, buckets, pairs, n_pairs, tl, ti, tn, st));
@@ -1669,7 +1670,6 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                 sa.affines = a.affines + size_t(j0) * 9;
                 sa.n = nj;
                 sa.frame_base = a.frame_base + j0;
-                sa.tile_base = int64_t(j0) * tiles_pf;
                 {
                     KernelScope ks("scatter_count", st, 1);
                     CUDA_TRY(launch_scatter_count(sa, s->count, buckets, pairs, n_pairs, tl, ti, tn, st));

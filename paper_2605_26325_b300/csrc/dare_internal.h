@@ -82,7 +82,7 @@ struct ScatterArgs {
     int32_t dims[3];
     int32_t frame_base;       // global id of frame 0 of this chunk
     int32_t small_steps;      // every |A|, |B| < 2^25: tiles step pixels in int32
-    int64_t tile_base;        // pair-list tile of frame 0 (frames uploaded in slices)
+    int64_t tile_base;        // unused (kept for the layout)
     const uint32_t* pix_mask; // H rows of ceil(W / 32) words, bit set = pixel used; NULL: every pixel
 };
 
@@ -127,8 +127,8 @@ cudaError_t launch_weight_tables(const TableJob* jobs_dev, const TableJob* one_j
 cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int max_w,
                                  int max_h, int K, int dtype, int half_weights, cudaStream_t st);
 // count: per-voxel entry counters (zero on entry; finalize returns them to zero); buckets: kBucket
-// 8-byte entries per voxel; pairs: kTile^2 16-byte (voxel, entry) overflow pairs per 32 x 32 frame
-// tile; n_pairs: overflow pairs per tile
+// 8-byte entries per voxel; pairs: the overflow list of 16-byte (voxel, entry) pairs, room for one
+// per pixel; *n_pairs: its length (zero before the chunk's first count launch)
 // touched (optional): voxels reached for the first time are listed, touched[i] = v and tindex[v] = i
 // for i < *n_touched (zero on entry)
 cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, unsigned long long* buckets, uint4* pairs,

@@ -219,7 +219,7 @@ __device__ void tile_box(const int64_t* aff, const int4* org, bool small_steps, 
 // Up to four (voxel, entry) results per thread and round: counter slots are
 // taken with four returning atomics in flight; the first kBucket entries of a
 // voxel go to its bucket (kBucket consecutive entries per voxel), later ones to
-// the tile's overflow region.  With s_new, a voxel whose first entry this is
+// the overflow list.  With s_new, a voxel whose first entry this is
 // (slot 0) is also listed as touched by this build.
 __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long long (&e)[4], int32_t* count,
                                       unsigned long long* buckets, uint4* ovf, int* n_ovf, int* s_new, int* s_n_new) {
@@ -233,7 +233,7 @@ __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long lo
             buckets[static_cast<int64_t>(vi[j]) * kBucket + slot[j]] = e[j];
             if (s_new && slot[j] == 0) s_new[atomicAdd(s_n_new, 1)] = vi[j];  // one per distinct voxel of the tile
         } else {
-            const int k = atomicAdd(n_ovf, 1);  // at most one pair per pixel of the tile
+            const int k = atomicAdd(n_ovf, 1);  // at most one pair per pixel of the chunk
             ovf[k] = make_uint4(static_cast<unsigned>(vi[j]), 0u, static_cast<unsigned>(e[j]),
                                 static_cast<unsigned>(e[j] >> 32));
         }
@@ -242,8 +242,9 @@ __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long lo
 
 // One CTA per 32 x 32 frame tile (blockIdx.z = frame): per-voxel sums of the
 // tile's pixels, then one (voxel, entry) per distinct voxel, entry = frame id
-// << 48 | npix << 32 | sum.  Tile t owns pairs[t * kTile^2, ...) for its
-// overflow pairs and n_pairs[t] says how many it wrote.  With `touched`, the
+// << 48 | npix << 32 | sum.  Overflow pairs (a voxel's entries past its
+// bucket, rare) are appended to one list, pairs[0, *n_pairs), which the host
+// empties before the chunk's first count launch.  With `touched`, the
 // voxels this build reaches for the first time are listed: touched[i], and
 // tindex[v] = i, i < *n_touched.
 __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_count(const __grid_constant__ ScatterArgs A,
@@ -256,12 +257,10 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
     __shared__ int64_t aff[9];
     __shared__ int4 org[3];  // small steps: the tile origin per axis (integer part, remainder, steps)
     __shared__ TileBox B;
-    __shared__ int n_list, n_ovf, n_new, new_base;
+    __shared__ int n_list, n_new, new_base;
     __shared__ int s_new[kTile * kTile];  // voxels whose first entry this tile made
     const int f = blockIdx.z;
     const int u0 = blockIdx.x * kTile, v0 = blockIdx.y * kTile;
-    const int64_t tile =
-        A.tile_base + (static_cast<int64_t>(blockIdx.z) * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
     if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
     if (A.small_steps && threadIdx.x >= 32 && threadIdx.x < 35) {  // (warp 0 sets up the box later)
         const int a = threadIdx.x - 32;
@@ -274,7 +273,6 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
     }
     if (threadIdx.x == 0) {
         n_list = 0;
-        n_ovf = 0;
         n_new = 0;
     }
     // the box of the direct-mapped path, cleared while the affine arrives
@@ -289,12 +287,8 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
     block_voxels(A, aff, org, u0, v0, P);  // (the other warps meanwhile)
     __syncthreads();
     const int cells = B.cells;
-    if (cells == 0) {  // no pixel of the tile lands in the grid
-        if (threadIdx.x == 0) n_pairs[tile] = 0;
-        return;
-    }
+    if (cells == 0) return;  // no pixel of the tile lands in the grid
     const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
-    uint4* ovf = pairs + tile * (kTile * kTile);
     if (cells <= kBoxCells) {
         // direct-mapped box: one packed counter per voxel of the box
         const int b0 = B.b[0], b1 = B.b[1], b2 = B.b[2], n0 = B.n[0], n1 = B.n[1];
@@ -323,7 +317,7 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
                     e[j] = fid | (static_cast<unsigned long long>(x >> kPackShift) << 32) | (x & ((1u << kPackShift) - 1));
                 }
             }
-            emit4(vi, e, count, buckets, ovf, &n_ovf, touched ? s_new : nullptr, &n_new);
+            emit4(vi, e, count, buckets, pairs, n_pairs, touched ? s_new : nullptr, &n_new);
         }
     } else {
         // hash table over voxel indices
@@ -357,15 +351,12 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
                     e[j] = fid | (static_cast<unsigned long long>(npx[h]) << 32) | sums[h];
                 }
             }
-            emit4(vi, e, count, buckets, ovf, &n_ovf, touched ? s_new : nullptr, &n_new);
+            emit4(vi, e, count, buckets, pairs, n_pairs, touched ? s_new : nullptr, &n_new);
         }
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        n_pairs[tile] = n_ovf;
-        if (touched) new_base = n_new ? atomicAdd(n_touched, n_new) : 0;
-    }
     if (touched) {
+        __syncthreads();
+        if (threadIdx.x == 0) new_base = n_new ? atomicAdd(n_touched, n_new) : 0;
         __syncthreads();
         for (int k = threadIdx.x; k < n_new; k += kThreads) {
             const int v = s_new[k];
@@ -387,56 +378,22 @@ __global__ void __launch_bounds__(256) k_touched_overflow(const int32_t* __restr
         ovf_cnt[i] = i < n ? max(count[touched[i]] - kBucket, 0) : 0;
 }
 
-// Overflow pairs (entries of a voxel beyond its bucket).  Few tiles have any,
-// so a CTA takes 256 consecutive tile regions at once: a block scan of their
-// pair counts, then its threads share out all of their pairs (each finds its
-// region by binary search over the scan).  Each pair takes a position in its
-// voxel's overflow range (by voxel, or by its place in the touched list with
-// tindex) from the voxel's counter, which counts back down to kBucket.
+// Overflow pairs (entries of a voxel beyond its bucket), from the list the
+// count pass appended them to: a grid-stride loop, so the work is even however
+// the pairs cluster.  Each pair takes a position in its voxel's overflow range
+// (by voxel, or by its place in the touched list with tindex) from the voxel's
+// counter, which counts back down to kBucket.
 __global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__ pairs,
-                                                       const int32_t* __restrict__ n_pairs, int64_t n_tiles,
+                                                       const int32_t* __restrict__ n_pairs,
                                                        int32_t* __restrict__ count, const int32_t* __restrict__ offsets,
                                                        const int32_t* __restrict__ tindex,
                                                        unsigned long long* __restrict__ entries) {
-    __shared__ int s_incl[256];
-    __shared__ int s_warp[8];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    for (int64_t t0 = static_cast<int64_t>(blockIdx.x) * 256; t0 < n_tiles;
-         t0 += static_cast<int64_t>(gridDim.x) * 256) {  // block-uniform
-        const int n = t0 + threadIdx.x < n_tiles ? __ldg(n_pairs + t0 + threadIdx.x) : 0;
-        if (!__syncthreads_or(n > 0)) continue;
-        int x = n;  // inclusive scan: warps, then the warp totals
-#pragma unroll
-        for (int d = 1; d < 32; d <<= 1) {
-            const int y = __shfl_up_sync(0xFFFFFFFFu, x, d);
-            if (lane >= d) x += y;
-        }
-        if (lane == 31) s_warp[warp] = x;
-        __syncthreads();
-        if (warp == 0) {
-            int w = lane < 8 ? s_warp[lane] : 0;
-#pragma unroll
-            for (int d = 1; d < 8; d <<= 1) {
-                const int y = __shfl_up_sync(0xFFFFFFFFu, w, d);
-                if (lane >= d) w += y;
-            }
-            if (lane < 8) s_warp[lane] = w;
-        }
-        __syncthreads();
-        s_incl[threadIdx.x] = x + (warp ? s_warp[warp - 1] : 0);
-        __syncthreads();
-        const int total = s_incl[255];
-        for (int k = threadIdx.x; k < total; k += 256) {
-            int j = 0;  // the region of pair k: the number of regions whose inclusive count is <= k
-#pragma unroll
-            for (int step = 128; step >= 1; step >>= 1)
-                if (s_incl[j + step - 1] <= k) j += step;
-            const int i = k - (j ? s_incl[j - 1] : 0);
-            const uint4 p = __ldg(pairs + (t0 + j) * (kTile * kTile) + i);
-            const int pos = offsets[tindex ? tindex[p.x] : p.x] + atomicSub(count + p.x, 1) - 1 - kBucket;
-            entries[pos] = (static_cast<unsigned long long>(p.w) << 32) | p.z;
-        }
-        __syncthreads();  // s_incl and s_warp are rewritten by the next round
+    const int64_t n = *n_pairs;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint4 p = __ldg(pairs + i);
+        const int pos = offsets[tindex ? tindex[p.x] : p.x] + atomicSub(count + p.x, 1) - 1 - kBucket;
+        entries[pos] = (static_cast<unsigned long long>(p.w) << 32) | p.z;
     }
 }
 
@@ -837,7 +794,7 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
 // so the host link sees whole lines.  A run shorter than 256 voxels (the
 // grid's tail) is stored thread by thread.
 template <int K, typename VT, bool kBulk>
-__global__ void __launch_bounds__(256) k_finalize_full(int32_t* __restrict__ count,
+__global__ void __launch_bounds__(256, 6) k_finalize_full(  // 40 registers: 6 CTAs per SMint32_t* __restrict__ count,
                                                        const unsigned long long* __restrict__ buckets,
                                                        const int32_t* __restrict__ offsets,
                                                        const unsigned long long* __restrict__ entries,
@@ -1019,16 +976,12 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
                                  const int32_t* offsets, const int32_t* tindex, unsigned long long* entries,
                                  cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    const dim3 g = scatter_grid(a);
-    const int64_t n_tiles = int64_t(g.x) * g.y * g.z;
     static int sms[64] = {};
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
     if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return cudaErrorInvalidDevice;
-    const int64_t want = (n_tiles + 255) / 256;  // a CTA per 256 tile regions
-    const int blocks = static_cast<int>(std::min<int64_t>(want, int64_t(sms[dev]) * 8));
-    k_scatter_place<<<blocks, 256, 0, st>>>(pairs, n_pairs, n_tiles, count, offsets, tindex, entries);
+    k_scatter_place<<<sms[dev] * 2, 256, 0, st>>>(pairs, n_pairs, count, offsets, tindex, entries);
     return cudaPeekAtLastError();
 }
 

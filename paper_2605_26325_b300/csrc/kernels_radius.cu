@@ -355,7 +355,7 @@ __device__ __forceinline__ void tile_body_r(const ResliceJob& J, const TileSetup
 }
 
 template <int K, typename VT, typename WT>
-__global__ void __launch_bounds__(kThreads) k_reslice_tiled_r(const ResliceJob* __restrict__ jobs, int n_jobs,
+__global__ void __launch_bounds__(kThreads, 3) k_reslice_tiled_r(const ResliceJob* __restrict__ jobs, int n_jobs,
                                                               int tile_offset, int uniform, int col_cap,
                                                               int slot_cap, const __grid_constant__ ResliceJob one) {
     extern __shared__ __align__(16) unsigned char smem_r[];
