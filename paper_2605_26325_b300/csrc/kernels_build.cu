@@ -685,7 +685,16 @@ __global__ void __launch_bounds__(256, kMode == 2 ? 6 : 4) k_finalize(int32_t* _
     for (int64_t it = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; it < n_items;
          it += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const int64_t v = touched ? static_cast<int64_t>(touched[it]) : it;
-        const int s = offsets[it], e = offsets[it + 1], c = count[v];
+        // the counter and the whole bucket in one round trip; a voxel has
+        // overflow entries (its offsets differ) only when its bucket is full
+        const int c = count[v];
+        ulonglong2 b[kBucket / 2];
+        bucket_load(buckets + v * kBucket, b);
+        int s = 0, e = 0;
+        if (c == kBucket) {
+            s = offsets[it];
+            e = offsets[it + 1];
+        }
         uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
         uint2* g_np = reinterpret_cast<uint2*>(npix + v * K);
         if (c == 0) {  // no entry (the overflow range is empty too)
@@ -746,7 +755,14 @@ __global__ void __launch_bounds__(256, kMode == 2 ? 6 : 4) k_finalize(int32_t* _
         const VoxelEntries E{buckets + v * kBucket, entries, c, s, c + (e - s)};
         count[v] = 0;
         uint32_t tot_sum, tot_cnt;
-        const bool over = voxel_merge<K, VT>(E, m_old, ids, vals, np, tot_sum, tot_cnt);
+        bool over;
+        if (E.n == c) {
+            unsigned long long ev[kBucket];
+            bucket_sort(b, c, ev);
+            over = voxel_merge_sorted<K, VT>(E, ev, m_old, ids, vals, np, tot_sum, tot_cnt);
+        } else {
+            over = voxel_merge<K, VT>(E, m_old, ids, vals, np, tot_sum, tot_cnt);
+        }
 #pragma unroll
         for (int i = 0; i < RB / 16; ++i) g_rec[i] = my_rec[i];
 #pragma unroll
@@ -793,8 +809,9 @@ __device__ __forceinline__ void bulk_store(void* gdst, const void* ssrc, uint32_
 // volume in mapped host memory) by all threads in consecutive 16-byte stores,
 // so the host link sees whole lines.  A run shorter than 256 voxels (the
 // grid's tail) is stored thread by thread.
+// 6 CTAs per SM (40 registers)
 template <int K, typename VT, bool kBulk>
-__global__ void __launch_bounds__(256, 6) k_finalize_full(  // 40 registers: 6 CTAs per SMint32_t* __restrict__ count,
+__global__ void __launch_bounds__(256, 6) k_finalize_full(int32_t* __restrict__ count,
                                                        const unsigned long long* __restrict__ buckets,
                                                        const int32_t* __restrict__ offsets,
                                                        const unsigned long long* __restrict__ entries,
