@@ -333,6 +333,32 @@ def _host_ptr(t, name, shape=None):
     return ctypes.c_void_p(t.data_ptr())
 
 
+def _dev_shape2(t, name):
+    """(rows, columns) of a contiguous 2-D float32 CUDA tensor."""
+    import torch
+    if type(t) is not torch.Tensor or not t.is_cuda or not t.is_contiguous() or t.dim() != 2 or \
+            t.dtype is not torch.float32:
+        raise TypeError(f"{name} must be a contiguous 2-D float32 CUDA tensor")
+    return t.shape
+
+
+def _dev_addr(t, name, shape):
+    """Device address of a contiguous 32-bit CUDA tensor of the given shape, as an int."""
+    import torch
+    if type(t) is not torch.Tensor or not t.is_cuda or not t.is_contiguous() or t.element_size() != 4:
+        raise TypeError(f"{name} must be a contiguous CUDA tensor of 32-bit words")
+    if t.shape != shape:
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _stream_addr(stream):
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return stream if isinstance(stream, int) else stream.cuda_stream
+
+
 def _dev_ptr(t, dtype_name, shape=None):
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda:
@@ -539,14 +565,22 @@ class Session:
     # ---- reslicing
     def reslice(self, image_to_world, out, mask, px_mm, params=None, stream=None):
         """Reslice one plane into out (H, W) float32 and mask (H, ceil(W/32)) int32 device tensors."""
-        H, W = (int(x) for x in out.shape)
-        pl = self.__dict__.get("_plane")
-        if pl is None:
-            pl = self._plane = dare_plane()  # reused: a session is driven by one thread at a time
-        fill_plane(pl, W, H, px_mm, image_to_world)
+        fast = self.__dict__.get("_fast")
+        if fast is None:
+            # one plane struct per session, reused (a session is driven by one thread
+            # at a time), with a numpy view of its pose for a cheap copy
+            pl = dare_plane()
+            fast = self._fast = (pl, ctypes.byref(pl), np.ctypeslib.as_array(pl.image_to_world), lib().dare_reslice)
+        pl, pl_ref, pose, fn = fast
+        H, W = _dev_shape2(out, "out")
+        pose[:] = np.asarray(image_to_world, dtype=np.float64).reshape(16)
+        pl.width, pl.height = W, H
+        pl.px_mm[0], pl.px_mm[1] = px_mm[0], px_mm[1]
         p = params if params is not None else params_default()
-        check(lib().dare_reslice(self._h, ctypes.byref(pl), ctypes.byref(p), _dev_ptr(out, "out"),
-                                 _dev_ptr(mask, "mask", (H, mask_words(W))), _stream_ptr(stream)), "dare_reslice")
+        rc = fn(self._h, pl_ref, ctypes.byref(p), out.data_ptr(), _dev_addr(mask, "mask", (H, (W + 31) >> 5)),
+                _stream_addr(stream))
+        if rc != DARE_OK:
+            raise DareError(rc, "dare_reslice", last_error())
 
     def reslice_scalar(self, image_to_world, out, mask, px_mm, unassigned=0.0, stream=None):
         H, W = (int(x) for x in out.shape)
