@@ -159,7 +159,7 @@ __device__ void tile_setup(const ResliceJob& J, int u0, int v0, int u1, int v1, 
     T.Od = static_cast<int>(lmax(lmin(Gd >> kFixBits, 1 << 24), -(1 << 24)));
 }
 
-template <int K, typename VT, typename WT, int D, bool kItems>
+template <int K, typename VT, typename WT, int D>
 __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& T, int u0, int v0, int u1, int v1,
                                           float2* sAB, int* sCol) {
     constexpr int E1 = Axes<D>::E1, E2 = Axes<D>::E2;
@@ -182,50 +182,26 @@ __device__ __forceinline__ void tile_body(const ResliceJob& J, const TileSetup& 
         const uint8_t* const rec = J.rec;
         const int64_t sx = 1, sy = J.dims[0], sz = static_cast<int64_t>(J.dims[0]) * J.dims[1];
         const int64_t st1 = E1 == 0 ? sx : sy, st2 = E2 == 1 ? sy : sz, std_ = D == 0 ? sx : (D == 1 ? sy : sz);
-        // column c's voxel column (c1, c2) and the levels lo .. top its pixels may read
-        auto bounds = [&](int c, int& c1, int& c2, int& lo, int& top) {
+        for (int c = threadIdx.x; c < ncol; c += kThreads) {
             const int k2 = static_cast<int>((static_cast<float>(c) + 0.5f) * inv_n1);
             const int k1 = c - k2 * n1;
-            c1 = b1 + k1;
-            c2 = b2 + k2;
+            const int c1 = b1 + k1, c2 = b2 + k2;
             const float uc = ou + m00 * c1 + m01 * c2;
             const float vc = ov + m10 * c1 + m11 * c2;
             const bool near = fabsf(uc - fminf(fmaxf(uc, fu0), fu1)) <= hu && fabsf(vc - fminf(fmaxf(vc, fv0), fv1)) <= hv;
             const float gd = alpha + beta1 * c1 + beta2 * c2;
-            lo = 0;
-            top = -1;
+            int lo = 0, top = -1;  // levels lo .. top may be read
             if (near && fabsf(gd) < 16384.0f && static_cast<unsigned>(c1) < static_cast<unsigned>(d1) &&
                 static_cast<unsigned>(c2) < static_cast<unsigned>(d2)) {
                 lo = static_cast<int>(floorf(gd - sm));
                 top = min(static_cast<int>(floorf(gd + sm)) + 1, dd - 1);
             }
-        };
-        if constexpr (kItems) {
-            // one (column, level) slot per thread and round: a record read each,
-            // so a tile's reads are not chained level after level (a lone
-            // plane, whose tiles do not fill the device, waits on that chain)
-            const float inv_l = 1.0f / static_cast<float>(L);
-            for (int it = threadIdx.x; it < ncol * L; it += kThreads) {
-                const int c = static_cast<int>((static_cast<float>(it) + 0.5f) * inv_l), lev = it - c * L;
-                int c1, c2, lo, top;
-                bounds(c, c1, c2, lo, top);
-                if (lev == 0) sCol[c] = lo;
+            sCol[c] = lo;
+            const int64_t base = c1 * st1 + c2 * st2;
+            for (int lev = 0; lev < L; ++lev) {
                 const int g = lo + lev;
-                sAB[it] = (g >= 0 && g <= top)
-                              ? collapse_voxel<K, VT, WT>(rec, c1 * st1 + c2 * st2 + g * std_, wt)
-                              : make_float2(0.0f, 0.0f);
-            }
-        } else {
-            for (int c = threadIdx.x; c < ncol; c += kThreads) {
-                int c1, c2, lo, top;
-                bounds(c, c1, c2, lo, top);
-                sCol[c] = lo;
-                const int64_t base = c1 * st1 + c2 * st2;
-                for (int lev = 0; lev < L; ++lev) {
-                    const int g = lo + lev;
-                    sAB[c * L + lev] = (g >= 0 && g <= top) ? collapse_voxel<K, VT, WT>(rec, base + g * std_, wt)
-                                                            : make_float2(0.0f, 0.0f);
-                }
+                sAB[c * L + lev] = (g >= 0 && g <= top) ? collapse_voxel<K, VT, WT>(rec, base + g * std_, wt)
+                                                        : make_float2(0.0f, 0.0f);
             }
         }
         __syncthreads();
@@ -333,20 +309,19 @@ __device__ __forceinline__ void tile_start(const ResliceJob* src, int job, int l
     if (threadIdx.x == 0 && T.direct && !J0.direct) atomicAdd(&g_fallback_tiles, 1ull);
 }
 
-template <int K, typename VT, typename WT, bool kItems = false>
+template <int K, typename VT, typename WT>
 __device__ __forceinline__ void tile_run(const ResliceJob& J, const TileSetup& T, float2* sAB, int* sCol) {
     switch (J.d) {
-    case 0: tile_body<K, VT, WT, 0, kItems>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
-    case 1: tile_body<K, VT, WT, 1, kItems>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
-    default: tile_body<K, VT, WT, 2, kItems>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    case 0: tile_body<K, VT, WT, 0>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    case 1: tile_body<K, VT, WT, 1>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
+    default: tile_body<K, VT, WT, 2>(J, T, T.u0, T.v0, T.u1, T.v1, sAB, sCol); break;
     }
 }
 
 // One CTA per tile.  With `uniform` every job has `n_tiles` tiles and the job
 // is blockIdx.y; otherwise blockIdx.x runs over all tiles of the launch and
 // the first warp finds the job by binary search over tile_base.
-// kItems (single planes): the column pass takes (column, level) slots.
-template <int K, typename VT, typename WT, bool kItems>
+template <int K, typename VT, typename WT>
 __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_tiled(const ResliceJob* __restrict__ jobs,
                                                                                    int n_jobs, int tile_offset,
                                                                                    int uniform,
@@ -370,7 +345,7 @@ __global__ void __launch_bounds__(kThreads, DARE_TILED_MIN_BLOCKS) k_reslice_til
     // launched with programmatic serialization after the weight-table kernel: its
     // table is complete and visible from here (no effect on an ordinary launch)
     asm volatile("griddepcontrol.wait;" ::: "memory");
-    tile_run<K, VT, WT, kItems>(sJob, T, sAB, sCol);
+    tile_run<K, VT, WT>(sJob, T, sAB, sCol);
 }
 
 // Persistent form: CTA b first takes tile b, then tiles gridDim.x + k for the
@@ -440,10 +415,8 @@ cudaError_t tiled_launch(const ResliceJob* jobs_dev, const ResliceJob* one, int 
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
     cfg.numAttrs = pdl ? 1 : 0;
-    // a single plane: its column passes spread over (column, level) slots
-    if (one)
-        return cudaLaunchKernelEx(&cfg, k_reslice_tiled<K, VT, WT, true>, nullptr, n_jobs, tile_offset, uniform, *one);
-    return cudaLaunchKernelEx(&cfg, k_reslice_tiled<K, VT, WT, false>, jobs_dev, n_jobs, tile_offset, uniform, dummy);
+    return cudaLaunchKernelEx(&cfg, k_reslice_tiled<K, VT, WT>, one ? nullptr : jobs_dev, n_jobs, tile_offset, uniform,
+                              one ? *one : dummy);
 }
 
 template <int K, typename VT>
