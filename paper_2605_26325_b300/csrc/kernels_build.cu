@@ -35,7 +35,10 @@ namespace {
 constexpr int kTile = kScatterTile;   // frame tile: 32 x 32 pixels
 constexpr int kThreads = 256;         // a 2 x 2 pixel block per thread
 #ifndef DARE_COUNT_MIN_BLOCKS
-#define DARE_COUNT_MIN_BLOCKS 6  // 40 registers, 8 bytes of spill: faster than 5 CTAs at 46
+#define DARE_COUNT_MIN_BLOCKS 6  // 40 registers: faster than 5 CTAs at 46
+#endif
+#ifndef DARE_COUNT_MIN_BLOCKS_FULL
+#define DARE_COUNT_MIN_BLOCKS_FULL 7  // without the touched list (4 KB less shared memory), 32 registers
 #endif
 constexpr int kHash = 2048;           // >= 2 x pixels per tile: never full
 constexpr int kEmptyKey = -1;
@@ -247,7 +250,9 @@ __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long lo
 // empties before the chunk's first count launch.  With `touched`, the
 // voxels this build reaches for the first time are listed: touched[i], and
 // tindex[v] = i, i < *n_touched.
-__global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_count(const __grid_constant__ ScatterArgs A,
+template <bool kTouched>
+__global__ void __launch_bounds__(kThreads, kTouched ? DARE_COUNT_MIN_BLOCKS : DARE_COUNT_MIN_BLOCKS_FULL)
+    k_scatter_count(const __grid_constant__ ScatterArgs A,
                                                             int32_t* __restrict__ count,
                                                             unsigned long long* __restrict__ buckets,
                                                             uint4* __restrict__ pairs, int32_t* __restrict__ n_pairs,
@@ -258,7 +263,7 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
     __shared__ int4 org[3];  // small steps: the tile origin per axis (integer part, remainder, steps)
     __shared__ TileBox B;
     __shared__ int n_list, n_new, new_base;
-    __shared__ int s_new[kTile * kTile];  // voxels whose first entry this tile made
+    __shared__ int s_new[kTouched ? kTile * kTile : 1];  // voxels whose first entry this tile made
     const int f = blockIdx.z;
     const int u0 = blockIdx.x * kTile, v0 = blockIdx.y * kTile;
     if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
@@ -317,7 +322,7 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
                     e[j] = fid | (static_cast<unsigned long long>(x >> kPackShift) << 32) | (x & ((1u << kPackShift) - 1));
                 }
             }
-            emit4(vi, e, count, buckets, pairs, n_pairs, touched ? s_new : nullptr, &n_new);
+            emit4(vi, e, count, buckets, pairs, n_pairs, kTouched ? s_new : nullptr, &n_new);
         }
     } else {
         // hash table over voxel indices
@@ -351,10 +356,10 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS) k_scatter_cou
                     e[j] = fid | (static_cast<unsigned long long>(npx[h]) << 32) | sums[h];
                 }
             }
-            emit4(vi, e, count, buckets, pairs, n_pairs, touched ? s_new : nullptr, &n_new);
+            emit4(vi, e, count, buckets, pairs, n_pairs, kTouched ? s_new : nullptr, &n_new);
         }
     }
-    if (touched) {
+    if constexpr (kTouched) {
         __syncthreads();
         if (threadIdx.x == 0) new_base = n_new ? atomicAdd(n_touched, n_new) : 0;
         __syncthreads();
@@ -975,8 +980,12 @@ cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, unsigned 
                                  int32_t* n_pairs, int32_t* touched, int32_t* tindex, int32_t* n_touched,
                                  cudaStream_t st) {
     if (a.n <= 0) return cudaSuccess;
-    k_scatter_count<<<scatter_grid(a), kThreads, 0, st>>>(a, count, buckets, pairs, n_pairs, touched, tindex,
-                                                          n_touched);
+    if (touched)
+        k_scatter_count<true><<<scatter_grid(a), kThreads, 0, st>>>(a, count, buckets, pairs, n_pairs, touched, tindex,
+                                                                    n_touched);
+    else
+        k_scatter_count<false><<<scatter_grid(a), kThreads, 0, st>>>(a, count, buckets, pairs, n_pairs, nullptr,
+                                                                     nullptr, nullptr);
     return cudaPeekAtLastError();
 }
 
