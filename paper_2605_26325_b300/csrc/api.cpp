@@ -311,6 +311,12 @@ struct dare_session_s {
     float* geom_dev = nullptr;             // max_frames x kGeomFloats: probe geometry (curvilinear kernel)
     double* geom_off_dev = nullptr;        // max_frames x 2: its FP64 apex-relative offsets
     unsigned long long* overflow_dev = nullptr;
+    // single-plane graph: the weight table and the tiled reslice as two kernel
+    // nodes, their parameters replaced on every call (one launch on the host)
+    cudaGraph_t sp_graph = nullptr;
+    cudaGraphExec_t sp_exec = nullptr;
+    cudaGraphNode_t sp_node[2] = {nullptr, nullptr};
+    void* sp_fn[2] = {nullptr, nullptr};
     std::vector<double> frames_host;       // n_frames x 9
     std::vector<double> probe_host;        // n_frames x 3: probe kind, FP64 offsets
     int32_t n_curv = 0;                    // frames from a curvilinear probe
@@ -1399,6 +1405,8 @@ dare_status dare_session_destroy(dare_session s) {
     if (s->order_ev) cudaEventSynchronize(s->order_ev);
     for (int k = 0; k < dare_session_s::kPinSlots; ++k)
         if (s->pinned_ev[k]) cudaEventSynchronize(s->pinned_ev[k]);
+    if (s->sp_exec) cudaGraphExecDestroy(s->sp_exec);
+    if (s->sp_graph) cudaGraphDestroy(s->sp_graph);
     if (s->ws) {
         s->dev_free(s->ws, s->ws_bytes, s->last_stream);
         g_in_use -= static_cast<int64_t>(s->ws_bytes);
@@ -1834,6 +1842,42 @@ dare_status dare_session_set_probe(dare_session s, const dare_probe* probe, cons
 }
 
 
+// One plane's weight table and tiled reslice as the session's two-node graph:
+// both nodes' parameters (grid and job) are replaced and the graph is launched
+// once, which costs the host about half of two kernel launches and starts the
+// reslice on the device right after the table.  The graph is rebuilt when the
+// kernels change (storage type, slots or weight precision), or if an update is
+// refused.
+dare_status single_plane_graph(dare_session s, const TableJob& tj, const ResliceJob& job, int n_tiles,
+                               const TableParams& tp, int half_w, cudaStream_t st) {
+    NodeArgs a_tab, a_res;
+    cudaKernelNodeParams p_tab, p_res;
+    CUDA_TRY(weight_table_node(tj, tj.n_frames, tp, a_tab, &p_tab));
+    CUDA_TRY(reslice_tiled_node(job, n_tiles, s->K, s->dtype, half_w, a_res, &p_res));
+    bool ready = s->sp_exec && s->sp_fn[0] == p_tab.func && s->sp_fn[1] == p_res.func;
+    if (ready && (cudaGraphExecKernelNodeSetParams(s->sp_exec, s->sp_node[0], &p_tab) != cudaSuccess ||
+                  cudaGraphExecKernelNodeSetParams(s->sp_exec, s->sp_node[1], &p_res) != cudaSuccess)) {
+        cudaGetLastError();
+        ready = false;
+    }
+    if (!ready) {
+        if (s->sp_exec) cudaGraphExecDestroy(s->sp_exec);
+        if (s->sp_graph) cudaGraphDestroy(s->sp_graph);
+        s->sp_exec = nullptr;
+        s->sp_graph = nullptr;
+        s->sp_fn[0] = s->sp_fn[1] = nullptr;
+        CUDA_TRY(cudaGraphCreate(&s->sp_graph, 0));
+        CUDA_TRY(cudaGraphAddKernelNode(&s->sp_node[0], s->sp_graph, nullptr, 0, &p_tab));
+        CUDA_TRY(cudaGraphAddKernelNode(&s->sp_node[1], s->sp_graph, &s->sp_node[0], 1, &p_res));
+        CUDA_TRY(cudaGraphInstantiate(&s->sp_exec, s->sp_graph, 0));
+        s->sp_fn[0] = p_tab.func;
+        s->sp_fn[1] = p_res.func;
+    }
+    g_launches += 2;
+    CUDA_TRY(cudaGraphLaunch(s->sp_exec, st));
+    return DARE_OK;
+}
+
 dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
                          uint32_t* mask_dev, void* stream) {
     if (!s) return fail(DARE_E_INVALID, "session is NULL");
@@ -1898,12 +1942,25 @@ dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_par
     tj.frames = s->frames_dev;
     tj.wtab = s->ws;
     tj.n_frames = s->n_frames;
+    ResliceJob job = make_job(s, plane, s->ws, out_dev, mask_dev, params->unassigned, params);
+    const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
+    if (s->n_frames > 0 && !g_trace_on.load() && !(s->cfg.flags & DARE_SESSION_L2_PERSIST) &&
+        !general_support(params) && use_tiled(params)) {
+        const int th = tile_rows_single(job, plane, params);
+        cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+        if (th > 0 && cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusNone) {
+            job.tile_h = th;
+            job.tile_base = 0;
+            rc = single_plane_graph(s, tj, job, tiles_of(plane, th), table_params(params), half_w, st);
+            if (rc != DARE_OK) return rc;
+            g_tiled_planes += 1;
+            return session_end(s, st);
+        }
+    }
     if (s->n_frames > 0) {
         KernelScope ks("weight_table", st, 1);
         CUDA_TRY(launch_weight_tables(nullptr, &tj, 1, s->n_frames, table_params(params), st));
     }
-    ResliceJob job = make_job(s, plane, s->ws, out_dev, mask_dev, params->unassigned, params);
-    const int half_w = params->weight_dtype == DARE_WEIGHTS_F16;
     L2Window l2((s->cfg.flags & DARE_SESSION_L2_PERSIST) ? s->rec : nullptr, size_t(s->n_vox) * s->rec_bytes, st);
     CUDA_TRY(launch_one(job, plane, params, s->K, s->dtype, half_w, s->n_frames > 0, st));
     return session_end(s, st);

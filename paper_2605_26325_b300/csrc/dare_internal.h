@@ -220,6 +220,21 @@ struct TileQueue {
     int32_t pad[2];
 };
 // persistent form: one CTA per resident slot of the device, tiles taken from the queue
+// Kernel-node parameters of the single-plane weight table and tiled reslice,
+// for a session's two-node CUDA graph: out->kernelParams points into `args`,
+// which must outlive the call that consumes out (node creation or update).
+struct NodeArgs {
+    const void* null_ptr = nullptr;
+    int32_t ints[3] = {0, 0, 0};
+    TableJob tj{};
+    TableParams tp{};
+    ResliceJob rj{};
+    void* ptrs[5] = {};
+};
+cudaError_t weight_table_node(const TableJob& one, int max_frames, const TableParams& p, NodeArgs& args,
+                              cudaKernelNodeParams* out);
+cudaError_t reslice_tiled_node(const ResliceJob& one, int n_tiles, int K, int dtype, int half_weights, NodeArgs& args,
+                               cudaKernelNodeParams* out);
 cudaError_t launch_reslice_tiled_persistent(const ResliceJob* jobs_dev, int n_jobs, TileQueue* queue, int K,
                                             int dtype, int half_weights, cudaStream_t st);
 // sizes (and loads) the persistent kernel for (K, dtype, weights): before a stream capture launches it

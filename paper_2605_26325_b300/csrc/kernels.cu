@@ -444,6 +444,25 @@ cudaError_t launch_weight_tables(const TableJob* jobs_dev, const TableJob* one_j
     return cudaPeekAtLastError();
 }
 
+cudaError_t weight_table_node(const TableJob& one, int max_frames, const TableParams& p, NodeArgs& args,
+                              cudaKernelNodeParams* out) {
+    if (max_frames <= 0 || !out) return cudaErrorInvalidValue;
+    const int threads = 256;
+    args.null_ptr = nullptr;
+    args.tj = one;
+    args.tp = p;
+    args.ptrs[0] = &args.null_ptr;  // jobs: none (one job by value)
+    args.ptrs[1] = &args.tj;
+    args.ptrs[2] = &args.tp;
+    *out = cudaKernelNodeParams{};
+    out->func = reinterpret_cast<void*>(k_weight_table);
+    out->gridDim = dim3((max_frames + threads - 1) / threads);
+    out->blockDim = dim3(threads);
+    out->sharedMemBytes = 0;
+    out->kernelParams = args.ptrs;
+    return cudaSuccess;
+}
+
 cudaError_t launch_reslice_plain(const ResliceJob* jobs_dev, const ResliceJob* one_job, int n_jobs, int max_w,
                                  int max_h, int K, int dtype, int half_weights, cudaStream_t st) {
     if (n_jobs <= 0) return cudaSuccess;

@@ -484,6 +484,53 @@ cudaError_t launch_reslice_tiled(const ResliceJob* jobs_dev, const ResliceJob* o
                      after_table, st);
 }
 
+namespace {
+template <int K, typename VT, typename WT>
+void* tiled_fn() {
+    return reinterpret_cast<void*>(k_reslice_tiled<K, VT, WT>);
+}
+template <int K>
+void* tiled_fn_k(int dtype, int half_w) {
+    switch (dtype) {
+    case DARE_U8: return half_w ? tiled_fn<K, uint8_t, __half>() : tiled_fn<K, uint8_t, float>();
+    case DARE_F16: return half_w ? tiled_fn<K, __half, __half>() : tiled_fn<K, __half, float>();
+    case DARE_BF16: return half_w ? tiled_fn<K, __nv_bfloat16, __half>() : tiled_fn<K, __nv_bfloat16, float>();
+    case DARE_F32: return half_w ? tiled_fn<K, float, __half>() : tiled_fn<K, float, float>();
+    }
+    return nullptr;
+}
+}  // namespace
+
+cudaError_t reslice_tiled_node(const ResliceJob& one, int n_tiles, int K, int dtype, int half_weights, NodeArgs& args,
+                               cudaKernelNodeParams* out) {
+    if (n_tiles <= 0 || !out) return cudaErrorInvalidValue;
+    void* fn = nullptr;
+    switch (K) {
+    case 4: fn = tiled_fn_k<4>(dtype, half_weights); break;
+    case 8: fn = tiled_fn_k<8>(dtype, half_weights); break;
+    case 12: fn = tiled_fn_k<12>(dtype, half_weights); break;
+    case 16: fn = tiled_fn_k<16>(dtype, half_weights); break;
+    }
+    if (!fn) return cudaErrorInvalidValue;
+    args.null_ptr = nullptr;
+    args.ints[0] = 1;  // n_jobs
+    args.ints[1] = 0;  // tile_offset
+    args.ints[2] = 0;  // uniform
+    args.rj = one;
+    args.ptrs[0] = &args.null_ptr;  // jobs: none (one job by value)
+    args.ptrs[1] = &args.ints[0];
+    args.ptrs[2] = &args.ints[1];
+    args.ptrs[3] = &args.ints[2];
+    args.ptrs[4] = &args.rj;
+    *out = cudaKernelNodeParams{};
+    out->func = fn;
+    out->gridDim = dim3(n_tiles);
+    out->blockDim = dim3(kThreads);
+    out->sharedMemBytes = 0;
+    out->kernelParams = args.ptrs;
+    return cudaSuccess;
+}
+
 cudaError_t launch_reslice_tiled_persistent(const ResliceJob* jobs_dev, int n_jobs, TileQueue* queue, int K,
                                             int dtype, int half_weights, cudaStream_t st) {
     if (n_jobs <= 0) return cudaSuccess;
