@@ -391,6 +391,10 @@ dare_status dare_session_cache_stats(dare_session s, int64_t out[4]);
  * both paths for radius_vox 1..16 (the tiled kernel up to a support of 9
  * voxels per axis, i.e. radius 4; planes beyond it, or whose tiles do not fit
  * shared memory, gather per pixel).  DARE_E_UNSUPPORTED above radius 16.
+ * A tiled TENT R = 1 plane runs as the session's two-node CUDA graph (weight
+ * table, reslice), built on the first such call and updated on later ones;
+ * with tracing on, on an L2-persist session or while `stream` is being
+ * captured, as two kernel launches.  The results are the same either way.
  */
 dare_status dare_reslice(dare_session s, const dare_plane* plane, const dare_params* params, float* out_dev,
                          uint32_t* mask_dev, void* stream);

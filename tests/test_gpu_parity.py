@@ -701,3 +701,32 @@ def test_build_frames_at_odd_address(tiny, W, H):
         assert np.array_equal(got["values"].view(np.uint32), vals.view(np.uint32))
         assert np.array_equal(got["npix"], npix)
         s.close()
+
+
+def test_single_plane_graph_equals_launches(tiny, tiny_f32):
+    """A single tiled plane runs as the session's two-node graph (weight table,
+    reslice) with its node parameters replaced each call; while tracing it runs
+    as two launches instead. Both give the same bits, across plane sizes (the
+    reslice node's grid changes), FP16 and FP32 weights (the graph is rebuilt)
+    and back."""
+    s, vol = tiny_f32
+    sizes = [(64, 48), (130, 101), (37, 29), (64, 48)]
+    for wd in (dare.DARE_WEIGHTS_F32, dare.DARE_WEIGHTS_F16, dare.DARE_WEIGHTS_F32):
+        p = dare.params_default(path=dare.DARE_PATH_TILED, weight_dtype=wd)
+        for k, (W, H) in enumerate(sizes):
+            T = tiny.reslice_poses[(3 * k + wd) % len(tiny.reslice_poses)]
+            n0 = dare.launch_count()
+            g = gpu_reslice(s, T, W, H, tiny.out_px, p)
+            assert dare.launch_count() - n0 == 2
+            dare.trace_read()
+            dare.trace_enable(True)
+            try:
+                d = gpu_reslice(s, T, W, H, tiny.out_px, p)
+                t = dare.trace_read()
+            finally:
+                dare.trace_enable(False)
+            assert t["weight_table"][0] == 1 and t["reslice_tiled"][0] == 1
+            assert np.array_equal(g[1], d[1]) and np.array_equal(g[0], d[0])
+            if wd == dare.DARE_WEIGHTS_F32:
+                ref, rm = oracle.reslice(vol, T, W, H, tiny.out_px, ora_params(p))
+                assert_parity(g[0], g[1], ref, rm, W)
