@@ -1868,7 +1868,14 @@ dare_status single_plane_graph(dare_session s, const TableJob& tj, const Reslice
         s->sp_fn[0] = s->sp_fn[1] = nullptr;
         CUDA_TRY(cudaGraphCreate(&s->sp_graph, 0));
         CUDA_TRY(cudaGraphAddKernelNode(&s->sp_node[0], s->sp_graph, nullptr, 0, &p_tab));
-        CUDA_TRY(cudaGraphAddKernelNode(&s->sp_node[1], s->sp_graph, &s->sp_node[0], 1, &p_res));
+        CUDA_TRY(cudaGraphAddKernelNode(&s->sp_node[1], s->sp_graph, nullptr, 0, &p_res));
+        // a programmatic edge: the reslice's CTAs start (and set their tiles up)
+        // as soon as the table kernel has begun; they wait for its results
+        // (griddepcontrol.wait) before reading the table
+        cudaGraphEdgeData edge{};
+        edge.from_port = cudaGraphKernelNodePortProgrammatic;
+        edge.type = cudaGraphDependencyTypeProgrammatic;
+        CUDA_TRY(cudaGraphAddDependencies(s->sp_graph, &s->sp_node[0], &s->sp_node[1], &edge, 1));
         CUDA_TRY(cudaGraphInstantiate(&s->sp_exec, s->sp_graph, 0));
         s->sp_fn[0] = p_tab.func;
         s->sp_fn[1] = p_res.func;
