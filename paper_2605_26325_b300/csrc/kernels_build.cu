@@ -895,7 +895,9 @@ __global__ void __launch_bounds__(256, 6) k_finalize_full(int32_t* __restrict__ 
                 const uint4* s_np4 = reinterpret_cast<const uint4*>(s_np);
                 for (int i = threadIdx.x; i < 256 * K * 2 / 16; i += 256) g_np[i] = s_np4[i];
             }
-            __syncthreads();
+            // only a CTA with another run waits here: otherwise the other warps exit
+            // while thread 0 waits for its copies to leave shared memory
+            if (v0 + static_cast<int64_t>(gridDim.x) * 256 < n_vox) __syncthreads();
         }
     }
     // Each run already waited until its copies had read shared memory; their
