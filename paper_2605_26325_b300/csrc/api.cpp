@@ -1657,7 +1657,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
         int32_t* tl = listed ? t_list : nullptr;
         int32_t* ti = listed ? t_index : nullptr;
         int32_t* tn = listed ? t_n : nullptr;
-        if (listed) CUDA_TRY(cudaMemsetAsync(t_n, 0, sizeof(int32_t), st));
+        if (listed || mode == 2) CUDA_TRY(cudaMemsetAsync(t_n, 0, sizeof(int32_t), st));
         CUDA_TRY(cudaMemsetAsync(n_pairs, 0, sizeof(int32_t), st));  // the chunk's overflow list starts empty
         if (!host) {
             KernelScope ks("scatter_count", st, 1);
@@ -1704,9 +1704,19 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
             }
             s->pending_clear = false;  // a full-write finalize (mode 2) writes every voxel
             s->fresh = false;          // from here on the records may hold samples
-            KernelScope ks("finalize", st, 1);
-            CUDA_TRY(launch_finalize(s->count, buckets, offsets, entries, s->n_vox, s->rec, s->npix, s->ssum, s->scnt,
-                                     s->K, s->dtype, mode, s->host_vol ? 0 : 1, s->overflow_dev, tl, tn, max_t, st));
+            // a full write lists the voxels with entries past their bucket in the touched
+            // list (unused in that mode) for its second kernel
+            {
+                KernelScope ks("finalize", st, 1);
+                CUDA_TRY(launch_finalize(s->count, buckets, offsets, entries, s->n_vox, s->rec, s->npix, s->ssum,
+                                         s->scnt, s->K, s->dtype, mode, s->host_vol ? 0 : 1, s->overflow_dev, tl, tn,
+                                         max_t, mode == 2 ? t_list : nullptr, mode == 2 ? t_n : nullptr, st));
+            }
+            if (mode == 2) {
+                KernelScope ks("finalize_deferred", st, 1);
+                CUDA_TRY(launch_finalize_deferred(t_list, t_n, buckets, offsets, entries, s->rec, s->npix, s->ssum,
+                                                  s->scnt, s->K, s->dtype, s->overflow_dev, max_t, st));
+            }
         }
     }
     rc = session_end(s, st);

@@ -153,11 +153,20 @@ int64_t scan_block_sums_needed(int64_t n);
 // a voxel's entries: count[v] (<= kBucket) in its bucket, then entries[offsets[v], offsets[v + 1]);
 // count is returned to zero
 // touched / n_touched (modes 0 and 1): only the listed voxels, offsets by list position, at most max_t
+// deferred / n_deferred (mode 2; *n_deferred zero on entry, room for every voxel with entries past its
+// bucket): the full-write pass lists such voxels and leaves them empty for launch_finalize_deferred
 cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, const int32_t* offsets,
                             const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
                             uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
                             unsigned long long* overflow, const int32_t* touched, const int32_t* n_touched,
-                            int64_t max_t, cudaStream_t st);
+                            int64_t max_t, int32_t* deferred, int32_t* n_deferred, cudaStream_t st);
+// the voxels a full-write finalize listed (at most max_items), one thread each: record, npix row,
+// scalar totals and the capacity-rule count, as the full-write pass would have written them
+cudaError_t launch_finalize_deferred(const int32_t* deferred, const int32_t* n_deferred,
+                                     const unsigned long long* buckets, const int32_t* offsets,
+                                     const unsigned long long* entries, uint8_t* rec, uint16_t* npix,
+                                     uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
+                                     unsigned long long* overflow, int64_t max_items, cudaStream_t st);
 cudaError_t launch_reslice_scalar(const ResliceJob& job, const uint32_t* scal_sum, const uint32_t* scal_cnt,
                                   cudaStream_t st);
 cudaError_t launch_footprint(const ResliceJob& job, uint32_t* bitmap, unsigned long long* count, cudaStream_t st);

@@ -595,13 +595,13 @@ __device__ __forceinline__ bool append_in_order(const VoxelEntries& E, int m_old
 // the m_old stored samples, entries of one frame merged.  Returns the new
 // sample count, or -1 when more than K samples exist (the general merge then
 // redoes the voxel from its stored samples).
-template <int K, typename VT>
-__device__ __forceinline__ int append_sorted(const unsigned long long (&e)[kBucket], int m_old, uint16_t* ids,
+template <int K, typename VT, int N = kBucket>
+__device__ __forceinline__ int append_sorted(const unsigned long long (&e)[N], int m_old, uint16_t* ids,
                                              VT* vals, uint16_t* np) {
     int m = m_old, cur = -1, cnt = 0, sum = 0;
 #pragma unroll
-    for (int j = 0; j <= kBucket; ++j) {
-        const bool end = j == kBucket || e[j] == ~0ull;
+    for (int j = 0; j <= N; ++j) {
+        const bool end = j == N || e[j] == ~0ull;
         const int f = end ? -2 : ent_frame(e[j]);
         if (f != cur) {
             if (cur >= 0) {
@@ -823,7 +823,8 @@ __global__ void __launch_bounds__(256, 6) k_finalize_full(int32_t* __restrict__ 
                                                        int64_t n_vox, uint8_t* __restrict__ rec,
                                                        uint16_t* __restrict__ npix, uint32_t* __restrict__ scal_sum,
                                                        uint32_t* __restrict__ scal_cnt,
-                                                       unsigned long long* overflow) {
+                                                       unsigned long long* overflow, int32_t* __restrict__ deferred,
+                                                       int32_t* __restrict__ n_deferred) {
     constexpr int RB = (2 * K + K * static_cast<int>(sizeof(VT)) + 15) / 16 * 16;
     __shared__ __align__(128) uint4 s_rec[256 * RB / 16];
     __shared__ __align__(128) uint2 s_np[256 * K / 4];
@@ -860,7 +861,10 @@ __global__ void __launch_bounds__(256, 6) k_finalize_full(int32_t* __restrict__ 
                     bucket_sort(b, c, ev);
                     over = voxel_merge_sorted<K, VT>(E, ev, 0, ids, vals, np, tot_sum, tot_cnt);
                 } else {
-                    over = voxel_merge<K, VT>(E, 0, ids, vals, np, tot_sum, tot_cnt);
+                    // entries past the bucket (rare, clustered): left to k_finalize_deferred, one
+                    // warp per voxel, so that no thread holds its CTA at the barrier below;
+                    // the empty record written here is overwritten there
+                    deferred[atomicAdd(n_deferred, 1)] = static_cast<int32_t>(v);
                 }
             }
             if (!whole) {
@@ -904,17 +908,137 @@ __global__ void __launch_bounds__(256, 6) k_finalize_full(int32_t* __restrict__ 
     // global writes complete with the grid, so the CTA exits without waiting.
 }
 
+// Voxels the full-write finalize deferred (entries past their bucket: about 3 %
+// of the working volume's covered voxels), one thread each, without barriers.
+// Up to kDeferSort entries are loaded together into registers, sorted by a
+// bitonic network and merged in one pass (a frame split across tiles summed);
+// more entries, or more samples than K (the capacity rule), take the general
+// merge.  The record and npix row are staged in shared memory and stored whole
+// over the empty ones the full-write pass left; the scalar totals sum every entry.
+constexpr int kDeferSort = 16;
+
+__device__ __forceinline__ void sort16(unsigned long long (&e)[kDeferSort]) {
+#pragma unroll
+    for (int k = 2; k <= kDeferSort; k <<= 1)
+#pragma unroll
+        for (int j = k >> 1; j > 0; j >>= 1)
+#pragma unroll
+            for (int i = 0; i < kDeferSort; ++i) {
+                const int l = i ^ j;
+                if (l > i) {
+                    const unsigned long long a = e[i], b = e[l];
+                    const bool swap = ((i & k) == 0) ? (a > b) : (a < b);
+                    e[i] = swap ? b : a;
+                    e[l] = swap ? a : b;
+                }
+            }
+}
+
+template <int K, typename VT>
+__global__ void __launch_bounds__(256) k_finalize_deferred(const int32_t* __restrict__ deferred,
+                                                         const int32_t* __restrict__ n_deferred,
+                                                         const unsigned long long* __restrict__ buckets,
+                                                         const int32_t* __restrict__ offsets,
+                                                         const unsigned long long* __restrict__ entries,
+                                                         uint8_t* __restrict__ rec, uint16_t* __restrict__ npix,
+                                                         uint32_t* __restrict__ scal_sum,
+                                                         uint32_t* __restrict__ scal_cnt,
+                                                         unsigned long long* overflow) {
+    constexpr int RB = (2 * K + K * static_cast<int>(sizeof(VT)) + 15) / 16 * 16;
+    __shared__ __align__(16) uint4 s_rec[256 * RB / 16];
+    __shared__ __align__(16) uint2 s_np[256 * K / 4];
+    uint4* my_rec = s_rec + threadIdx.x * (RB / 16);
+    uint2* my_np = s_np + threadIdx.x * (K / 4);
+    uint16_t* ids = reinterpret_cast<uint16_t*>(my_rec);
+    VT* vals = reinterpret_cast<VT*>(reinterpret_cast<uint8_t*>(my_rec) + 2 * K);
+    uint16_t* np = reinterpret_cast<uint16_t*>(my_np);
+    const int n_items = *n_deferred;
+    for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n_items; it += gridDim.x * blockDim.x) {
+        const int64_t v = deferred[it];
+        const int s0 = offsets[v], n = kBucket + (offsets[v + 1] - s0);
+        empty_record<K, RB>(my_rec);
+#pragma unroll
+        for (int i = 0; i < K / 4; ++i) my_np[i] = make_uint2(0u, 0u);
+        const VoxelEntries E{buckets + v * kBucket, entries, kBucket, s0, n};
+        uint32_t ts = 0, tc = 0;
+        bool over = false;
+        bool done = false;
+        if (n <= kDeferSort) {
+            unsigned long long e[kDeferSort];
+#pragma unroll
+            for (int j = 0; j < kDeferSort; ++j)
+                e[j] = j < kBucket ? __ldg(E.bucket + j) : (j < n ? __ldg(entries + s0 + (j - kBucket)) : ~0ull);
+#pragma unroll
+            for (int j = 0; j < kDeferSort; ++j)
+                if (j < n) {
+                    ts += static_cast<uint32_t>(ent_sum(e[j]));
+                    tc += static_cast<uint32_t>(ent_npix(e[j]));
+                }
+            sort16(e);
+            done = append_sorted<K, VT, kDeferSort>(e, 0, ids, vals, np) >= 0;
+            if (!done) {  // more than K samples: redone by the general merge below
+                empty_record<K, RB>(my_rec);
+#pragma unroll
+                for (int i = 0; i < K / 4; ++i) my_np[i] = make_uint2(0u, 0u);
+            }
+        }
+        if (!done) over = voxel_merge<K, VT>(E, 0, ids, vals, np, ts, tc);
+        uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
+        uint2* g_np = reinterpret_cast<uint2*>(npix + v * K);
+#pragma unroll
+        for (int i = 0; i < RB / 16; ++i) g_rec[i] = my_rec[i];
+#pragma unroll
+        for (int i = 0; i < K / 4; ++i) g_np[i] = my_np[i];
+        if (scal_sum) {
+            scal_sum[v] = ts;
+            scal_cnt[v] = tc;
+        }
+        if (over) atomicAdd(overflow, 1ull);
+    }
+}
+
 template <int K, typename VT>
 cudaError_t finalize_full_v(int32_t* cnt, const unsigned long long* bk, const int32_t* off,
                             const unsigned long long* ent, int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss,
-                            uint32_t* sc, unsigned long long* ovf, bool bulk, cudaStream_t st) {
+                            uint32_t* sc, unsigned long long* ovf, bool bulk, int32_t* dl, int32_t* dn,
+                            cudaStream_t st) {
     const int64_t want = (n_vox + 255) / 256;
     const int blocks = static_cast<int>(want < (1 << 30) ? want : (1 << 30));  // one run per CTA
     if (bulk)
-        k_finalize_full<K, VT, true><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize_full<K, VT, true><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, dl, dn);
     else
-        k_finalize_full<K, VT, false><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf);
+        k_finalize_full<K, VT, false><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, dl, dn);
     return cudaPeekAtLastError();
+}
+
+template <int K, typename VT>
+cudaError_t finalize_deferred_v(const int32_t* dl, const int32_t* dn, const unsigned long long* bk, const int32_t* off,
+                                const unsigned long long* ent, uint8_t* rec, uint16_t* npix, uint32_t* ss,
+                                uint32_t* sc, unsigned long long* ovf, int64_t max_items, cudaStream_t st) {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    // a thread per listed voxel up to 16 CTAs of 256 per SM, then grid-stride
+    const int64_t want = std::max<int64_t>(1, (max_items + 255) / 256);
+    const int blocks = static_cast<int>(std::min<int64_t>(want, int64_t(sms[dev]) * 16));
+    k_finalize_deferred<K, VT><<<blocks, 256, 0, st>>>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf);
+    return cudaPeekAtLastError();
+}
+
+template <int K>
+cudaError_t finalize_deferred_k(const int32_t* dl, const int32_t* dn, const unsigned long long* bk, const int32_t* off,
+                                const unsigned long long* ent, uint8_t* rec, uint16_t* npix, uint32_t* ss,
+                                uint32_t* sc, int dtype, unsigned long long* ovf, int64_t max_items, cudaStream_t st) {
+    switch (dtype) {
+    case DARE_U8: return finalize_deferred_v<K, uint8_t>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
+    case DARE_F16: return finalize_deferred_v<K, __half>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
+    case DARE_BF16:
+        return finalize_deferred_v<K, __nv_bfloat16>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
+    case DARE_F32: return finalize_deferred_v<K, float>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
+    }
+    return cudaErrorInvalidValue;
 }
 
 template <int K, int kMode>
@@ -951,15 +1075,16 @@ template <int K>
 cudaError_t finalize_k(int32_t* cnt, const unsigned long long* bk, const int32_t* off, const unsigned long long* ent,
                        int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int mode,
                        int bulk, unsigned long long* ovf, const int32_t* tl, const int32_t* tn, int64_t max_t,
-                       cudaStream_t st) {
-    if (mode == 2 && tl) return cudaErrorInvalidValue;  // a full write visits every voxel
+                       int32_t* dl, int32_t* dn, cudaStream_t st) {
+    if (mode == 2 && (tl || !dl || !dn)) return cudaErrorInvalidValue;  // a full write visits every voxel
     if (mode == 2) {
         const bool b = bulk != 0;
         switch (dtype) {
-        case DARE_U8: return finalize_full_v<K, uint8_t>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, st);
-        case DARE_F16: return finalize_full_v<K, __half>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, st);
-        case DARE_BF16: return finalize_full_v<K, __nv_bfloat16>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, st);
-        case DARE_F32: return finalize_full_v<K, float>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, st);
+        case DARE_U8: return finalize_full_v<K, uint8_t>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dn, st);
+        case DARE_F16: return finalize_full_v<K, __half>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dn, st);
+        case DARE_BF16:
+            return finalize_full_v<K, __nv_bfloat16>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dn, st);
+        case DARE_F32: return finalize_full_v<K, float>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dn, st);
         }
         return cudaErrorInvalidValue;
     }
@@ -1013,18 +1138,34 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
     return cudaPeekAtLastError();
 }
 
+cudaError_t launch_finalize_deferred(const int32_t* deferred, const int32_t* n_deferred,
+                                     const unsigned long long* buckets, const int32_t* offsets,
+                                     const unsigned long long* entries, uint8_t* rec, uint16_t* npix,
+                                     uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
+                                     unsigned long long* overflow, int64_t max_items, cudaStream_t st) {
+    switch (K) {
+    case 4: return finalize_deferred_k<4>(deferred, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
+    case 8: return finalize_deferred_k<8>(deferred, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
+    case 12: return finalize_deferred_k<12>(deferred, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
+    case 16: return finalize_deferred_k<16>(deferred, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, const int32_t* offsets,
                             const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
                             uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
                             unsigned long long* overflow, const int32_t* touched, const int32_t* n_touched,
-                            int64_t max_t, cudaStream_t st) {
+                            int64_t max_t, int32_t* deferred, int32_t* n_deferred, cudaStream_t st) {
+    int32_t* dl = deferred;
+    int32_t* dn = n_deferred;
     const int32_t* tl = touched;
     const int32_t* tn = n_touched;
     switch (K) {
-    case 4: return finalize_k<4>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, st);
-    case 8: return finalize_k<8>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, st);
-    case 12: return finalize_k<12>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, st);
-    case 16: return finalize_k<16>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, st);
+    case 4: return finalize_k<4>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dn, st);
+    case 8: return finalize_k<8>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dn, st);
+    case 12: return finalize_k<12>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dn, st);
+    case 16: return finalize_k<16>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dn, st);
     }
     return cudaErrorInvalidValue;
 }
