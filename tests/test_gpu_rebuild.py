@@ -22,10 +22,10 @@ pytestmark = pytest.mark.gpu
 DTYPES = [dare.DARE_U8, dare.DARE_F16, dare.DARE_BF16, dare.DARE_F32]
 
 
-def rebuilt(w, dtype, K, first=50):
+def rebuilt(w, dtype, K, first=50, flags=0):
     """A session that held `first` frames, was reset and rebuilt from all of w's frames."""
     s = dare.Session(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, dtype=dtype, max_slots=K,
-                     flags=dare.DARE_SESSION_SCALAR)
+                     flags=dare.DARE_SESSION_SCALAR | flags)
     ft = torch.from_numpy(np.ascontiguousarray(w.frames)).to(DEV)
     s.build(ft[:first], w.frame_poses[:first], w.frame_px)
     s.reset()
@@ -69,13 +69,17 @@ def test_rebuild_ragged_grids(tiny, dims):
 
 
 @pytest.mark.parametrize("K", [4, 12])
-def test_rebuild_dense_voxels(tiny, K):
+@pytest.mark.parametrize("host", [False, True])
+def test_rebuild_dense_voxels(tiny, K, host):
     """Coarse voxels reached by many frames and tiles: entries past a voxel's
-    bucket of 8 (its overflow range) and more samples than K (the capacity rule)."""
+    bucket of 8 (its overflow range: about 1000 voxels with 9 to 16 entries, which
+    the second finalize pass sorts in registers, and about 300 with up to 54, which
+    take the general merge) and more samples than K (the capacity rule); records
+    in device memory and in mapped host memory."""
     g = synth.centred_grid((12, 12, 12), 2.5)
     w = types.SimpleNamespace(grid=g, frames=tiny.frames, frame_poses=tiny.frame_poses, frame_px=(0.2, 0.2))
     for dtype in (dare.DARE_F32, dare.DARE_U8):
-        s = rebuilt(w, dtype, K, first=10)
+        s = rebuilt(w, dtype, K, first=10, flags=dare.DARE_SESSION_HOST_VOLUME if host else 0)
         check_against_oracle(s, w, dtype, K)
         assert oracle_volume(w, dtype, 12).n_overflow > 0  # more than 12 samples, so more than 8 entries
         s.close()
