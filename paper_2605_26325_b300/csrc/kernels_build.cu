@@ -4,11 +4,12 @@
 // order.
 //
 // Pipeline per chunk of frames:
-//   count  -- each CTA takes a 32 x 32 pixel tile of one frame and sums its
-//             pixels per voxel in shared memory: a direct-mapped box of the
-//             tile's voxels (one packed 32-bit add per voxel a thread's 2 x 2
-//             pixel block reaches) when that box is small, a hash table
-//             otherwise.  Every (voxel, tile) entry takes a slot from the
+//   count  -- each CTA takes a 32 x 64 pixel region of one frame (two 2 x 2
+//             pixel blocks a thread; a 32 x 32 tile when the build lists the
+//             voxels it reaches) and sums its pixels per voxel in shared
+//             memory: a direct-mapped box of the region's voxels (one packed
+//             32-bit add per voxel a 2 x 2 block reaches) when that box is
+//             small, a hash table otherwise.  Every (voxel, tile) entry takes a slot from the
 //             voxel's counter; the first kBucket entries of a voxel go straight
 //             into its bucket, later ones (rare) to the tile's overflow list;
 //   scan   -- exclusive prefix sum of the overflow counts max(count - kBucket, 0)
@@ -37,8 +38,8 @@ constexpr int kThreads = 256;         // a 2 x 2 pixel block per thread
 #ifndef DARE_COUNT_MIN_BLOCKS
 #define DARE_COUNT_MIN_BLOCKS 6  // 40 registers: faster than 5 CTAs at 46
 #endif
-#ifndef DARE_COUNT_MIN_BLOCKS_FULL
-#define DARE_COUNT_MIN_BLOCKS_FULL 7  // without the touched list (4 KB less shared memory), 32 registers
+#ifndef DARE_COUNT2_MIN_BLOCKS
+#define DARE_COUNT2_MIN_BLOCKS 6  // 32 x 64 regions: 40 registers (a few spills), faster than 5 at 48 or 7 at 32
 #endif
 constexpr int kHash = 2048;           // >= 2 x pixels per tile: never full
 constexpr int kEmptyKey = -1;
@@ -251,7 +252,7 @@ __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long lo
 // voxels this build reaches for the first time are listed: touched[i], and
 // tindex[v] = i, i < *n_touched.
 template <bool kTouched>
-__global__ void __launch_bounds__(kThreads, kTouched ? DARE_COUNT_MIN_BLOCKS : DARE_COUNT_MIN_BLOCKS_FULL)
+__global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS)
     k_scatter_count(const __grid_constant__ ScatterArgs A,
                                                             int32_t* __restrict__ count,
                                                             unsigned long long* __restrict__ buckets,
@@ -368,6 +369,170 @@ __global__ void __launch_bounds__(kThreads, kTouched ? DARE_COUNT_MIN_BLOCKS : D
             touched[new_base + k] = v;
             tindex[v] = new_base + k;
         }
+    }
+}
+
+// The full-rebuild form of the count pass: one CTA per 32 x 64 pixel region of
+// a frame (two 32-row halves, a 2 x 2 block of each per thread), so the set-up
+// (affine, origins, box clear, tile box) and the three barriers serve 2048
+// pixels.  Each half has its own fixed-point origin, so the int32 pixel steps
+// stay within the range of the 32-row form.  Boxes past kBoxCells take the
+// hash table one half at a time (at most kTile^2 keys per pass).  The packed
+// box accumulator holds npix <= 2048 above bit 19 and sum <= 2048 x 255 below.
+// No touched list: used where the count pass need not list new voxels.
+constexpr int kRows2 = 2 * kTile;
+constexpr int kPackShift2 = 19;
+
+// Corner coordinates from the origin of the half a corner lies in (small steps).
+__device__ void tile_box2(const int64_t* aff, const int4* org, const int4* org2, bool small_steps, const int* dims,
+                          int u0, int v0, int u1, int v1, TileBox& B) {
+    const int lane = threadIdx.x & 31;
+    const int k = lane / 3, a = lane < 12 ? lane % 3 : 0;
+    const int u = (k & 1) ? u1 : u0, v = (k & 2) ? v1 : v0;
+    int64_t q = 0;
+    if (lane < 12) {
+        if (small_steps) {
+            const bool hi = v >= v0 + kTile;
+            const int4 o = hi ? org2[a] : org[a];
+            q = o.x + ((o.y + (u - u0) * o.z + (v - v0 - (hi ? kTile : 0)) * o.w) >> kFixBits);
+        } else {
+            q = (aff[a] + static_cast<int64_t>(u) * aff[3 + a] + static_cast<int64_t>(v) * aff[6 + a] + kFixOne / 2) >>
+                kFixBits;
+        }
+    }
+    const int64_t q3 = __shfl_down_sync(0xFFFFFFFFu, q, 3), q6 = __shfl_down_sync(0xFFFFFFFFu, q, 6);
+    const int64_t q9 = __shfl_down_sync(0xFFFFFFFFu, q, 9);
+    const int64_t lo_a = min(min(q, q3), min(q6, q9)), hi_a = max(max(q, q3), max(q6, q9));
+    int64_t lo[3], hi[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        lo[i] = __shfl_sync(0xFFFFFFFFu, lo_a, i);
+        hi[i] = __shfl_sync(0xFFFFFFFFu, hi_a, i);
+    }
+    if (lane != 0) return;
+    int64_t cells = 1;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        const int64_t l = lo[i] < 0 ? 0 : lo[i];
+        const int64_t h = hi[i] > dims[i] - 1 ? dims[i] - 1 : hi[i];
+        const int64_t n = h >= l ? h - l + 1 : 0;
+        B.b[i] = static_cast<int>(l < dims[i] ? l : 0);
+        B.n[i] = static_cast<int>(n);
+        cells *= n;
+    }
+    B.cells = cells > kBoxCells ? INT_MAX : static_cast<int>(cells);
+}
+
+__global__ void __launch_bounds__(kThreads, DARE_COUNT2_MIN_BLOCKS)
+    k_scatter_count2(const __grid_constant__ ScatterArgs A, int32_t* __restrict__ count,
+                     unsigned long long* __restrict__ buckets, uint4* __restrict__ pairs,
+                     int32_t* __restrict__ n_pairs) {
+    __shared__ __align__(16) unsigned smem[kSmemWords];
+    __shared__ int64_t aff[9];
+    __shared__ int4 org[2][3];  // small steps: each half's origin per axis (integer part, remainder, steps)
+    __shared__ TileBox B;
+    __shared__ int n_list;
+    const int f = blockIdx.z;
+    const int u0 = blockIdx.x * kTile, v0 = blockIdx.y * kRows2;
+    if (threadIdx.x < 9) aff[threadIdx.x] = A.affines[9 * static_cast<int64_t>(f) + threadIdx.x];
+    if (A.small_steps && threadIdx.x >= 32 && threadIdx.x < 38) {  // (warp 0 sets up the box later)
+        const int a = (threadIdx.x - 32) % 3, h = (threadIdx.x - 32) / 3;
+        const int64_t* af = A.affines + 9 * static_cast<int64_t>(f);
+        const int64_t ga = af[3 + a], gb = af[6 + a];
+        const int64_t G = af[a] + static_cast<int64_t>(u0) * ga + static_cast<int64_t>(v0 + h * kTile) * gb + kFixOne / 2;
+        const int64_t F = G >> kFixBits;
+        org[h][a] = make_int4(static_cast<int>(F < -(1 << 24) ? -(1 << 24) : (F > (1 << 24) ? (1 << 24) : F)),
+                              static_cast<int>(G & (kFixOne - 1)), static_cast<int>(ga), static_cast<int>(gb));
+    }
+    if (threadIdx.x == 0) n_list = 0;
+    BlockPixels P0, P1;
+    block_values(A, f, u0, v0, P0);  // both halves' pixels in flight during the set-up
+    block_values(A, f, u0, v0 + kTile, P1);
+    uint4* c4 = reinterpret_cast<uint4*>(smem);
+    for (int i = threadIdx.x; i < kBoxCells / 4; i += kThreads) c4[i] = make_uint4(0u, 0u, 0u, 0u);
+    __syncthreads();
+    if (threadIdx.x < 32)
+        tile_box2(aff, org[0], org[1], A.small_steps != 0, A.dims, u0, v0, min(u0 + kTile, A.width) - 1,
+                  min(v0 + kRows2, A.height) - 1, B);
+    block_voxels(A, aff, org[0], u0, v0, P0);  // (the second half's voxels once the first half is summed)
+    __syncthreads();
+    const int cells = B.cells;
+    if (cells == 0) return;  // no pixel of the region lands in the grid
+    const unsigned long long fid = static_cast<unsigned long long>(A.frame_base + f) << 48;
+    if (cells <= kBoxCells) {
+        const int b0 = B.b[0], b1 = B.b[1], b2 = B.b[2], n0 = B.n[0], n1 = B.n[1];
+        auto add = [&](int k, unsigned n, unsigned sm) { atomicAdd(smem + k, (n << kPackShift2) | sm); };
+        int key[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) key[q] = P0.in[q] ? (P0.c[q][0] - b0) + n0 * ((P0.c[q][1] - b1) + n1 * (P0.c[q][2] - b2)) : -1;
+        block_combine(key, P0.val, add);
+        block_voxels(A, aff, org[1], u0, v0 + kTile, P1);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) key[q] = P1.in[q] ? (P1.c[q][0] - b0) + n0 * ((P1.c[q][1] - b1) + n1 * (P1.c[q][2] - b2)) : -1;
+        block_combine(key, P1.val, add);
+        __syncthreads();
+        const int64_t d0 = A.dims[0], d01 = static_cast<int64_t>(A.dims[0]) * A.dims[1];
+        const float inv01 = 1.0f / static_cast<float>(n0 * n1), inv0 = 1.0f / static_cast<float>(n0);
+        for (int r = 0; r < cells; r += 4 * kThreads) {
+            int vi[4];
+            unsigned long long e[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int idx = r + j * kThreads + threadIdx.x;
+                const unsigned x = idx < cells ? smem[idx] : 0u;
+                vi[j] = -1;
+                e[j] = 0;
+                if (x) {
+                    const int i2 = static_cast<int>((static_cast<float>(idx) + 0.5f) * inv01);
+                    const int rem = idx - i2 * (n0 * n1);
+                    const int i1 = static_cast<int>((static_cast<float>(rem) + 0.5f) * inv0), i0 = rem - i1 * n0;
+                    vi[j] = static_cast<int>((b0 + i0) + d0 * (b1 + i1) + d01 * (b2 + i2));
+                    e[j] = fid | (static_cast<unsigned long long>(x >> kPackShift2) << 32) | (x & ((1u << kPackShift2) - 1));
+                }
+            }
+            emit4(vi, e, count, buckets, pairs, n_pairs, nullptr, nullptr);
+        }
+    } else {
+        // hash table over voxel indices, one half at a time
+        int* keys = reinterpret_cast<int*>(smem);
+        unsigned* npx = smem + kHash;
+        unsigned* sums = smem + 2 * kHash;
+        int* list = reinterpret_cast<int*>(smem + 3 * kHash);
+        uint4* keys4 = reinterpret_cast<uint4*>(keys);
+        uint4* both4 = reinterpret_cast<uint4*>(npx);
+        static_assert(kEmptyKey == -1, "keys cleared to all-ones words");
+        auto hash_half = [&](const BlockPixels& P) {
+            for (int i = threadIdx.x; i < kHash / 4; i += kThreads) keys4[i] = make_uint4(~0u, ~0u, ~0u, ~0u);
+            for (int i = threadIdx.x; i < kHash / 2; i += kThreads) both4[i] = make_uint4(0u, 0u, 0u, 0u);
+            if (threadIdx.x == 0) n_list = 0;
+            int key[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) key[q] = P.in[q] ? P.c[q][0] + A.dims[0] * (P.c[q][1] + A.dims[1] * P.c[q][2]) : -1;
+            __syncthreads();  // table cleared
+            block_combine(key, P.val, [&](int k, unsigned n, unsigned sm) { hash_add(keys, npx, sums, list, &n_list, k, n, sm); });
+            __syncthreads();
+            const int n = n_list;
+            for (int r = 0; r < n; r += 4 * kThreads) {
+                int vi[4];
+                unsigned long long e[4];
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int i = r + j * kThreads + threadIdx.x;
+                    vi[j] = -1;
+                    e[j] = 0;
+                    if (i < n) {
+                        const int hh = list[i];
+                        vi[j] = keys[hh];
+                        e[j] = fid | (static_cast<unsigned long long>(npx[hh]) << 32) | sums[hh];
+                    }
+                }
+                emit4(vi, e, count, buckets, pairs, n_pairs, nullptr, nullptr);
+            }
+            __syncthreads();  // the list and table are read before the next half clears them
+        };
+        hash_half(P0);
+        block_voxels(A, aff, org[1], u0, v0 + kTile, P1);
+        hash_half(P1);
     }
 }
 
@@ -1110,9 +1275,9 @@ cudaError_t launch_scatter_count(const ScatterArgs& a, int32_t* count, unsigned 
     if (touched)
         k_scatter_count<true><<<scatter_grid(a), kThreads, 0, st>>>(a, count, buckets, pairs, n_pairs, touched, tindex,
                                                                     n_touched);
-    else
-        k_scatter_count<false><<<scatter_grid(a), kThreads, 0, st>>>(a, count, buckets, pairs, n_pairs, nullptr,
-                                                                     nullptr, nullptr);
+    else  // every voxel's list is visited anyway: the 32 x 64 form
+        k_scatter_count2<<<dim3((a.width + kTile - 1) / kTile, (a.height + kRows2 - 1) / kRows2, a.n), kThreads, 0,
+                           st>>>(a, count, buckets, pairs, n_pairs);
     return cudaPeekAtLastError();
 }
 
