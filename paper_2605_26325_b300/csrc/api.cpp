@@ -349,13 +349,14 @@ struct dare_session_s {
     void* host_vol = nullptr;              // DARE_SESSION_HOST_VOLUME: the mapped host block
     void* ws = nullptr;
     size_t ws_bytes = 0;
-    // pinned host staging: [0] frame affines / rotations of a build, [1..8] batch
-    // descriptors, used in turn so the host can run a few batches ahead
-    static constexpr int kPinSlots = 9;
+    // pinned host staging: [0] and [9] frame affines / rotations of builds in
+    // turn, [1..8] batch descriptors in turn, so the host can run a few calls ahead
+    static constexpr int kPinSlots = 10;
     void* pinned[kPinSlots] = {};
     size_t pinned_bytes[kPinSlots] = {};
     cudaEvent_t pinned_ev[kPinSlots] = {};  // last copy out of each staging buffer
     int next_desc = 0;
+    int next_build = 0;
     cudaEvent_t order_ev = nullptr;        // end of the session's last queued call
     cudaStream_t last_stream = nullptr;
     // host-buffer calls: a two-slot upload ring (build) and a two-slot download
@@ -1609,7 +1610,10 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                           {s->ring_free[0], s->ring_free[1], s->ring_full[0], s->ring_full[1]}, st);
         if (rc != DARE_OK) return rc;
     }
-    rc = ensure_pinned(s, 0, size_t(n) * (9 * 8 * 2 + kGeomFloats * 4 + 2 * 8));
+    // two staging buffers in turn, so the host can queue a build while the
+    // previous one's upload is still waiting on the stream
+    const int bpin = (s->next_build++ & 1) ? 9 : 0;
+    rc = ensure_pinned(s, bpin, size_t(n) * (9 * 8 * 2 + kGeomFloats * 4 + 2 * 8));
     if (rc != DARE_OK) return rc;
     uint8_t* ws = static_cast<uint8_t*>(s->ws);
     int32_t* offsets = reinterpret_cast<int32_t*>(ws + o_off);
@@ -1623,7 +1627,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
     int32_t* t_index = reinterpret_cast<int32_t*>(ws + o_ti);
     int32_t* t_ovf = reinterpret_cast<int32_t*>(ws + o_tc);
     int32_t* t_n = reinterpret_cast<int32_t*>(ws + o_tn);
-    uint8_t* pin = static_cast<uint8_t*>(s->pinned[0]);
+    uint8_t* pin = static_cast<uint8_t*>(s->pinned[bpin]);
     const size_t p_rot = aff.size() * 8, p_geo = p_rot + rot.size() * 8, p_off = p_geo + grow.size() * 4;
     std::memcpy(pin, aff.data(), aff.size() * 8);
     std::memcpy(pin + p_rot, rot.data(), rot.size() * 8);
@@ -1636,7 +1640,7 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                              cudaMemcpyHostToDevice, st));
     CUDA_TRY(cudaMemcpyAsync(s->geom_off_dev + size_t(s->n_frames) * 2, pin + p_off, goff.size() * 8,
                              cudaMemcpyHostToDevice, st));
-    CUDA_TRY(cudaEventRecord(s->pinned_ev[0], st));
+    CUDA_TRY(cudaEventRecord(s->pinned_ev[bpin], st));
     for (int32_t c0 = 0; c0 < n; c0 += n_chunk) {
         const int32_t nc = std::min(n_chunk, n - c0);
         ScatterArgs a{};
