@@ -380,7 +380,7 @@ def run_dare(args, dist):
     P, W, H = args.poses, w.out_w, w.out_h
     dtype = DTYPE_NAMES[args.dtype]
     s = dare.Session(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, dtype=dtype, max_slots=args.slots,
-                     device=dev, flags=0 if args.quick else dare.DARE_SESSION_SCALAR)
+                     device=dev)  # the comparators' totals are kept by a session of their own (extras)
     curv_apex = (0.0, -40.0) if args.probe == "curvilinear" else None
     if curv_apex is not None:
         s.set_probe(dare.DARE_PROBE_CURVILINEAR, curv_apex)
@@ -759,7 +759,12 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
         s.build(frames_d, w.frame_poses, w.frame_px, stream)
 
     ms_build = timed(build_only, 5)
-    ms_scalar = timed(lambda: [s.reslice_scalar(w.reslice_poses[i], outs[i], masks[i], w.out_px, stream=stream)
+    # the comparators' session: the same volume plus the mean-compounding totals
+    # (kept apart so that the timed step rebuilds only what DARE reslices)
+    sc = dare.Session(w.grid.dims, w.grid.spacing, w.grid.vol_to_world, dtype=DTYPE_NAMES[args.dtype],
+                      max_slots=args.slots, device=dist.local, flags=dare.DARE_SESSION_SCALAR)
+    sc.build(frames_d, w.frame_poses, w.frame_px, stream)
+    ms_scalar = timed(lambda: [sc.reslice_scalar(w.reslice_poses[i], outs[i], masks[i], w.out_px, stream=stream)
                                for i in range(P)], 2)
     px = P * W * H
     line["paths_mpix_s"] = {"tiled_batched": px / ms_tiled / 1e3, "plain_fp32_batched": px / ms_plain / 1e3,
@@ -881,7 +886,8 @@ def extras(args, dist, dare, torch, s, w, stream, frames_d, outs, masks, reqs, p
     # NCC / SSIM against the acquired image, on rendered data): the phantom
     # rendered at the virtual probe's pose vs DARE and the mean-compounding
     # (orientation-blind, trilinear) comparator, over the pixels both cover
-    line["quality"] = quality(dare, torch, s, w, stream, tiled)
+    line["quality"] = quality(dare, torch, sc, w, stream, tiled)
+    sc.close()
 
     line["latency"] = {"tiled": lat(tiled), "plain_fp32": lat(plain),
                        "note": "wall time from the host call to the 512x512 image and mask on the device, "
