@@ -103,3 +103,27 @@ def test_rebuild_equals_fresh_build(tiny):
     assert np.array_equal(ra["values"].view(np.uint32), rb["values"].view(np.uint32))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("case", ["large_boxes", "large_steps"])
+def test_rebuild_fine_grids(tiny, case):
+    """Voxels much finer than pixels.  At 2.5 voxels per pixel a 32 x 64 frame
+    region spans a voxel box far past 4096 cells, so the count pass sums it in
+    the hash table, one 32-row band at a time; at about 36 voxels per pixel the
+    pixel steps exceed 2^25 in fixed point, so pixel coordinates are evaluated in
+    int64 instead of int32 steps from each band's origin.  A reset + rebuild
+    and a build into a new session both equal the oracle."""
+    if case == "large_boxes":
+        g = synth.centred_grid((96, 96, 96), 0.1)
+    else:
+        g = synth.centred_grid((160, 160, 160), 0.006)
+    w = types.SimpleNamespace(grid=g, frames=tiny.frames, frame_poses=tiny.frame_poses, frame_px=tiny.frame_px)
+    s = rebuilt(w, dare.DARE_F32, 8)
+    e = check_against_oracle(s, w, dare.DARE_F32, 8)
+    assert e["tot_npix"].sum() > 0
+    s.close()
+    fresh = dare.Session(g.dims, g.spacing, g.vol_to_world, dtype=dare.DARE_F32, max_slots=8,
+                         flags=dare.DARE_SESSION_SCALAR)
+    fresh.build(torch.from_numpy(np.ascontiguousarray(tiny.frames)).to(DEV), tiny.frame_poses, tiny.frame_px)
+    check_against_oracle(fresh, w, dare.DARE_F32, 8)
+    fresh.close()
