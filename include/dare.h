@@ -310,7 +310,10 @@ dare_status dare_session_create(const dare_session_config* cfg, dare_session* ou
 /* Wait for the session's queued work, then free everything it holds. */
 dare_status dare_session_destroy(dare_session s);
 
-/* Wait for the session's queued work; report a device-side failure. */
+/* Wait for the session's queued work; report a device-side failure.  The
+ * calling thread first polls the completion of the session's last call for up
+ * to 200 microseconds (a preview loop waiting on one plane resumes as soon as
+ * it is ready, without a blocking wait's wake-up), then blocks. */
 dare_status dare_session_sync(dare_session s);
 
 dare_status dare_session_query(dare_session s, dare_session_info* out);

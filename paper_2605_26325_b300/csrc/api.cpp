@@ -6,6 +6,7 @@
 // canonical FP64 evaluation order documented in dare.h.
 #include <algorithm>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -1465,6 +1466,17 @@ dare_status dare_session_destroy(dare_session s) {
 dare_status dare_session_sync(dare_session s) {
     if (!s) return fail(DARE_E_INVALID, "session is NULL");
     DeviceGuard dg(s->cfg.device);
+    // poll first (short waits resume at once), then block
+    const auto t0 = std::chrono::steady_clock::now();
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(s->order_ev);
+        if (e == cudaSuccess) return DARE_OK;
+        if (e != cudaErrorNotReady) {
+            cudaGetLastError();
+            return fail(DARE_E_CUDA, "device failure: %s", cudaGetErrorString(e));
+        }
+        if (std::chrono::steady_clock::now() - t0 > std::chrono::microseconds(200)) break;
+    }
     CUDA_TRY(cudaEventSynchronize(s->order_ev));
     return DARE_OK;
 }
