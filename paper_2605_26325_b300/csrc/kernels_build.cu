@@ -9,9 +9,10 @@
 //             voxels it reaches) and sums its pixels per voxel in shared
 //             memory: a direct-mapped box of the region's voxels (one packed
 //             32-bit add per voxel a 2 x 2 block reaches) when that box is
-//             small, a hash table otherwise.  Every (voxel, tile) entry takes a slot from the
-//             voxel's counter; the first kBucket entries of a voxel go straight
-//             into its bucket, later ones (rare) to the tile's overflow list;
+//             small, a hash table otherwise.  Every (voxel, region) entry
+//             takes a slot from the voxel's counter; the first kBucket entries
+//             of a voxel go straight into its bucket, later ones (rare) to the
+//             overflow list;
 //   scan   -- exclusive prefix sum of the overflow counts max(count - kBucket, 0)
 //             (kernels.cu);
 //   place  -- every overflow pair writes its entry into its voxel's overflow
@@ -20,7 +21,9 @@
 //             range) by frame id (a frame split across tiles has several),
 //             appends the new samples after the stored ones (their ids are all
 //             lower), applies the capacity rule when more than K samples exist,
-//             and returns the counter to zero.
+//             and returns the counter to zero.  After a reset every voxel is
+//             written; voxels with entries past their bucket are left to a
+//             second kernel (a thread each, no barrier).
 // Integer sums make the result independent of scheduling order.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -372,8 +375,9 @@ __global__ void __launch_bounds__(kThreads, DARE_COUNT_MIN_BLOCKS)
     }
 }
 
-// The full-rebuild form of the count pass: one CTA per 32 x 64 pixel region of
-// a frame (two 32-row halves, a 2 x 2 block of each per thread), so the set-up
+// The count pass of builds that do not list the voxels they reach (full
+// rebuilds, large appends): one CTA per 32 x 64 pixel region of a frame (two
+// 32-row halves, a 2 x 2 block of each per thread), so the set-up
 // (affine, origins, box clear, tile box) and the three barriers serve 2048
 // pixels.  Each half has its own fixed-point origin, so the int32 pixel steps
 // stay within the range of the 32-row form.  Boxes past kBoxCells take the
