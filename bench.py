@@ -482,7 +482,8 @@ def run_dare(args, dist):
         roof["roofline_frac"] = max(t_hbm, t_l2) / t_launch
     # the reconstruction as a whole (count + scan + place + finalize): its method's
     # bytes are the frames read and every voxel's record data and npix row written
-    build_kernels = ("scatter_count", "exclusive_scan", "scatter_place", "finalize", "finalize_deferred")
+    build_kernels = ("scatter_count", "exclusive_scan", "overflow_alloc", "scatter_place", "finalize",
+                     "finalize_deferred")
     build_ms = sum(trace[k][1] for k in build_kernels if k in trace) / args.steps
     n_vox = int(np.prod(w.grid.dims))
     build_bytes = float(w.frames.size + n_vox * rec_data + n_vox * args.slots * 2)

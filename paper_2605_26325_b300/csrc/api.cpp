@@ -1674,7 +1674,9 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
         int32_t* ti = listed ? t_index : nullptr;
         int32_t* tn = listed ? t_n : nullptr;
         if (listed || mode == 2) CUDA_TRY(cudaMemsetAsync(t_n, 0, sizeof(int32_t), st));
-        CUDA_TRY(cudaMemsetAsync(n_pairs, 0, sizeof(int32_t), st));  // the chunk's overflow list starts empty
+        // the chunk's overflow list starts empty (and, in the full-write mode, the cursor of
+        // its overflow ranges, n_pairs[1])
+        CUDA_TRY(cudaMemsetAsync(n_pairs, 0, 2 * sizeof(int32_t), st));
         if (!host) {
             KernelScope ks("scatter_count", st, 1);
             CUDA_TRY(launch_scatter_count(a, s->count, buckets, pairs, n_pairs, tl, ti, tn, st));
@@ -1701,15 +1703,24 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
                 CUDA_TRY(cudaEventRecord(s->ring_free[b], st));
             }
         }
-        if (listed) {
-            KernelScope ks("exclusive_scan", st, 4);
-            CUDA_TRY(launch_touched_overflow(s->count, t_list, t_n, max_t, t_ovf, st));
-            CUDA_TRY(launch_exclusive_scan(t_ovf, offsets, max_t, bsums, nbs, 0, st));
+        if (mode == 2) {
+            // full write: an overflow range for each voxel past its bucket only, no scan of
+            // every counter; the counters keep every entry for the finalize passes
+            {
+                KernelScope ks("overflow_alloc", st, 1);
+                CUDA_TRY(launch_overflow_alloc(pairs, n_pairs, s->count, offsets, n_pairs + 1, st));
+            }
+            KernelScope ks("scatter_place", st, 1);
+            CUDA_TRY(launch_overflow_place(pairs, n_pairs, offsets, entries, st));
         } else {
-            KernelScope ks("exclusive_scan", st, 3);
-            CUDA_TRY(launch_exclusive_scan(s->count, offsets, s->n_vox, bsums, nbs, kBucket, st));
-        }
-        {
+            if (listed) {
+                KernelScope ks("exclusive_scan", st, 4);
+                CUDA_TRY(launch_touched_overflow(s->count, t_list, t_n, max_t, t_ovf, st));
+                CUDA_TRY(launch_exclusive_scan(t_ovf, offsets, max_t, bsums, nbs, 0, st));
+            } else {
+                KernelScope ks("exclusive_scan", st, 3);
+                CUDA_TRY(launch_exclusive_scan(s->count, offsets, s->n_vox, bsums, nbs, kBucket, st));
+            }
             KernelScope ks("scatter_place", st, 1);
             CUDA_TRY(launch_scatter_place(a, pairs, n_pairs, s->count, offsets, ti, entries, st));
         }
@@ -1720,17 +1731,18 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
             }
             s->pending_clear = false;  // a full-write finalize (mode 2) writes every voxel
             s->fresh = false;          // from here on the records may hold samples
-            // a full write lists the voxels with entries past their bucket in the touched
-            // list (unused in that mode) for its second kernel
+            // a full write lists the voxels with entries past their bucket, and their entry
+            // counts, in the touched list and its counts (unused in that mode) for its second kernel
             {
                 KernelScope ks("finalize", st, 1);
                 CUDA_TRY(launch_finalize(s->count, buckets, offsets, entries, s->n_vox, s->rec, s->npix, s->ssum,
                                          s->scnt, s->K, s->dtype, mode, s->host_vol ? 0 : 1, s->overflow_dev, tl, tn,
-                                         max_t, mode == 2 ? t_list : nullptr, mode == 2 ? t_n : nullptr, st));
+                                         max_t, mode == 2 ? t_list : nullptr, mode == 2 ? t_ovf : nullptr,
+                                         mode == 2 ? t_n : nullptr, st));
             }
             if (mode == 2) {
                 KernelScope ks("finalize_deferred", st, 1);
-                CUDA_TRY(launch_finalize_deferred(t_list, t_n, buckets, offsets, entries, s->rec, s->npix, s->ssum,
+                CUDA_TRY(launch_finalize_deferred(t_list, t_ovf, t_n, buckets, offsets, entries, s->rec, s->npix, s->ssum,
                                                   s->scnt, s->K, s->dtype, s->overflow_dev, max_t, st));
             }
         }

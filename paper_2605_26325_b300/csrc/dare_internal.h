@@ -153,16 +153,28 @@ int64_t scan_block_sums_needed(int64_t n);
 // a voxel's entries: count[v] (<= kBucket) in its bucket, then entries[offsets[v], offsets[v + 1]);
 // count is returned to zero
 // touched / n_touched (modes 0 and 1): only the listed voxels, offsets by list position, at most max_t
-// deferred / n_deferred (mode 2; *n_deferred zero on entry, room for every voxel with entries past its
-// bucket): the full-write pass lists such voxels and leaves them empty for launch_finalize_deferred
+// deferred / deferred_cnt / n_deferred (mode 2; *n_deferred zero on entry, room for every voxel with
+// entries past its bucket): the full-write pass lists such voxels with their entry counts, clears
+// their counters and leaves their records empty for launch_finalize_deferred;
+// in mode 2 the counters hold every entry (launch_overflow_alloc / _place instead of scan and place)
 cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, const int32_t* offsets,
                             const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
                             uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
                             unsigned long long* overflow, const int32_t* touched, const int32_t* n_touched,
-                            int64_t max_t, int32_t* deferred, int32_t* n_deferred, cudaStream_t st);
+                            int64_t max_t, int32_t* deferred, int32_t* deferred_cnt, int32_t* n_deferred,
+                            cudaStream_t st);
+// full-write mode (after a reset), in place of the scan and the counting-down place pass: each
+// voxel with entries past its bucket gets a range of count - kBucket overflow entries starting at
+// offsets[v] (reserved from *cursor, zero on entry; other offsets are not written) ...
+cudaError_t launch_overflow_alloc(const uint4* pairs, const int32_t* n_pairs, const int32_t* count, int32_t* offsets,
+                                  int32_t* cursor, cudaStream_t st);
+// ... and every overflow pair's entry goes to its range by its slot; the counters keep every
+// voxel's entry count
+cudaError_t launch_overflow_place(const uint4* pairs, const int32_t* n_pairs, const int32_t* offsets,
+                                  unsigned long long* entries, cudaStream_t st);
 // the voxels a full-write finalize listed (at most max_items), one thread each: record, npix row,
-// scalar totals and the capacity-rule count, as the full-write pass would have written them
-cudaError_t launch_finalize_deferred(const int32_t* deferred, const int32_t* n_deferred,
+// scalar totals and the capacity-rule count from all deferred_cnt[i] of the voxel's entries
+cudaError_t launch_finalize_deferred(const int32_t* deferred, const int32_t* deferred_cnt, const int32_t* n_deferred,
                                      const unsigned long long* buckets, const int32_t* offsets,
                                      const unsigned long long* entries, uint8_t* rec, uint16_t* npix,
                                      uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,

@@ -241,8 +241,8 @@ __device__ __forceinline__ void emit4(const int (&vi)[4], const unsigned long lo
             if (s_new && slot[j] == 0) s_new[atomicAdd(s_n_new, 1)] = vi[j];  // one per distinct voxel of the tile
         } else {
             const int k = atomicAdd(n_ovf, 1);  // at most one pair per pixel of the chunk
-            ovf[k] = make_uint4(static_cast<unsigned>(vi[j]), 0u, static_cast<unsigned>(e[j]),
-                                static_cast<unsigned>(e[j] >> 32));
+            ovf[k] = make_uint4(static_cast<unsigned>(vi[j]), static_cast<unsigned>(slot[j]),
+                                static_cast<unsigned>(e[j]), static_cast<unsigned>(e[j] >> 32));
         }
     }
 }
@@ -568,6 +568,66 @@ __global__ void __launch_bounds__(256) k_scatter_place(const uint4* __restrict__
         const uint4 p = __ldg(pairs + i);
         const int pos = offsets[tindex ? tindex[p.x] : p.x] + atomicSub(count + p.x, 1) - 1 - kBucket;
         entries[pos] = (static_cast<unsigned long long>(p.w) << 32) | p.z;
+    }
+}
+
+// Full-write mode (after a reset): each voxel with entries past its bucket gets
+// an overflow range of count - kBucket entries, reserved by the one pair that
+// took the voxel's first slot past the bucket; a CTA scans its pairs' lengths
+// and takes its share of the cursor with one atomic.  The ranges' starts go to
+// offsets[v] (other voxels' offsets are not written).  This replaces the scan
+// of every voxel's counter that appends need.
+__global__ void __launch_bounds__(256) k_overflow_alloc(const uint4* __restrict__ pairs,
+                                                        const int32_t* __restrict__ n_pairs,
+                                                        const int32_t* __restrict__ count,
+                                                        int32_t* __restrict__ offsets, int32_t* __restrict__ cursor) {
+    __shared__ int s_warp[8];
+    __shared__ int s_base;
+    const int64_t n = *n_pairs;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int64_t i0 = static_cast<int64_t>(blockIdx.x) * 256; i0 < n; i0 += static_cast<int64_t>(gridDim.x) * 256) {
+        const int64_t i = i0 + threadIdx.x;
+        int len = 0;
+        unsigned v = 0;
+        if (i < n) {
+            const uint4 p = __ldg(pairs + i);
+            if (p.y == kBucket) {
+                v = p.x;
+                len = count[v] - kBucket;
+            }
+        }
+        int x = len;  // inclusive warp scan
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const int y = __shfl_up_sync(0xFFFFFFFFu, x, d);
+            if (lane >= d) x += y;
+        }
+        if (lane == 31) s_warp[warp] = x;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            int total = 0;
+            for (int k = 0; k < 8; ++k) total += s_warp[k];
+            s_base = total ? atomicAdd(cursor, total) : 0;
+        }
+        __syncthreads();
+        int base = s_base;
+        for (int k = 0; k < warp; ++k) base += s_warp[k];
+        if (len) offsets[v] = base + x - len;
+        __syncthreads();  // s_warp and s_base are rewritten by the next round
+    }
+}
+
+// Full-write mode: every overflow pair's entry at its voxel's range start plus
+// (its slot - kBucket).
+__global__ void __launch_bounds__(256) k_overflow_place(const uint4* __restrict__ pairs,
+                                                        const int32_t* __restrict__ n_pairs,
+                                                        const int32_t* __restrict__ offsets,
+                                                        unsigned long long* __restrict__ entries) {
+    const int64_t n = *n_pairs;
+    for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const uint4 p = __ldg(pairs + i);
+        entries[offsets[p.x] + static_cast<int>(p.y) - kBucket] = (static_cast<unsigned long long>(p.w) << 32) | p.z;
     }
 }
 
@@ -993,6 +1053,7 @@ __global__ void __launch_bounds__(256, 6) k_finalize_full(int32_t* __restrict__ 
                                                        uint16_t* __restrict__ npix, uint32_t* __restrict__ scal_sum,
                                                        uint32_t* __restrict__ scal_cnt,
                                                        unsigned long long* overflow, int32_t* __restrict__ deferred,
+                                                       int32_t* __restrict__ deferred_cnt,
                                                        int32_t* __restrict__ n_deferred) {
     constexpr int RB = (2 * K + K * static_cast<int>(sizeof(VT)) + 15) / 16 * 16;
     __shared__ __align__(128) uint4 s_rec[256 * RB / 16];
@@ -1006,35 +1067,31 @@ __global__ void __launch_bounds__(256, 6) k_finalize_full(int32_t* __restrict__ 
             empty_record<K, RB>(my_rec);
 #pragma unroll
             for (int i = 0; i < K / 4; ++i) my_np[i] = make_uint2(0u, 0u);
-            // the counter and the whole bucket in one round trip; after the
-            // place pass c = min(entries, kBucket), and a voxel has overflow
-            // entries (its offsets differ) only when its bucket is full
-            const int c = count[v];
+            // the counter (all of the voxel's entries: in this mode the place
+            // pass does not count it down) and the whole bucket in one round trip
+            const int n_all = count[v];
             ulonglong2 b[kBucket / 2];
             bucket_load(buckets + v * kBucket, b);
             uint32_t tot_sum = 0, tot_cnt = 0;
             bool over = false;
-            if (c > 0) {
-                int s = 0, e = 0;
-                if (c == kBucket) {
-                    s = offsets[v];
-                    e = offsets[v + 1];
-                }
-                const VoxelEntries E{buckets + v * kBucket, entries, c, s, c + (e - s)};
+            if (n_all > kBucket) {
+                // entries past the bucket (rare, clustered): left to k_finalize_deferred, a
+                // thread per voxel, so that no thread holds its CTA at the barrier below; the
+                // empty record written here is overwritten there.  The list takes the voxel and
+                // its entry count; the counter is cleared here, with the others.
+                const int i = atomicAdd(n_deferred, 1);
+                deferred[i] = static_cast<int32_t>(v);
+                deferred_cnt[i] = n_all;
+                count[v] = 0;
+            } else if (n_all > 0) {
+                const VoxelEntries E{buckets + v * kBucket, entries, n_all, 0, n_all};
                 count[v] = 0;
                 uint16_t* ids = reinterpret_cast<uint16_t*>(my_rec);
                 VT* vals = reinterpret_cast<VT*>(reinterpret_cast<uint8_t*>(my_rec) + 2 * K);
                 uint16_t* np = reinterpret_cast<uint16_t*>(my_np);
-                if (E.n == c) {
-                    unsigned long long ev[kBucket];
-                    bucket_sort(b, c, ev);
-                    over = voxel_merge_sorted<K, VT>(E, ev, 0, ids, vals, np, tot_sum, tot_cnt);
-                } else {
-                    // entries past the bucket (rare, clustered): left to k_finalize_deferred, one
-                    // warp per voxel, so that no thread holds its CTA at the barrier below;
-                    // the empty record written here is overwritten there
-                    deferred[atomicAdd(n_deferred, 1)] = static_cast<int32_t>(v);
-                }
+                unsigned long long ev[kBucket];
+                bucket_sort(b, n_all, ev);
+                over = voxel_merge_sorted<K, VT>(E, ev, 0, ids, vals, np, tot_sum, tot_cnt);
             }
             if (!whole) {
                 uint4* g_rec = reinterpret_cast<uint4*>(rec + v * RB);
@@ -1105,6 +1162,7 @@ __device__ __forceinline__ void sort16(unsigned long long (&e)[kDeferSort]) {
 
 template <int K, typename VT>
 __global__ void __launch_bounds__(256) k_finalize_deferred(const int32_t* __restrict__ deferred,
+                                                         const int32_t* __restrict__ deferred_cnt,
                                                          const int32_t* __restrict__ n_deferred,
                                                          const unsigned long long* __restrict__ buckets,
                                                          const int32_t* __restrict__ offsets,
@@ -1124,7 +1182,7 @@ __global__ void __launch_bounds__(256) k_finalize_deferred(const int32_t* __rest
     const int n_items = *n_deferred;
     for (int it = blockIdx.x * blockDim.x + threadIdx.x; it < n_items; it += gridDim.x * blockDim.x) {
         const int64_t v = deferred[it];
-        const int s0 = offsets[v], n = kBucket + (offsets[v + 1] - s0);
+        const int n = deferred_cnt[it], s0 = offsets[v];  // all entries; the first kBucket in the bucket
         empty_record<K, RB>(my_rec);
 #pragma unroll
         for (int i = 0; i < K / 4; ++i) my_np[i] = make_uint2(0u, 0u);
@@ -1169,19 +1227,20 @@ __global__ void __launch_bounds__(256) k_finalize_deferred(const int32_t* __rest
 template <int K, typename VT>
 cudaError_t finalize_full_v(int32_t* cnt, const unsigned long long* bk, const int32_t* off,
                             const unsigned long long* ent, int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss,
-                            uint32_t* sc, unsigned long long* ovf, bool bulk, int32_t* dl, int32_t* dn,
+                            uint32_t* sc, unsigned long long* ovf, bool bulk, int32_t* dl, int32_t* dc, int32_t* dn,
                             cudaStream_t st) {
     const int64_t want = (n_vox + 255) / 256;
     const int blocks = static_cast<int>(want < (1 << 30) ? want : (1 << 30));  // one run per CTA
     if (bulk)
-        k_finalize_full<K, VT, true><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, dl, dn);
+        k_finalize_full<K, VT, true><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, dl, dc, dn);
     else
-        k_finalize_full<K, VT, false><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, dl, dn);
+        k_finalize_full<K, VT, false><<<blocks, 256, 0, st>>>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, dl, dc, dn);
     return cudaPeekAtLastError();
 }
 
 template <int K, typename VT>
-cudaError_t finalize_deferred_v(const int32_t* dl, const int32_t* dn, const unsigned long long* bk, const int32_t* off,
+cudaError_t finalize_deferred_v(const int32_t* dl, const int32_t* dc, const int32_t* dn, const unsigned long long* bk,
+                                const int32_t* off,
                                 const unsigned long long* ent, uint8_t* rec, uint16_t* npix, uint32_t* ss,
                                 uint32_t* sc, unsigned long long* ovf, int64_t max_items, cudaStream_t st) {
     static int sms[64] = {};
@@ -1192,20 +1251,20 @@ cudaError_t finalize_deferred_v(const int32_t* dl, const int32_t* dn, const unsi
     // a thread per listed voxel up to 16 CTAs of 256 per SM, then grid-stride
     const int64_t want = std::max<int64_t>(1, (max_items + 255) / 256);
     const int blocks = static_cast<int>(std::min<int64_t>(want, int64_t(sms[dev]) * 16));
-    k_finalize_deferred<K, VT><<<blocks, 256, 0, st>>>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf);
+    k_finalize_deferred<K, VT><<<blocks, 256, 0, st>>>(dl, dc, dn, bk, off, ent, rec, npix, ss, sc, ovf);
     return cudaPeekAtLastError();
 }
 
 template <int K>
-cudaError_t finalize_deferred_k(const int32_t* dl, const int32_t* dn, const unsigned long long* bk, const int32_t* off,
+cudaError_t finalize_deferred_k(const int32_t* dl, const int32_t* dc, const int32_t* dn, const unsigned long long* bk, const int32_t* off,
                                 const unsigned long long* ent, uint8_t* rec, uint16_t* npix, uint32_t* ss,
                                 uint32_t* sc, int dtype, unsigned long long* ovf, int64_t max_items, cudaStream_t st) {
     switch (dtype) {
-    case DARE_U8: return finalize_deferred_v<K, uint8_t>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
-    case DARE_F16: return finalize_deferred_v<K, __half>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
+    case DARE_U8: return finalize_deferred_v<K, uint8_t>(dl, dc, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
+    case DARE_F16: return finalize_deferred_v<K, __half>(dl, dc, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
     case DARE_BF16:
-        return finalize_deferred_v<K, __nv_bfloat16>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
-    case DARE_F32: return finalize_deferred_v<K, float>(dl, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
+        return finalize_deferred_v<K, __nv_bfloat16>(dl, dc, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
+    case DARE_F32: return finalize_deferred_v<K, float>(dl, dc, dn, bk, off, ent, rec, npix, ss, sc, ovf, max_items, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -1244,16 +1303,16 @@ template <int K>
 cudaError_t finalize_k(int32_t* cnt, const unsigned long long* bk, const int32_t* off, const unsigned long long* ent,
                        int64_t n_vox, uint8_t* rec, uint16_t* npix, uint32_t* ss, uint32_t* sc, int dtype, int mode,
                        int bulk, unsigned long long* ovf, const int32_t* tl, const int32_t* tn, int64_t max_t,
-                       int32_t* dl, int32_t* dn, cudaStream_t st) {
-    if (mode == 2 && (tl || !dl || !dn)) return cudaErrorInvalidValue;  // a full write visits every voxel
+                       int32_t* dl, int32_t* dc, int32_t* dn, cudaStream_t st) {
+    if (mode == 2 && (tl || !dl || !dc || !dn)) return cudaErrorInvalidValue;  // a full write visits every voxel
     if (mode == 2) {
         const bool b = bulk != 0;
         switch (dtype) {
-        case DARE_U8: return finalize_full_v<K, uint8_t>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dn, st);
-        case DARE_F16: return finalize_full_v<K, __half>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dn, st);
+        case DARE_U8: return finalize_full_v<K, uint8_t>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dc, dn, st);
+        case DARE_F16: return finalize_full_v<K, __half>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dc, dn, st);
         case DARE_BF16:
-            return finalize_full_v<K, __nv_bfloat16>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dn, st);
-        case DARE_F32: return finalize_full_v<K, float>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dn, st);
+            return finalize_full_v<K, __nv_bfloat16>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dc, dn, st);
+        case DARE_F32: return finalize_full_v<K, float>(cnt, bk, off, ent, n_vox, rec, npix, ss, sc, ovf, b, dl, dc, dn, st);
         }
         return cudaErrorInvalidValue;
     }
@@ -1307,16 +1366,38 @@ cudaError_t launch_scatter_place(const ScatterArgs& a, const uint4* pairs, const
     return cudaPeekAtLastError();
 }
 
-cudaError_t launch_finalize_deferred(const int32_t* deferred, const int32_t* n_deferred,
+cudaError_t launch_overflow_alloc(const uint4* pairs, const int32_t* n_pairs, const int32_t* count, int32_t* offsets,
+                                  int32_t* cursor, cudaStream_t st) {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    k_overflow_alloc<<<sms[dev] * 2, 256, 0, st>>>(pairs, n_pairs, count, offsets, cursor);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_overflow_place(const uint4* pairs, const int32_t* n_pairs, const int32_t* offsets,
+                                  unsigned long long* entries, cudaStream_t st) {
+    static int sms[64] = {};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    if (!sms[dev] && cudaDeviceGetAttribute(&sms[dev], cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return cudaErrorInvalidDevice;
+    k_overflow_place<<<sms[dev] * 2, 256, 0, st>>>(pairs, n_pairs, offsets, entries);
+    return cudaPeekAtLastError();
+}
+
+cudaError_t launch_finalize_deferred(const int32_t* deferred, const int32_t* deferred_cnt, const int32_t* n_deferred,
                                      const unsigned long long* buckets, const int32_t* offsets,
                                      const unsigned long long* entries, uint8_t* rec, uint16_t* npix,
                                      uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype,
                                      unsigned long long* overflow, int64_t max_items, cudaStream_t st) {
     switch (K) {
-    case 4: return finalize_deferred_k<4>(deferred, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
-    case 8: return finalize_deferred_k<8>(deferred, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
-    case 12: return finalize_deferred_k<12>(deferred, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
-    case 16: return finalize_deferred_k<16>(deferred, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
+    case 4: return finalize_deferred_k<4>(deferred, deferred_cnt, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
+    case 8: return finalize_deferred_k<8>(deferred, deferred_cnt, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
+    case 12: return finalize_deferred_k<12>(deferred, deferred_cnt, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
+    case 16: return finalize_deferred_k<16>(deferred, deferred_cnt, n_deferred, buckets, offsets, entries, rec, npix, scal_sum, scal_cnt, dtype, overflow, max_items, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -1325,16 +1406,17 @@ cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, c
                             const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
                             uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
                             unsigned long long* overflow, const int32_t* touched, const int32_t* n_touched,
-                            int64_t max_t, int32_t* deferred, int32_t* n_deferred, cudaStream_t st) {
+                            int64_t max_t, int32_t* deferred, int32_t* deferred_cnt, int32_t* n_deferred, cudaStream_t st) {
     int32_t* dl = deferred;
+    int32_t* dc = deferred_cnt;
     int32_t* dn = n_deferred;
     const int32_t* tl = touched;
     const int32_t* tn = n_touched;
     switch (K) {
-    case 4: return finalize_k<4>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dn, st);
-    case 8: return finalize_k<8>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dn, st);
-    case 12: return finalize_k<12>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dn, st);
-    case 16: return finalize_k<16>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dn, st);
+    case 4: return finalize_k<4>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dc, dn, st);
+    case 8: return finalize_k<8>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dc, dn, st);
+    case 12: return finalize_k<12>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dc, dn, st);
+    case 16: return finalize_k<16>(count, buckets, offsets, entries, n_vox, rec, npix, scal_sum, scal_cnt, dtype, mode, bulk, overflow, tl, tn, max_t, dl, dc, dn, st);
     }
     return cudaErrorInvalidValue;
 }
