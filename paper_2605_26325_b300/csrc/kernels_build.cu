@@ -17,6 +17,10 @@
 //             (kernels.cu);
 //   place  -- every overflow pair writes its entry into its voxel's overflow
 //             range (tiles without overflow return at once);
+//   (after a reset, alloc + place instead: the pair holding a voxel's first
+//             entry past its bucket reserves the voxel's range from a cursor,
+//             then every pair writes its entry at its slot in that range, and
+//             the counters keep the full counts);
 //   finalize -- one thread per voxel groups its entries (bucket, then overflow
 //             range) by frame id (a frame split across tiles has several),
 //             appends the new samples after the stored ones (their ids are all
