@@ -410,11 +410,17 @@ def run_dare(args, dist):
     dist.barrier()
     torch.cuda.synchronize()
     dare.trace_read()
-    dare.trace_counters(reset=True)
-    dare.trace_enable(True)
+    dare.trace_counters(reset=True)  # (reads a device counter: synchronises)
     clocks = ClockSampler(dev)
     clocks.start()
-    time.sleep(0.1)
+    # untimed steps while the sampler starts: a GPU left idle for that long comes
+    # back to the timed region slower (about 0.05 ms a step on a B300); nothing
+    # between them and the timed steps waits for the device
+    t_warm, n_warm = time.perf_counter(), 0
+    while time.perf_counter() - t_warm < 0.15:
+        step()
+        n_warm += 1
+    dare.trace_enable(True)
     n0 = dare.launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -503,7 +509,9 @@ def run_dare(args, dist):
             "gpu_launches": int(launches),
             "roofline": roof,
             "build_roofline": build_roof,
-            "path_counters": counters,
+            "path_counters": dict(counters, steps=args.steps + n_warm,
+                                  note="planes by path over the timed steps and the untimed steps run while "
+                                       "the clock sampler starts"),
             "kernels_ms_per_step": {k: v[1] / args.steps for k, v in sorted(trace.items())}}
 
     if not args.quick:
