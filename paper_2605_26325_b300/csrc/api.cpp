@@ -1735,8 +1735,11 @@ dare_status build_impl(dare_session s, const uint8_t* frames, bool host, int32_t
             // counts, in the touched list and its counts (unused in that mode) for its second kernel
             {
                 KernelScope ks("finalize", st, 1);
+                // fewer than 8 pixels per voxel: most buckets are empty (1600 frames of 256 x 512
+                // into 256^3 give 12.5 and 83 % of the voxels covered; 400 frames give 3.1)
+                const int sparse = int64_t(nc) * npx < 8 * s->n_vox ? 1 : 0;
                 CUDA_TRY(launch_finalize(s->count, buckets, offsets, entries, s->n_vox, s->rec, s->npix, s->ssum,
-                                         s->scnt, s->K, s->dtype, mode, s->host_vol ? 0 : 1, s->overflow_dev, tl, tn,
+                                         s->scnt, s->K, s->dtype, mode, s->host_vol ? 0 : 1, sparse, s->overflow_dev, tl, tn,
                                          max_t, mode == 2 ? t_list : nullptr, mode == 2 ? t_ovf : nullptr,
                                          mode == 2 ? t_n : nullptr, st));
             }

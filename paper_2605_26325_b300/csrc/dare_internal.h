@@ -150,6 +150,8 @@ int64_t scan_block_sums_needed(int64_t n);
 // reset since), stored records are not read; 2: as 1 and not cleared since a reset:
 // every voxel's record, npix row and scalar totals are written (empty where no entry)
 // bulk: records and npix in device memory, so mode 2 may store whole runs with bulk copies
+// sparse (mode 2 with bulk): few pixels per voxel, most buckets empty: a bucket is read only as far as
+// its counter says (a second round trip) instead of together with the counter
 // a voxel's entries: count[v] (<= kBucket) in its bucket, then entries[offsets[v], offsets[v + 1]);
 // count is returned to zero
 // touched / n_touched (modes 0 and 1): only the listed voxels, offsets by list position, at most max_t
@@ -160,7 +162,7 @@ int64_t scan_block_sums_needed(int64_t n);
 cudaError_t launch_finalize(int32_t* count, const unsigned long long* buckets, const int32_t* offsets,
                             const unsigned long long* entries, int64_t n_vox, uint8_t* rec, uint16_t* npix,
                             uint32_t* scal_sum, uint32_t* scal_cnt, int K, int dtype, int mode, int bulk,
-                            unsigned long long* overflow, const int32_t* touched, const int32_t* n_touched,
+                            int sparse, unsigned long long* overflow, const int32_t* touched, const int32_t* n_touched,
                             int64_t max_t, int32_t* deferred, int32_t* deferred_cnt, int32_t* n_deferred,
                             cudaStream_t st);
 // full-write mode (after a reset), in place of the scan and the counting-down place pass: each
