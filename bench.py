@@ -213,6 +213,31 @@ def profiled_counters(kernel, n_slices):
     return out
 
 
+def build_source_hash():
+    """Hash of what the reconstruction kernels are built from (their source and
+    the internal header)."""
+    csrc = os.path.join(ROOT, "paper_2605_26325_b300", "csrc")
+    h = hashlib.sha256()
+    for f in ("kernels_build.cu", "dare_internal.h"):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def build_counters(n_frames):
+    """Per-launch DRAM bytes of the count and full-write finalize kernels from the
+    committed ncu summary of the full rebuild; None when the sources changed since
+    the counters were taken or the rebuild is not the one captured."""
+    path = os.path.join(ROOT, "profiles", "build_kernels_dram_traffic.txt")
+    try:
+        kv = dict(line.split("=", 1) for line in open(path).read().split("\n") if "=" in line and not line.startswith("#"))
+        if kv.get("src_sha256_16", "").strip() != build_source_hash() or int(kv["frames"]) != n_frames:
+            return None
+        return {k: float(kv[f"{k}_dram_bytes"]) for k in ("scatter_count", "finalize")}
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def host_cores():
     """Host threads this process may run on (its CPU affinity), as nproc reports."""
     try:
@@ -500,6 +525,14 @@ def run_dare(args, dist):
                           "whole); intermediate pair and entry lists are not the method's bytes"}
     if build_roof["achieved"]:
         build_roof["frac"] = build_roof["achieved"] / peak
+    # DRAM bytes the two large build kernels move (ncu, one launch each), against
+    # their CUDA-event launch times here
+    bc = build_counters(len(w.frames))
+    build_roof["traffic"] = None if bc is None else {
+        k: {"dram_bytes": v, "launch_ms": trace[k][1] / max(trace[k][0], 1),
+            "dram_gbs": v / (trace[k][1] / max(trace[k][0], 1) * 1e-3) / 1e9,
+            "dram_frac": v / (trace[k][1] / max(trace[k][0], 1) * 1e-3) / 1e9 / peak}
+        for k, v in bc.items() if k in trace}
     line = {"metric": METRIC, "value": value, "unit": "Mpix/s", "n_gpus": dist.world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
