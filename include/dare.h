@@ -196,7 +196,10 @@ typedef struct {
  * them.  Meant for volumes under about 100 MB.  The window is set on the
  * caller's stream for the library's own launches and the stream's previous
  * window is restored before the call returns.  Not applied on the legacy
- * default (NULL) stream or inside plans. */
+ * default (NULL) stream or inside plans.  Destroying such a session returns
+ * every persisting L2 line of the device context to normal, so that the freed
+ * records keep no share of L2 from later kernels; another such session's
+ * records are marked again by its next reslice. */
 #define DARE_SESSION_L2_PERSIST 2
 /* Keep the records, npix and scalar totals in page-locked host memory mapped
  * into the device's address space instead of device memory, for volumes

@@ -1409,6 +1409,11 @@ dare_status dare_session_destroy(dare_session s) {
         if (s->pinned_ev[k]) cudaEventSynchronize(s->pinned_ev[k]);
     if (s->sp_exec) cudaGraphExecDestroy(s->sp_exec);
     if (s->sp_graph) cudaGraphDestroy(s->sp_graph);
+    // lines marked persisting stay so after the records are freed and would keep
+    // their share of L2 from every later kernel; this returns all of the context's
+    // persisting lines to normal (another persisting session's lines are marked
+    // again by its next call)
+    if ((s->cfg.flags & DARE_SESSION_L2_PERSIST) && cudaCtxResetPersistingL2Cache() != cudaSuccess) cudaGetLastError();
     if (s->ws) {
         s->dev_free(s->ws, s->ws_bytes, s->last_stream);
         g_in_use -= static_cast<int64_t>(s->ws_bytes);
